@@ -1,0 +1,467 @@
+#!/usr/bin/env python3
+"""Benchmark of the segmented-NCC hot path on GB300.
+
+Workload (default "hd"): a 1920 x 1080 uint8 source (blobs plus 1/f noise)
+and a 64 x 64 template cropped from it with sigma-3 noise, std thresholds
+5, 10 and 20 swept, coarse precision 0.85 (tau_c = 0.85 * rho_max), exact
+refine threshold 0.85.  One step = one pass of the whole path over the source:
+the sum tables once, then for each threshold the coarse pass (segmented NCC
+map, threshold, candidates) and the exact refine of the candidates.  The
+metric counts offsets evaluated: 3 * U * V per step.
+
+Printed: one JSON line (rank 0).  Timing: CUDA events on the launching stream
+around every step, an L2 flush (a 256 MiB write) between steps outside the
+events, a barrier and synchronize on both sides of the timed region, the max
+over ranks.  --impl reference times the FP64 CPU oracle on a bounded sample
+of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "segmented-NCC Goffsets/s vs exact NCC on same GB300 at stated max |dNCC|"
+UNIT = "Goffsets/s"
+SIGMAS = (5.0, 10.0, 20.0)
+PRECISION = 0.85
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["sncc", "reference"], default="sncc")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; no collective on the data path)
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "sncc" else "gloo"
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, value: float) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, value: float) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.time(), ln.strip()))
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [ln for (ts, ln) in self.lines if self.t0 is not None and self.t0 <= ts <= (self.t1 or ts) + 0.1]
+        if not rows:
+            rows = [ln for (_, ln) in self.lines]
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in rows:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 10:
+                continue
+            try:
+                sm.append(float(p[2]))
+                smax.append(float(p[3]))
+                power.append(float(p[4]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[6:10]):
+                if val == "Active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(case, sigmas, rows_per_sigma, seed=0):
+    """Runs the oracle's version of one step on `rows_per_sigma` offset rows
+    per threshold: sum tables + segmented NCC (Eq. 10 - 18) on those rows,
+    candidates, exact refine.  Returns (offsets, seconds, threads, maps)."""
+    import oracle as O
+    f, t = case.f, case.t
+    N, M = f.shape
+    H, W = t.shape
+    U, V = M - W + 1, N - H + 1
+    rng = np.random.default_rng(seed)
+    threads = O.default_threads()
+    total, secs, maps = 0, 0.0, {}
+    for s in sigmas:
+        ap = O.precompute_template_approximation(t, s)
+        rows = np.sort(rng.choice(V, size=min(rows_per_sigma, V), replace=False))
+        t0 = time.perf_counter()
+        rho = O.segmented_ncc_map(f, ap, "sat", rows=rows, nthreads=threads)
+        cand = O.candidates(rho, PRECISION * ap.rho_max)
+        O.refine(f, t, cand, U, PRECISION)
+        secs += time.perf_counter() - t0
+        total += len(rows) * U
+        maps[s] = (rows, rho)
+    return total, secs, threads, maps
+
+
+def calibrate_rows(case, budget_s: float) -> int:
+    _, secs, _, _ = oracle_sample(case, SIGMAS, 2, seed=12345)
+    per_row = secs / (2 * len(SIGMAS))
+    return max(1, int(budget_s / (per_row * len(SIGMAS))))
+
+
+def run_reference(args, world, rank, pg):
+    """The reference arm: the FP64 CPU oracle as it stands, timed on the host
+    cores, each step a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    from paper_2502_01286_gb300 import synth
+    case = synth.case_hd()
+    N, M = case.f.shape
+    H, W = case.t.shape
+    U, V = M - W + 1, N - H + 1
+    budget_total = 150.0
+    rows = calibrate_rows(case, budget_total / max(1, args.steps + args.warmup))
+    for i in range(args.warmup):
+        oracle_sample(case, SIGMAS, rows, seed=i)
+    offsets, secs, threads = 0, 0.0, 1
+    for i in range(args.steps):
+        o, s, threads, _ = oracle_sample(case, SIGMAS, rows, seed=1000 + i)
+        offsets += o
+        secs += s
+    value = offsets / secs / 1e9
+    sample = "%d random offset rows x %d offsets per threshold per step (of %d rows), thresholds %s" % (
+        rows, U, V, list(SIGMAS))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(case, U, V),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(case, U, V):
+    N, M = case.f.shape
+    H, W = case.t.shape
+    return {"workload": "hd-%dx%d-t%dx%d-sigma5-10-20" % (M, N, W, H), "source": [M, N], "template": [W, H],
+            "sigma_max": list(SIGMAS), "precision": PRECISION, "offsets_per_step": 3 * U * V,
+            "l2": "flushed between steps (256 MiB write)", "sum_tables": "s int32, s2 int64"}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("sncc_match.cu", "sncc_ptx.cuh", "sncc_internal.h"):
+        with open(os.path.join(ROOT, "paper_2502_01286_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch of the segment-sum kernel from a committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "match_kernel_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_hash") != kernel_hash() or d.get("workload") != workload:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_gpu(args, world, rank, local, pg):
+    import torch
+    from paper_2502_01286_gb300 import build as lib_build
+    if rank == 0 or not os.path.exists(lib_build.LIB):
+        lib_build.build()
+    barrier(pg)
+    from paper_2502_01286_gb300 import sncc, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    case = synth.case_hd(seed=synth.BASE_SEED + 1 + rank)  # independent problem per rank
+    N, M = case.f.shape
+    H, W = case.t.shape
+    U, V = M - W + 1, N - H + 1
+    offsets_per_step = len(SIGMAS) * U * V
+
+    # --- preparation (host template approximation, plans, buffers) ---
+    t_prep = time.perf_counter()
+    segs = [sncc.build_segments(case.t, s) for s in SIGMAS]
+    prep_s = time.perf_counter() - t_prep
+    fd = torch.as_tensor(case.f).to(dev)
+    td = torch.as_tensor(case.t).to(dev)
+    plans = [sncc.upload_plan(s, dev) for s in segs]
+    tables = sncc.alloc_tables(M, N, None, dev)
+    ws = sncc.integral_workspace(M, N, dev)
+    cand_cap, out_cap = U * V, 1 << 16
+    mbs = [sncc.alloc_match(M, N, W, H, cand_cap, True, dev) for _ in SIGMAS]
+    rbs = [sncc.alloc_refine(out_cap, dev) for _ in SIGMAS]
+    taus = [PRECISION * s.rho_max for s in segs]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    match_ev = []
+
+    def step(record_match=False):
+        sncc.integral(fd, tables, workspace=ws)
+        for i, s in enumerate(segs):
+            if record_match:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            sncc.match(s, plans[i], tables, taus[i], mbs[i])
+            if record_match:
+                b.record(stream)
+                match_ev.append((i, a, b))
+            sncc.refine(fd, td, s, mbs[i], PRECISION, rbs[i])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks.mark_start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        starts[k].record(stream)
+        step(record_match=True)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    wall = time.perf_counter() - wall0
+    clocks.mark_end()
+    clk = clocks.stop()
+    ms_steps = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms_per_step = max_over_ranks(pg, sum(ms_steps) / args.steps)
+    status = [int(m.status.item()) for m in mbs]
+    counts = [int(m.count.item()) for m in mbs]
+    nmatch = [int(r.nout.item()) for r in rbs]
+
+    # per-kernel time of the segment-sum launches (same stream, same region)
+    per_sigma_ms = {i: [] for i in range(len(SIGMAS))}
+    for i, a, b in match_ev:
+        per_sigma_ms[i].append(a.elapsed_time(b))
+
+    # --- end to end through the public API with host buffers ---
+    f_host = torch.as_tensor(case.f).pin_memory()
+    e2e_steps = max(3, min(args.steps, 200))
+    h2d = f_host.numel()
+    d2h_total = 0
+    e2e_ms = []
+    for k in range(args.warmup + e2e_steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fd.copy_(f_host, non_blocking=True)
+        step()
+        counts_h = torch.cat([r.nout for r in rbs]).cpu()
+        got = 4 * len(rbs)
+        for r, c in zip(rbs, counts_h.tolist()):
+            n = min(int(c), r.cap)
+            if n:
+                r.out[:n].cpu()
+                got += 12 * n
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_ms.append(1e3 * (t1 - t0))
+            d2h_total += got
+    e2e_ms_step = max_over_ranks(pg, statistics.mean(e2e_ms))
+
+    # --- the same-GPU comparator: exact NCC map ---
+    exact_rho = torch.empty((V, U), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        sncc.exact_map(fd, td, segs[0].T, segs[0].T2, tables, exact_rho)
+    ex_ms = []
+    for k in range(10):
+        flush.fill_(k)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sncc.exact_map(fd, td, segs[0].T, segs[0].T2, tables, exact_rho)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ex_ms.append(a.elapsed_time(b))
+    exact_ms = statistics.median(ex_ms)
+    max_dncc = [float((m.rho - exact_rho).abs().max().item()) for m in mbs]
+
+    # --- shared-memory read roofline of the segment-sum kernel ---
+    sink = torch.empty(152 * 8 * 256, dtype=torch.int32, device=dev)
+    sncc.probe_smem_read(sink, 152 * 8, 64)
+    smem_gbs = []
+    for _ in range(5):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nbytes = sncc.probe_smem_read(sink, 152 * 8, 2048)
+        b.record(stream)
+        torch.cuda.synchronize()
+        smem_gbs.append(nbytes / (a.elapsed_time(b) * 1e-3) / 1e9)
+    smem_peak = max(smem_gbs)
+
+    # dominant kernel: the segment-sum launch with the most corners
+    infos = [s.plan_info() for s in segs]
+    dom = max(range(len(SIGMAS)), key=lambda i: infos[i]["corners"])
+    dom_ms = statistics.mean(per_sigma_ms[dom])
+    dom_bytes = U * V * infos[dom]["corners"] * 4  # one 32-bit shared load per (offset, corner)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+
+    value = sum_over_ranks(pg, offsets_per_step) / (ms_per_step * 1e-3) / 1e9
+    e2e_value = sum_over_ranks(pg, offsets_per_step) / (e2e_ms_step * 1e-3) / 1e9
+
+    cpu = None
+    oracle_check = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = calibrate_rows(case, args.cpu_seconds)
+        offs, secs, threads, maps = oracle_sample(case, SIGMAS, rows, seed=7)
+        cpu = {"value": offs / secs / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d random offset rows x %d offsets per threshold (of %d rows), thresholds %s; "
+                         "sum tables + segmented NCC + candidates + exact refine" % (rows, U, V, list(SIGMAS)),
+               "seconds": secs}
+        errs = []
+        for i, s in enumerate(SIGMAS):
+            rws, rho = maps[s]
+            g = mbs[i].rho[torch.as_tensor(rws, device=dev)].cpu().numpy().astype(np.float64)
+            errs.append(float(np.abs(g - rho[rws]).max()))
+        oracle_check = {"max_abs_drho_vs_oracle": max(errs), "rows_checked": int(rows) * len(SIGMAS)}
+
+    peaks = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic", "config": workload_config(case, U, V),
+        "exact_ncc": {"value": U * V / (exact_ms * 1e-3) / 1e9, "unit": UNIT, "ms": exact_ms,
+                      "kernel": "direct integer correlation, CUDA cores"},
+        "speedup_vs_exact": value / (U * V / (exact_ms * 1e-3) / 1e9),
+        "max_abs_dncc_vs_exact": dict(zip([str(s) for s in SIGMAS], max_dncc)),
+        "per_sigma": [{"sigma_max": s, "K": seg.K, "corners": infos[i]["corners"], "rho_max": seg.rho_max,
+                       "tau_c": taus[i], "match_ms": statistics.mean(per_sigma_ms[i]),
+                       "candidates": counts[i], "matches": nmatch[i], "status": status[i],
+                       "goffsets_s_coarse": U * V / (statistics.mean(per_sigma_ms[i]) * 1e-3) / 1e9}
+                      for i, (s, seg) in enumerate(zip(SIGMAS, segs))],
+        "prep_s": prep_s,
+        "roofline": {"bound": "smem", "kernel": "match_kernel", "sigma_max": SIGMAS[dom], "achieved": achieved,
+                     "peak": smem_peak, "unit": "GB/s", "frac": achieved / smem_peak,
+                     "traffic": recorded_traffic("hd"), "bytes_per_launch": dom_bytes, "ms_per_launch": dom_ms,
+                     "peak_source": "measured: shared-memory read probe (all SMs), this run",
+                     "hbm_peak_gbs": peaks.get("hbm_gbs")},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h_total / e2e_steps, "ms_per_step": e2e_ms_step},
+        "gpu_launches": args.steps * (3 + 3 * len(SIGMAS)),
+        "clocks": clk, "wall_s_timed": wall,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if oracle_check is not None:
+        line["oracle_check"] = oracle_check
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+    else:
+        run_gpu(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

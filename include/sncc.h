@@ -1,0 +1,280 @@
+/*
+ * sncc.h - C ABI of the GB300 segmented-NCC library (libsncc.so).
+ *
+ * Method: Marusic, Popovic, Kalafatic, "Template Matching in Images using
+ * Segmented Normalized Cross-Correlation" (arXiv 2502.01286).
+ *
+ * Conventions (paper Section 2)
+ *   Source f: M x N pixels (M columns, N rows), uint8, row-major with a row
+ *   stride in bytes, pixel (x, y) at f[y * f_stride + x].
+ *   Template t: W x H pixels, uint8, t[y * t_stride + x].
+ *   Offsets (u, v) in {0..M-W} x {0..N-H} (main algorithm, step 7):
+ *   U = M-W+1 columns and V = N-H+1 rows of offsets, linear index v*U + u.
+ *
+ * Memory and ownership
+ *   Every pointer named d_* is device memory owned by the caller.  The
+ *   library never allocates device memory and never frees caller memory.
+ *   sncc_segments is host memory owned by the library (sncc_free_segments).
+ *   Scratch space is passed in as a caller-owned workspace whose size the
+ *   matching *_workspace_bytes call returns.
+ *
+ * Streams and errors
+ *   Device entry points are asynchronous on the given stream (NULL = the
+ *   legacy default stream).  Each returns SNCC_OK or a negative SNCC_ERR_*
+ *   code for errors found on the host (bad arguments, launch failures).
+ *   Errors found on the device (capacity overflow, a bounded wait that ran
+ *   out) are OR-ed as SNCC_STATUS_* bits into a caller-owned int32 status
+ *   word, which the caller reads after synchronising the stream; the calls
+ *   that take one clear it first, in stream order.
+ *
+ * Thread safety: calls are reentrant; concurrent calls must not share
+ * output buffers or workspaces.
+ */
+#ifndef SNCC_H
+#define SNCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t / CUstream); NULL selects the default stream. */
+typedef struct CUstream_st* sncc_stream_t;
+
+/* Host-side return codes. */
+#define SNCC_OK 0
+#define SNCC_ERR_ARG (-1)       /* bad argument: null pointer, size, stride, bits */
+#define SNCC_ERR_UNIFORM (-2)   /* uniform template or zero-energy approximation (Section 2) */
+#define SNCC_ERR_DTYPE (-3)     /* a 32-bit table was requested where sums can reach 2^31 */
+#define SNCC_ERR_CAPACITY (-4)  /* a host-visible capacity is too small */
+#define SNCC_ERR_CUDA (-5)      /* a CUDA runtime call or kernel launch failed */
+#define SNCC_ERR_WORKSPACE (-6) /* workspace missing, misaligned or too small */
+#define SNCC_ERR_NOMEM (-7)     /* host allocation failed */
+#define SNCC_ERR_UNSUPPORTED (-8) /* size outside what this build supports */
+
+/* Device status bits (OR-ed into the caller's int32 status word). */
+#define SNCC_STATUS_CAND_OVERFLOW 1  /* more candidates than cand_cap; count is still exact */
+#define SNCC_STATUS_MATCH_OVERFLOW 2 /* more matches than out_cap; count is still exact */
+#define SNCC_STATUS_WAIT_TIMEOUT 4   /* a bounded wait on an asynchronous copy ran out */
+#define SNCC_STATUS_SORT_OVERFLOW 8  /* more matches than the sort scratch holds */
+
+/* Human-readable text of a return code (static storage). */
+const char* sncc_error_string(int code);
+
+/* ------------------------------------------------------------------ */
+/* Template preparation (host)                                         */
+/* ------------------------------------------------------------------ */
+
+/* One rectangular segment S_i, the 5-tuple of Eq. 6 plus its exact sum. */
+typedef struct {
+    int32_t x, y;  /* top-left corner in template coordinates */
+    int32_t w, h;  /* width W_i and height H_i */
+    int64_t sum;   /* exact sum of t over the rectangle */
+    double mean;   /* k_i = sum / (w*h), Eq. 4 (double, correctly rounded) */
+} sncc_seg;
+
+/* The segmented approximation k of a template (Section 3). */
+typedef struct {
+    sncc_seg* seg;      /* K segments, ascending (y, x); owned by the library */
+    int32_t K;          /* number of segments after merging */
+    int32_t K_split;    /* number of segments split_segment produced */
+    int32_t W, H;       /* template size */
+    double sigma_used;  /* sigma_max of the last split (after K_max raises) */
+    double kbar;        /* Eq. 7: mean of k (equal to the template mean) */
+    double Ek;          /* energy of k: sum_i W_i H_i (k_i - kbar)^2 */
+    double rho_max;     /* NCC(t, k) by steps 5-7 of precompute_template_approximation */
+    int64_t T, T2;      /* sum of t and of t^2 (exact) */
+    double err_bound;   /* bound on |rho_gpu - rho| from weight quantisation */
+    void* plan;         /* library-private matching plan (host memory) */
+} sncc_segments;
+
+/*
+ * sncc_build_segments - split-and-merge template approximation.
+ * Paper: Section 3 (Eq. 2 - Eq. 7) and Section 5, functions
+ * precompute_template_approximation, split_segment, merge_redundant_segments.
+ *
+ *   t, W, H, t_stride  host template (uint8, row stride in bytes >= W)
+ *   sigma_max          std threshold of Eq. 2 (segments need std < sigma_max,
+ *                      evaluated as n*S2 - S^2 < n^2 sigma_max^2 with the
+ *                      segment's exact sum S, sum of squares S2, size n)
+ *   k_max              segment cap; > 0 repeats the split with sigma_max + 1
+ *                      until K_split <= k_max (steps 1-2); 0 = no cap
+ *   out                receives the approximation (overwritten; call
+ *                      sncc_free_segments when done)
+ * Also builds the matching plan: fixed-point segment weights and the
+ * per-block corner lists sncc_match reads (see sncc_plan_bytes).
+ * Returns SNCC_OK, SNCC_ERR_ARG, SNCC_ERR_UNSUPPORTED (W*H > 2^23) or
+ * SNCC_ERR_NOMEM.  A uniform template is not an error here (K = 1, Ek = 0);
+ * sncc_match reports it.
+ */
+int sncc_build_segments(const uint8_t* t, int W, int H, int t_stride, double sigma_max, int k_max,
+                        sncc_segments* out);
+
+/* Releases what sncc_build_segments allocated; safe on a zeroed struct. */
+void sncc_free_segments(sncc_segments* s);
+
+/* ------------------------------------------------------------------ */
+/* Sum tables (GPU)                                                    */
+/* ------------------------------------------------------------------ */
+
+/* Row pitch, in elements, of the padded sum tables for an M-wide source:
+ * the smallest multiple of 32 that is >= M+1. */
+int sncc_sat_pitch(int M);
+
+/* Scratch bytes sncc_integral needs for an M x N source. */
+size_t sncc_integral_workspace_bytes(int M, int N);
+
+/*
+ * sncc_integral - sum tables of f and f^2 (Eq. 10 and Eq. 14).
+ *
+ *   d_f, M, N, f_stride  device source (uint8), f_stride >= M bytes
+ *   d_s                  output, (N+1) rows x sat_pitch elements of int32
+ *                        (s_bits = 32) or int64 (s_bits = 64); entry
+ *                        [Y * pitch + X] = sum of f over x < X, y < Y, so row
+ *                        0 and column 0 are zero and [(y+1)*pitch + (x+1)]
+ *                        is s(x, y) of Eq. 10.  Columns beyond M are not
+ *                        written.
+ *   d_s2                 output, the same layout in int64, for f^2 (Eq. 14)
+ *   sat_pitch            row pitch in elements, >= sncc_sat_pitch(M) and a
+ *                        multiple of 4
+ *   d_ws, ws_bytes       workspace, >= sncc_integral_workspace_bytes(M, N),
+ *                        16-byte aligned
+ * s_bits = 32 needs 255*M*N < 2^31 (else SNCC_ERR_DTYPE); sums stay exact.
+ */
+int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int s_bits, int64_t* d_s2,
+                  int sat_pitch, void* d_ws, size_t ws_bytes, sncc_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Coarse pass: segmented NCC, threshold, candidates (GPU)             */
+/* ------------------------------------------------------------------ */
+
+/* Device bytes of the matching plan of seg (corner lists and block table). */
+size_t sncc_plan_bytes(const sncc_segments* seg);
+
+/* Copies the plan into caller-owned device memory d_plan (>= sncc_plan_bytes,
+ * 16-byte aligned), asynchronously on stream.  The host plan must stay alive
+ * until the copy completes (it lives as long as seg). */
+int sncc_plan_upload(const sncc_segments* seg, void* d_plan, size_t plan_bytes, sncc_stream_t stream);
+
+/*
+ * sncc_match - approximate NCC at every offset and its candidates.
+ * Paper: Section 4, Eq. 9 - Eq. 18; Section 5 main algorithm steps 7a-7f.
+ *
+ * For each offset (u, v): num = sum_i (k_i - kbar) * S_i(u, v), where S_i is
+ * the four-corner box sum (Eq. 11) of the source over segment i; the local
+ * energy E_f = sum f^2 - (sum f)^2 / n (Eq. 13, 15, 16), formed exactly in
+ * integers and divided in double; rho = num / sqrt(E_f * Ek) (Eq. 17, 18,
+ * with the weighted template energy).  A uniform window gives rho = 0.
+ * Offsets with rho >= tau are candidates.
+ *
+ *   seg, d_plan          approximation and its uploaded plan
+ *   d_s, s_bits, d_s2    sum tables from sncc_integral, pitch sat_pitch
+ *   M, N                 source size
+ *   tau                  coarse threshold (e.g. precision * rho_max)
+ *   d_rho, rho_pitch     optional FP32 map, V rows x rho_pitch (>= U)
+ *                        floats; NULL skips it
+ *   d_cand, cand_cap     candidate linear indices v*U+u (unordered)
+ *   d_count              int32, receives the exact candidate count (may
+ *                        exceed cand_cap; then only cand_cap are stored and
+ *                        SNCC_STATUS_CAND_OVERFLOW is set)
+ *   d_status             int32 status word (cleared first)
+ * Returns SNCC_ERR_UNIFORM when Ek = 0 (nothing launched).
+ */
+int sncc_match(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits, const int64_t* d_s2,
+               int sat_pitch, int M, int N, float tau, float* d_rho, int rho_pitch, int32_t* d_cand,
+               int cand_cap, int32_t* d_count, int32_t* d_status, sncc_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Fine pass: exact NCC at the candidates (GPU)                        */
+/* ------------------------------------------------------------------ */
+
+/* One match (u, v, rho) of the output collection (Section 5, "matches"). */
+typedef struct {
+    int32_t u, v;
+    float rho;
+} sncc_match_t;
+
+/* Scratch bytes sncc_refine needs for out_cap matches. */
+size_t sncc_refine_workspace_bytes(int out_cap);
+
+/*
+ * sncc_refine - exact NCC (Eq. 1) at each candidate and the match list.
+ * Paper: Eq. 1; Section 5 main algorithm steps 7g-7j, with the second
+ * stage computed exactly instead of with a finer approximation.
+ *
+ * For candidate (u, v): rho_t = (n*Sft - T*Sf) / sqrt((n*Sff - Sf^2)(n*T2 - T^2))
+ * with the exact integer sums Sft = sum f*t, Sf, Sff over the window and
+ * T, T2 over the template, divided in double.  Matches have rho_t >= tau.
+ *
+ *   d_f, M, N, f_stride  device source
+ *   d_t, W, H, t_stride  device template (uint8)
+ *   T, T2                sum of t and t^2 (from sncc_segments)
+ *   d_cand, d_count      candidates and their count from sncc_match; only
+ *                        the first min(*d_count, cand_cap) are read
+ *   tau                  exact threshold
+ *   d_out, out_cap       matches sorted by v*U+u
+ *   d_nout               int32, receives the exact match count (may exceed
+ *                        out_cap: SNCC_STATUS_MATCH_OVERFLOW)
+ *   d_ws, ws_bytes       workspace, >= sncc_refine_workspace_bytes(out_cap)
+ *   d_status             int32 status word (not cleared: sncc_match clears it)
+ */
+int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t* d_t, int W, int H, int t_stride,
+                int64_t T, int64_t T2, const int32_t* d_cand, const int32_t* d_count, int cand_cap, float tau,
+                sncc_match_t* d_out, int out_cap, int32_t* d_nout, void* d_ws, size_t ws_bytes,
+                int32_t* d_status, sncc_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Same-GPU comparator: exact NCC at every offset                      */
+/* ------------------------------------------------------------------ */
+
+/*
+ * sncc_exact_map - Eq. 1 at every offset by direct correlation with exact
+ * integer sums (the paper's "naive algorithm", Section 2 and Table 1), as
+ * the same-GPU reference for speed and approximation error.
+ *
+ *   d_f, M, N, f_stride  device source; d_t, W, H, t_stride device template
+ *   T, T2                sum of t and t^2
+ *   d_s, s_bits, d_s2    sum tables from sncc_integral (window sums)
+ *   d_rho, rho_pitch     FP32 map, V rows x rho_pitch floats
+ * Returns SNCC_ERR_UNIFORM for a uniform template.
+ */
+int sncc_exact_map(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t* d_t, int W, int H,
+                   int t_stride, int64_t T, int64_t T2, const void* d_s, int s_bits, const int64_t* d_s2,
+                   int sat_pitch, float* d_rho, int rho_pitch, sncc_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Introspection and measurement helpers                               */
+/* ------------------------------------------------------------------ */
+
+/* Shape of the matching plan built by sncc_build_segments. */
+typedef struct {
+    int32_t F;            /* fraction bits of the fixed-point weights q_i */
+    int32_t blocks;       /* template blocks */
+    int32_t block_w;      /* block width and height (edge blocks may be smaller) */
+    int32_t block_h;
+    int32_t corners;      /* distinct weighted corner points, summed over blocks */
+    int32_t max_corners;  /* largest corner count of one block */
+    int64_t Q0;           /* sum of the weights over all pixels, sum_i W_i H_i q_i */
+} sncc_plan_info;
+
+/* Fills *out for seg; SNCC_ERR_UNIFORM when seg has no plan (Ek = 0). */
+int sncc_get_plan_info(const sncc_segments* seg, sncc_plan_info* out);
+
+/* Shared-memory read-bandwidth probe: `ctas` CTAs of 256 threads each read
+ * 32-bit words from shared memory with conflict-free accesses, `iters`
+ * rounds of 32 loads per thread, and store one checksum word per thread into
+ * d_sink (ctas * 256 int32, device).  Bytes read = ctas*256*iters*32*4.
+ * Used by the benchmark to measure the on-chip roofline of the segment-sum
+ * kernel; not part of the matching path. */
+int sncc_probe_smem_read(int32_t* d_sink, int ctas, int iters, sncc_stream_t stream);
+
+/* Library version string. */
+const char* sncc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNCC_H */

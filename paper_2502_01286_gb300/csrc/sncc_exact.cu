@@ -1,0 +1,151 @@
+// sncc_exact.cu - exact NCC (Eq. 1) at every offset by direct correlation,
+// the paper's "naive algorithm" (Section 2, Table 1), kept as the same-GPU
+// reference for speed and for the approximation error of segmented NCC.
+//
+// A CTA of 8 warps computes a 32 x 8R tile of offsets.  The template is cut
+// into 64 x 64 blocks; for each block the CTA stages the template block and
+// the source region its offsets touch in shared memory (bytes), and every
+// thread accumulates sum f*t for its R offsets in exact 32-bit partials
+// (a block adds at most 4096 * 65025 < 2^32), flushed into 64-bit totals.
+// The window sums come from the sum tables; the final ratio is formed in
+// double from exact integers.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sncc.h"
+#include "sncc_internal.h"
+
+namespace sncc {
+namespace {
+
+constexpr int kTB = 64;                    // template block edge
+constexpr int kFSP = TILE_U + kTB + 4;     // source region pitch (bytes)
+
+template <bool S64>
+__device__ __forceinline__ long long sat_read(const void* s, int pitch, int X, int Y) {
+    if constexpr (S64)
+        return static_cast<const long long*>(s)[(size_t)Y * pitch + X];
+    else
+        return static_cast<const int*>(s)[(size_t)Y * pitch + X];
+}
+
+template <int R, bool S64>
+__global__ void __launch_bounds__(256)
+    exact_kernel(const uint8_t* __restrict__ f, int M, int N, int f_stride, const uint8_t* __restrict__ t, int W,
+                 int H, int t_stride, long long T, long long T2, const void* __restrict__ s,
+                 const int64_t* __restrict__ s2, int pitch, float* __restrict__ rho, int rho_pitch) {
+    constexpr int FR = WARPS * R + kTB;  // region rows (one spare)
+    __shared__ __align__(16) uint8_t fs[FR * kFSP];
+    __shared__ __align__(16) uint8_t ts[kTB * kTB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int u0 = blockIdx.x * TILE_U, v0 = blockIdx.y * (WARPS * R);
+    const int U = M - W + 1, V = N - H + 1;
+    unsigned long long acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0ull;
+
+    for (int by = 0; by < H; by += kTB) {
+        const int bh = min(kTB, H - by);
+        for (int bx = 0; bx < W; bx += kTB) {
+            const int bw = min(kTB, W - bx);
+            const int bw4 = (bw + 3) & ~3;
+            __syncthreads();
+            // template block, zero-padded to a multiple of 4 columns
+            for (int i = tid; i < kTB * kTB; i += 256) {
+                const int y = i / kTB, x = i - y * kTB;
+                ts[i] = (y < bh && x < bw) ? t[(size_t)(by + y) * t_stride + bx + x] : (uint8_t)0;
+            }
+            // source region: rows v0+by .. , columns u0+bx ..
+            for (int i = tid; i < FR * kFSP; i += 256) {
+                const int Y = i / kFSP, X = i - Y * kFSP;
+                const int gy = v0 + by + Y, gx = u0 + bx + X;
+                fs[i] = (gy < N && gx < M) ? f[(size_t)gy * f_stride + gx] : (uint8_t)0;
+            }
+            __syncthreads();
+            unsigned part[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) part[r] = 0u;
+            for (int y = 0; y < bh; ++y) {
+                const uint8_t* frow = fs + (warp * R + y) * kFSP + lane;
+                const uint32_t* trow = reinterpret_cast<const uint32_t*>(ts + y * kTB);
+                for (int x = 0; x < bw4; x += 4) {
+                    const uint32_t tw = trow[x >> 2];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const unsigned tv = (tw >> (8 * k)) & 0xffu;
+#pragma unroll
+                        for (int r = 0; r < R; ++r) part[r] += tv * (unsigned)frow[r * kFSP + x + k];
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] += part[r];
+        }
+    }
+
+    const int u = u0 + lane;
+    const long long n = (long long)W * H;
+    const long long vt = n * T2 - T * T;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = v0 + warp * R + r;
+        if (u >= U || v >= V) continue;
+        const long long sf = sat_read<S64>(s, pitch, u + W, v + H) - sat_read<S64>(s, pitch, u, v + H) -
+                             sat_read<S64>(s, pitch, u + W, v) + sat_read<S64>(s, pitch, u, v);
+        const long long sf2 = s2[(size_t)(v + H) * pitch + u + W] - s2[(size_t)(v + H) * pitch + u] -
+                              s2[(size_t)v * pitch + u + W] + s2[(size_t)v * pitch + u];
+        const long long vf = n * sf2 - sf * sf;
+        const long long num = n * (long long)acc[r] - T * sf;
+        const float out = (vf > 0 && vt > 0) ? (float)((double)num / sqrt((double)vf * (double)vt)) : 0.0f;
+        rho[(size_t)v * rho_pitch + u] = out;
+    }
+}
+
+template <int R>
+cudaError_t launch_exact(bool s64, dim3 grid, cudaStream_t st, const uint8_t* f, int M, int N, int f_stride,
+                         const uint8_t* t, int W, int H, int t_stride, long long T, long long T2, const void* s,
+                         const int64_t* s2, int pitch, float* rho, int rho_pitch) {
+    if (s64)
+        exact_kernel<R, true><<<grid, 256, 0, st>>>(f, M, N, f_stride, t, W, H, t_stride, T, T2, s, s2, pitch, rho,
+                                                     rho_pitch);
+    else
+        exact_kernel<R, false><<<grid, 256, 0, st>>>(f, M, N, f_stride, t, W, H, t_stride, T, T2, s, s2, pitch,
+                                                      rho, rho_pitch);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace sncc
+
+extern "C" int sncc_exact_map(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t* d_t, int W, int H,
+                              int t_stride, int64_t T, int64_t T2, const void* d_s, int s_bits, const int64_t* d_s2,
+                              int sat_pitch, float* d_rho, int rho_pitch, sncc_stream_t stream) {
+    using namespace sncc;
+    if (!d_f || !d_t || !d_s || !d_s2 || !d_rho || W <= 0 || H <= 0 || M < W || N < H) return SNCC_ERR_ARG;
+    if (f_stride < M || t_stride < W || (s_bits != 32 && s_bits != 64) || sat_pitch < M + 1) return SNCC_ERR_ARG;
+    const int U = M - W + 1, V = N - H + 1;
+    if (rho_pitch < U) return SNCC_ERR_ARG;
+    if ((int64_t)W * H > ((int64_t)1 << 23)) return SNCC_ERR_UNSUPPORTED;
+    const long long n = (long long)W * H;
+    if (n * T2 - T * T <= 0) return SNCC_ERR_UNIFORM;
+    const int tu = (U + TILE_U - 1) / TILE_U;
+    int R = 2;
+    for (int c : {8, 4}) {
+        if ((long long)tu * ((V + WARPS * c - 1) / (WARPS * c)) >= 2 * 152) { R = c; break; }
+    }
+    dim3 grid(tu, (V + WARPS * R - 1) / (WARPS * R));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    const bool s64 = (s_bits == 64);
+    if (R == 8)
+        e = launch_exact<8>(s64, grid, st, d_f, M, N, f_stride, d_t, W, H, t_stride, T, T2, d_s, d_s2, sat_pitch,
+                            d_rho, rho_pitch);
+    else if (R == 4)
+        e = launch_exact<4>(s64, grid, st, d_f, M, N, f_stride, d_t, W, H, t_stride, T, T2, d_s, d_s2, sat_pitch,
+                            d_rho, rho_pitch);
+    else
+        e = launch_exact<2>(s64, grid, st, d_f, M, N, f_stride, d_t, W, H, t_stride, T, T2, d_s, d_s2, sat_pitch,
+                            d_rho, rho_pitch);
+    return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+}

@@ -1,0 +1,367 @@
+// sncc_host.cpp - host side of the library: split-and-merge template
+// approximation (Section 3, Section 5) and the matching plan.
+//
+// The segmentation follows the paper's definitions step for step (the table
+// it produces is part of the method's result and is compared bit for bit),
+// but the statistics of each candidate rectangle come from exact integer sum
+// tables of the template instead of per-pixel loops.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sncc.h"
+#include "sncc_internal.h"
+
+namespace sncc {
+
+namespace {
+
+// Exact integer sum tables of a uint8 template, padded with a zero row and
+// column: tab[Y * (W+1) + X] = sum over x < X, y < Y.
+struct TemplateSums {
+    int W = 0, H = 0;
+    std::vector<int64_t> s, s2;
+    void build(const uint8_t* t, int W_, int H_, int stride) {
+        W = W_;
+        H = H_;
+        const int P = W + 1;
+        s.assign((size_t)P * (H + 1), 0);
+        s2.assign((size_t)P * (H + 1), 0);
+        for (int y = 0; y < H; ++y) {
+            int64_t row = 0, row2 = 0;
+            for (int x = 0; x < W; ++x) {
+                const int64_t v = t[(size_t)y * stride + x];
+                row += v;
+                row2 += v * v;
+                s[(size_t)(y + 1) * P + x + 1] = s[(size_t)y * P + x + 1] + row;
+                s2[(size_t)(y + 1) * P + x + 1] = s2[(size_t)y * P + x + 1] + row2;
+            }
+        }
+    }
+    int64_t box(const std::vector<int64_t>& tab, int x, int y, int w, int h) const {
+        const int P = W + 1;
+        return tab[(size_t)(y + h) * P + x + w] - tab[(size_t)y * P + x + w] - tab[(size_t)(y + h) * P + x] +
+               tab[(size_t)y * P + x];
+    }
+};
+
+struct Seg {
+    int x, y, w, h;
+    int64_t sum;
+    double mean;
+};
+
+// split_segment (Section 5), depth first with the first half before the
+// second, as the recursion orders it.  Eq. 2 is tested as
+// n*S2 - S*S < n*n*sigma^2 in double with the same association everywhere.
+void split(const TemplateSums& ts, const uint8_t* t, int stride, double sigma, std::vector<Seg>& out) {
+    struct R { int x, y, w, h; };
+    std::vector<R> stack;
+    stack.push_back({0, 0, ts.W, ts.H});
+    out.clear();
+    while (!stack.empty()) {
+        const R r = stack.back();
+        stack.pop_back();
+        if (r.w == 1 && r.h == 1) {
+            const int64_t v = t[(size_t)r.y * stride + r.x];
+            out.push_back({r.x, r.y, 1, 1, v, (double)v});
+            continue;
+        }
+        const int64_t S = ts.box(ts.s, r.x, r.y, r.w, r.h);
+        const int64_t S2 = ts.box(ts.s2, r.x, r.y, r.w, r.h);
+        const double n = (double)r.w * (double)r.h;
+        const double Sd = (double)S, S2d = (double)S2;
+        const double lhs = n * S2d - Sd * Sd;
+        const double rhs = n * n * sigma * sigma;
+        if (lhs < rhs) {
+            out.push_back({r.x, r.y, r.w, r.h, S, Sd / n});
+            continue;
+        }
+        if (r.w > r.h) {
+            const int a = (r.w + 1) / 2;
+            stack.push_back({r.x + a, r.y, r.w - a, r.h});
+            stack.push_back({r.x, r.y, a, r.h});
+        } else {
+            const int a = (r.h + 1) / 2;
+            stack.push_back({r.x, r.y + a, r.w, r.h - a});
+            stack.push_back({r.x, r.y, r.w, a});
+        }
+    }
+}
+
+// merge_redundant_segments (Section 5): alternate a vertical pass over the
+// (x, y)-sorted list and a horizontal pass over the (y, x)-sorted list, each
+// extending a segment by the chain of equal-mean neighbours that share its
+// column (row) span, until a round removes nothing.
+void merge(std::vector<Seg>& k) {
+    auto by_xy = [](const Seg& a, const Seg& b) { return a.x != b.x ? a.x < b.x : a.y < b.y; };
+    auto by_yx = [](const Seg& a, const Seg& b) { return a.y != b.y ? a.y < b.y : a.x < b.x; };
+    for (;;) {
+        std::sort(k.begin(), k.end(), by_xy);
+        for (size_t i = 0; i + 1 < k.size();) {
+            if (k[i].w == 0 || k[i].h == 0) { ++i; continue; }
+            size_t j = i + 1;
+            while (j < k.size() && k[j].x == k[i].x && k[j].w == k[i].w && k[j].y == k[i].y + k[i].h &&
+                   k[j].mean == k[i].mean) {
+                k[i].h += k[j].h;
+                k[i].sum += k[j].sum;
+                k[j].h = 0;
+                ++j;
+            }
+            i = j;
+        }
+        std::sort(k.begin(), k.end(), by_yx);
+        for (size_t i = 0; i + 1 < k.size();) {
+            if (k[i].w == 0 || k[i].h == 0) { ++i; continue; }
+            size_t j = i + 1;
+            while (j < k.size() && k[j].y == k[i].y && k[j].h == k[i].h && k[j].x == k[i].x + k[i].w &&
+                   k[j].mean == k[i].mean) {
+                k[i].w += k[j].w;
+                k[i].sum += k[j].sum;
+                k[j].w = 0;
+                ++j;
+            }
+            i = j;
+        }
+        const size_t before = k.size();
+        k.erase(std::remove_if(k.begin(), k.end(), [](const Seg& s) { return s.w == 0 || s.h == 0; }), k.end());
+        if (k.size() == before) return;
+    }
+}
+
+// round(num / den) to nearest, ties away from zero, den > 0.
+__int128 round_div(__int128 num, __int128 den) {
+    if (num >= 0) return (2 * num + den) / (2 * den);
+    return -((2 * (-num) + den) / (2 * den));
+}
+
+// Builds the fixed-point weights and the per-block corner lists.
+int build_plan(const sncc_segments* s, Plan& p) {
+    const int W = s->W, H = s->H;
+    const int64_t n = (int64_t)W * H;
+    p.W = W;
+    p.H = H;
+    p.n = (double)n;
+    p.Ek = s->Ek;
+    if (W <= BLOCK_SINGLE_MAX && H <= BLOCK_SINGLE_MAX) {
+        p.BW = W;
+        p.BH = H;
+    } else {
+        p.BW = std::min(W, BLOCK_MULTI);
+        p.BH = std::min(H, BLOCK_MULTI);
+    }
+    p.nbx = (W + p.BW - 1) / p.BW;
+    p.nby = (H + p.BH - 1) / p.BH;
+    // Work-region pitch is one of two compile-time widths of the kernel.
+    p.WP = (p.BW <= 32) ? TILE_U + 32 + 1 : TILE_U + 64 + 1;
+
+    // Fixed-point scale: every |G| <= 4 max|q_i| must stay below 2^31.
+    double maxc = 0.0;
+    for (int i = 0; i < s->K; ++i) maxc = std::max(maxc, std::fabs(s->seg[i].mean - s->kbar));
+    int F = 30;
+    if (maxc > 0.0) {
+        while (F > 0 && maxc * std::ldexp(1.0, F) + 1.0 >= std::ldexp(1.0, 29)) --F;
+    }
+    p.F = F;
+
+    // q_i = round(2^F (sum_i * n - T * n_i) / (n_i * n)), exact in 128 bits.
+    std::vector<int32_t> qimg((size_t)W * H, 0);
+    int64_t Q0 = 0;
+    for (int i = 0; i < s->K; ++i) {
+        const sncc_seg& g = s->seg[i];
+        const int64_t ni = (int64_t)g.w * g.h;
+        const __int128 num = ((__int128)g.sum * n - (__int128)s->T * ni) * ((__int128)1 << F);
+        const __int128 q = round_div(num, (__int128)ni * n);
+        const int32_t qi = (int32_t)q;
+        for (int y = g.y; y < g.y + g.h; ++y)
+            for (int x = g.x; x < g.x + g.w; ++x) qimg[(size_t)y * W + x] = qi;
+        Q0 += (int64_t)qi * ni;
+    }
+    p.Q0 = Q0;
+
+    // Corner lists, block by block.
+    const int nblk = p.nbx * p.nby;
+    std::vector<int32_t> blocks((size_t)4 * nblk);
+    std::vector<int32_t> corners;
+    p.max_corners = 0;
+    for (int by_i = 0; by_i < p.nby; ++by_i) {
+        for (int bx_i = 0; bx_i < p.nbx; ++bx_i) {
+            const int bx = bx_i * p.BW, by = by_i * p.BH;
+            const int bw = std::min(p.BW, W - bx), bh = std::min(p.BH, H - by);
+            auto q = [&](int X, int Y) -> int64_t {  // block-local, zero outside
+                if (X < 0 || Y < 0 || X >= bw || Y >= bh) return 0;
+                return qimg[(size_t)(by + Y) * W + (bx + X)];
+            };
+            const int first = (int)(corners.size() / 2);
+            for (int Y = 0; Y <= bh; ++Y)
+                for (int X = 0; X <= bw; ++X) {
+                    const int64_t G = q(X - 1, Y - 1) - q(X, Y - 1) - q(X - 1, Y) + q(X, Y);
+                    if (G != 0) {
+                        corners.push_back(Y * p.WP + X);
+                        corners.push_back((int32_t)G);
+                    }
+                }
+            const int cnt = (int)(corners.size() / 2) - first;
+            const int b = by_i * p.nbx + bx_i;
+            blocks[4 * b + 0] = bx;
+            blocks[4 * b + 1] = by;
+            blocks[4 * b + 2] = first;
+            blocks[4 * b + 3] = cnt;
+            p.max_corners = std::max(p.max_corners, cnt);
+        }
+    }
+    p.total_corners = (int)(corners.size() / 2);
+    p.blocks_offset = 0;
+    p.corners_offset = (size_t)nblk * 16;
+    p.image.resize(blocks.size() + corners.size() + 4, 0);
+    std::memcpy(p.image.data(), blocks.data(), blocks.size() * sizeof(int32_t));
+    if (!corners.empty())
+        std::memcpy(p.image.data() + blocks.size(), corners.data(), corners.size() * sizeof(int32_t));
+    return SNCC_OK;
+}
+
+}  // namespace
+
+Plan* plan_of(const sncc_segments* s) { return s ? static_cast<Plan*>(s->plan) : nullptr; }
+
+const char* error_string(int code) {
+    switch (code) {
+        case SNCC_OK: return "ok";
+        case SNCC_ERR_ARG: return "invalid argument";
+        case SNCC_ERR_UNIFORM: return "uniform template or zero-energy approximation";
+        case SNCC_ERR_DTYPE: return "32-bit sum table would overflow";
+        case SNCC_ERR_CAPACITY: return "capacity too small";
+        case SNCC_ERR_CUDA: return "CUDA error";
+        case SNCC_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case SNCC_ERR_NOMEM: return "host allocation failed";
+        case SNCC_ERR_UNSUPPORTED: return "size not supported";
+        default: return "unknown error";
+    }
+}
+
+}  // namespace sncc
+
+extern "C" {
+
+const char* sncc_error_string(int code) { return sncc::error_string(code); }
+
+const char* sncc_version(void) { return "sncc 0.1 (sm_103a)"; }
+
+void sncc_free_segments(sncc_segments* s) {
+    if (!s) return;
+    std::free(s->seg);
+    delete static_cast<sncc::Plan*>(s->plan);
+    std::memset(s, 0, sizeof(*s));
+}
+
+int sncc_build_segments(const uint8_t* t, int W, int H, int t_stride, double sigma_max, int k_max,
+                        sncc_segments* out) {
+    using namespace sncc;
+    if (!t || !out || W <= 0 || H <= 0 || t_stride < W || !(sigma_max == sigma_max)) return SNCC_ERR_ARG;
+    if ((int64_t)W * H > ((int64_t)1 << 23)) return SNCC_ERR_UNSUPPORTED;
+    std::memset(out, 0, sizeof(*out));
+    try {
+        TemplateSums ts;
+        ts.build(t, W, H, t_stride);
+        std::vector<Seg> k;
+        double sigma = sigma_max, used = sigma_max;
+        // precompute_template_approximation steps 1-2
+        for (;;) {
+            split(ts, t, t_stride, sigma, k);
+            used = sigma;
+            sigma = sigma + 1.0;
+            if (k_max <= 0 || (int64_t)k.size() <= k_max) break;
+        }
+        const int k_split = (int)k.size();
+        merge(k);  // step 3
+
+        const int64_t n = (int64_t)W * H;
+        const int64_t T = ts.box(ts.s, 0, 0, W, H);
+        const int64_t T2 = ts.box(ts.s2, 0, 0, W, H);
+        out->K = (int32_t)k.size();
+        out->K_split = k_split;
+        out->W = W;
+        out->H = H;
+        out->sigma_used = used;
+        out->T = T;
+        out->T2 = T2;
+        // Eq. 7: sum_i n_i k_i = sum_i (segment sum) = T, so kbar = T / n.
+        out->kbar = (double)T / (double)n;
+        out->seg = static_cast<sncc_seg*>(std::malloc(sizeof(sncc_seg) * (k.size() ? k.size() : 1)));
+        if (!out->seg) return SNCC_ERR_NOMEM;
+        double Ek = 0.0;
+        for (size_t i = 0; i < k.size(); ++i) {
+            sncc_seg& g = out->seg[i];
+            g.x = k[i].x;
+            g.y = k[i].y;
+            g.w = k[i].w;
+            g.h = k[i].h;
+            g.sum = k[i].sum;
+            g.mean = k[i].mean;
+            const double c = g.mean - out->kbar;
+            Ek += (double)g.w * (double)g.h * c * c;
+        }
+        out->Ek = Ek;
+        // Steps 4-7: the numerator sum_i (sum_i - tbar n_i)(k_i - kbar) equals
+        // Ek because k_i n_i = sum_i and tbar = kbar, so rho_max = sqrt(Ek / Et)
+        // with Et = (n T2 - T^2) / n exactly.
+        const double Et = (double)(n * T2 - T * T) / (double)n;
+        out->rho_max = (Et > 0.0 && Ek > 0.0) ? std::sqrt(Ek / Et) : 0.0;
+
+        Plan* p = new Plan();
+        out->plan = p;
+        if (Ek > 0.0) {
+            build_plan(out, *p);
+            // |rho_gpu - rho| from quantising c_i to q_i / 2^F is at most
+            // 2^-(F+1) sqrt(n / Ek); float rounding adds a few 1e-7.
+            out->err_bound = std::ldexp(1.0, -(p->F + 1)) * std::sqrt((double)n / Ek) + 1e-6;
+        }
+    } catch (const std::bad_alloc&) {
+        sncc_free_segments(out);
+        return SNCC_ERR_NOMEM;
+    }
+    return SNCC_OK;
+}
+
+int sncc_get_plan_info(const sncc_segments* seg, sncc_plan_info* out) {
+    const sncc::Plan* p = sncc::plan_of(seg);
+    if (!out || !p) return SNCC_ERR_ARG;
+    if (p->image.empty()) return SNCC_ERR_UNIFORM;
+    out->F = p->F;
+    out->blocks = p->nbx * p->nby;
+    out->block_w = p->BW;
+    out->block_h = p->BH;
+    out->corners = p->total_corners;
+    out->max_corners = p->max_corners;
+    out->Q0 = p->Q0;
+    return SNCC_OK;
+}
+
+int sncc_sat_pitch(int M) {
+    if (M < 0) return -1;
+    return ((M + 1) + 31) / 32 * 32;
+}
+
+size_t sncc_plan_bytes(const sncc_segments* seg) {
+    const sncc::Plan* p = sncc::plan_of(seg);
+    if (!p) return 0;
+    return p->image.size() * sizeof(int32_t);
+}
+
+int sncc_plan_upload(const sncc_segments* seg, void* d_plan, size_t plan_bytes, sncc_stream_t stream) {
+    const sncc::Plan* p = sncc::plan_of(seg);
+    if (!p || !d_plan) return SNCC_ERR_ARG;
+    if (p->image.empty()) return SNCC_ERR_UNIFORM;
+    const size_t need = p->image.size() * sizeof(int32_t);
+    if (plan_bytes < need || (reinterpret_cast<uintptr_t>(d_plan) & 15)) return SNCC_ERR_WORKSPACE;
+    if (cudaMemcpyAsync(d_plan, p->image.data(), need, cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess)
+        return SNCC_ERR_CUDA;
+    return SNCC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// sncc_internal.h - private declarations shared by the library's translation
+// units (host plan layout, tile geometry, launch helpers).  Not installed.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "sncc.h"
+
+namespace sncc {
+
+// ---------------------------------------------------------------------------
+// Segment-sum tile geometry.
+//
+// A CTA of 8 warps computes a tile of TILE_U x (8 * R) offsets: lane l of warp
+// w owns offsets (u0 + l, v0 + w*R + r), r < R.  The template is cut into
+// blocks of at most BLOCK x BLOCK pixels; for each block the CTA stages the
+// sum-table region its offsets touch, (TILE_U + bw + 1) x (8R + bh + 1)
+// entries, re-based to the region's own origin so every entry fits in 32 bits.
+// ---------------------------------------------------------------------------
+constexpr int TILE_U = 32;
+constexpr int WARPS = 8;
+constexpr int BLOCK_SINGLE_MAX = 64;  // a template up to 64 x 64 is one block
+constexpr int BLOCK_MULTI = 32;       // larger templates use 32 x 32 blocks
+
+// Host-side matching plan (built by sncc_build_segments).
+//
+// The zero-mean segment values c_i = k_i - kbar are quantised to
+// q_i = round(c_i * 2^F).  With q(x, y) the rendered image of q_i, the kernel
+// computes the exact integer correlation A(u, v) = sum_{x,y} q(x,y) f(u+x, v+y)
+// as a sparse sum over corner points of each block:
+//   A = sum_blocks sum_p G_p * s(u + bx + X_p, v + by + Y_p),
+//   G(X, Y) = q(X-1, Y-1) - q(X, Y-1) - q(X-1, Y) + q(X, Y)   (block-local,
+// q = 0 outside the block), i.e. Eq. 11 applied to every segment and summed,
+// with the shared corners of neighbouring segments combined.
+struct Plan {
+    int W = 0, H = 0;
+    int BW = 0, BH = 0;     // block size (the last block in a row/column may be smaller)
+    int nbx = 0, nby = 0;   // blocks across / down
+    int WP = 0;             // pitch (elements) of the re-based work region: 65 (BW <= 32) or 97
+    int F = 0;              // fixed-point fraction bits of q_i
+    int64_t Q0 = 0;         // sum over the template of q(x, y)
+    double Ek = 0.0;        // weighted energy of the approximation
+    double n = 0.0;         // W * H
+    int max_corners = 0;    // largest corner count of one block
+    int total_corners = 0;
+    // Device image: int4 blocks[nblk] = {bx, by, first, count}, then int2
+    // corners[total] = {Y * WP + X, G}.
+    std::vector<int32_t> image;
+    size_t blocks_offset = 0;   // bytes
+    size_t corners_offset = 0;  // bytes
+};
+
+Plan* plan_of(const sncc_segments* s);
+
+// Status helpers.
+const char* error_string(int code);
+
+}  // namespace sncc

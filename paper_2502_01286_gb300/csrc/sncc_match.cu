@@ -1,0 +1,331 @@
+// sncc_match.cu - the coarse pass of segmented NCC: for every offset the
+// approximate numerator sum_i (k_i - kbar) S_i(u, v) (Eq. 9, Eq. 11, Eq. 12),
+// normalised by the local energy and the approximation energy (Eq. 13 -
+// Eq. 18), thresholded and compacted into a candidate list (main algorithm,
+// steps 7a-7f).
+//
+// Kernel design (one CTA = 8 warps = a 32 x 8R tile of offsets):
+//  * The segment values enter as fixed-point weights q_i = round(c_i 2^F),
+//    c_i = k_i - kbar, and the CTA computes the exact integer correlation
+//    A(u, v) = sum_{x,y} q(x, y) f(u+x, v+y) through the corner form of
+//    Eq. 11: every segment contributes +-q_i at its four corners and corners
+//    shared by neighbouring segments are combined on the host, so each
+//    offset needs one sum-table read and one 32x32->64-bit multiply-add per
+//    distinct corner.
+//  * The template is processed in blocks; for each block a TMA tile load
+//    brings the sum-table region the tile touches into shared memory, which
+//    is re-based to the region origin (exact in wrapped 32-bit arithmetic,
+//    since every re-based entry is a box sum below 2^31) and then read with
+//    conflict-free 32-bit loads: lane l reads column l, warp w reads its own
+//    R rows.  The next block's TMA load is issued as soon as the raw buffer
+//    has been re-based, so it overlaps this block's arithmetic.
+//  * Epilogue: window sums from the global tables, exact integer variance
+//    n sum f^2 - (sum f)^2 divided by n in FP64, rho in FP32, warp-aggregated
+//    atomic append of candidates.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <mutex>
+#include <type_traits>
+
+#include "sncc.h"
+#include "sncc_internal.h"
+#include "sncc_ptx.cuh"
+
+namespace sncc {
+namespace {
+
+struct MatchArgs {
+    const int4* blocks;
+    const int2* corners;
+    int nblk;
+    int RWB;  // raw box width (elements)
+    int RH;   // region rows = 8R + BH + 1
+    int U, V, W, H;
+    const void* s;
+    const int64_t* s2;
+    int pitch;
+    long long n;
+    float inv_n;
+    float Ek;
+    float scale;  // 2^-F
+    long long Q0;
+    float tau;
+    float* rho;
+    int rho_pitch;
+    int32_t* cand;
+    int cand_cap;
+    int32_t* count;
+    int32_t* status;
+};
+
+__host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+template <bool S64>
+__device__ __forceinline__ long long sat_at(const void* s, int pitch, int X, int Y) {
+    if constexpr (S64)
+        return static_cast<const long long*>(s)[(size_t)Y * pitch + X];
+    else
+        return static_cast<const int*>(s)[(size_t)Y * pitch + X];
+}
+
+template <int R, bool S64, int WP>
+__global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUtensorMap tmap, const MatchArgs a) {
+    using RawT = typename std::conditional<S64, long long, int>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem + 8);
+    RawT* raw = reinterpret_cast<RawT*>(smem + 128);
+    const int raw_bytes = align_up(a.RWB * a.RH * (int)sizeof(RawT), 128);
+    int* work = reinterpret_cast<int*>(smem + 128 + raw_bytes);
+    const uint32_t tx_bytes = (uint32_t)(a.RWB * a.RH * (int)sizeof(RawT));
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int u0 = blockIdx.x * TILE_U, v0 = blockIdx.y * (WARPS * R);
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        *flag = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int4 b0 = a.blocks[0];
+        mbar_arrive_expect_tx(bar, tx_bytes);
+        tma_load_2d(raw, &tmap, u0 + b0.x, v0 + b0.y, bar);
+    }
+
+    long long acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
+    const int* wbase = work + warp * R * WP + lane;
+    uint32_t parity = 0;
+
+    for (int b = 0; b < a.nblk; ++b) {
+        if (tid == 0 && !mbar_wait_bounded(bar, parity)) *flag = 1;
+        __syncthreads();
+        if (*flag) {
+            if (tid == 0) atomicOr(a.status, SNCC_STATUS_WAIT_TIMEOUT);
+            return;
+        }
+        (void)mbar_try_wait(bar, parity);  // phase is complete: acquire for this thread
+        parity ^= 1u;
+
+        // Re-base the raw region to its own origin, into the 32-bit work buffer.
+        const uint32_t c00 = (uint32_t)raw[0];
+        for (int Y = warp; Y < a.RH; Y += WARPS) {
+            const uint32_t cy = (uint32_t)raw[Y * a.RWB];
+            for (int X = lane; X < WP; X += 32) {
+                const uint32_t val = (uint32_t)raw[Y * a.RWB + X] - (uint32_t)raw[X] - cy + c00;
+                work[Y * WP + X] = (int)val;
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && b + 1 < a.nblk) {  // raw is free: prefetch the next block
+            fence_proxy_async();
+            const int4 nb = a.blocks[b + 1];
+            mbar_arrive_expect_tx(bar, tx_bytes);
+            tma_load_2d(raw, &tmap, u0 + nb.x, v0 + nb.y, bar);
+        }
+
+        const int4 blk = a.blocks[b];
+        const int2* cp = a.corners + blk.z;
+        const int cnt = blk.w;
+        int p = 0;
+        for (; p + 4 <= cnt; p += 4) {
+            int2 c[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c[j] = __ldg(cp + p + j);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int* w = wbase + c[j].x;
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] += (long long)c[j].y * (long long)w[r * WP];
+            }
+        }
+        for (; p < cnt; ++p) {
+            const int2 c = __ldg(cp + p);
+            const int* w = wbase + c.x;
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] += (long long)c.y * (long long)w[r * WP];
+        }
+        __syncthreads();  // work is overwritten by the next block
+    }
+
+    // Epilogue: normalise, threshold, compact.
+    const int u = u0 + lane;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = v0 + warp * R + r;
+        const bool valid = (u < a.U) && (v < a.V);
+        float rho = 0.0f;
+        if (valid) {
+            // Eq. 13 and Eq. 15 in padded coordinates
+            const long long sf = sat_at<S64>(a.s, a.pitch, u + a.W, v + a.H) - sat_at<S64>(a.s, a.pitch, u, v + a.H) -
+                                 sat_at<S64>(a.s, a.pitch, u + a.W, v) + sat_at<S64>(a.s, a.pitch, u, v);
+            const long long sf2 = a.s2[(size_t)(v + a.H) * a.pitch + u + a.W] - a.s2[(size_t)(v + a.H) * a.pitch + u] -
+                                  a.s2[(size_t)v * a.pitch + u + a.W] + a.s2[(size_t)v * a.pitch + u];
+            // Eq. 16 times n, exact
+            const long long var = a.n * sf2 - sf * sf;
+            if (var > 0) {
+                const double ef = (double)var / (double)a.n;
+                const float den = sqrtf((float)ef * a.Ek);
+                const float num = ((float)acc[r] - (float)(a.Q0 * sf) * a.inv_n) * a.scale;
+                rho = num / den;
+            }
+        }
+        if (a.rho != nullptr && valid) a.rho[(size_t)v * a.rho_pitch + u] = rho;
+        const bool pred = valid && (rho >= a.tau);
+        const unsigned m = __ballot_sync(0xffffffffu, pred);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(a.count, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (pred) {
+                const int pos = base + __popc(m & ((1u << lane) - 1u));
+                if (pos < a.cand_cap)
+                    a.cand[pos] = v * a.U + u;
+                else
+                    atomicOr(a.status, SNCC_STATUS_CAND_OVERFLOW);
+            }
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+template <int R, bool S64, int WP>
+size_t smem_bytes_for(int RWB, int RH) {
+    const int es = S64 ? 8 : 4;
+    return 128 + (size_t)align_up(RWB * RH * es, 128) + (size_t)WP * RH * 4;
+}
+
+template <int R, bool S64, int WP>
+cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
+    const int RH = WARPS * R + BH + 1;
+    MatchArgs args = a;
+    args.RH = RH;
+    const size_t sm = smem_bytes_for<R, S64, WP>(a.RWB, RH);
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    dim3 grid((a.U + TILE_U - 1) / TILE_U, (a.V + WARPS * R - 1) / (WARPS * R));
+    match_kernel<R, S64, WP><<<grid, WARPS * 32, sm, st>>>(map, args);
+    return cudaGetLastError();
+}
+
+template <bool S64, int WP>
+cudaError_t dispatch_r(int R, const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
+    switch (R) {
+        case 8: return launch_match<8, S64, WP>(map, a, BH, st);
+        case 4: return launch_match<4, S64, WP>(map, a, BH, st);
+        default: return launch_match<2, S64, WP>(map, a, BH, st);
+    }
+}
+
+// Offsets per thread: the largest R in {8, 4, 2} that still gives two CTAs
+// per SM.
+int choose_r(int U, int V) {
+    const int tu = (U + TILE_U - 1) / TILE_U;
+    for (int R : {8, 4}) {
+        const long long ctas = (long long)tu * ((V + WARPS * R - 1) / (WARPS * R));
+        if (ctas >= 2 * 152) return R;
+    }
+    return 2;
+}
+
+}  // namespace
+}  // namespace sncc
+
+extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits,
+                          const int64_t* d_s2, int sat_pitch, int M, int N, float tau, float* d_rho, int rho_pitch,
+                          int32_t* d_cand, int cand_cap, int32_t* d_count, int32_t* d_status, sncc_stream_t stream) {
+    using namespace sncc;
+    const Plan* p = plan_of(seg);
+    if (!seg || !p || !d_plan || !d_s || !d_s2 || !d_count || !d_status || (cand_cap > 0 && !d_cand))
+        return SNCC_ERR_ARG;
+    if (cand_cap < 0 || (s_bits != 32 && s_bits != 64)) return SNCC_ERR_ARG;
+    if (!(seg->Ek > 0.0) || p->image.empty()) return SNCC_ERR_UNIFORM;
+    const int W = seg->W, H = seg->H;
+    const int U = M - W + 1, V = N - H + 1;
+    if (W <= 0 || H <= 0 || U <= 0 || V <= 0) return SNCC_ERR_ARG;
+    if (sat_pitch < M + 1 || (sat_pitch & 3)) return SNCC_ERR_ARG;
+    if (s_bits == 32 && (int64_t)255 * M * N >= ((int64_t)1 << 31)) return SNCC_ERR_DTYPE;
+    if (d_rho && rho_pitch < U) return SNCC_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_plan) & 15) || (reinterpret_cast<uintptr_t>(d_s) & 15)) return SNCC_ERR_ARG;
+    if ((int64_t)U * V >= ((int64_t)1 << 31)) return SNCC_ERR_UNSUPPORTED;
+
+    PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode();
+    if (!encode) return SNCC_ERR_CUDA;
+    const bool s64 = (s_bits == 64);
+    const int es = s64 ? 8 : 4;
+    const int R = choose_r(U, V);
+    const int RH = WARPS * R + p->BH + 1;
+    const int RWB = align_up(p->WP, 16 / es);
+
+    CUtensorMap map;
+    cuuint64_t gdim[2] = {(cuuint64_t)(M + 1), (cuuint64_t)(N + 1)};
+    cuuint64_t gstride[1] = {(cuuint64_t)sat_pitch * es};
+    cuuint32_t box[2] = {(cuuint32_t)RWB, (cuuint32_t)RH};
+    cuuint32_t estride[2] = {1, 1};
+    CUresult cr = encode(&map, s64 ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_INT32, 2,
+                         const_cast<void*>(d_s), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return SNCC_ERR_CUDA;
+
+    MatchArgs a;
+    a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->blocks_offset);
+    a.corners = reinterpret_cast<const int2*>(static_cast<const char*>(d_plan) + p->corners_offset);
+    a.nblk = p->nbx * p->nby;
+    a.RWB = RWB;
+    a.RH = RH;
+    a.U = U;
+    a.V = V;
+    a.W = W;
+    a.H = H;
+    a.s = d_s;
+    a.s2 = d_s2;
+    a.pitch = sat_pitch;
+    a.n = (long long)W * H;
+    a.inv_n = (float)(1.0 / ((double)W * H));
+    a.Ek = (float)seg->Ek;
+    a.scale = (float)std::ldexp(1.0, -p->F);
+    a.Q0 = p->Q0;
+    a.tau = tau;
+    a.rho = d_rho;
+    a.rho_pitch = rho_pitch;
+    a.cand = d_cand;
+    a.cand_cap = cand_cap;
+    a.count = d_count;
+    a.status = d_status;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(d_count, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
+    cudaError_t e;
+    if (p->WP == 65)
+        e = s64 ? dispatch_r<true, 65>(R, map, a, p->BH, st) : dispatch_r<false, 65>(R, map, a, p->BH, st);
+    else
+        e = s64 ? dispatch_r<true, 97>(R, map, a, p->BH, st) : dispatch_r<false, 97>(R, map, a, p->BH, st);
+    return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+}

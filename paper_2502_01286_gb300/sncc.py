@@ -1,0 +1,367 @@
+"""Thin Python binding of libsncc.so (the C ABI declared in include/sncc.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels or its host segmentation.  PyTorch supplies device memory and the
+current stream.  The library is loaded from this package's ``_build``
+directory; if it has not been built, importing this module raises.
+
+Names follow the C ABI: build_segments, integral, match, refine, exact_map.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsncc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libsncc.so is not built (%s); run paper_2502_01286_gb300/build.py or "
+                      "__graft_entry__.build()" % LIB_PATH)
+_lib = C.CDLL(LIB_PATH)
+
+# Return codes and status bits (include/sncc.h).
+OK = 0
+ERR_ARG, ERR_UNIFORM, ERR_DTYPE, ERR_CAPACITY, ERR_CUDA, ERR_WORKSPACE, ERR_NOMEM, ERR_UNSUPPORTED = \
+    -1, -2, -3, -4, -5, -6, -7, -8
+STATUS_CAND_OVERFLOW, STATUS_MATCH_OVERFLOW, STATUS_WAIT_TIMEOUT, STATUS_SORT_OVERFLOW = 1, 2, 4, 8
+
+EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_sat_pitch",
+            "sncc_integral_workspace_bytes", "sncc_integral", "sncc_plan_bytes", "sncc_plan_upload", "sncc_match",
+            "sncc_refine_workspace_bytes", "sncc_refine", "sncc_exact_map", "sncc_get_plan_info",
+            "sncc_probe_smem_read"]
+
+
+class SnccError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, _lib.sncc_error_string(code).decode(), code))
+
+
+class _Seg(C.Structure):
+    _fields_ = [("x", C.c_int32), ("y", C.c_int32), ("w", C.c_int32), ("h", C.c_int32),
+                ("sum", C.c_int64), ("mean", C.c_double)]
+
+
+class _Segments(C.Structure):
+    _fields_ = [("seg", C.POINTER(_Seg)), ("K", C.c_int32), ("K_split", C.c_int32), ("W", C.c_int32),
+                ("H", C.c_int32), ("sigma_used", C.c_double), ("kbar", C.c_double), ("Ek", C.c_double),
+                ("rho_max", C.c_double), ("T", C.c_int64), ("T2", C.c_int64), ("err_bound", C.c_double),
+                ("plan", C.c_void_p)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("F", C.c_int32), ("blocks", C.c_int32), ("block_w", C.c_int32), ("block_h", C.c_int32),
+                ("corners", C.c_int32), ("max_corners", C.c_int32), ("Q0", C.c_int64)]
+
+
+class MatchT(C.Structure):
+    _fields_ = [("u", C.c_int32), ("v", C.c_int32), ("rho", C.c_float)]
+
+
+_vp = C.c_void_p
+_lib.sncc_error_string.restype = C.c_char_p
+_lib.sncc_error_string.argtypes = [C.c_int]
+_lib.sncc_version.restype = C.c_char_p
+_lib.sncc_build_segments.argtypes = [_vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(_Segments)]
+_lib.sncc_free_segments.argtypes = [C.POINTER(_Segments)]
+_lib.sncc_free_segments.restype = None
+_lib.sncc_sat_pitch.argtypes = [C.c_int]
+_lib.sncc_integral_workspace_bytes.argtypes = [C.c_int, C.c_int]
+_lib.sncc_integral_workspace_bytes.restype = C.c_size_t
+_lib.sncc_integral.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp, C.c_size_t, _vp]
+_lib.sncc_plan_bytes.argtypes = [C.POINTER(_Segments)]
+_lib.sncc_plan_bytes.restype = C.c_size_t
+_lib.sncc_plan_upload.argtypes = [C.POINTER(_Segments), _vp, C.c_size_t, _vp]
+_lib.sncc_match.argtypes = [C.POINTER(_Segments), _vp, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_float,
+                            _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp]
+_lib.sncc_refine_workspace_bytes.argtypes = [C.c_int]
+_lib.sncc_refine_workspace_bytes.restype = C.c_size_t
+_lib.sncc_refine.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64,
+                             _vp, _vp, C.c_int, C.c_float, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp]
+_lib.sncc_get_plan_info.argtypes = [C.POINTER(_Segments), C.POINTER(PlanInfo)]
+_lib.sncc_probe_smem_read.argtypes = [_vp, C.c_int, C.c_int, _vp]
+_lib.sncc_exact_map.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64,
+                                C.c_int64, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp]
+
+
+def lib() -> C.CDLL:
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise SnccError(code, what)
+
+
+def version() -> str:
+    return _lib.sncc_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# Template preparation
+# ---------------------------------------------------------------------------
+class Segments:
+    """Owns an sncc_segments (host); exposes the table as numpy arrays."""
+
+    def __init__(self, t: np.ndarray, sigma_max: float, k_max: int = 0):
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.uint8))
+        if t.ndim != 2:
+            raise ValueError("template must be 2-D (H, W)")
+        H, W = t.shape
+        self._s = _Segments()
+        self._t = t
+        _check(_lib.sncc_build_segments(t.ctypes.data, W, H, W, float(sigma_max), int(k_max), C.byref(self._s)),
+               "sncc_build_segments")
+        self.W, self.H = W, H
+        self.sigma_max = float(sigma_max)
+        self.k_max = int(k_max)
+
+    def __del__(self):
+        s = getattr(self, "_s", None)
+        if s is not None and _lib is not None:
+            _lib.sncc_free_segments(C.byref(s))
+
+    def ref(self):
+        return C.byref(self._s)
+
+    K = property(lambda self: int(self._s.K))
+    K_split = property(lambda self: int(self._s.K_split))
+    sigma_used = property(lambda self: float(self._s.sigma_used))
+    kbar = property(lambda self: float(self._s.kbar))
+    Ek = property(lambda self: float(self._s.Ek))
+    rho_max = property(lambda self: float(self._s.rho_max))
+    T = property(lambda self: int(self._s.T))
+    T2 = property(lambda self: int(self._s.T2))
+    err_bound = property(lambda self: float(self._s.err_bound))
+
+    @property
+    def table(self) -> np.ndarray:
+        """(K, 4) int64 array of (x, y, w, h)."""
+        return np.array([(self._s.seg[i].x, self._s.seg[i].y, self._s.seg[i].w, self._s.seg[i].h)
+                         for i in range(self.K)], dtype=np.int64).reshape(-1, 4)
+
+    @property
+    def sums(self) -> np.ndarray:
+        return np.array([self._s.seg[i].sum for i in range(self.K)], dtype=np.int64)
+
+    @property
+    def means(self) -> np.ndarray:
+        return np.array([self._s.seg[i].mean for i in range(self.K)], dtype=np.float64)
+
+    def plan_bytes(self) -> int:
+        return int(_lib.sncc_plan_bytes(C.byref(self._s)))
+
+    def plan_info(self) -> dict:
+        pi = PlanInfo()
+        _check(_lib.sncc_get_plan_info(C.byref(self._s), C.byref(pi)), "sncc_get_plan_info")
+        return {k: int(getattr(pi, k)) for k, _ in PlanInfo._fields_}
+
+
+def build_segments(t: np.ndarray, sigma_max: float, k_max: int = 0) -> Segments:
+    return Segments(t, sigma_max, k_max)
+
+
+def sat_pitch(M: int) -> int:
+    return int(_lib.sncc_sat_pitch(M))
+
+
+# ---------------------------------------------------------------------------
+# Device calls (torch tensors for memory, current stream)
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+@dataclass
+class Tables:
+    """Padded sum tables of one source: s (int32 or int64) and s2 (int64),
+    each (N+1, pitch) on the device."""
+    s: "object"
+    s2: "object"
+    s_bits: int
+    pitch: int
+    M: int
+    N: int
+
+
+def choose_bits(M: int, N: int) -> int:
+    """int32 where 255*M*N cannot overflow it, int64 otherwise."""
+    return 32 if 255 * M * N < 2 ** 31 else 64
+
+
+def alloc_tables(M: int, N: int, s_bits: Optional[int] = None, device="cuda") -> Tables:
+    torch = _torch()
+    bits = s_bits or choose_bits(M, N)
+    P = sat_pitch(M)
+    s = torch.empty((N + 1, P), dtype=torch.int32 if bits == 32 else torch.int64, device=device)
+    s2 = torch.empty((N + 1, P), dtype=torch.int64, device=device)
+    return Tables(s, s2, bits, P, M, N)
+
+
+def integral_workspace(M: int, N: int, device="cuda"):
+    torch = _torch()
+    return torch.empty(int(_lib.sncc_integral_workspace_bytes(M, N)), dtype=torch.uint8, device=device)
+
+
+def integral(f, tables: Optional[Tables] = None, s_bits: Optional[int] = None, workspace=None, stream=None) -> Tables:
+    """sncc_integral on a (N, M) uint8 CUDA tensor (row stride = its stride)."""
+    torch = _torch()
+    if f.dtype != torch.uint8 or f.dim() != 2 or not f.is_cuda or f.stride(1) != 1:
+        raise ValueError("f must be a 2-D uint8 CUDA tensor with unit column stride")
+    N, M = f.shape
+    tb = tables or alloc_tables(M, N, s_bits, f.device)
+    ws = workspace if workspace is not None else integral_workspace(M, N, f.device)
+    _check(_lib.sncc_integral(f.data_ptr(), M, N, f.stride(0), tb.s.data_ptr(), tb.s_bits, tb.s2.data_ptr(),
+                              tb.pitch, ws.data_ptr(), ws.numel(), _stream(stream)), "sncc_integral")
+    return tb
+
+
+def upload_plan(seg: Segments, device="cuda", stream=None):
+    torch = _torch()
+    nbytes = seg.plan_bytes()
+    buf = torch.empty(max(16, (nbytes + 15) // 16 * 16), dtype=torch.uint8, device=device)
+    _check(_lib.sncc_plan_upload(seg.ref(), buf.data_ptr(), buf.numel(), _stream(stream)), "sncc_plan_upload")
+    return buf
+
+
+@dataclass
+class MatchBuffers:
+    cand: "object"
+    count: "object"
+    status: "object"
+    rho: "object"
+
+
+def alloc_match(M: int, N: int, W: int, H: int, cand_cap: int, with_rho: bool = True, device="cuda") -> MatchBuffers:
+    torch = _torch()
+    U, V = M - W + 1, N - H + 1
+    return MatchBuffers(cand=torch.empty(max(cand_cap, 1), dtype=torch.int32, device=device),
+                        count=torch.zeros(1, dtype=torch.int32, device=device),
+                        status=torch.zeros(1, dtype=torch.int32, device=device),
+                        rho=torch.empty((V, U), dtype=torch.float32, device=device) if with_rho else None)
+
+
+def match(seg: Segments, plan, tables: Tables, tau: float, bufs: MatchBuffers, cand_cap: Optional[int] = None,
+          stream=None) -> None:
+    """sncc_match: fills bufs.rho (if allocated), bufs.cand, bufs.count, bufs.status."""
+    cap = bufs.cand.numel() if cand_cap is None else cand_cap
+    rho_pitch = bufs.rho.stride(0) if bufs.rho is not None else 0
+    _check(_lib.sncc_match(seg.ref(), plan.data_ptr(), tables.s.data_ptr(), tables.s_bits, tables.s2.data_ptr(),
+                           tables.pitch, tables.M, tables.N, float(tau), _ptr(bufs.rho), rho_pitch,
+                           bufs.cand.data_ptr(), cap, bufs.count.data_ptr(), bufs.status.data_ptr(),
+                           _stream(stream)), "sncc_match")
+
+
+@dataclass
+class RefineBuffers:
+    out: "object"      # (out_cap, 3) int32 view of sncc_match_t records
+    nout: "object"
+    ws: "object"
+    cap: int
+
+
+def alloc_refine(out_cap: int, device="cuda") -> RefineBuffers:
+    torch = _torch()
+    return RefineBuffers(out=torch.empty((max(out_cap, 1), 3), dtype=torch.int32, device=device),
+                         nout=torch.zeros(1, dtype=torch.int32, device=device),
+                         ws=torch.empty(int(_lib.sncc_refine_workspace_bytes(out_cap)), dtype=torch.uint8,
+                                        device=device),
+                         cap=out_cap)
+
+
+def refine(f, t_dev, seg: Segments, bufs: MatchBuffers, tau: float, rb: RefineBuffers, cand_cap: Optional[int] = None,
+           stream=None) -> None:
+    """sncc_refine on the candidates in bufs; matches land in rb.out sorted by v*U+u."""
+    N, M = f.shape
+    H, W = t_dev.shape
+    cap = bufs.cand.numel() if cand_cap is None else cand_cap
+    _check(_lib.sncc_refine(f.data_ptr(), M, N, f.stride(0), t_dev.data_ptr(), W, H, t_dev.stride(0), seg.T, seg.T2,
+                            bufs.cand.data_ptr(), bufs.count.data_ptr(), cap, float(tau), rb.out.data_ptr(), rb.cap,
+                            rb.nout.data_ptr(), rb.ws.data_ptr(), rb.ws.numel(), bufs.status.data_ptr(),
+                            _stream(stream)), "sncc_refine")
+
+
+def matches_to_numpy(rb: RefineBuffers):
+    """(u, v, rho) arrays of the stored matches (after the stream is synced)."""
+    import torch
+    n = min(int(rb.nout.item()), rb.cap)
+    raw = rb.out[:n].cpu().numpy()
+    u = raw[:, 0].astype(np.int64)
+    v = raw[:, 1].astype(np.int64)
+    rho = raw[:, 2].copy().view(np.float32)
+    return u, v, rho
+
+
+def exact_map(f, t_dev, T: int, T2: int, tables: Tables, rho=None, stream=None):
+    """sncc_exact_map: exact NCC at every offset (FP32 map)."""
+    torch = _torch()
+    N, M = f.shape
+    H, W = t_dev.shape
+    U, V = M - W + 1, N - H + 1
+    out = rho if rho is not None else torch.empty((V, U), dtype=torch.float32, device=f.device)
+    _check(_lib.sncc_exact_map(f.data_ptr(), M, N, f.stride(0), t_dev.data_ptr(), W, H, t_dev.stride(0), int(T),
+                               int(T2), tables.s.data_ptr(), tables.s_bits, tables.s2.data_ptr(), tables.pitch,
+                               out.data_ptr(), out.stride(0), _stream(stream)), "sncc_exact_map")
+    return out
+
+
+def probe_smem_read(sink, ctas: int, iters: int, stream=None) -> int:
+    """Launches the shared-memory read probe; returns the bytes it reads."""
+    _check(_lib.sncc_probe_smem_read(sink.data_ptr(), ctas, iters, _stream(stream)), "sncc_probe_smem_read")
+    return ctas * 256 * iters * 32 * 4
+
+
+# ---------------------------------------------------------------------------
+# The whole path, as a user calls it
+# ---------------------------------------------------------------------------
+class Matcher:
+    """Segmented-NCC template matcher for one template on one GPU.
+
+    Prepares the approximation once (host), uploads its plan, and owns every
+    device buffer, so that run() only launches kernels: sum tables, coarse
+    pass, exact refine (Section 5 main algorithm with an exact second stage)."""
+
+    def __init__(self, t: np.ndarray, sigma_max: float, M: int, N: int, precision: float = 0.9,
+                 tau_exact: Optional[float] = None, k_max: int = 0, cand_cap: int = 1 << 20, out_cap: int = 1 << 16,
+                 keep_rho: bool = True, device="cuda"):
+        torch = _torch()
+        self.seg = build_segments(t, sigma_max, k_max)
+        if not self.seg.Ek > 0:
+            raise SnccError(ERR_UNIFORM, "Matcher")
+        self.M, self.N = M, N
+        self.W, self.H = self.seg.W, self.seg.H
+        self.U, self.V = M - self.W + 1, N - self.H + 1
+        self.tau_c = float(precision) * self.seg.rho_max
+        self.tau_e = float(precision) if tau_exact is None else float(tau_exact)
+        self.device = device
+        self.t_dev = torch.as_tensor(np.ascontiguousarray(t, np.uint8)).to(device)
+        self.plan = upload_plan(self.seg, device)
+        self.tables = alloc_tables(M, N, None, device)
+        self.ws = integral_workspace(M, N, device)
+        self.mb = alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device)
+        self.rb = alloc_refine(out_cap, device)
+
+    def run(self, f, stream=None):
+        """Launch the whole path on a (N, M) uint8 CUDA tensor (asynchronous)."""
+        integral(f, self.tables, workspace=self.ws, stream=stream)
+        match(self.seg, self.plan, self.tables, self.tau_c, self.mb, stream=stream)
+        refine(f, self.t_dev, self.seg, self.mb, self.tau_e, self.rb, stream=stream)
+
+    def status(self) -> int:
+        return int(self.mb.status.item())

@@ -11,7 +11,12 @@ Recipe (every parameter the paper leaves open is a stated choice):
                centres uniform over the image, s_j ~ U(8, 40) px
   uniform      additive U(-a, a) noise
   fractal      white Gaussian noise whose FFT amplitude is scaled by 1/|w|
-               (DC removed), rescaled so that max |.| = amplitude
+               (DC removed), rescaled so that its standard deviation
+               ("rms") or its largest magnitude ("max") equals the amplitude;
+               the HD case uses rms (so the swept thresholds 5/10/20 stay
+               below the template's std, as Section 3 requires), the
+               high-texture case uses max (several thousand segments at
+               threshold 5)
   rectangles   axis-aligned rectangles, sides U(4, 512), intensity U(0, 255),
                painted in order over a mid-grey canvas
   quantise     clip to [0, 255], round half to even, uint8
@@ -46,8 +51,9 @@ def blobs(g: np.random.Generator, M: int, N: int, count: int = 20, base: float =
     return img
 
 
-def fractal_noise(g: np.random.Generator, M: int, N: int, amplitude: float) -> np.ndarray:
-    """1/f noise (N, M) with max |value| = amplitude."""
+def fractal_noise(g: np.random.Generator, M: int, N: int, amplitude: float, scale: str = "max") -> np.ndarray:
+    """1/f noise (N, M) whose max |value| (scale="max") or standard deviation
+    (scale="rms") equals amplitude."""
     w = g.standard_normal((N, M))
     F = np.fft.rfft2(w)
     fy = np.fft.fftfreq(N)[:, None]
@@ -57,7 +63,7 @@ def fractal_noise(g: np.random.Generator, M: int, N: int, amplitude: float) -> n
     F = F / r
     F[0, 0] = 0.0
     out = np.fft.irfft2(F, s=(N, M))
-    m = np.max(np.abs(out))
+    m = np.std(out) if scale == "rms" else np.max(np.abs(out))
     return out * (amplitude / m) if m > 0 else out
 
 
@@ -112,9 +118,9 @@ def case_plain(M: int = 256, N: int = 256, W: int = 32, H: int = 32, seed: int =
 
 def case_hd(M: int = 1920, N: int = 1080, W: int = 64, H: int = 64, seed: int = BASE_SEED + 1,
             noise: float = 3.0, sigma_max: float = 10.0, precision: float = 0.85) -> Case:
-    """Blobs plus 1/f fractal noise of amplitude 60; a template with sigma-3 noise."""
+    """Blobs plus 1/f fractal noise of rms amplitude 60; a template with sigma-3 noise."""
     g = rng(seed)
-    img = blobs(g, M, N, 20) + fractal_noise(g, M, N, 60.0)
+    img = blobs(g, M, N, 20) + fractal_noise(g, M, N, 60.0, "rms")
     f = quantise(img)
     t, org = crop_template(g, f, W, H, noise)
     return Case("hd", f, t, org, sigma_max, precision, seed)
@@ -122,9 +128,9 @@ def case_hd(M: int = 1920, N: int = 1080, W: int = 64, H: int = 64, seed: int = 
 
 def case_texture(M: int = 4096, N: int = 4096, W: int = 256, H: int = 256, seed: int = BASE_SEED + 2,
                  noise: float = 0.0, sigma_max: float = 5.0, precision: float = 0.85) -> Case:
-    """Random rectangles plus 1/f noise of amplitude 40 (high texture)."""
+    """Random rectangles plus 1/f noise of peak amplitude 40 (high texture)."""
     g = rng(seed)
-    img = rectangles(g, M, N, 300) + fractal_noise(g, M, N, 40.0)
+    img = rectangles(g, M, N, 300) + fractal_noise(g, M, N, 40.0, "max")
     f = quantise(img)
     t, org = crop_template(g, f, W, H, noise)
     return Case("texture", f, t, org, sigma_max, precision, seed)

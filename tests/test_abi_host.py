@@ -1,0 +1,141 @@
+"""CPU tests of the C ABI: the library builds and loads, exports every entry
+point include/sncc.h declares, and its host logic (split-and-merge
+segmentation, argument checks) agrees with the oracle.  No GPU is touched:
+only host-side functions and calls rejected before any CUDA work run here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_01286_gb300 import build as sncc_build
+from paper_2502_01286_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sncc():
+    sncc_build.build()
+    from paper_2502_01286_gb300 import sncc as mod
+    return mod
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "sncc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sncc_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_four_paper_calls():
+    fns = header_functions()
+    for name in ["sncc_build_segments", "sncc_integral", "sncc_match", "sncc_refine"]:
+        assert name in fns
+
+
+def test_library_exports_every_declared_symbol(sncc):
+    lib = sncc.lib()
+    missing = [f for f in header_functions() if not hasattr(lib, f)]
+    assert missing == []
+    assert set(sncc.EXPORTED) <= set(header_functions())
+
+
+def test_version_and_error_strings(sncc):
+    assert "sm_103a" in sncc.version()
+    assert sncc.lib().sncc_error_string(-2).decode().startswith("uniform")
+
+
+def test_sat_pitch(sncc):
+    for M in [1, 30, 31, 32, 255, 1920, 4096]:
+        p = sncc.sat_pitch(M)
+        assert p >= M + 1 and p % 32 == 0 and p - (M + 1) < 32
+
+
+@pytest.mark.parametrize("shape,sigma,kmax", [
+    ((32, 32), 10.0, 0), ((64, 64), 5.0, 0), ((64, 64), 20.0, 0), ((37, 29), 0.0, 0), ((29, 37), 3.0, 0),
+    ((48, 48), 12.0, 0), ((40, 40), 0.0, 150), ((1, 1), 1.0, 0), ((7, 1), 0.5, 0), ((1, 9), 2.0, 0)])
+def test_segmentation_bit_exact_vs_oracle(sncc, shape, sigma, kmax):
+    """Segment table, K before merging and the sigma of the last split equal
+    the oracle's exactly (Section 5)."""
+    H, W = shape
+    c = synth.case_plain(M=max(64, W + 8), N=max(64, H + 8), W=W, H=H)
+    seg = sncc.build_segments(c.t, sigma, kmax)
+    ap = O.precompute_template_approximation(c.t, sigma, kmax)
+    np.testing.assert_array_equal(seg.table, ap.segments)
+    np.testing.assert_array_equal(seg.means, ap.mu)
+    assert seg.K_split == ap.k_split and seg.sigma_used == ap.sigma_used
+    assert abs(seg.kbar - ap.kbar) < 1e-12
+    assert abs(seg.Ek - ap.ek) <= 1e-9 * max(1.0, ap.ek)
+    assert abs(seg.rho_max - ap.rho_max) < 1e-12
+    # exact sums agree with the template
+    for (x, y, w, h), s in zip(seg.table, seg.sums):
+        assert s == int(c.t[y:y + h, x:x + w].astype(np.int64).sum())
+    assert seg.T == int(c.t.astype(np.int64).sum())
+    assert seg.T2 == int((c.t.astype(np.int64) ** 2).sum())
+
+
+def test_segmentation_large_template_bit_exact(sncc):
+    """A 256 x 256 high-texture template at sigma 5 (thousands of segments)."""
+    f = synth.rectangles(synth.rng(77), 300, 300, 40) + synth.fractal_noise(synth.rng(78), 300, 300, 40.0)
+    t = synth.quantise(f)[20:276, 10:266]
+    seg = sncc.build_segments(t, 5.0)
+    ap = O.precompute_template_approximation(t, 5.0)
+    assert seg.K > 1000
+    np.testing.assert_array_equal(seg.table, ap.segments)
+    np.testing.assert_array_equal(seg.means, ap.mu)
+
+
+@pytest.mark.parametrize("name", sorted(f for f in os.listdir(os.path.join(ROOT, "tests", "golden"))
+                                        if f.endswith(".txt") and f != "README.txt"))
+def test_segmentation_golden(sncc, name):
+    from conftest import load_golden
+    g = load_golden(name)
+    t = np.array(g["t"], np.uint8)
+    seg = sncc.build_segments(t, g["sigma"], g["kmax"])
+    got = [tuple(int(v) for v in r) + (float(m),) for r, m in zip(seg.table, seg.means)]
+    assert got == g["segments"]
+    if "sigma_used" in g:
+        assert seg.sigma_used == g["sigma_used"]
+
+
+def test_uniform_template_has_zero_energy(sncc):
+    seg = sncc.build_segments(np.full((8, 8), 7, np.uint8), 1.0)
+    assert seg.K == 1 and seg.Ek == 0.0 and seg.plan_bytes() == 0
+    assert sncc.lib().sncc_plan_upload(seg.ref(), C.c_void_p(16), 0, None) == sncc.ERR_UNIFORM
+
+
+def test_quantisation_error_bound_is_small(sncc):
+    c = synth.case_hd(M=200, N=200)
+    for sigma in (5.0, 10.0, 20.0):
+        seg = sncc.build_segments(c.t, sigma)
+        assert 0 < seg.err_bound < 5e-6
+
+
+def test_host_argument_errors(sncc):
+    lib = sncc.lib()
+    seg = sncc.build_segments(synth.case_plain().t, 10.0)
+    out = sncc._Segments()
+    assert lib.sncc_build_segments(None, 4, 4, 4, 1.0, 0, C.byref(out)) == sncc.ERR_ARG
+    t = np.zeros((4, 4), np.uint8)
+    assert lib.sncc_build_segments(t.ctypes.data, 4, 4, 3, 1.0, 0, C.byref(out)) == sncc.ERR_ARG
+    assert lib.sncc_build_segments(t.ctypes.data, 0, 4, 4, 1.0, 0, C.byref(out)) == sncc.ERR_ARG
+    big = np.zeros(1, np.uint8)
+    assert lib.sncc_build_segments(big.ctypes.data, 4096, 4096, 4096, 1.0, 0, C.byref(out)) == sncc.ERR_UNSUPPORTED
+    # device calls rejected on their arguments before any CUDA call
+    assert lib.sncc_integral(None, 10, 10, 10, None, 32, None, 32, None, 0, None) == sncc.ERR_ARG
+    assert lib.sncc_integral(C.c_void_p(256), 10, 10, 10, C.c_void_p(256), 16, C.c_void_p(256), 32, None, 0,
+                             None) == sncc.ERR_ARG
+    assert lib.sncc_integral(C.c_void_p(256), 4096, 4096, 4096, C.c_void_p(256), 32, C.c_void_p(256), 4128,
+                             C.c_void_p(256), 1 << 30, None) == sncc.ERR_DTYPE
+    assert lib.sncc_integral(C.c_void_p(256), 10, 10, 10, C.c_void_p(256), 32, C.c_void_p(256), 32, None, 0,
+                             None) == sncc.ERR_WORKSPACE
+    assert lib.sncc_match(seg.ref(), None, None, 32, None, 32, 64, 64, 0.5, None, 0, None, 0, None, None,
+                          None) == sncc.ERR_ARG
+    assert lib.sncc_refine(None, 64, 64, 64, None, 8, 8, 8, 0, 0, None, None, 0, 0.5, None, 0, None, None, 0,
+                           None, None) == sncc.ERR_ARG
+    assert lib.sncc_exact_map(C.c_void_p(256), 64, 64, 64, C.c_void_p(256), 8, 8, 8, 64 * 7, 64 * 49,
+                              C.c_void_p(256), 32, C.c_void_p(256), 96, C.c_void_p(256), 57,
+                              None) == sncc.ERR_UNIFORM
+    assert lib.sncc_integral_workspace_bytes(0, 5) == 0

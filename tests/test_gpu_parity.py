@@ -1,0 +1,329 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bars: sum tables and segment tables bit-exact; NCC maps within 1e-5 absolute;
+candidate and match sets exact outside a +-1e-5 band around each threshold
+(inside the band the FP32 decision may legitimately go either way, and such
+offsets are counted); match values within 1e-5."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_01286_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sncc():
+    if not torch.cuda.is_available():
+        pytest.fail("the -m gpu tests need a CUDA GPU")
+    from paper_2502_01286_gb300 import build
+    build.build()
+    from paper_2502_01286_gb300 import sncc as mod
+    return mod
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def run_match(sncc, f, t, sigma, tau, cand_cap=1 << 20, k_max=0, s_bits=None):
+    N, M = f.shape
+    seg = sncc.build_segments(t, sigma, k_max)
+    fd = dev(f)
+    tb = sncc.integral(fd, s_bits=s_bits)
+    plan = sncc.upload_plan(seg)
+    mb = sncc.alloc_match(M, N, seg.W, seg.H, cand_cap)
+    sncc.match(seg, plan, tb, tau, mb)
+    torch.cuda.synchronize()
+    return seg, fd, tb, mb
+
+
+def check_candidates(rho64, cand, count, tau, rows=None):
+    """Every offset with rho64 >= tau + TOL is a candidate and every one with
+    rho64 < tau - TOL is not; returns the number of offsets inside the band."""
+    V, U = rho64.shape
+    cand = np.asarray(cand, np.int64)
+    assert len(np.unique(cand)) == len(cand) == count
+    got = np.zeros(U * V, bool)
+    got[cand] = True
+    got = got.reshape(V, U)
+    sel = slice(None) if rows is None else rows
+    r = rho64[sel]
+    g = got[sel]
+    assert np.all(g[r >= tau + TOL])
+    assert not np.any(g[r < tau - TOL])
+    return int(np.sum((r >= tau - TOL) & (r < tau + TOL)))
+
+
+# ------------------------------------------------------------------ sum tables
+@pytest.mark.parametrize("M,N", [(1, 1), (5, 3), (33, 17), (257, 129), (256, 256), (1920, 1080), (4095, 7)])
+@pytest.mark.parametrize("bits", [32, 64])
+def test_integral_bit_exact(sncc, M, N, bits):
+    f = synth.random_image(1000 + M + N, M, N)
+    tb = sncc.integral(dev(f), s_bits=bits)
+    torch.cuda.synchronize()
+    s, s2 = O.sum_tables(f)
+    got_s = tb.s[:, :M + 1].cpu().numpy().astype(np.int64)
+    got_s2 = tb.s2[:, :M + 1].cpu().numpy()
+    np.testing.assert_array_equal(got_s, s.astype(np.int64))
+    np.testing.assert_array_equal(got_s2, s2.astype(np.int64))
+
+
+def test_integral_strided_source(sncc):
+    """A source that is a column window of a wider image (row stride > M)."""
+    big = synth.random_image(5, 300, 90)
+    fd = dev(big)[:, 17:17 + 211]
+    tb = sncc.integral(fd, s_bits=32)
+    torch.cuda.synchronize()
+    s, s2 = O.sum_tables(big[:, 17:17 + 211])
+    np.testing.assert_array_equal(tb.s[:, :212].cpu().numpy().astype(np.int64), s.astype(np.int64))
+    np.testing.assert_array_equal(tb.s2[:, :212].cpu().numpy(), s2.astype(np.int64))
+
+
+def test_integral_int64_full_size(sncc):
+    """4096 x 4096 at full intensity: entries reach 255*4096^2 > 2^31."""
+    f = synth.random_image(9, 4096, 4096, lo=200)
+    tb = sncc.integral(dev(f))
+    assert tb.s_bits == 64
+    torch.cuda.synchronize()
+    s, s2 = O.sum_tables(f)
+    for rows in (slice(0, 3), slice(2000, 2003), slice(4094, 4097)):
+        np.testing.assert_array_equal(tb.s[rows, :4097].cpu().numpy(), s[rows].astype(np.int64))
+        np.testing.assert_array_equal(tb.s2[rows, :4097].cpu().numpy(), s2[rows].astype(np.int64))
+    assert int(tb.s[-1, 4096]) == int(s[-1, -1])
+
+
+def test_integral_rejects_int32_overflow(sncc):
+    f = torch.zeros((4096, 4096), dtype=torch.uint8, device="cuda")
+    with pytest.raises(sncc.SnccError) as e:
+        sncc.integral(f, s_bits=32)
+    assert e.value.code == sncc.ERR_DTYPE
+
+
+# ------------------------------------------------------------------ coarse pass
+SHAPES = [
+    # (M, N, W, H, sigma)
+    (256, 256, 32, 32, 10.0),   # the 256^2 / 32^2 workload, sigma 10
+    (70, 45, 13, 9, 3.0),       # ragged tail in both directions
+    (100, 100, 64, 64, 5.0),    # largest single-block template
+    (130, 90, 100, 70, 6.0),    # multi-block template (32 x 32 blocks, ragged)
+    (40, 300, 40, 17, 4.0),     # U = 1
+    (300, 40, 23, 40, 4.0),     # V = 1
+    (120, 110, 37, 29, 0.0),    # sigma 0: every pixel its own segment before merging
+    (97, 61, 2, 1, 0.5),        # two-pixel template
+]
+
+
+@pytest.mark.parametrize("M,N,W,H,sigma", SHAPES)
+def test_match_map_and_candidates(sncc, M, N, W, H, sigma):
+    c = synth.case_plain(M=M, N=N, W=W, H=H, seed=4242 + M * 7 + W)
+    seg = sncc.build_segments(c.t, sigma)
+    if not seg.Ek > 0:
+        pytest.skip("uniform approximation")
+    ap = O.precompute_template_approximation(c.t, sigma)
+    np.testing.assert_array_equal(seg.table, ap.segments)
+    tau = 0.8 * seg.rho_max
+    seg, fd, tb, mb = run_match(sncc, c.f, c.t, sigma, tau)
+    ref = O.segmented_ncc_map(c.f, ap, "sat")
+    got = mb.rho.cpu().numpy().astype(np.float64)
+    assert got.shape == ref.shape
+    err = np.abs(got - ref).max()
+    assert err <= TOL, err
+    assert int(mb.status.item()) == 0
+    cnt = int(mb.count.item())
+    check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, tau)
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+def test_match_table_width_independent(sncc, bits):
+    """The same source through 32- and 64-bit sum tables gives one map."""
+    c = synth.case_plain(M=200, N=150, W=48, H=40)
+    ap = O.precompute_template_approximation(c.t, 7.0)
+    _, _, _, mb = run_match(sncc, c.f, c.t, 7.0, 0.5, s_bits=bits)
+    ref = O.segmented_ncc_map(c.f, ap, "sat")
+    assert np.abs(mb.rho.cpu().numpy() - ref).max() <= TOL
+
+
+def test_match_repeatable(sncc):
+    c = synth.case_plain()
+    _, _, _, a = run_match(sncc, c.f, c.t, 10.0, 0.5)
+    _, _, _, b = run_match(sncc, c.f, c.t, 10.0, 0.5)
+    assert torch.equal(a.rho, b.rho)
+    ca = np.sort(a.cand[:int(a.count.item())].cpu().numpy())
+    cb = np.sort(b.cand[:int(b.count.item())].cpu().numpy())
+    np.testing.assert_array_equal(ca, cb)
+
+
+def test_match_uniform_windows_are_zero(sncc):
+    c = synth.case_plain(M=120, N=100, W=20, H=16)
+    f = c.f.copy()
+    f[30:70, 40:90] = 111
+    _, _, _, mb = run_match(sncc, f, c.t, 6.0, 0.5)
+    rho = mb.rho.cpu().numpy()
+    assert np.all(rho[30:55, 40:71] == 0.0)
+
+
+def test_match_candidate_overflow(sncc):
+    c = synth.case_plain()
+    _, _, _, full = run_match(sncc, c.f, c.t, 10.0, -1.0)
+    n = int(full.count.item())
+    assert n == (256 - 31) ** 2
+    _, _, _, small = run_match(sncc, c.f, c.t, 10.0, -1.0, cand_cap=100)
+    assert int(small.count.item()) == n
+    assert int(small.status.item()) & sncc.STATUS_CAND_OVERFLOW
+    stored = small.cand[:100].cpu().numpy()
+    assert len(np.unique(stored)) == 100 and stored.min() >= 0 and stored.max() < n
+
+
+def test_match_uniform_template_rejected(sncc):
+    t = np.full((16, 16), 50, np.uint8)
+    seg = sncc.build_segments(t, 3.0)
+    tb = sncc.integral(dev(synth.random_image(1, 64, 64)))
+    mb = sncc.alloc_match(64, 64, 16, 16, 10)
+    plan = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(sncc.SnccError) as e:
+        sncc.match(seg, plan, tb, 0.5, mb)
+    assert e.value.code == sncc.ERR_UNIFORM
+
+
+def test_match_kmax(sncc):
+    c = synth.case_plain(M=150, N=150, W=40, H=40)
+    seg = sncc.build_segments(c.t, 0.0, 200)
+    ap = O.precompute_template_approximation(c.t, 0.0, 200)
+    assert seg.K_split <= 200 and seg.sigma_used == ap.sigma_used
+    _, _, _, mb = run_match(sncc, c.f, c.t, 0.0, 0.5, k_max=200)
+    assert np.abs(mb.rho.cpu().numpy() - O.segmented_ncc_map(c.f, ap, "sat")).max() <= TOL
+
+
+@pytest.mark.parametrize("sigma", [5.0, 10.0, 20.0])
+def test_match_hd_full_size_sampled(sncc, sigma):
+    """1920 x 1080 source, 64 x 64 template (the HD workload), full launch;
+    the oracle checks a seeded sample of offset rows."""
+    c = synth.case_hd(sigma_max=sigma)
+    ap = O.precompute_template_approximation(c.t, sigma)
+    tau = c.precision * ap.rho_max
+    seg, fd, tb, mb = run_match(sncc, c.f, c.t, sigma, tau)
+    V = c.f.shape[0] - 64 + 1
+    rows = np.unique(np.r_[np.random.default_rng(int(sigma)).choice(V, 10, replace=False), 0, V - 1,
+                            c.origin[1]])
+    ref = O.segmented_ncc_map(c.f, ap, "sat", rows=rows)
+    got = mb.rho.cpu().numpy()
+    assert np.abs(got[rows] - ref[rows]).max() <= TOL
+    cnt = int(mb.count.item())
+    check_candidates(ref, mb.cand[:min(cnt, mb.cand.numel())].cpu().numpy(), cnt, tau, rows=rows)
+
+
+def test_match_texture_full_size_sampled(sncc):
+    """4096 x 4096 high-texture source with a 256 x 256 template at sigma 5
+    (thousands of segments, 64-bit sum tables), full launch, sampled rows."""
+    c = synth.case_texture()
+    ap = O.precompute_template_approximation(c.t, 5.0)
+    assert ap.K > 1000
+    tau = c.precision * ap.rho_max
+    seg, fd, tb, mb = run_match(sncc, c.f, c.t, 5.0, tau)
+    assert tb.s_bits == 64
+    V = 4096 - 256 + 1
+    rows = np.array([0, 1234, c.origin[1], V - 1])
+    ref = O.segmented_ncc_map(c.f, ap, "sat", rows=rows)
+    got = mb.rho.cpu().numpy()
+    assert np.abs(got[rows] - ref[rows]).max() <= TOL
+    u0, v0 = c.origin
+    assert abs(got[v0, u0] - ap.rho_max) <= TOL  # noise-free crop: rho = NCC(t, k)
+
+
+# ------------------------------------------------------------------ fine pass
+def oracle_matches(f, t, ap, tau_c, tau_e):
+    rho_seg = O.segmented_ncc_map(f, ap, "sat")
+    cand = O.candidates(rho_seg, tau_c)
+    U = rho_seg.shape[1]
+    idx, rho = O.refine(f, t, cand, U, tau_e)
+    return rho_seg, idx, rho
+
+
+@pytest.mark.parametrize("M,N,W,H,sigma,p", [(256, 256, 32, 32, 10.0, 0.9), (180, 140, 48, 30, 4.0, 0.7),
+                                             (90, 70, 90, 20, 3.0, 0.5)])
+def test_refine_matches_oracle(sncc, M, N, W, H, sigma, p):
+    c = synth.case_plain(M=M, N=N, W=W, H=H, seed=99 + M)
+    ap = O.precompute_template_approximation(c.t, sigma)
+    tau_c, tau_e = p * ap.rho_max, p
+    rho_seg, idx_o, rho_o = oracle_matches(c.f, c.t, ap, tau_c, tau_e)
+    seg, fd, tb, mb = run_match(sncc, c.f, c.t, sigma, tau_c)
+    td = dev(c.t)
+    rb = sncc.alloc_refine(1 << 14)
+    sncc.refine(fd, td, seg, mb, tau_e, rb)
+    torch.cuda.synchronize()
+    assert int(mb.status.item()) == 0
+    u, v, rho = sncc.matches_to_numpy(rb)
+    U = M - W + 1
+    key = v * U + u
+    assert np.all(np.diff(key) > 0)  # sorted, distinct
+    ex = O.ncc_exact_at(c.f, c.t, u, v)
+    assert np.abs(rho - ex).max(initial=0) <= TOL
+    # sets agree outside the threshold bands
+    band_c = np.abs(rho_seg.ravel() - tau_c) < TOL
+    exact_all = O.ncc_exact_map(c.f, c.t).ravel()
+    band_e = np.abs(exact_all - tau_e) < TOL
+    amb = band_c | band_e
+    got = set(key.tolist())
+    want = set(idx_o.tolist())
+    diff = got ^ want
+    assert all(amb[d] for d in diff), sorted(diff)[:10]
+    if W == 32:
+        assert c.origin[1] * U + c.origin[0] in got
+
+
+def test_refine_output_overflow(sncc):
+    c = synth.case_plain()
+    seg, fd, tb, mb = run_match(sncc, c.f, c.t, 10.0, -1.0)
+    rb = sncc.alloc_refine(10)
+    sncc.refine(fd, dev(c.t), seg, mb, -1.0, rb)
+    torch.cuda.synchronize()
+    assert int(rb.nout.item()) == (256 - 31) ** 2
+    assert int(mb.status.item()) & sncc.STATUS_MATCH_OVERFLOW
+    u, v, rho = sncc.matches_to_numpy(rb)
+    assert len(u) == 10 and np.all(np.diff(v * 225 + u) > 0)
+
+
+# ------------------------------------------------------------------ exact comparator
+@pytest.mark.parametrize("M,N,W,H", [(256, 256, 32, 32), (70, 45, 13, 9), (200, 150, 100, 70), (97, 61, 97, 3)])
+def test_exact_map_vs_oracle(sncc, M, N, W, H):
+    c = synth.case_plain(M=M, N=N, W=W, H=H, seed=7 + W)
+    fd = dev(c.f)
+    tb = sncc.integral(fd)
+    seg = sncc.build_segments(c.t, 1.0)
+    rho = sncc.exact_map(fd, dev(c.t), seg.T, seg.T2, tb)
+    torch.cuda.synchronize()
+    ref = O.ncc_exact_map(c.f, c.t)
+    assert np.abs(rho.cpu().numpy() - ref).max() <= TOL
+
+
+def test_exact_map_hd_sampled(sncc):
+    c = synth.case_hd()
+    fd = dev(c.f)
+    tb = sncc.integral(fd)
+    seg = sncc.build_segments(c.t, 10.0)
+    rho = sncc.exact_map(fd, dev(c.t), seg.T, seg.T2, tb).cpu().numpy()
+    rows = np.array([0, 500, c.origin[1], 1016])
+    ref = O.ncc_exact_map(c.f, c.t, rows=rows)
+    assert np.abs(rho[rows] - ref[rows]).max() <= TOL
+    assert abs(rho[c.origin[1], c.origin[0]] - ref[c.origin[1], c.origin[0]]) <= TOL
+
+
+# ------------------------------------------------------------------ whole path
+def test_matcher_end_to_end(sncc):
+    c = synth.case_plain()
+    m = sncc.Matcher(c.t, c.sigma_max, 256, 256, precision=c.precision)
+    fd = dev(c.f)
+    m.run(fd)
+    torch.cuda.synchronize()
+    ap = O.precompute_template_approximation(c.t, c.sigma_max)
+    rho_seg, idx_o, rho_o = oracle_matches(c.f, c.t, ap, c.precision * ap.rho_max, c.precision)
+    u, v, rho = sncc.matches_to_numpy(m.rb)
+    assert m.status() == 0
+    np.testing.assert_array_equal(v * 225 + u, idx_o)
+    assert np.abs(rho - rho_o).max(initial=0) <= TOL
