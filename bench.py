@@ -182,9 +182,13 @@ def oracle_sample(case, sigmas, rows_per_sigma, seed=0):
 
 
 def calibrate_rows(case, budget_s: float) -> int:
-    _, secs, _, _ = oracle_sample(case, SIGMAS, 2, seed=12345)
-    per_row = secs / (2 * len(SIGMAS))
-    return max(1, int(budget_s / (per_row * len(SIGMAS))))
+    """Rows per threshold so that one oracle_sample takes about budget_s:
+    time = fixed (sum tables per call) + per_row * rows, fitted on 2 and 12 rows."""
+    _, t_small, _, _ = oracle_sample(case, SIGMAS, 2, seed=12345)
+    _, t_large, _, _ = oracle_sample(case, SIGMAS, 12, seed=12346)
+    per_row = max((t_large - t_small) / 10.0, 1e-6)
+    fixed = max(t_small - 2 * per_row, 0.0)
+    return max(1, int((budget_s - fixed) / per_row))
 
 
 def run_reference(args, world, rank, pg):

@@ -254,7 +254,7 @@ typedef struct {
     int32_t blocks;       /* template blocks */
     int32_t block_w;      /* block width and height (edge blocks may be smaller) */
     int32_t block_h;
-    int32_t corners;      /* distinct weighted corner points, summed over blocks */
+    int32_t corners;      /* distinct corner points with a nonzero weight, summed over blocks */
     int32_t max_corners;  /* largest corner count of one block */
     int64_t Q0;           /* sum of the weights over all pixels, sum_i W_i H_i q_i */
 } sncc_plan_info;

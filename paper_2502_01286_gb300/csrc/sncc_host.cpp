@@ -157,8 +157,9 @@ int build_plan(const sncc_segments* s, Plan& p) {
     }
     p.nbx = (W + p.BW - 1) / p.BW;
     p.nby = (H + p.BH - 1) / p.BH;
-    // Work-region pitch is one of two compile-time widths of the kernel.
-    p.WP = (p.BW <= 32) ? TILE_U + 32 + 1 : TILE_U + 64 + 1;
+    // Work-region pitch is one of two compile-time widths of the kernel,
+    // multiples of 4 so that a region row is a whole number of 16-byte units.
+    p.WP = (p.BW <= 32) ? 68 : 100;
 
     // Fixed-point scale: every |G| <= 4 max|q_i| must stay below 2^31.
     double maxc = 0.0;
@@ -188,6 +189,7 @@ int build_plan(const sncc_segments* s, Plan& p) {
     const int nblk = p.nbx * p.nby;
     std::vector<int32_t> blocks((size_t)4 * nblk);
     std::vector<int32_t> corners;
+    int nonzero = 0;
     p.max_corners = 0;
     for (int by_i = 0; by_i < p.nby; ++by_i) {
         for (int bx_i = 0; bx_i < p.nbx; ++bx_i) {
@@ -204,8 +206,15 @@ int build_plan(const sncc_segments* s, Plan& p) {
                     if (G != 0) {
                         corners.push_back(Y * p.WP + X);
                         corners.push_back((int32_t)G);
+                        ++nonzero;
                     }
                 }
+            // pad to a multiple of 4 corners with zero weights (16-byte loads
+            // of two corners, groups of four, no tail in the kernel)
+            while (((corners.size() / 2) - first) % 4 != 0) {
+                corners.push_back(0);
+                corners.push_back(0);
+            }
             const int cnt = (int)(corners.size() / 2) - first;
             const int b = by_i * p.nbx + bx_i;
             blocks[4 * b + 0] = bx;
@@ -216,6 +225,7 @@ int build_plan(const sncc_segments* s, Plan& p) {
         }
     }
     p.total_corners = (int)(corners.size() / 2);
+    p.nonzero_corners = nonzero;
     p.blocks_offset = 0;
     p.corners_offset = (size_t)nblk * 16;
     p.image.resize(blocks.size() + corners.size() + 4, 0);
@@ -336,7 +346,7 @@ int sncc_get_plan_info(const sncc_segments* seg, sncc_plan_info* out) {
     out->blocks = p->nbx * p->nby;
     out->block_w = p->BW;
     out->block_h = p->BH;
-    out->corners = p->total_corners;
+    out->corners = p->nonzero_corners;
     out->max_corners = p->max_corners;
     out->Q0 = p->Q0;
     return SNCC_OK;

@@ -38,15 +38,17 @@ struct Plan {
     int W = 0, H = 0;
     int BW = 0, BH = 0;     // block size (the last block in a row/column may be smaller)
     int nbx = 0, nby = 0;   // blocks across / down
-    int WP = 0;             // pitch (elements) of the re-based work region: 65 (BW <= 32) or 97
+    int WP = 0;             // pitch (elements) of the re-based work region: 68 (BW <= 32) or 100
     int F = 0;              // fixed-point fraction bits of q_i
     int64_t Q0 = 0;         // sum over the template of q(x, y)
     double Ek = 0.0;        // weighted energy of the approximation
     double n = 0.0;         // W * H
     int max_corners = 0;    // largest corner count of one block
-    int total_corners = 0;
+    int total_corners = 0;    // including the zero-weight padding
+    int nonzero_corners = 0;
     // Device image: int4 blocks[nblk] = {bx, by, first, count}, then int2
-    // corners[total] = {Y * WP + X, G}.
+    // corners[total] = {Y * WP + X, G}; each block's list starts on a
+    // multiple of 4 corners and is padded with zero weights to a multiple of 4.
     std::vector<int32_t> image;
     size_t blocks_offset = 0;   // bytes
     size_t corners_offset = 0;  // bytes

@@ -12,13 +12,18 @@
 //    shared by neighbouring segments are combined on the host, so each
 //    offset needs one sum-table read and one 32x32->64-bit multiply-add per
 //    distinct corner.
-//  * The template is processed in blocks; for each block a TMA tile load
-//    brings the sum-table region the tile touches into shared memory, which
-//    is re-based to the region origin (exact in wrapped 32-bit arithmetic,
-//    since every re-based entry is a box sum below 2^31) and then read with
-//    conflict-free 32-bit loads: lane l reads column l, warp w reads its own
-//    R rows.  The next block's TMA load is issued as soon as the raw buffer
-//    has been re-based, so it overlaps this block's arithmetic.
+//  * The template is processed in blocks.  For each block the sum-table
+//    region the tile touches is staged in one shared-memory buffer: a 2-D
+//    TMA tile load for 32-bit tables, 4-byte cp.async copies of the low
+//    words for 64-bit tables (box sums only need the table modulo 2^32).
+//    The region is then re-based in place to its own origin (exact in
+//    wrapped 32-bit arithmetic, since every re-based entry is a box sum
+//    below 2^31) and read with conflict-free 32-bit loads: lane l reads
+//    column l, warp w its own R rows.  One buffer keeps the footprint small
+//    enough for four CTAs per SM, whose staging overlaps each other's
+//    arithmetic.
+//  * Corner records are read two per 16-byte load, one group of four ahead
+//    of their use.
 //  * Epilogue: window sums from the global tables, exact integer variance
 //    n sum f^2 - (sum f)^2 divided by n in FP64, rho in FP32, warp-aggregated
 //    atomic append of candidates.
@@ -27,6 +32,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 #include <type_traits>
 
@@ -41,8 +47,8 @@ struct MatchArgs {
     const int4* blocks;
     const int2* corners;
     int nblk;
-    int RWB;  // raw box width (elements)
-    int RH;   // region rows = 8R + BH + 1
+    int RH;  // region rows = 8R + BH + 1
+    int M, N;
     int U, V, W, H;
     const void* s;
     const int64_t* s2;
@@ -63,6 +69,11 @@ struct MatchArgs {
 
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// Shared-memory layout (32-bit words from a 128-byte aligned base):
+//   work[align32(RH*WP)] | row0[128] | col0[160] | mbarrier (8 B) | flag
+__host__ __device__ constexpr int work_words(int RH, int WP) { return align_up(RH * WP, 32); }
+__host__ __device__ constexpr int smem_words(int RH, int WP) { return work_words(RH, WP) + 128 + 160 + 4; }
+
 template <bool S64>
 __device__ __forceinline__ long long sat_at(const void* s, int pitch, int X, int Y) {
     if constexpr (S64)
@@ -71,31 +82,36 @@ __device__ __forceinline__ long long sat_at(const void* s, int pitch, int X, int
         return static_cast<const int*>(s)[(size_t)Y * pitch + X];
 }
 
+template <int R, int WP>
+__device__ __forceinline__ void apply_corner(long long (&acc)[R], const int* wbase, int off, int g) {
+    const int* w = wbase + off;
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] += (long long)g * (long long)w[r * WP];
+}
+
 template <int R, bool S64, int WP>
 __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUtensorMap tmap, const MatchArgs a) {
-    using RawT = typename std::conditional<S64, long long, int>::type;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    volatile int* flag = reinterpret_cast<volatile int*>(smem + 8);
-    RawT* raw = reinterpret_cast<RawT*>(smem + 128);
-    const int raw_bytes = align_up(a.RWB * a.RH * (int)sizeof(RawT), 128);
-    int* work = reinterpret_cast<int*>(smem + 128 + raw_bytes);
-    const uint32_t tx_bytes = (uint32_t)(a.RWB * a.RH * (int)sizeof(RawT));
+    extern __shared__ __align__(128) unsigned char smem_base[];
+    // The TMA destination must start on a 128-byte boundary of the shared
+    // window; the host allocates 128 spare bytes for this adjustment.
+    int* work = reinterpret_cast<int*>(smem_base + ((128u - (smem_u32(smem_base) & 127u)) & 127u));
+    const int RH = a.RH;
+    int* row0 = work + work_words(RH, WP);
+    int* col0 = row0 + 128;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(col0 + 160);
+    volatile int* flag = reinterpret_cast<volatile int*>(bar + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int u0 = blockIdx.x * TILE_U, v0 = blockIdx.y * (WARPS * R);
 
     if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
+        if constexpr (!S64) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+        }
         *flag = 0;
     }
     __syncthreads();
-    if (tid == 0) {
-        const int4 b0 = a.blocks[0];
-        mbar_arrive_expect_tx(bar, tx_bytes);
-        tma_load_2d(raw, &tmap, u0 + b0.x, v0 + b0.y, bar);
-    }
 
     long long acc[R];
 #pragma unroll
@@ -104,52 +120,63 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
     uint32_t parity = 0;
 
     for (int b = 0; b < a.nblk; ++b) {
-        if (tid == 0 && !mbar_wait_bounded(bar, parity)) *flag = 1;
-        __syncthreads();
-        if (*flag) {
-            if (tid == 0) atomicOr(a.status, SNCC_STATUS_WAIT_TIMEOUT);
-            return;
-        }
-        (void)mbar_try_wait(bar, parity);  // phase is complete: acquire for this thread
-        parity ^= 1u;
-
-        // Re-base the raw region to its own origin, into the 32-bit work buffer.
-        const uint32_t c00 = (uint32_t)raw[0];
-        for (int Y = warp; Y < a.RH; Y += WARPS) {
-            const uint32_t cy = (uint32_t)raw[Y * a.RWB];
-            for (int X = lane; X < WP; X += 32) {
-                const uint32_t val = (uint32_t)raw[Y * a.RWB + X] - (uint32_t)raw[X] - cy + c00;
-                work[Y * WP + X] = (int)val;
-            }
-        }
-        __syncthreads();
-        if (tid == 0 && b + 1 < a.nblk) {  // raw is free: prefetch the next block
-            fence_proxy_async();
-            const int4 nb = a.blocks[b + 1];
-            mbar_arrive_expect_tx(bar, tx_bytes);
-            tma_load_2d(raw, &tmap, u0 + nb.x, v0 + nb.y, bar);
-        }
-
         const int4 blk = a.blocks[b];
-        const int2* cp = a.corners + blk.z;
-        const int cnt = blk.w;
-        int p = 0;
-        for (; p + 4 <= cnt; p += 4) {
-            int2 c[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) c[j] = __ldg(cp + p + j);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int* w = wbase + c[j].x;
-#pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] += (long long)c[j].y * (long long)w[r * WP];
+        const int x0 = u0 + blk.x, y0 = v0 + blk.y;
+        // ---- stage the region's sum-table entries (mod 2^32) ----
+        if constexpr (!S64) {
+            if (tid == 0) {
+                fence_proxy_async();  // earlier generic accesses to work precede the async write
+                mbar_arrive_expect_tx(bar, (uint32_t)(RH * WP * 4));
+                tma_load_2d(work, &tmap, x0, y0, bar);
+                if (!mbar_wait_bounded(bar, parity)) *flag = 1;
+            }
+            __syncthreads();
+            if (*flag) {
+                if (tid == 0) atomicOr(a.status, SNCC_STATUS_WAIT_TIMEOUT);
+                return;
+            }
+            (void)mbar_try_wait(bar, parity);  // phase complete: acquire for this thread
+            parity ^= 1u;
+        } else {
+            const long long* sp = static_cast<const long long*>(a.s);
+            for (int i = tid; i < RH * WP; i += WARPS * 32) {
+                const int Y = i / WP, X = i - Y * WP;
+                const int gx = x0 + X, gy = y0 + Y;
+                const bool in = (gx <= a.M) && (gy <= a.N);
+                cp_async_4(work + i, in ? sp + (size_t)gy * a.pitch + gx : sp, in);
+            }
+            cp_async_wait_all();
+            __syncthreads();
+        }
+        // ---- re-base in place to the region origin ----
+        for (int X = tid; X < WP; X += WARPS * 32) row0[X] = work[X];
+        for (int Y = tid; Y < RH; Y += WARPS * 32) col0[Y] = work[Y * WP];
+        __syncthreads();
+        {
+            const uint32_t c00 = (uint32_t)row0[0];
+            for (int Y = warp; Y < RH; Y += WARPS) {
+                const uint32_t cy = (uint32_t)col0[Y] - c00;
+                for (int X = lane; X < WP; X += 32)
+                    work[Y * WP + X] = (int)((uint32_t)work[Y * WP + X] - (uint32_t)row0[X] - cy);
             }
         }
-        for (; p < cnt; ++p) {
-            const int2 c = __ldg(cp + p);
-            const int* w = wbase + c.x;
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] += (long long)c.y * (long long)w[r * WP];
+        __syncthreads();
+        // ---- corner sum: one shared read and one multiply-add per (offset, corner) ----
+        const int4* cq = reinterpret_cast<const int4*>(a.corners + blk.z);
+        const int groups = blk.w >> 2;
+        if (groups > 0) {
+            int4 n0 = __ldg(cq), n1 = __ldg(cq + 1);
+            for (int g = 0; g < groups; ++g) {
+                const int4 c0 = n0, c1 = n1;
+                if (g + 1 < groups) {
+                    n0 = __ldg(cq + 2 * g + 2);
+                    n1 = __ldg(cq + 2 * g + 3);
+                }
+                apply_corner<R, WP>(acc, wbase, c0.x, c0.y);
+                apply_corner<R, WP>(acc, wbase, c0.z, c0.w);
+                apply_corner<R, WP>(acc, wbase, c1.x, c1.y);
+                apply_corner<R, WP>(acc, wbase, c1.z, c1.w);
+            }
         }
         __syncthreads();  // work is overwritten by the next block
     }
@@ -210,22 +237,16 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 template <int R, bool S64, int WP>
-size_t smem_bytes_for(int RWB, int RH) {
-    const int es = S64 ? 8 : 4;
-    return 128 + (size_t)align_up(RWB * RH * es, 128) + (size_t)WP * RH * 4;
-}
-
-template <int R, bool S64, int WP>
 cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
     const int RH = WARPS * R + BH + 1;
     MatchArgs args = a;
     args.RH = RH;
-    const size_t sm = smem_bytes_for<R, S64, WP>(a.RWB, RH);
+    const size_t sm = 128 + (size_t)smem_words(RH, WP) * 4;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
         attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        200 * 1024);
+                                        128 + smem_words(WARPS * R + 64 + 1, WP) * 4);
     });
     if (attr_err != cudaSuccess) return attr_err;
     dim3 grid((a.U + TILE_U - 1) / TILE_U, (a.V + WARPS * R - 1) / (WARPS * R));
@@ -274,31 +295,31 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
     if ((reinterpret_cast<uintptr_t>(d_plan) & 15) || (reinterpret_cast<uintptr_t>(d_s) & 15)) return SNCC_ERR_ARG;
     if ((int64_t)U * V >= ((int64_t)1 << 31)) return SNCC_ERR_UNSUPPORTED;
 
-    PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode();
-    if (!encode) return SNCC_ERR_CUDA;
     const bool s64 = (s_bits == 64);
-    const int es = s64 ? 8 : 4;
     const int R = choose_r(U, V);
     const int RH = WARPS * R + p->BH + 1;
-    const int RWB = align_up(p->WP, 16 / es);
-
     CUtensorMap map;
-    cuuint64_t gdim[2] = {(cuuint64_t)(M + 1), (cuuint64_t)(N + 1)};
-    cuuint64_t gstride[1] = {(cuuint64_t)sat_pitch * es};
-    cuuint32_t box[2] = {(cuuint32_t)RWB, (cuuint32_t)RH};
-    cuuint32_t estride[2] = {1, 1};
-    CUresult cr = encode(&map, s64 ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_INT32, 2,
-                         const_cast<void*>(d_s), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return SNCC_ERR_CUDA;
+    std::memset(&map, 0, sizeof(map));
+    if (!s64) {  // 2-D TMA tile map over the 32-bit table, box WP x RH
+        PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode();
+        if (!encode) return SNCC_ERR_CUDA;
+        cuuint64_t gdim[2] = {(cuuint64_t)(M + 1), (cuuint64_t)(N + 1)};
+        cuuint64_t gstride[1] = {(cuuint64_t)sat_pitch * 4};
+        cuuint32_t box[2] = {(cuuint32_t)p->WP, (cuuint32_t)RH};
+        cuuint32_t estride[2] = {1, 1};
+        CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, const_cast<void*>(d_s), gdim, gstride, box,
+                             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) return SNCC_ERR_CUDA;
+    }
 
     MatchArgs a;
     a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->blocks_offset);
     a.corners = reinterpret_cast<const int2*>(static_cast<const char*>(d_plan) + p->corners_offset);
     a.nblk = p->nbx * p->nby;
-    a.RWB = RWB;
     a.RH = RH;
+    a.M = M;
+    a.N = N;
     a.U = U;
     a.V = V;
     a.W = W;
@@ -323,9 +344,9 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
     if (cudaMemsetAsync(d_count, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
     if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
     cudaError_t e;
-    if (p->WP == 65)
-        e = s64 ? dispatch_r<true, 65>(R, map, a, p->BH, st) : dispatch_r<false, 65>(R, map, a, p->BH, st);
+    if (p->WP == 68)
+        e = s64 ? dispatch_r<true, 68>(R, map, a, p->BH, st) : dispatch_r<false, 68>(R, map, a, p->BH, st);
     else
-        e = s64 ? dispatch_r<true, 97>(R, map, a, p->BH, st) : dispatch_r<false, 97>(R, map, a, p->BH, st);
+        e = s64 ? dispatch_r<true, 100>(R, map, a, p->BH, st) : dispatch_r<false, 100>(R, map, a, p->BH, st);
     return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }

@@ -245,7 +245,7 @@ def oracle_matches(f, t, ap, tau_c, tau_e):
     return rho_seg, idx, rho
 
 
-@pytest.mark.parametrize("M,N,W,H,sigma,p", [(256, 256, 32, 32, 10.0, 0.9), (180, 140, 48, 30, 4.0, 0.7),
+@pytest.mark.parametrize("M,N,W,H,sigma,p", [(256, 256, 32, 32, 6.0, 0.9), (180, 140, 48, 30, 4.0, 0.7),
                                              (90, 70, 90, 20, 3.0, 0.5)])
 def test_refine_matches_oracle(sncc, M, N, W, H, sigma, p):
     c = synth.case_plain(M=M, N=N, W=W, H=H, seed=99 + M)
