@@ -146,6 +146,36 @@ size_t sncc_integral_workspace_bytes(int M, int N);
 int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int s_bits, int64_t* d_s2,
                   int sat_pitch, void* d_ws, size_t ws_bytes, sncc_stream_t stream);
 
+/* Size of the library's built-in scratch array used by sncc_integral_noalloc. */
+#define SNCC_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/*
+ * sncc_integral_noalloc - sncc_integral without a caller-supplied workspace
+ * and without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory where they call it, e.g. plug-ins whose host
+ * application owns the whole device-memory budget and forbids allocations by
+ * libraries, latency-critical loops that cannot afford the device-wide
+ * synchronisation cudaMalloc implies, or plain C callers that have no
+ * allocator to hand for a workspace buffer.
+ *
+ * Arguments, layout and results are those of sncc_integral (same kernels);
+ * the band sums live instead in a fixed array of SNCC_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) of device memory that every GPU which loads the library holds
+ * until the process exits.  That covers every source up to 6898 columns
+ * wide (any N up to 65535); larger sources return SNCC_ERR_CAPACITY and
+ * launch nothing.  No call allocates or frees memory.
+ *
+ * The first call on a device (with that device current) looks up the
+ * array's device address; make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind; nothing
+ * in it needs to start at zero, because each call writes every entry it
+ * later reads.  Calls whose executions overlap on the GPU (other streams,
+ * other host threads) race on the array: serialise them.
+ */
+int sncc_integral_noalloc(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int s_bits, int64_t* d_s2,
+                          int sat_pitch, sncc_stream_t stream);
+
 /* ------------------------------------------------------------------ */
 /* Coarse pass: segmented NCC, threshold, candidates (GPU)             */
 /* ------------------------------------------------------------------ */

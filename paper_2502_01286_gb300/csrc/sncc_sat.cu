@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "sncc.h"
 #include "sncc_internal.h"
@@ -269,4 +270,45 @@ extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, voi
     cudaError_t e = (g.E == 8) ? launch_emit<8>(g, d_f, M, N, f_stride, sat_pitch, cs1, cs2, d_s, s_bits, d_s2, st)
                                : launch_emit<16>(g, d_f, M, N, f_stride, sat_pitch, cs1, cs2, d_s, s_bits, d_s2, st);
     return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.  The band sums normally live in the caller's
+// workspace; here they live in this fixed array instead, which the library
+// owns for the life of the process on every device that loads it.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) int32_t sncc_noalloc_scratch[SNCC_NOALLOC_SCRATCH_BYTES / sizeof(int32_t)];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 128;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the array's name as a device pointer).
+int noalloc_scratch_address(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return SNCC_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, sncc_noalloc_scratch) != cudaSuccess || p == nullptr) return SNCC_ERR_CUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return SNCC_OK;
+}
+
+}  // namespace
+
+extern "C" int sncc_integral_noalloc(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int s_bits,
+                                     int64_t* d_s2, int sat_pitch, sncc_stream_t stream) {
+    if (!d_f || !d_s || !d_s2 || M <= 0 || N <= 0 || f_stride < M) return SNCC_ERR_ARG;
+    if (sncc_integral_workspace_bytes(M, N) > (size_t)SNCC_NOALLOC_SCRATCH_BYTES) return SNCC_ERR_CAPACITY;
+    void* scratch = nullptr;
+    const int rc = noalloc_scratch_address(&scratch);
+    if (rc != SNCC_OK) return rc;
+    return sncc_integral(d_f, M, N, f_stride, d_s, s_bits, d_s2, sat_pitch, scratch, SNCC_NOALLOC_SCRATCH_BYTES,
+                         stream);
 }

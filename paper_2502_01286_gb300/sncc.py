@@ -33,7 +33,8 @@ STATUS_CAND_OVERFLOW, STATUS_MATCH_OVERFLOW, STATUS_WAIT_TIMEOUT, STATUS_SORT_OV
 EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_sat_pitch",
             "sncc_integral_workspace_bytes", "sncc_integral", "sncc_plan_bytes", "sncc_plan_upload", "sncc_match",
             "sncc_refine_workspace_bytes", "sncc_refine", "sncc_exact_map", "sncc_get_plan_info",
-            "sncc_probe_smem_read"]
+            "sncc_probe_smem_read", "sncc_integral_noalloc"]
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class SnccError(RuntimeError):
@@ -74,6 +75,7 @@ _lib.sncc_sat_pitch.argtypes = [C.c_int]
 _lib.sncc_integral_workspace_bytes.argtypes = [C.c_int, C.c_int]
 _lib.sncc_integral_workspace_bytes.restype = C.c_size_t
 _lib.sncc_integral.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp, C.c_size_t, _vp]
+_lib.sncc_integral_noalloc.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp]
 _lib.sncc_plan_bytes.argtypes = [C.POINTER(_Segments)]
 _lib.sncc_plan_bytes.restype = C.c_size_t
 _lib.sncc_plan_upload.argtypes = [C.POINTER(_Segments), _vp, C.c_size_t, _vp]
@@ -229,6 +231,19 @@ def integral(f, tables: Optional[Tables] = None, s_bits: Optional[int] = None, w
     ws = workspace if workspace is not None else integral_workspace(M, N, f.device)
     _check(_lib.sncc_integral(f.data_ptr(), M, N, f.stride(0), tb.s.data_ptr(), tb.s_bits, tb.s2.data_ptr(),
                               tb.pitch, ws.data_ptr(), ws.numel(), _stream(stream)), "sncc_integral")
+    return tb
+
+
+def integral_noalloc(f, tables: Optional[Tables] = None, s_bits: Optional[int] = None, stream=None) -> Tables:
+    """sncc_integral_noalloc: the same sum tables with no workspace argument;
+    the library's fixed scratch array is used instead (see include/sncc.h)."""
+    torch = _torch()
+    if f.dtype != torch.uint8 or f.dim() != 2 or not f.is_cuda or f.stride(1) != 1:
+        raise ValueError("f must be a 2-D uint8 CUDA tensor with unit column stride")
+    N, M = f.shape
+    tb = tables or alloc_tables(M, N, s_bits, f.device)
+    _check(_lib.sncc_integral_noalloc(f.data_ptr(), M, N, f.stride(0), tb.s.data_ptr(), tb.s_bits,
+                                      tb.s2.data_ptr(), tb.pitch, _stream(stream)), "sncc_integral_noalloc")
     return tb
 
 
