@@ -255,6 +255,33 @@ int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t* d
                 sncc_match_t* d_out, int out_cap, int32_t* d_nout, void* d_ws, size_t ws_bytes,
                 int32_t* d_status, sncc_stream_t stream);
 
+/*
+ * sncc_refine_segmented - the paper's own fine stage: segmented NCC with a
+ * second, finer approximation at each candidate.
+ * Paper: Section 5 main algorithm steps 7g-7j (k_slow, threshold_slow =
+ * precision * rho_slow), Eq. 12 - Eq. 18.
+ *
+ * For candidate (u, v) of the coarse pass, rho is computed exactly as
+ * sncc_match computes it, but with `seg` (the fine approximation, e.g.
+ * sigma_max = 0.1 sigma_t with K_max = 5000) and only at the candidates.
+ * Matches have rho >= tau.
+ *
+ *   seg, d_plan             fine approximation and its uploaded plan
+ *   d_s, s_bits, d_s2       sum tables from sncc_integral, pitch sat_pitch
+ *   M, N                    source size
+ *   d_cand, d_count         candidates and count from sncc_match; the first
+ *                           min(*d_count, cand_cap) are read
+ *   tau                     fine threshold
+ *   d_out, out_cap, d_nout  matches sorted by v*U+u and their exact count
+ *                           (SNCC_STATUS_MATCH_OVERFLOW beyond out_cap)
+ *   d_ws, ws_bytes          workspace, >= sncc_refine_workspace_bytes(out_cap)
+ *   d_status                int32 status word (not cleared)
+ */
+int sncc_refine_segmented(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits,
+                          const int64_t* d_s2, int sat_pitch, int M, int N, const int32_t* d_cand,
+                          const int32_t* d_count, int cand_cap, float tau, sncc_match_t* d_out, int out_cap,
+                          int32_t* d_nout, void* d_ws, size_t ws_bytes, int32_t* d_status, sncc_stream_t stream);
+
 /* ------------------------------------------------------------------ */
 /* Same-GPU comparator: exact NCC at every offset                      */
 /* ------------------------------------------------------------------ */

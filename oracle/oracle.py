@@ -282,3 +282,32 @@ def refine(f, t, cand: np.ndarray, U: int, tau_exact: float) -> tuple[np.ndarray
     rho = ncc_exact_at(f, t, u, v)
     keep = rho >= tau_exact
     return cand[keep], rho[keep]
+
+
+def main_algorithm(f, t, precision: float = 0.9, fast: float = 0.99, slow: float = 0.1, k_max: int = 5000,
+                   weighted: bool = True):
+    """Section 5 main algorithm as printed: k_fast and k_slow from
+    precompute_template_approximation with sigma_max = fast * sigma_t and
+    slow * sigma_t (sigma_t the template's std, same definition as Eq. 2),
+    thresholds precision * rho_fast and precision * rho_slow (step 5), the
+    coarse pass at every offset (steps 7a-7f) and the fine pass at the
+    offsets that survive it (steps 7g-7j).
+
+    Returns a dict with both approximations, thresholds, the coarse map, the
+    candidate indices, the fine rho at each candidate and the matches
+    (indices, rho)."""
+    t64 = _as_f64(t)
+    sigma_t = float(np.sqrt(np.mean((t64 - t64.mean()) ** 2)))
+    ap_f = precompute_template_approximation(t64, fast * sigma_t, k_max, weighted)
+    ap_s = precompute_template_approximation(t64, slow * sigma_t, k_max, weighted)
+    thr_f = precision * ap_f.rho_max
+    thr_s = precision * ap_s.rho_max
+    rho_f = segmented_ncc_map(f, ap_f, "sat")
+    cand = candidates(rho_f, thr_f)
+    U = rho_f.shape[1]
+    rows = np.unique(cand // U)
+    rho_s_map = segmented_ncc_map(f, ap_s, "sat", rows=rows) if rows.size else np.full_like(rho_f, np.nan)
+    rho_s = rho_s_map.ravel()[cand] if cand.size else np.zeros(0)
+    keep = rho_s >= thr_s
+    return {"fast": ap_f, "slow": ap_s, "thr_fast": thr_f, "thr_slow": thr_s, "rho_fast": rho_f,
+            "cand": cand, "rho_slow_at_cand": rho_s, "idx": cand[keep], "rho": rho_s[keep]}

@@ -22,7 +22,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsncc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sncc_host.cpp", "sncc_sat.cu", "sncc_match.cu", "sncc_refine.cu", "sncc_exact.cu", "sncc_probe.cu"]
+SOURCES = ["sncc_host.cpp", "sncc_sat.cu", "sncc_match.cu", "sncc_refine.cu", "sncc_exact.cu", "sncc_probe.cu",
+           "sncc_refine_seg.cu"]
 
 
 def _nvcc() -> str:

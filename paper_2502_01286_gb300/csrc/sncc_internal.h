@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "sncc.h"
 
 namespace sncc {
@@ -55,6 +57,11 @@ struct Plan {
 };
 
 Plan* plan_of(const sncc_segments* s);
+
+// Writes the first min(*d_n, cap) records of `in` to `out` in ascending
+// v*U+u order (keys are distinct).  Defined in sncc_refine.cu.
+cudaError_t launch_rank_sort(const sncc_match_t* in, const int32_t* d_n, int cap, int U, sncc_match_t* out,
+                             cudaStream_t st);
 
 // Status helpers.
 const char* error_string(int code);

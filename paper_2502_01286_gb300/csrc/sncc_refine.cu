@@ -120,6 +120,15 @@ __global__ void __launch_bounds__(kSortThreads)
 }
 
 }  // namespace
+
+cudaError_t launch_rank_sort(const sncc_match_t* in, const int32_t* d_n, int cap, int U, sncc_match_t* out,
+                             cudaStream_t st) {
+    if (cap <= 0) return cudaSuccess;
+    const int sgrid = (cap + kSortThreads - 1) / kSortThreads;
+    rank_sort_kernel<<<sgrid, kSortThreads, 0, st>>>(in, d_n, cap, U, out);
+    return cudaGetLastError();
+}
+
 }  // namespace sncc
 
 extern "C" size_t sncc_refine_workspace_bytes(int out_cap) {
@@ -150,10 +159,6 @@ extern "C" int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const
                                                    d_cand, d_count, cand_cap, tau, U, V, scratch, out_cap, d_nout,
                                                    d_status);
     if (cudaGetLastError() != cudaSuccess) return SNCC_ERR_CUDA;
-    if (out_cap > 0) {
-        const int sgrid = (out_cap + kSortThreads - 1) / kSortThreads;
-        rank_sort_kernel<<<sgrid, kSortThreads, 0, st>>>(scratch, d_nout, out_cap, U, d_out);
-        if (cudaGetLastError() != cudaSuccess) return SNCC_ERR_CUDA;
-    }
+    if (launch_rank_sort(scratch, d_nout, out_cap, U, d_out, st) != cudaSuccess) return SNCC_ERR_CUDA;
     return SNCC_OK;
 }

@@ -78,12 +78,39 @@ __global__ void sat_band_colsum(const uint8_t* __restrict__ f, int M, int N, int
 }
 
 // Pass 2: in place, cs[b][x] := sum_{b' < b} cs[b'][x] (exclusive over bands).
-__global__ void sat_band_scan(int M, int nb, int32_t* __restrict__ cs1, int32_t* __restrict__ cs2) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= M) return;
+// One CTA per 32 columns: lane = column (coalesced rows), warp w owns a
+// contiguous chunk of bands; chunk totals are exchanged through shared memory
+// so every warp walks only nb/8 bands, twice.
+__global__ void __launch_bounds__(256) sat_band_scan(int M, int nb, int32_t* __restrict__ cs1,
+                                                     int32_t* __restrict__ cs2) {
+    __shared__ int32_t tot1[8][32], tot2[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = blockIdx.x * 32 + lane;
+    const int per = (nb + 7) / 8;
+    const int b0 = min(warp * per, nb), b1 = min(b0 + per, nb);
+    int32_t s1 = 0, s2 = 0;
+    if (x < M) {
+        int b = b0;
+        for (; b + 8 <= b1; b += 8) {
+            int32_t v1[8], v2[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                v1[i] = cs1[(size_t)(b + i) * M + x];
+                v2[i] = cs2[(size_t)(b + i) * M + x];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { s1 += v1[i]; s2 += v2[i]; }
+        }
+        for (; b < b1; ++b) { s1 += cs1[(size_t)b * M + x]; s2 += cs2[(size_t)b * M + x]; }
+    }
+    tot1[warp][lane] = s1;
+    tot2[warp][lane] = s2;
+    __syncthreads();
     int32_t r1 = 0, r2 = 0;
-    int b = 0;
-    for (; b + 8 <= nb; b += 8) {
+    for (int w = 0; w < warp; ++w) { r1 += tot1[w][lane]; r2 += tot2[w][lane]; }
+    if (x >= M) return;
+    int b = b0;
+    for (; b + 8 <= b1; b += 8) {
         int32_t v1[8], v2[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -98,7 +125,7 @@ __global__ void sat_band_scan(int M, int nb, int32_t* __restrict__ cs1, int32_t*
             r2 += v2[i];
         }
     }
-    for (; b < nb; ++b) {
+    for (; b < b1; ++b) {
         const int32_t v1 = cs1[(size_t)b * M + x], v2 = cs2[(size_t)b * M + x];
         cs1[(size_t)b * M + x] = r1;
         cs2[(size_t)b * M + x] = r2;
@@ -266,7 +293,7 @@ extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, voi
     cudaStream_t st = (cudaStream_t)stream;
     dim3 g1((M / 4 + 1 + 255) / 256, g.nb);
     sat_band_colsum<<<g1, 256, 0, st>>>(d_f, M, N, f_stride, g.R, cs1, cs2);
-    sat_band_scan<<<(M + 255) / 256, 256, 0, st>>>(M, g.nb, cs1, cs2);
+    sat_band_scan<<<(M + 31) / 32, 256, 0, st>>>(M, g.nb, cs1, cs2);
     cudaError_t e = (g.E == 8) ? launch_emit<8>(g, d_f, M, N, f_stride, sat_pitch, cs1, cs2, d_s, s_bits, d_s2, st)
                                : launch_emit<16>(g, d_f, M, N, f_stride, sat_pitch, cs1, cs2, d_s, s_bits, d_s2, st);
     return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;

@@ -33,7 +33,7 @@ STATUS_CAND_OVERFLOW, STATUS_MATCH_OVERFLOW, STATUS_WAIT_TIMEOUT, STATUS_SORT_OV
 EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_sat_pitch",
             "sncc_integral_workspace_bytes", "sncc_integral", "sncc_plan_bytes", "sncc_plan_upload", "sncc_match",
             "sncc_refine_workspace_bytes", "sncc_refine", "sncc_exact_map", "sncc_get_plan_info",
-            "sncc_probe_smem_read", "sncc_integral_noalloc"]
+            "sncc_probe_smem_read", "sncc_integral_noalloc", "sncc_refine_segmented"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -85,6 +85,8 @@ _lib.sncc_refine_workspace_bytes.argtypes = [C.c_int]
 _lib.sncc_refine_workspace_bytes.restype = C.c_size_t
 _lib.sncc_refine.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64,
                              _vp, _vp, C.c_int, C.c_float, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp]
+_lib.sncc_refine_segmented.argtypes = [C.POINTER(_Segments), _vp, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int,
+                                       _vp, _vp, C.c_int, C.c_float, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp]
 _lib.sncc_get_plan_info.argtypes = [C.POINTER(_Segments), C.POINTER(PlanInfo)]
 _lib.sncc_probe_smem_read.argtypes = [_vp, C.c_int, C.c_int, _vp]
 _lib.sncc_exact_map.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64,
@@ -312,6 +314,18 @@ def refine(f, t_dev, seg: Segments, bufs: MatchBuffers, tau: float, rb: RefineBu
                             _stream(stream)), "sncc_refine")
 
 
+def refine_segmented(seg_fine: Segments, plan_fine, tables: Tables, bufs: MatchBuffers, tau: float,
+                     rb: RefineBuffers, cand_cap: Optional[int] = None, stream=None) -> None:
+    """sncc_refine_segmented: the paper's fine stage (k_slow) at the coarse
+    candidates in bufs; matches land in rb.out sorted by v*U+u."""
+    cap = bufs.cand.numel() if cand_cap is None else cand_cap
+    _check(_lib.sncc_refine_segmented(seg_fine.ref(), plan_fine.data_ptr(), tables.s.data_ptr(), tables.s_bits,
+                                      tables.s2.data_ptr(), tables.pitch, tables.M, tables.N, bufs.cand.data_ptr(),
+                                      bufs.count.data_ptr(), cap, float(tau), rb.out.data_ptr(), rb.cap,
+                                      rb.nout.data_ptr(), rb.ws.data_ptr(), rb.ws.numel(), bufs.status.data_ptr(),
+                                      _stream(stream)), "sncc_refine_segmented")
+
+
 def matches_to_numpy(rb: RefineBuffers):
     """(u, v, rho) arrays of the stored matches (after the stream is synced)."""
     import torch
@@ -345,6 +359,45 @@ def probe_smem_read(sink, ctas: int, iters: int, stream=None) -> int:
 # ---------------------------------------------------------------------------
 # The whole path, as a user calls it
 # ---------------------------------------------------------------------------
+def template_sigma(t: np.ndarray) -> float:
+    """sigma_t of the paper's thresholds: the population std of the template."""
+    return float(np.asarray(t, np.float64).std())
+
+
+class PaperMatcher:
+    """The paper's own two-approximation search (Section 5 main algorithm):
+    coarse k_fast (sigma_max = 0.99 sigma_t) at every offset, then the finer
+    k_slow (sigma_max = 0.1 sigma_t, K_max = 5000) at the candidates,
+    thresholds precision * rho_fast and precision * rho_slow."""
+
+    def __init__(self, t: np.ndarray, M: int, N: int, precision: float = 0.9, fast: float = 0.99,
+                 slow: float = 0.1, k_max: int = 5000, cand_cap: int = 1 << 20, out_cap: int = 1 << 16,
+                 keep_rho: bool = True, device="cuda"):
+        st = template_sigma(t)
+        self.fast = build_segments(t, fast * st, k_max)
+        self.slow = build_segments(t, slow * st, k_max)
+        if not (self.fast.Ek > 0 and self.slow.Ek > 0):
+            raise SnccError(ERR_UNIFORM, "PaperMatcher")
+        self.M, self.N = M, N
+        self.W, self.H = self.fast.W, self.fast.H
+        self.tau_fast = float(precision) * self.fast.rho_max
+        self.tau_slow = float(precision) * self.slow.rho_max
+        self.plan_fast = upload_plan(self.fast, device)
+        self.plan_slow = upload_plan(self.slow, device)
+        self.tables = alloc_tables(M, N, None, device)
+        self.ws = integral_workspace(M, N, device)
+        self.mb = alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device)
+        self.rb = alloc_refine(out_cap, device)
+
+    def run(self, f, stream=None):
+        integral(f, self.tables, workspace=self.ws, stream=stream)
+        match(self.fast, self.plan_fast, self.tables, self.tau_fast, self.mb, stream=stream)
+        refine_segmented(self.slow, self.plan_slow, self.tables, self.mb, self.tau_slow, self.rb, stream=stream)
+
+    def status(self) -> int:
+        return int(self.mb.status.item())
+
+
 class Matcher:
     """Segmented-NCC template matcher for one template on one GPU.
 

@@ -327,3 +327,37 @@ def test_matcher_end_to_end(sncc):
     assert m.status() == 0
     np.testing.assert_array_equal(v * 225 + u, idx_o)
     assert np.abs(rho - rho_o).max(initial=0) <= TOL
+
+
+# ------------------------------------------------------------------ the paper's two-approximation search
+@pytest.mark.parametrize("M,N,W,H,p,seed", [(256, 256, 32, 32, 0.9, 0), (300, 220, 64, 48, 0.8, 5),
+                                            (200, 180, 100, 70, 0.7, 9)])
+def test_paper_two_stage_matches_oracle(sncc, M, N, W, H, p, seed):
+    """Coarse k_fast at every offset, k_slow at the candidates (Section 5),
+    through sncc_match + sncc_refine_segmented, against the oracle's main
+    algorithm; sets agree outside the +-TOL bands of both thresholds."""
+    c = synth.case_plain(M=M, N=N, W=W, H=H, seed=synth.BASE_SEED + seed)
+    r = O.main_algorithm(c.f, c.t, precision=p)
+    m = sncc.PaperMatcher(c.t, M, N, precision=p)
+    np.testing.assert_array_equal(m.fast.table, r["fast"].segments)
+    np.testing.assert_array_equal(m.slow.table, r["slow"].segments)
+    fd = dev(c.f)
+    m.run(fd)
+    torch.cuda.synchronize()
+    assert m.status() == 0
+    assert np.abs(m.mb.rho.cpu().numpy() - r["rho_fast"]).max() <= TOL
+    u, v, rho = sncc.matches_to_numpy(m.rb)
+    U = M - W + 1
+    key = v * U + u
+    assert np.all(np.diff(key) > 0)
+    ap_s = r["slow"]
+    rows = np.unique(v)
+    ref_s = O.segmented_ncc_map(c.f, ap_s, "sat", rows=rows) if rows.size else None
+    if rows.size:
+        assert np.abs(rho - ref_s[v, u]).max() <= TOL
+    # set agreement outside the bands
+    full_s = O.segmented_ncc_map(c.f, ap_s, "sat").ravel()
+    amb = (np.abs(r["rho_fast"].ravel() - r["thr_fast"]) < TOL) | (np.abs(full_s - r["thr_slow"]) < TOL)
+    diff = set(key.tolist()) ^ set(r["idx"].tolist())
+    assert all(amb[d] for d in diff), sorted(diff)[:10]
+    assert len(r["idx"]) > 0

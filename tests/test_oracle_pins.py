@@ -348,3 +348,24 @@ def test_candidates_and_refine_brute_force():
     np.testing.assert_allclose(rho, ex.ravel()[want], atol=1e-12)
     u0, v0 = c.origin
     assert v0 * U + u0 in set(idx.tolist())
+
+
+def test_main_algorithm_two_approximations_brute_force():
+    """Section 5 main algorithm: matches are the offsets where Eq. 1 against
+    the rendered k_fast passes precision * rho_fast and Eq. 1 against the
+    rendered k_slow passes precision * rho_slow (numpy Pearson correlation),
+    with sigma_fast = 0.99 sigma_t and sigma_slow = 0.1 sigma_t."""
+    c = synth.case_plain(M=56, N=44, W=12, H=10, noise=1.0, seed=4321)
+    p = 0.6
+    r = O.main_algorithm(c.f, c.t, precision=p)
+    st = c.t.astype(np.float64).std()
+    ap_f = O.precompute_template_approximation(c.t, 0.99 * st, 5000)
+    ap_s = O.precompute_template_approximation(c.t, 0.1 * st, 5000)
+    np.testing.assert_array_equal(r["fast"].segments, ap_f.segments)
+    np.testing.assert_array_equal(r["slow"].segments, ap_s.segments)
+    pf = pearson_map(c.f, ap_f.render())
+    ps = pearson_map(c.f, ap_s.render())
+    want = np.flatnonzero(((pf >= p * ap_f.rho_max) & (ps >= p * ap_s.rho_max)).ravel())
+    np.testing.assert_array_equal(r["idx"], want)
+    np.testing.assert_allclose(r["rho"], ps.ravel()[want], atol=1e-10)
+    assert len(want) > 0 and ap_s.K > ap_f.K
