@@ -308,7 +308,7 @@ int sncc_exact_map(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t
 /* Shape of the matching plan built by sncc_build_segments. */
 typedef struct {
     int32_t F;            /* fraction bits of the fixed-point weights q_i */
-    int32_t blocks;       /* template blocks */
+    int32_t blocks;       /* template blocks that hold at least one corner */
     int32_t block_w;      /* block width and height (edge blocks may be smaller) */
     int32_t block_h;
     int32_t corners;      /* distinct corner points with a nonzero weight, summed over blocks */

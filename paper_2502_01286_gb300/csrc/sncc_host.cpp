@@ -186,8 +186,7 @@ int build_plan(const sncc_segments* s, Plan& p) {
     p.Q0 = Q0;
 
     // Corner lists, block by block.
-    const int nblk = p.nbx * p.nby;
-    std::vector<int32_t> blocks((size_t)4 * nblk);
+    std::vector<int32_t> blocks;
     std::vector<int32_t> corners;
     int nonzero = 0;
     p.max_corners = 0;
@@ -216,18 +215,19 @@ int build_plan(const sncc_segments* s, Plan& p) {
                 corners.push_back(0);
             }
             const int cnt = (int)(corners.size() / 2) - first;
-            const int b = by_i * p.nbx + bx_i;
-            blocks[4 * b + 0] = bx;
-            blocks[4 * b + 1] = by;
-            blocks[4 * b + 2] = first;
-            blocks[4 * b + 3] = cnt;
+            if (cnt == 0) continue;  // a block inside one segment adds nothing
+            blocks.push_back(bx);
+            blocks.push_back(by);
+            blocks.push_back(first);
+            blocks.push_back(cnt);
             p.max_corners = std::max(p.max_corners, cnt);
         }
     }
+    p.nblk = (int)(blocks.size() / 4);
     p.total_corners = (int)(corners.size() / 2);
     p.nonzero_corners = nonzero;
     p.blocks_offset = 0;
-    p.corners_offset = (size_t)nblk * 16;
+    p.corners_offset = (size_t)p.nblk * 16;
     p.image.resize(blocks.size() + corners.size() + 4, 0);
     std::memcpy(p.image.data(), blocks.data(), blocks.size() * sizeof(int32_t));
     if (!corners.empty())
@@ -343,7 +343,7 @@ int sncc_get_plan_info(const sncc_segments* seg, sncc_plan_info* out) {
     if (!out || !p) return SNCC_ERR_ARG;
     if (p->image.empty()) return SNCC_ERR_UNIFORM;
     out->F = p->F;
-    out->blocks = p->nbx * p->nby;
+    out->blocks = p->nblk;
     out->block_w = p->BW;
     out->block_h = p->BH;
     out->corners = p->nonzero_corners;

@@ -40,6 +40,7 @@ struct Plan {
     int W = 0, H = 0;
     int BW = 0, BH = 0;     // block size (the last block in a row/column may be smaller)
     int nbx = 0, nby = 0;   // blocks across / down
+    int nblk = 0;           // blocks that hold at least one corner (the others are dropped)
     int WP = 0;             // pitch (elements) of the re-based work region: 68 (BW <= 32) or 100
     int F = 0;              // fixed-point fraction bits of q_i
     int64_t Q0 = 0;         // sum over the template of q(x, y)

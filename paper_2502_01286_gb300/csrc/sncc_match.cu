@@ -13,15 +13,16 @@
 //    offset needs one sum-table read and one 32x32->64-bit multiply-add per
 //    distinct corner.
 //  * The template is processed in blocks.  For each block the sum-table
-//    region the tile touches is staged in one shared-memory buffer: a 2-D
-//    TMA tile load for 32-bit tables, 4-byte cp.async copies of the low
-//    words for 64-bit tables (box sums only need the table modulo 2^32).
-//    The region is then re-based in place to its own origin (exact in
-//    wrapped 32-bit arithmetic, since every re-based entry is a box sum
-//    below 2^31) and read with conflict-free 32-bit loads: lane l reads
-//    column l, warp w its own R rows.  One buffer keeps the footprint small
-//    enough for four CTAs per SM, whose staging overlaps each other's
-//    arithmetic.
+//    region the tile touches is staged in shared memory and re-based to its
+//    own origin (exact in wrapped 32-bit arithmetic, since every re-based
+//    entry is a box sum below 2^31):
+//      - 32-bit tables: a 2-D TMA tile load completing on an mbarrier, then
+//        an in-place re-base; templates of several blocks double-buffer, so
+//        block b+1's tile is in flight while block b computes;
+//      - 64-bit tables: the low words (box sums only need the table modulo
+//        2^32) are loaded through registers and stored already re-based.
+//    The region is read with conflict-free 32-bit loads: lane l reads
+//    column l, warp w its own R rows.
 //  * Corner records are read two per 16-byte load, one group of four ahead
 //    of their use.
 //  * Epilogue: window sums from the global tables, exact integer variance
@@ -70,9 +71,11 @@ struct MatchArgs {
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
 // Shared-memory layout (32-bit words from a 128-byte aligned base):
-//   work[align32(RH*WP)] | row0[128] | col0[160] | mbarrier (8 B) | flag
+//   work[NBUF][align32(RH*WP)] | row0[128] | col0[160] | mbarrier[2] (16 B) | flag
 __host__ __device__ constexpr int work_words(int RH, int WP) { return align_up(RH * WP, 32); }
-__host__ __device__ constexpr int smem_words(int RH, int WP) { return work_words(RH, WP) + 128 + 160 + 4; }
+__host__ __device__ constexpr int smem_words(int RH, int WP, int nbuf) {
+    return nbuf * work_words(RH, WP) + 128 + 160 + 8;
+}
 
 template <bool S64>
 __device__ __forceinline__ long long sat_at(const void* s, int pitch, int X, int Y) {
@@ -89,24 +92,67 @@ __device__ __forceinline__ void apply_corner(long long (&acc)[R], const int* wba
     for (int r = 0; r < R; ++r) acc[r] += (long long)g * (long long)w[r * WP];
 }
 
-template <int R, bool S64, int WP>
+// 32-bit tables: starts the TMA tile copy of a block's region into `buf`
+// (thread 0 issues; completion on `bar`).
+template <int WP>
+__device__ __forceinline__ void stage_region_tma(const CUtensorMap* map, int* buf, uint64_t* bar, int x0, int y0,
+                                                 int RH, int tid) {
+    if (tid == 0) {
+        fence_proxy_async();  // earlier generic accesses to buf precede the async write
+        mbar_arrive_expect_tx(bar, (uint32_t)(RH * WP * 4));
+        tma_load_2d(buf, map, x0, y0, bar);
+    }
+}
+
+// 64-bit tables: loads the low words of a block's region through registers
+// and stores them already re-based to the region origin (wrapped 32-bit
+// arithmetic).  Lane l owns columns l, l+32, ...; warp w owns rows w, w+8, ...
+// Entries past the table, which only invalid offsets read, load as zero.
+template <int WP>
+__device__ __forceinline__ void stage_region_regs(const MatchArgs& a, int* buf, int x0, int y0, int RH, int lane,
+                                                  int warp) {
+    constexpr int KX = (WP + 31) / 32;
+    const uint32_t* lo = static_cast<const uint32_t*>(a.s);  // little endian: low word first
+    auto at = [&](int gx, int gy) -> uint32_t {
+        return (gx <= a.M && gy <= a.N) ? __ldg(lo + 2 * ((size_t)gy * a.pitch + gx)) : 0u;
+    };
+    const uint32_t c00 = at(x0, y0);
+    uint32_t r0[KX];
+#pragma unroll
+    for (int k = 0; k < KX; ++k) r0[k] = at(x0 + lane + 32 * k, y0) - c00;
+    for (int Y = warp; Y < RH; Y += WARPS) {
+        const int gy = y0 + Y;
+        const uint32_t cy = at(x0, gy);
+        uint32_t v[KX];
+#pragma unroll
+        for (int k = 0; k < KX; ++k) v[k] = (lane + 32 * k < WP) ? at(x0 + lane + 32 * k, gy) : 0u;
+#pragma unroll
+        for (int k = 0; k < KX; ++k)
+            if (lane + 32 * k < WP) buf[Y * WP + lane + 32 * k] = (int)(v[k] - r0[k] - cy);
+    }
+}
+
+template <int R, bool S64, int WP, bool PIPE>
 __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUtensorMap tmap, const MatchArgs a) {
+    constexpr int NBUF = PIPE ? 2 : 1;
     extern __shared__ __align__(128) unsigned char smem_base[];
     // The TMA destination must start on a 128-byte boundary of the shared
     // window; the host allocates 128 spare bytes for this adjustment.
-    int* work = reinterpret_cast<int*>(smem_base + ((128u - (smem_u32(smem_base) & 127u)) & 127u));
+    int* work0 = reinterpret_cast<int*>(smem_base + ((128u - (smem_u32(smem_base) & 127u)) & 127u));
     const int RH = a.RH;
-    int* row0 = work + work_words(RH, WP);
+    const int WW = work_words(RH, WP);
+    int* row0 = work0 + NBUF * WW;
     int* col0 = row0 + 128;
     uint64_t* bar = reinterpret_cast<uint64_t*>(col0 + 160);
-    volatile int* flag = reinterpret_cast<volatile int*>(bar + 1);
+    volatile int* flag = reinterpret_cast<volatile int*>(bar + 2);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int u0 = blockIdx.x * TILE_U, v0 = blockIdx.y * (WARPS * R);
 
     if (tid == 0) {
         if constexpr (!S64) {
-            mbar_init(bar, 1);
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
             fence_mbar_init();
         }
         *flag = 0;
@@ -116,52 +162,53 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
     long long acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
-    const int* wbase = work + warp * R * WP + lane;
-    uint32_t parity = 0;
+    uint32_t parity_bits = 0u;  // bit i: phase parity expected next on bar[i]
 
+    if (!S64 && a.nblk > 0) {
+        const int4 b0 = a.blocks[0];
+        stage_region_tma<WP>(&tmap, work0, &bar[0], u0 + b0.x, v0 + b0.y, RH, tid);
+    }
+    const int* wbase0 = work0 + warp * R * WP + lane;
     for (int b = 0; b < a.nblk; ++b) {
+        const int cur = PIPE ? (b & 1) : 0;
+        int* work = PIPE ? work0 + cur * WW : work0;
         const int4 blk = a.blocks[b];
-        const int x0 = u0 + blk.x, y0 = v0 + blk.y;
-        // ---- stage the region's sum-table entries (mod 2^32) ----
         if constexpr (!S64) {
-            if (tid == 0) {
-                fence_proxy_async();  // earlier generic accesses to work precede the async write
-                mbar_arrive_expect_tx(bar, (uint32_t)(RH * WP * 4));
-                tma_load_2d(work, &tmap, x0, y0, bar);
-                if (!mbar_wait_bounded(bar, parity)) *flag = 1;
+            const bool ahead = PIPE && (b + 1 < a.nblk);
+            if (ahead) {  // the other buffer was released by the barrier ending block b-1
+                const int4 nb = a.blocks[b + 1];
+                stage_region_tma<WP>(&tmap, work0 + (cur ^ 1) * WW, &bar[cur ^ 1], u0 + nb.x, v0 + nb.y, RH, tid);
             }
+            // ---- wait for block b's region, then re-base it in place ----
+            const uint32_t par = (parity_bits >> cur) & 1u;
+            if (tid == 0 && !mbar_wait_bounded(&bar[cur], par)) *flag = 1;
             __syncthreads();
             if (*flag) {
                 if (tid == 0) atomicOr(a.status, SNCC_STATUS_WAIT_TIMEOUT);
+                // let an outstanding prefetch land before the CTA's memory is released
+                if (tid == 0 && ahead) (void)mbar_wait_bounded(&bar[cur ^ 1], (parity_bits >> (cur ^ 1)) & 1u);
+                __syncthreads();
                 return;
             }
-            (void)mbar_try_wait(bar, parity);  // phase complete: acquire for this thread
-            parity ^= 1u;
-        } else {
-            const long long* sp = static_cast<const long long*>(a.s);
-            for (int i = tid; i < RH * WP; i += WARPS * 32) {
-                const int Y = i / WP, X = i - Y * WP;
-                const int gx = x0 + X, gy = y0 + Y;
-                const bool in = (gx <= a.M) && (gy <= a.N);
-                cp_async_4(work + i, in ? sp + (size_t)gy * a.pitch + gx : sp, in);
-            }
-            cp_async_wait_all();
+            (void)mbar_try_wait(&bar[cur], par);  // phase complete: acquire for this thread
+            parity_bits ^= 1u << cur;
+            for (int X = tid; X < WP; X += WARPS * 32) row0[X] = work[X];
+            for (int Y = tid; Y < RH; Y += WARPS * 32) col0[Y] = work[Y * WP];
             __syncthreads();
-        }
-        // ---- re-base in place to the region origin ----
-        for (int X = tid; X < WP; X += WARPS * 32) row0[X] = work[X];
-        for (int Y = tid; Y < RH; Y += WARPS * 32) col0[Y] = work[Y * WP];
-        __syncthreads();
-        {
-            const uint32_t c00 = (uint32_t)row0[0];
-            for (int Y = warp; Y < RH; Y += WARPS) {
-                const uint32_t cy = (uint32_t)col0[Y] - c00;
-                for (int X = lane; X < WP; X += 32)
-                    work[Y * WP + X] = (int)((uint32_t)work[Y * WP + X] - (uint32_t)row0[X] - cy);
+            {
+                const uint32_t c00 = (uint32_t)row0[0];
+                for (int Y = warp; Y < RH; Y += WARPS) {
+                    const uint32_t cy = (uint32_t)col0[Y] - c00;
+                    for (int X = lane; X < WP; X += 32)
+                        work[Y * WP + X] = (int)((uint32_t)work[Y * WP + X] - (uint32_t)row0[X] - cy);
+                }
             }
+        } else {
+            stage_region_regs<WP>(a, work, u0 + blk.x, v0 + blk.y, RH, lane, warp);
         }
         __syncthreads();
         // ---- corner sum: one shared read and one multiply-add per (offset, corner) ----
+        const int* wbase = PIPE ? wbase0 + cur * WW : wbase0;
         const int4* cq = reinterpret_cast<const int4*>(a.corners + blk.z);
         const int groups = blk.w >> 2;
         if (groups > 0) {
@@ -178,7 +225,11 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
                 apply_corner<R, WP>(acc, wbase, c1.z, c1.w);
             }
         }
-        __syncthreads();  // work is overwritten by the next block
+        __syncthreads();  // this buffer is restaged two blocks later (PIPE) or next block
+        if (!S64 && !PIPE && b + 1 < a.nblk) {
+            const int4 nb = a.blocks[b + 1];
+            stage_region_tma<WP>(&tmap, work0, &bar[0], u0 + nb.x, v0 + nb.y, RH, tid);
+        }
     }
 
     // Epilogue: normalise, threshold, compact.
@@ -236,30 +287,31 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-template <int R, bool S64, int WP>
+template <int R, bool S64, int WP, bool PIPE>
 cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
+    constexpr int NBUF = PIPE ? 2 : 1;
     const int RH = WARPS * R + BH + 1;
     MatchArgs args = a;
     args.RH = RH;
-    const size_t sm = 128 + (size_t)smem_words(RH, WP) * 4;
+    const size_t sm = 128 + (size_t)smem_words(RH, WP, NBUF) * 4;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        128 + smem_words(WARPS * R + 64 + 1, WP) * 4);
+        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP, PIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        128 + smem_words(WARPS * R + 64 + 1, WP, NBUF) * 4);
     });
     if (attr_err != cudaSuccess) return attr_err;
     dim3 grid((a.U + TILE_U - 1) / TILE_U, (a.V + WARPS * R - 1) / (WARPS * R));
-    match_kernel<R, S64, WP><<<grid, WARPS * 32, sm, st>>>(map, args);
+    match_kernel<R, S64, WP, PIPE><<<grid, WARPS * 32, sm, st>>>(map, args);
     return cudaGetLastError();
 }
 
-template <bool S64, int WP>
+template <bool S64, int WP, bool PIPE>
 cudaError_t dispatch_r(int R, const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
     switch (R) {
-        case 8: return launch_match<8, S64, WP>(map, a, BH, st);
-        case 4: return launch_match<4, S64, WP>(map, a, BH, st);
-        default: return launch_match<2, S64, WP>(map, a, BH, st);
+        case 8: return launch_match<8, S64, WP, PIPE>(map, a, BH, st);
+        case 4: return launch_match<4, S64, WP, PIPE>(map, a, BH, st);
+        default: return launch_match<2, S64, WP, PIPE>(map, a, BH, st);
     }
 }
 
@@ -316,7 +368,7 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
     MatchArgs a;
     a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->blocks_offset);
     a.corners = reinterpret_cast<const int2*>(static_cast<const char*>(d_plan) + p->corners_offset);
-    a.nblk = p->nbx * p->nby;
+    a.nblk = p->nblk;
     a.RH = RH;
     a.M = M;
     a.N = N;
@@ -344,9 +396,15 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
     if (cudaMemsetAsync(d_count, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
     if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
     cudaError_t e;
-    if (p->WP == 68)
-        e = s64 ? dispatch_r<true, 68>(R, map, a, p->BH, st) : dispatch_r<false, 68>(R, map, a, p->BH, st);
+    // Single-block templates (up to 64 x 64) stage once; multi-block ones
+    // double-buffer so that block b+1 is in flight while block b computes.
+    if (p->WP == 68 && p->nblk > 1 && !s64)
+        e = dispatch_r<false, 68, true>(R, map, a, p->BH, st);
+    else if (p->WP == 68)
+        e = s64 ? dispatch_r<true, 68, false>(R, map, a, p->BH, st)
+                : dispatch_r<false, 68, false>(R, map, a, p->BH, st);
     else
-        e = s64 ? dispatch_r<true, 100>(R, map, a, p->BH, st) : dispatch_r<false, 100>(R, map, a, p->BH, st);
+        e = s64 ? dispatch_r<true, 100, false>(R, map, a, p->BH, st)
+                : dispatch_r<false, 100, false>(R, map, a, p->BH, st);
     return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }

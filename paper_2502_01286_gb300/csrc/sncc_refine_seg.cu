@@ -131,7 +131,7 @@ extern "C" int sncc_refine_segmented(const sncc_segments* seg, const void* d_pla
     RefineSegArgs a;
     a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->blocks_offset);
     a.corners = reinterpret_cast<const int2*>(static_cast<const char*>(d_plan) + p->corners_offset);
-    a.nblk = p->nbx * p->nby;
+    a.nblk = p->nblk;
     a.WP = p->WP;
     a.s = d_s;
     a.s2 = d_s2;
