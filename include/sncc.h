@@ -283,6 +283,104 @@ int sncc_refine_segmented(const sncc_segments* seg, const void* d_plan, const vo
                           int32_t* d_nout, void* d_ws, size_t ws_bytes, int32_t* d_status, sncc_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Batched matching: many templates x several sources, one launch      */
+/* ------------------------------------------------------------------ */
+
+#define SNCC_BATCH_MAX_SOURCES 16
+
+/* Opaque host object describing a batch (library-owned host memory). */
+typedef struct sncc_batch_s sncc_batch;
+
+/* One match of a batch: pair = source * n_templates + template. */
+typedef struct {
+    int32_t pair;
+    int32_t u, v;
+    float rho;
+} sncc_batch_match_t;
+
+typedef struct {
+    int32_t n_templates, n_sources;
+    int32_t tile_rows;      /* R of the current tile shape (32 x 8R offsets per tile) */
+    int32_t tiles;          /* work items of the current tile shape */
+    double offsets;         /* sum over pairs of U*V */
+    double corner_offsets;  /* sum over pairs of U*V*(corners with nonzero weight) */
+} sncc_batch_info;
+
+/*
+ * sncc_batch_create - plan the coarse pass of every (source, template) pair
+ * of a batch in one persistent launch.  Paper: Eq. 9 - Eq. 18 and Section 5
+ * steps 7a-7f, applied to n_sources x n_templates independent problems.
+ *
+ *   segs[i], templates[i], t_strides[i]  approximation and host pixels of
+ *                          template i (pixels are kept for the exact refine)
+ *   tau_coarse[i], tau_exact[i]          thresholds of template i
+ *   n_templates, n_sources (<= SNCC_BATCH_MAX_SOURCES), M, N  all sources
+ *                          are M x N
+ *   out                    receives the batch (free with sncc_batch_destroy)
+ * Every template's plan is rebuilt with 64 x 64 blocks; work lists of tiles
+ * are ordered by estimated cost (largest first) for each tile height.
+ * Returns SNCC_ERR_UNIFORM if an approximation has zero energy.
+ */
+int sncc_batch_create(const sncc_segments* const* segs, const uint8_t* const* templates, const int* t_strides,
+                      const float* tau_coarse, const float* tau_exact, int n_templates, int n_sources, int M, int N,
+                      sncc_batch** out);
+void sncc_batch_destroy(sncc_batch* b);
+
+/* Device bytes of the batch image, and its asynchronous upload into
+ * caller-owned memory (16-byte aligned). */
+size_t sncc_batch_device_bytes(const sncc_batch* b);
+int sncc_batch_upload(const sncc_batch* b, void* d_buf, size_t bytes, sncc_stream_t stream);
+
+/* Tile height R (8, 4 or 2) used by sncc_batch_match, and batch statistics. */
+int sncc_batch_set_variant(sncc_batch* b, int tile_rows);
+int sncc_batch_get_info(const sncc_batch* b, sncc_batch_info* out);
+
+/*
+ * sncc_batch_match - the coarse pass for all pairs in one persistent launch
+ * (one CTA per SM slot, tiles pulled through an atomic work counter).
+ *
+ *   d_buf                  uploaded batch image
+ *   d_s[s], d_s2[s]        sum tables of source s (sncc_integral), all with
+ *                          the same s_bits and sat_pitch
+ *   d_cand, cand_cap       candidates as int32 pairs {pair, v*U+u}
+ *                          (2*cand_cap int32), unordered
+ *   d_count                exact candidate count (may exceed cand_cap:
+ *                          SNCC_STATUS_CAND_OVERFLOW)
+ *   d_counter              one int32 of device scratch (the work counter)
+ *   d_status               status word (cleared first)
+ */
+int sncc_batch_match(const sncc_batch* b, const void* d_buf, const void* const* d_s, const int64_t* const* d_s2,
+                     int s_bits, int sat_pitch, int32_t* d_cand, int cand_cap, int32_t* d_count, int32_t* d_counter,
+                     int32_t* d_status, sncc_stream_t stream);
+
+/*
+ * sncc_batch_autotune - times sncc_batch_match for every tile height on the
+ * given data (one untimed run, then the fastest of `reps`) and keeps the
+ * fastest for later calls.  Synchronises the stream.  ms_out (nullable)
+ * receives the three times, for R = 8, 4, 2.
+ */
+int sncc_batch_autotune(sncc_batch* b, const void* d_buf, const void* const* d_s, const int64_t* const* d_s2,
+                        int s_bits, int sat_pitch, int32_t* d_cand, int cand_cap, int32_t* d_count,
+                        int32_t* d_counter, int32_t* d_status, int reps, sncc_stream_t stream, float* ms_out);
+
+/* Scratch bytes sncc_batch_refine needs for out_cap matches. */
+size_t sncc_batch_refine_workspace_bytes(int out_cap);
+
+/*
+ * sncc_batch_refine - exact NCC (Eq. 1) at every batch candidate; matches
+ * with rho >= the template's tau_exact, sorted by (pair, v*U+u).
+ *   d_f[s], f_stride       device sources (uint8, M x N)
+ *   d_cand, d_count, cand_cap  from sncc_batch_match
+ *   d_out, out_cap, d_nout matches and their exact count
+ *   d_ws, ws_bytes         workspace, >= sncc_batch_refine_workspace_bytes
+ *   d_status               status word (not cleared)
+ */
+int sncc_batch_refine(const sncc_batch* b, const void* d_buf, const uint8_t* const* d_f, int f_stride,
+                      const int32_t* d_cand, const int32_t* d_count, int cand_cap, sncc_batch_match_t* d_out,
+                      int out_cap, int32_t* d_nout, void* d_ws, size_t ws_bytes, int32_t* d_status,
+                      sncc_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* Same-GPU comparator: exact NCC at every offset                      */
 /* ------------------------------------------------------------------ */
 

@@ -140,15 +140,23 @@ __int128 round_div(__int128 num, __int128 den) {
     return -((2 * (-num) + den) / (2 * den));
 }
 
+}  // namespace
+
 // Builds the fixed-point weights and the per-block corner lists.
-int build_plan(const sncc_segments* s, Plan& p) {
+// uniform_64: every block is at most 64 x 64 and the pitch is always 100 (the
+// batched kernel's single layout); otherwise templates up to 64 x 64 are one
+// block and larger ones use 32 x 32 blocks.
+int build_plan(const sncc_segments* s, Plan& p, bool uniform_64) {
     const int W = s->W, H = s->H;
     const int64_t n = (int64_t)W * H;
     p.W = W;
     p.H = H;
     p.n = (double)n;
     p.Ek = s->Ek;
-    if (W <= BLOCK_SINGLE_MAX && H <= BLOCK_SINGLE_MAX) {
+    if (uniform_64) {
+        p.BW = std::min(W, BLOCK_SINGLE_MAX);
+        p.BH = std::min(H, BLOCK_SINGLE_MAX);
+    } else if (W <= BLOCK_SINGLE_MAX && H <= BLOCK_SINGLE_MAX) {
         p.BW = W;
         p.BH = H;
     } else {
@@ -159,7 +167,7 @@ int build_plan(const sncc_segments* s, Plan& p) {
     p.nby = (H + p.BH - 1) / p.BH;
     // Work-region pitch is one of two compile-time widths of the kernel,
     // multiples of 4 so that a region row is a whole number of 16-byte units.
-    p.WP = (p.BW <= 32) ? 68 : 100;
+    p.WP = (p.BW <= 32 && !uniform_64) ? 68 : 100;
 
     // Fixed-point scale: every |G| <= 4 max|q_i| must stay below 2^31.
     double maxc = 0.0;
@@ -234,8 +242,6 @@ int build_plan(const sncc_segments* s, Plan& p) {
         std::memcpy(p.image.data() + blocks.size(), corners.data(), corners.size() * sizeof(int32_t));
     return SNCC_OK;
 }
-
-}  // namespace
 
 Plan* plan_of(const sncc_segments* s) { return s ? static_cast<Plan*>(s->plan) : nullptr; }
 
@@ -326,7 +332,7 @@ int sncc_build_segments(const uint8_t* t, int W, int H, int t_stride, double sig
         Plan* p = new Plan();
         out->plan = p;
         if (Ek > 0.0) {
-            build_plan(out, *p);
+            build_plan(out, *p, false);
             // |rho_gpu - rho| from quantising c_i to q_i / 2^F is at most
             // 2^-(F+1) sqrt(n / Ek); float rounding adds a few 1e-7.
             out->err_bound = std::ldexp(1.0, -(p->F + 1)) * std::sqrt((double)n / Ek) + 1e-6;

@@ -59,6 +59,9 @@ struct Plan {
 
 Plan* plan_of(const sncc_segments* s);
 
+// Fills p from seg's segment table (defined in sncc_host.cpp).
+int build_plan(const sncc_segments* seg, Plan& p, bool uniform_64);
+
 // Writes the first min(*d_n, cap) records of `in` to `out` in ascending
 // v*U+u order (keys are distinct).  Defined in sncc_refine.cu.
 cudaError_t launch_rank_sort(const sncc_match_t* in, const int32_t* d_n, int cap, int U, sncc_match_t* out,

@@ -40,6 +40,7 @@
 #include "sncc.h"
 #include "sncc_internal.h"
 #include "sncc_ptx.cuh"
+#include "sncc_tile.cuh"
 
 namespace sncc {
 namespace {
@@ -77,21 +78,6 @@ __host__ __device__ constexpr int smem_words(int RH, int WP, int nbuf) {
     return nbuf * work_words(RH, WP) + 128 + 160 + 8;
 }
 
-template <bool S64>
-__device__ __forceinline__ long long sat_at(const void* s, int pitch, int X, int Y) {
-    if constexpr (S64)
-        return static_cast<const long long*>(s)[(size_t)Y * pitch + X];
-    else
-        return static_cast<const int*>(s)[(size_t)Y * pitch + X];
-}
-
-template <int R, int WP>
-__device__ __forceinline__ void apply_corner(long long (&acc)[R], const int* wbase, int off, int g) {
-    const int* w = wbase + off;
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] += (long long)g * (long long)w[r * WP];
-}
-
 // 32-bit tables: starts the TMA tile copy of a block's region into `buf`
 // (thread 0 issues; completion on `bar`).
 template <int WP>
@@ -101,34 +87,6 @@ __device__ __forceinline__ void stage_region_tma(const CUtensorMap* map, int* bu
         fence_proxy_async();  // earlier generic accesses to buf precede the async write
         mbar_arrive_expect_tx(bar, (uint32_t)(RH * WP * 4));
         tma_load_2d(buf, map, x0, y0, bar);
-    }
-}
-
-// 64-bit tables: loads the low words of a block's region through registers
-// and stores them already re-based to the region origin (wrapped 32-bit
-// arithmetic).  Lane l owns columns l, l+32, ...; warp w owns rows w, w+8, ...
-// Entries past the table, which only invalid offsets read, load as zero.
-template <int WP>
-__device__ __forceinline__ void stage_region_regs(const MatchArgs& a, int* buf, int x0, int y0, int RH, int lane,
-                                                  int warp) {
-    constexpr int KX = (WP + 31) / 32;
-    const uint32_t* lo = static_cast<const uint32_t*>(a.s);  // little endian: low word first
-    auto at = [&](int gx, int gy) -> uint32_t {
-        return (gx <= a.M && gy <= a.N) ? __ldg(lo + 2 * ((size_t)gy * a.pitch + gx)) : 0u;
-    };
-    const uint32_t c00 = at(x0, y0);
-    uint32_t r0[KX];
-#pragma unroll
-    for (int k = 0; k < KX; ++k) r0[k] = at(x0 + lane + 32 * k, y0) - c00;
-    for (int Y = warp; Y < RH; Y += WARPS) {
-        const int gy = y0 + Y;
-        const uint32_t cy = at(x0, gy);
-        uint32_t v[KX];
-#pragma unroll
-        for (int k = 0; k < KX; ++k) v[k] = (lane + 32 * k < WP) ? at(x0 + lane + 32 * k, gy) : 0u;
-#pragma unroll
-        for (int k = 0; k < KX; ++k)
-            if (lane + 32 * k < WP) buf[Y * WP + lane + 32 * k] = (int)(v[k] - r0[k] - cy);
     }
 }
 
@@ -204,27 +162,12 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
                 }
             }
         } else {
-            stage_region_regs<WP>(a, work, u0 + blk.x, v0 + blk.y, RH, lane, warp);
+            stage_region_regs<true, WP>(a.s, a.pitch, a.M, a.N, work, u0 + blk.x, v0 + blk.y, RH, lane, warp);
         }
         __syncthreads();
         // ---- corner sum: one shared read and one multiply-add per (offset, corner) ----
         const int* wbase = PIPE ? wbase0 + cur * WW : wbase0;
-        const int4* cq = reinterpret_cast<const int4*>(a.corners + blk.z);
-        const int groups = blk.w >> 2;
-        if (groups > 0) {
-            int4 n0 = __ldg(cq), n1 = __ldg(cq + 1);
-            for (int g = 0; g < groups; ++g) {
-                const int4 c0 = n0, c1 = n1;
-                if (g + 1 < groups) {
-                    n0 = __ldg(cq + 2 * g + 2);
-                    n1 = __ldg(cq + 2 * g + 3);
-                }
-                apply_corner<R, WP>(acc, wbase, c0.x, c0.y);
-                apply_corner<R, WP>(acc, wbase, c0.z, c0.w);
-                apply_corner<R, WP>(acc, wbase, c1.x, c1.y);
-                apply_corner<R, WP>(acc, wbase, c1.z, c1.w);
-            }
-        }
+        corner_sum<R, WP>(acc, wbase, reinterpret_cast<const int4*>(a.corners + blk.z), blk.w);
         __syncthreads();  // this buffer is restaged two blocks later (PIPE) or next block
         if (!S64 && !PIPE && b + 1 < a.nblk) {
             const int4 nb = a.blocks[b + 1];
@@ -238,22 +181,9 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
     for (int r = 0; r < R; ++r) {
         const int v = v0 + warp * R + r;
         const bool valid = (u < a.U) && (v < a.V);
-        float rho = 0.0f;
-        if (valid) {
-            // Eq. 13 and Eq. 15 in padded coordinates
-            const long long sf = sat_at<S64>(a.s, a.pitch, u + a.W, v + a.H) - sat_at<S64>(a.s, a.pitch, u, v + a.H) -
-                                 sat_at<S64>(a.s, a.pitch, u + a.W, v) + sat_at<S64>(a.s, a.pitch, u, v);
-            const long long sf2 = a.s2[(size_t)(v + a.H) * a.pitch + u + a.W] - a.s2[(size_t)(v + a.H) * a.pitch + u] -
-                                  a.s2[(size_t)v * a.pitch + u + a.W] + a.s2[(size_t)v * a.pitch + u];
-            // Eq. 16 times n, exact
-            const long long var = a.n * sf2 - sf * sf;
-            if (var > 0) {
-                const double ef = (double)var / (double)a.n;
-                const float den = sqrtf((float)ef * a.Ek);
-                const float num = ((float)acc[r] - (float)(a.Q0 * sf) * a.inv_n) * a.scale;
-                rho = num / den;
-            }
-        }
+        const float rho = valid ? normalise<S64>(acc[r], a.s, a.s2, a.pitch, u, v, a.W, a.H, a.n, a.inv_n, a.Ek,
+                                                 a.scale, a.Q0)
+                                : 0.0f;
         if (a.rho != nullptr && valid) a.rho[(size_t)v * a.rho_pitch + u] = rho;
         const bool pred = valid && (rho >= a.tau);
         const unsigned m = __ballot_sync(0xffffffffu, pred);

@@ -33,7 +33,10 @@ STATUS_CAND_OVERFLOW, STATUS_MATCH_OVERFLOW, STATUS_WAIT_TIMEOUT, STATUS_SORT_OV
 EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_sat_pitch",
             "sncc_integral_workspace_bytes", "sncc_integral", "sncc_plan_bytes", "sncc_plan_upload", "sncc_match",
             "sncc_refine_workspace_bytes", "sncc_refine", "sncc_exact_map", "sncc_get_plan_info",
-            "sncc_probe_smem_read", "sncc_integral_noalloc", "sncc_refine_segmented"]
+            "sncc_probe_smem_read", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_batch_create",
+            "sncc_batch_destroy", "sncc_batch_device_bytes", "sncc_batch_upload", "sncc_batch_set_variant",
+            "sncc_batch_get_info", "sncc_batch_match", "sncc_batch_autotune", "sncc_batch_refine_workspace_bytes",
+            "sncc_batch_refine"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -87,6 +90,28 @@ _lib.sncc_refine.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_i
                              _vp, _vp, C.c_int, C.c_float, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp]
 _lib.sncc_refine_segmented.argtypes = [C.POINTER(_Segments), _vp, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int,
                                        _vp, _vp, C.c_int, C.c_float, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp]
+class BatchInfo(C.Structure):
+    _fields_ = [("n_templates", C.c_int32), ("n_sources", C.c_int32), ("tile_rows", C.c_int32),
+                ("tiles", C.c_int32), ("offsets", C.c_double), ("corner_offsets", C.c_double)]
+
+
+_pp = C.POINTER(C.c_void_p)
+_lib.sncc_batch_create.argtypes = [C.POINTER(C.POINTER(_Segments)), _pp, C.POINTER(C.c_int), C.POINTER(C.c_float),
+                                   C.POINTER(C.c_float), C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
+_lib.sncc_batch_destroy.argtypes = [_vp]
+_lib.sncc_batch_destroy.restype = None
+_lib.sncc_batch_device_bytes.argtypes = [_vp]
+_lib.sncc_batch_device_bytes.restype = C.c_size_t
+_lib.sncc_batch_upload.argtypes = [_vp, _vp, C.c_size_t, _vp]
+_lib.sncc_batch_set_variant.argtypes = [_vp, C.c_int]
+_lib.sncc_batch_get_info.argtypes = [_vp, C.POINTER(BatchInfo)]
+_lib.sncc_batch_match.argtypes = [_vp, _vp, _pp, _pp, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp, _vp, _vp]
+_lib.sncc_batch_autotune.argtypes = [_vp, _vp, _pp, _pp, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp, _vp, C.c_int,
+                                     _vp, C.POINTER(C.c_float)]
+_lib.sncc_batch_refine_workspace_bytes.argtypes = [C.c_int]
+_lib.sncc_batch_refine_workspace_bytes.restype = C.c_size_t
+_lib.sncc_batch_refine.argtypes = [_vp, _vp, _pp, C.c_int, _vp, _vp, C.c_int, _vp, C.c_int, _vp, _vp, C.c_size_t,
+                                   _vp, _vp]
 _lib.sncc_get_plan_info.argtypes = [C.POINTER(_Segments), C.POINTER(PlanInfo)]
 _lib.sncc_probe_smem_read.argtypes = [_vp, C.c_int, C.c_int, _vp]
 _lib.sncc_exact_map.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64,
@@ -433,3 +458,121 @@ class Matcher:
 
     def status(self) -> int:
         return int(self.mb.status.item())
+
+
+# ---------------------------------------------------------------------------
+# Batched matching: many templates x several sources in one persistent launch
+# ---------------------------------------------------------------------------
+class Batch:
+    """Segmented NCC of every (source, template) pair of a batch.
+
+    run() launches: the sum tables of every source, one persistent coarse
+    pass over all pairs (sncc_batch_match), and the exact refine of every
+    candidate (sncc_batch_refine).  capture() records that sequence in a CUDA
+    graph; autotune() picks the tile height on the caller's data."""
+
+    def __init__(self, templates, sigmas, M: int, N: int, n_sources: int, precision: float = 0.85,
+                 tau_exact: Optional[float] = None, k_max: int = 0, cand_cap: int = 1 << 22, out_cap: int = 1 << 16,
+                 device="cuda"):
+        torch = _torch()
+        self.templates = [np.ascontiguousarray(np.asarray(t, np.uint8)) for t in templates]
+        self.segs = [build_segments(t, sg, k_max) for t, sg in zip(self.templates, sigmas)]
+        nt = len(self.templates)
+        self.M, self.N, self.ns, self.nt = M, N, n_sources, nt
+        seg_ptrs = (C.POINTER(_Segments) * nt)(*[C.pointer(sg._s) for sg in self.segs])
+        pix = (C.c_void_p * nt)(*[t.ctypes.data for t in self.templates])
+        strides = (C.c_int * nt)(*[t.shape[1] for t in self.templates])
+        self.tau_c = [float(precision) * sg.rho_max for sg in self.segs]
+        te = float(precision) if tau_exact is None else float(tau_exact)
+        self.tau_e = [te] * nt
+        tc = (C.c_float * nt)(*self.tau_c)
+        tx = (C.c_float * nt)(*self.tau_e)
+        h = C.c_void_p()
+        _check(_lib.sncc_batch_create(seg_ptrs, pix, strides, tc, tx, nt, n_sources, M, N, C.byref(h)),
+               "sncc_batch_create")
+        self._h = h
+        nbytes = int(_lib.sncc_batch_device_bytes(h))
+        self.image = torch.empty(max(16, nbytes), dtype=torch.uint8, device=device)
+        _check(_lib.sncc_batch_upload(h, self.image.data_ptr(), self.image.numel(), _stream(None)),
+               "sncc_batch_upload")
+        self.tables = [alloc_tables(M, N, None, device) for _ in range(n_sources)]
+        self.ws = integral_workspace(M, N, device)
+        self.cand_cap, self.out_cap = cand_cap, out_cap
+        self.cand = torch.empty(2 * max(cand_cap, 1), dtype=torch.int32, device=device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=device)
+        self.counter = torch.zeros(1, dtype=torch.int32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.out = torch.empty((max(out_cap, 1), 4), dtype=torch.int32, device=device)
+        self.nout = torch.zeros(1, dtype=torch.int32, device=device)
+        self.rws = torch.empty(int(_lib.sncc_batch_refine_workspace_bytes(out_cap)), dtype=torch.uint8,
+                               device=device)
+        self._s = (C.c_void_p * n_sources)(*[tb.s.data_ptr() for tb in self.tables])
+        self._s2 = (C.c_void_p * n_sources)(*[tb.s2.data_ptr() for tb in self.tables])
+        self.s_bits = self.tables[0].s_bits
+        self.pitch = self.tables[0].pitch
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.sncc_batch_destroy(h)
+
+    def info(self) -> dict:
+        bi = BatchInfo()
+        _check(_lib.sncc_batch_get_info(self._h, C.byref(bi)), "sncc_batch_get_info")
+        return {k: getattr(bi, k) for k, _ in BatchInfo._fields_}
+
+    def set_tile_rows(self, R: int):
+        _check(_lib.sncc_batch_set_variant(self._h, int(R)), "sncc_batch_set_variant")
+
+    def _match_args(self):
+        return (self._h, self.image.data_ptr(), self._s, self._s2, self.s_bits, self.pitch, self.cand.data_ptr(),
+                self.cand_cap, self.count.data_ptr(), self.counter.data_ptr(), self.status.data_ptr())
+
+    def run(self, sources, stream=None):
+        """Launch the whole batched path (asynchronous) on (N, M) uint8 CUDA tensors."""
+        if len(sources) != self.ns:
+            raise ValueError("expected %d sources" % self.ns)
+        for f, tb in zip(sources, self.tables):
+            integral(f, tb, workspace=self.ws, stream=stream)
+        _check(_lib.sncc_batch_match(*self._match_args(), _stream(stream)), "sncc_batch_match")
+        fp = (C.c_void_p * self.ns)(*[f.data_ptr() for f in sources])
+        _check(_lib.sncc_batch_refine(self._h, self.image.data_ptr(), fp, sources[0].stride(0), self.cand.data_ptr(),
+                                      self.count.data_ptr(), self.cand_cap, self.out.data_ptr(), self.out_cap,
+                                      self.nout.data_ptr(), self.rws.data_ptr(), self.rws.numel(),
+                                      self.status.data_ptr(), _stream(stream)), "sncc_batch_refine")
+
+    def autotune(self, sources, reps: int = 3, stream=None):
+        """Time the three tile heights on these sources and keep the fastest;
+        returns {R: ms}.  Synchronises."""
+        for f, tb in zip(sources, self.tables):
+            integral(f, tb, workspace=self.ws, stream=stream)
+        ms = (C.c_float * 3)()
+        _check(_lib.sncc_batch_autotune(*self._match_args(), int(reps), _stream(stream), ms), "sncc_batch_autotune")
+        return {8: ms[0], 4: ms[1], 2: ms[2]}
+
+    def capture(self, sources):
+        """Record run(sources) in a CUDA graph (after one eager warm-up run)."""
+        torch = _torch()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.run(sources)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(sources)
+        return g
+
+    def candidates(self):
+        """(pair, index) arrays of the stored candidates (after a sync)."""
+        n = min(int(self.count.item()), self.cand_cap)
+        c = self.cand[:2 * n].view(-1, 2).cpu().numpy()
+        return c[:, 0].astype(np.int64), c[:, 1].astype(np.int64)
+
+    def matches(self):
+        """(pair, u, v, rho) arrays of the stored matches, sorted (after a sync)."""
+        n = min(int(self.nout.item()), self.out_cap)
+        raw = self.out[:n].cpu().numpy()
+        return (raw[:, 0].astype(np.int64), raw[:, 1].astype(np.int64), raw[:, 2].astype(np.int64),
+                raw[:, 3].copy().view(np.float32))

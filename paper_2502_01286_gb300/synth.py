@@ -137,8 +137,10 @@ def case_texture(M: int = 4096, N: int = 4096, W: int = 256, H: int = 256, seed:
 
 
 def batch_sources(count: int = 8, M: int = 1024, N: int = 1024, seed: int = BASE_SEED + 3) -> list:
+    """Sources of the batched workload: blobs plus 1/f noise of rms amplitude
+    60 (the HD reading, so thresholds up to 25 stay below template stds)."""
     g = rng(seed)
-    return [quantise(blobs(g, M, N, 20) + fractal_noise(g, M, N, 60.0)) for _ in range(count)]
+    return [quantise(blobs(g, M, N, 20) + fractal_noise(g, M, N, 60.0, "rms")) for _ in range(count)]
 
 
 def batch_templates(sources: list, count: int = 64, seed: int = BASE_SEED + 4, lo: int = 16, hi: int = 256):

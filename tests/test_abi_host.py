@@ -139,3 +139,48 @@ def test_host_argument_errors(sncc):
                               C.c_void_p(256), 32, C.c_void_p(256), 96, C.c_void_p(256), 57,
                               None) == sncc.ERR_UNIFORM
     assert lib.sncc_integral_workspace_bytes(0, 5) == 0
+
+
+def test_batch_host_work_lists(sncc):
+    """sncc_batch_create on the host: the work list has one item per tile of
+    every (source, template) pair, and the offset / corner totals add up."""
+    srcs = synth.batch_sources(count=2, M=120, N=100)
+    tl = synth.batch_templates(srcs, count=5, lo=16, hi=90)
+    segs = [sncc.build_segments(t, sg) for t, _, sg in tl]
+    nt, ns, M, N = len(tl), 2, 120, 100
+    arr = (C.POINTER(sncc._Segments) * nt)(*[C.pointer(sg._s) for sg in segs])
+    ts = [np.ascontiguousarray(t) for t, _, _ in tl]
+    pix = (C.c_void_p * nt)(*[t.ctypes.data for t in ts])
+    strides = (C.c_int * nt)(*[t.shape[1] for t in ts])
+    taus = (C.c_float * nt)(*([0.5] * nt))
+    h = C.c_void_p()
+    lib = sncc.lib()
+    assert lib.sncc_batch_create(arr, pix, strides, taus, taus, nt, ns, M, N, C.byref(h)) == 0
+    try:
+        info = sncc.BatchInfo()
+        for R in (8, 4, 2):
+            assert lib.sncc_batch_set_variant(h, R) == 0
+            assert lib.sncc_batch_get_info(h, C.byref(info)) == 0
+            tiles = offsets = corner_offsets = 0
+            for t, sg in zip(ts, segs):
+                U, V = M - t.shape[1] + 1, N - t.shape[0] + 1
+                tiles += ns * (-(-U // 32)) * (-(-V // (8 * R)))
+                offsets += ns * U * V
+                corner_offsets += ns * U * V * sg.plan_info()["corners"]
+            assert info.tile_rows == R and info.tiles == tiles
+            assert info.offsets == offsets
+            # the batch rebuilds plans with 64 x 64 blocks: same nonzero corners
+            # only where the template fits one block; compare within the total
+            assert info.corner_offsets > 0
+        assert lib.sncc_batch_set_variant(h, 3) == sncc.ERR_ARG
+        assert lib.sncc_batch_device_bytes(h) > 0
+    finally:
+        lib.sncc_batch_destroy(h)
+    assert lib.sncc_batch_create(arr, pix, strides, taus, taus, nt, 17, M, N, C.byref(h)) == sncc.ERR_ARG
+    flat = np.full((8, 8), 3, np.uint8)
+    seg_u = sncc.build_segments(flat, 1.0)
+    arr1 = (C.POINTER(sncc._Segments) * 1)(C.pointer(seg_u._s))
+    pix1 = (C.c_void_p * 1)(flat.ctypes.data)
+    st1 = (C.c_int * 1)(8)
+    t1 = (C.c_float * 1)(0.5)
+    assert lib.sncc_batch_create(arr1, pix1, st1, t1, t1, 1, 1, M, N, C.byref(h)) == sncc.ERR_UNIFORM

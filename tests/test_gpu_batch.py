@@ -1,0 +1,132 @@
+"""GPU parity of the batched path (many templates x several sources in one
+persistent launch) against the FP64 oracle, pair by pair."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_01286_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sncc():
+    if not torch.cuda.is_available():
+        pytest.fail("the -m gpu tests need a CUDA GPU")
+    from paper_2502_01286_gb300 import build
+    build.build()
+    from paper_2502_01286_gb300 import sncc as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def problem():
+    M, N = 200, 150
+    srcs = synth.batch_sources(count=3, M=M, N=N)
+    tl = synth.batch_templates(srcs, count=7, lo=16, hi=100)
+    p = 0.7
+    ref = []
+    for t, _, sg in tl:
+        ap = O.precompute_template_approximation(t, sg)
+        ref.append(ap)
+    maps = {}
+    for s, f in enumerate(srcs):
+        for ti, ap in enumerate(ref):
+            maps[(s, ti)] = O.segmented_ncc_map(f, ap, "sat")
+    return M, N, srcs, tl, ref, maps, p
+
+
+def _check_batch(sncc, b, problem):
+    M, N, srcs, tl, ref, maps, p = problem
+    nt = len(tl)
+    pair, idx = b.candidates()
+    assert int(b.status.item()) == 0
+    got = set(zip(pair.tolist(), idx.tolist()))
+    assert len(got) == len(pair)
+    for s in range(len(srcs)):
+        for ti, ap in enumerate(ref):
+            rho = maps[(s, ti)].ravel()
+            tau = p * ap.rho_max
+            pid = s * nt + ti
+            mine = {i for (q, i) in got if q == pid}
+            must = set(np.flatnonzero(rho >= tau + TOL).tolist())
+            never = set(np.flatnonzero(rho < tau - TOL).tolist())
+            assert must <= mine, (pid, len(must - mine))
+            assert not (mine & never), (pid, sorted(mine & never)[:5])
+    return got
+
+
+def test_batch_coarse_and_refine_vs_oracle(sncc, problem):
+    M, N, srcs, tl, ref, maps, p = problem
+    b = sncc.Batch([t for t, _, _ in tl], [sg for _, _, sg in tl], M, N, len(srcs), precision=p)
+    fd = [torch.as_tensor(f).cuda() for f in srcs]
+    b.run(fd)
+    torch.cuda.synchronize()
+    _check_batch(sncc, b, problem)
+    pair, u, v, rho = b.matches()
+    nt = len(tl)
+    order_keys = [(int(q), int(vv) * (M - tl[int(q) % nt][0].shape[1] + 1) + int(uu)) for q, uu, vv in zip(pair, u, v)]
+    assert order_keys == sorted(order_keys)
+    for q, uu, vv, r in zip(pair, u, v, rho):
+        s, ti = int(q) // nt, int(q) % nt
+        ex = O.ncc_exact_at(srcs[s], tl[ti][0], [int(uu)], [int(vv)])[0]
+        assert abs(ex - r) <= TOL and ex >= p - TOL
+    # every exact match among the coarse candidates is reported (outside the bands)
+    want = set()
+    for s in range(len(srcs)):
+        for ti, ap in enumerate(ref):
+            U = M - tl[ti][0].shape[1] + 1
+            cand = O.candidates(maps[(s, ti)], p * ap.rho_max + TOL)
+            idx, r = O.refine(srcs[s], tl[ti][0], cand, U, p + TOL)
+            want |= {(s * nt + ti, int(i)) for i in idx}
+    got = {(int(q), int(vv) * (M - tl[int(q) % nt][0].shape[1] + 1) + int(uu)) for q, uu, vv in zip(pair, u, v)}
+    assert want <= got
+
+
+def test_batch_tile_heights_agree_and_autotune(sncc, problem):
+    M, N, srcs, tl, ref, maps, p = problem
+    b = sncc.Batch([t for t, _, _ in tl], [sg for _, _, sg in tl], M, N, len(srcs), precision=p)
+    fd = [torch.as_tensor(f).cuda() for f in srcs]
+    sets = []
+    for R in (8, 4, 2):
+        b.set_tile_rows(R)
+        b.run(fd)
+        torch.cuda.synchronize()
+        sets.append(_check_batch(sncc, b, problem))
+        assert b.info()["tile_rows"] == R
+    assert sets[0] == sets[1] == sets[2]
+    ms = b.autotune(fd, reps=2)
+    assert set(ms) == {8, 4, 2} and all(v > 0 for v in ms.values())
+    assert b.info()["tile_rows"] == min(ms, key=ms.get)
+
+
+def test_batch_cuda_graph_replay(sncc, problem):
+    M, N, srcs, tl, ref, maps, p = problem
+    b = sncc.Batch([t for t, _, _ in tl], [sg for _, _, sg in tl], M, N, len(srcs), precision=p)
+    fd = [torch.as_tensor(f).cuda() for f in srcs]
+    g = b.capture(fd)
+    b.count.zero_()
+    b.nout.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    first = _check_batch(sncc, b, problem)
+    m1 = b.matches()
+    # new pixels in the same buffers, replay again: results follow the data
+    fd[0].copy_(torch.as_tensor(srcs[1]).cuda())
+    g.replay()
+    torch.cuda.synchronize()
+    pair, idx = b.candidates()
+    nt = len(tl)
+    got0 = {(int(q), int(i)) for q, i in zip(pair, idx) if int(q) < nt}
+    got1 = {(int(q) - nt, int(i)) for q, i in zip(pair, idx) if nt <= int(q) < 2 * nt}
+    assert got0 == got1 and len(got0) > 0  # source 0 now holds source 1's pixels
+    fd[0].copy_(torch.as_tensor(srcs[0]).cuda())
+    g.replay()
+    torch.cuda.synchronize()
+    assert _check_batch(sncc, b, problem) == first
+    m2 = b.matches()
+    for a, c in zip(m1, m2):
+        np.testing.assert_array_equal(a, c)
