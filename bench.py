@@ -45,6 +45,7 @@ WORKLOADS = {
     "plain": ("case_plain", (10.0,), 0.9),
     "texture": ("case_texture", (5.0,), 0.85),
     "batch": ("batch", None, 0.85),
+    "diff": ("diff", None, None),
 }
 SIGMAS = WORKLOADS["hd"][1]
 PRECISION = WORKLOADS["hd"][2]
@@ -221,6 +222,8 @@ def run_reference(args, world, rank, pg):
         return
     if args.workload == "batch":
         return run_reference_batch(args)
+    if args.workload == "diff":
+        return run_reference_diff(args)
     case, sigmas, precision = make_case(args.workload)
     N, M = case.f.shape
     H, W = case.t.shape
@@ -242,6 +245,34 @@ def run_reference(args, world, rank, pg):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args.workload, case, sigmas, precision, U, V),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_diff(args):
+    """The oracle's FP64 loss and analytic gradients (oracle/diff.py) on a
+    128 x 128 crop of the differentiation source with the same template."""
+    from oracle import diff as D
+    from paper_2502_01286_gb300 import sncc, synth
+    f, t, org, sigma = synth.case_diff()
+    seg = sncc.build_segments(np.rint(np.clip(t, 0, 255)).astype(np.uint8), sigma)
+    rects = seg.table
+    k0 = np.array([t[y:y + h, x:x + w].mean() for x, y, w, h in rects])
+    fc = f[:128, :128].astype(np.float64)
+    U = V = 128 - 48 + 1
+    for _ in range(args.warmup):
+        D.gradients(fc, t.astype(np.float64), rects, k0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        D.gradients(fc, t.astype(np.float64), rects, k0)
+    secs = time.perf_counter() - t0
+    value = args.steps * U * V / secs / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "diff-512x512f32-t48x48-sigma12"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "loss + analytic gradients on a 128 x 128 crop (81 x 81 offsets) per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -747,11 +778,73 @@ def run_gpu_batch(args, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def run_gpu_diff(args, world, rank, local, pg):
+    """Differentiation workload: loss between segmented and exact NCC over a
+    512 x 512 float source (48 x 48 template, segmentation at std 12), one
+    step = forward + hand-written backward w.r.t. segment values and source."""
+    import torch
+    from paper_2502_01286_gb300 import build as lib_build
+    if rank == 0 or not os.path.exists(lib_build.LIB):
+        lib_build.build()
+    barrier(pg)
+    from paper_2502_01286_gb300 import sncc, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    f, t, org, sigma = synth.case_diff(seed=synth.BASE_SEED + 5 + 1000 * rank)
+    N, M = f.shape
+    seg = sncc.build_segments(np.rint(np.clip(t, 0, 255)).astype(np.uint8), sigma)
+    rects = seg.table
+    k0 = np.array([t[y:y + h, x:x + w].mean() for x, y, w, h in rects], np.float32)
+    pb = sncc.DiffProblem(t, rects, M, N, device=dev)
+    fd = torch.as_tensor(f).to(dev).requires_grad_(True)
+    kd = torch.as_tensor(k0).to(dev).requires_grad_(True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        fd.grad = None
+        kd.grad = None
+        loss = pb.loss(fd, kd)
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(pg)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    ms = max_over_ranks(pg, sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / args.steps)
+    U, V = pb.U, pb.V
+    _, losses = sncc.refit_segment_values(pb, fd.detach(), k0, steps=50, lr=0.5)
+    value = sum_over_ranks(pg, U * V) / (ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "diff-512x512f32-t48x48-sigma12", "segments": int(seg.K),
+                       "step": "loss forward + backward w.r.t. segment values and source (kernel launches: "
+                               "forward 2, backward 2 + forward 2 recomputed + 4)"},
+            "refit": {"steps": 50, "loss_first": losses[0], "loss_last": losses[-1]},
+            "gpu_launches": args.steps * 10}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank, pg)
+    elif args.workload == "diff":
+        run_gpu_diff(args, world, rank, local, pg)
     elif args.workload == "batch":
         run_gpu_batch(args, world, rank, local, pg)
     else:

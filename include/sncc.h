@@ -381,6 +381,49 @@ int sncc_batch_refine(const sncc_batch* b, const void* d_buf, const uint8_t* con
                       sncc_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Differentiation: the approximation-error loss and its gradients     */
+/* ------------------------------------------------------------------ */
+
+/* Workspace bytes of sncc_diff_forward / sncc_diff_backward (the same buffer
+ * must be passed to both: the backward pass reads what the forward left). */
+size_t sncc_diff_workspace_bytes(int M, int N, int W, int H);
+
+/*
+ * sncc_diff_forward - loss of a fixed segmentation on a float source.
+ * Paper: Eq. 1 (rho_t), Eq. 7, Eq. 9, Eq. 17, Eq. 18 (rho_k with raw segment
+ * values k_i, c_i = k_i - kbar, weighted energy).
+ *
+ * L = sum over offsets (u, v) of (rho_k(u, v) - rho_t(u, v))^2.
+ *   d_f, M, N, f_stride  float32 source (row stride in elements)
+ *   d_t, W, H            float32 template, contiguous (W, H <= 64)
+ *   d_rects, d_k, K      segmentation: K records {x, y, w, h} (int32) tiling
+ *                        the template, and the segment values (float32)
+ *   d_rho_k, d_rho_t     outputs, (N-H+1) x (M-W+1) float32 each
+ *   d_loss               output, one double
+ *   d_ws, ws_bytes       workspace (256-byte aligned)
+ * Every window is assumed non-uniform.
+ */
+int sncc_diff_forward(const float* d_f, int M, int N, int f_stride, const float* d_t, int W, int H,
+                      const int32_t* d_rects, const float* d_k, int K, float* d_rho_k, float* d_rho_t,
+                      double* d_loss, void* d_ws, size_t ws_bytes, sncc_stream_t stream);
+
+/*
+ * sncc_diff_backward - gradients of dloss * L with respect to k and f, after
+ * sncc_diff_forward on the same inputs and workspace.
+ * With g = 2 dloss (rho_k - rho_t), a = g / sqrt(E_f E_k), b = g / sqrt(E_f E_t),
+ * h = g (rho_k - rho_t) / E_f:
+ *   dL/dk_j  = sum_{x in S_j} sum_o a(o) f(o+x) - n_j sum_o a fbar - n_j c_j sum_o g rho_k / E_k
+ *   dL/df(p) = sum_{o: p in window(o)} a(o) c(p-o) - b(o) t0(p-o) + h(o) (fbar(o) - f(p))
+ *   d_dloss              upstream gradient (one double, device)
+ *   d_grad_f, grad_f_stride  output N x M float32
+ *   d_grad_k             output K float32
+ */
+int sncc_diff_backward(const float* d_f, int M, int N, int f_stride, int W, int H, const int32_t* d_rects,
+                       const float* d_k, int K, const float* d_rho_k, const float* d_rho_t, const double* d_dloss,
+                       float* d_grad_f, int grad_f_stride, float* d_grad_k, void* d_ws, size_t ws_bytes,
+                       sncc_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* Same-GPU comparator: exact NCC at every offset                      */
 /* ------------------------------------------------------------------ */
 

@@ -1,0 +1,385 @@
+// sncc_diff.cu - the segmented-NCC loss L = sum_o (rho_k(o) - rho_t(o))^2 on a
+// float source with a fixed segmentation, and its hand-written gradients with
+// respect to the segment values k_i and the source image f.
+//
+// rho_k is segmented NCC (Eq. 9, Eq. 17, Eq. 18 with the weighted energy) of
+// the approximation with values k_i; rho_t is exact NCC (Eq. 1).  With
+// c_i = k_i - kbar (kbar of Eq. 7), g = 2 (rho_k - rho_t),
+// a = g / sqrt(E_f E_k), b = g / sqrt(E_f E_t), h = g (rho_k - rho_t) / E_f:
+//   dL/dk_j  = sum_{x in S_j} Gt(x) - n_j sum_o a fbar - n_j c_j sum_o g rho_k / E_k,
+//              Gt(x) = sum_o a(o) f(o + x);
+//   dL/df(p) = sum_{o : p in window(o)} a(o) c(p-o) - b(o) t0(p-o) + h(o) (fbar(o) - f(p)).
+// Templates up to 64 x 64 (every window and the template fit in shared
+// memory).  Sums run in FP32 along a template row and in FP64 across rows.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sncc.h"
+#include "sncc_internal.h"
+
+namespace sncc {
+namespace {
+
+constexpr int kDiffMax = 64;      // largest template edge
+constexpr int kTX = 32, kTY = 8;  // offsets / pixels per CTA tile
+constexpr int kGtChunks = 16;     // offset-row chunks of the Gt correlation
+
+// Workspace layout (bytes), 256-aligned sections.
+struct DiffLayout {
+    size_t scal, c, t0, ef, fbar, a, b, h, hf, gtp, gt, total;
+};
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+DiffLayout diff_layout(int M, int N, int W, int H) {
+    const size_t U = (size_t)(M - W + 1), V = (size_t)(N - H + 1), T = (size_t)W * H, UV = U * V;
+    DiffLayout L;
+    size_t o = 0;
+    L.scal = o; o = al256(o + 8 * sizeof(double));
+    L.c = o; o = al256(o + T * 4);
+    L.t0 = o; o = al256(o + T * 4);
+    L.ef = o; o = al256(o + UV * 4);
+    L.fbar = o; o = al256(o + UV * 4);
+    L.a = o; o = al256(o + UV * 4);
+    L.b = o; o = al256(o + UV * 4);
+    L.h = o; o = al256(o + UV * 4);
+    L.hf = o; o = al256(o + UV * 4);
+    L.gtp = o; o = al256(o + (size_t)kGtChunks * T * sizeof(double));
+    L.gt = o; o = al256(o + T * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ double block_sum_double(double v, double* sm) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sm[w];
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+// scal[0] = kbar, scal[1] = E_k, scal[2] = E_t, scal[3] = sum a fbar, scal[4] = sum g rho_k.
+// Renders c(x) = k_i - kbar and t0 = t - tbar.  One CTA.
+__global__ void __launch_bounds__(256) diff_prep_kernel(const float* __restrict__ t, int W, int H,
+                                                        const int4* __restrict__ rects, const float* __restrict__ k,
+                                                        int K, double* scal, float* c, float* t0) {
+    __shared__ double sm[8];
+    __shared__ double sh_kbar, sh_tbar;
+    const double n = (double)W * H;
+    double sk = 0.0, st = 0.0;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) sk += (double)rects[i].z * rects[i].w * (double)k[i];
+    for (int i = threadIdx.x; i < W * H; i += blockDim.x) st += (double)t[i];
+    sk = block_sum_double(sk, sm);
+    st = block_sum_double(st, sm);
+    if (threadIdx.x == 0) {
+        sh_kbar = sk / n;
+        sh_tbar = st / n;
+    }
+    __syncthreads();
+    const double kbar = sh_kbar, tbar = sh_tbar;
+    double ek = 0.0, et = 0.0;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+        const int4 r = rects[i];
+        const double ci = (double)k[i] - kbar;
+        ek += (double)r.z * r.w * ci * ci;
+        // rectangles are clamped to the template, so a bad record cannot write outside c
+        for (int y = max(r.y, 0); y < min(r.y + r.w, H); ++y)
+            for (int x = max(r.x, 0); x < min(r.x + r.z, W); ++x) c[y * W + x] = (float)ci;
+    }
+    for (int i = threadIdx.x; i < W * H; i += blockDim.x) {
+        const double d = (double)t[i] - tbar;
+        t0[i] = (float)d;
+        et += d * d;
+    }
+    ek = block_sum_double(ek, sm);
+    et = block_sum_double(et, sm);
+    if (threadIdx.x == 0) {
+        scal[0] = kbar;
+        scal[1] = ek;
+        scal[2] = et;
+        scal[3] = 0.0;
+        scal[4] = 0.0;
+    }
+}
+
+// One thread per offset of a 32 x 8 tile.
+__global__ void __launch_bounds__(256) diff_forward_kernel(const float* __restrict__ f, int M, int N, int stride,
+                                                           int W, int H, const float* __restrict__ c,
+                                                           const float* __restrict__ t0, const double* scal,
+                                                           float* __restrict__ rho_k, float* __restrict__ rho_t,
+                                                           float* __restrict__ ef_out, float* __restrict__ fbar_out,
+                                                           double* loss) {
+    extern __shared__ float sm[];
+    const int RW = kTX + W - 1, RH = kTY + H - 1;
+    float* fs = sm;                  // RH x RW source region
+    float* cs = fs + RW * RH;        // W x H
+    float* ts = cs + W * H;          // W x H
+    __shared__ double red[8];
+    const int U = M - W + 1, V = N - H + 1;
+    const int u0 = blockIdx.x * kTX, v0 = blockIdx.y * kTY;
+    for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
+        const int Y = i / RW, X = i - Y * RW;
+        const int gx = u0 + X, gy = v0 + Y;
+        fs[i] = (gx < M && gy < N) ? f[(size_t)gy * stride + gx] : 0.0f;
+    }
+    for (int i = threadIdx.x; i < W * H; i += blockDim.x) {
+        cs[i] = c[i];
+        ts[i] = t0[i];
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+    const int u = u0 + lx, v = v0 + ly;
+    double contrib = 0.0;
+    if (u < U && v < V) {
+        const double n = (double)W * H;
+        double sf = 0.0;
+        for (int y = 0; y < H; ++y) {
+            const float* row = fs + (ly + y) * RW + lx;
+            float r = 0.0f;
+            for (int x = 0; x < W; ++x) r += row[x];
+            sf += r;
+        }
+        const double fbar = sf / n;
+        const float fb = (float)fbar;
+        double e = 0.0, nk = 0.0, nt = 0.0;
+        for (int y = 0; y < H; ++y) {
+            const float* row = fs + (ly + y) * RW + lx;
+            const float* crow = cs + y * W;
+            const float* trow = ts + y * W;
+            float re = 0.0f, rk = 0.0f, rt = 0.0f;
+            for (int x = 0; x < W; ++x) {
+                const float d = row[x] - fb;
+                re += d * d;
+                rk += crow[x] * d;
+                rt += trow[x] * d;
+            }
+            e += re;
+            nk += rk;
+            nt += rt;
+        }
+        const double rk_ = nk / sqrt(e * scal[1]);
+        const double rt_ = nt / sqrt(e * scal[2]);
+        rho_k[(size_t)v * U + u] = (float)rk_;
+        rho_t[(size_t)v * U + u] = (float)rt_;
+        ef_out[(size_t)v * U + u] = (float)e;
+        fbar_out[(size_t)v * U + u] = fb;
+        contrib = (rk_ - rt_) * (rk_ - rt_);
+    }
+    const double s = block_sum_double(contrib, red);
+    if (threadIdx.x == 0) atomicAdd(loss, s);
+}
+
+// Per-offset coefficients of the backward pass, and the sums A1, A2.
+__global__ void __launch_bounds__(256) diff_coeff_kernel(int UV, const float* __restrict__ rho_k,
+                                                         const float* __restrict__ rho_t,
+                                                         const float* __restrict__ ef,
+                                                         const float* __restrict__ fbar, const double* dloss,
+                                                         double* scal, float* a, float* b, float* h, float* hf) {
+    __shared__ double red[8];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double s1 = 0.0, s2 = 0.0;
+    if (i < UV) {
+        const double d = (double)rho_k[i] - (double)rho_t[i];
+        const double g = 2.0 * (*dloss) * d;
+        const double e = ef[i];
+        const double ai = g / sqrt(e * scal[1]);
+        const double hi = g * d / e;
+        a[i] = (float)ai;
+        b[i] = (float)(g / sqrt(e * scal[2]));
+        h[i] = (float)hi;
+        hf[i] = (float)(hi * fbar[i]);
+        s1 = ai * fbar[i];
+        s2 = g * rho_k[i];
+    }
+    const double r1 = block_sum_double(s1, red);
+    const double r2 = block_sum_double(s2, red);
+    if (threadIdx.x == 0) {
+        atomicAdd(&scal[3], r1);
+        atomicAdd(&scal[4], r2);
+    }
+}
+
+// dL/df for a 32 x 8 tile of pixels.  Offsets o = p - x with x in the
+// template; the tile needs offsets in [p0 - (W-1, H-1), p0 + (31, 7)].
+__global__ void __launch_bounds__(256) diff_grad_f_kernel(const float* __restrict__ f, int M, int N, int stride,
+                                                          int W, int H, const float* __restrict__ c,
+                                                          const float* __restrict__ t0, const float* __restrict__ a,
+                                                          const float* __restrict__ b, const float* __restrict__ h,
+                                                          const float* __restrict__ hf, float* __restrict__ grad,
+                                                          int gstride) {
+    extern __shared__ float sm[];
+    const int RW = kTX + W - 1, RH = kTY + H - 1;
+    const int U = M - W + 1, V = N - H + 1;
+    float* as = sm;
+    float* bs = as + RW * RH;
+    float* hs = bs + RW * RH;
+    float* hfs = hs + RW * RH;
+    float* cs = hfs + RW * RH;
+    float* ts = cs + W * H;
+    const int px0 = blockIdx.x * kTX, py0 = blockIdx.y * kTY;
+    const int ox0 = px0 - (W - 1), oy0 = py0 - (H - 1);
+    for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
+        const int Y = i / RW, X = i - Y * RW;
+        const int ou = ox0 + X, ov = oy0 + Y;
+        const bool in = (ou >= 0 && ov >= 0 && ou < U && ov < V);
+        const size_t o = in ? (size_t)ov * U + ou : 0;
+        as[i] = in ? a[o] : 0.0f;
+        bs[i] = in ? b[o] : 0.0f;
+        hs[i] = in ? h[o] : 0.0f;
+        hfs[i] = in ? hf[o] : 0.0f;
+    }
+    for (int i = threadIdx.x; i < W * H; i += blockDim.x) {
+        cs[i] = c[i];
+        ts[i] = t0[i];
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+    const int px = px0 + lx, py = py0 + ly;
+    if (px >= M || py >= N) return;
+    double acc = 0.0, hsum = 0.0;
+    for (int y = 0; y < H; ++y) {
+        // offset row of template row y: ov = py - y  ->  region row (ly + H - 1 - y)
+        const int rbase = (ly + H - 1 - y) * RW + (lx + W - 1);
+        const float* crow = cs + y * W;
+        const float* trow = ts + y * W;
+        float r = 0.0f, rh = 0.0f;
+        for (int x = 0; x < W; ++x) {
+            const int k = rbase - x;
+            r += as[k] * crow[x] - bs[k] * trow[x] + hfs[k];
+            rh += hs[k];
+        }
+        acc += r;
+        hsum += rh;
+    }
+    grad[(size_t)py * gstride + px] = (float)(acc - (double)f[(size_t)py * stride + px] * hsum);
+}
+
+// Partial Gt(x, y) = sum_{o in chunk} a(o) f(o + (x, y)): grid (H, kGtChunks).
+__global__ void __launch_bounds__(256) diff_gt_kernel(const float* __restrict__ f, int M, int N, int stride, int W,
+                                                      int H, const float* __restrict__ a, double* __restrict__ gtp) {
+    __shared__ double part[256];
+    const int U = M - W + 1, V = N - H + 1;
+    const int y = blockIdx.x, chunk = blockIdx.y;
+    const int groups = blockDim.x / W;
+    const int x = threadIdx.x % W, gph = threadIdx.x / W;
+    const int vb = (int)((long long)V * chunk / kGtChunks), ve = (int)((long long)V * (chunk + 1) / kGtChunks);
+    double acc = 0.0;
+    if (gph < groups) {
+        for (int v = vb; v < ve; ++v) {
+            const float* arow = a + (size_t)v * U;
+            const float* frow = f + (size_t)(v + y) * stride + x;
+            float r = 0.0f;
+            for (int u = gph; u < U; u += groups) r += arow[u] * frow[u];
+            acc += r;
+        }
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < W) {
+        double s = 0.0;
+        for (int g = 0; g < groups; ++g) s += part[g * W + threadIdx.x];
+        gtp[((size_t)chunk * H + y) * W + threadIdx.x] = s;
+    }
+}
+
+// dL/dk_j for every segment: sum of Gt over the rectangle, minus the mean and
+// energy terms (one thread per segment; Gt reduced over chunks on the fly).
+__global__ void __launch_bounds__(256) diff_grad_k_kernel(int W, int H, const int4* __restrict__ rects,
+                                                          const float* __restrict__ k, int K,
+                                                          const double* __restrict__ gtp, const double* scal,
+                                                          float* __restrict__ grad_k) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K) return;
+    const int4 r = rects[j];
+    double s = 0.0;
+    for (int y = max(r.y, 0); y < min(r.y + r.w, H); ++y)
+        for (int x = max(r.x, 0); x < min(r.x + r.z, W); ++x)
+            for (int ch = 0; ch < kGtChunks; ++ch) s += gtp[((size_t)ch * H + y) * W + x];
+    const double nj = (double)r.z * r.w;
+    const double cj = (double)k[j] - scal[0];
+    grad_k[j] = (float)(s - nj * scal[3] - nj * cj * scal[4] / scal[1]);
+}
+
+bool diff_args_ok(int M, int N, int W, int H, int K, int f_stride) {
+    return M > 0 && N > 0 && W > 0 && H > 0 && W <= kDiffMax && H <= kDiffMax && W <= M && H <= N && K > 0 &&
+           K <= W * H && f_stride >= M && 256 / W >= 1;
+}
+
+}  // namespace
+}  // namespace sncc
+
+extern "C" size_t sncc_diff_workspace_bytes(int M, int N, int W, int H) {
+    if (M <= 0 || N <= 0 || W <= 0 || H <= 0 || W > M || H > N) return 0;
+    return sncc::diff_layout(M, N, W, H).total;
+}
+
+extern "C" int sncc_diff_forward(const float* d_f, int M, int N, int f_stride, const float* d_t, int W, int H,
+                                 const int32_t* d_rects, const float* d_k, int K, float* d_rho_k, float* d_rho_t,
+                                 double* d_loss, void* d_ws, size_t ws_bytes, sncc_stream_t stream) {
+    using namespace sncc;
+    if (!d_f || !d_t || !d_rects || !d_k || !d_rho_k || !d_rho_t || !d_loss) return SNCC_ERR_ARG;
+    if (!diff_args_ok(M, N, W, H, K, f_stride)) return SNCC_ERR_ARG;
+    const DiffLayout L = diff_layout(M, N, W, H);
+    if (!d_ws || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return SNCC_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(d_ws);
+    double* scal = reinterpret_cast<double*>(ws + L.scal);
+    float* c = reinterpret_cast<float*>(ws + L.c);
+    float* t0 = reinterpret_cast<float*>(ws + L.t0);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(d_loss, 0, sizeof(double), st) != cudaSuccess) return SNCC_ERR_CUDA;
+    diff_prep_kernel<<<1, 256, 0, st>>>(d_t, W, H, reinterpret_cast<const int4*>(d_rects), d_k, K, scal, c, t0);
+    const int U = M - W + 1, V = N - H + 1;
+    const size_t sm = ((size_t)(kTX + W - 1) * (kTY + H - 1) + 2 * (size_t)W * H) * 4;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(diff_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(diff_grad_f_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr_done = true;
+    }
+    dim3 grid((U + kTX - 1) / kTX, (V + kTY - 1) / kTY);
+    diff_forward_kernel<<<grid, 256, sm, st>>>(d_f, M, N, f_stride, W, H, c, t0, scal, d_rho_k, d_rho_t,
+                                               reinterpret_cast<float*>(ws + L.ef),
+                                               reinterpret_cast<float*>(ws + L.fbar), d_loss);
+    return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+}
+
+extern "C" int sncc_diff_backward(const float* d_f, int M, int N, int f_stride, int W, int H,
+                                  const int32_t* d_rects, const float* d_k, int K, const float* d_rho_k,
+                                  const float* d_rho_t, const double* d_dloss, float* d_grad_f, int grad_f_stride,
+                                  float* d_grad_k, void* d_ws, size_t ws_bytes, sncc_stream_t stream) {
+    using namespace sncc;
+    if (!d_f || !d_rects || !d_k || !d_rho_k || !d_rho_t || !d_dloss || !d_grad_f || !d_grad_k) return SNCC_ERR_ARG;
+    if (!diff_args_ok(M, N, W, H, K, f_stride) || grad_f_stride < M) return SNCC_ERR_ARG;
+    const DiffLayout L = diff_layout(M, N, W, H);
+    if (!d_ws || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return SNCC_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(d_ws);
+    double* scal = reinterpret_cast<double*>(ws + L.scal);
+    const float* c = reinterpret_cast<const float*>(ws + L.c);
+    const float* t0 = reinterpret_cast<const float*>(ws + L.t0);
+    float* a = reinterpret_cast<float*>(ws + L.a);
+    float* b = reinterpret_cast<float*>(ws + L.b);
+    float* h = reinterpret_cast<float*>(ws + L.h);
+    float* hf = reinterpret_cast<float*>(ws + L.hf);
+    double* gtp = reinterpret_cast<double*>(ws + L.gtp);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int U = M - W + 1, V = N - H + 1;
+    const int UV = U * V;
+    // A1, A2 are accumulated from zero (scal[3], scal[4])
+    if (cudaMemsetAsync(scal + 3, 0, 2 * sizeof(double), st) != cudaSuccess) return SNCC_ERR_CUDA;
+    diff_coeff_kernel<<<(UV + 255) / 256, 256, 0, st>>>(UV, d_rho_k, d_rho_t, reinterpret_cast<const float*>(ws + L.ef),
+                                                        reinterpret_cast<const float*>(ws + L.fbar), d_dloss, scal, a,
+                                                        b, h, hf);
+    const size_t smf = (4 * (size_t)(kTX + W - 1) * (kTY + H - 1) + 2 * (size_t)W * H) * 4;
+    dim3 gridf((M + kTX - 1) / kTX, (N + kTY - 1) / kTY);
+    diff_grad_f_kernel<<<gridf, 256, smf, st>>>(d_f, M, N, f_stride, W, H, c, t0, a, b, h, hf, d_grad_f,
+                                                grad_f_stride);
+    diff_gt_kernel<<<dim3(H, kGtChunks), 256, 0, st>>>(d_f, M, N, f_stride, W, H, a, gtp);
+    diff_grad_k_kernel<<<(K + 255) / 256, 256, 0, st>>>(W, H, reinterpret_cast<const int4*>(d_rects), d_k, K, gtp,
+                                                        scal, d_grad_k);
+    return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+}

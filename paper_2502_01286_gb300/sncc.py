@@ -36,7 +36,7 @@ EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_fr
             "sncc_probe_smem_read", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_batch_create",
             "sncc_batch_destroy", "sncc_batch_device_bytes", "sncc_batch_upload", "sncc_batch_set_variant",
             "sncc_batch_get_info", "sncc_batch_match", "sncc_batch_autotune", "sncc_batch_refine_workspace_bytes",
-            "sncc_batch_refine"]
+            "sncc_batch_refine", "sncc_diff_workspace_bytes", "sncc_diff_forward", "sncc_diff_backward"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -112,6 +112,12 @@ _lib.sncc_batch_refine_workspace_bytes.argtypes = [C.c_int]
 _lib.sncc_batch_refine_workspace_bytes.restype = C.c_size_t
 _lib.sncc_batch_refine.argtypes = [_vp, _vp, _pp, C.c_int, _vp, _vp, C.c_int, _vp, C.c_int, _vp, _vp, C.c_size_t,
                                    _vp, _vp]
+_lib.sncc_diff_workspace_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+_lib.sncc_diff_workspace_bytes.restype = C.c_size_t
+_lib.sncc_diff_forward.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp,
+                                   _vp, _vp, _vp, C.c_size_t, _vp]
+_lib.sncc_diff_backward.argtypes = [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp, _vp,
+                                    _vp, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp]
 _lib.sncc_get_plan_info.argtypes = [C.POINTER(_Segments), C.POINTER(PlanInfo)]
 _lib.sncc_probe_smem_read.argtypes = [_vp, C.c_int, C.c_int, _vp]
 _lib.sncc_exact_map.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64,
@@ -576,3 +582,105 @@ class Batch:
         raw = self.out[:n].cpu().numpy()
         return (raw[:, 0].astype(np.int64), raw[:, 1].astype(np.int64), raw[:, 2].astype(np.int64),
                 raw[:, 3].copy().view(np.float32))
+
+
+# ---------------------------------------------------------------------------
+# Differentiation: L = sum_o (rho_k - rho_t)^2 with hand-written gradients
+# ---------------------------------------------------------------------------
+class DiffProblem:
+    """Fixed segmentation (rectangles) of a float template t, with workspace,
+    for the loss between segmented and exact NCC over a float source."""
+
+    def __init__(self, t, rects, M: int, N: int, device="cuda"):
+        torch = _torch()
+        self.t = torch.as_tensor(np.ascontiguousarray(np.asarray(t, np.float32))).to(device)
+        self.rects = torch.as_tensor(np.ascontiguousarray(np.asarray(rects, np.int32))).to(device)
+        self.H, self.W = self.t.shape
+        self.M, self.N = M, N
+        self.K = self.rects.shape[0]
+        nbytes = int(_lib.sncc_diff_workspace_bytes(M, N, self.W, self.H))
+        if nbytes == 0:
+            raise SnccError(ERR_ARG, "sncc_diff_workspace_bytes")
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws_ptr = self.ws.data_ptr() + off
+        self.ws_bytes = nbytes
+        self.U, self.V = M - self.W + 1, N - self.H + 1
+
+    def loss(self, f, k):
+        """Differentiable L(f, k) (float64 scalar tensor)."""
+        return _SegmentedNCCLoss.apply(f, k, self)
+
+
+def _diff_forward(pb: DiffProblem, f, k):
+    torch = _torch()
+    rho_k = torch.empty((pb.V, pb.U), dtype=torch.float32, device=f.device)
+    rho_t = torch.empty_like(rho_k)
+    loss = torch.empty(1, dtype=torch.float64, device=f.device)
+    _check(_lib.sncc_diff_forward(f.data_ptr(), pb.M, pb.N, f.stride(0), pb.t.data_ptr(), pb.W, pb.H,
+                                  pb.rects.data_ptr(), k.data_ptr(), pb.K, rho_k.data_ptr(), rho_t.data_ptr(),
+                                  loss.data_ptr(), pb.ws_ptr, pb.ws_bytes, _stream(None)), "sncc_diff_forward")
+    return rho_k, rho_t, loss
+
+
+def _make_autograd():
+    import torch
+
+    class SegmentedNCCLoss(torch.autograd.Function):
+        """L = sum_o (rho_k - rho_t)^2; backward by the library's kernels."""
+
+        @staticmethod
+        def forward(ctx, f, k, pb):
+            if f.dtype != torch.float32 or k.dtype != torch.float32 or not f.is_cuda or f.stride(1) != 1:
+                raise ValueError("f and k must be float32 CUDA tensors (f with unit column stride)")
+            k = k.contiguous()
+            rho_k, rho_t, loss = _diff_forward(pb, f, k)
+            ctx.pb = pb
+            ctx.save_for_backward(f, k, rho_k, rho_t)
+            return loss[0]
+
+        @staticmethod
+        def backward(ctx, dloss):
+            f, k, rho_k, rho_t = ctx.saved_tensors
+            pb = ctx.pb
+            # the workspace must hold this forward's intermediates
+            _diff_forward(pb, f, k)
+            dl = dloss.reshape(1).to(torch.float64).contiguous()
+            grad_f = torch.empty((pb.N, pb.M), dtype=torch.float32, device=f.device)
+            grad_k = torch.empty(pb.K, dtype=torch.float32, device=f.device)
+            _check(_lib.sncc_diff_backward(f.data_ptr(), pb.M, pb.N, f.stride(0), pb.W, pb.H, pb.rects.data_ptr(),
+                                           k.data_ptr(), pb.K, rho_k.data_ptr(), rho_t.data_ptr(), dl.data_ptr(),
+                                           grad_f.data_ptr(), pb.M, grad_k.data_ptr(), pb.ws_ptr, pb.ws_bytes,
+                                           _stream(None)), "sncc_diff_backward")
+            return grad_f, grad_k, None
+
+    return SegmentedNCCLoss
+
+
+class _LazyFn:
+    fn = None
+
+    @classmethod
+    def apply(cls, *a):
+        if cls.fn is None:
+            cls.fn = _make_autograd()
+        return cls.fn.apply(*a)
+
+
+_SegmentedNCCLoss = _LazyFn
+
+
+def refit_segment_values(pb: DiffProblem, f, k0, steps: int = 100, lr: float = 0.5):
+    """Refits the segment values at a fixed segmentation so that segmented NCC
+    tracks exact NCC (Adam on L); returns (k, losses)."""
+    torch = _torch()
+    k = torch.nn.Parameter(torch.as_tensor(np.asarray(k0, np.float32)).to(f.device).clone())
+    opt = torch.optim.Adam([k], lr=lr)
+    losses = []
+    for _ in range(steps):
+        opt.zero_grad()
+        loss = pb.loss(f, k)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.item()))
+    return k.detach(), losses

@@ -161,3 +161,20 @@ def batch_templates(sources: list, count: int = 64, seed: int = BASE_SEED + 4, l
 def random_image(seed: int, M: int, N: int, lo: int = 0, hi: int = 256) -> np.ndarray:
     """Uniform random uint8 image (N, M) for small edge-case tests."""
     return rng(seed).integers(lo, hi, size=(N, M), dtype=np.int64).astype(np.uint8)
+
+
+def case_diff(M: int = 512, N: int = 512, W: int = 48, H: int = 48, seed: int = BASE_SEED + 5,
+              noise: float = 2.0, sigma_max: float = 12.0):
+    """Float source for the differentiation workload: 20 blobs plus 1/f noise
+    of rms 30 (so the std threshold 12 stays below the template's std, as
+    Section 3 requires), scaled linearly to [0, 255] (float32, not quantised);
+    the template is a W x H crop plus N(0, noise^2), float32.
+    Returns (f, t, origin, sigma)."""
+    g = rng(seed)
+    img = blobs(g, M, N, 20) + fractal_noise(g, M, N, 30.0, "rms")
+    img = (img - img.min()) * (255.0 / (img.max() - img.min()))
+    f = img.astype(np.float32)
+    u0 = int(g.integers(0, M - W + 1))
+    v0 = int(g.integers(0, N - H + 1))
+    t = (f[v0:v0 + H, u0:u0 + W].astype(np.float64) + g.normal(0.0, noise, size=(H, W))).astype(np.float32)
+    return f, t, (u0, v0), sigma_max

@@ -369,3 +369,60 @@ def test_main_algorithm_two_approximations_brute_force():
     np.testing.assert_array_equal(r["idx"], want)
     np.testing.assert_allclose(r["rho"], ps.ravel()[want], atol=1e-10)
     assert len(want) > 0 and ap_s.K > ap_f.K
+
+
+# ---------------------------------------------------------------- differentiable loss
+def _diff_problem(seed=3, M=15, N=12, W=6, H=5, sigma=4.0):
+    from oracle import diff as D  # noqa: F401
+    g = np.random.default_rng(seed)
+    f = g.uniform(0, 255, size=(N, M))
+    t = f[3:3 + H, 4:4 + W] + g.normal(0, 3.0, size=(H, W))
+    ap = O.precompute_template_approximation(t, sigma)
+    kv = ap.mu + g.normal(0, 2.0, size=ap.K)  # move off the fitted means
+    return f, t, ap.segments, kv
+
+
+def test_diff_forward_matches_segmented_ncc():
+    """The differentiable forward with k_i = the segment means is the
+    segmented NCC of Eq. 18 (weighted energy) and Eq. 1."""
+    from oracle import diff as D
+    f, t, rects, _ = _diff_problem()
+    ap = O.precompute_template_approximation(t, 4.0)
+    fw = D.forward(f, t, rects, ap.mu)
+    np.testing.assert_allclose(fw["rho_k"], O.segmented_ncc_map(f, ap, "direct"), atol=1e-12)
+    np.testing.assert_allclose(fw["rho_t"], O.ncc_exact_map(f, t), atol=1e-12)
+
+
+def test_diff_gradients_vs_central_differences():
+    """Analytic dL/dk and dL/df against FP64 central differences of the loss
+    (step 1e-5 in intensity units)."""
+    from oracle import diff as D
+    f, t, rects, kv = _diff_problem()
+    gr = D.gradients(f, t, rects, kv)
+    eps = 1e-5
+    num_k = np.empty(len(kv))
+    for j in range(len(kv)):
+        kp = kv.copy(); kp[j] += eps
+        km = kv.copy(); km[j] -= eps
+        num_k[j] = (D.forward(f, t, rects, kp)["loss"] - D.forward(f, t, rects, km)["loss"]) / (2 * eps)
+    np.testing.assert_allclose(gr["dk"], num_k, rtol=1e-6, atol=1e-9 * np.abs(num_k).max())
+    rng = np.random.default_rng(0)
+    for _ in range(25):
+        y, x = int(rng.integers(0, f.shape[0])), int(rng.integers(0, f.shape[1]))
+        fp = f.copy(); fp[y, x] += eps
+        fm = f.copy(); fm[y, x] -= eps
+        num = (D.forward(fp, t, rects, kv)["loss"] - D.forward(fm, t, rects, kv)["loss"]) / (2 * eps)
+        assert abs(gr["df"][y, x] - num) <= 1e-6 * max(1e-3, np.abs(gr["df"]).max())
+    assert np.abs(gr["df"]).max() > 0 and np.abs(gr["dk"]).max() > 0
+
+
+def test_diff_loss_zero_when_k_is_t():
+    """With every pixel its own segment and k = t, rho_k = rho_t and L = 0,
+    so both gradients vanish."""
+    from oracle import diff as D
+    f, t, _, _ = _diff_problem()
+    H, W = t.shape
+    rects = np.array([(x, y, 1, 1) for y in range(H) for x in range(W)])
+    gr = D.gradients(f, t, rects, t.ravel())
+    assert gr["loss"] < 1e-20
+    assert np.abs(gr["dk"]).max() < 1e-9 and np.abs(gr["df"]).max() < 1e-9
