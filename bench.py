@@ -318,7 +318,7 @@ def workload_config(name, case, sigmas, precision, U, V):
 # ---------------------------------------------------------------------------
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("sncc_match.cu", "sncc_ptx.cuh", "sncc_internal.h"):
+    for fn in ("sncc_match.cu", "sncc_ptx.cuh", "sncc_internal.h", "sncc_tile.cuh"):
         with open(os.path.join(ROOT, "paper_2502_01286_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -157,7 +157,8 @@ __device__ __forceinline__ void block_scan2(int64_t& a, int64_t& b, int64_t* sm)
     }
     __syncthreads();
     if (warp > 0) { a += sm[64 + warp - 1]; b += sm[96 + warp - 1]; }
-    __syncthreads();  // sm is reused by the next row
+    // no trailing barrier: callers alternate between two scratch copies, and
+    // the next use of this copy is two scans (and two barriers) later
 }
 
 // Pass 3.  Thread t owns output columns X in [tE, tE+E), i.e. inputs
@@ -167,7 +168,7 @@ template <int E, typename ST>
 __global__ void sat_emit(const uint8_t* __restrict__ f, int M, int N, int stride, int R, int pitch,
                          const int32_t* __restrict__ cs1, const int32_t* __restrict__ cs2, ST* __restrict__ s,
                          int64_t* __restrict__ s2) {
-    __shared__ int64_t sm[128];
+    __shared__ int64_t sm[2][128];
     const int b = blockIdx.x;
     const int t = threadIdx.x;
     const int X0 = t * E;
@@ -186,13 +187,13 @@ __global__ void sat_emit(const uint8_t* __restrict__ f, int M, int N, int stride
         for (int e = 0; e < E; ++e)
             if (X0 + e <= M) { s[X0 + e] = 0; s2[X0 + e] = 0; }
     }
-    const bool vec = ((stride & 7) == 0) && ((reinterpret_cast<uintptr_t>(f) & 7) == 0) && (E == 8);
-    for (int y = y0; y < y1; ++y) {
+    const bool vec = ((stride & 7) == 0) && ((reinterpret_cast<uintptr_t>(f) & 7) == 0) && (E == 8) &&
+                     (X0 + E - 1 < M) && (X0 >= 1);
+    // Loads the E input bytes x = X0-1 .. X0+E-2 of row y (zero outside the row).
+    auto load_row = [&](int y, int (&v)[E]) {
         const uint8_t* row = f + (size_t)y * stride;
-        int v[E];
-        if (vec && X0 + E - 1 < M && X0 >= 1) {
-            // bytes X0-1 .. X0+6: one aligned 8-byte load (X0 .. X0+7, all
-            // inside the row) plus the byte before
+        if (vec) {
+            // one aligned 8-byte load (X0 .. X0+7, inside the row) plus the byte before
             const uint2 w = __ldg(reinterpret_cast<const uint2*>(row + X0));
             v[0] = row[X0 - 1];
             v[1] = w.x & 0xff; v[2] = (w.x >> 8) & 0xff; v[3] = (w.x >> 16) & 0xff; v[4] = w.x >> 24;
@@ -204,6 +205,14 @@ __global__ void sat_emit(const uint8_t* __restrict__ f, int M, int N, int stride
                 v[e] = (x >= 0 && x < M) ? row[x] : 0;
             }
         }
+    };
+    int nxt[E];
+    if (y0 < y1) load_row(y0, nxt);
+    for (int y = y0; y < y1; ++y) {
+        int v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = nxt[e];
+        if (y + 1 < y1) load_row(y + 1, nxt);  // in flight during this row's scan
         int64_t p[E], p2[E];
         int64_t run = 0, run2 = 0;
 #pragma unroll
@@ -216,7 +225,7 @@ __global__ void sat_emit(const uint8_t* __restrict__ f, int M, int N, int stride
             p2[e] = run2;
         }
         int64_t inc = run, inc2 = run2;
-        block_scan2(inc, inc2, sm);
+        block_scan2(inc, inc2, sm[(y - y0) & 1]);
         const int64_t base = inc - run, base2 = inc2 - run2;
         ST* srow = s + (size_t)(y + 1) * pitch + X0;
         int64_t* s2row = s2 + (size_t)(y + 1) * pitch + X0;
