@@ -162,9 +162,10 @@ int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int
  * Arguments, layout and results are those of sncc_integral (same kernels);
  * the band sums live instead in a fixed array of SNCC_NOALLOC_SCRATCH_BYTES
  * (16 MiB) of device memory that every GPU which loads the library holds
- * until the process exits.  That covers every source up to 6898 columns
- * wide (any N up to 65535); larger sources return SNCC_ERR_CAPACITY and
- * launch nothing.  No call allocates or frees memory.
+ * until the process exits.  That covers every source of up to 100 million
+ * pixels (e.g. 10000 x 10000 or 16383 x 6100); a source whose
+ * sncc_integral_workspace_bytes exceeds it returns SNCC_ERR_CAPACITY and
+ * launches nothing.  No call allocates or frees memory.
  *
  * The first call on a device (with that device current) looks up the
  * array's device address; make that first call before any stream capture.

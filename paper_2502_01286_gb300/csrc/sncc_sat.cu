@@ -3,15 +3,21 @@
 // Layout: padded tables of (N+1) rows x pitch elements, entry [Y*pitch + X]
 // = sum of f over x < X, y < Y (row 0 and column 0 are zero).
 //
-// Three passes, all coalesced along rows:
-//   1. band column sums: for every band of R rows and every column x, the sum
-//      of f (and f^2) over the band's rows (reads f once);
-//   2. band scan: exclusive prefix of those sums over the bands, giving for
-//      each band the column sums of everything above it;
-//   3. emit: one CTA per band walks its rows, keeps the running column sums in
-//      registers, scans each row across the full width and writes s and s^2.
+// The table is produced in tiles of (band of R rows) x (chunk of 1024
+// columns), so that every tile is independent once two kinds of carry are
+// known:
+//   1. band column sums: for every band and column, the sum of f (and f^2)
+//      over the band's rows;
+//   2. band scan: exclusive prefix of those over the bands, i.e. for every
+//      band and column the sum of the column above the band;
+//   3. row carries (one warp per row): for every row and chunk, the sum of the
+//      row left of the chunk;
+//   4. tile emit (one CTA of 256 threads per tile, four output columns per
+//      thread, 16-byte stores): s(X, Y) = corner + sum of the row carries of
+//      the band's rows so far + CTA-wide prefix over the tile of the running
+//      column sums, where corner = the band's column carries left of the tile.
 // Algorithmic traffic: 1 B/px read, 4 or 8 B/px (s) + 8 B/px (s^2) written;
-// passes 1-2 add one more read of f and a small band x width array.
+// passes 1 and 3 read f once more each, and the carries are small arrays.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -23,24 +29,26 @@
 namespace sncc {
 namespace {
 
-constexpr int kTargetBands = 304;  // two bands per SM on 152 SMs
+constexpr int kThreads = 256;             // threads per emit CTA
+constexpr int kPer = 4;                   // source columns per emit thread
+constexpr int kChunk = kThreads * kPer;   // columns per tile
+constexpr int kTargetTiles = 8 * 152;     // about eight emit CTAs per SM
 
 struct SatGeometry {
-    int R;      // rows per band
-    int nb;     // number of bands
-    int E;      // output columns per thread in the emit pass
-    int T;      // threads per emit CTA
+    int R;   // rows per band
+    int nb;  // bands
+    int nc;  // column chunks
 };
 
 SatGeometry sat_geometry(int M, int N) {
     SatGeometry g;
-    g.R = (N + kTargetBands - 1) / kTargetBands;
-    if (g.R < 1) g.R = 1;
+    g.nc = (M + 1 + kChunk - 1) / kChunk;  // chunks cover output columns 0 .. M
+    long long r = ((long long)N * g.nc + kTargetTiles - 1) / kTargetTiles;
+    if (r < 2) r = 2;
+    if (r > 64) r = 64;
+    if (r > N) r = N;
+    g.R = (int)r;
     g.nb = (N + g.R - 1) / g.R;
-    g.E = (M + 1 <= 8192) ? 8 : 16;
-    const int threads = (M + 1 + g.E - 1) / g.E;
-    g.T = (threads + 31) / 32 * 32;
-    if (g.T < 32) g.T = 32;
     return g;
 }
 
@@ -134,7 +142,60 @@ __global__ void __launch_bounds__(256) sat_band_scan(int M, int nb, int32_t* __r
     }
 }
 
-// Inclusive CTA-wide scan of two 64-bit values.  All threads call it.
+// Pass 3: rc[c][y] = sum of f (f^2) over source columns x < 1024c of row y.
+// One warp per row: lane l reads bytes 1024c + 32l .. 32l+31 of each chunk,
+// the warp reduces the chunk sums, and lane 0 writes their exclusive prefix.
+// Chunk sums fit int32 (M <= 16383).
+__global__ void __launch_bounds__(256) sat_row_carry(const uint8_t* __restrict__ f, int M, int N, int stride,
+                                                     int nc, int32_t* __restrict__ rc1, int32_t* __restrict__ rc2) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int y = blockIdx.x * 8 + warp;
+    if (y >= N) return;  // warp-uniform; no CTA barrier below
+    const uint8_t* row = f + (size_t)y * stride;
+    const bool vec = ((stride & 15) == 0) && ((reinterpret_cast<uintptr_t>(f) & 15) == 0);
+    int32_t run1 = 0, run2 = 0;
+    for (int c = 0; c < nc; ++c) {
+        const int xb = c * kChunk + lane * 32;
+        int s1 = 0, s2 = 0;
+        if (vec && xb + 31 < M) {
+            const uint4* q = reinterpret_cast<const uint4*>(row + xb);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint4 w = __ldg(q + h);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int a = (ws[i] >> (8 * k)) & 0xff;
+                        s1 += a;
+                        s2 += a * a;
+                    }
+            }
+        } else {
+            for (int k = 0; k < 32; ++k)
+                if (xb + k < M) {
+                    const int v = row[xb + k];
+                    s1 += v;
+                    s2 += v * v;
+                }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            rc1[(size_t)c * N + y] = run1;
+            rc2[(size_t)c * N + y] = run2;
+        }
+        run1 += s1;
+        run2 += s2;
+    }
+}
+
+// Inclusive CTA-wide scan of two 64-bit values.  All threads call it; sm is
+// one of two scratch copies that callers alternate (see below).
 __device__ __forceinline__ void block_scan2(int64_t& a, int64_t& b, int64_t* sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -161,116 +222,126 @@ __device__ __forceinline__ void block_scan2(int64_t& a, int64_t& b, int64_t* sm)
     // the next use of this copy is two scans (and two barriers) later
 }
 
-// Pass 3.  Thread t owns output columns X in [tE, tE+E), i.e. inputs
-// x = X - 1 in [tE-1, tE+E-1); it keeps their running column sums (the
-// column prefix of f above the current row) in registers.
-template <int E, typename ST>
-__global__ void sat_emit(const uint8_t* __restrict__ f, int M, int N, int stride, int R, int pitch,
-                         const int32_t* __restrict__ cs1, const int32_t* __restrict__ cs2, ST* __restrict__ s,
-                         int64_t* __restrict__ s2) {
+// Pass 4: one CTA per tile (chunk c = blockIdx.x, band b = blockIdx.y).
+// Thread t owns output columns X = 1024c + 4t .. 4t+3 (16-byte aligned
+// stores), i.e. source columns x = X - 1; the tile's inputs therefore start
+// at x = 1024c - 1, and the left carry is the table at X = 1024c - 1:
+//   corner  = sum_{x < 1024c-1} (column sums above the band),
+//   row y   : sum_{x < 1024c-1} f(x, y) = rc[c][y] - f(1024c - 1, y).
+template <typename ST>
+__global__ void __launch_bounds__(kThreads) sat_tile_emit(const uint8_t* __restrict__ f, int M, int N, int stride,
+                                                          int R, int pitch, const int32_t* __restrict__ cs1,
+                                                          const int32_t* __restrict__ cs2,
+                                                          const int32_t* __restrict__ rc1,
+                                                          const int32_t* __restrict__ rc2, ST* __restrict__ s,
+                                                          int64_t* __restrict__ s2) {
     __shared__ int64_t sm[2][128];
-    const int b = blockIdx.x;
-    const int t = threadIdx.x;
-    const int X0 = t * E;
-    const int y0 = b * R;
-    const int y1 = min(y0 + R, N);
-    int32_t col[E], col2[E];
+    __shared__ int32_t rcs1[64], rcs2[64];
+    const int c = blockIdx.x, b = blockIdx.y, t = threadIdx.x;
+    const int lane = t & 31;
+    const int X0 = c * kChunk;          // first output column of the tile
+    const int Xt = X0 + kPer * t;       // this thread's first output column
+    const int xe = X0 - 1;              // the source column just left of the tile's own
+    const int y0 = b * R, y1 = min(y0 + R, N);
+    // corner = column sums above the band over x < X0 - 1
+    int64_t k1 = 0, k2 = 0;
+    for (int i = t; i < xe; i += kThreads) {
+        k1 += cs1[(size_t)b * M + i];
+        k2 += cs2[(size_t)b * M + i];
+    }
+    if (t < y1 - y0) {  // the band's row carries, to shared memory
+        rcs1[t] = rc1[(size_t)c * N + y0 + t];
+        rcs2[t] = rc2[(size_t)c * N + y0 + t];
+    }
+    block_scan2(k1, k2, sm[0]);  // inclusive: the last thread holds the totals
+    __syncthreads();
+    if (t == kThreads - 1) { sm[1][0] = k1; sm[1][1] = k2; }
+    __syncthreads();
+    int64_t left1 = sm[1][0], left2 = sm[1][1];
+    __syncthreads();
+    int32_t col1[kPer], col2[kPer];
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int x = X0 + e - 1;
+    for (int e = 0; e < kPer; ++e) {
+        const int x = Xt + e - 1;
         const bool in = (x >= 0) && (x < M);
-        col[e] = in ? cs1[(size_t)b * M + x] : 0;
+        col1[e] = in ? cs1[(size_t)b * M + x] : 0;
         col2[e] = in ? cs2[(size_t)b * M + x] : 0;
     }
-    const bool full = (X0 + E - 1 <= M);
+    const bool full = (Xt + kPer - 1 <= M);  // all four outputs exist
     if (b == 0) {  // row Y = 0 is all zero
-        for (int e = 0; e < E; ++e)
-            if (X0 + e <= M) { s[X0 + e] = 0; s2[X0 + e] = 0; }
+#pragma unroll
+        for (int e = 0; e < kPer; ++e)
+            if (Xt + e <= M) { s[Xt + e] = 0; s2[Xt + e] = 0; }
     }
-    const bool vec = ((stride & 7) == 0) && ((reinterpret_cast<uintptr_t>(f) & 7) == 0) && (E == 8) &&
-                     (X0 + E - 1 < M) && (X0 >= 1);
-    // Loads the E input bytes x = X0-1 .. X0+E-2 of row y (zero outside the row).
-    auto load_row = [&](int y, int (&v)[E]) {
+    // Inputs x = Xt-1 .. Xt+2: an aligned 4-byte load of Xt .. Xt+3 gives the
+    // last three; the first is the previous lane's fourth byte (lane 0 loads it).
+    const bool vec = ((stride & 3) == 0) && ((reinterpret_cast<uintptr_t>(f) & 3) == 0) && (Xt + kPer - 1 < M);
+    auto load = [&](int y, int (&v)[kPer], int& edge) {
         const uint8_t* row = f + (size_t)y * stride;
+        uint32_t w = 0;
         if (vec) {
-            // one aligned 8-byte load (X0 .. X0+7, inside the row) plus the byte before
-            const uint2 w = __ldg(reinterpret_cast<const uint2*>(row + X0));
-            v[0] = row[X0 - 1];
-            v[1] = w.x & 0xff; v[2] = (w.x >> 8) & 0xff; v[3] = (w.x >> 16) & 0xff; v[4] = w.x >> 24;
-            v[5] = w.y & 0xff; v[6] = (w.y >> 8) & 0xff; v[7] = (w.y >> 16) & 0xff;
+            w = __ldg(reinterpret_cast<const uint32_t*>(row + Xt));
         } else {
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int x = X0 + e - 1;
-                v[e] = (x >= 0 && x < M) ? row[x] : 0;
-            }
+            for (int e = 0; e < kPer; ++e)
+                if (Xt + e < M) w |= (uint32_t)row[Xt + e] << (8 * e);
         }
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, w, 1);
+        const int x_first = Xt - 1;
+        v[0] = (lane > 0) ? (int)(prev >> 24) : ((x_first >= 0 && x_first < M) ? row[x_first] : 0);
+#pragma unroll
+        for (int e = 1; e < kPer; ++e) v[e] = (w >> (8 * (e - 1))) & 0xff;
+        edge = (xe >= 0) ? row[xe] : 0;  // uniform
     };
-    int nxt[E];
-    if (y0 < y1) load_row(y0, nxt);
+    int nxt[kPer], nedge = 0;
+    if (y0 < y1) load(y0, nxt, nedge);
     for (int y = y0; y < y1; ++y) {
-        int v[E];
+        int v[kPer];
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = nxt[e];
-        if (y + 1 < y1) load_row(y + 1, nxt);  // in flight during this row's scan
-        int64_t p[E], p2[E];
-        int64_t run = 0, run2 = 0;
+        for (int e = 0; e < kPer; ++e) v[e] = nxt[e];
+        const int edge = nedge;
+        if (y + 1 < y1) load(y + 1, nxt, nedge);  // in flight during this row's scan
+        int64_t p1[kPer], p2[kPer];
+        int64_t r1 = 0, r2 = 0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            col[e] += v[e];
+        for (int e = 0; e < kPer; ++e) {
+            col1[e] += v[e];
             col2[e] += v[e] * v[e];
-            run += col[e];
-            run2 += col2[e];
-            p[e] = run;
-            p2[e] = run2;
+            r1 += col1[e];
+            r2 += col2[e];
+            p1[e] = r1;
+            p2[e] = r2;
         }
-        int64_t inc = run, inc2 = run2;
-        block_scan2(inc, inc2, sm[(y - y0) & 1]);
-        const int64_t base = inc - run, base2 = inc2 - run2;
-        ST* srow = s + (size_t)(y + 1) * pitch + X0;
-        int64_t* s2row = s2 + (size_t)(y + 1) * pitch + X0;
+        int64_t i1 = r1, i2 = r2;
+        block_scan2(i1, i2, sm[(y - y0) & 1]);
+        if (xe >= 0) {
+            left1 += rcs1[y - y0] - edge;
+            left2 += rcs2[y - y0] - edge * edge;
+        }
+        const int64_t base1 = left1 + i1 - r1, base2 = left2 + i2 - r2;
+        ST* srow = s + (size_t)(y + 1) * pitch + Xt;
+        int64_t* s2row = s2 + (size_t)(y + 1) * pitch + Xt;
         if (full) {
             if constexpr (sizeof(ST) == 4) {
-#pragma unroll
-                for (int e = 0; e < E; e += 4) {
-                    int4 o;
-                    o.x = (int)(base + p[e]); o.y = (int)(base + p[e + 1]);
-                    o.z = (int)(base + p[e + 2]); o.w = (int)(base + p[e + 3]);
-                    *reinterpret_cast<int4*>(srow + e) = o;
-                }
+                int4 o;
+                o.x = (int)(base1 + p1[0]); o.y = (int)(base1 + p1[1]);
+                o.z = (int)(base1 + p1[2]); o.w = (int)(base1 + p1[3]);
+                *reinterpret_cast<int4*>(srow) = o;
             } else {
-#pragma unroll
-                for (int e = 0; e < E; e += 2) {
-                    longlong2 o;
-                    o.x = base + p[e]; o.y = base + p[e + 1];
-                    *reinterpret_cast<longlong2*>(srow + e) = o;
-                }
+                *reinterpret_cast<longlong2*>(srow) = make_longlong2(base1 + p1[0], base1 + p1[1]);
+                *reinterpret_cast<longlong2*>(srow + 2) = make_longlong2(base1 + p1[2], base1 + p1[3]);
             }
-#pragma unroll
-            for (int e = 0; e < E; e += 2) {
-                longlong2 o;
-                o.x = base2 + p2[e]; o.y = base2 + p2[e + 1];
-                *reinterpret_cast<longlong2*>(s2row + e) = o;
-            }
+            *reinterpret_cast<longlong2*>(s2row) = make_longlong2(base2 + p2[0], base2 + p2[1]);
+            *reinterpret_cast<longlong2*>(s2row + 2) = make_longlong2(base2 + p2[2], base2 + p2[3]);
         } else {
-            for (int e = 0; e < E; ++e)
-                if (X0 + e <= M) {
-                    srow[e] = (ST)(base + p[e]);
+#pragma unroll
+            for (int e = 0; e < kPer; ++e)
+                if (Xt + e <= M) {
+                    srow[e] = (ST)(base1 + p1[e]);
                     s2row[e] = base2 + p2[e];
                 }
         }
     }
-}
-
-template <int E>
-cudaError_t launch_emit(const SatGeometry& g, const uint8_t* f, int M, int N, int stride, int pitch,
-                        const int32_t* cs1, const int32_t* cs2, void* s, int s_bits, int64_t* s2,
-                        cudaStream_t st) {
-    if (s_bits == 32)
-        sat_emit<E, int32_t><<<g.nb, g.T, 0, st>>>(f, M, N, stride, g.R, pitch, cs1, cs2, (int32_t*)s, s2);
-    else
-        sat_emit<E, int64_t><<<g.nb, g.T, 0, st>>>(f, M, N, stride, g.R, pitch, cs1, cs2, (int64_t*)s, s2);
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -279,7 +350,7 @@ cudaError_t launch_emit(const SatGeometry& g, const uint8_t* f, int M, int N, in
 extern "C" size_t sncc_integral_workspace_bytes(int M, int N) {
     if (M <= 0 || N <= 0) return 0;
     const sncc::SatGeometry g = sncc::sat_geometry(M, N);
-    return (size_t)2 * g.nb * (size_t)M * sizeof(int32_t) + 256;
+    return (size_t)2 * g.nb * (size_t)M * sizeof(int32_t) + (size_t)2 * g.nc * (size_t)N * sizeof(int32_t) + 256;
 }
 
 extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int s_bits, int64_t* d_s2,
@@ -299,13 +370,21 @@ extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, voi
     const SatGeometry g = sat_geometry(M, N);
     int32_t* cs1 = static_cast<int32_t*>(d_ws);
     int32_t* cs2 = cs1 + (size_t)g.nb * M;
+    int32_t* rc1 = cs2 + (size_t)g.nb * M;
+    int32_t* rc2 = rc1 + (size_t)g.nc * N;
     cudaStream_t st = (cudaStream_t)stream;
     dim3 g1((M / 4 + 1 + 255) / 256, g.nb);
     sat_band_colsum<<<g1, 256, 0, st>>>(d_f, M, N, f_stride, g.R, cs1, cs2);
     sat_band_scan<<<(M + 31) / 32, 256, 0, st>>>(M, g.nb, cs1, cs2);
-    cudaError_t e = (g.E == 8) ? launch_emit<8>(g, d_f, M, N, f_stride, sat_pitch, cs1, cs2, d_s, s_bits, d_s2, st)
-                               : launch_emit<16>(g, d_f, M, N, f_stride, sat_pitch, cs1, cs2, d_s, s_bits, d_s2, st);
-    return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+    sat_row_carry<<<(N + 7) / 8, 256, 0, st>>>(d_f, M, N, f_stride, g.nc, rc1, rc2);
+    dim3 g4(g.nc, g.nb);
+    if (s_bits == 32)
+        sat_tile_emit<int32_t><<<g4, kThreads, 0, st>>>(d_f, M, N, f_stride, g.R, sat_pitch, cs1, cs2, rc1, rc2,
+                                                      static_cast<int32_t*>(d_s), d_s2);
+    else
+        sat_tile_emit<int64_t><<<g4, kThreads, 0, st>>>(d_f, M, N, f_stride, g.R, sat_pitch, cs1, cs2, rc1, rc2,
+                                                      static_cast<int64_t*>(d_s), d_s2);
+    return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------

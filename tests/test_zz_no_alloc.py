@@ -70,11 +70,11 @@ def test_noalloc_shrinking_sizes_leave_no_stale_state(sncc):
 
 def test_noalloc_rejects_sources_beyond_the_scratch(sncc):
     """A source whose band sums need more than the built-in 16 MiB is refused
-    with SNCC_ERR_CAPACITY and nothing is launched."""
-    M, N = 16000, 400
+    with SNCC_ERR_CAPACITY before anything is launched or read (the buffers
+    passed here are far too small for the size and are never touched)."""
+    M, N = 16383, 65535
     assert sncc.lib().sncc_integral_workspace_bytes(M, N) > sncc.NOALLOC_SCRATCH_BYTES
-    f = torch.zeros((N, M), dtype=torch.uint8, device="cuda")
-    tb = sncc.alloc_tables(M, N, 64)
-    with pytest.raises(sncc.SnccError) as e:
-        sncc.integral_noalloc(f, tb)
-    assert e.value.code == sncc.ERR_CAPACITY
+    dummy = torch.zeros(64, dtype=torch.int64, device="cuda")
+    rc = sncc.lib().sncc_integral_noalloc(dummy.data_ptr(), M, N, M, dummy.data_ptr(), 64, dummy.data_ptr(),
+                                          sncc.sat_pitch(M), None)
+    assert rc == sncc.ERR_CAPACITY
