@@ -344,6 +344,38 @@ def measured_peaks():
         return {}
 
 
+def measure_ceilings(sncc, torch, stream, dev):
+    """On-chip ceilings measured live by the library's probes (best of 5):
+    shared-memory read GB/s, dp4a and 32x32->64-bit multiply-add
+    instructions per second (lane operations)."""
+    sink = torch.empty(152 * 8 * 256, dtype=torch.int32, device=dev)
+
+    def best(launch):
+        launch(8)
+        rates = []
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            n = launch(2048)
+            b.record(stream)
+            torch.cuda.synchronize()
+            rates.append(n / (a.elapsed_time(b) * 1e-3))
+        return max(rates)
+
+    return {"smem_gbs": best(lambda it: sncc.probe_smem_read(sink, 152 * 8, it)) / 1e9,
+            "dp4a_per_s": best(lambda it: sncc.probe_alu(sncc.PROBE_DP4A, sink, 152 * 8, it // 4)),
+            "imad_wide_per_s": best(lambda it: sncc.probe_alu(sncc.PROBE_IMAD_WIDE, sink, 152 * 8, it // 4))}
+
+
+def exact_roofline(macs, ms, ceil):
+    """The exact comparator against the dp4a ceiling (4 pixel MACs each)."""
+    achieved = macs / (ms * 1e-3) / 1e12
+    peak = 4 * ceil["dp4a_per_s"] / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TMAC/s", "frac": achieved / peak,
+            "peak_source": "measured: dp4a instruction probe (all SMs) x 4 MACs, this run"}
+
+
 def run_gpu(args, world, rank, local, pg):
     import torch
     from paper_2502_01286_gb300 import build as lib_build
@@ -507,19 +539,9 @@ def run_gpu(args, world, rank, local, pg):
     except sncc.SnccError as e:
         two = {"unavailable": str(e)}
 
-    # --- shared-memory read roofline of the segment-sum kernel ---
-    sink = torch.empty(152 * 8 * 256, dtype=torch.int32, device=dev)
-    sncc.probe_smem_read(sink, 152 * 8, 64)
-    smem_gbs = []
-    for _ in range(5):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        nbytes = sncc.probe_smem_read(sink, 152 * 8, 2048)
-        b.record(stream)
-        torch.cuda.synchronize()
-        smem_gbs.append(nbytes / (a.elapsed_time(b) * 1e-3) / 1e9)
-    smem_peak = max(smem_gbs)
+    # --- on-chip ceilings of the segment-sum kernel and the comparator ---
+    ceil = measure_ceilings(sncc, torch, stream, dev)
+    smem_peak = ceil["smem_gbs"]
 
     # dominant kernel: the segment-sum launch with the most corners
     infos = [s.plan_info() for s in segs]
@@ -557,7 +579,8 @@ def run_gpu(args, world, rank, local, pg):
         "dtype": "int64", "data": "synthetic",
         "config": workload_config(args.workload, case, SIGMAS, PRECISION, U, V),
         "exact_ncc": {"value": U * V / (exact_ms * 1e-3) / 1e9, "unit": UNIT, "ms": exact_ms,
-                      "kernel": "direct integer correlation, CUDA cores"},
+                      "kernel": "direct integer correlation, dp4a (4 byte MACs per instruction)",
+                      "roofline": exact_roofline(U * V * W * H, exact_ms, ceil)},
         "speedup_vs_exact": value / (U * V / (exact_ms * 1e-3) / 1e9),
         "max_abs_dncc_vs_exact": dict(zip([str(s) for s in SIGMAS], max_dncc)),
         "per_sigma": [{"sigma_max": s, "K": seg.K, "corners": infos[i]["corners"], "rho_max": seg.rho_max,
@@ -576,10 +599,13 @@ def run_gpu(args, world, rank, local, pg):
                      "traffic": recorded_traffic(args.workload), "bytes_per_launch": dom_bytes,
                      "ms_per_launch": dom_ms,
                      "peak_source": "measured: shared-memory read probe (all SMs), this run",
-                     "hbm_peak_gbs": peaks.get("hbm_gbs")},
+                     "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                     "imad_wide_ceiling": {"achieved": dom_bytes / 4 / (dom_ms * 1e-3),
+                                           "peak": ceil["imad_wide_per_s"], "unit": "corner-ops/s",
+                                           "frac": dom_bytes / 4 / (dom_ms * 1e-3) / ceil["imad_wide_per_s"]}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h_total / e2e_steps, "ms_per_step": e2e_ms_step},
-        "gpu_launches": args.steps * (3 + 3 * len(SIGMAS)),
+        "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS + 3 * len(SIGMAS)),
         "clocks": clk, "wall_s_timed": wall,
     }
     if cpu is not None:
@@ -681,18 +707,8 @@ def run_gpu_batch(args, world, rank, local, pg):
         mk.append(a.elapsed_time(e))
     match_ms = statistics.median(mk)
     bytes_launch = info["corner_offsets"] * 4.0
-    sink = torch.empty(152 * 8 * 256, dtype=torch.int32, device=dev)
-    sncc.probe_smem_read(sink, 152 * 8, 64)
-    pk = []
-    for _ in range(5):
-        a = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        nbytes = sncc.probe_smem_read(sink, 152 * 8, 2048)
-        e.record(stream)
-        torch.cuda.synchronize()
-        pk.append(nbytes / (a.elapsed_time(e) * 1e-3) / 1e9)
-    smem_peak = max(pk)
+    ceil = measure_ceilings(sncc, torch, stream, dev)
+    smem_peak = ceil["smem_gbs"]
 
     # end to end: sources from pinned host memory, graph replay, matches back
     host = [torch.as_tensor(f).pin_memory() for f in srcs]
@@ -723,9 +739,11 @@ def run_gpu_batch(args, world, rank, local, pg):
     a = torch.cuda.Event(enable_timing=True)
     e = torch.cuda.Event(enable_timing=True)
     a.record(stream)
+    exact_macs = 0
     for si in range(len(srcs)):
         for ti, (t, _, _) in enumerate(tl):
             H, W = t.shape
+            exact_macs += (N - H + 1) * (M - W + 1) * H * W
             out = rho_buf[:(N - H + 1) * (M - W + 1)].view(N - H + 1, M - W + 1)
             sncc.exact_map(fd[si], t_devs[ti], segs[ti].T, segs[ti].T2, tb[si], out)
     e.record(stream)
@@ -757,7 +775,8 @@ def run_gpu_batch(args, world, rank, local, pg):
                    "launch": "one CUDA graph: sum tables x8, one persistent coarse launch, refine, sort",
                    "tile_rows": info["tile_rows"], "autotune_ms": tune},
         "exact_ncc": {"value": info["offsets"] / (exact_ms * 1e-3) / 1e9, "unit": UNIT, "ms": exact_ms,
-                      "kernel": "direct integer correlation, CUDA cores, one launch per pair"},
+                      "kernel": "direct integer correlation, dp4a (4 byte MACs per instruction), one launch "
+                                "per pair", "roofline": exact_roofline(exact_macs, exact_ms, ceil)},
         "speedup_vs_exact": value / (info["offsets"] / (exact_ms * 1e-3) / 1e9),
         "candidates": ncand, "matches": nmatch, "status": status, "prep_s": prep_s,
         "roofline": {"bound": "smem", "kernel": "batch_match_kernel", "achieved": bytes_launch / (match_ms * 1e-3) / 1e9,
@@ -765,11 +784,15 @@ def run_gpu_batch(args, world, rank, local, pg):
                      "frac": bytes_launch / (match_ms * 1e-3) / 1e9 / smem_peak, "traffic": None,
                      "bytes_per_launch": bytes_launch, "ms_per_launch": match_ms,
                      "peak_source": "measured: shared-memory read probe (all SMs), this run",
-                     "hbm_peak_gbs": peaks.get("hbm_gbs")},
+                     "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                     "imad_wide_ceiling": {"achieved": info["corner_offsets"] / (match_ms * 1e-3),
+                                           "peak": ceil["imad_wide_per_s"], "unit": "corner-ops/s",
+                                           "frac": info["corner_offsets"] / (match_ms * 1e-3)
+                                           / ceil["imad_wide_per_s"]}},
         "e2e": {"value": offsets / (e2e_ms_step * 1e-3) / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": sum(f.size for f in srcs), "d2h_bytes_per_step": d2h / e2e_steps,
                 "ms_per_step": e2e_ms_step},
-        "gpu_launches": args.steps * (3 * len(srcs) + 3),
+        "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS * len(srcs) + 3),
         "clocks": clk, "wall_s_timed": wall,
     }
     if cpu is not None:

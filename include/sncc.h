@@ -469,6 +469,20 @@ int sncc_get_plan_info(const sncc_segments* seg, sncc_plan_info* out);
  * kernel; not part of the matching path. */
 int sncc_probe_smem_read(int32_t* d_sink, int ctas, int iters, sncc_stream_t stream);
 
+/* Instruction-rate probe: `ctas` CTAs of 256 threads each issue `iters`
+ * rounds of 64 instructions of one kind, in eight independent chains, and
+ * store one checksum word per thread into d_sink (ctas * 256 int32, device).
+ * kind SNCC_PROBE_DP4A: four-way unsigned byte dot product with 32-bit
+ * accumulate (the exact comparator's multiply-add, 4 pixel MACs each);
+ * kind SNCC_PROBE_IMAD_WIDE: signed 32 x 32 -> 64-bit multiply-add (the
+ * segment-sum kernel's per-corner operation).  Instructions issued =
+ * ctas*256*iters*64.  SNCC_ERR_ARG for another kind or a non-positive
+ * size.  Used by the benchmark to measure ALU ceilings; not part of the
+ * matching path. */
+#define SNCC_PROBE_DP4A 0
+#define SNCC_PROBE_IMAD_WIDE 1
+int sncc_probe_alu(int kind, int32_t* d_sink, int ctas, int iters, sncc_stream_t stream);
+
 /* Library version string. */
 const char* sncc_version(void);
 

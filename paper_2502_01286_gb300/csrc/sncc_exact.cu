@@ -4,11 +4,16 @@
 //
 // A CTA of 8 warps computes a 32 x 8R tile of offsets.  The template is cut
 // into 64 x 64 blocks; for each block the CTA stages the template block and
-// the source region its offsets touch in shared memory (bytes), and every
-// thread accumulates sum f*t for its R offsets in exact 32-bit partials
-// (a block adds at most 4096 * 65025 < 2^32), flushed into 64-bit totals.
-// The window sums come from the sum tables; the final ratio is formed in
-// double from exact integers.
+// the source region its offsets touch in shared memory.  The region is kept
+// as four byte-shifted copies (copy k, word j = bytes 4j+k .. 4j+k+3 of a
+// row), so that the four source bytes a lane multiplies with four template
+// bytes are always one aligned 32-bit word: lane l reads copy (l & 3), word
+// (l >> 2) + x/4, and __dp4a multiplies and adds the four byte pairs.  The
+// copies are spaced 8 words (mod 32) apart, so the 32 lanes hit 32 banks.
+// A block adds at most 4096 * 65025 < 2^32 per offset, so the per-block
+// sums are exact in uint32 and are flushed into 64-bit totals.  The window
+// sums come from the sum tables; the final ratio is formed in double from
+// exact integers.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -19,8 +24,10 @@
 namespace sncc {
 namespace {
 
-constexpr int kTB = 64;                    // template block edge
-constexpr int kFSP = TILE_U + kTB + 4;     // source region pitch (bytes)
+constexpr int kTB = 64;            // template block edge
+constexpr int kRB = TILE_U + kTB + 4;  // source region row, bytes (100)
+constexpr int kRW = kRB / 4;           // source region row, words (25)
+constexpr int kTR = kTB + 8;           // staged template rows (8 >= R zero rows)
 
 template <bool S64>
 __device__ __forceinline__ long long sat_read(const void* s, int pitch, int X, int Y) {
@@ -30,52 +37,86 @@ __device__ __forceinline__ long long sat_read(const void* s, int pitch, int X, i
         return static_cast<const int*>(s)[(size_t)Y * pitch + X];
 }
 
+// words of one byte-shifted copy of a region of FR rows, padded so that the
+// four copies start 8 banks apart
+__host__ __device__ constexpr int copy_words(int FR) { return ((FR * kRW + 24) / 32) * 32 + 8; }
+
+template <int R>
+constexpr size_t exact_smem_bytes() {
+    return (size_t)4 * copy_words(WARPS * R + kTB) * 4 + (size_t)kTR * kTB;
+}
+
 template <int R, bool S64>
 __global__ void __launch_bounds__(256)
     exact_kernel(const uint8_t* __restrict__ f, int M, int N, int f_stride, const uint8_t* __restrict__ t, int W,
                  int H, int t_stride, long long T, long long T2, const void* __restrict__ s,
                  const int64_t* __restrict__ s2, int pitch, float* __restrict__ rho, int rho_pitch) {
     constexpr int FR = WARPS * R + kTB;  // region rows (one spare)
-    __shared__ __align__(16) uint8_t fs[FR * kFSP];
-    __shared__ __align__(16) uint8_t ts[kTB * kTB];
+    constexpr int CW = copy_words(FR);
+    extern __shared__ __align__(16) uint32_t smx[];
+    uint32_t* cp = smx;                                            // 4 copies x CW words
+    uint8_t* ts = reinterpret_cast<uint8_t*>(smx + 4 * CW);        // kTR x kTB template bytes
+    uint8_t* fb = reinterpret_cast<uint8_t*>(cp);                  // copy 0 viewed as bytes
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int u0 = blockIdx.x * TILE_U, v0 = blockIdx.y * (WARPS * R);
     const int U = M - W + 1, V = N - H + 1;
     unsigned long long acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0ull;
+    // lane l's words: copy (l & 3), word (l >> 2) + x/4 of its rows
+    const uint32_t* lbase = cp + (lane & 3) * CW + (warp * R) * kRW + (lane >> 2);
 
     for (int by = 0; by < H; by += kTB) {
         const int bh = min(kTB, H - by);
         for (int bx = 0; bx < W; bx += kTB) {
             const int bw = min(kTB, W - bx);
-            const int bw4 = (bw + 3) & ~3;
+            const int bq = (bw + 3) >> 2;
             __syncthreads();
-            // template block, zero-padded to a multiple of 4 columns
-            for (int i = tid; i < kTB * kTB; i += 256) {
+            // template block, zero-padded to a multiple of 4 columns and with
+            // zero rows below it, read by the register window's last rows
+            for (int i = tid; i < kTR * kTB; i += 256) {
                 const int y = i / kTB, x = i - y * kTB;
                 ts[i] = (y < bh && x < bw) ? t[(size_t)(by + y) * t_stride + bx + x] : (uint8_t)0;
             }
-            // source region: rows v0+by .. , columns u0+bx ..
-            for (int i = tid; i < FR * kFSP; i += 256) {
-                const int Y = i / kFSP, X = i - Y * kFSP;
+            // copy 0: the source region as bytes (rows of kRB), zero outside the image
+            for (int i = tid; i < FR * kRB; i += 256) {
+                const int Y = i / kRB, X = i - Y * kRB;
                 const int gy = v0 + by + Y, gx = u0 + bx + X;
-                fs[i] = (gy < N && gx < M) ? f[(size_t)gy * f_stride + gx] : (uint8_t)0;
+                fb[i] = (gy < N && gx < M) ? f[(size_t)gy * f_stride + gx] : (uint8_t)0;
             }
             __syncthreads();
+            // copies 1..3: word j of copy k = bytes 4j+k .. 4j+k+3 of the row
+            for (int i = tid; i < FR * kRW; i += 256) {
+                const int Y = i / kRW, j = i - Y * kRW;
+                const uint32_t w0 = cp[Y * kRW + j];
+                const uint32_t w1 = (j + 1 < kRW) ? cp[Y * kRW + j + 1] : 0u;
+                cp[1 * CW + i] = __byte_perm(w0, w1, 0x4321);
+                cp[2 * CW + i] = __byte_perm(w0, w1, 0x5432);
+                cp[3 * CW + i] = __byte_perm(w0, w1, 0x6543);
+            }
+            __syncthreads();
+            // Column q of words outer, source rows j inner: the word a lane
+            // reads at source row j serves all R offset rows of the warp (with
+            // template row j - r for offset row r), and the last R template
+            // words of column q stay in registers, so each j costs two shared
+            // loads (source word, broadcast template word) and R dp4a.
             unsigned part[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) part[r] = 0u;
-            for (int y = 0; y < bh; ++y) {
-                const uint8_t* frow = fs + (warp * R + y) * kFSP + lane;
-                const uint32_t* trow = reinterpret_cast<const uint32_t*>(ts + y * kTB);
-                for (int x = 0; x < bw4; x += 4) {
-                    const uint32_t tw = trow[x >> 2];
+            const uint32_t* tw = reinterpret_cast<const uint32_t*>(ts);
+            for (int q = 0; q < bq; ++q) {
+                uint32_t win[R];  // win[j % R] = template word (row j, column q)
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const unsigned tv = (tw >> (8 * k)) & 0xffu;
+                for (int r = 0; r < R; ++r) win[r] = 0u;
+                const uint32_t* lcol = lbase + q;
+                const uint32_t* tcol = tw + q;
+                for (int jb = 0; jb < bh + R - 1; jb += R) {
 #pragma unroll
-                        for (int r = 0; r < R; ++r) part[r] += tv * (unsigned)frow[r * kFSP + x + k];
+                    for (int jj = 0; jj < R; ++jj) {
+                        const uint32_t w = lcol[(jb + jj) * kRW];
+                        win[jj] = tcol[(jb + jj) * (kTB / 4)];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) part[r] = __dp4a(w, win[(jj - r + R) % R], part[r]);
                     }
                 }
             }
@@ -106,12 +147,17 @@ template <int R>
 cudaError_t launch_exact(bool s64, dim3 grid, cudaStream_t st, const uint8_t* f, int M, int N, int f_stride,
                          const uint8_t* t, int W, int H, int t_stride, long long T, long long T2, const void* s,
                          const int64_t* s2, int pitch, float* rho, int rho_pitch) {
+    constexpr size_t sm = exact_smem_bytes<R>();
+    cudaError_t attr = cudaFuncSetAttribute(exact_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (attr == cudaSuccess)
+        attr = cudaFuncSetAttribute(exact_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (attr != cudaSuccess) return attr;
     if (s64)
-        exact_kernel<R, true><<<grid, 256, 0, st>>>(f, M, N, f_stride, t, W, H, t_stride, T, T2, s, s2, pitch, rho,
-                                                     rho_pitch);
+        exact_kernel<R, true><<<grid, 256, sm, st>>>(f, M, N, f_stride, t, W, H, t_stride, T, T2, s, s2, pitch, rho,
+                                                      rho_pitch);
     else
-        exact_kernel<R, false><<<grid, 256, 0, st>>>(f, M, N, f_stride, t, W, H, t_stride, T, T2, s, s2, pitch,
-                                                      rho, rho_pitch);
+        exact_kernel<R, false><<<grid, 256, sm, st>>>(f, M, N, f_stride, t, W, H, t_stride, T, T2, s, s2, pitch,
+                                                       rho, rho_pitch);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,12 @@
-// sncc_probe.cu - shared-memory read-bandwidth probe.  The segment-sum kernel
-// reads one 32-bit shared-memory word per (offset, corner) with lane-
-// consecutive addresses; this kernel performs the same access pattern with
-// nothing else in the loop, so its rate is the on-chip ceiling the segment-sum
-// kernel is compared against.
+// sncc_probe.cu - on-chip ceilings the kernels are compared against.
+//
+// Shared-memory read bandwidth: the segment-sum kernel reads one 32-bit
+// shared-memory word per (offset, corner) with lane-consecutive addresses;
+// probe_smem_read performs the same access pattern with nothing else in the
+// loop.  Instruction rates: the segment-sum kernel adds one 32 x 32 -> 64-bit
+// integer multiply-add per (offset, corner), and the exact comparator one
+// four-way byte dot product (dp4a) per four template pixels; probe_alu issues
+// only that instruction, in eight independent chains per thread.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -34,11 +38,73 @@ __global__ void __launch_bounds__(256) probe_smem_read(int32_t* __restrict__ sin
     sink[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1 ^ a2 ^ a3;
 }
 
+constexpr int kChains = 8;
+
+// kind 0: dp4a, 64 per thread and iteration
+__global__ void __launch_bounds__(256) probe_dp4a(int32_t* __restrict__ sink, int iters, unsigned b) {
+    unsigned a[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) a[i] = threadIdx.x * 7u + i;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int i = 0; i < kChains; ++i) a[i] = __dp4a(a[i], b + q, a[i]);
+    }
+    unsigned x = 0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) x ^= a[i];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = (int32_t)x;
+}
+
+__device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
+    long long d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+// kind 1: signed 32 x 32 -> 64-bit multiply-add into a 64-bit accumulator,
+// 64 per thread and iteration; the multiplicands are the accumulators' low
+// and high words at the start of the iteration, so nothing can be hoisted
+__global__ void __launch_bounds__(256) probe_imad_wide(int32_t* __restrict__ sink, int iters) {
+    long long acc[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i)
+        acc[i] = (long long)((threadIdx.x * 7 + i + 1) * 0x10001u) << 16 | (threadIdx.x * 13 + i);
+    for (int it = 0; it < iters; ++it) {
+        int x[kChains], y[kChains];
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) {
+            x[i] = (int)acc[i];
+            y[i] = (int)(acc[i] >> 32);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int i = 0; i < kChains; ++i)
+                acc[i] = mad_wide(x[(i + q) & (kChains - 1)], y[(i + 2 * q + 1) & (kChains - 1)], acc[i]);
+    }
+    long long x = 0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) x ^= acc[i];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = (int32_t)(x ^ (x >> 32));
+}
+
 }  // namespace
 }  // namespace sncc
 
 extern "C" int sncc_probe_smem_read(int32_t* d_sink, int ctas, int iters, sncc_stream_t stream) {
     if (!d_sink || ctas <= 0 || iters <= 0) return SNCC_ERR_ARG;
     sncc::probe_smem_read<<<ctas, 256, 0, (cudaStream_t)stream>>>(d_sink, iters);
+    return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+}
+
+extern "C" int sncc_probe_alu(int kind, int32_t* d_sink, int ctas, int iters, sncc_stream_t stream) {
+    if (!d_sink || ctas <= 0 || iters <= 0 || (kind != SNCC_PROBE_DP4A && kind != SNCC_PROBE_IMAD_WIDE))
+        return SNCC_ERR_ARG;
+    if (kind == SNCC_PROBE_DP4A)
+        sncc::probe_dp4a<<<ctas, 256, 0, (cudaStream_t)stream>>>(d_sink, iters, 0x01020304u);
+    else
+        sncc::probe_imad_wide<<<ctas, 256, 0, (cudaStream_t)stream>>>(d_sink, iters);
     return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }

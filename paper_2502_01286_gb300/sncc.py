@@ -33,7 +33,7 @@ STATUS_CAND_OVERFLOW, STATUS_MATCH_OVERFLOW, STATUS_WAIT_TIMEOUT, STATUS_SORT_OV
 EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_sat_pitch",
             "sncc_integral_workspace_bytes", "sncc_integral", "sncc_plan_bytes", "sncc_plan_upload", "sncc_match",
             "sncc_refine_workspace_bytes", "sncc_refine", "sncc_exact_map", "sncc_get_plan_info",
-            "sncc_probe_smem_read", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_batch_create",
+            "sncc_probe_smem_read", "sncc_probe_alu", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_batch_create",
             "sncc_batch_destroy", "sncc_batch_device_bytes", "sncc_batch_upload", "sncc_batch_set_variant",
             "sncc_batch_get_info", "sncc_batch_match", "sncc_batch_autotune", "sncc_batch_refine_workspace_bytes",
             "sncc_batch_refine", "sncc_diff_workspace_bytes", "sncc_diff_forward", "sncc_diff_backward"]
@@ -120,6 +120,7 @@ _lib.sncc_diff_backward.argtypes = [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c
                                     _vp, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp]
 _lib.sncc_get_plan_info.argtypes = [C.POINTER(_Segments), C.POINTER(PlanInfo)]
 _lib.sncc_probe_smem_read.argtypes = [_vp, C.c_int, C.c_int, _vp]
+_lib.sncc_probe_alu.argtypes = [C.c_int, _vp, C.c_int, C.c_int, _vp]
 _lib.sncc_exact_map.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64,
                                 C.c_int64, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp]
 
@@ -254,6 +255,11 @@ def integral_workspace(M: int, N: int, device="cuda"):
     return torch.empty(int(_lib.sncc_integral_workspace_bytes(M, N)), dtype=torch.uint8, device=device)
 
 
+# kernels one sncc_integral call launches: column sums of bands, band scan,
+# row carries, tile emit
+INTEGRAL_KERNELS = 4
+
+
 def integral(f, tables: Optional[Tables] = None, s_bits: Optional[int] = None, workspace=None, stream=None) -> Tables:
     """sncc_integral on a (N, M) uint8 CUDA tensor (row stride = its stride)."""
     torch = _torch()
@@ -385,6 +391,16 @@ def probe_smem_read(sink, ctas: int, iters: int, stream=None) -> int:
     """Launches the shared-memory read probe; returns the bytes it reads."""
     _check(_lib.sncc_probe_smem_read(sink.data_ptr(), ctas, iters, _stream(stream)), "sncc_probe_smem_read")
     return ctas * 256 * iters * 32 * 4
+
+
+PROBE_DP4A, PROBE_IMAD_WIDE = 0, 1
+
+
+def probe_alu(kind: int, sink, ctas: int, iters: int, stream=None) -> int:
+    """Launches the instruction-rate probe; returns the instructions it issues
+    (lane operations)."""
+    _check(_lib.sncc_probe_alu(kind, sink.data_ptr(), ctas, iters, _stream(stream)), "sncc_probe_alu")
+    return ctas * 256 * iters * 64
 
 
 # ---------------------------------------------------------------------------

@@ -138,6 +138,9 @@ def test_host_argument_errors(sncc):
     assert lib.sncc_exact_map(C.c_void_p(256), 64, 64, 64, C.c_void_p(256), 8, 8, 8, 64 * 7, 64 * 49,
                               C.c_void_p(256), 32, C.c_void_p(256), 96, C.c_void_p(256), 57,
                               None) == sncc.ERR_UNIFORM
+    assert lib.sncc_probe_alu(2, C.c_void_p(256), 1, 1, None) == sncc.ERR_ARG
+    assert lib.sncc_probe_alu(sncc.PROBE_DP4A, C.c_void_p(256), 0, 1, None) == sncc.ERR_ARG
+    assert lib.sncc_probe_alu(sncc.PROBE_IMAD_WIDE, None, 1, 1, None) == sncc.ERR_ARG
     assert lib.sncc_integral_workspace_bytes(0, 5) == 0
 
 

@@ -302,6 +302,18 @@ def test_exact_map_vs_oracle(sncc, M, N, W, H):
     assert np.abs(rho.cpu().numpy() - ref).max() <= TOL
 
 
+def test_exact_map_int64_tables_multi_block(sncc):
+    # a 130 x 129 template spans 3 x 3 template blocks with ragged edges; 64-bit tables
+    c = synth.case_plain(M=300, N=260, W=130, H=129, seed=31)
+    fd = dev(c.f)
+    tb = sncc.integral(fd, s_bits=64)
+    seg = sncc.build_segments(c.t, 1.0)
+    rho = sncc.exact_map(fd, dev(c.t), seg.T, seg.T2, tb)
+    torch.cuda.synchronize()
+    ref = O.ncc_exact_map(c.f, c.t)
+    assert np.abs(rho.cpu().numpy() - ref).max() <= TOL
+
+
 def test_exact_map_hd_sampled(sncc):
     c = synth.case_hd()
     fd = dev(c.f)
