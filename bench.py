@@ -368,6 +368,41 @@ def measure_ceilings(sncc, torch, stream, dev):
             "imad_wide_per_s": best(lambda it: sncc.probe_alu(sncc.PROBE_IMAD_WIDE, sink, 152 * 8, it // 4))}
 
 
+IMAD_WIDE_PER_CLK_SM = 32  # 16-lane integer multiplier per SM sub-partition, two passes per 64-bit product
+SM_COUNT, SM_MAX_MHZ = 152, 2070
+
+
+def match_tile_rows(U, V):
+    """Tile height the library picks for one match launch (largest R in
+    {8, 4} giving at least two CTAs per SM, else 2)."""
+    tu = -(-U // 32)
+    for R in (8, 4):
+        if tu * -(-V // (8 * R)) >= 2 * SM_COUNT:
+            return R
+    return 2
+
+
+def segsum_roofline(kernel, corner_ops, ms, ceil, traffic=None, smem_words=None, **extra):
+    """The segment-sum kernel against its ALU ceiling: one 32x32->64-bit
+    multiply-add per (offset, corner), peak from unit counts and the maximum
+    SM clock; the live probe and the shared-memory reads are reported beside it."""
+    achieved = corner_ops / (ms * 1e-3) / 1e12
+    peak = SM_COUNT * IMAD_WIDE_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    out = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "Tops/s",
+           "frac": achieved / peak, "traffic": traffic, "ops_per_launch": corner_ops, "ms_per_launch": ms,
+           "peak_source": "152 SMs x 32 IMAD.WIDE lane-ops/clk/SM x 2070 MHz (nominal)",
+           "imad_wide_probe": {"peak": ceil["imad_wide_per_s"] / 1e12, "unit": "Tops/s",
+                               "frac": achieved * 1e12 / ceil["imad_wide_per_s"],
+                               "source": "measured: IMAD.WIDE instruction probe (all SMs), this run"}}
+    if smem_words is not None:
+        gbs = smem_words * 4 / (ms * 1e-3) / 1e9
+        out["smem"] = {"words_per_launch": smem_words, "achieved": gbs, "peak": ceil["smem_gbs"], "unit": "GB/s",
+                       "frac": gbs / ceil["smem_gbs"],
+                       "source": "measured: shared-memory read probe (all SMs), this run"}
+    out.update(extra)
+    return out
+
+
 def exact_roofline(macs, ms, ceil):
     """The exact comparator against the dp4a ceiling (4 pixel MACs each)."""
     achieved = macs / (ms * 1e-3) / 1e12
@@ -541,14 +576,16 @@ def run_gpu(args, world, rank, local, pg):
 
     # --- on-chip ceilings of the segment-sum kernel and the comparator ---
     ceil = measure_ceilings(sncc, torch, stream, dev)
-    smem_peak = ceil["smem_gbs"]
 
     # dominant kernel: the segment-sum launch with the most corners
     infos = [s.plan_info() for s in segs]
     dom = max(range(len(SIGMAS)), key=lambda i: infos[i]["corners"])
     dom_ms = statistics.mean(per_sigma_ms[dom])
-    dom_bytes = U * V * infos[dom]["corners"] * 4  # one 32-bit shared load per (offset, corner)
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    dom_ops = U * V * infos[dom]["corners"]  # one multiply-add per (offset, corner)
+    Rt = match_tile_rows(U, V)
+    pi = infos[dom]
+    # table words a lane reads per R offsets: R + L - 1 per run of L corners
+    dom_words = U * V * sum(pi["runs%d" % L] * (Rt + L - 1) for L in (8, 4, 2, 1)) / Rt
 
     value = sum_over_ranks(pg, offsets_per_step) / (ms_per_step * 1e-3) / 1e9
     e2e_value = sum_over_ranks(pg, offsets_per_step) / (e2e_ms_step * 1e-3) / 1e9
@@ -594,15 +631,10 @@ def run_gpu(args, world, rank, local, pg):
                        "frac_of_hbm": (sat_bytes / (sat_med * 1e-3) / 1e9) / peaks_hbm if peaks_hbm else None,
                        "peak": "MEASURED_PEAKS hbm_gbs"},
         "paper_two_stage": two,
-        "roofline": {"bound": "smem", "kernel": "match_kernel", "sigma_max": SIGMAS[dom], "achieved": achieved,
-                     "peak": smem_peak, "unit": "GB/s", "frac": achieved / smem_peak,
-                     "traffic": recorded_traffic(args.workload), "bytes_per_launch": dom_bytes,
-                     "ms_per_launch": dom_ms,
-                     "peak_source": "measured: shared-memory read probe (all SMs), this run",
-                     "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                     "imad_wide_ceiling": {"achieved": dom_bytes / 4 / (dom_ms * 1e-3),
-                                           "peak": ceil["imad_wide_per_s"], "unit": "corner-ops/s",
-                                           "frac": dom_bytes / 4 / (dom_ms * 1e-3) / ceil["imad_wide_per_s"]}},
+        "roofline": segsum_roofline("match_kernel", dom_ops, dom_ms, ceil, traffic=recorded_traffic(args.workload),
+                                    smem_words=dom_words, sigma_max=SIGMAS[dom], tile_rows=Rt,
+                                    runs={L: pi["runs%d" % L] for L in (8, 4, 2, 1)},
+                                    hbm_peak_gbs=peaks.get("hbm_gbs")),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h_total / e2e_steps, "ms_per_step": e2e_ms_step},
         "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS + 3 * len(SIGMAS)),
@@ -706,9 +738,7 @@ def run_gpu_batch(args, world, rank, local, pg):
         torch.cuda.synchronize()
         mk.append(a.elapsed_time(e))
     match_ms = statistics.median(mk)
-    bytes_launch = info["corner_offsets"] * 4.0
     ceil = measure_ceilings(sncc, torch, stream, dev)
-    smem_peak = ceil["smem_gbs"]
 
     # end to end: sources from pinned host memory, graph replay, matches back
     host = [torch.as_tensor(f).pin_memory() for f in srcs]
@@ -779,16 +809,8 @@ def run_gpu_batch(args, world, rank, local, pg):
                                 "per pair", "roofline": exact_roofline(exact_macs, exact_ms, ceil)},
         "speedup_vs_exact": value / (info["offsets"] / (exact_ms * 1e-3) / 1e9),
         "candidates": ncand, "matches": nmatch, "status": status, "prep_s": prep_s,
-        "roofline": {"bound": "smem", "kernel": "batch_match_kernel", "achieved": bytes_launch / (match_ms * 1e-3) / 1e9,
-                     "peak": smem_peak, "unit": "GB/s",
-                     "frac": bytes_launch / (match_ms * 1e-3) / 1e9 / smem_peak, "traffic": None,
-                     "bytes_per_launch": bytes_launch, "ms_per_launch": match_ms,
-                     "peak_source": "measured: shared-memory read probe (all SMs), this run",
-                     "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                     "imad_wide_ceiling": {"achieved": info["corner_offsets"] / (match_ms * 1e-3),
-                                           "peak": ceil["imad_wide_per_s"], "unit": "corner-ops/s",
-                                           "frac": info["corner_offsets"] / (match_ms * 1e-3)
-                                           / ceil["imad_wide_per_s"]}},
+        "roofline": segsum_roofline("batch_match_kernel", info["corner_offsets"], match_ms, ceil,
+                                    hbm_peak_gbs=peaks.get("hbm_gbs")),
         "e2e": {"value": offsets / (e2e_ms_step * 1e-3) / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": sum(f.size for f in srcs), "d2h_bytes_per_step": d2h / e2e_steps,
                 "ms_per_step": e2e_ms_step},

@@ -456,6 +456,10 @@ typedef struct {
     int32_t corners;      /* distinct corner points with a nonzero weight, summed over blocks */
     int32_t max_corners;  /* largest corner count of one block */
     int64_t Q0;           /* sum of the weights over all pixels, sum_i W_i H_i q_i */
+    int32_t runs8;        /* the corners regrouped into vertical runs (consecutive rows of */
+    int32_t runs4;        /* one column, all weights nonzero) of 8, 4, 2 and 1 corners: */
+    int32_t runs2;        /* 8 runs8 + 4 runs4 + 2 runs2 + runs1 = corners.  The segment-sum */
+    int32_t runs1;        /* kernels read R + L - 1 table words per run of L for R rows. */
 } sncc_plan_info;
 
 /* Fills *out for seg; SNCC_ERR_UNIFORM when seg has no plan (Ek = 0). */

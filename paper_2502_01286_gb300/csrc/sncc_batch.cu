@@ -53,7 +53,8 @@ struct BatchArgs {
     const int4* pairs;  // {source, template, U, V}
     const TmplDesc* tmpl;
     const int4* blocks;
-    const int2* corners;
+    const int4* runblk;  // two per block
+    const int4* runs;
     const int2* items;  // {pair, (tile row << 16) | tile column}
     int n_items;
     int* counter;
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(WARPS * 32) batch_match_kernel(const __grid_co
             stage_region_regs<S64, WP>(s, a.pitch, a.M, a.N, work, u0 + blk.x, v0 + blk.y, WARPS * R + bh + 1, lane,
                                        warp, TILE_U + bw + 1);
             __syncthreads();
-            corner_sum<R, WP>(acc, wbase, reinterpret_cast<const int4*>(a.corners + blk.z), blk.w);
+            const int gb = td.blk_first + b;
+            run_sum<R, WP>(acc, wbase, a.runs, __ldg(a.runblk + 2 * gb), __ldg(a.runblk + 2 * gb + 1));
             __syncthreads();
         }
         const int u = u0 + lane;
@@ -249,7 +251,8 @@ struct sncc_batch_s {
     int nt = 0, ns = 0, M = 0, N = 0;
     std::vector<sncc::TmplDesc> tmpl;
     std::vector<int32_t> corner_counts;  // nonzero corners per template
-    size_t off_pairs = 0, off_tmpl = 0, off_blocks = 0, off_corners = 0, off_pix = 0, off_items[3] = {0, 0, 0};
+    size_t off_pairs = 0, off_tmpl = 0, off_blocks = 0, off_runblk = 0, off_runs = 0, off_pix = 0,
+           off_items[3] = {0, 0, 0};
     int n_items[3] = {0, 0, 0};
     std::vector<unsigned char> image;
     int variant = 8;
@@ -310,7 +313,7 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
         b->ns = n_sources;
         b->M = M;
         b->N = N;
-        std::vector<int32_t> blocks, corners;
+        std::vector<int32_t> blocks, runblk, runs;
         std::vector<unsigned char> pix;
         for (int t = 0; t < n_templates; ++t) {
             const sncc_segments* sg = segs[t];
@@ -348,16 +351,17 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
                 pix.insert(pix.end(), templates[t] + (size_t)y * t_strides[t],
                            templates[t] + (size_t)y * t_strides[t] + sg->W);
             while (pix.size() % 16) pix.push_back(0);
-            const int corner_base = (int)(corners.size() / 2);
+            const int run_base = (int)(runs.size() / 4);  // int4 units
             const int32_t* img_blocks = p.image.data();
-            const int32_t* img_corners = p.image.data() + p.corners_offset / 4;
+            const int32_t* img_runblk = p.image.data() + p.runblk_offset / 4;
+            const int32_t* img_runs = p.image.data() + p.runs_offset / 4;
+            const size_t run_words = p.image.size() - 4 - p.runs_offset / 4;
             for (int k = 0; k < p.nblk; ++k) {
-                blocks.push_back(img_blocks[4 * k + 0]);
-                blocks.push_back(img_blocks[4 * k + 1]);
-                blocks.push_back(img_blocks[4 * k + 2] + corner_base);
-                blocks.push_back(img_blocks[4 * k + 3]);
+                for (int j = 0; j < 4; ++j) blocks.push_back(img_blocks[4 * k + j]);
+                for (int j = 0; j < 8; ++j)  // firsts (even words) move by run_base
+                    runblk.push_back(img_runblk[8 * k + j] + ((j % 2 == 0) ? run_base : 0));
             }
-            corners.insert(corners.end(), img_corners, img_corners + 2 * p.total_corners);
+            runs.insert(runs.end(), img_runs, img_runs + run_words);
             b->tmpl.push_back(d);
             b->corner_counts.push_back(p.nonzero_corners);
         }
@@ -403,8 +407,10 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
         off = align16(off + b->tmpl.size() * sizeof(TmplDesc));
         b->off_blocks = off;
         off = align16(off + blocks.size() * 4);
-        b->off_corners = off;
-        off = align16(off + corners.size() * 4);
+        b->off_runblk = off;
+        off = align16(off + runblk.size() * 4);
+        b->off_runs = off;
+        off = align16(off + runs.size() * 4);
         b->off_pix = off;
         off = align16(off + pix.size());
         for (int vi = 0; vi < 3; ++vi) {
@@ -415,7 +421,8 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
         std::memcpy(b->image.data() + b->off_pairs, pairs.data(), pairs.size() * 4);
         std::memcpy(b->image.data() + b->off_tmpl, b->tmpl.data(), b->tmpl.size() * sizeof(TmplDesc));
         std::memcpy(b->image.data() + b->off_blocks, blocks.data(), blocks.size() * 4);
-        std::memcpy(b->image.data() + b->off_corners, corners.data(), corners.size() * 4);
+        if (!runblk.empty()) std::memcpy(b->image.data() + b->off_runblk, runblk.data(), runblk.size() * 4);
+        if (!runs.empty()) std::memcpy(b->image.data() + b->off_runs, runs.data(), runs.size() * 4);
         std::memcpy(b->image.data() + b->off_pix, pix.data(), pix.size());
         for (int vi = 0; vi < 3; ++vi)
             std::memcpy(b->image.data() + b->off_items[vi], items[vi].data(), items[vi].size() * 4);
@@ -473,7 +480,8 @@ extern "C" int sncc_batch_match(const sncc_batch* b, const void* d_buf, const vo
     a.pairs = reinterpret_cast<const int4*>(base + b->off_pairs);
     a.tmpl = reinterpret_cast<const TmplDesc*>(base + b->off_tmpl);
     a.blocks = reinterpret_cast<const int4*>(base + b->off_blocks);
-    a.corners = reinterpret_cast<const int2*>(base + b->off_corners);
+    a.runblk = reinterpret_cast<const int4*>(base + b->off_runblk);
+    a.runs = reinterpret_cast<const int4*>(base + b->off_runs);
     a.items = reinterpret_cast<const int2*>(base + b->off_items[vi]);
     a.n_items = b->n_items[vi];
     a.counter = d_counter;

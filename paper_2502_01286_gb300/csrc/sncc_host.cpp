@@ -196,6 +196,8 @@ int build_plan(const sncc_segments* s, Plan& p, bool uniform_64) {
     // Corner lists, block by block.
     std::vector<int32_t> blocks;
     std::vector<int32_t> corners;
+    std::vector<int32_t> runblk;
+    std::vector<int32_t> runs;  // int4 units, 4 words each
     int nonzero = 0;
     p.max_corners = 0;
     for (int by_i = 0; by_i < p.nby; ++by_i) {
@@ -206,13 +208,15 @@ int build_plan(const sncc_segments* s, Plan& p, bool uniform_64) {
                 if (X < 0 || Y < 0 || X >= bw || Y >= bh) return 0;
                 return qimg[(size_t)(by + Y) * W + (bx + X)];
             };
+            std::vector<int32_t> G((size_t)(bw + 1) * (bh + 1));  // G[X * (bh + 1) + Y], column-major
             const int first = (int)(corners.size() / 2);
             for (int Y = 0; Y <= bh; ++Y)
                 for (int X = 0; X <= bw; ++X) {
-                    const int64_t G = q(X - 1, Y - 1) - q(X, Y - 1) - q(X - 1, Y) + q(X, Y);
-                    if (G != 0) {
+                    const int64_t g = q(X - 1, Y - 1) - q(X, Y - 1) - q(X - 1, Y) + q(X, Y);
+                    G[(size_t)X * (bh + 1) + Y] = (int32_t)g;
+                    if (g != 0) {
                         corners.push_back(Y * p.WP + X);
-                        corners.push_back((int32_t)G);
+                        corners.push_back((int32_t)g);
                         ++nonzero;
                     }
                 }
@@ -229,6 +233,45 @@ int build_plan(const sncc_segments* s, Plan& p, bool uniform_64) {
             blocks.push_back(first);
             blocks.push_back(cnt);
             p.max_corners = std::max(p.max_corners, cnt);
+
+            // Vertical runs: walking each column downwards, the first
+            // uncovered corner starts the longest run of 8, 4 or 2 whose rows
+            // all hold corners (and stay inside the block's corner grid);
+            // otherwise it is a single corner.
+            std::vector<int32_t> cls[4];
+            for (int X = 0; X <= bw; ++X) {
+                const int32_t* col = &G[(size_t)X * (bh + 1)];
+                for (int Y = 0; Y <= bh;) {
+                    if (col[Y] == 0) {
+                        ++Y;
+                        continue;
+                    }
+                    int k = 3;
+                    for (int c = 0; c < 3; ++c) {
+                        const int L = RUN_LEN[c];
+                        if (Y + L - 1 > bh) continue;
+                        bool full = true;
+                        for (int i = 0; i < L && full; ++i) full = col[Y + i] != 0;
+                        if (full) {
+                            k = c;
+                            break;
+                        }
+                    }
+                    const int L = RUN_LEN[k];
+                    cls[k].push_back(Y * p.WP + X);
+                    for (int i = 0; i < L; ++i) cls[k].push_back(col[Y + i]);
+                    if (k < 3)  // pad the record to its int4 units
+                        while (cls[k].size() % (4 * RUN_INT4[k]) != 0) cls[k].push_back(0);
+                    ++p.runs[k];
+                    Y += L;
+                }
+            }
+            while (cls[3].size() % 8 != 0) cls[3].push_back(0);  // whole groups of 4 single corners
+            for (int k = 0; k < 4; ++k) {
+                runblk.push_back((int32_t)(runs.size() / 4));
+                runblk.push_back(k < 3 ? (int32_t)(cls[k].size() / (4 * RUN_INT4[k])) : (int32_t)(cls[3].size() / 2));
+                runs.insert(runs.end(), cls[k].begin(), cls[k].end());
+            }
         }
     }
     p.nblk = (int)(blocks.size() / 4);
@@ -236,10 +279,14 @@ int build_plan(const sncc_segments* s, Plan& p, bool uniform_64) {
     p.nonzero_corners = nonzero;
     p.blocks_offset = 0;
     p.corners_offset = (size_t)p.nblk * 16;
-    p.image.resize(blocks.size() + corners.size() + 4, 0);
-    std::memcpy(p.image.data(), blocks.data(), blocks.size() * sizeof(int32_t));
-    if (!corners.empty())
-        std::memcpy(p.image.data() + blocks.size(), corners.data(), corners.size() * sizeof(int32_t));
+    p.runblk_offset = p.corners_offset + corners.size() * 4;
+    p.runs_offset = p.runblk_offset + runblk.size() * 4;
+    p.image.assign(p.runs_offset / 4 + runs.size() + 4, 0);
+    int32_t* img = p.image.data();
+    std::memcpy(img, blocks.data(), blocks.size() * sizeof(int32_t));
+    if (!corners.empty()) std::memcpy(img + p.corners_offset / 4, corners.data(), corners.size() * sizeof(int32_t));
+    if (!runblk.empty()) std::memcpy(img + p.runblk_offset / 4, runblk.data(), runblk.size() * sizeof(int32_t));
+    if (!runs.empty()) std::memcpy(img + p.runs_offset / 4, runs.data(), runs.size() * sizeof(int32_t));
     return SNCC_OK;
 }
 
@@ -355,6 +402,10 @@ int sncc_get_plan_info(const sncc_segments* seg, sncc_plan_info* out) {
     out->corners = p->nonzero_corners;
     out->max_corners = p->max_corners;
     out->Q0 = p->Q0;
+    out->runs8 = p->runs[0];
+    out->runs4 = p->runs[1];
+    out->runs2 = p->runs[2];
+    out->runs1 = p->runs[3];
     return SNCC_OK;
 }
 

@@ -49,13 +49,31 @@ struct Plan {
     int max_corners = 0;    // largest corner count of one block
     int total_corners = 0;    // including the zero-weight padding
     int nonzero_corners = 0;
-    // Device image: int4 blocks[nblk] = {bx, by, first, count}, then int2
-    // corners[total] = {Y * WP + X, G}; each block's list starts on a
-    // multiple of 4 corners and is padded with zero weights to a multiple of 4.
+    int runs[4] = {0, 0, 0, 0};  // vertical runs of 8, 4, 2 and 1 corners, over all blocks
+    // Device image, four int4-aligned arrays:
+    //  * int4 blocks[nblk] = {bx, by, first, count};
+    //  * int2 corners[total] = {Y * WP + X, G}, the plain corner list; each
+    //    block's list starts on a multiple of 4 corners and is padded with
+    //    zero weights to a multiple of 4;
+    //  * int4 runblk[2 * nblk] = {first8, n8, first4, n4}, {first2, n2,
+    //    first1, n1}: the same corners of block b regrouped into vertical
+    //    runs (a run of L corners occupies rows Y .. Y+L-1 of one column X,
+    //    every weight nonzero); first* index int4 units of runs[];
+    //  * int4 runs[]: a run of 8 is {idx, G0, G1, G2} {G3, G4, G5, G6}
+    //    {G7, 0, 0, 0}, a run of 4 is {idx, G0, G1, G2} {G3, 0, 0, 0}, a run
+    //    of 2 is {idx, G0, G1, 0}, with idx = Y * WP + X; single corners are
+    //    int2 {idx, G}, two per int4, padded with zero weights to a multiple
+    //    of 4 (n1 counts corners, not int4 units).
     std::vector<int32_t> image;
     size_t blocks_offset = 0;   // bytes
     size_t corners_offset = 0;  // bytes
+    size_t runblk_offset = 0;   // bytes
+    size_t runs_offset = 0;     // bytes
 };
+
+// Lengths of the vertical corner runs and the int4 units one run occupies.
+constexpr int RUN_LEN[4] = {8, 4, 2, 1};
+constexpr int RUN_INT4[3] = {3, 2, 1};
 
 Plan* plan_of(const sncc_segments* s);
 

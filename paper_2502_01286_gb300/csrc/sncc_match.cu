@@ -10,8 +10,7 @@
 //    A(u, v) = sum_{x,y} q(x, y) f(u+x, v+y) through the corner form of
 //    Eq. 11: every segment contributes +-q_i at its four corners and corners
 //    shared by neighbouring segments are combined on the host, so each
-//    offset needs one sum-table read and one 32x32->64-bit multiply-add per
-//    distinct corner.
+//    offset needs one 32x32->64-bit multiply-add per distinct corner.
 //  * The template is processed in blocks.  For each block the sum-table
 //    region the tile touches is staged in shared memory and re-based to its
 //    own origin (exact in wrapped 32-bit arithmetic, since every re-based
@@ -23,8 +22,11 @@
 //        2^32) are loaded through registers and stored already re-based.
 //    The region is read with conflict-free 32-bit loads: lane l reads
 //    column l, warp w its own R rows.
-//  * Corner records are read two per 16-byte load, one group of four ahead
-//    of their use.
+//  * The corners come regrouped into vertical runs of 8, 4, 2 and 1 corners
+//    (consecutive rows of one column): a lane's R rows share R + L - 1
+//    region loads per run of L, so on dense templates the shared-memory reads
+//    drop well below one per (offset, corner) and the 64-bit multiply-add is
+//    the only limit.  Run records are loaded one ahead of their use.
 //  * Epilogue: window sums from the global tables, exact integer variance
 //    n sum f^2 - (sum f)^2 divided by n in FP64, rho in FP32, warp-aggregated
 //    atomic append of candidates.
@@ -47,7 +49,8 @@ namespace {
 
 struct MatchArgs {
     const int4* blocks;
-    const int2* corners;
+    const int4* runblk;  // two per block
+    const int4* runs;
     int nblk;
     int RH;  // region rows = 8R + BH + 1
     int M, N;
@@ -165,9 +168,9 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
             stage_region_regs<true, WP>(a.s, a.pitch, a.M, a.N, work, u0 + blk.x, v0 + blk.y, RH, lane, warp);
         }
         __syncthreads();
-        // ---- corner sum: one shared read and one multiply-add per (offset, corner) ----
+        // ---- corner sum over vertical runs: one multiply-add per (offset, corner) ----
         const int* wbase = PIPE ? wbase0 + cur * WW : wbase0;
-        corner_sum<R, WP>(acc, wbase, reinterpret_cast<const int4*>(a.corners + blk.z), blk.w);
+        run_sum<R, WP>(acc, wbase, a.runs, __ldg(a.runblk + 2 * b), __ldg(a.runblk + 2 * b + 1));
         __syncthreads();  // this buffer is restaged two blocks later (PIPE) or next block
         if (!S64 && !PIPE && b + 1 < a.nblk) {
             const int4 nb = a.blocks[b + 1];
@@ -297,7 +300,8 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
 
     MatchArgs a;
     a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->blocks_offset);
-    a.corners = reinterpret_cast<const int2*>(static_cast<const char*>(d_plan) + p->corners_offset);
+    a.runblk = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->runblk_offset);
+    a.runs = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->runs_offset);
     a.nblk = p->nblk;
     a.RH = RH;
     a.M = M;

@@ -83,6 +83,61 @@ __device__ __forceinline__ void corner_sum(long long (&acc)[R], const int* wbase
     }
 }
 
+// A vertical run of L corners at rows Y .. Y+L-1 of column X (idx = Y*WP + X)
+// with weights g[0..L-1]: offset row r needs the region words of rows
+// Y+r .. Y+r+L-1, so the R rows of a lane share R + L - 1 loads, and each
+// load feeds up to L multiply-adds instead of one.
+template <int R, int WP, int L>
+__device__ __forceinline__ void apply_run(long long (&acc)[R], const int* wbase, int idx, const int (&g)[L]) {
+    const int* w = wbase + idx;
+    int v[R + L - 1];
+#pragma unroll
+    for (int i = 0; i < R + L - 1; ++i) v[i] = w[i * WP];
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += (long long)g[l] * (long long)v[r + l];
+}
+
+// All runs of length L of one block: `n` records of S int4 units each
+// ({idx, G0, ...}), the next record loaded while the current one is applied.
+template <int R, int WP, int L, int S>
+__device__ __forceinline__ void run_class(long long (&acc)[R], const int* wbase, const int4* rec, int n) {
+    if (n <= 0) return;
+    int4 nx[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) nx[k] = __ldg(rec + k);
+    for (int i = 0; i < n; ++i) {
+        int wd[4 * S];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            wd[4 * k + 0] = nx[k].x;
+            wd[4 * k + 1] = nx[k].y;
+            wd[4 * k + 2] = nx[k].z;
+            wd[4 * k + 3] = nx[k].w;
+        }
+        if (i + 1 < n) {
+#pragma unroll
+            for (int k = 0; k < S; ++k) nx[k] = __ldg(rec + (size_t)(i + 1) * S + k);
+        }
+        int g[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) g[l] = wd[1 + l];
+        apply_run<R, WP, L>(acc, wbase, wd[0], g);
+    }
+}
+
+// acc[r] += the block's corner sum, from its vertical runs: d0 = {first8,
+// n8, first4, n4}, d1 = {first2, n2, first1, n1} (first* in int4 units of
+// `runs`, n1 single corners in groups of four).
+template <int R, int WP>
+__device__ __forceinline__ void run_sum(long long (&acc)[R], const int* wbase, const int4* runs, int4 d0, int4 d1) {
+    run_class<R, WP, 8, 3>(acc, wbase, runs + d0.x, d0.y);
+    run_class<R, WP, 4, 2>(acc, wbase, runs + d0.z, d0.w);
+    run_class<R, WP, 2, 1>(acc, wbase, runs + d1.x, d1.y);
+    corner_sum<R, WP>(acc, wbase, runs + d1.z, d1.w);
+}
+
 // rho at offset (u, v) from the exact numerator acc = 2^F num + Q0 * sum f / n
 // (Eq. 13, 15, 16 exact in integers; E_f divided in FP64; Eq. 17-18 in FP32).
 // A uniform window gives 0.

@@ -113,6 +113,25 @@ def test_quantisation_error_bound_is_small(sncc):
         assert 0 < seg.err_bound < 5e-6
 
 
+def test_vertical_runs_partition_the_corners(sncc):
+    # every nonzero corner lands in exactly one run of 8, 4, 2 or 1
+    yy, xx = np.mgrid[0:19, 0:21]
+    checker = ((xx + yy) % 2 * 200).astype(np.uint8)
+    cases = [synth.case_hd(M=200, N=200).t, synth.case_plain().t, checker,
+             synth.case_texture(M=600, N=600, W=150, H=90).t]
+    for t in cases:
+        for sigma in (2.0, 8.0, 20.0):
+            seg = sncc.build_segments(t, sigma)
+            if seg.Ek == 0.0:
+                continue
+            pi = seg.plan_info()
+            assert 8 * pi["runs8"] + 4 * pi["runs4"] + 2 * pi["runs2"] + pi["runs1"] == pi["corners"]
+    # a 1-pixel checkerboard puts a corner on every point of the 22 x 20
+    # corner grid: each column of 20 splits into runs of 8, 8 and 4
+    pi = sncc.build_segments(checker, 1.0).plan_info()
+    assert (pi["corners"], pi["runs8"], pi["runs4"], pi["runs2"], pi["runs1"]) == (440, 44, 22, 0, 0)
+
+
 def test_host_argument_errors(sncc):
     lib = sncc.lib()
     seg = sncc.build_segments(synth.case_plain().t, 10.0)
