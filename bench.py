@@ -566,7 +566,8 @@ def run_gpu(args, world, rank, local, pg):
             tw_ms.append(a.elapsed_time(b))
         two = {"value": U * V / (statistics.median(tw_ms) * 1e-3) / 1e9, "unit": UNIT,
                "ms": statistics.median(tw_ms), "K_fast": pm.fast.K, "K_slow": pm.slow.K,
-               "corners_fast": pm.fast.plan_info()["corners"], "corners_slow": pm.slow.plan_info()["corners"],
+               "corners_fast": pm.fast.plan_info()["template_corners"],
+               "corners_slow": pm.slow.plan_info()["template_corners"],
                "candidates": int(pm.mb.count.item()), "matches": int(pm.rb.nout.item()), "status": pm.status(),
                "max_abs_dncc_fast_vs_exact": float((pm.mb.rho - exact_rho).abs().max().item()),
                "what": "sum tables + coarse k_fast (0.99 sigma_t) at every offset + k_slow (0.1 sigma_t, "
@@ -579,13 +580,17 @@ def run_gpu(args, world, rank, local, pg):
 
     # dominant kernel: the segment-sum launch with the most corners
     infos = [s.plan_info() for s in segs]
-    dom = max(range(len(SIGMAS)), key=lambda i: infos[i]["corners"])
+    dom = max(range(len(SIGMAS)), key=lambda i: infos[i]["template_corners"])
     dom_ms = statistics.mean(per_sigma_ms[dom])
-    dom_ops = U * V * infos[dom]["corners"]  # one multiply-add per (offset, corner)
+    dom_ops = U * V * infos[dom]["template_corners"]  # one multiply-add per (offset, corner)
     Rt = match_tile_rows(U, V)
     pi = infos[dom]
     # table words a lane reads per R offsets: R + L - 1 per run of L corners
-    dom_words = U * V * sum(pi["runs%d" % L] * (Rt + L - 1) for L in (8, 4, 2, 1)) / Rt
+    # (the run counts describe the 32-bit-table layout; 64-bit tables on a
+    # template of several blocks use the 64 x 64 layout)
+    dom_words = None
+    if tables.s_bits == 32 or pi["blocks"] == 1:
+        dom_words = U * V * sum(pi["runs%d" % L] * (Rt + L - 1) for L in (8, 4, 2, 1)) / Rt
 
     value = sum_over_ranks(pg, offsets_per_step) / (ms_per_step * 1e-3) / 1e9
     e2e_value = sum_over_ranks(pg, offsets_per_step) / (e2e_ms_step * 1e-3) / 1e9
@@ -620,7 +625,9 @@ def run_gpu(args, world, rank, local, pg):
                       "roofline": exact_roofline(U * V * W * H, exact_ms, ceil)},
         "speedup_vs_exact": value / (U * V / (exact_ms * 1e-3) / 1e9),
         "max_abs_dncc_vs_exact": dict(zip([str(s) for s in SIGMAS], max_dncc)),
-        "per_sigma": [{"sigma_max": s, "K": seg.K, "corners": infos[i]["corners"], "rho_max": seg.rho_max,
+        "per_sigma": [{"sigma_max": s, "K": seg.K, "corners": infos[i]["template_corners"],
+                       "block_corners": infos[i]["corners"] if tables.s_bits == 32 or infos[i]["blocks"] == 1
+                       else infos[i]["wide_corners"], "rho_max": seg.rho_max,
                        "tau_c": taus[i], "match_ms": statistics.mean(per_sigma_ms[i]),
                        "candidates": counts[i], "matches": nmatch[i], "status": status[i],
                        "goffsets_s_coarse": U * V / (statistics.mean(per_sigma_ms[i]) * 1e-3) / 1e9}

@@ -304,7 +304,7 @@ typedef struct {
     int32_t tile_rows;      /* R of the current tile shape (32 x 8R offsets per tile) */
     int32_t tiles;          /* work items of the current tile shape */
     double offsets;         /* sum over pairs of U*V */
-    double corner_offsets;  /* sum over pairs of U*V*(corners with nonzero weight) */
+    double corner_offsets;  /* sum over pairs of U*V*(nonzero corners of the whole template) */
 } sncc_batch_info;
 
 /*
@@ -447,7 +447,9 @@ int sncc_exact_map(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t
 /* Introspection and measurement helpers                               */
 /* ------------------------------------------------------------------ */
 
-/* Shape of the matching plan built by sncc_build_segments. */
+/* Shape of the matching plan built by sncc_build_segments.  blocks ..
+ * runs1 describe the block layout used with 32-bit tables: one block for a
+ * template up to 64 x 64, else blocks of 32 x 32. */
 typedef struct {
     int32_t F;            /* fraction bits of the fixed-point weights q_i */
     int32_t blocks;       /* template blocks that hold at least one corner */
@@ -460,6 +462,10 @@ typedef struct {
     int32_t runs4;        /* one column, all weights nonzero) of 8, 4, 2 and 1 corners: */
     int32_t runs2;        /* 8 runs8 + 4 runs4 + 2 runs2 + runs1 = corners.  The segment-sum */
     int32_t runs1;        /* kernels read R + L - 1 table words per run of L for R rows. */
+    int32_t template_corners; /* nonzero corners of the whole template taken as one block: the
+                                 algorithmic multiply-adds per offset (block edges add corners) */
+    int32_t wide_blocks;  /* blocks and nonzero corners of the 64 x 64 block layout, which the */
+    int32_t wide_corners; /* segment-sum kernel uses with 64-bit tables for larger templates */
 } sncc_plan_info;
 
 /* Fills *out for seg; SNCC_ERR_UNIFORM when seg has no plan (Ek = 0). */

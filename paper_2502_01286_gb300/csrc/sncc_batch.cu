@@ -250,14 +250,15 @@ size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 struct sncc_batch_s {
     int nt = 0, ns = 0, M = 0, N = 0;
     std::vector<sncc::TmplDesc> tmpl;
-    std::vector<int32_t> corner_counts;  // nonzero corners per template
+    std::vector<int32_t> corner_counts;    // nonzero corners per template in the 64 x 64 layout (the work)
+    std::vector<int32_t> template_corners;  // corners of each whole template (the algorithmic count)
     size_t off_pairs = 0, off_tmpl = 0, off_blocks = 0, off_runblk = 0, off_runs = 0, off_pix = 0,
            off_items[3] = {0, 0, 0};
     int n_items[3] = {0, 0, 0};
     std::vector<unsigned char> image;
     int variant = 8;
     int grid[3] = {0, 0, 0};
-    double corner_offsets = 0.0;  // sum over pairs of U*V*(nonzero corners)
+    double corner_offsets = 0.0;  // sum over pairs of U*V*(corners of the whole template)
     double offsets = 0.0;         // sum over pairs of U*V
 };
 
@@ -330,12 +331,13 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
                 return SNCC_ERR_ARG;
             }
             Plan p;
-            build_plan(sg, p, true);
+            build_plan(sg, p);
+            const Layout& L = p.lay[1];  // blocks of at most 64 x 64, pitch 100
             TmplDesc d;
             std::memset(&d, 0, sizeof(d));
             d.W = sg->W;
             d.H = sg->H;
-            d.nblk = p.nblk;
+            d.nblk = L.nblk;
             d.blk_first = (int)(blocks.size() / 4);
             d.n = (long long)sg->W * sg->H;
             d.Q0 = p.Q0;
@@ -352,18 +354,19 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
                            templates[t] + (size_t)y * t_strides[t] + sg->W);
             while (pix.size() % 16) pix.push_back(0);
             const int run_base = (int)(runs.size() / 4);  // int4 units
-            const int32_t* img_blocks = p.image.data();
-            const int32_t* img_runblk = p.image.data() + p.runblk_offset / 4;
-            const int32_t* img_runs = p.image.data() + p.runs_offset / 4;
-            const size_t run_words = p.image.size() - 4 - p.runs_offset / 4;
-            for (int k = 0; k < p.nblk; ++k) {
+            const int32_t* img_blocks = p.image.data() + L.blocks_offset / 4;
+            const int32_t* img_runblk = p.image.data() + L.runblk_offset / 4;
+            const int32_t* img_runs = p.image.data() + L.runs_offset / 4;
+            const size_t run_words = (L.end_offset - L.runs_offset) / 4;
+            for (int k = 0; k < L.nblk; ++k) {
                 for (int j = 0; j < 4; ++j) blocks.push_back(img_blocks[4 * k + j]);
                 for (int j = 0; j < 8; ++j)  // firsts (even words) move by run_base
                     runblk.push_back(img_runblk[8 * k + j] + ((j % 2 == 0) ? run_base : 0));
             }
             runs.insert(runs.end(), img_runs, img_runs + run_words);
             b->tmpl.push_back(d);
-            b->corner_counts.push_back(p.nonzero_corners);
+            b->corner_counts.push_back(L.nonzero_corners);
+            b->template_corners.push_back(p.template_corners);
         }
         // pairs: source-major
         std::vector<int32_t> pairs;
@@ -378,7 +381,7 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
                 pairs.push_back(V);
                 // per-tile cost: corner sum plus region staging per block
                 cost.push_back((double)b->corner_counts[t] * 8.0 + (double)d.nblk * 1600.0);
-                b->corner_offsets += (double)U * V * b->corner_counts[t];
+                b->corner_offsets += (double)U * V * b->template_corners[t];
                 b->offsets += (double)U * V;
             }
         const int npairs = n_templates * n_sources;
@@ -486,7 +489,7 @@ extern "C" int sncc_batch_match(const sncc_batch* b, const void* d_buf, const vo
     a.n_items = b->n_items[vi];
     a.counter = d_counter;
     for (int s = 0; s < b->ns; ++s) {
-        if (!d_s[s] || !d_s2[s]) return SNCC_ERR_ARG;
+        if (!d_s[s] || !d_s2[s] || (reinterpret_cast<uintptr_t>(d_s[s]) & 15)) return SNCC_ERR_ARG;
         a.s[s] = d_s[s];
         a.s2[s] = d_s2[s];
     }

@@ -142,32 +142,115 @@ __int128 round_div(__int128 num, __int128 den) {
 
 }  // namespace
 
-// Builds the fixed-point weights and the per-block corner lists.
-// uniform_64: every block is at most 64 x 64 and the pitch is always 100 (the
-// batched kernel's single layout); otherwise templates up to 64 x 64 are one
-// block and larger ones use 32 x 32 blocks.
-int build_plan(const sncc_segments* s, Plan& p, bool uniform_64) {
+// Cuts the rendered weights qimg (W x H) into blocks of BW x BH with region
+// pitch WP and appends the layout's arrays (blocks, corner list, run
+// descriptors, runs) to `image`, recording their byte offsets in L.
+static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW, int BH, int WP, Layout& L,
+                  std::vector<int32_t>& image) {
+    L.BW = BW;
+    L.BH = BH;
+    L.WP = WP;
+    L.nbx = (W + BW - 1) / BW;
+    L.nby = (H + BH - 1) / BH;
+    std::vector<int32_t> blocks, corners, runblk, runs;
+    L.max_corners = 0;
+    L.nonzero_corners = 0;
+    for (int k = 0; k < 4; ++k) L.runs[k] = 0;
+    for (int by_i = 0; by_i < L.nby; ++by_i) {
+        for (int bx_i = 0; bx_i < L.nbx; ++bx_i) {
+            const int bx = bx_i * BW, by = by_i * BH;
+            const int bw = std::min(BW, W - bx), bh = std::min(BH, H - by);
+            auto q = [&](int X, int Y) -> int64_t {  // block-local, zero outside
+                if (X < 0 || Y < 0 || X >= bw || Y >= bh) return 0;
+                return qimg[(size_t)(by + Y) * W + (bx + X)];
+            };
+            std::vector<int32_t> G((size_t)(bw + 1) * (bh + 1));  // G[X * (bh + 1) + Y], column-major
+            const int first = (int)(corners.size() / 2);
+            for (int Y = 0; Y <= bh; ++Y)
+                for (int X = 0; X <= bw; ++X) {
+                    const int64_t g = q(X - 1, Y - 1) - q(X, Y - 1) - q(X - 1, Y) + q(X, Y);
+                    G[(size_t)X * (bh + 1) + Y] = (int32_t)g;
+                    if (g != 0) {
+                        corners.push_back(Y * WP + X);
+                        corners.push_back((int32_t)g);
+                        ++L.nonzero_corners;
+                    }
+                }
+            // pad to a multiple of 4 corners with zero weights (16-byte loads
+            // of two corners, groups of four, no tail in the kernel)
+            while (((corners.size() / 2) - first) % 4 != 0) {
+                corners.push_back(0);
+                corners.push_back(0);
+            }
+            const int cnt = (int)(corners.size() / 2) - first;
+            if (cnt == 0) continue;  // a block inside one segment adds nothing
+            blocks.push_back(bx);
+            blocks.push_back(by);
+            blocks.push_back(first);
+            blocks.push_back(cnt);
+            L.max_corners = std::max(L.max_corners, cnt);
+
+            // Vertical runs: walking each column downwards, the first
+            // uncovered corner starts the longest run of 8, 4 or 2 whose rows
+            // all hold corners (and stay inside the block's corner grid);
+            // otherwise it is a single corner.
+            std::vector<int32_t> cls[4];
+            for (int X = 0; X <= bw; ++X) {
+                const int32_t* col = &G[(size_t)X * (bh + 1)];
+                for (int Y = 0; Y <= bh;) {
+                    if (col[Y] == 0) {
+                        ++Y;
+                        continue;
+                    }
+                    int k = 3;
+                    for (int c = 0; c < 3; ++c) {
+                        const int len = RUN_LEN[c];
+                        if (Y + len - 1 > bh) continue;
+                        bool full = true;
+                        for (int i = 0; i < len && full; ++i) full = col[Y + i] != 0;
+                        if (full) {
+                            k = c;
+                            break;
+                        }
+                    }
+                    const int len = RUN_LEN[k];
+                    cls[k].push_back(Y * WP + X);
+                    for (int i = 0; i < len; ++i) cls[k].push_back(col[Y + i]);
+                    if (k < 3)  // pad the record to its int4 units
+                        while (cls[k].size() % (4 * RUN_INT4[k]) != 0) cls[k].push_back(0);
+                    ++L.runs[k];
+                    Y += len;
+                }
+            }
+            while (cls[3].size() % 8 != 0) cls[3].push_back(0);  // whole groups of 4 single corners
+            for (int k = 0; k < 4; ++k) {
+                runblk.push_back((int32_t)(runs.size() / 4));
+                runblk.push_back(k < 3 ? (int32_t)(cls[k].size() / (4 * RUN_INT4[k])) : (int32_t)(cls[3].size() / 2));
+                runs.insert(runs.end(), cls[k].begin(), cls[k].end());
+            }
+        }
+    }
+    L.nblk = (int)(blocks.size() / 4);
+    L.total_corners = (int)(corners.size() / 2);
+    L.blocks_offset = image.size() * 4;
+    image.insert(image.end(), blocks.begin(), blocks.end());
+    L.corners_offset = image.size() * 4;
+    image.insert(image.end(), corners.begin(), corners.end());
+    L.runblk_offset = image.size() * 4;
+    image.insert(image.end(), runblk.begin(), runblk.end());
+    L.runs_offset = image.size() * 4;
+    image.insert(image.end(), runs.begin(), runs.end());
+    L.end_offset = image.size() * 4;
+}
+
+// Builds the fixed-point weights and both block layouts of the plan.
+int build_plan(const sncc_segments* s, Plan& p) {
     const int W = s->W, H = s->H;
     const int64_t n = (int64_t)W * H;
     p.W = W;
     p.H = H;
     p.n = (double)n;
     p.Ek = s->Ek;
-    if (uniform_64) {
-        p.BW = std::min(W, BLOCK_SINGLE_MAX);
-        p.BH = std::min(H, BLOCK_SINGLE_MAX);
-    } else if (W <= BLOCK_SINGLE_MAX && H <= BLOCK_SINGLE_MAX) {
-        p.BW = W;
-        p.BH = H;
-    } else {
-        p.BW = std::min(W, BLOCK_MULTI);
-        p.BH = std::min(H, BLOCK_MULTI);
-    }
-    p.nbx = (W + p.BW - 1) / p.BW;
-    p.nby = (H + p.BH - 1) / p.BH;
-    // Work-region pitch is one of two compile-time widths of the kernel,
-    // multiples of 4 so that a region row is a whole number of 16-byte units.
-    p.WP = (p.BW <= 32 && !uniform_64) ? 68 : 100;
 
     // Fixed-point scale: every |G| <= 4 max|q_i| must stay below 2^31.
     double maxc = 0.0;
@@ -193,100 +276,23 @@ int build_plan(const sncc_segments* s, Plan& p, bool uniform_64) {
     }
     p.Q0 = Q0;
 
-    // Corner lists, block by block.
-    std::vector<int32_t> blocks;
-    std::vector<int32_t> corners;
-    std::vector<int32_t> runblk;
-    std::vector<int32_t> runs;  // int4 units, 4 words each
-    int nonzero = 0;
-    p.max_corners = 0;
-    for (int by_i = 0; by_i < p.nby; ++by_i) {
-        for (int bx_i = 0; bx_i < p.nbx; ++bx_i) {
-            const int bx = bx_i * p.BW, by = by_i * p.BH;
-            const int bw = std::min(p.BW, W - bx), bh = std::min(p.BH, H - by);
-            auto q = [&](int X, int Y) -> int64_t {  // block-local, zero outside
-                if (X < 0 || Y < 0 || X >= bw || Y >= bh) return 0;
-                return qimg[(size_t)(by + Y) * W + (bx + X)];
-            };
-            std::vector<int32_t> G((size_t)(bw + 1) * (bh + 1));  // G[X * (bh + 1) + Y], column-major
-            const int first = (int)(corners.size() / 2);
-            for (int Y = 0; Y <= bh; ++Y)
-                for (int X = 0; X <= bw; ++X) {
-                    const int64_t g = q(X - 1, Y - 1) - q(X, Y - 1) - q(X - 1, Y) + q(X, Y);
-                    G[(size_t)X * (bh + 1) + Y] = (int32_t)g;
-                    if (g != 0) {
-                        corners.push_back(Y * p.WP + X);
-                        corners.push_back((int32_t)g);
-                        ++nonzero;
-                    }
-                }
-            // pad to a multiple of 4 corners with zero weights (16-byte loads
-            // of two corners, groups of four, no tail in the kernel)
-            while (((corners.size() / 2) - first) % 4 != 0) {
-                corners.push_back(0);
-                corners.push_back(0);
-            }
-            const int cnt = (int)(corners.size() / 2) - first;
-            if (cnt == 0) continue;  // a block inside one segment adds nothing
-            blocks.push_back(bx);
-            blocks.push_back(by);
-            blocks.push_back(first);
-            blocks.push_back(cnt);
-            p.max_corners = std::max(p.max_corners, cnt);
+    // Corners of the whole template as one block: the algorithmic count.
+    p.template_corners = 0;
+    auto qa = [&](int X, int Y) -> int64_t {
+        return (X < 0 || Y < 0 || X >= W || Y >= H) ? 0 : qimg[(size_t)Y * W + X];
+    };
+    for (int Y = 0; Y <= H; ++Y)
+        for (int X = 0; X <= W; ++X)
+            p.template_corners += (qa(X - 1, Y - 1) - qa(X, Y - 1) - qa(X - 1, Y) + qa(X, Y)) != 0;
 
-            // Vertical runs: walking each column downwards, the first
-            // uncovered corner starts the longest run of 8, 4 or 2 whose rows
-            // all hold corners (and stay inside the block's corner grid);
-            // otherwise it is a single corner.
-            std::vector<int32_t> cls[4];
-            for (int X = 0; X <= bw; ++X) {
-                const int32_t* col = &G[(size_t)X * (bh + 1)];
-                for (int Y = 0; Y <= bh;) {
-                    if (col[Y] == 0) {
-                        ++Y;
-                        continue;
-                    }
-                    int k = 3;
-                    for (int c = 0; c < 3; ++c) {
-                        const int L = RUN_LEN[c];
-                        if (Y + L - 1 > bh) continue;
-                        bool full = true;
-                        for (int i = 0; i < L && full; ++i) full = col[Y + i] != 0;
-                        if (full) {
-                            k = c;
-                            break;
-                        }
-                    }
-                    const int L = RUN_LEN[k];
-                    cls[k].push_back(Y * p.WP + X);
-                    for (int i = 0; i < L; ++i) cls[k].push_back(col[Y + i]);
-                    if (k < 3)  // pad the record to its int4 units
-                        while (cls[k].size() % (4 * RUN_INT4[k]) != 0) cls[k].push_back(0);
-                    ++p.runs[k];
-                    Y += L;
-                }
-            }
-            while (cls[3].size() % 8 != 0) cls[3].push_back(0);  // whole groups of 4 single corners
-            for (int k = 0; k < 4; ++k) {
-                runblk.push_back((int32_t)(runs.size() / 4));
-                runblk.push_back(k < 3 ? (int32_t)(cls[k].size() / (4 * RUN_INT4[k])) : (int32_t)(cls[3].size() / 2));
-                runs.insert(runs.end(), cls[k].begin(), cls[k].end());
-            }
-        }
-    }
-    p.nblk = (int)(blocks.size() / 4);
-    p.total_corners = (int)(corners.size() / 2);
-    p.nonzero_corners = nonzero;
-    p.blocks_offset = 0;
-    p.corners_offset = (size_t)p.nblk * 16;
-    p.runblk_offset = p.corners_offset + corners.size() * 4;
-    p.runs_offset = p.runblk_offset + runblk.size() * 4;
-    p.image.assign(p.runs_offset / 4 + runs.size() + 4, 0);
-    int32_t* img = p.image.data();
-    std::memcpy(img, blocks.data(), blocks.size() * sizeof(int32_t));
-    if (!corners.empty()) std::memcpy(img + p.corners_offset / 4, corners.data(), corners.size() * sizeof(int32_t));
-    if (!runblk.empty()) std::memcpy(img + p.runblk_offset / 4, runblk.data(), runblk.size() * sizeof(int32_t));
-    if (!runs.empty()) std::memcpy(img + p.runs_offset / 4, runs.data(), runs.size() * sizeof(int32_t));
+    // Region pitches are compile-time widths of the kernels, multiples of 4
+    // so that a region row is a whole number of 16-byte units.
+    p.image.clear();
+    const bool single = W <= BLOCK_SINGLE_MAX && H <= BLOCK_SINGLE_MAX;
+    const int bw0 = single ? W : std::min(W, BLOCK_MULTI), bh0 = single ? H : std::min(H, BLOCK_MULTI);
+    build_layout(qimg, W, H, bw0, bh0, bw0 <= 32 ? 68 : 100, p.lay[0], p.image);
+    build_layout(qimg, W, H, std::min(W, BLOCK_SINGLE_MAX), std::min(H, BLOCK_SINGLE_MAX), 100, p.lay[1], p.image);
+    p.image.insert(p.image.end(), 4, 0);
     return SNCC_OK;
 }
 
@@ -379,7 +385,7 @@ int sncc_build_segments(const uint8_t* t, int W, int H, int t_stride, double sig
         Plan* p = new Plan();
         out->plan = p;
         if (Ek > 0.0) {
-            build_plan(out, *p, false);
+            build_plan(out, *p);
             // |rho_gpu - rho| from quantising c_i to q_i / 2^F is at most
             // 2^-(F+1) sqrt(n / Ek); float rounding adds a few 1e-7.
             out->err_bound = std::ldexp(1.0, -(p->F + 1)) * std::sqrt((double)n / Ek) + 1e-6;
@@ -396,16 +402,20 @@ int sncc_get_plan_info(const sncc_segments* seg, sncc_plan_info* out) {
     if (!out || !p) return SNCC_ERR_ARG;
     if (p->image.empty()) return SNCC_ERR_UNIFORM;
     out->F = p->F;
-    out->blocks = p->nblk;
-    out->block_w = p->BW;
-    out->block_h = p->BH;
-    out->corners = p->nonzero_corners;
-    out->max_corners = p->max_corners;
+    const sncc::Layout& L = p->lay[0];
+    out->blocks = L.nblk;
+    out->block_w = L.BW;
+    out->block_h = L.BH;
+    out->corners = L.nonzero_corners;
+    out->max_corners = L.max_corners;
     out->Q0 = p->Q0;
-    out->runs8 = p->runs[0];
-    out->runs4 = p->runs[1];
-    out->runs2 = p->runs[2];
-    out->runs1 = p->runs[3];
+    out->runs8 = L.runs[0];
+    out->runs4 = L.runs[1];
+    out->runs2 = L.runs[2];
+    out->runs1 = L.runs[3];
+    out->template_corners = p->template_corners;
+    out->wide_blocks = p->lay[1].nblk;
+    out->wide_corners = p->lay[1].nonzero_corners;
     return SNCC_OK;
 }
 

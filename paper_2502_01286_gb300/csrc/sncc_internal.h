@@ -36,39 +36,52 @@ constexpr int BLOCK_MULTI = 32;       // larger templates use 32 x 32 blocks
 //   G(X, Y) = q(X-1, Y-1) - q(X, Y-1) - q(X-1, Y) + q(X, Y)   (block-local,
 // q = 0 outside the block), i.e. Eq. 11 applied to every segment and summed,
 // with the shared corners of neighbouring segments combined.
-struct Plan {
-    int W = 0, H = 0;
+// One way of cutting the template into blocks, with its corner lists.
+// Device image section (offsets in bytes from the start of the plan image,
+// each array 16-byte aligned):
+//  * int4 blocks[nblk] = {bx, by, first, count};
+//  * int2 corners[total] = {Y * WP + X, G}, the plain corner list; each
+//    block's list starts on a multiple of 4 corners and is padded with zero
+//    weights to a multiple of 4;
+//  * int4 runblk[2 * nblk] = {first8, n8, first4, n4}, {first2, n2, first1,
+//    n1}: the same corners of block b regrouped into vertical runs (a run of
+//    L corners occupies rows Y .. Y+L-1 of one column X, every weight
+//    nonzero); first* index int4 units of runs[];
+//  * int4 runs[]: a run of 8 is {idx, G0, G1, G2} {G3, G4, G5, G6}
+//    {G7, 0, 0, 0}, a run of 4 is {idx, G0, G1, G2} {G3, 0, 0, 0}, a run of
+//    2 is {idx, G0, G1, 0}, with idx = Y * WP + X; single corners are int2
+//    {idx, G}, two per int4, padded with zero weights to a multiple of 4
+//    (n1 counts corners, not int4 units).
+struct Layout {
     int BW = 0, BH = 0;     // block size (the last block in a row/column may be smaller)
     int nbx = 0, nby = 0;   // blocks across / down
     int nblk = 0;           // blocks that hold at least one corner (the others are dropped)
     int WP = 0;             // pitch (elements) of the re-based work region: 68 (BW <= 32) or 100
+    int max_corners = 0;    // largest corner count of one block
+    int total_corners = 0;  // including the zero-weight padding
+    int nonzero_corners = 0;
+    int runs[4] = {0, 0, 0, 0};  // vertical runs of 8, 4, 2 and 1 corners, over all blocks
+    size_t blocks_offset = 0;
+    size_t corners_offset = 0;
+    size_t runblk_offset = 0;
+    size_t runs_offset = 0;
+    size_t end_offset = 0;  // one past the section
+};
+
+struct Plan {
+    int W = 0, H = 0;
     int F = 0;              // fixed-point fraction bits of q_i
     int64_t Q0 = 0;         // sum over the template of q(x, y)
     double Ek = 0.0;        // weighted energy of the approximation
     double n = 0.0;         // W * H
-    int max_corners = 0;    // largest corner count of one block
-    int total_corners = 0;    // including the zero-weight padding
-    int nonzero_corners = 0;
-    int runs[4] = {0, 0, 0, 0};  // vertical runs of 8, 4, 2 and 1 corners, over all blocks
-    // Device image, four int4-aligned arrays:
-    //  * int4 blocks[nblk] = {bx, by, first, count};
-    //  * int2 corners[total] = {Y * WP + X, G}, the plain corner list; each
-    //    block's list starts on a multiple of 4 corners and is padded with
-    //    zero weights to a multiple of 4;
-    //  * int4 runblk[2 * nblk] = {first8, n8, first4, n4}, {first2, n2,
-    //    first1, n1}: the same corners of block b regrouped into vertical
-    //    runs (a run of L corners occupies rows Y .. Y+L-1 of one column X,
-    //    every weight nonzero); first* index int4 units of runs[];
-    //  * int4 runs[]: a run of 8 is {idx, G0, G1, G2} {G3, G4, G5, G6}
-    //    {G7, 0, 0, 0}, a run of 4 is {idx, G0, G1, G2} {G3, 0, 0, 0}, a run
-    //    of 2 is {idx, G0, G1, 0}, with idx = Y * WP + X; single corners are
-    //    int2 {idx, G}, two per int4, padded with zero weights to a multiple
-    //    of 4 (n1 counts corners, not int4 units).
-    std::vector<int32_t> image;
-    size_t blocks_offset = 0;   // bytes
-    size_t corners_offset = 0;  // bytes
-    size_t runblk_offset = 0;   // bytes
-    size_t runs_offset = 0;     // bytes
+    int template_corners = 0;  // corners of the whole template taken as one block
+    // lay[0]: a template up to 64 x 64 is one block (pitch 68 when it is at
+    // most 32 wide, else 100); larger ones use 32 x 32 blocks (pitch 68),
+    // which the 32-bit-table kernel double-buffers.  lay[1]: blocks of at
+    // most 64 x 64 with pitch 100, used with 64-bit tables (fewer, larger
+    // blocks halve the register staging per corner) and by the batched kernel.
+    Layout lay[2];
+    std::vector<int32_t> image;  // both sections, then 4 zero words
 };
 
 // Lengths of the vertical corner runs and the int4 units one run occupies.
@@ -78,7 +91,12 @@ constexpr int RUN_INT4[3] = {3, 2, 1};
 Plan* plan_of(const sncc_segments* s);
 
 // Fills p from seg's segment table (defined in sncc_host.cpp).
-int build_plan(const sncc_segments* seg, Plan& p, bool uniform_64);
+int build_plan(const sncc_segments* seg, Plan& p);
+
+// The layout the single-problem kernels use with a table of s_bits bits.
+inline const Layout& layout_for(const Plan& p, bool s64) {
+    return (s64 && p.lay[0].nbx * p.lay[0].nby > 1) ? p.lay[1] : p.lay[0];
+}
 
 // Writes the first min(*d_n, cap) records of `in` to `out` in ascending
 // v*U+u order (keys are distinct).  Defined in sncc_refine.cu.

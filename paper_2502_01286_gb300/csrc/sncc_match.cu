@@ -281,8 +281,9 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
     if ((int64_t)U * V >= ((int64_t)1 << 31)) return SNCC_ERR_UNSUPPORTED;
 
     const bool s64 = (s_bits == 64);
+    const Layout& L = layout_for(*p, s64);
     const int R = choose_r(U, V);
-    const int RH = WARPS * R + p->BH + 1;
+    const int RH = WARPS * R + L.BH + 1;
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     if (!s64) {  // 2-D TMA tile map over the 32-bit table, box WP x RH
@@ -290,7 +291,7 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
         if (!encode) return SNCC_ERR_CUDA;
         cuuint64_t gdim[2] = {(cuuint64_t)(M + 1), (cuuint64_t)(N + 1)};
         cuuint64_t gstride[1] = {(cuuint64_t)sat_pitch * 4};
-        cuuint32_t box[2] = {(cuuint32_t)p->WP, (cuuint32_t)RH};
+        cuuint32_t box[2] = {(cuuint32_t)L.WP, (cuuint32_t)RH};
         cuuint32_t estride[2] = {1, 1};
         CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, const_cast<void*>(d_s), gdim, gstride, box,
                              estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -299,10 +300,10 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
     }
 
     MatchArgs a;
-    a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->blocks_offset);
-    a.runblk = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->runblk_offset);
-    a.runs = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->runs_offset);
-    a.nblk = p->nblk;
+    a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.blocks_offset);
+    a.runblk = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.runblk_offset);
+    a.runs = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.runs_offset);
+    a.nblk = L.nblk;
     a.RH = RH;
     a.M = M;
     a.N = N;
@@ -332,13 +333,12 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
     cudaError_t e;
     // Single-block templates (up to 64 x 64) stage once; multi-block ones
     // double-buffer so that block b+1 is in flight while block b computes.
-    if (p->WP == 68 && p->nblk > 1 && !s64)
-        e = dispatch_r<false, 68, true>(R, map, a, p->BH, st);
-    else if (p->WP == 68)
-        e = s64 ? dispatch_r<true, 68, false>(R, map, a, p->BH, st)
-                : dispatch_r<false, 68, false>(R, map, a, p->BH, st);
+    if (L.WP == 68 && L.nblk > 1 && !s64)
+        e = dispatch_r<false, 68, true>(R, map, a, L.BH, st);
+    else if (L.WP == 68)
+        e = s64 ? dispatch_r<true, 68, false>(R, map, a, L.BH, st) : dispatch_r<false, 68, false>(R, map, a, L.BH, st);
     else
-        e = s64 ? dispatch_r<true, 100, false>(R, map, a, p->BH, st)
-                : dispatch_r<false, 100, false>(R, map, a, p->BH, st);
+        e = s64 ? dispatch_r<true, 100, false>(R, map, a, L.BH, st)
+                : dispatch_r<false, 100, false>(R, map, a, L.BH, st);
     return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }

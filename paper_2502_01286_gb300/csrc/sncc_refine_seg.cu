@@ -129,10 +129,11 @@ extern "C" int sncc_refine_segmented(const sncc_segments* seg, const void* d_pla
     if (cand_cap == 0) return SNCC_OK;
 
     RefineSegArgs a;
-    a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->blocks_offset);
-    a.corners = reinterpret_cast<const int2*>(static_cast<const char*>(d_plan) + p->corners_offset);
-    a.nblk = p->nblk;
-    a.WP = p->WP;
+    const Layout& L = p->lay[0];
+    a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.blocks_offset);
+    a.corners = reinterpret_cast<const int2*>(static_cast<const char*>(d_plan) + L.corners_offset);
+    a.nblk = L.nblk;
+    a.WP = L.WP;
     a.s = d_s;
     a.s2 = d_s2;
     a.pitch = sat_pitch;

@@ -29,12 +29,21 @@ __device__ __forceinline__ uint32_t table_low(const void* s, int pitch, int X, i
 // buf (RH rows x WP words), re-based to the origin in wrapped 32-bit
 // arithmetic: buf[Y][X] = s(x0+X, y0+Y) - s(x0+X, y0) - s(x0, y0+Y) + s(x0, y0)
 // (mod 2^32), which is the box sum over the region and exact below 2^31.
-// Lane l owns columns l, l+32, ...; warp w owns rows w, w+WARPS, ...; only
-// columns below `cols` (<= WP) are written.
-// Entries past the table, which only offsets outside the map read, load as 0.
+// At least the first `cols` (<= WP) columns are written; warp w owns rows w,
+// w + WARPS, ...
+//
+// Regions inside the table take the fast path: lane l loads entries
+// x0 + 2j and x0 + 2j + 1 (j = l, l + 32, ...) with one 16-byte (int64
+// table) or 8-byte (int32 table) load and stores their low words with one
+// 8-byte store; the origin column comes from lane 0 by shuffle.  This needs
+// x0 even, an even table pitch and a 16-byte aligned table, which the callers
+// guarantee (x0 is a multiple of 32 plus a multiple of the block width 64,
+// the pitch a multiple of 32).  Regions that cross the table's edge take the
+// checked path, where entries past the table, which only offsets outside the
+// map read, load as 0.
 template <bool S64, int WP>
-__device__ __forceinline__ void stage_region_regs(const void* s, int pitch, int M, int N, int* buf, int x0, int y0,
-                                                  int RH, int lane, int warp, int cols = WP) {
+__device__ __forceinline__ void stage_region_checked(const void* s, int pitch, int M, int N, int* buf, int x0,
+                                                     int y0, int RH, int lane, int warp, int cols) {
     constexpr int KX = (WP + 31) / 32;
     auto at = [&](int gx, int gy) -> uint32_t {
         return (gx <= M && gy <= N) ? table_low<S64>(s, pitch, gx, gy) : 0u;
@@ -52,6 +61,61 @@ __device__ __forceinline__ void stage_region_regs(const void* s, int pitch, int 
 #pragma unroll
         for (int k = 0; k < KX; ++k)
             if (lane + 32 * k < cols) buf[Y * WP + lane + 32 * k] = (int)(v[k] - r0[k] - cy);
+    }
+}
+
+// Low words of table entries x0 + 2j and x0 + 2j + 1 of the row at `rowp`.
+template <bool S64>
+__device__ __forceinline__ uint2 load_pair(const char* rowp, int j) {
+    if constexpr (S64) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(rowp) + j);
+        return make_uint2(q.x, q.z);
+    } else {
+        return __ldg(reinterpret_cast<const uint2*>(rowp) + j);
+    }
+}
+
+template <bool S64, int WP>
+__device__ __forceinline__ void stage_region_regs(const void* s, int pitch, int M, int N, int* buf, int x0, int y0,
+                                                  int RH, int lane, int warp, int cols = WP) {
+    constexpr int KP = (WP / 2 + 31) / 32;  // column pairs per lane
+    const int npairs = (cols + 1) >> 1;
+    if (x0 + 2 * npairs - 1 > M || y0 + RH - 1 > N) {
+        stage_region_checked<S64, WP>(s, pitch, M, N, buf, x0, y0, RH, lane, warp, cols);
+        return;
+    }
+    constexpr size_t esz = S64 ? 8 : 4;
+    const char* base = static_cast<const char*>(s) + ((size_t)y0 * pitch + x0) * esz;
+    const size_t rstride = (size_t)pitch * esz;
+    uint2 r0[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+        const int j = lane + 32 * k;
+        r0[k] = (j < npairs) ? load_pair<S64>(base, j) : make_uint2(0u, 0u);
+    }
+    const uint32_t c00 = __shfl_sync(0xffffffffu, r0[0].x, 0);
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+        r0[k].x -= c00;
+        r0[k].y -= c00;
+    }
+    for (int Y = warp; Y < RH; Y += WARPS) {
+        const char* rowp = base + (size_t)Y * rstride;
+        uint2 v[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const int j = lane + 32 * k;
+            v[k] = (j < npairs) ? load_pair<S64>(rowp, j) : make_uint2(0u, 0u);
+        }
+        const uint32_t cy = __shfl_sync(0xffffffffu, v[0].x, 0);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const int j = lane + 32 * k;
+            if (j < npairs) {
+                const uint2 o = make_uint2(v[k].x - r0[k].x - cy, v[k].y - r0[k].y - cy);
+                *reinterpret_cast<uint2*>(buf + Y * WP + 2 * j) = o;
+            }
+        }
     }
 }
 

@@ -61,7 +61,8 @@ class _Segments(C.Structure):
 class PlanInfo(C.Structure):
     _fields_ = [("F", C.c_int32), ("blocks", C.c_int32), ("block_w", C.c_int32), ("block_h", C.c_int32),
                 ("corners", C.c_int32), ("max_corners", C.c_int32), ("Q0", C.c_int64), ("runs8", C.c_int32),
-                ("runs4", C.c_int32), ("runs2", C.c_int32), ("runs1", C.c_int32)]
+                ("runs4", C.c_int32), ("runs2", C.c_int32), ("runs1", C.c_int32), ("template_corners", C.c_int32),
+                ("wide_blocks", C.c_int32), ("wide_corners", C.c_int32)]
 
 
 class MatchT(C.Structure):
