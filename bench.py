@@ -865,27 +865,121 @@ def run_gpu_diff(args, world, rank, local, pg):
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
     barrier(pg)
     torch.cuda.synchronize()
+    clocks.mark_start()
     for k in range(args.steps):
         flush.fill_(k & 0xff)
         starts[k].record(stream)
         step()
         ends[k].record(stream)
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier(pg)
+    clk = clocks.stop()
     ms = max_over_ranks(pg, sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / args.steps)
     U, V = pb.U, pb.V
+    H, W = t.shape
+
+    # end to end: the source from pinned host memory every step, loss and dL/dk read back
+    host_f = torch.as_tensor(f).pin_memory()
+    e2e_ms = []
+    for k in range(max(3, min(args.steps, 20))):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fe = host_f.to(dev, non_blocking=True).requires_grad_(True)
+        ke = kd.detach().clone().requires_grad_(True)
+        loss = pb.loss(fe, ke)
+        loss.backward()
+        out_loss = loss.detach().to("cpu", non_blocking=True)
+        out_dk = ke.grad.to("cpu", non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_ms_step = max_over_ranks(pg, statistics.mean(e2e_ms))
+
+    # the backward call alone (coefficients, dL/df, template-space correlation, dL/dk)
+    ceil = measure_ceilings(sncc, torch, stream, dev)
+    fdet, kdet = fd.detach(), kd.detach().contiguous()
+    rho_k, rho_t, _ = sncc._diff_forward(pb, fdet, kdet)
+    dl = torch.ones(1, dtype=torch.float64, device=dev)
+    gf = torch.empty((N, M), dtype=torch.float32, device=dev)
+    gk = torch.empty(pb.K, dtype=torch.float32, device=dev)
+
+    def backward_call():
+        sncc._check(sncc._lib.sncc_diff_backward(fdet.data_ptr(), M, N, fdet.stride(0), W, H, pb.rects.data_ptr(),
+                                                 kdet.data_ptr(), pb.K, rho_k.data_ptr(), rho_t.data_ptr(),
+                                                 dl.data_ptr(), gf.data_ptr(), M, gk.data_ptr(), pb.ws_ptr,
+                                                 pb.ws_bytes, sncc._stream(None)), "sncc_diff_backward")
+
+    def forward_call():
+        sncc._diff_forward(pb, fdet, kdet)
+
+    def timed(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for k in range(reps):
+            flush.fill_(k & 0xff)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    bwd_ms = timed(backward_call)
+    fwd_ms = timed(forward_call)
+    pairs = U * V * W * H
+    bwd_bytes = 16 * pairs  # dL/df: four 4-byte shared reads (a, b, h, h*fbar) per (offset, template pixel)
+    bwd_gbs = bwd_bytes / (bwd_ms * 1e-3) / 1e9
+
     _, losses = sncc.refit_segment_values(pb, fd.detach(), k0, steps=50, lr=0.5)
     value = sum_over_ranks(pg, U * V) / (ms * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import diff as OD
+        rects_np = np.asarray(rects)
+
+        def sample(rows):
+            sub = f[:rows + H - 1]
+            t0_ = time.perf_counter()
+            OD.gradients(sub, t, rects_np, k0)
+            return time.perf_counter() - t0_
+
+        s1 = sample(4)
+        rows = int(max(4, min(V, 4 * args.cpu_seconds / max(s1, 1e-3))))
+        secs = sample(rows)
+        cpu = {"value": rows * U / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "loss and both gradients (FP64 numpy, one thread) over the first %d of %d offset rows"
+                         % (rows, V), "seconds": secs}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "diff-512x512f32-t48x48-sigma12", "segments": int(seg.K),
+                       "l2": "flushed between steps (256 MiB write)",
                        "step": "loss forward + backward w.r.t. segment values and source (kernel launches: "
                                "forward 2, backward 2 + forward 2 recomputed + 4)"},
+            "forward_call_ms": fwd_ms, "backward_call_ms": bwd_ms,
+            "roofline": {"bound": "smem", "kernel": "sncc_diff_backward (diff_coeff, diff_grad_f, diff_gt, diff_grad_k)",
+                         "achieved": bwd_gbs, "peak": ceil["smem_gbs"], "unit": "GB/s",
+                         "frac": bwd_gbs / ceil["smem_gbs"], "traffic": None, "bytes_per_launch": bwd_bytes,
+                         "ms_per_launch": bwd_ms,
+                         "peak_source": "measured: shared-memory read probe (all SMs), this run"},
+            "e2e": {"value": sum_over_ranks(pg, U * V) / (e2e_ms_step * 1e-3) / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": M * N * 4, "d2h_bytes_per_step": 8 + 4 * pb.K, "ms_per_step": e2e_ms_step},
             "refit": {"steps": 50, "loss_first": losses[0], "loss_last": losses[-1]},
-            "gpu_launches": args.steps * 10}
+            "gpu_launches": args.steps * 10, "clocks": clk}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -23,7 +23,12 @@ namespace {
 
 constexpr int kDiffMax = 64;      // largest template edge
 constexpr int kTX = 32, kTY = 8;  // offsets / pixels per CTA tile
-constexpr int kGtChunks = 16;     // offset-row chunks of the Gt correlation
+constexpr int kGtChunks = 64;     // offset-row chunks of the Gt correlation
+constexpr int kGtYB = 16;         // template rows per Gt CTA
+constexpr int kGtXB = 8;          // template columns per Gt thread (register window)
+constexpr int kGtVS = 8;          // offset rows staged at a time
+constexpr int kGtUS = 256;        // offset columns staged at a time
+constexpr int kGtFW = kGtUS + 64;  // staged source row pitch: kGtUS + 8 * kGtXB - 1 columns used
 
 // Workspace layout (bytes), 256-aligned sections.
 struct DiffLayout {
@@ -259,47 +264,97 @@ __global__ void __launch_bounds__(256) diff_grad_f_kernel(const float* __restric
     grad[(size_t)py * gstride + px] = (float)(acc - (double)f[(size_t)py * stride + px] * hsum);
 }
 
-// Partial Gt(x, y) = sum_{o in chunk} a(o) f(o + (x, y)): grid (H, kGtChunks).
-__global__ void __launch_bounds__(256) diff_gt_kernel(const float* __restrict__ f, int M, int N, int stride, int W,
+// Partial Gt(x, y) = sum_{o in chunk} a(o) f(o + (x, y)): grid
+// (ceil(H / kGtYB), kGtChunks), kGtYB * ceil(W / kGtXB) threads; thread
+// (yy, xg) owns template row y0 + yy and columns xg*kGtXB .. +kGtXB-1.  The
+// CTA stages kGtVS offset rows x kGtUS offset columns of a, and the source
+// rows and columns they meet, in shared memory; along u the thread keeps the
+// last kGtXB source values in registers, so each step is one broadcast load
+// of a, one load of f and kGtXB multiply-adds.  Per offset row and column
+// block the products are summed in FP32 (at most kGtUS terms), then in FP64.
+__global__ void __launch_bounds__(128) diff_gt_kernel(const float* __restrict__ f, int M, int N, int stride, int W,
                                                       int H, const float* __restrict__ a, double* __restrict__ gtp) {
-    __shared__ double part[256];
+    __shared__ float fs[(kGtVS + kGtYB - 1) * kGtFW];
+    __shared__ float as[kGtVS * kGtUS];
     const int U = M - W + 1, V = N - H + 1;
-    const int y = blockIdx.x, chunk = blockIdx.y;
-    const int groups = blockDim.x / W;
-    const int x = threadIdx.x % W, gph = threadIdx.x / W;
+    const int XG = (W + kGtXB - 1) / kGtXB;
+    const int y0 = blockIdx.x * kGtYB, chunk = blockIdx.y;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int yy = tid / XG, xg = tid - yy * XG;
+    const int y = y0 + yy, x0 = xg * kGtXB;
+    const bool active = y < H;
     const int vb = (int)((long long)V * chunk / kGtChunks), ve = (int)((long long)V * (chunk + 1) / kGtChunks);
-    double acc = 0.0;
-    if (gph < groups) {
-        for (int v = vb; v < ve; ++v) {
-            const float* arow = a + (size_t)v * U;
-            const float* frow = f + (size_t)(v + y) * stride + x;
-            float r = 0.0f;
-            for (int u = gph; u < U; u += groups) r += arow[u] * frow[u];
-            acc += r;
+    double accd[kGtXB];
+#pragma unroll
+    for (int j = 0; j < kGtXB; ++j) accd[j] = 0.0;
+    for (int vs = vb; vs < ve; vs += kGtVS) {
+        for (int us = 0; us < U; us += kGtUS) {
+            __syncthreads();  // the previous block's reads are done
+            for (int i = tid; i < kGtVS * kGtUS; i += nthr) {
+                const int vv = i / kGtUS, uu = i - vv * kGtUS;
+                const int v = vs + vv, u = us + uu;
+                as[i] = (v < ve && u < U) ? a[(size_t)v * U + u] : 0.0f;
+            }
+            for (int i = tid; i < (kGtVS + kGtYB - 1) * kGtFW; i += nthr) {
+                const int rr = i / kGtFW, cc = i - rr * kGtFW;
+                const int row = vs + y0 + rr, col = us + cc;
+                fs[i] = (row < N && col < M) ? f[(size_t)row * stride + col] : 0.0f;
+            }
+            __syncthreads();
+            if (active) {
+                for (int vv = 0; vv < kGtVS; ++vv) {
+                    const float* fr = fs + (vv + yy) * kGtFW + x0;
+                    const float* ar = as + vv * kGtUS;
+                    float acc[kGtXB], win[kGtXB];
+#pragma unroll
+                    for (int j = 0; j < kGtXB; ++j) acc[j] = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < kGtXB - 1; ++j) win[j] = fr[j];
+                    for (int u = 0; u < kGtUS; u += kGtXB) {
+#pragma unroll
+                        for (int k = 0; k < kGtXB; ++k) {
+                            // win[(k + j) % kGtXB] holds fr[u + k + j]
+                            win[(k + kGtXB - 1) % kGtXB] = fr[u + k + kGtXB - 1];
+                            const float av = ar[u + k];
+#pragma unroll
+                            for (int j = 0; j < kGtXB; ++j) acc[j] += av * win[(k + j) % kGtXB];
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < kGtXB; ++j) accd[j] += acc[j];
+                }
+            }
         }
     }
-    part[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < W) {
-        double s = 0.0;
-        for (int g = 0; g < groups; ++g) s += part[g * W + threadIdx.x];
-        gtp[((size_t)chunk * H + y) * W + threadIdx.x] = s;
+    if (active) {
+#pragma unroll
+        for (int j = 0; j < kGtXB; ++j)
+            if (x0 + j < W) gtp[((size_t)chunk * H + y) * W + x0 + j] = accd[j];
     }
 }
 
+// Gt = the sum of the chunk partials, in a fixed order.
+__global__ void __launch_bounds__(256) diff_gt_reduce_kernel(int T, const double* __restrict__ gtp,
+                                                             double* __restrict__ gt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    double s = 0.0;
+    for (int ch = 0; ch < kGtChunks; ++ch) s += gtp[(size_t)ch * T + i];
+    gt[i] = s;
+}
+
 // dL/dk_j for every segment: sum of Gt over the rectangle, minus the mean and
-// energy terms (one thread per segment; Gt reduced over chunks on the fly).
+// energy terms (one thread per segment).
 __global__ void __launch_bounds__(256) diff_grad_k_kernel(int W, int H, const int4* __restrict__ rects,
                                                           const float* __restrict__ k, int K,
-                                                          const double* __restrict__ gtp, const double* scal,
+                                                          const double* __restrict__ gt, const double* scal,
                                                           float* __restrict__ grad_k) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= K) return;
     const int4 r = rects[j];
     double s = 0.0;
     for (int y = max(r.y, 0); y < min(r.y + r.w, H); ++y)
-        for (int x = max(r.x, 0); x < min(r.x + r.z, W); ++x)
-            for (int ch = 0; ch < kGtChunks; ++ch) s += gtp[((size_t)ch * H + y) * W + x];
+        for (int x = max(r.x, 0); x < min(r.x + r.z, W); ++x) s += gt[(size_t)y * W + x];
     const double nj = (double)r.z * r.w;
     const double cj = (double)k[j] - scal[0];
     grad_k[j] = (float)(s - nj * scal[3] - nj * cj * scal[4] / scal[1]);
@@ -378,8 +433,12 @@ extern "C" int sncc_diff_backward(const float* d_f, int M, int N, int f_stride, 
     dim3 gridf((M + kTX - 1) / kTX, (N + kTY - 1) / kTY);
     diff_grad_f_kernel<<<gridf, 256, smf, st>>>(d_f, M, N, f_stride, W, H, c, t0, a, b, h, hf, d_grad_f,
                                                 grad_f_stride);
-    diff_gt_kernel<<<dim3(H, kGtChunks), 256, 0, st>>>(d_f, M, N, f_stride, W, H, a, gtp);
-    diff_grad_k_kernel<<<(K + 255) / 256, 256, 0, st>>>(W, H, reinterpret_cast<const int4*>(d_rects), d_k, K, gtp,
+    const int gt_threads = kGtYB * ((W + kGtXB - 1) / kGtXB);
+    diff_gt_kernel<<<dim3((H + kGtYB - 1) / kGtYB, kGtChunks), gt_threads, 0, st>>>(d_f, M, N, f_stride, W, H, a,
+                                                                                    gtp);
+    double* gt = reinterpret_cast<double*>(ws + L.gt);
+    diff_gt_reduce_kernel<<<(W * H + 255) / 256, 256, 0, st>>>(W * H, gtp, gt);
+    diff_grad_k_kernel<<<(K + 255) / 256, 256, 0, st>>>(W, H, reinterpret_cast<const int4*>(d_rects), d_k, K, gt,
                                                         scal, d_grad_k);
     return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }

@@ -624,6 +624,7 @@ class DiffProblem:
         self.ws_ptr = self.ws.data_ptr() + off
         self.ws_bytes = nbytes
         self.U, self.V = M - self.W + 1, N - self.H + 1
+        self._ws_holds = None  # (f, k) identity and versions of the forward the workspace holds
 
     def loss(self, f, k):
         """Differentiable L(f, k) (float64 scalar tensor)."""
@@ -638,7 +639,13 @@ def _diff_forward(pb: DiffProblem, f, k):
     _check(_lib.sncc_diff_forward(f.data_ptr(), pb.M, pb.N, f.stride(0), pb.t.data_ptr(), pb.W, pb.H,
                                   pb.rects.data_ptr(), k.data_ptr(), pb.K, rho_k.data_ptr(), rho_t.data_ptr(),
                                   loss.data_ptr(), pb.ws_ptr, pb.ws_bytes, _stream(None)), "sncc_diff_forward")
+    pb._ws_holds = _ws_token(f, k)
     return rho_k, rho_t, loss
+
+
+def _ws_token(f, k):
+    """Identity of a forward's inputs: storage, layout and in-place version."""
+    return (f.data_ptr(), f.stride(0), f._version, k.data_ptr(), k._version)
 
 
 def _make_autograd():
@@ -661,8 +668,10 @@ def _make_autograd():
         def backward(ctx, dloss):
             f, k, rho_k, rho_t = ctx.saved_tensors
             pb = ctx.pb
-            # the workspace must hold this forward's intermediates
-            _diff_forward(pb, f, k)
+            # the workspace must hold this forward's intermediates; it still does
+            # unless another forward ran on it or the inputs changed in place
+            if pb._ws_holds != _ws_token(f, k):
+                _diff_forward(pb, f, k)
             dl = dloss.reshape(1).to(torch.float64).contiguous()
             grad_f = torch.empty((pb.N, pb.M), dtype=torch.float32, device=f.device)
             grad_k = torch.empty(pb.K, dtype=torch.float32, device=f.device)

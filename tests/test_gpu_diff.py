@@ -101,3 +101,34 @@ def test_refit_segment_values_reduces_loss(sncc, problem):
     ref0 = D.forward(f.astype(np.float64), t.astype(np.float64), rects, k0)["loss"]
     ref1 = D.forward(f.astype(np.float64), t.astype(np.float64), rects, k.cpu().numpy().astype(np.float64))["loss"]
     assert ref1 < ref0
+
+
+def test_backward_after_another_forward_on_the_same_workspace(sncc, problem):
+    """Two losses on one DiffProblem, then backward of the first: the
+    workspace holds the second forward, so the first backward must redo its
+    own forward and give the same gradients as a clean forward + backward."""
+    f, t, rects, k0 = problem
+    N, M = f.shape
+    pb = sncc.DiffProblem(t, rects, M, N)
+    k32 = k0.astype(np.float32)
+    fa = torch.as_tensor(f).cuda().requires_grad_(True)
+    ka = torch.as_tensor(k32).cuda().requires_grad_(True)
+    fb = torch.as_tensor(np.ascontiguousarray(f[::-1])).cuda().requires_grad_(True)
+    kb = torch.as_tensor(k32[::-1].copy()).cuda().requires_grad_(True)
+    la = pb.loss(fa, ka)
+    lb = pb.loss(fb, kb)
+    la.backward()
+    lb.backward()
+    fc = torch.as_tensor(f).cuda().requires_grad_(True)
+    kc = torch.as_tensor(k32).cuda().requires_grad_(True)
+    pb.loss(fc, kc).backward()
+    fd2 = torch.as_tensor(np.ascontiguousarray(f[::-1])).cuda().requires_grad_(True)
+    kd2 = torch.as_tensor(k32[::-1].copy()).cuda().requires_grad_(True)
+    pb.loss(fd2, kd2).backward()
+    torch.cuda.synchronize()
+    # dL/df has no cross-block reduction and repeats bit for bit; dL/dk sums
+    # block partials with atomics, so it repeats to rounding
+    assert torch.equal(fa.grad, fc.grad) and torch.equal(fb.grad, fd2.grad)
+    for g1, g2 in ((ka.grad, kc.grad), (kb.grad, kd2.grad)):
+        assert float((g1 - g2).abs().max()) <= 1e-6 * float(g2.abs().max())
+    assert float((ka.grad - kb.grad).abs().max()) > 1e-3 * float(kb.grad.abs().max())
