@@ -903,7 +903,6 @@ def run_gpu_diff(args, world, rank, local, pg):
     e2e_ms_step = max_over_ranks(pg, statistics.mean(e2e_ms))
 
     # the backward call alone (coefficients, dL/df, template-space correlation, dL/dk)
-    ceil = measure_ceilings(sncc, torch, stream, dev)
     fdet, kdet = fd.detach(), kd.detach().contiguous()
     rho_k, rho_t, _ = sncc._diff_forward(pb, fdet, kdet)
     dl = torch.ones(1, dtype=torch.float64, device=dev)
@@ -937,8 +936,11 @@ def run_gpu_diff(args, world, rank, local, pg):
     bwd_ms = timed(backward_call)
     fwd_ms = timed(forward_call)
     pairs = U * V * W * H
-    bwd_bytes = 16 * pairs  # dL/df: four 4-byte shared reads (a, b, h, h*fbar) per (offset, template pixel)
-    bwd_gbs = bwd_bytes / (bwd_ms * 1e-3) / 1e9
+    # algorithmic work of the backward call: per (offset, template pixel) two
+    # FP32 multiply-adds of dL/df (a c and b t0) and one of Gt (a f)
+    bwd_flops = 2 * 3 * pairs
+    bwd_tflops = bwd_flops / (bwd_ms * 1e-3) / 1e12
+    fp32_peak = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 128 FP32 FMA lanes per SM
 
     _, losses = sncc.refit_segment_values(pb, fd.detach(), k0, steps=50, lr=0.5)
     value = sum_over_ranks(pg, U * V) / (ms * 1e-3) / 1e9
@@ -969,11 +971,11 @@ def run_gpu_diff(args, world, rank, local, pg):
                        "step": "loss forward + backward w.r.t. segment values and source (kernel launches: "
                                "forward 2, backward 2 + forward 2 recomputed + 4)"},
             "forward_call_ms": fwd_ms, "backward_call_ms": bwd_ms,
-            "roofline": {"bound": "smem", "kernel": "sncc_diff_backward (diff_coeff, diff_grad_f, diff_gt, diff_grad_k)",
-                         "achieved": bwd_gbs, "peak": ceil["smem_gbs"], "unit": "GB/s",
-                         "frac": bwd_gbs / ceil["smem_gbs"], "traffic": None, "bytes_per_launch": bwd_bytes,
-                         "ms_per_launch": bwd_ms,
-                         "peak_source": "measured: shared-memory read probe (all SMs), this run"},
+            "roofline": {"bound": "alu", "kernel": "sncc_diff_backward (diff_coeff, diff_rowbox, diff_grad_f, diff_gt, "
+                                                    "diff_gt_reduce, diff_grad_k)",
+                         "achieved": bwd_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": bwd_tflops / fp32_peak,
+                         "traffic": None, "flops_per_launch": bwd_flops, "ms_per_launch": bwd_ms,
+                         "peak_source": "152 SMs x 128 FP32 FMA lanes x 2 x 2070 MHz (nominal)"},
             "e2e": {"value": sum_over_ranks(pg, U * V) / (e2e_ms_step * 1e-3) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": M * N * 4, "d2h_bytes_per_step": 8 + 4 * pb.K, "ms_per_step": e2e_ms_step},
             "refit": {"steps": 50, "loss_first": losses[0], "loss_last": losses[-1]},

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "sncc.h"
 #include "sncc_internal.h"
@@ -32,13 +33,14 @@ constexpr int kGtFW = kGtUS + 64;  // staged source row pitch: kGtUS + 8 * kGtXB
 
 // Workspace layout (bytes), 256-aligned sections.
 struct DiffLayout {
-    size_t scal, c, t0, ef, fbar, a, b, h, hf, gtp, gt, total;
+    size_t scal, c, t0, ef, fbar, a, b, h, hf, rh, rhf, gtp, gt, total;
 };
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 DiffLayout diff_layout(int M, int N, int W, int H) {
     const size_t U = (size_t)(M - W + 1), V = (size_t)(N - H + 1), T = (size_t)W * H, UV = U * V;
+    (void)N;
     DiffLayout L;
     size_t o = 0;
     L.scal = o; o = al256(o + 8 * sizeof(double));
@@ -50,6 +52,8 @@ DiffLayout diff_layout(int M, int N, int W, int H) {
     L.b = o; o = al256(o + UV * 4);
     L.h = o; o = al256(o + UV * 4);
     L.hf = o; o = al256(o + UV * 4);
+    L.rh = o; o = al256(o + V * (size_t)M * 4);
+    L.rhf = o; o = al256(o + V * (size_t)M * 4);
     L.gtp = o; o = al256(o + (size_t)kGtChunks * T * sizeof(double));
     L.gt = o; o = al256(o + T * sizeof(double));
     L.total = o;
@@ -209,24 +213,56 @@ __global__ void __launch_bounds__(256) diff_coeff_kernel(int UV, const float* __
     }
 }
 
-// dL/df for a 32 x 8 tile of pixels.  Offsets o = p - x with x in the
-// template; the tile needs offsets in [p0 - (W-1, H-1), p0 + (31, 7)].
-__global__ void __launch_bounds__(256) diff_grad_f_kernel(const float* __restrict__ f, int M, int N, int stride,
-                                                          int W, int H, const float* __restrict__ c,
-                                                          const float* __restrict__ t0, const float* __restrict__ a,
-                                                          const float* __restrict__ b, const float* __restrict__ h,
-                                                          const float* __restrict__ hf, float* __restrict__ grad,
-                                                          int gstride) {
+// Row sums of h and h*fbar over the template width, for the two window-sum
+// terms of dL/df: rh(v, px) = sum_{x < W, 0 <= px-x < U} h(v, px - x) in FP32
+// (x ascending), the same for hf.  Grid (ceil(M / 256), V).
+__global__ void __launch_bounds__(256) diff_rowbox_kernel(int M, int U, int W, const float* __restrict__ h,
+                                                          const float* __restrict__ hf, float* __restrict__ rh,
+                                                          float* __restrict__ rhf) {
+    const int px = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y;
+    if (px >= M) return;
+    const float* hr = h + (size_t)v * U;
+    const float* hfr = hf + (size_t)v * U;
+    float s = 0.0f, sf = 0.0f;
+    for (int x = max(0, px - U + 1); x < min(W, px + 1); ++x) {
+        s += hr[px - x];
+        sf += hfr[px - x];
+    }
+    rh[(size_t)v * M + px] = s;
+    rhf[(size_t)v * M + px] = sf;
+}
+
+// dL/df(p) = sum_x [a(p-x) c(x) - b(p-x) t0(x)] + sum_x hf(p-x) - f(p) sum_x h(p-x)
+// over template positions x with p - x a valid offset.  A CTA covers 64 x 16
+// pixels; thread (ry, gx) owns pixels px0 + 8gx .. +7 of row py0 + ry.  The
+// a and b regions the tile needs are staged in shared memory, with the
+// template's columns reversed (x' = W-1-x, zero-padded to a multiple of 8), so
+// that along x' the thread's eight pixels read one sliding window of eight
+// consecutive region columns: each step loads one new a and one new b value
+// and does 16 multiply-adds.  The h and h*fbar window sums come from the
+// row sums of diff_rowbox_kernel, summed over template rows in FP64.
+constexpr int kGfTX = 64, kGfTY = 16, kGfXB = 8;
+constexpr int kGfThreads = (kGfTX / kGfXB) * kGfTY;
+
+__host__ __device__ inline int gf_w8(int W) { return (W + 7) & ~7; }
+__host__ __device__ inline int gf_rw(int W) { return kGfTX + gf_w8(W) - 1 + 1; }  // region pitch (one spare)
+
+__global__ void __launch_bounds__(kGfThreads) diff_grad_f_kernel(const float* __restrict__ f, int M, int N,
+                                                                 int stride, int W, int H, const float* __restrict__ c,
+                                                                 const float* __restrict__ t0,
+                                                                 const float* __restrict__ a,
+                                                                 const float* __restrict__ b,
+                                                                 const float* __restrict__ rh,
+                                                                 const float* __restrict__ rhf,
+                                                                 float* __restrict__ grad, int gstride) {
     extern __shared__ float sm[];
-    const int RW = kTX + W - 1, RH = kTY + H - 1;
+    const int W8 = gf_w8(W), RW = gf_rw(W), RH = kGfTY + H - 1;
     const int U = M - W + 1, V = N - H + 1;
     float* as = sm;
     float* bs = as + RW * RH;
-    float* hs = bs + RW * RH;
-    float* hfs = hs + RW * RH;
-    float* cs = hfs + RW * RH;
-    float* ts = cs + W * H;
-    const int px0 = blockIdx.x * kTX, py0 = blockIdx.y * kTY;
+    float* cr = bs + RW * RH;  // H x W8, reversed columns
+    float* tr = cr + H * W8;
+    const int px0 = blockIdx.x * kGfTX, py0 = blockIdx.y * kGfTY;
     const int ox0 = px0 - (W - 1), oy0 = py0 - (H - 1);
     for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
         const int Y = i / RW, X = i - Y * RW;
@@ -235,33 +271,60 @@ __global__ void __launch_bounds__(256) diff_grad_f_kernel(const float* __restric
         const size_t o = in ? (size_t)ov * U + ou : 0;
         as[i] = in ? a[o] : 0.0f;
         bs[i] = in ? b[o] : 0.0f;
-        hs[i] = in ? h[o] : 0.0f;
-        hfs[i] = in ? hf[o] : 0.0f;
     }
-    for (int i = threadIdx.x; i < W * H; i += blockDim.x) {
-        cs[i] = c[i];
-        ts[i] = t0[i];
+    for (int i = threadIdx.x; i < H * W8; i += blockDim.x) {
+        const int y = i / W8, xr = i - y * W8;
+        const bool in = xr < W;
+        cr[i] = in ? c[y * W + (W - 1 - xr)] : 0.0f;
+        tr[i] = in ? t0[y * W + (W - 1 - xr)] : 0.0f;
     }
     __syncthreads();
-    const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
-    const int px = px0 + lx, py = py0 + ly;
-    if (px >= M || py >= N) return;
-    double acc = 0.0, hsum = 0.0;
+    const int gx = threadIdx.x % (kGfTX / kGfXB), ry = threadIdx.x / (kGfTX / kGfXB);
+    const int py = py0 + ry, pxb = px0 + gx * kGfXB;
+    if (py >= N || pxb >= M) return;
+    double acc[kGfXB];
+#pragma unroll
+    for (int j = 0; j < kGfXB; ++j) acc[j] = 0.0;
     for (int y = 0; y < H; ++y) {
-        // offset row of template row y: ov = py - y  ->  region row (ly + H - 1 - y)
-        const int rbase = (ly + H - 1 - y) * RW + (lx + W - 1);
-        const float* crow = cs + y * W;
-        const float* trow = ts + y * W;
-        float r = 0.0f, rh = 0.0f;
-        for (int x = 0; x < W; ++x) {
-            const int k = rbase - x;
-            r += as[k] * crow[x] - bs[k] * trow[x] + hfs[k];
-            rh += hs[k];
+        // offset row py - y  ->  region row ry + H - 1 - y; pixel pxb + j, x = W-1-x'
+        // ->  offset column pxb + j - x  ->  region column gx*8 + j + x'
+        const float* arow = as + (ry + H - 1 - y) * RW + gx * kGfXB;
+        const float* brow = bs + (ry + H - 1 - y) * RW + gx * kGfXB;
+        const float* crow = cr + y * W8;
+        const float* trow = tr + y * W8;
+        float r[kGfXB], wa[kGfXB], wb[kGfXB];
+#pragma unroll
+        for (int j = 0; j < kGfXB; ++j) r[j] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kGfXB - 1; ++j) {
+            wa[j] = arow[j];
+            wb[j] = brow[j];
         }
-        acc += r;
-        hsum += rh;
+        for (int xq = 0; xq < W8; xq += kGfXB) {
+#pragma unroll
+            for (int k = 0; k < kGfXB; ++k) {
+                // wa[(k + j) % 8] holds region column xq + k + j
+                wa[(k + kGfXB - 1) % kGfXB] = arow[xq + k + kGfXB - 1];
+                wb[(k + kGfXB - 1) % kGfXB] = brow[xq + k + kGfXB - 1];
+                const float cv = crow[xq + k], tv = trow[xq + k];
+#pragma unroll
+                for (int j = 0; j < kGfXB; ++j) r[j] += wa[(k + j) % kGfXB] * cv - wb[(k + j) % kGfXB] * tv;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kGfXB; ++j) acc[j] += r[j];
     }
-    grad[(size_t)py * gstride + px] = (float)(acc - (double)f[(size_t)py * stride + px] * hsum);
+#pragma unroll
+    for (int j = 0; j < kGfXB; ++j) {
+        const int px = pxb + j;
+        if (px >= M) break;
+        double hs = 0.0, hfs = 0.0;
+        for (int y = max(0, py - V + 1); y < min(H, py + 1); ++y) {
+            hs += rh[(size_t)(py - y) * M + px];
+            hfs += rhf[(size_t)(py - y) * M + px];
+        }
+        grad[(size_t)py * gstride + px] = (float)(acc[j] + hfs - (double)f[(size_t)py * stride + px] * hs);
+    }
 }
 
 // Partial Gt(x, y) = sum_{o in chunk} a(o) f(o + (x, y)): grid
@@ -360,6 +423,18 @@ __global__ void __launch_bounds__(256) diff_grad_k_kernel(int W, int H, const in
     grad_k[j] = (float)(s - nj * scal[3] - nj * cj * scal[4] / scal[1]);
 }
 
+// Opt-in shared-memory limits of the two large-tile kernels (once per process).
+cudaError_t set_diff_attributes() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(diff_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(diff_grad_f_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+    });
+    return err;
+}
+
 bool diff_args_ok(int M, int N, int W, int H, int K, int f_stride) {
     return M > 0 && N > 0 && W > 0 && H > 0 && W <= kDiffMax && H <= kDiffMax && W <= M && H <= N && K > 0 &&
            K <= W * H && f_stride >= M && 256 / W >= 1;
@@ -390,12 +465,7 @@ extern "C" int sncc_diff_forward(const float* d_f, int M, int N, int f_stride, c
     diff_prep_kernel<<<1, 256, 0, st>>>(d_t, W, H, reinterpret_cast<const int4*>(d_rects), d_k, K, scal, c, t0);
     const int U = M - W + 1, V = N - H + 1;
     const size_t sm = ((size_t)(kTX + W - 1) * (kTY + H - 1) + 2 * (size_t)W * H) * 4;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(diff_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        cudaFuncSetAttribute(diff_grad_f_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr_done = true;
-    }
+    if (set_diff_attributes() != cudaSuccess) return SNCC_ERR_CUDA;
     dim3 grid((U + kTX - 1) / kTX, (V + kTY - 1) / kTY);
     diff_forward_kernel<<<grid, 256, sm, st>>>(d_f, M, N, f_stride, W, H, c, t0, scal, d_rho_k, d_rho_t,
                                                reinterpret_cast<float*>(ws + L.ef),
@@ -424,15 +494,19 @@ extern "C" int sncc_diff_backward(const float* d_f, int M, int N, int f_stride, 
     cudaStream_t st = (cudaStream_t)stream;
     const int U = M - W + 1, V = N - H + 1;
     const int UV = U * V;
+    if (set_diff_attributes() != cudaSuccess) return SNCC_ERR_CUDA;
     // A1, A2 are accumulated from zero (scal[3], scal[4])
     if (cudaMemsetAsync(scal + 3, 0, 2 * sizeof(double), st) != cudaSuccess) return SNCC_ERR_CUDA;
     diff_coeff_kernel<<<(UV + 255) / 256, 256, 0, st>>>(UV, d_rho_k, d_rho_t, reinterpret_cast<const float*>(ws + L.ef),
                                                         reinterpret_cast<const float*>(ws + L.fbar), d_dloss, scal, a,
                                                         b, h, hf);
-    const size_t smf = (4 * (size_t)(kTX + W - 1) * (kTY + H - 1) + 2 * (size_t)W * H) * 4;
-    dim3 gridf((M + kTX - 1) / kTX, (N + kTY - 1) / kTY);
-    diff_grad_f_kernel<<<gridf, 256, smf, st>>>(d_f, M, N, f_stride, W, H, c, t0, a, b, h, hf, d_grad_f,
-                                                grad_f_stride);
+    float* rh = reinterpret_cast<float*>(ws + L.rh);
+    float* rhf = reinterpret_cast<float*>(ws + L.rhf);
+    diff_rowbox_kernel<<<dim3((M + 255) / 256, V), 256, 0, st>>>(M, U, W, h, hf, rh, rhf);
+    const size_t smf = (2 * (size_t)gf_rw(W) * (kGfTY + H - 1) + 2 * (size_t)H * gf_w8(W)) * 4;
+    dim3 gridf((M + kGfTX - 1) / kGfTX, (N + kGfTY - 1) / kGfTY);
+    diff_grad_f_kernel<<<gridf, kGfThreads, smf, st>>>(d_f, M, N, f_stride, W, H, c, t0, a, b, rh, rhf, d_grad_f,
+                                                       grad_f_stride);
     const int gt_threads = kGtYB * ((W + kGtXB - 1) / kGtXB);
     diff_gt_kernel<<<dim3((H + kGtYB - 1) / kGtYB, kGtChunks), gt_threads, 0, st>>>(d_f, M, N, f_stride, W, H, a,
                                                                                     gtp);

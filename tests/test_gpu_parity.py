@@ -139,12 +139,19 @@ def test_match_map_and_candidates(sncc, M, N, W, H, sigma):
     check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, tau)
 
 
+@pytest.mark.parametrize("M,N,W,H", [(200, 150, 48, 40), (300, 260, 130, 129), (420, 150, 97, 65)])
 @pytest.mark.parametrize("bits", [32, 64])
-def test_match_table_width_independent(sncc, bits):
-    """The same source through 32- and 64-bit sum tables gives one map."""
-    c = synth.case_plain(M=200, N=150, W=48, H=40)
+def test_match_table_width_independent(sncc, bits, M, N, W, H):
+    """The same source through 32- and 64-bit sum tables gives one map.  The
+    multi-block templates use 32 x 32 blocks with 32-bit tables and 64 x 64
+    blocks with 64-bit ones (ragged edge blocks; tiles inside the table and
+    on its edge)."""
+    c = synth.case_plain(M=M, N=N, W=W, H=H, seed=11 + W)
     ap = O.precompute_template_approximation(c.t, 7.0)
-    _, _, _, mb = run_match(sncc, c.f, c.t, 7.0, 0.5, s_bits=bits)
+    seg, _, _, mb = run_match(sncc, c.f, c.t, 7.0, 0.5, s_bits=bits)
+    if W > 64 or H > 64:
+        pi = seg.plan_info()
+        assert pi["blocks"] > 1 and pi["wide_blocks"] > 1 and pi["wide_blocks"] < pi["blocks"]
     ref = O.segmented_ncc_map(c.f, ap, "sat")
     assert np.abs(mb.rho.cpu().numpy() - ref).max() <= TOL
 
