@@ -24,10 +24,10 @@ namespace {
 
 constexpr int kDiffMax = 64;      // largest template edge
 constexpr int kTX = 32, kTY = 8;  // offsets / pixels per CTA tile
-constexpr int kGtChunks = 64;     // offset-row chunks of the Gt correlation
+constexpr int kGtChunks = 192;    // offset-row chunks of the Gt correlation
 constexpr int kGtYB = 16;         // template rows per Gt CTA
 constexpr int kGtXB = 8;          // template columns per Gt thread (register window)
-constexpr int kGtVS = 8;          // offset rows staged at a time
+constexpr int kGtVS = 4;          // offset rows staged at a time
 constexpr int kGtUS = 256;        // offset columns staged at a time
 constexpr int kGtFW = kGtUS + 64;  // staged source row pitch: kGtUS + 8 * kGtXB - 1 columns used
 
@@ -234,20 +234,30 @@ __global__ void __launch_bounds__(256) diff_rowbox_kernel(int M, int U, int W, c
 
 // dL/df(p) = sum_x [a(p-x) c(x) - b(p-x) t0(x)] + sum_x hf(p-x) - f(p) sum_x h(p-x)
 // over template positions x with p - x a valid offset.  A CTA covers 64 x 16
-// pixels; thread (ry, gx) owns pixels px0 + 8gx .. +7 of row py0 + ry.  The
-// a and b regions the tile needs are staged in shared memory, with the
-// template's columns reversed (x' = W-1-x, zero-padded to a multiple of 8), so
-// that along x' the thread's eight pixels read one sliding window of eight
-// consecutive region columns: each step loads one new a and one new b value
-// and does 16 multiply-adds.  The h and h*fbar window sums come from the
-// row sums of diff_rowbox_kernel, summed over template rows in FP64.
-constexpr int kGfTX = 64, kGfTY = 16, kGfXB = 8;
-constexpr int kGfThreads = (kGfTX / kGfXB) * kGfTY;
+// pixels with kGfYG groups of threads; thread (g, ry, gx) owns pixels
+// px0 + 8gx .. +7 of row py0 + ry for the template rows y = g, g + kGfYG, ...,
+// and the groups' partial sums meet in shared memory at the end.  The a and b
+// regions the tile needs are staged in shared memory, with the template's
+// columns reversed (x' = W-1-x, zero-padded to a multiple of 8), so that along
+// x' the thread's eight pixels read one sliding window of eight consecutive
+// region columns: each step loads one new a and one new b value and does 16
+// multiply-adds.  The h and h*fbar window sums come from the row sums of
+// diff_rowbox_kernel, summed over template rows in FP64.
+constexpr int kGfTX = 64, kGfTY = 16, kGfXB = 8, kGfYG = 4;
+constexpr int kGfGroup = (kGfTX / kGfXB) * kGfTY;  // threads of one group
+constexpr int kGfThreads = kGfGroup * kGfYG;
 
 __host__ __device__ inline int gf_w8(int W) { return (W + 7) & ~7; }
 __host__ __device__ inline int gf_rw(int W) { return kGfTX + gf_w8(W) - 1 + 1; }  // region pitch (one spare)
+// dynamic shared memory: the staged a, b regions and reversed c, t0, or the
+// partial sums of groups 1.. (whichever is larger)
+__host__ __device__ inline size_t gf_smem(int W, int H) {
+    const size_t stage = (2 * (size_t)gf_rw(W) * (kGfTY + H - 1) + 2 * (size_t)H * gf_w8(W)) * 4;
+    const size_t part = (size_t)(kGfYG - 1) * kGfGroup * kGfXB * 8;
+    return stage > part ? stage : part;
+}
 
-__global__ void __launch_bounds__(kGfThreads) diff_grad_f_kernel(const float* __restrict__ f, int M, int N,
+__global__ void __launch_bounds__(kGfThreads, 2) diff_grad_f_kernel(const float* __restrict__ f, int M, int N,
                                                                  int stride, int W, int H, const float* __restrict__ c,
                                                                  const float* __restrict__ t0,
                                                                  const float* __restrict__ a,
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(kGfThreads) diff_grad_f_kernel(const float* __
                                                                  const float* __restrict__ rh,
                                                                  const float* __restrict__ rhf,
                                                                  float* __restrict__ grad, int gstride) {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     const int W8 = gf_w8(W), RW = gf_rw(W), RH = kGfTY + H - 1;
     const int U = M - W + 1, V = N - H + 1;
     float* as = sm;
@@ -279,40 +289,55 @@ __global__ void __launch_bounds__(kGfThreads) diff_grad_f_kernel(const float* __
         tr[i] = in ? t0[y * W + (W - 1 - xr)] : 0.0f;
     }
     __syncthreads();
-    const int gx = threadIdx.x % (kGfTX / kGfXB), ry = threadIdx.x / (kGfTX / kGfXB);
+    const int grp = threadIdx.x / kGfGroup, t = threadIdx.x - grp * kGfGroup;
+    const int gx = t % (kGfTX / kGfXB), ry = t / (kGfTX / kGfXB);
     const int py = py0 + ry, pxb = px0 + gx * kGfXB;
-    if (py >= N || pxb >= M) return;
     double acc[kGfXB];
 #pragma unroll
     for (int j = 0; j < kGfXB; ++j) acc[j] = 0.0;
-    for (int y = 0; y < H; ++y) {
-        // offset row py - y  ->  region row ry + H - 1 - y; pixel pxb + j, x = W-1-x'
-        // ->  offset column pxb + j - x  ->  region column gx*8 + j + x'
-        const float* arow = as + (ry + H - 1 - y) * RW + gx * kGfXB;
-        const float* brow = bs + (ry + H - 1 - y) * RW + gx * kGfXB;
-        const float* crow = cr + y * W8;
-        const float* trow = tr + y * W8;
-        float r[kGfXB], wa[kGfXB], wb[kGfXB];
+    if (py < N && pxb < M) {
+        for (int y = grp; y < H; y += kGfYG) {
+            // offset row py - y  ->  region row ry + H - 1 - y; pixel pxb + j, x = W-1-x'
+            // ->  offset column pxb + j - x  ->  region column gx*8 + j + x'
+            const float* arow = as + (ry + H - 1 - y) * RW + gx * kGfXB;
+            const float* brow = bs + (ry + H - 1 - y) * RW + gx * kGfXB;
+            const float* crow = cr + y * W8;
+            const float* trow = tr + y * W8;
+            float r[kGfXB], wa[kGfXB], wb[kGfXB];
 #pragma unroll
-        for (int j = 0; j < kGfXB; ++j) r[j] = 0.0f;
+            for (int j = 0; j < kGfXB; ++j) r[j] = 0.0f;
 #pragma unroll
-        for (int j = 0; j < kGfXB - 1; ++j) {
-            wa[j] = arow[j];
-            wb[j] = brow[j];
-        }
-        for (int xq = 0; xq < W8; xq += kGfXB) {
-#pragma unroll
-            for (int k = 0; k < kGfXB; ++k) {
-                // wa[(k + j) % 8] holds region column xq + k + j
-                wa[(k + kGfXB - 1) % kGfXB] = arow[xq + k + kGfXB - 1];
-                wb[(k + kGfXB - 1) % kGfXB] = brow[xq + k + kGfXB - 1];
-                const float cv = crow[xq + k], tv = trow[xq + k];
-#pragma unroll
-                for (int j = 0; j < kGfXB; ++j) r[j] += wa[(k + j) % kGfXB] * cv - wb[(k + j) % kGfXB] * tv;
+            for (int j = 0; j < kGfXB - 1; ++j) {
+                wa[j] = arow[j];
+                wb[j] = brow[j];
             }
-        }
+            for (int xq = 0; xq < W8; xq += kGfXB) {
 #pragma unroll
-        for (int j = 0; j < kGfXB; ++j) acc[j] += r[j];
+                for (int k = 0; k < kGfXB; ++k) {
+                    // wa[(k + j) % 8] holds region column xq + k + j
+                    wa[(k + kGfXB - 1) % kGfXB] = arow[xq + k + kGfXB - 1];
+                    wb[(k + kGfXB - 1) % kGfXB] = brow[xq + k + kGfXB - 1];
+                    const float cv = crow[xq + k], tv = trow[xq + k];
+#pragma unroll
+                    for (int j = 0; j < kGfXB; ++j) r[j] += wa[(k + j) % kGfXB] * cv - wb[(k + j) % kGfXB] * tv;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kGfXB; ++j) acc[j] += r[j];
+        }
+    }
+    // groups 1.. hand their partial sums to group 0 (the staging area is free now)
+    __syncthreads();
+    double* part = reinterpret_cast<double*>(sm);
+    if (grp > 0) {
+#pragma unroll
+        for (int j = 0; j < kGfXB; ++j) part[((size_t)(grp - 1) * kGfXB + j) * kGfGroup + t] = acc[j];
+    }
+    __syncthreads();
+    if (grp > 0 || py >= N || pxb >= M) return;
+    for (int g = 1; g < kGfYG; ++g) {
+#pragma unroll
+        for (int j = 0; j < kGfXB; ++j) acc[j] += part[((size_t)(g - 1) * kGfXB + j) * kGfGroup + t];
     }
 #pragma unroll
     for (int j = 0; j < kGfXB; ++j) {
@@ -330,7 +355,7 @@ __global__ void __launch_bounds__(kGfThreads) diff_grad_f_kernel(const float* __
 // Partial Gt(x, y) = sum_{o in chunk} a(o) f(o + (x, y)): grid
 // (ceil(H / kGtYB), kGtChunks), kGtYB * ceil(W / kGtXB) threads; thread
 // (yy, xg) owns template row y0 + yy and columns xg*kGtXB .. +kGtXB-1.  The
-// CTA stages kGtVS offset rows x kGtUS offset columns of a, and the source
+// CTA stages up to kGtVS offset rows x kGtUS offset columns of a, and the source
 // rows and columns they meet, in shared memory; along u the thread keeps the
 // last kGtXB source values in registers, so each step is one broadcast load
 // of a, one load of f and kGtXB multiply-adds.  Per offset row and column
@@ -503,7 +528,7 @@ extern "C" int sncc_diff_backward(const float* d_f, int M, int N, int f_stride, 
     float* rh = reinterpret_cast<float*>(ws + L.rh);
     float* rhf = reinterpret_cast<float*>(ws + L.rhf);
     diff_rowbox_kernel<<<dim3((M + 255) / 256, V), 256, 0, st>>>(M, U, W, h, hf, rh, rhf);
-    const size_t smf = (2 * (size_t)gf_rw(W) * (kGfTY + H - 1) + 2 * (size_t)H * gf_w8(W)) * 4;
+    const size_t smf = gf_smem(W, H);
     dim3 gridf((M + kGfTX - 1) / kGfTX, (N + kGfTY - 1) / kGfTY);
     diff_grad_f_kernel<<<gridf, kGfThreads, smf, st>>>(d_f, M, N, f_stride, W, H, c, t0, a, b, rh, rhf, d_grad_f,
                                                        grad_f_stride);
