@@ -3,21 +3,23 @@
 // Layout: padded tables of (N+1) rows x pitch elements, entry [Y*pitch + X]
 // = sum of f over x < X, y < Y (row 0 and column 0 are zero).
 //
-// The table is produced in tiles of (band of R rows) x (chunk of 1024
-// columns), so that every tile is independent once two kinds of carry are
-// known:
+// The table is produced band by band (R rows each).  A band is independent
+// once its column carries are known:
 //   1. band column sums: for every band and column, the sum of f (and f^2)
 //      over the band's rows;
 //   2. band scan: exclusive prefix of those over the bands, i.e. for every
 //      band and column the sum of the column above the band;
-//   3. row carries (one warp per row): for every row and chunk, the sum of the
-//      row left of the chunk;
-//   4. tile emit (one CTA of 256 threads per tile, four output columns per
-//      thread, 16-byte stores): s(X, Y) = corner + sum of the row carries of
-//      the band's rows so far + CTA-wide prefix over the tile of the running
-//      column sums, where corner = the band's column carries left of the tile.
+//   3. band emit (one CTA of 8 warps per band): the band's columns are cut
+//      into 256-column tiles, one lane per 8 output columns.  The CTA first
+//      sums, per tile, the column carries and every row's own values, and
+//      prefixes those sums over the tiles (the corner above-left of each tile
+//      and each row's sum left of it); then each warp walks its tiles row by
+//      row: running column sums in registers, a lane prefix and one warp scan
+//      per row (no CTA barrier), values relative to the tile in int32 and the
+//      carries added in int64, and 16-byte stores.
 // Algorithmic traffic: 1 B/px read, 4 or 8 B/px (s) + 8 B/px (s^2) written;
-// passes 1 and 3 read f once more each, and the carries are small arrays.
+// pass 1 and the emit's first phase read f once more each (from L2), and the
+// carries are small arrays.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -29,23 +31,28 @@
 namespace sncc {
 namespace {
 
-constexpr int kThreads = 256;             // threads per emit CTA
-constexpr int kPer = 4;                   // source columns per emit thread
-constexpr int kChunk = kThreads * kPer;   // columns per tile
-constexpr int kTargetTiles = 8 * 152;     // about eight emit CTAs per SM
+constexpr int kEmitWarps = 8;                 // warps per band-emit CTA
+constexpr int kLaneCols = 8;                  // output columns per lane
+constexpr int kTileCols = 32 * kLaneCols;     // output columns per warp tile
+constexpr int kMaxTiles = 16384 / kTileCols;  // tiles of the widest table (M + 1 <= 16384)
+constexpr int kMaxR = 64;                     // rows per band at most
+constexpr int kTargetTiles = 32 * 152;        // about 32 warp tiles (band x 256 columns) per SM
 
 struct SatGeometry {
     int R;   // rows per band
     int nb;  // bands
-    int nc;  // column chunks
+    int nc;  // 256-column tiles per band
 };
 
 SatGeometry sat_geometry(int M, int N) {
     SatGeometry g;
-    g.nc = (M + 1 + kChunk - 1) / kChunk;  // chunks cover output columns 0 .. M
+    g.nc = (M + 1 + kTileCols - 1) / kTileCols;  // tiles cover output columns 0 .. M
+    // bands of R rows with about kTargetTiles warp tiles in all; the column-sum
+    // workspace is then 2 * (N / R) * M * 4 bytes <= about 12.6 MB for any
+    // source up to 10^8 pixels
     long long r = ((long long)N * g.nc + kTargetTiles - 1) / kTargetTiles;
     if (r < 2) r = 2;
-    if (r > 64) r = 64;
+    if (r > kMaxR) r = kMaxR;
     if (r > N) r = N;
     g.R = (int)r;
     g.nb = (N + g.R - 1) / g.R;
@@ -62,21 +69,26 @@ __global__ void sat_band_colsum(const uint8_t* __restrict__ f, int M, int N, int
     const int y1 = min(y0 + R, N);
     int a0 = 0, a1 = 0, a2 = 0, a3 = 0, q0 = 0, q1 = 0, q2 = 0, q3 = 0;
     const bool vec = (x0 + 3 < M) && ((stride & 3) == 0) && ((reinterpret_cast<uintptr_t>(f) & 3) == 0);
-    for (int y = y0; y < y1; ++y) {
+    auto word = [&](int y) -> uint32_t {
         const uint8_t* row = f + (size_t)y * stride;
-        int p0, p1, p2, p3;
-        if (vec) {
-            const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(row + x0));
-            p0 = w & 0xff; p1 = (w >> 8) & 0xff; p2 = (w >> 16) & 0xff; p3 = w >> 24;
-        } else {
-            p0 = row[x0];
-            p1 = (x0 + 1 < M) ? row[x0 + 1] : 0;
-            p2 = (x0 + 2 < M) ? row[x0 + 2] : 0;
-            p3 = (x0 + 3 < M) ? row[x0 + 3] : 0;
-        }
+        if (vec) return __ldg(reinterpret_cast<const uint32_t*>(row + x0));
+        uint32_t w = row[x0];
+        if (x0 + 1 < M) w |= (uint32_t)row[x0 + 1] << 8;
+        if (x0 + 2 < M) w |= (uint32_t)row[x0 + 2] << 16;
+        if (x0 + 3 < M) w |= (uint32_t)row[x0 + 3] << 24;
+        return w;
+    };
+    auto add = [&](uint32_t w) {
+        const int p0 = w & 0xff, p1 = (w >> 8) & 0xff, p2 = (w >> 16) & 0xff, p3 = w >> 24;
         a0 += p0; a1 += p1; a2 += p2; a3 += p3;
         q0 += p0 * p0; q1 += p1 * p1; q2 += p2 * p2; q3 += p3 * p3;
+    };
+    int y = y0;
+    for (; y + 4 <= y1; y += 4) {  // four rows of loads in flight
+        const uint32_t w0 = word(y), w1 = word(y + 1), w2 = word(y + 2), w3 = word(y + 3);
+        add(w0); add(w1); add(w2); add(w3);
     }
+    for (; y < y1; ++y) add(word(y));
     int32_t* o1 = cs1 + (size_t)b * M + x0;
     int32_t* o2 = cs2 + (size_t)b * M + x0;
     o1[0] = a0; o2[0] = q0;
@@ -86,15 +98,17 @@ __global__ void sat_band_colsum(const uint8_t* __restrict__ f, int M, int N, int
 }
 
 // Pass 2: in place, cs[b][x] := sum_{b' < b} cs[b'][x] (exclusive over bands).
-// One CTA per 32 columns: lane = column (coalesced rows), warp w owns a
-// contiguous chunk of bands; chunk totals are exchanged through shared memory
-// so every warp walks only nb/8 bands, twice.
-__global__ void __launch_bounds__(256) sat_band_scan(int M, int nb, int32_t* __restrict__ cs1,
-                                                     int32_t* __restrict__ cs2) {
-    __shared__ int32_t tot1[8][32], tot2[8][32];
+// One CTA per 32 columns: lane = column (coalesced rows), warp w of 32 owns a
+// contiguous run of bands; run totals are exchanged through shared memory,
+// so every warp walks only nb/32 bands, twice.
+constexpr int kScanWarps = 32;
+
+__global__ void __launch_bounds__(kScanWarps * 32) sat_band_scan(int M, int nb, int32_t* __restrict__ cs1,
+                                                                 int32_t* __restrict__ cs2) {
+    __shared__ int32_t tot1[kScanWarps][32], tot2[kScanWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = blockIdx.x * 32 + lane;
-    const int per = (nb + 7) / 8;
+    const int per = (nb + kScanWarps - 1) / kScanWarps;
     const int b0 = min(warp * per, nb), b1 = min(b0 + per, nb);
     int32_t s1 = 0, s2 = 0;
     if (x < M) {
@@ -142,206 +156,270 @@ __global__ void __launch_bounds__(256) sat_band_scan(int M, int nb, int32_t* __r
     }
 }
 
-// Pass 3: rc[c][y] = sum of f (f^2) over source columns x < 1024c of row y.
-// One warp per row: lane l reads bytes 1024c + 32l .. 32l+31 of each chunk,
-// the warp reduces the chunk sums, and lane 0 writes their exclusive prefix.
-// Chunk sums fit int32 (M <= 16383).
-__global__ void __launch_bounds__(256) sat_row_carry(const uint8_t* __restrict__ f, int M, int N, int stride,
-                                                     int nc, int32_t* __restrict__ rc1, int32_t* __restrict__ rc2) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int y = blockIdx.x * 8 + warp;
-    if (y >= N) return;  // warp-uniform; no CTA barrier below
-    const uint8_t* row = f + (size_t)y * stride;
-    const bool vec = ((stride & 15) == 0) && ((reinterpret_cast<uintptr_t>(f) & 15) == 0);
-    int32_t run1 = 0, run2 = 0;
-    for (int c = 0; c < nc; ++c) {
-        const int xb = c * kChunk + lane * 32;
-        int s1 = 0, s2 = 0;
-        if (vec && xb + 31 < M) {
-            const uint4* q = reinterpret_cast<const uint4*>(row + xb);
+// Pass 3: one CTA per band b.  Output column X of the table holds sources
+// x < X, so tile c (outputs X = 256c .. 256c+255) owns the sources
+// x = 256c - 1 .. 256c + 254, and lane l of a tile the sources
+// 256c + 8l - 1 .. 256c + 8l + 6.  For output (X, Y) of the band, Y = y + 1:
+//   s = [x < 256c-1, y < y0]        corner[c]        (prefix of P over tiles)
+//     + [x < 256c-1, y0 <= y' <= y] sum of left[c][y'] (prefix of T over tiles)
+//     + [own x <= X-1, y < y0]      top carry of the lane's column
+//     + [own x <= X-1, y0 <= y' <= y] running column sums, prefixed along the tile.
+// The first two come from the CTA's first phase (P: a tile's column carries
+// summed; T: a tile's own values of one row summed), the last two from a lane
+// prefix plus a warp scan.  Relative sums of one band and tile stay below
+// 256 * 64 * 65025 < 2^31.
+
+// Raw source bytes xa .. xa+7 of a row (zero from column M on), one 8-byte
+// load when aligned and inside the row.
+__device__ __forceinline__ uint2 load_word(const uint8_t* row, int M, int xa, bool vec) {
+    if (vec && xa + 7 < M) return __ldg(reinterpret_cast<const uint2*>(row + xa));
+    uint32_t lo = 0, hi = 0;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint4 w = __ldg(q + h);
-                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int a = (ws[i] >> (8 * k)) & 0xff;
-                        s1 += a;
-                        s2 += a * a;
-                    }
-            }
-        } else {
-            for (int k = 0; k < 32; ++k)
-                if (xb + k < M) {
-                    const int v = row[xb + k];
-                    s1 += v;
-                    s2 += v * v;
-                }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        }
-        if (lane == 0) {
-            rc1[(size_t)c * N + y] = run1;
-            rc2[(size_t)c * N + y] = run2;
-        }
-        run1 += s1;
-        run2 += s2;
+    for (int e = 0; e < 8; ++e) {
+        const uint32_t b = (xa + e < M) ? row[xa + e] : 0u;
+        if (e < 4) lo |= b << (8 * e); else hi |= b << (8 * (e - 4));
     }
+    return make_uint2(lo, hi);
 }
 
-// Inclusive CTA-wide scan of two 64-bit values.  All threads call it; sm is
-// one of two scratch copies that callers alternate (see below).
-__device__ __forceinline__ void block_scan2(int64_t& a, int64_t& b, int64_t* sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Lane l of a tile starting at output column X0 owns the sources
+// x = X0 + 8l - 1 .. X0 + 8l + 6: bytes 0..6 of its own word (xa = X0 + 8l)
+// and byte 7 of the previous lane's word; lane 0 reads x = X0 - 1 itself.
+struct LaneRow {
+    uint2 w;
+    int edge;  // lane 0: source X0 - 1 (0 outside the row); other lanes unused
+};
+
+__device__ __forceinline__ LaneRow load_lane_row(const uint8_t* row, int M, int X0, int lane, bool vec) {
+    const int xa = X0 + kLaneCols * lane;
+    LaneRow r;
+    r.w = load_word(row, M, xa, vec);
+    r.edge = (lane == 0 && xa >= 1 && xa - 1 < M) ? row[xa - 1] : 0;
+    return r;
+}
+
+__device__ __forceinline__ void unpack_lane_row(const LaneRow& r, int lane, int (&v)[8]) {
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, r.w.y, 1);
+    v[0] = (lane > 0) ? (int)(prev >> 24) : r.edge;
+#pragma unroll
+    for (int e = 1; e < 8; ++e)
+        v[e] = (int)(((e - 1 < 4) ? (r.w.x >> (8 * (e - 1))) : (r.w.y >> (8 * (e - 5)))) & 0xff);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_exclusive_scan(T v, int lane) {
+    T inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int64_t ta = __shfl_up_sync(0xffffffffu, a, o);
-        const int64_t tb = __shfl_up_sync(0xffffffffu, b, o);
-        if (lane >= o) { a += ta; b += tb; }
+        const T t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
     }
-    if (lane == 31) { sm[warp] = a; sm[32 + warp] = b; }
-    __syncthreads();
-    if (warp == 0) {
-        int64_t wa = (lane < nw) ? sm[lane] : 0, wb = (lane < nw) ? sm[32 + lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t ta = __shfl_up_sync(0xffffffffu, wa, o);
-            const int64_t tb = __shfl_up_sync(0xffffffffu, wb, o);
-            if (lane >= o) { wa += ta; wb += tb; }
-        }
-        if (lane < nw) { sm[64 + lane] = wa; sm[96 + lane] = wb; }
-    }
-    __syncthreads();
-    if (warp > 0) { a += sm[64 + warp - 1]; b += sm[96 + warp - 1]; }
-    // no trailing barrier: callers alternate between two scratch copies, and
-    // the next use of this copy is two scans (and two barriers) later
+    return inc - v;
 }
 
-// Pass 4: one CTA per tile (chunk c = blockIdx.x, band b = blockIdx.y).
-// Thread t owns output columns X = 1024c + 4t .. 4t+3 (16-byte aligned
-// stores), i.e. source columns x = X - 1; the tile's inputs therefore start
-// at x = 1024c - 1, and the left carry is the table at X = 1024c - 1:
-//   corner  = sum_{x < 1024c-1} (column sums above the band),
-//   row y   : sum_{x < 1024c-1} f(x, y) = rc[c][y] - f(1024c - 1, y).
+constexpr int kAhead = 4;  // source rows in flight per warp
+constexpr int kLaneStride = 80;  // staging bytes per lane: up to 64 data + 16 pad (conflict-free quarter-warps)
+constexpr int kStageBytes = 32 * kLaneStride;
+
+// Writes the lane's eight outputs a + col[0], a + col[0] + col[1], ... (as T)
+// into the warp's staging buffer, then the warp stores the 256 values of the
+// tile row to dst with 16-byte lane-consecutive stores (512 bytes each).
+template <typename T>
+__device__ __forceinline__ void stage_row(unsigned char* stage, int lane, const int32_t (&col)[kLaneCols], int64_t a,
+                                          T* dst) {
+    T o[kLaneCols];
+#pragma unroll
+    for (int e = 0; e < kLaneCols; ++e) {
+        a += col[e];
+        o[e] = (T)a;
+    }
+    unsigned char* mine = stage + lane * kLaneStride;
+#pragma unroll
+    for (int k = 0; k < (int)(kLaneCols * sizeof(T)) / 16; ++k)
+        *reinterpret_cast<int4*>(mine + 16 * k) = *reinterpret_cast<const int4*>(reinterpret_cast<const char*>(o) + 16 * k);
+    __syncwarp();
+    constexpr int rowbytes = kTileCols * (int)sizeof(T);
+#pragma unroll
+    for (int j = 0; j < rowbytes / 512; ++j) {
+        const int byte = 16 * lane + 512 * j;  // logical offset in the tile row
+        const int4 v = *reinterpret_cast<const int4*>(stage + (byte / (kLaneCols * (int)sizeof(T))) * kLaneStride +
+                                                      byte % (kLaneCols * (int)sizeof(T)));
+        *reinterpret_cast<int4*>(reinterpret_cast<char*>(dst) + byte) = v;
+    }
+    __syncwarp();
+}
+
 template <typename ST>
-__global__ void __launch_bounds__(kThreads) sat_tile_emit(const uint8_t* __restrict__ f, int M, int N, int stride,
-                                                          int R, int pitch, const int32_t* __restrict__ cs1,
-                                                          const int32_t* __restrict__ cs2,
-                                                          const int32_t* __restrict__ rc1,
-                                                          const int32_t* __restrict__ rc2, ST* __restrict__ s,
-                                                          int64_t* __restrict__ s2) {
-    __shared__ int64_t sm[2][128];
-    __shared__ int32_t rcs1[64], rcs2[64];
-    const int c = blockIdx.x, b = blockIdx.y, t = threadIdx.x;
-    const int lane = t & 31;
-    const int X0 = c * kChunk;          // first output column of the tile
-    const int Xt = X0 + kPer * t;       // this thread's first output column
-    const int xe = X0 - 1;              // the source column just left of the tile's own
-    const int y0 = b * R, y1 = min(y0 + R, N);
-    // corner = column sums above the band over x < X0 - 1
-    int64_t k1 = 0, k2 = 0;
-    for (int i = t; i < xe; i += kThreads) {
-        k1 += cs1[(size_t)b * M + i];
-        k2 += cs2[(size_t)b * M + i];
-    }
-    if (t < y1 - y0) {  // the band's row carries, to shared memory
-        rcs1[t] = rc1[(size_t)c * N + y0 + t];
-        rcs2[t] = rc2[(size_t)c * N + y0 + t];
-    }
-    block_scan2(k1, k2, sm[0]);  // inclusive: the last thread holds the totals
-    __syncthreads();
-    if (t == kThreads - 1) { sm[1][0] = k1; sm[1][1] = k2; }
-    __syncthreads();
-    int64_t left1 = sm[1][0], left2 = sm[1][1];
-    __syncthreads();
-    int32_t col1[kPer], col2[kPer];
+__global__ void __launch_bounds__(kEmitWarps * 32, 3) sat_band_emit(const uint8_t* __restrict__ f, int M, int N,
+                                                                 int stride, int R, int nc, int pitch,
+                                                                 const int32_t* __restrict__ ca1,
+                                                                 const int32_t* __restrict__ ca2,
+                                                                 ST* __restrict__ s, int64_t* __restrict__ s2) {
+    extern __shared__ __align__(16) unsigned char emit_smem[];
+    // per-warp output staging (lane stride 80 bytes: 64 data + 16 pad), then
+    // the per-tile row sums T (nc x R int32 each)
+    unsigned char* stage = emit_smem + (size_t)(threadIdx.x >> 5) * kStageBytes;
+    int32_t* T1 = reinterpret_cast<int32_t*>(emit_smem + kEmitWarps * kStageBytes);
+    int32_t* T2 = T1 + (size_t)nc * R;
+    __shared__ int64_t P1[kMaxTiles], P2[kMaxTiles];
+    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int y0 = b * R, nr = min(R, N - y0);
+    const int32_t* cab1 = ca1 + (size_t)b * M;  // column sums above this band
+    const int32_t* cab2 = ca2 + (size_t)b * M;
+    const bool vec = ((stride & 7) == 0) && ((reinterpret_cast<uintptr_t>(f) & 7) == 0);
+    const uint8_t* fband = f + (size_t)y0 * stride;
+
+    // Phase 1: per tile, the column sums above the band over its sources (P)
+    // and every row's own values (T), each summed over the tile.
+    for (int c = warp; c < nc; c += kEmitWarps) {
+        const int X0 = c * kTileCols;
+        int64_t p1 = 0, p2 = 0;
 #pragma unroll
-    for (int e = 0; e < kPer; ++e) {
-        const int x = Xt + e - 1;
-        const bool in = (x >= 0) && (x < M);
-        col1[e] = in ? cs1[(size_t)b * M + x] : 0;
-        col2[e] = in ? cs2[(size_t)b * M + x] : 0;
-    }
-    const bool full = (Xt + kPer - 1 <= M);  // all four outputs exist
-    if (b == 0) {  // row Y = 0 is all zero
-#pragma unroll
-        for (int e = 0; e < kPer; ++e)
-            if (Xt + e <= M) { s[Xt + e] = 0; s2[Xt + e] = 0; }
-    }
-    // Inputs x = Xt-1 .. Xt+2: an aligned 4-byte load of Xt .. Xt+3 gives the
-    // last three; the first is the previous lane's fourth byte (lane 0 loads it).
-    const bool vec = ((stride & 3) == 0) && ((reinterpret_cast<uintptr_t>(f) & 3) == 0) && (Xt + kPer - 1 < M);
-    auto load = [&](int y, int (&v)[kPer], int& edge) {
-        const uint8_t* row = f + (size_t)y * stride;
-        uint32_t w = 0;
-        if (vec) {
-            w = __ldg(reinterpret_cast<const uint32_t*>(row + Xt));
-        } else {
-#pragma unroll
-            for (int e = 0; e < kPer; ++e)
-                if (Xt + e < M) w |= (uint32_t)row[Xt + e] << (8 * e);
-        }
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, w, 1);
-        const int x_first = Xt - 1;
-        v[0] = (lane > 0) ? (int)(prev >> 24) : ((x_first >= 0 && x_first < M) ? row[x_first] : 0);
-#pragma unroll
-        for (int e = 1; e < kPer; ++e) v[e] = (w >> (8 * (e - 1))) & 0xff;
-        edge = (xe >= 0) ? row[xe] : 0;  // uniform
-    };
-    int nxt[kPer], nedge = 0;
-    if (y0 < y1) load(y0, nxt, nedge);
-    for (int y = y0; y < y1; ++y) {
-        int v[kPer];
-#pragma unroll
-        for (int e = 0; e < kPer; ++e) v[e] = nxt[e];
-        const int edge = nedge;
-        if (y + 1 < y1) load(y + 1, nxt, nedge);  // in flight during this row's scan
-        int64_t p1[kPer], p2[kPer];
-        int64_t r1 = 0, r2 = 0;
-#pragma unroll
-        for (int e = 0; e < kPer; ++e) {
-            col1[e] += v[e];
-            col2[e] += v[e] * v[e];
-            r1 += col1[e];
-            r2 += col2[e];
-            p1[e] = r1;
-            p2[e] = r2;
-        }
-        int64_t i1 = r1, i2 = r2;
-        block_scan2(i1, i2, sm[(y - y0) & 1]);
-        if (xe >= 0) {
-            left1 += rcs1[y - y0] - edge;
-            left2 += rcs2[y - y0] - edge * edge;
-        }
-        const int64_t base1 = left1 + i1 - r1, base2 = left2 + i2 - r2;
-        ST* srow = s + (size_t)(y + 1) * pitch + Xt;
-        int64_t* s2row = s2 + (size_t)(y + 1) * pitch + Xt;
-        if (full) {
-            if constexpr (sizeof(ST) == 4) {
-                int4 o;
-                o.x = (int)(base1 + p1[0]); o.y = (int)(base1 + p1[1]);
-                o.z = (int)(base1 + p1[2]); o.w = (int)(base1 + p1[3]);
-                *reinterpret_cast<int4*>(srow) = o;
-            } else {
-                *reinterpret_cast<longlong2*>(srow) = make_longlong2(base1 + p1[0], base1 + p1[1]);
-                *reinterpret_cast<longlong2*>(srow + 2) = make_longlong2(base1 + p1[2], base1 + p1[3]);
+        for (int e = 0; e < kLaneCols; ++e) {
+            const int x = X0 + kLaneCols * lane - 1 + e;
+            if (x >= 0 && x < M) {
+                p1 += cab1[x];
+                p2 += cab2[x];
             }
-            *reinterpret_cast<longlong2*>(s2row) = make_longlong2(base2 + p2[0], base2 + p2[1]);
-            *reinterpret_cast<longlong2*>(s2row + 2) = make_longlong2(base2 + p2[2], base2 + p2[3]);
-        } else {
+        }
+        p1 = warp_sum(p1);
+        p2 = warp_sum(p2);
+        if (lane == 0) {
+            P1[c] = p1;
+            P2[c] = p2;
+        }
+        for (int r0 = 0; r0 < nr; r0 += kAhead) {
+            LaneRow q[kAhead];
 #pragma unroll
-            for (int e = 0; e < kPer; ++e)
-                if (Xt + e <= M) {
-                    srow[e] = (ST)(base1 + p1[e]);
-                    s2row[e] = base2 + p2[e];
+            for (int i = 0; i < kAhead; ++i)
+                if (r0 + i < nr) q[i] = load_lane_row(fband + (size_t)(r0 + i) * stride, M, X0, lane, vec);
+#pragma unroll
+            for (int i = 0; i < kAhead; ++i) {
+                if (r0 + i >= nr) break;
+                int v[8];
+                unpack_lane_row(q[i], lane, v);
+                int t1 = 0, t2 = 0;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    t1 += v[e];
+                    t2 += v[e] * v[e];
                 }
+                t1 = warp_sum(t1);
+                t2 = warp_sum(t2);
+                if (lane == 0) {
+                    T1[c * R + r0 + i] = t1;
+                    T2[c * R + r0 + i] = t2;
+                }
+            }
         }
     }
+    __syncthreads();
+    // Exclusive prefixes over the tiles: thread r < nr for row r, thread nr for P.
+    if ((int)threadIdx.x < nr) {
+        const int r = threadIdx.x;
+        int32_t a1 = 0, a2 = 0;
+        for (int c = 0; c < nc; ++c) {
+            const int32_t t1 = T1[c * R + r], t2 = T2[c * R + r];
+            T1[c * R + r] = a1;
+            T2[c * R + r] = a2;
+            a1 += t1;
+            a2 += t2;
+        }
+    } else if ((int)threadIdx.x == nr) {
+        int64_t a1 = 0, a2 = 0;
+        for (int c = 0; c < nc; ++c) {
+            const int64_t p1 = P1[c], p2 = P2[c];
+            P1[c] = a1;
+            P2[c] = a2;
+            a1 += p1;
+            a2 += p2;
+        }
+    }
+    __syncthreads();
+
+    // Phase 2: the band's outputs, tile by tile.  col holds the lane's
+    // absolute column sums (above the band plus the band's rows so far), which
+    // fit int32; the prefix along the tile is formed in int64 as it is stored.
+    if (b == 0) {  // row Y = 0 of the table is zero
+        for (int X = threadIdx.x; X <= M; X += blockDim.x) {
+            s[X] = 0;
+            s2[X] = 0;
+        }
+    }
+    for (int c = warp; c < nc; c += kEmitWarps) {
+        const int X0 = c * kTileCols, Xl = X0 + kLaneCols * lane;
+        int32_t col1[kLaneCols], col2[kLaneCols];
+#pragma unroll
+        for (int e = 0; e < kLaneCols; ++e) {
+            const int x = Xl - 1 + e;
+            const bool in = (x >= 0 && x < M);
+            col1[e] = in ? cab1[x] : 0;
+            col2[e] = in ? cab2[x] : 0;
+        }
+        int64_t left1 = P1[c], left2 = P2[c];  // corner, then plus the rows' left sums
+        const bool full_tile = (X0 + kTileCols - 1 <= M);  // warp-uniform
+        LaneRow q[kAhead];
+#pragma unroll
+        for (int i = 0; i < kAhead; ++i)
+            if (i < nr) q[i] = load_lane_row(fband + (size_t)i * stride, M, X0, lane, vec);
+        for (int r = 0; r < nr; ++r) {
+            int v[8];
+            unpack_lane_row(q[0], lane, v);
+#pragma unroll
+            for (int i = 0; i < kAhead - 1; ++i) q[i] = q[i + 1];
+            if (r + kAhead < nr) q[kAhead - 1] = load_lane_row(fband + (size_t)(r + kAhead) * stride, M, X0, lane, vec);
+            int64_t t1 = 0, t2 = 0;
+#pragma unroll
+            for (int e = 0; e < kLaneCols; ++e) {
+                col1[e] += v[e];
+                col2[e] += v[e] * v[e];
+                t1 += col1[e];
+                t2 += col2[e];
+            }
+            left1 += T1[c * R + r];
+            left2 += T2[c * R + r];
+            int64_t a1 = left1 + warp_exclusive_scan(t1, lane), a2 = left2 + warp_exclusive_scan(t2, lane);
+            ST* srow = s + (size_t)(y0 + r + 1) * pitch;
+            int64_t* s2row = s2 + (size_t)(y0 + r + 1) * pitch;
+            if (full_tile) {
+                // through the warp's staging buffer, so that every global store
+                // instruction writes 512 contiguous bytes
+                stage_row<ST>(stage, lane, col1, a1, srow + X0);
+                stage_row<int64_t>(stage, lane, col2, a2, s2row + X0);
+            } else {
+#pragma unroll
+                for (int e = 0; e < kLaneCols; ++e) {
+                    a1 += col1[e];
+                    a2 += col2[e];
+                    if (Xl + e <= M) {
+                        srow[Xl + e] = (ST)a1;
+                        s2row[Xl + e] = a2;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// The emit kernel's dynamic shared memory can exceed the 48 KB default
+// (staging 20 KB + row sums up to 32 KB).
+cudaError_t set_emit_attributes() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        const int most = kEmitWarps * kStageBytes + 2 * kMaxTiles * kMaxR * (int)sizeof(int32_t);
+        err = cudaFuncSetAttribute(sat_band_emit<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(sat_band_emit<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    });
+    return err;
 }
 
 }  // namespace
@@ -350,7 +428,7 @@ __global__ void __launch_bounds__(kThreads) sat_tile_emit(const uint8_t* __restr
 extern "C" size_t sncc_integral_workspace_bytes(int M, int N) {
     if (M <= 0 || N <= 0) return 0;
     const sncc::SatGeometry g = sncc::sat_geometry(M, N);
-    return (size_t)2 * g.nb * (size_t)M * sizeof(int32_t) + (size_t)2 * g.nc * (size_t)N * sizeof(int32_t) + 256;
+    return (size_t)2 * g.nb * (size_t)M * sizeof(int32_t) + 256;
 }
 
 extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int s_bits, int64_t* d_s2,
@@ -370,20 +448,18 @@ extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, voi
     const SatGeometry g = sat_geometry(M, N);
     int32_t* cs1 = static_cast<int32_t*>(d_ws);
     int32_t* cs2 = cs1 + (size_t)g.nb * M;
-    int32_t* rc1 = cs2 + (size_t)g.nb * M;
-    int32_t* rc2 = rc1 + (size_t)g.nc * N;
     cudaStream_t st = (cudaStream_t)stream;
     dim3 g1((M / 4 + 1 + 255) / 256, g.nb);
     sat_band_colsum<<<g1, 256, 0, st>>>(d_f, M, N, f_stride, g.R, cs1, cs2);
-    sat_band_scan<<<(M + 31) / 32, 256, 0, st>>>(M, g.nb, cs1, cs2);
-    sat_row_carry<<<(N + 7) / 8, 256, 0, st>>>(d_f, M, N, f_stride, g.nc, rc1, rc2);
-    dim3 g4(g.nc, g.nb);
+    sat_band_scan<<<(M + 31) / 32, kScanWarps * 32, 0, st>>>(M, g.nb, cs1, cs2);
+    const size_t smem = (size_t)kEmitWarps * kStageBytes + (size_t)2 * g.nc * g.R * sizeof(int32_t);
+    if (set_emit_attributes() != cudaSuccess) return SNCC_ERR_CUDA;
     if (s_bits == 32)
-        sat_tile_emit<int32_t><<<g4, kThreads, 0, st>>>(d_f, M, N, f_stride, g.R, sat_pitch, cs1, cs2, rc1, rc2,
-                                                      static_cast<int32_t*>(d_s), d_s2);
+        sat_band_emit<int32_t><<<g.nb, kEmitWarps * 32, smem, st>>>(d_f, M, N, f_stride, g.R, g.nc, sat_pitch, cs1,
+                                                                   cs2, static_cast<int32_t*>(d_s), d_s2);
     else
-        sat_tile_emit<int64_t><<<g4, kThreads, 0, st>>>(d_f, M, N, f_stride, g.R, sat_pitch, cs1, cs2, rc1, rc2,
-                                                      static_cast<int64_t*>(d_s), d_s2);
+        sat_band_emit<int64_t><<<g.nb, kEmitWarps * 32, smem, st>>>(d_f, M, N, f_stride, g.R, g.nc, sat_pitch, cs1,
+                                                                   cs2, static_cast<int64_t*>(d_s), d_s2);
     return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }
 

@@ -258,8 +258,8 @@ def integral_workspace(M: int, N: int, device="cuda"):
 
 
 # kernels one sncc_integral call launches: column sums of bands, band scan,
-# row carries, tile emit
-INTEGRAL_KERNELS = 4
+# band emit
+INTEGRAL_KERNELS = 3
 
 
 def integral(f, tables: Optional[Tables] = None, s_bits: Optional[int] = None, workspace=None, stream=None) -> Tables:
