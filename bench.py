@@ -571,7 +571,7 @@ def run_gpu(args, world, rank, local, pg):
                "candidates": int(pm.mb.count.item()), "matches": int(pm.rb.nout.item()), "status": pm.status(),
                "max_abs_dncc_fast_vs_exact": float((pm.mb.rho - exact_rho).abs().max().item()),
                "what": "sum tables + coarse k_fast (0.99 sigma_t) at every offset + k_slow (0.1 sigma_t, "
-                       "K_max 5000) at the candidates (Section 5 main algorithm)"}
+                       "K_max 5000) on the tiles that hold candidates (Section 5 main algorithm)"}
     except sncc.SnccError as e:
         two = {"unavailable": str(e)}
 

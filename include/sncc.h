@@ -283,6 +283,31 @@ int sncc_refine_segmented(const sncc_segments* seg, const void* d_plan, const vo
                           const int32_t* d_count, int cand_cap, float tau, sncc_match_t* d_out, int out_cap,
                           int32_t* d_nout, void* d_ws, size_t ws_bytes, int32_t* d_status, sncc_stream_t stream);
 
+/*
+ * sncc_refine_segmented_tiles - the same fine stage as sncc_refine_segmented
+ * (Section 5 main algorithm steps 7g-7j, Eq. 12 - Eq. 18), evaluated tile by
+ * tile: every tile of 32 x 8R offsets (R as sncc_match picks it) that holds a
+ * candidate is computed by the segment-sum kernel of sncc_match with the
+ * fine plan, and its candidates with rho >= tau become matches.  The result
+ * is the same set (rho identical); the cost follows the number of tiles that
+ * hold candidates rather than the number of candidates, which pays when the
+ * coarse stage passes many.
+ *
+ *   arguments as sncc_refine_segmented, except the workspace:
+ *   d_ws, ws_bytes          256-byte aligned workspace of at least
+ *                           sncc_refine_segmented_tiles_workspace_bytes(M, N, W, H, out_cap)
+ *                           (match records, one candidate bit per offset,
+ *                           a flag and a list entry per tile)
+ * Errors as sncc_refine_segmented; SNCC_ERR_WORKSPACE for a missing, short or
+ * misaligned workspace.
+ */
+size_t sncc_refine_segmented_tiles_workspace_bytes(int M, int N, int W, int H, int out_cap);
+int sncc_refine_segmented_tiles(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits,
+                                const int64_t* d_s2, int sat_pitch, int M, int N, const int32_t* d_cand,
+                                const int32_t* d_count, int cand_cap, float tau, sncc_match_t* d_out, int out_cap,
+                                int32_t* d_nout, void* d_ws, size_t ws_bytes, int32_t* d_status,
+                                sncc_stream_t stream);
+
 /* ------------------------------------------------------------------ */
 /* Batched matching: many templates x several sources, one launch      */
 /* ------------------------------------------------------------------ */

@@ -70,6 +70,15 @@ struct MatchArgs {
     int cand_cap;
     int32_t* count;
     int32_t* status;
+    // fine mode (sncc_refine_segmented_tiles): the tiles to evaluate, the
+    // candidate bit of every offset and the (u, v, rho) output records
+    const int32_t* tile_list;
+    const int32_t* tile_count;
+    int tiles_u;
+    const uint32_t* cand_bits;
+    sncc_match_t* out;
+    int out_cap;
+    int32_t* nout;
 };
 
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
@@ -93,7 +102,7 @@ __device__ __forceinline__ void stage_region_tma(const CUtensorMap* map, int* bu
     }
 }
 
-template <int R, bool S64, int WP, bool PIPE>
+template <int R, bool S64, int WP, bool PIPE, bool FINE>
 __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUtensorMap tmap, const MatchArgs a) {
     constexpr int NBUF = PIPE ? 2 : 1;
     extern __shared__ __align__(128) unsigned char smem_base[];
@@ -108,7 +117,13 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
     volatile int* flag = reinterpret_cast<volatile int*>(bar + 2);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int u0 = blockIdx.x * TILE_U, v0 = blockIdx.y * (WARPS * R);
+    int u0 = blockIdx.x * TILE_U, v0 = blockIdx.y * (WARPS * R);
+    if constexpr (FINE) {  // a 1-D grid over the listed tiles; the rest exit at once
+        if ((int)blockIdx.x >= *a.tile_count) return;
+        const int t = a.tile_list[blockIdx.x];
+        u0 = (t % a.tiles_u) * TILE_U;
+        v0 = (t / a.tiles_u) * (WARPS * R);
+    }
 
     if (tid == 0) {
         if constexpr (!S64) {
@@ -183,27 +198,68 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = v0 + warp * R + r;
-        const bool valid = (u < a.U) && (v < a.V);
+        bool valid = (u < a.U) && (v < a.V);
+        if constexpr (FINE) {
+            if (valid) {
+                const int idx = v * a.U + u;
+                valid = (a.cand_bits[idx >> 5] >> (idx & 31)) & 1u;
+            }
+        }
         const float rho = valid ? normalise<S64>(acc[r], a.s, a.s2, a.pitch, u, v, a.W, a.H, a.n, a.inv_n, a.Ek,
                                                  a.scale, a.Q0)
                                 : 0.0f;
-        if (a.rho != nullptr && valid) a.rho[(size_t)v * a.rho_pitch + u] = rho;
+        if (!FINE && a.rho != nullptr && valid) a.rho[(size_t)v * a.rho_pitch + u] = rho;
         const bool pred = valid && (rho >= a.tau);
         const unsigned m = __ballot_sync(0xffffffffu, pred);
         if (m) {
             const int leader = __ffs(m) - 1;
             int base = 0;
-            if (lane == leader) base = atomicAdd(a.count, __popc(m));
+            if (lane == leader) base = atomicAdd(FINE ? a.nout : a.count, __popc(m));
             base = __shfl_sync(0xffffffffu, base, leader);
             if (pred) {
                 const int pos = base + __popc(m & ((1u << lane) - 1u));
-                if (pos < a.cand_cap)
-                    a.cand[pos] = v * a.U + u;
-                else
-                    atomicOr(a.status, SNCC_STATUS_CAND_OVERFLOW);
+                if constexpr (FINE) {
+                    if (pos < a.out_cap) {
+                        sncc_match_t rec;
+                        rec.u = u;
+                        rec.v = v;
+                        rec.rho = rho;
+                        a.out[pos] = rec;
+                    } else {
+                        atomicOr(a.status, SNCC_STATUS_MATCH_OVERFLOW);
+                    }
+                } else {
+                    if (pos < a.cand_cap)
+                        a.cand[pos] = v * a.U + u;
+                    else
+                        atomicOr(a.status, SNCC_STATUS_CAND_OVERFLOW);
+                }
             }
         }
     }
+}
+
+// Fine mode, step 1: the candidate bit of every listed offset, and a flag on
+// every tile (32 x rows offsets) that holds a candidate.
+__global__ void __launch_bounds__(256) mark_candidate_tiles(const int32_t* __restrict__ cand,
+                                                            const int32_t* __restrict__ count, int cand_cap, int U,
+                                                            int V, int tiles_u, int rows, uint32_t* __restrict__ bits,
+                                                            int32_t* __restrict__ tile_flag) {
+    const int n = min(*count, cand_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int idx = cand[i];
+        if (idx < 0 || idx >= U * V) continue;  // not an offset
+        const int u = idx % U, v = idx / U;
+        atomicOr(&bits[idx >> 5], 1u << (idx & 31));
+        tile_flag[(v / rows) * tiles_u + u / TILE_U] = 1;
+    }
+}
+
+// Fine mode, step 2: the flagged tiles as a list (any order).
+__global__ void __launch_bounds__(256) list_tiles(const int32_t* __restrict__ tile_flag, int ntiles,
+                                                  int32_t* __restrict__ tile_list, int32_t* __restrict__ tile_count) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
+        if (tile_flag[t]) tile_list[atomicAdd(tile_count, 1)] = t;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -220,7 +276,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-template <int R, bool S64, int WP, bool PIPE>
+template <int R, bool S64, int WP, bool PIPE, bool FINE>
 cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
     constexpr int NBUF = PIPE ? 2 : 1;
     const int RH = WARPS * R + BH + 1;
@@ -230,22 +286,36 @@ cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cud
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP, PIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP, PIPE, FINE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         128 + smem_words(WARPS * R + 64 + 1, WP, NBUF) * 4);
     });
     if (attr_err != cudaSuccess) return attr_err;
-    dim3 grid((a.U + TILE_U - 1) / TILE_U, (a.V + WARPS * R - 1) / (WARPS * R));
-    match_kernel<R, S64, WP, PIPE><<<grid, WARPS * 32, sm, st>>>(map, args);
+    const int tu = (a.U + TILE_U - 1) / TILE_U, tv = (a.V + WARPS * R - 1) / (WARPS * R);
+    const dim3 grid = FINE ? dim3(tu * tv) : dim3(tu, tv);
+    match_kernel<R, S64, WP, PIPE, FINE><<<grid, WARPS * 32, sm, st>>>(map, args);
     return cudaGetLastError();
 }
 
-template <bool S64, int WP, bool PIPE>
+template <bool S64, int WP, bool PIPE, bool FINE>
 cudaError_t dispatch_r(int R, const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
     switch (R) {
-        case 8: return launch_match<8, S64, WP, PIPE>(map, a, BH, st);
-        case 4: return launch_match<4, S64, WP, PIPE>(map, a, BH, st);
-        default: return launch_match<2, S64, WP, PIPE>(map, a, BH, st);
+        case 8: return launch_match<8, S64, WP, PIPE, FINE>(map, a, BH, st);
+        case 4: return launch_match<4, S64, WP, PIPE, FINE>(map, a, BH, st);
+        default: return launch_match<2, S64, WP, PIPE, FINE>(map, a, BH, st);
     }
+}
+
+// The segment-sum launch on a prepared MatchArgs: picks the kernel instance
+// for the layout and table width.
+template <bool FINE>
+cudaError_t launch_layout(const Layout& L, bool s64, int R, const CUtensorMap& map, const MatchArgs& a,
+                          cudaStream_t st) {
+    if (L.WP == 68 && L.nblk > 1 && !s64) return dispatch_r<false, 68, true, FINE>(R, map, a, L.BH, st);
+    if (L.WP == 68)
+        return s64 ? dispatch_r<true, 68, false, FINE>(R, map, a, L.BH, st)
+                   : dispatch_r<false, 68, false, FINE>(R, map, a, L.BH, st);
+    return s64 ? dispatch_r<true, 100, false, FINE>(R, map, a, L.BH, st)
+               : dispatch_r<false, 100, false, FINE>(R, map, a, L.BH, st);
 }
 
 // Offsets per thread: the largest R in {8, 4, 2} that still gives two CTAs
@@ -259,32 +329,27 @@ int choose_r(int U, int V) {
     return 2;
 }
 
-}  // namespace
-}  // namespace sncc
-
-extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits,
-                          const int64_t* d_s2, int sat_pitch, int M, int N, float tau, float* d_rho, int rho_pitch,
-                          int32_t* d_cand, int cand_cap, int32_t* d_count, int32_t* d_status, sncc_stream_t stream) {
-    using namespace sncc;
+// Shared by sncc_match and sncc_refine_segmented_tiles: checks the common
+// arguments and fills the kernel arguments and (32-bit tables) the TMA map.
+int prepare_match(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits, const int64_t* d_s2,
+                  int sat_pitch, int M, int N, float tau, MatchArgs& a, CUtensorMap& map, int& R, const Layout*& Lout) {
     const Plan* p = plan_of(seg);
-    if (!seg || !p || !d_plan || !d_s || !d_s2 || !d_count || !d_status || (cand_cap > 0 && !d_cand))
-        return SNCC_ERR_ARG;
-    if (cand_cap < 0 || (s_bits != 32 && s_bits != 64)) return SNCC_ERR_ARG;
+    if (!seg || !p || !d_plan || !d_s || !d_s2) return SNCC_ERR_ARG;
+    if (s_bits != 32 && s_bits != 64) return SNCC_ERR_ARG;
     if (!(seg->Ek > 0.0) || p->image.empty()) return SNCC_ERR_UNIFORM;
     const int W = seg->W, H = seg->H;
     const int U = M - W + 1, V = N - H + 1;
     if (W <= 0 || H <= 0 || U <= 0 || V <= 0) return SNCC_ERR_ARG;
     if (sat_pitch < M + 1 || (sat_pitch & 3)) return SNCC_ERR_ARG;
     if (s_bits == 32 && (int64_t)255 * M * N >= ((int64_t)1 << 31)) return SNCC_ERR_DTYPE;
-    if (d_rho && rho_pitch < U) return SNCC_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(d_plan) & 15) || (reinterpret_cast<uintptr_t>(d_s) & 15)) return SNCC_ERR_ARG;
     if ((int64_t)U * V >= ((int64_t)1 << 31)) return SNCC_ERR_UNSUPPORTED;
 
     const bool s64 = (s_bits == 64);
     const Layout& L = layout_for(*p, s64);
-    const int R = choose_r(U, V);
+    Lout = &L;
+    R = choose_r(U, V);
     const int RH = WARPS * R + L.BH + 1;
-    CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     if (!s64) {  // 2-D TMA tile map over the 32-bit table, box WP x RH
         PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode();
@@ -298,8 +363,7 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (cr != CUDA_SUCCESS) return SNCC_ERR_CUDA;
     }
-
-    MatchArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.blocks_offset);
     a.runblk = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.runblk_offset);
     a.runs = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.runs_offset);
@@ -320,25 +384,113 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
     a.scale = (float)std::ldexp(1.0, -p->F);
     a.Q0 = p->Q0;
     a.tau = tau;
+    a.tiles_u = (U + TILE_U - 1) / TILE_U;
+    return SNCC_OK;
+}
+
+// Workspace of sncc_refine_segmented_tiles, in order: match records
+// (out_cap, 16-byte aligned), candidate bits (one per offset), tile flags,
+// tile list, tile count.
+struct TilesLayout {
+    size_t recs, bits, flags, list, count, total;
+    int ntiles, rows;
+};
+
+TilesLayout tiles_layout(int M, int N, int W, int H, int out_cap) {
+    const int U = M - W + 1, V = N - H + 1;
+    const int R = choose_r(U, V);
+    TilesLayout t;
+    t.rows = WARPS * R;
+    t.ntiles = ((U + TILE_U - 1) / TILE_U) * ((V + t.rows - 1) / t.rows);
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    size_t o = 0;
+    t.recs = o;
+    o = al(o + (size_t)(out_cap > 0 ? out_cap : 1) * sizeof(sncc_match_t));
+    t.bits = o;
+    o = al(o + (((size_t)U * V + 31) / 32) * 4);
+    t.flags = o;
+    o = al(o + (size_t)t.ntiles * 4);
+    t.list = o;
+    o = al(o + (size_t)t.ntiles * 4);
+    t.count = o;
+    o = al(o + 16);
+    t.total = o;
+    return t;
+}
+
+}  // namespace
+}  // namespace sncc
+
+extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits,
+                          const int64_t* d_s2, int sat_pitch, int M, int N, float tau, float* d_rho, int rho_pitch,
+                          int32_t* d_cand, int cand_cap, int32_t* d_count, int32_t* d_status, sncc_stream_t stream) {
+    using namespace sncc;
+    if (!d_count || !d_status || cand_cap < 0 || (cand_cap > 0 && !d_cand)) return SNCC_ERR_ARG;
+    MatchArgs a;
+    CUtensorMap map;
+    int R = 0;
+    const Layout* L = nullptr;
+    const int rc = prepare_match(seg, d_plan, d_s, s_bits, d_s2, sat_pitch, M, N, tau, a, map, R, L);
+    if (rc != SNCC_OK) return rc;
+    if (d_rho && rho_pitch < a.U) return SNCC_ERR_ARG;
     a.rho = d_rho;
     a.rho_pitch = rho_pitch;
     a.cand = d_cand;
     a.cand_cap = cand_cap;
     a.count = d_count;
     a.status = d_status;
-
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(d_count, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
     if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
-    cudaError_t e;
-    // Single-block templates (up to 64 x 64) stage once; multi-block ones
-    // double-buffer so that block b+1 is in flight while block b computes.
-    if (L.WP == 68 && L.nblk > 1 && !s64)
-        e = dispatch_r<false, 68, true>(R, map, a, L.BH, st);
-    else if (L.WP == 68)
-        e = s64 ? dispatch_r<true, 68, false>(R, map, a, L.BH, st) : dispatch_r<false, 68, false>(R, map, a, L.BH, st);
-    else
-        e = s64 ? dispatch_r<true, 100, false>(R, map, a, L.BH, st)
-                : dispatch_r<false, 100, false>(R, map, a, L.BH, st);
-    return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+    // Single-block templates (up to 64 x 64) stage once; multi-block ones with
+    // 32-bit tables double-buffer so that block b+1 is in flight while block b
+    // computes.
+    return launch_layout<false>(*L, s_bits == 64, R, map, a, st) == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+}
+
+extern "C" size_t sncc_refine_segmented_tiles_workspace_bytes(int M, int N, int W, int H, int out_cap) {
+    if (M <= 0 || N <= 0 || W <= 0 || H <= 0 || W > M || H > N || out_cap < 0) return 0;
+    return sncc::tiles_layout(M, N, W, H, out_cap).total;
+}
+
+extern "C" int sncc_refine_segmented_tiles(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits,
+                                           const int64_t* d_s2, int sat_pitch, int M, int N, const int32_t* d_cand,
+                                           const int32_t* d_count, int cand_cap, float tau, sncc_match_t* d_out,
+                                           int out_cap, int32_t* d_nout, void* d_ws, size_t ws_bytes,
+                                           int32_t* d_status, sncc_stream_t stream) {
+    using namespace sncc;
+    if (!d_count || !d_nout || !d_status || cand_cap < 0 || out_cap < 0) return SNCC_ERR_ARG;
+    if ((cand_cap > 0 && !d_cand) || (out_cap > 0 && !d_out)) return SNCC_ERR_ARG;
+    MatchArgs a;
+    CUtensorMap map;
+    int R = 0;
+    const Layout* L = nullptr;
+    const int rc = prepare_match(seg, d_plan, d_s, s_bits, d_s2, sat_pitch, M, N, tau, a, map, R, L);
+    if (rc != SNCC_OK) return rc;
+    const TilesLayout t = tiles_layout(M, N, seg->W, seg->H, out_cap);
+    if (!d_ws || ws_bytes < t.total || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return SNCC_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(d_ws);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(ws + t.bits);
+    int32_t* flags = reinterpret_cast<int32_t*>(ws + t.flags);
+    int32_t* list = reinterpret_cast<int32_t*>(ws + t.list);
+    int32_t* tcount = reinterpret_cast<int32_t*>(ws + t.count);
+    sncc_match_t* recs = reinterpret_cast<sncc_match_t*>(ws + t.recs);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(d_nout, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
+    if (cudaMemsetAsync(ws + t.bits, 0, t.list - t.bits, st) != cudaSuccess) return SNCC_ERR_CUDA;  // bits, flags
+    if (cudaMemsetAsync(tcount, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
+    if (cand_cap == 0) return SNCC_OK;
+    mark_candidate_tiles<<<2 * 152, 256, 0, st>>>(d_cand, d_count, cand_cap, a.U, a.V, a.tiles_u, t.rows, bits, flags);
+    list_tiles<<<(t.ntiles + 255) / 256, 256, 0, st>>>(flags, t.ntiles, list, tcount);
+    if (cudaGetLastError() != cudaSuccess) return SNCC_ERR_CUDA;
+    a.tile_list = list;
+    a.tile_count = tcount;
+    a.cand_bits = bits;
+    a.out = recs;
+    a.out_cap = out_cap;
+    a.nout = d_nout;
+    a.status = d_status;
+    if (launch_layout<true>(*L, s_bits == 64, R, map, a, st) != cudaSuccess) return SNCC_ERR_CUDA;
+    if (launch_rank_sort(recs, d_nout, out_cap, a.U, d_out, st) != cudaSuccess) return SNCC_ERR_CUDA;
+    return SNCC_OK;
 }

@@ -33,7 +33,8 @@ STATUS_CAND_OVERFLOW, STATUS_MATCH_OVERFLOW, STATUS_WAIT_TIMEOUT, STATUS_SORT_OV
 EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_sat_pitch",
             "sncc_integral_workspace_bytes", "sncc_integral", "sncc_plan_bytes", "sncc_plan_upload", "sncc_match",
             "sncc_refine_workspace_bytes", "sncc_refine", "sncc_exact_map", "sncc_get_plan_info",
-            "sncc_probe_smem_read", "sncc_probe_alu", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_batch_create",
+            "sncc_probe_smem_read", "sncc_probe_alu", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_refine_segmented_tiles",
+            "sncc_refine_segmented_tiles_workspace_bytes", "sncc_batch_create",
             "sncc_batch_destroy", "sncc_batch_device_bytes", "sncc_batch_upload", "sncc_batch_set_variant",
             "sncc_batch_get_info", "sncc_batch_match", "sncc_batch_autotune", "sncc_batch_refine_workspace_bytes",
             "sncc_batch_refine", "sncc_diff_workspace_bytes", "sncc_diff_forward", "sncc_diff_backward"]
@@ -92,6 +93,9 @@ _lib.sncc_refine.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_i
                              _vp, _vp, C.c_int, C.c_float, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp]
 _lib.sncc_refine_segmented.argtypes = [C.POINTER(_Segments), _vp, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int,
                                        _vp, _vp, C.c_int, C.c_float, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp]
+_lib.sncc_refine_segmented_tiles.argtypes = _lib.sncc_refine_segmented.argtypes
+_lib.sncc_refine_segmented_tiles_workspace_bytes.argtypes = [C.c_int] * 5
+_lib.sncc_refine_segmented_tiles_workspace_bytes.restype = C.c_size_t
 class BatchInfo(C.Structure):
     _fields_ = [("n_templates", C.c_int32), ("n_sources", C.c_int32), ("tile_rows", C.c_int32),
                 ("tiles", C.c_int32), ("offsets", C.c_double), ("corner_offsets", C.c_double)]
@@ -365,6 +369,30 @@ def refine_segmented(seg_fine: Segments, plan_fine, tables: Tables, bufs: MatchB
                                       _stream(stream)), "sncc_refine_segmented")
 
 
+def tiles_workspace(M: int, N: int, W: int, H: int, out_cap: int, device="cuda"):
+    """Workspace for refine_segmented_tiles (256-byte aligned)."""
+    torch = _torch()
+    nbytes = int(_lib.sncc_refine_segmented_tiles_workspace_bytes(M, N, W, H, out_cap))
+    if nbytes == 0:
+        raise SnccError(ERR_ARG, "sncc_refine_segmented_tiles_workspace_bytes")
+    raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-raw.data_ptr()) % 256
+    return raw[off:off + nbytes]
+
+
+def refine_segmented_tiles(seg_fine: Segments, plan_fine, tables: Tables, bufs: MatchBuffers, tau: float,
+                           rb: RefineBuffers, ws, cand_cap: Optional[int] = None, stream=None) -> None:
+    """sncc_refine_segmented_tiles: the paper's fine stage evaluated on the
+    tiles that hold coarse candidates; matches land in rb.out sorted by v*U+u."""
+    cap = bufs.cand.numel() if cand_cap is None else cand_cap
+    _check(_lib.sncc_refine_segmented_tiles(seg_fine.ref(), plan_fine.data_ptr(), tables.s.data_ptr(),
+                                            tables.s_bits, tables.s2.data_ptr(), tables.pitch, tables.M, tables.N,
+                                            bufs.cand.data_ptr(), bufs.count.data_ptr(), cap, float(tau),
+                                            rb.out.data_ptr(), rb.cap, rb.nout.data_ptr(), ws.data_ptr(),
+                                            ws.numel(), bufs.status.data_ptr(), _stream(stream)),
+           "sncc_refine_segmented_tiles")
+
+
 def matches_to_numpy(rb: RefineBuffers):
     """(u, v, rho) arrays of the stored matches (after the stream is synced)."""
     import torch
@@ -417,7 +445,8 @@ class PaperMatcher:
     """The paper's own two-approximation search (Section 5 main algorithm):
     coarse k_fast (sigma_max = 0.99 sigma_t) at every offset, then the finer
     k_slow (sigma_max = 0.1 sigma_t, K_max = 5000) at the candidates,
-    thresholds precision * rho_fast and precision * rho_slow."""
+    thresholds precision * rho_fast and precision * rho_slow.  The fine stage
+    runs tile by tile on the tiles that hold candidates."""
 
     def __init__(self, t: np.ndarray, M: int, N: int, precision: float = 0.9, fast: float = 0.99,
                  slow: float = 0.1, k_max: int = 5000, cand_cap: int = 1 << 20, out_cap: int = 1 << 16,
@@ -437,11 +466,13 @@ class PaperMatcher:
         self.ws = integral_workspace(M, N, device)
         self.mb = alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device)
         self.rb = alloc_refine(out_cap, device)
+        self.tws = tiles_workspace(M, N, self.W, self.H, out_cap, device)
 
     def run(self, f, stream=None):
         integral(f, self.tables, workspace=self.ws, stream=stream)
         match(self.fast, self.plan_fast, self.tables, self.tau_fast, self.mb, stream=stream)
-        refine_segmented(self.slow, self.plan_slow, self.tables, self.mb, self.tau_slow, self.rb, stream=stream)
+        refine_segmented_tiles(self.slow, self.plan_slow, self.tables, self.mb, self.tau_slow, self.rb, self.tws,
+                               stream=stream)
 
     def status(self) -> int:
         return int(self.mb.status.item())

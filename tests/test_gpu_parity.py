@@ -353,8 +353,8 @@ def test_matcher_end_to_end(sncc):
                                             (200, 180, 100, 70, 0.7, 9)])
 def test_paper_two_stage_matches_oracle(sncc, M, N, W, H, p, seed):
     """Coarse k_fast at every offset, k_slow at the candidates (Section 5),
-    through sncc_match + sncc_refine_segmented, against the oracle's main
-    algorithm; sets agree outside the +-TOL bands of both thresholds."""
+    through sncc_match + sncc_refine_segmented_tiles, against the oracle's
+    main algorithm; sets agree outside the +-TOL bands of both thresholds."""
     c = synth.case_plain(M=M, N=N, W=W, H=H, seed=synth.BASE_SEED + seed)
     r = O.main_algorithm(c.f, c.t, precision=p)
     m = sncc.PaperMatcher(c.t, M, N, precision=p)
@@ -380,3 +380,43 @@ def test_paper_two_stage_matches_oracle(sncc, M, N, W, H, p, seed):
     diff = set(key.tolist()) ^ set(r["idx"].tolist())
     assert all(amb[d] for d in diff), sorted(diff)[:10]
     assert len(r["idx"]) > 0
+
+
+@pytest.mark.parametrize("M,N,W,H,p,seed,bits", [(300, 220, 64, 48, 0.6, 5, 32), (260, 200, 100, 70, 0.5, 9, 64),
+                                                 (256, 256, 32, 32, 0.3, 0, 32)])
+def test_fine_stage_per_candidate_and_tiled_agree(sncc, M, N, W, H, p, seed, bits):
+    """The two implementations of the paper's fine stage return the same
+    match list (same offsets, identical rho) on the same coarse candidates,
+    with many candidates (low precision) and both table widths."""
+    c = synth.case_plain(M=M, N=N, W=W, H=H, seed=synth.BASE_SEED + seed)
+    m = sncc.PaperMatcher(c.t, M, N, precision=p)
+    fd = dev(c.f)
+    tb = sncc.integral(fd, s_bits=bits)
+    sncc.match(m.fast, m.plan_fast, tb, m.tau_fast, m.mb)
+    rb1 = sncc.alloc_refine(1 << 16)
+    sncc.refine_segmented(m.slow, m.plan_slow, tb, m.mb, m.tau_slow, rb1)
+    rb2 = sncc.alloc_refine(1 << 16)
+    ws = sncc.tiles_workspace(M, N, W, H, 1 << 16)
+    sncc.refine_segmented_tiles(m.slow, m.plan_slow, tb, m.mb, m.tau_slow, rb2, ws)
+    torch.cuda.synchronize()
+    assert int(m.mb.count.item()) > 100
+    a, b = sncc.matches_to_numpy(rb1), sncc.matches_to_numpy(rb2)
+    assert int(rb1.nout.item()) == int(rb2.nout.item()) > 0
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_fine_stage_tiled_output_overflow(sncc):
+    c = synth.case_plain(seed=synth.BASE_SEED)
+    m = sncc.PaperMatcher(c.t, 256, 256, precision=0.2)
+    fd = dev(c.f)
+    tb = sncc.integral(fd)
+    sncc.match(m.fast, m.plan_fast, tb, m.tau_fast, m.mb)
+    rb = sncc.alloc_refine(7)
+    ws = sncc.tiles_workspace(256, 256, 32, 32, 7)
+    sncc.refine_segmented_tiles(m.slow, m.plan_slow, tb, m.mb, m.tau_slow, rb, ws)
+    torch.cuda.synchronize()
+    assert int(rb.nout.item()) > 7
+    assert int(m.mb.status.item()) & sncc.STATUS_MATCH_OVERFLOW
+    u, v, rho = sncc.matches_to_numpy(rb)
+    assert len(u) == 7 and np.all(np.diff(v * 225 + u) > 0)
