@@ -276,14 +276,25 @@ int build_plan(const sncc_segments* s, Plan& p) {
     }
     p.Q0 = Q0;
 
-    // Corners of the whole template as one block: the algorithmic count.
+    // Corners of the whole template as one block: the algorithmic count, and
+    // for sparse templates the direct corner list.
     p.template_corners = 0;
     auto qa = [&](int X, int Y) -> int64_t {
         return (X < 0 || Y < 0 || X >= W || Y >= H) ? 0 : qimg[(size_t)Y * W + X];
     };
+    std::vector<int32_t> direct;
     for (int Y = 0; Y <= H; ++Y)
-        for (int X = 0; X <= W; ++X)
-            p.template_corners += (qa(X - 1, Y - 1) - qa(X, Y - 1) - qa(X - 1, Y) + qa(X, Y)) != 0;
+        for (int X = 0; X <= W; ++X) {
+            const int64_t g = qa(X - 1, Y - 1) - qa(X, Y - 1) - qa(X - 1, Y) + qa(X, Y);
+            if (g == 0) continue;
+            ++p.template_corners;
+            if ((int)direct.size() / 4 < DIRECT_MAX + 1) {
+                direct.push_back(X);
+                direct.push_back(Y);
+                direct.push_back((int32_t)g);
+                direct.push_back(0);
+            }
+        }
 
     // Region pitches are compile-time widths of the kernels, multiples of 4
     // so that a region row is a whole number of 16-byte units.
@@ -292,6 +303,9 @@ int build_plan(const sncc_segments* s, Plan& p) {
     const int bw0 = single ? W : std::min(W, BLOCK_MULTI), bh0 = single ? H : std::min(H, BLOCK_MULTI);
     build_layout(qimg, W, H, bw0, bh0, bw0 <= 32 ? 68 : 100, p.lay[0], p.image);
     build_layout(qimg, W, H, std::min(W, BLOCK_SINGLE_MAX), std::min(H, BLOCK_SINGLE_MAX), 100, p.lay[1], p.image);
+    p.direct_count = p.template_corners <= DIRECT_MAX ? p.template_corners : 0;
+    p.direct_offset = p.image.size() * 4;
+    if (p.direct_count > 0) p.image.insert(p.image.end(), direct.begin(), direct.begin() + 4 * p.direct_count);
     p.image.insert(p.image.end(), 4, 0);
     return SNCC_OK;
 }

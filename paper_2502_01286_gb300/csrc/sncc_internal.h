@@ -81,8 +81,16 @@ struct Plan {
     // most 64 x 64 with pitch 100, used with 64-bit tables (fewer, larger
     // blocks halve the register staging per corner) and by the batched kernel.
     Layout lay[2];
-    std::vector<int32_t> image;  // both sections, then 4 zero words
+    // Templates with at most DIRECT_MAX corners in all also carry their
+    // whole-template corner list, int4 {X, Y, G, 0}, at direct_offset: the
+    // segment-sum kernel then reads the table at those corners directly
+    // instead of staging block regions (direct_count = 0 otherwise).
+    int direct_count = 0;
+    size_t direct_offset = 0;
+    std::vector<int32_t> image;  // both layouts, the direct list, then 4 zero words
 };
+
+constexpr int DIRECT_MAX = 64;
 
 // Lengths of the vertical corner runs and the int4 units one run occupies.
 constexpr int RUN_LEN[4] = {8, 4, 2, 1};

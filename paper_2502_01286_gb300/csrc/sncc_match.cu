@@ -74,6 +74,9 @@ struct MatchArgs {
     // candidate bit of every offset and the (u, v, rho) output records
     const int32_t* tile_list;
     const int32_t* tile_count;
+    // direct mode: the whole template's corners {X, Y, G, 0}, read in place
+    const int4* direct;
+    int ndirect;
     int tiles_u;
     const uint32_t* cand_bits;
     sncc_match_t* out;
@@ -102,7 +105,7 @@ __device__ __forceinline__ void stage_region_tma(const CUtensorMap* map, int* bu
     }
 }
 
-template <int R, bool S64, int WP, bool PIPE, bool FINE>
+template <int R, bool S64, int WP, bool PIPE, bool FINE, bool DIRECT>
 __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUtensorMap tmap, const MatchArgs a) {
     constexpr int NBUF = PIPE ? 2 : 1;
     extern __shared__ __align__(128) unsigned char smem_base[];
@@ -138,58 +141,81 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
     long long acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
-    uint32_t parity_bits = 0u;  // bit i: phase parity expected next on bar[i]
-
-    if (!S64 && a.nblk > 0) {
-        const int4 b0 = a.blocks[0];
-        stage_region_tma<WP>(&tmap, work0, &bar[0], u0 + b0.x, v0 + b0.y, RH, tid);
-    }
-    const int* wbase0 = work0 + warp * R * WP + lane;
-    for (int b = 0; b < a.nblk; ++b) {
-        const int cur = PIPE ? (b & 1) : 0;
-        int* work = PIPE ? work0 + cur * WW : work0;
-        const int4 blk = a.blocks[b];
-        if constexpr (!S64) {
-            const bool ahead = PIPE && (b + 1 < a.nblk);
-            if (ahead) {  // the other buffer was released by the barrier ending block b-1
-                const int4 nb = a.blocks[b + 1];
-                stage_region_tma<WP>(&tmap, work0 + (cur ^ 1) * WW, &bar[cur ^ 1], u0 + nb.x, v0 + nb.y, RH, tid);
+    if constexpr (DIRECT) {
+        // Sparse template: A = sum_p G_p s(u + X_p, v + Y_p) over its few
+        // corners, table entries read in place (full 64-bit entries of 64-bit
+        // tables) and summed modulo 2^64, which is exact since |A| < 2^63.
+        // Lanes and rows outside the map read the last valid offset's entries.
+        const int uu = min(u0 + lane, a.U - 1);
+        unsigned long long accu[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) accu[r] = 0ull;
+        for (int q = 0; q < a.ndirect; ++q) {
+            const int4 cr = __ldg(a.direct + q);
+            const int x = uu + cr.x;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int y = min(v0 + warp * R + r, a.V - 1) + cr.y;
+                const long long sv = table_entry<S64>(a.s, a.pitch, x, y);
+                accu[r] += (unsigned long long)(long long)cr.z * (unsigned long long)sv;
             }
-            // ---- wait for block b's region, then re-base it in place ----
-            const uint32_t par = (parity_bits >> cur) & 1u;
-            if (tid == 0 && !mbar_wait_bounded(&bar[cur], par)) *flag = 1;
-            __syncthreads();
-            if (*flag) {
-                if (tid == 0) atomicOr(a.status, SNCC_STATUS_WAIT_TIMEOUT);
-                // let an outstanding prefetch land before the CTA's memory is released
-                if (tid == 0 && ahead) (void)mbar_wait_bounded(&bar[cur ^ 1], (parity_bits >> (cur ^ 1)) & 1u);
-                __syncthreads();
-                return;
-            }
-            (void)mbar_try_wait(&bar[cur], par);  // phase complete: acquire for this thread
-            parity_bits ^= 1u << cur;
-            for (int X = tid; X < WP; X += WARPS * 32) row0[X] = work[X];
-            for (int Y = tid; Y < RH; Y += WARPS * 32) col0[Y] = work[Y * WP];
-            __syncthreads();
-            {
-                const uint32_t c00 = (uint32_t)row0[0];
-                for (int Y = warp; Y < RH; Y += WARPS) {
-                    const uint32_t cy = (uint32_t)col0[Y] - c00;
-                    for (int X = lane; X < WP; X += 32)
-                        work[Y * WP + X] = (int)((uint32_t)work[Y * WP + X] - (uint32_t)row0[X] - cy);
-                }
-            }
-        } else {
-            stage_region_regs<true, WP>(a.s, a.pitch, a.M, a.N, work, u0 + blk.x, v0 + blk.y, RH, lane, warp);
         }
-        __syncthreads();
-        // ---- corner sum over vertical runs: one multiply-add per (offset, corner) ----
-        const int* wbase = PIPE ? wbase0 + cur * WW : wbase0;
-        run_sum<R, WP>(acc, wbase, a.runs, __ldg(a.runblk + 2 * b), __ldg(a.runblk + 2 * b + 1));
-        __syncthreads();  // this buffer is restaged two blocks later (PIPE) or next block
-        if (!S64 && !PIPE && b + 1 < a.nblk) {
-            const int4 nb = a.blocks[b + 1];
-            stage_region_tma<WP>(&tmap, work0, &bar[0], u0 + nb.x, v0 + nb.y, RH, tid);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = (long long)accu[r];
+    } else {
+        uint32_t parity_bits = 0u;  // bit i: phase parity expected next on bar[i]
+
+        if (!S64 && a.nblk > 0) {
+            const int4 b0 = a.blocks[0];
+            stage_region_tma<WP>(&tmap, work0, &bar[0], u0 + b0.x, v0 + b0.y, RH, tid);
+        }
+        const int* wbase0 = work0 + warp * R * WP + lane;
+        for (int b = 0; b < a.nblk; ++b) {
+            const int cur = PIPE ? (b & 1) : 0;
+            int* work = PIPE ? work0 + cur * WW : work0;
+            const int4 blk = a.blocks[b];
+            if constexpr (!S64) {
+                const bool ahead = PIPE && (b + 1 < a.nblk);
+                if (ahead) {  // the other buffer was released by the barrier ending block b-1
+                    const int4 nb = a.blocks[b + 1];
+                    stage_region_tma<WP>(&tmap, work0 + (cur ^ 1) * WW, &bar[cur ^ 1], u0 + nb.x, v0 + nb.y, RH, tid);
+                }
+                // ---- wait for block b's region, then re-base it in place ----
+                const uint32_t par = (parity_bits >> cur) & 1u;
+                if (tid == 0 && !mbar_wait_bounded(&bar[cur], par)) *flag = 1;
+                __syncthreads();
+                if (*flag) {
+                    if (tid == 0) atomicOr(a.status, SNCC_STATUS_WAIT_TIMEOUT);
+                    // let an outstanding prefetch land before the CTA's memory is released
+                    if (tid == 0 && ahead) (void)mbar_wait_bounded(&bar[cur ^ 1], (parity_bits >> (cur ^ 1)) & 1u);
+                    __syncthreads();
+                    return;
+                }
+                (void)mbar_try_wait(&bar[cur], par);  // phase complete: acquire for this thread
+                parity_bits ^= 1u << cur;
+                for (int X = tid; X < WP; X += WARPS * 32) row0[X] = work[X];
+                for (int Y = tid; Y < RH; Y += WARPS * 32) col0[Y] = work[Y * WP];
+                __syncthreads();
+                {
+                    const uint32_t c00 = (uint32_t)row0[0];
+                    for (int Y = warp; Y < RH; Y += WARPS) {
+                        const uint32_t cy = (uint32_t)col0[Y] - c00;
+                        for (int X = lane; X < WP; X += 32)
+                            work[Y * WP + X] = (int)((uint32_t)work[Y * WP + X] - (uint32_t)row0[X] - cy);
+                    }
+                }
+            } else {
+                stage_region_regs<true, WP>(a.s, a.pitch, a.M, a.N, work, u0 + blk.x, v0 + blk.y, RH, lane, warp);
+            }
+            __syncthreads();
+            // ---- corner sum over vertical runs: one multiply-add per (offset, corner) ----
+            const int* wbase = PIPE ? wbase0 + cur * WW : wbase0;
+            run_sum<R, WP>(acc, wbase, a.runs, __ldg(a.runblk + 2 * b), __ldg(a.runblk + 2 * b + 1));
+            __syncthreads();  // this buffer is restaged two blocks later (PIPE) or next block
+            if (!S64 && !PIPE && b + 1 < a.nblk) {
+                const int4 nb = a.blocks[b + 1];
+                stage_region_tma<WP>(&tmap, work0, &bar[0], u0 + nb.x, v0 + nb.y, RH, tid);
+            }
         }
     }
 
@@ -276,32 +302,33 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-template <int R, bool S64, int WP, bool PIPE, bool FINE>
+template <int R, bool S64, int WP, bool PIPE, bool FINE, bool DIRECT>
 cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
     constexpr int NBUF = PIPE ? 2 : 1;
-    const int RH = WARPS * R + BH + 1;
+    const int RH = DIRECT ? 0 : WARPS * R + BH + 1;  // direct mode stages nothing
     MatchArgs args = a;
     args.RH = RH;
     const size_t sm = 128 + (size_t)smem_words(RH, WP, NBUF) * 4;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP, PIPE, FINE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP, PIPE, FINE, DIRECT>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         128 + smem_words(WARPS * R + 64 + 1, WP, NBUF) * 4);
     });
     if (attr_err != cudaSuccess) return attr_err;
     const int tu = (a.U + TILE_U - 1) / TILE_U, tv = (a.V + WARPS * R - 1) / (WARPS * R);
     const dim3 grid = FINE ? dim3(tu * tv) : dim3(tu, tv);
-    match_kernel<R, S64, WP, PIPE, FINE><<<grid, WARPS * 32, sm, st>>>(map, args);
+    match_kernel<R, S64, WP, PIPE, FINE, DIRECT><<<grid, WARPS * 32, sm, st>>>(map, args);
     return cudaGetLastError();
 }
 
-template <bool S64, int WP, bool PIPE, bool FINE>
+template <bool S64, int WP, bool PIPE, bool FINE, bool DIRECT = false>
 cudaError_t dispatch_r(int R, const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
     switch (R) {
-        case 8: return launch_match<8, S64, WP, PIPE, FINE>(map, a, BH, st);
-        case 4: return launch_match<4, S64, WP, PIPE, FINE>(map, a, BH, st);
-        default: return launch_match<2, S64, WP, PIPE, FINE>(map, a, BH, st);
+        case 8: return launch_match<8, S64, WP, PIPE, FINE, DIRECT>(map, a, BH, st);
+        case 4: return launch_match<4, S64, WP, PIPE, FINE, DIRECT>(map, a, BH, st);
+        default: return launch_match<2, S64, WP, PIPE, FINE, DIRECT>(map, a, BH, st);
     }
 }
 
@@ -310,6 +337,9 @@ cudaError_t dispatch_r(int R, const CUtensorMap& map, const MatchArgs& a, int BH
 template <bool FINE>
 cudaError_t launch_layout(const Layout& L, bool s64, int R, const CUtensorMap& map, const MatchArgs& a,
                           cudaStream_t st) {
+    if (a.ndirect > 0)  // sparse template: no staging
+        return s64 ? dispatch_r<true, 100, false, FINE, true>(R, map, a, 0, st)
+                   : dispatch_r<false, 100, false, FINE, true>(R, map, a, 0, st);
     if (L.WP == 68 && L.nblk > 1 && !s64) return dispatch_r<false, 68, true, FINE>(R, map, a, L.BH, st);
     if (L.WP == 68)
         return s64 ? dispatch_r<true, 68, false, FINE>(R, map, a, L.BH, st)
@@ -385,6 +415,8 @@ int prepare_match(const sncc_segments* seg, const void* d_plan, const void* d_s,
     a.Q0 = p->Q0;
     a.tau = tau;
     a.tiles_u = (U + TILE_U - 1) / TILE_U;
+    a.ndirect = p->direct_count;
+    a.direct = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->direct_offset);
     return SNCC_OK;
 }
 

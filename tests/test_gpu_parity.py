@@ -156,6 +156,25 @@ def test_match_table_width_independent(sncc, bits, M, N, W, H):
     assert np.abs(mb.rho.cpu().numpy() - ref).max() <= TOL
 
 
+@pytest.mark.parametrize("bits", [32, 64])
+def test_match_direct_sparse_multiblock_template(sncc, bits):
+    """A 200 x 150 template approximated by a few segments (sigma near the
+    template's own std, as the paper's k_fast) has few corners in all; the
+    kernel reads the table at those corners directly instead of staging
+    blocks.  Map against the oracle, with 32- and 64-bit tables."""
+    c = synth.case_plain(M=420, N=330, W=200, H=150, seed=23)
+    sigma = 0.99 * sncc.template_sigma(c.t)
+    seg = sncc.build_segments(c.t, sigma)
+    pi = seg.plan_info()
+    assert pi["blocks"] > 1 and 0 < pi["template_corners"] <= 64
+    ap = O.precompute_template_approximation(c.t, sigma)
+    _, _, _, mb = run_match(sncc, c.f, c.t, sigma, 0.5 * seg.rho_max, s_bits=bits)
+    ref = O.segmented_ncc_map(c.f, ap, "sat")
+    assert np.abs(mb.rho.cpu().numpy() - ref).max() <= TOL
+    cnt = int(mb.count.item())
+    check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, 0.5 * seg.rho_max)
+
+
 def test_match_repeatable(sncc):
     c = synth.case_plain()
     _, _, _, a = run_match(sncc, c.f, c.t, 10.0, 0.5)
