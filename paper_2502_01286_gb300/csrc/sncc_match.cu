@@ -2,7 +2,8 @@
 // approximate numerator sum_i (k_i - kbar) S_i(u, v) (Eq. 9, Eq. 11, Eq. 12),
 // normalised by the local energy and the approximation energy (Eq. 13 -
 // Eq. 18), thresholded and compacted into a candidate list (main algorithm,
-// steps 7a-7f).
+// steps 7a-7f); and, with a second approximation on the tiles that hold
+// candidates, the paper's fine stage (steps 7g-7j).
 //
 // Kernel design (one CTA = 8 warps = a 32 x 8R tile of offsets):
 //  * The segment values enter as fixed-point weights q_i = round(c_i 2^F),
@@ -11,25 +12,31 @@
 //    Eq. 11: every segment contributes +-q_i at its four corners and corners
 //    shared by neighbouring segments are combined on the host, so each
 //    offset needs one 32x32->64-bit multiply-add per distinct corner.
-//  * The template is processed in blocks.  For each block the sum-table
-//    region the tile touches is staged in shared memory and re-based to its
-//    own origin (exact in wrapped 32-bit arithmetic, since every re-based
-//    entry is a box sum below 2^31):
+//  * Staged mode: the template is processed in blocks (one block up to
+//    64 x 64; larger templates in 32 x 32 blocks with 32-bit tables, 64 x 64
+//    with 64-bit tables).  For each block the sum-table region the tile
+//    touches is staged in shared memory and re-based to its own origin
+//    (exact in wrapped 32-bit arithmetic, since every re-based entry is a box
+//    sum below 2^31):
 //      - 32-bit tables: a 2-D TMA tile load completing on an mbarrier, then
-//        an in-place re-base; templates of several blocks double-buffer, so
-//        block b+1's tile is in flight while block b computes;
+//        an in-place re-base; 32 x 32 blocks double-buffer, so block b+1's
+//        tile is in flight while block b computes;
 //      - 64-bit tables: the low words (box sums only need the table modulo
-//        2^32) are loaded through registers and stored already re-based.
+//        2^32) are loaded through registers, two entries per load, and
+//        stored already re-based.
 //    The region is read with conflict-free 32-bit loads: lane l reads
-//    column l, warp w its own R rows.
-//  * The corners come regrouped into vertical runs of 8, 4, 2 and 1 corners
-//    (consecutive rows of one column): a lane's R rows share R + L - 1
-//    region loads per run of L, so on dense templates the shared-memory reads
-//    drop well below one per (offset, corner) and the 64-bit multiply-add is
-//    the only limit.  Run records are loaded one ahead of their use.
+//    column l, warp w its own R rows.  The corners come regrouped into
+//    vertical runs of 8, 4, 2 and 1 corners (consecutive rows of one
+//    column): a lane's R rows share R + L - 1 region loads per run of L, so
+//    on dense templates the shared-memory reads drop well below one per
+//    (offset, corner) and the 64-bit multiply-add is the only limit.  Run
+//    records are loaded one ahead of their use.
+//  * Direct mode: a template with at most 64 corners in all is summed by
+//    reading the table at its corners in place (no staging, no block edges).
 //  * Epilogue: window sums from the global tables, exact integer variance
-//    n sum f^2 - (sum f)^2 divided by n in FP64, rho in FP32, warp-aggregated
-//    atomic append of candidates.
+//    n sum f^2 - (sum f)^2 divided by n in FP64, rho in FP32; the coarse pass
+//    appends candidates (v*U+u) with warp-aggregated atomics, the fine mode
+//    appends (u, v, rho) records of the offsets whose candidate bit is set.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
