@@ -478,6 +478,23 @@ class PaperMatcher:
         return int(self.mb.status.item())
 
 
+def capture_graph(launch):
+    """Records the launches that launch() makes on the current stream into a
+    CUDA graph, after one eager run on a side stream (which also performs the
+    library's one-time setup outside the capture)."""
+    torch = _torch()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        launch()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        launch()
+    return g
+
+
 class Matcher:
     """Segmented-NCC template matcher for one template on one GPU.
 
@@ -510,6 +527,11 @@ class Matcher:
         integral(f, self.tables, workspace=self.ws, stream=stream)
         match(self.seg, self.plan, self.tables, self.tau_c, self.mb, stream=stream)
         refine(f, self.t_dev, self.seg, self.mb, self.tau_e, self.rb, stream=stream)
+
+    def capture(self, f):
+        """Record run(f) in a CUDA graph (after one eager warm-up run); replay
+        it after writing each new source into f."""
+        return capture_graph(lambda: self.run(f))
 
     def status(self) -> int:
         return int(self.mb.status.item())
@@ -607,17 +629,7 @@ class Batch:
 
     def capture(self, sources):
         """Record run(sources) in a CUDA graph (after one eager warm-up run)."""
-        torch = _torch()
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            self.run(sources)
-        torch.cuda.current_stream().wait_stream(side)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            self.run(sources)
-        return g
+        return capture_graph(lambda: self.run(sources))
 
     def candidates(self):
         """(pair, index) arrays of the stored candidates (after a sync)."""

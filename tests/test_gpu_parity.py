@@ -367,6 +367,27 @@ def test_matcher_end_to_end(sncc):
     assert np.abs(rho - rho_o).max(initial=0) <= TOL
 
 
+def test_matcher_graph_replay_matches_eager(sncc):
+    """A captured step replayed on a new source gives the eager results."""
+    a = synth.case_plain(seed=synth.BASE_SEED + 3)
+    b = synth.case_plain(seed=synth.BASE_SEED + 4)
+    m = sncc.Matcher(a.t, 3.0, 256, 256, precision=0.5)
+    fd = dev(a.f)
+    g = m.capture(fd)
+    fd.copy_(dev(b.f))
+    g.replay()
+    torch.cuda.synchronize()
+    got = [x.copy() for x in sncc.matches_to_numpy(m.rb)]
+    rho_g = m.mb.rho.clone()
+    m.run(fd)
+    torch.cuda.synchronize()
+    want = sncc.matches_to_numpy(m.rb)
+    assert torch.equal(rho_g, m.mb.rho)
+    assert len(want[0]) > 0
+    for x, y in zip(got, want):
+        np.testing.assert_array_equal(x, y)
+
+
 # ------------------------------------------------------------------ the paper's two-approximation search
 @pytest.mark.parametrize("M,N,W,H,p,seed", [(256, 256, 32, 32, 0.9, 0), (300, 220, 64, 48, 0.8, 5),
                                             (200, 180, 100, 70, 0.7, 9)])
