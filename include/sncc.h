@@ -514,6 +514,13 @@ int sncc_probe_smem_read(int32_t* d_sink, int ctas, int iters, sncc_stream_t str
  * ctas*256*iters*64.  SNCC_ERR_ARG for another kind or a non-positive
  * size.  Used by the benchmark to measure ALU ceilings; not part of the
  * matching path. */
+/* Bounded-wait test hook (no counterpart in the paper): one CTA waits on a
+ * shared-memory mbarrier that nothing completes, with the same bounded wait
+ * the segment-sum kernel uses for its TMA copies; after the wait limit (1 s)
+ * it ORs SNCC_STATUS_WAIT_TIMEOUT into *d_status (int32, device) and returns.
+ * No fault: the context stays usable.  SNCC_ERR_ARG for a null status. */
+int sncc_probe_wait_timeout(int32_t* d_status, sncc_stream_t stream);
+
 #define SNCC_PROBE_DP4A 0
 #define SNCC_PROBE_IMAD_WIDE 1
 int sncc_probe_alu(int kind, int32_t* d_sink, int ctas, int iters, sncc_stream_t stream);

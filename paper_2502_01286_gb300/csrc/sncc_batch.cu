@@ -470,6 +470,7 @@ extern "C" int sncc_batch_get_info(const sncc_batch* b, sncc_batch_info* out) {
 extern "C" int sncc_batch_match(const sncc_batch* b, const void* d_buf, const void* const* d_s,
                                 const int64_t* const* d_s2, int s_bits, int sat_pitch, int32_t* d_cand, int cand_cap,
                                 int32_t* d_count, int32_t* d_counter, int32_t* d_status, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_batch_match");
     using namespace sncc;
     if (!b || !d_buf || !d_s || !d_s2 || !d_count || !d_counter || !d_status || cand_cap < 0) return SNCC_ERR_ARG;
     if (cand_cap > 0 && !d_cand) return SNCC_ERR_ARG;
@@ -568,6 +569,7 @@ extern "C" int sncc_batch_refine(const sncc_batch* b, const void* d_buf, const u
                                  const int32_t* d_cand, const int32_t* d_count, int cand_cap,
                                  sncc_batch_match_t* d_out, int out_cap, int32_t* d_nout, void* d_ws,
                                  size_t ws_bytes, int32_t* d_status, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_batch_refine");
     using namespace sncc;
     if (!b || !d_buf || !d_f || !d_count || !d_nout || !d_status || f_stride < b->M || cand_cap < 0 || out_cap < 0)
         return SNCC_ERR_ARG;

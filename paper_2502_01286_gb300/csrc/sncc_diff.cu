@@ -476,6 +476,7 @@ extern "C" size_t sncc_diff_workspace_bytes(int M, int N, int W, int H) {
 extern "C" int sncc_diff_forward(const float* d_f, int M, int N, int f_stride, const float* d_t, int W, int H,
                                  const int32_t* d_rects, const float* d_k, int K, float* d_rho_k, float* d_rho_t,
                                  double* d_loss, void* d_ws, size_t ws_bytes, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_diff_forward");
     using namespace sncc;
     if (!d_f || !d_t || !d_rects || !d_k || !d_rho_k || !d_rho_t || !d_loss) return SNCC_ERR_ARG;
     if (!diff_args_ok(M, N, W, H, K, f_stride)) return SNCC_ERR_ARG;
@@ -502,6 +503,7 @@ extern "C" int sncc_diff_backward(const float* d_f, int M, int N, int f_stride, 
                                   const int32_t* d_rects, const float* d_k, int K, const float* d_rho_k,
                                   const float* d_rho_t, const double* d_dloss, float* d_grad_f, int grad_f_stride,
                                   float* d_grad_k, void* d_ws, size_t ws_bytes, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_diff_backward");
     using namespace sncc;
     if (!d_f || !d_rects || !d_k || !d_rho_k || !d_rho_t || !d_dloss || !d_grad_f || !d_grad_k) return SNCC_ERR_ARG;
     if (!diff_args_ok(M, N, W, H, K, f_stride) || grad_f_stride < M) return SNCC_ERR_ARG;

@@ -167,6 +167,7 @@ cudaError_t launch_exact(bool s64, dim3 grid, cudaStream_t st, const uint8_t* f,
 extern "C" int sncc_exact_map(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t* d_t, int W, int H,
                               int t_stride, int64_t T, int64_t T2, const void* d_s, int s_bits, const int64_t* d_s2,
                               int sat_pitch, float* d_rho, int rho_pitch, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_exact_map");
     using namespace sncc;
     if (!d_f || !d_t || !d_s || !d_s2 || !d_rho || W <= 0 || H <= 0 || M < W || N < H) return SNCC_ERR_ARG;
     if (f_stride < M || t_stride < W || (s_bits != 32 && s_bits != 64) || sat_pitch < M + 1) return SNCC_ERR_ARG;

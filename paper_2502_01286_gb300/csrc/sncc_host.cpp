@@ -344,6 +344,7 @@ void sncc_free_segments(sncc_segments* s) {
 
 int sncc_build_segments(const uint8_t* t, int W, int H, int t_stride, double sigma_max, int k_max,
                         sncc_segments* out) {
+    sncc::NvtxRange nvtx_range("sncc_build_segments");
     using namespace sncc;
     if (!t || !out || W <= 0 || H <= 0 || t_stride < W || !(sigma_max == sigma_max)) return SNCC_ERR_ARG;
     if ((int64_t)W * H > ((int64_t)1 << 23)) return SNCC_ERR_UNSUPPORTED;

@@ -463,6 +463,7 @@ TilesLayout tiles_layout(int M, int N, int W, int H, int out_cap) {
 extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits,
                           const int64_t* d_s2, int sat_pitch, int M, int N, float tau, float* d_rho, int rho_pitch,
                           int32_t* d_cand, int cand_cap, int32_t* d_count, int32_t* d_status, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_match");
     using namespace sncc;
     if (!d_count || !d_status || cand_cap < 0 || (cand_cap > 0 && !d_cand)) return SNCC_ERR_ARG;
     MatchArgs a;
@@ -497,6 +498,7 @@ extern "C" int sncc_refine_segmented_tiles(const sncc_segments* seg, const void*
                                            const int32_t* d_count, int cand_cap, float tau, sncc_match_t* d_out,
                                            int out_cap, int32_t* d_nout, void* d_ws, size_t ws_bytes,
                                            int32_t* d_status, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_refine_segmented_tiles");
     using namespace sncc;
     if (!d_count || !d_nout || !d_status || cand_cap < 0 || out_cap < 0) return SNCC_ERR_ARG;
     if ((cand_cap > 0 && !d_cand) || (out_cap > 0 && !d_out)) return SNCC_ERR_ARG;

@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "sncc.h"
+#include "sncc_ptx.cuh"
 
 namespace sncc {
 namespace {
@@ -90,6 +91,19 @@ __global__ void __launch_bounds__(256) probe_imad_wide(int32_t* __restrict__ sin
     sink[blockIdx.x * blockDim.x + threadIdx.x] = (int32_t)(x ^ (x >> 32));
 }
 
+// The bounded wait of the segment-sum kernel on an mbarrier that nothing
+// completes: thread 0 gives up after the library's wait limit and records
+// SNCC_STATUS_WAIT_TIMEOUT, the CTA returns, and the context stays usable.
+__global__ void __launch_bounds__(32) probe_wait_timeout(int32_t* __restrict__ status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);  // one arrival expected; none comes
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u)) atomicOr(status, SNCC_STATUS_WAIT_TIMEOUT);
+}
+
 }  // namespace
 }  // namespace sncc
 
@@ -106,5 +120,11 @@ extern "C" int sncc_probe_alu(int kind, int32_t* d_sink, int ctas, int iters, sn
         sncc::probe_dp4a<<<ctas, 256, 0, (cudaStream_t)stream>>>(d_sink, iters, 0x01020304u);
     else
         sncc::probe_imad_wide<<<ctas, 256, 0, (cudaStream_t)stream>>>(d_sink, iters);
+    return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+}
+
+extern "C" int sncc_probe_wait_timeout(int32_t* d_status, sncc_stream_t stream) {
+    if (!d_status) return SNCC_ERR_ARG;
+    sncc::probe_wait_timeout<<<1, 32, 0, (cudaStream_t)stream>>>(d_status);
     return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }

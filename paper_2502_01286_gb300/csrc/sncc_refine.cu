@@ -140,6 +140,7 @@ extern "C" int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const
                            int t_stride, int64_t T, int64_t T2, const int32_t* d_cand, const int32_t* d_count,
                            int cand_cap, float tau, sncc_match_t* d_out, int out_cap, int32_t* d_nout, void* d_ws,
                            size_t ws_bytes, int32_t* d_status, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_refine");
     using namespace sncc;
     if (!d_f || !d_t || !d_count || !d_nout || !d_status || W <= 0 || H <= 0) return SNCC_ERR_ARG;
     if (f_stride < M || t_stride < W || M < W || N < H || cand_cap < 0 || out_cap < 0) return SNCC_ERR_ARG;

@@ -109,6 +109,7 @@ extern "C" int sncc_refine_segmented(const sncc_segments* seg, const void* d_pla
                                      const int32_t* d_count, int cand_cap, float tau, sncc_match_t* d_out,
                                      int out_cap, int32_t* d_nout, void* d_ws, size_t ws_bytes, int32_t* d_status,
                                      sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_refine_segmented");
     using namespace sncc;
     const Plan* p = plan_of(seg);
     if (!seg || !p || !d_plan || !d_s || !d_s2 || !d_count || !d_nout || !d_status) return SNCC_ERR_ARG;

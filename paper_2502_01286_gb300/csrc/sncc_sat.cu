@@ -433,6 +433,7 @@ extern "C" size_t sncc_integral_workspace_bytes(int M, int N) {
 
 extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int s_bits, int64_t* d_s2,
                              int sat_pitch, void* d_ws, size_t ws_bytes, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_integral");
     using namespace sncc;
     if (!d_f || !d_s || !d_s2 || M <= 0 || N <= 0 || f_stride < M) return SNCC_ERR_ARG;
     if (s_bits != 32 && s_bits != 64) return SNCC_ERR_ARG;

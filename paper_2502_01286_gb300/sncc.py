@@ -33,7 +33,7 @@ STATUS_CAND_OVERFLOW, STATUS_MATCH_OVERFLOW, STATUS_WAIT_TIMEOUT, STATUS_SORT_OV
 EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_sat_pitch",
             "sncc_integral_workspace_bytes", "sncc_integral", "sncc_plan_bytes", "sncc_plan_upload", "sncc_match",
             "sncc_refine_workspace_bytes", "sncc_refine", "sncc_exact_map", "sncc_get_plan_info",
-            "sncc_probe_smem_read", "sncc_probe_alu", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_refine_segmented_tiles",
+            "sncc_probe_smem_read", "sncc_probe_alu", "sncc_probe_wait_timeout", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_refine_segmented_tiles",
             "sncc_refine_segmented_tiles_workspace_bytes", "sncc_batch_create",
             "sncc_batch_destroy", "sncc_batch_device_bytes", "sncc_batch_upload", "sncc_batch_set_variant",
             "sncc_batch_get_info", "sncc_batch_match", "sncc_batch_autotune", "sncc_batch_refine_workspace_bytes",
@@ -127,6 +127,7 @@ _lib.sncc_diff_backward.argtypes = [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c
 _lib.sncc_get_plan_info.argtypes = [C.POINTER(_Segments), C.POINTER(PlanInfo)]
 _lib.sncc_probe_smem_read.argtypes = [_vp, C.c_int, C.c_int, _vp]
 _lib.sncc_probe_alu.argtypes = [C.c_int, _vp, C.c_int, C.c_int, _vp]
+_lib.sncc_probe_wait_timeout.argtypes = [_vp, _vp]
 _lib.sncc_exact_map.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64,
                                 C.c_int64, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp]
 
@@ -424,6 +425,12 @@ def probe_smem_read(sink, ctas: int, iters: int, stream=None) -> int:
 
 
 PROBE_DP4A, PROBE_IMAD_WIDE = 0, 1
+
+
+def probe_wait_timeout(status, stream=None) -> None:
+    """Runs the bounded-wait test hook: a wait that nothing completes gives up
+    after the library's limit and sets STATUS_WAIT_TIMEOUT in status."""
+    _check(_lib.sncc_probe_wait_timeout(status.data_ptr(), _stream(stream)), "sncc_probe_wait_timeout")
 
 
 def probe_alu(kind: int, sink, ctas: int, iters: int, stream=None) -> int:

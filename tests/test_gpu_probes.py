@@ -75,3 +75,22 @@ def test_smem_probe_runs(sncc):
     sink = torch.zeros(4 * 256, dtype=torch.int32, device="cuda")
     assert sncc.probe_smem_read(sink, 4, 2) == 4 * 256 * 2 * 32 * 4
     torch.cuda.synchronize()
+
+
+def test_bounded_wait_gives_up_and_reports(sncc):
+    """A wait that nothing completes ends after the wait limit with the
+    timeout status bit, and the context keeps working afterwards."""
+    import time
+    import torch
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sncc.probe_wait_timeout(status)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    assert int(status.item()) & sncc.STATUS_WAIT_TIMEOUT
+    assert 0.5 < secs < 30.0
+    sink = torch.zeros(256, dtype=torch.int32, device="cuda")
+    sncc.probe_alu(sncc.PROBE_DP4A, sink, 1, 1)
+    torch.cuda.synchronize()
+    assert int(sink[0].item()) == _replay_dp4a(0, 1)
