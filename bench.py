@@ -55,8 +55,13 @@ def make_case(workload: str, seed_offset: int = 0):
     from paper_2502_01286_gb300 import synth
     factory, sigmas, precision = WORKLOADS[workload]
     fn = getattr(synth, factory)
-    base = {"case_plain": 0, "case_hd": 1, "case_texture": 2}[factory]
-    return fn(seed=synth.BASE_SEED + base + seed_offset), sigmas, precision
+    return fn(seed=case_seed_of(workload, seed_offset)), sigmas, precision
+
+
+def case_seed_of(workload: str, seed_offset: int = 0) -> int:
+    from paper_2502_01286_gb300 import synth
+    factory = WORKLOADS[workload][0]
+    return synth.BASE_SEED + {"case_plain": 0, "case_hd": 1, "case_texture": 2}[factory] + seed_offset
 
 
 def parse():
@@ -430,6 +435,7 @@ def run_gpu(args, world, rank, local, pg):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     case, SIGMAS, PRECISION = make_case(args.workload, rank)  # independent problem per rank
+    case_seed = case_seed_of(args.workload, rank)
     N, M = case.f.shape
     H, W = case.t.shape
     U, V = M - W + 1, N - H + 1
@@ -452,18 +458,24 @@ def run_gpu(args, world, rank, local, pg):
 
     match_ev = []
 
+    refine_ev = []
+
     def step(record_match=False):
         sncc.integral(fd, tables, workspace=ws)
         for i, s in enumerate(segs):
             if record_match:
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
+                c = torch.cuda.Event(enable_timing=True)
                 a.record(stream)
             sncc.match(s, plans[i], tables, taus[i], mbs[i])
             if record_match:
                 b.record(stream)
                 match_ev.append((i, a, b))
             sncc.refine(fd, td, s, mbs[i], PRECISION, rbs[i])
+            if record_match:
+                c.record(stream)
+                refine_ev.append((i, b, c))
 
     for _ in range(args.warmup):
         step()
@@ -508,6 +520,9 @@ def run_gpu(args, world, rank, local, pg):
     per_sigma_ms = {i: [] for i in range(len(SIGMAS))}
     for i, a, b in match_ev:
         per_sigma_ms[i].append(a.elapsed_time(b))
+    refine_ms = {i: [] for i in range(len(SIGMAS))}
+    for i, a, b in refine_ev:
+        refine_ms[i].append(a.elapsed_time(b))
 
     # --- end to end through the public API with host buffers ---
     f_host = torch.as_tensor(case.f).pin_memory()
@@ -637,7 +652,7 @@ def run_gpu(args, world, rank, local, pg):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
-        "config": dict(workload_config(args.workload, case, SIGMAS, PRECISION, U, V),
+        "config": dict(workload_config(args.workload, case, SIGMAS, PRECISION, U, V), seed=case_seed,
                        launch="one CUDA graph per step: sum tables, then per threshold segment sum, exact "
                               "refine and sort"),
         "exact_ncc": {"value": U * V / (exact_ms * 1e-3) / 1e9, "unit": UNIT, "ms": exact_ms,
@@ -649,6 +664,7 @@ def run_gpu(args, world, rank, local, pg):
                        "block_corners": infos[i]["corners"] if tables.s_bits == 32 or infos[i]["blocks"] == 1
                        else infos[i]["wide_corners"], "rho_max": seg.rho_max,
                        "tau_c": taus[i], "match_ms": statistics.mean(per_sigma_ms[i]),
+                       "refine_ms": statistics.mean(refine_ms[i]),
                        "candidates": counts[i], "matches": nmatch[i], "status": status[i],
                        "goffsets_s_coarse": U * V / (statistics.mean(per_sigma_ms[i]) * 1e-3) / 1e9}
                       for i, (s, seg) in enumerate(zip(SIGMAS, segs))],
