@@ -22,6 +22,7 @@
 // carries are small arrays.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -51,7 +52,10 @@ SatGeometry sat_geometry(int M, int N) {
     // workspace is then 2 * (N / R) * M * 4 bytes <= about 12.6 MB for any
     // source up to 10^8 pixels
     long long r = ((long long)N * g.nc + kTargetTiles - 1) / kTargetTiles;
-    if (r < 2) r = 2;
+    // at least N/128 rows (2 to 8): short sources keep about 128 bands for
+    // parallelism, taller ones fewer, shorter passes over the bands
+    const long long rmin = std::min(8LL, std::max(2LL, (long long)N / 128));
+    if (r < rmin) r = rmin;
     if (r > kMaxR) r = kMaxR;
     if (r > N) r = N;
     g.R = (int)r;
