@@ -460,3 +460,44 @@ def test_fine_stage_tiled_output_overflow(sncc):
     assert int(m.mb.status.item()) & sncc.STATUS_MATCH_OVERFLOW
     u, v, rho = sncc.matches_to_numpy(rb)
     assert len(u) == 7 and np.all(np.diff(v * 225 + u) > 0)
+
+
+def test_paper_two_stage_texture_full_size_sampled(sncc):
+    """The 4096 x 4096 / 256 x 256 workload through the two-stage search
+    (k_fast summed directly at its few corners, k_slow on the tiles that hold
+    the ~1.3 M candidates), against the oracle on sampled offset rows: the
+    coarse map and the matches of those rows agree outside the bands."""
+    c = synth.case_texture()
+    N, M = c.f.shape
+    H, W = c.t.shape
+    U, V = M - W + 1, N - H + 1
+    m = sncc.PaperMatcher(c.t, M, N, precision=c.precision, cand_cap=U * V)
+    assert m.fast.plan_info()["template_corners"] <= 64
+    fd = dev(c.f)
+    m.run(fd)
+    torch.cuda.synchronize()
+    assert m.status() == 0
+    rows = np.array([0, 777, c.origin[1], V - 1])
+    ap_f, ap_s = O.precompute_template_approximation(c.t, 0.99 * sncc.template_sigma(c.t), 5000), \
+        O.precompute_template_approximation(c.t, 0.1 * sncc.template_sigma(c.t), 5000)
+    np.testing.assert_array_equal(m.fast.table, ap_f.segments)
+    np.testing.assert_array_equal(m.slow.table, ap_s.segments)
+    rf = O.segmented_ncc_map(c.f, ap_f, "sat", rows=rows)
+    rs = O.segmented_ncc_map(c.f, ap_s, "sat", rows=rows)
+    got_f = m.mb.rho.cpu().numpy()
+    assert np.abs(got_f[rows] - rf[rows]).max() <= TOL
+    thr_f, thr_s = c.precision * ap_f.rho_max, c.precision * ap_s.rho_max
+    u, v, rho = sncc.matches_to_numpy(m.rb)
+    sel = np.isin(v, rows)
+    got = set((v[sel] * U + u[sel]).tolist())
+    want, amb = set(), set()
+    for r in rows:
+        for x in range(U):
+            a, b = rf[r, x], rs[r, x]
+            if (a >= thr_f + TOL) and (b >= thr_s + TOL):
+                want.add(r * U + x)
+            elif abs(a - thr_f) < TOL or abs(b - thr_s) < TOL:
+                amb.add(r * U + x)
+    assert (got ^ want) <= amb
+    assert c.origin[1] * U + c.origin[0] in got
+    assert np.abs(rho[sel] - rs[v[sel], u[sel]]).max() <= TOL
