@@ -457,24 +457,46 @@ def run_gpu(args, world, rank, local, pg):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     match_ev = []
-
     refine_ev = []
+    # the thresholds' segment sums as one launch over (tile, threshold)
+    # pairs where the library can fuse them (same template, one block each)
+    fused = len(segs) > 1
+    if fused:
+        try:
+            sncc.match_multi(segs, plans, tables, taus, mbs)
+        except sncc.SnccError as e:
+            if e.code != sncc.ERR_UNSUPPORTED:
+                raise
+            fused = False
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
 
     def step(record_match=False):
         sncc.integral(fd, tables, workspace=ws)
+        if fused:
+            a = ev() if record_match else None
+            sncc.match_multi(segs, plans, tables, taus, mbs)
+            prev = ev() if record_match else None
+            if record_match:
+                match_ev.append((-1, a, prev))
+            for i, s in enumerate(segs):
+                sncc.refine(fd, td, s, mbs[i], PRECISION, rbs[i])
+                if record_match:
+                    c = ev()
+                    refine_ev.append((i, prev, c))
+                    prev = c
+            return
         for i, s in enumerate(segs):
-            if record_match:
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                c = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
+            a = ev() if record_match else None
             sncc.match(s, plans[i], tables, taus[i], mbs[i])
-            if record_match:
-                b.record(stream)
-                match_ev.append((i, a, b))
+            b = ev() if record_match else None
             sncc.refine(fd, td, s, mbs[i], PRECISION, rbs[i])
             if record_match:
-                c.record(stream)
+                c = ev()
+                match_ev.append((i, a, b))
                 refine_ev.append((i, b, c))
 
     for _ in range(args.warmup):
@@ -517,9 +539,22 @@ def run_gpu(args, world, rank, local, pg):
         flush.fill_(k & 0xff)
         step(record_match=True)
     torch.cuda.synchronize()
-    per_sigma_ms = {i: [] for i in range(len(SIGMAS))}
+    per_sigma_ms = {i: [] for i in range(-1, len(SIGMAS))}
     for i, a, b in match_ev:
         per_sigma_ms[i].append(a.elapsed_time(b))
+    if fused:  # each threshold's segment sum launched on its own, for the per-threshold figures
+        for k in range(max(3, min(args.steps, 50))):
+            for i, s in enumerate(segs):
+                flush.fill_(k & 0xff)
+                a = ev()
+                sncc.match(s, plans[i], tables, taus[i], mbs[i])
+                b = ev()
+                per_sigma_ms[i].append((a, b))
+        torch.cuda.synchronize()
+        for i in range(len(SIGMAS)):
+            per_sigma_ms[i] = [a.elapsed_time(b) for a, b in per_sigma_ms[i]]
+        step()  # leave the step's own outputs in the buffers
+        torch.cuda.synchronize()
     refine_ms = {i: [] for i in range(len(SIGMAS))}
     for i, a, b in refine_ev:
         refine_ms[i].append(a.elapsed_time(b))
@@ -611,19 +646,23 @@ def run_gpu(args, world, rank, local, pg):
     # --- on-chip ceilings of the segment-sum kernel and the comparator ---
     ceil = measure_ceilings(sncc, torch, stream, dev)
 
-    # dominant kernel: the segment-sum launch with the most corners
+    # dominant kernel: the fused segment-sum launch, else the one with the
+    # most corners
     infos = [s.plan_info() for s in segs]
-    dom = max(range(len(SIGMAS)), key=lambda i: infos[i]["template_corners"])
+    dom_set = list(range(len(SIGMAS))) if fused else \
+        [max(range(len(SIGMAS)), key=lambda i: infos[i]["template_corners"])]
+    dom = dom_set[0] if not fused else -1
     dom_ms = statistics.mean(per_sigma_ms[dom])
-    dom_ops = U * V * infos[dom]["template_corners"]  # one multiply-add per (offset, corner)
+    # one multiply-add per (offset, corner)
+    dom_ops = U * V * sum(infos[i]["template_corners"] for i in dom_set)
     Rt = match_tile_rows(U, V)
-    pi = infos[dom]
     # table words a lane reads per R offsets: R + L - 1 per run of L corners
     # (the run counts describe the 32-bit-table layout; 64-bit tables on a
     # template of several blocks use the 64 x 64 layout)
     dom_words = None
-    if tables.s_bits == 32 or pi["blocks"] == 1:
-        dom_words = U * V * sum(pi["runs%d" % L] * (Rt + L - 1) for L in (8, 4, 2, 1)) / Rt
+    if tables.s_bits == 32 or all(infos[i]["blocks"] == 1 for i in dom_set):
+        dom_words = U * V * sum(infos[i]["runs%d" % L] * (Rt + L - 1) for i in dom_set for L in (8, 4, 2, 1)) / Rt
+    dom_runs = {L: sum(infos[i]["runs%d" % L] for i in dom_set) for L in (8, 4, 2, 1)}
 
     value = sum_over_ranks(pg, offsets_per_step) / (ms_per_step * 1e-3) / 1e9
     e2e_value = sum_over_ranks(pg, offsets_per_step) / (e2e_ms_step * 1e-3) / 1e9
@@ -653,7 +692,9 @@ def run_gpu(args, world, rank, local, pg):
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
         "config": dict(workload_config(args.workload, case, SIGMAS, PRECISION, U, V), seed=case_seed,
-                       launch="one CUDA graph per step: sum tables, then per threshold segment sum, exact "
+                       launch=("one CUDA graph per step: sum tables, one segment-sum launch over every "
+                               "(tile, threshold) pair, then per threshold exact refine and sort") if fused else
+                              "one CUDA graph per step: sum tables, then per threshold segment sum, exact "
                               "refine and sort"),
         "exact_ncc": {"value": U * V / (exact_ms * 1e-3) / 1e9, "unit": UNIT, "ms": exact_ms,
                       "kernel": "direct integer correlation, dp4a (4 byte MACs per instruction)",
@@ -674,13 +715,15 @@ def run_gpu(args, world, rank, local, pg):
                        "frac_of_hbm": (sat_bytes / (sat_med * 1e-3) / 1e9) / peaks_hbm if peaks_hbm else None,
                        "peak": "MEASURED_PEAKS hbm_gbs"},
         "paper_two_stage": two,
-        "roofline": segsum_roofline("match_kernel", dom_ops, dom_ms, ceil, traffic=recorded_traffic(args.workload),
-                                    smem_words=dom_words, sigma_max=SIGMAS[dom], tile_rows=Rt,
-                                    runs={L: pi["runs%d" % L] for L in (8, 4, 2, 1)},
-                                    hbm_peak_gbs=peaks.get("hbm_gbs")),
+        "roofline": segsum_roofline("match_kernel" + (" (fused over %d thresholds)" % len(SIGMAS) if fused else ""),
+                                    dom_ops, dom_ms, ceil, traffic=recorded_traffic(args.workload),
+                                    smem_words=dom_words, sigma_max=[SIGMAS[i] for i in dom_set], tile_rows=Rt,
+                                    runs=dom_runs, hbm_peak_gbs=peaks.get("hbm_gbs")),
+        "coarse_fused": {"ms": dom_ms, "separate_ms": sum(statistics.mean(per_sigma_ms[i]) for i in dom_set),
+                         "goffsets_s": len(SIGMAS) * U * V / (dom_ms * 1e-3) / 1e9} if fused else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h_total / e2e_steps, "ms_per_step": e2e_ms_step},
-        "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS + 3 * len(SIGMAS)),
+        "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS + (1 + 2 * len(SIGMAS) if fused else 3 * len(SIGMAS))),
         "clocks": clk, "wall_s_timed": wall,
     }
     if cpu is not None:

@@ -217,6 +217,34 @@ int sncc_match(const sncc_segments* seg, const void* d_plan, const void* d_s, in
                int sat_pitch, int M, int N, float tau, float* d_rho, int rho_pitch, int32_t* d_cand,
                int cand_cap, int32_t* d_count, int32_t* d_status, sncc_stream_t stream);
 
+/* Most approximations sncc_match_multi fuses into one launch. */
+#define SNCC_MULTI_MAX 4
+
+/*
+ * sncc_match_multi - sncc_match for n approximations of one template size
+ * in a single launch (Section 5 step 7 once per approximation, as in the
+ * multi-threshold search of Section 6).  The grid covers every (tile,
+ * approximation) pair, the approximation with most corners first, so the
+ * lighter ones fill the last wave of the heavier ones.  Output q (rho map,
+ * candidates, count) is bit-identical to sncc_match with segs[q],
+ * d_plans[q] and taus[q].
+ *
+ *   segs, d_plans, taus  n approximations, plans and thresholds
+ *   n                    1 .. SNCC_MULTI_MAX
+ *   d_rho                NULL, or n pointers (each NULL or a V x rho_pitch map)
+ *   d_cand, d_count      n pointers each; cand_cap applies to every list
+ *   d_status             one status word for all n (cleared first)
+ * The other arguments are those of sncc_match.  Returns
+ * SNCC_ERR_UNSUPPORTED unless every approximation has the same template
+ * size, at most 64 x 64 (one staged block of the same layout), and more
+ * than 64 corners (not summed in place); callers then use sncc_match.
+ * SNCC_ERR_UNIFORM when some Ek = 0 (nothing launched).
+ */
+int sncc_match_multi(const sncc_segments* const* segs, const void* const* d_plans, int n, const void* d_s,
+                     int s_bits, const int64_t* d_s2, int sat_pitch, int M, int N, const float* taus,
+                     float* const* d_rho, int rho_pitch, int32_t* const* d_cand, int cand_cap,
+                     int32_t* const* d_count, int32_t* d_status, sncc_stream_t stream);
+
 /* ------------------------------------------------------------------ */
 /* Fine pass: exact NCC at the candidates (GPU)                        */
 /* ------------------------------------------------------------------ */

@@ -33,6 +33,11 @@
 //    records are loaded one ahead of their use.
 //  * Direct mode: a template with at most 64 corners in all is summed by
 //    reading the table at its corners in place (no staging, no block edges).
+//  * Fused launch: several approximations of one template size (the
+//    thresholds of a multi-threshold search) in one grid, slice z = one
+//    approximation, the one with most corners first.  A launch of 8R-row
+//    tiles leaves the last wave partly empty; over the whole set the lighter
+//    slices fill it.
 //  * Epilogue: window sums from the global tables, exact integer variance
 //    n sum f^2 - (sum f)^2 divided by n in FP64, rho in FP32; the coarse pass
 //    appends candidates (v*U+u) with warp-aggregated atomics, the fine mode
@@ -42,6 +47,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -53,6 +59,20 @@
 
 namespace sncc {
 namespace {
+
+// One approximation of a fused multi-plan launch (sncc_match_multi): its
+// corner runs, normalisation constants, threshold and outputs.
+struct MultiPlan {
+    const int4* runblk;
+    const int4* runs;
+    long long Q0;
+    float Ek, scale, tau;
+    int cand_cap;
+    float* rho;
+    int32_t* cand;
+    int32_t* count;
+};
+constexpr int kMaxMultiPlans = SNCC_MULTI_MAX;
 
 struct MatchArgs {
     const int4* blocks;
@@ -84,6 +104,9 @@ struct MatchArgs {
     // direct mode: the whole template's corners {X, Y, G, 0}, read in place
     const int4* direct;
     int ndirect;
+    // multi-plan mode: several approximations of one template size, one block
+    int nplans;
+    MultiPlan mp[kMaxMultiPlans];
     int tiles_u;
     const uint32_t* cand_bits;
     sncc_match_t* out;
@@ -112,7 +135,59 @@ __device__ __forceinline__ void stage_region_tma(const CUtensorMap* map, int* bu
     }
 }
 
-template <int R, bool S64, int WP, bool PIPE, bool FINE, bool DIRECT>
+// Epilogue: normalise, threshold, compact (coarse: candidate indices and
+// the rho map; fine: (u, v, rho) records of the offsets whose candidate bit
+// is set).
+template <int R, bool S64, bool FINE>
+__device__ __forceinline__ void match_epilogue(const MatchArgs& a, const long long (&acc)[R], int u0, int v0, int lane,
+                                               int warp, float Ek, float scale, long long Q0, float tau, float* rho_map,
+                                               int32_t* cand, int cand_cap, int32_t* count) {
+    const int u = u0 + lane;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = v0 + warp * R + r;
+        bool valid = (u < a.U) && (v < a.V);
+        if constexpr (FINE) {
+            if (valid) {
+                const int idx = v * a.U + u;
+                valid = (a.cand_bits[idx >> 5] >> (idx & 31)) & 1u;
+            }
+        }
+        const float rho = valid ? normalise<S64>(acc[r], a.s, a.s2, a.pitch, u, v, a.W, a.H, a.n, a.inv_n, Ek,
+                                                 scale, Q0)
+                                : 0.0f;
+        if (!FINE && rho_map != nullptr && valid) rho_map[(size_t)v * a.rho_pitch + u] = rho;
+        const bool pred = valid && (rho >= tau);
+        const unsigned m = __ballot_sync(0xffffffffu, pred);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(FINE ? a.nout : count, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (pred) {
+                const int pos = base + __popc(m & ((1u << lane) - 1u));
+                if constexpr (FINE) {
+                    if (pos < a.out_cap) {
+                        sncc_match_t rec;
+                        rec.u = u;
+                        rec.v = v;
+                        rec.rho = rho;
+                        a.out[pos] = rec;
+                    } else {
+                        atomicOr(a.status, SNCC_STATUS_MATCH_OVERFLOW);
+                    }
+                } else {
+                    if (pos < cand_cap)
+                        cand[pos] = v * a.U + u;
+                    else
+                        atomicOr(a.status, SNCC_STATUS_CAND_OVERFLOW);
+                }
+            }
+        }
+    }
+}
+
+template <int R, bool S64, int WP, bool PIPE, bool FINE, bool DIRECT, bool MULTI>
 __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUtensorMap tmap, const MatchArgs a) {
     constexpr int NBUF = PIPE ? 2 : 1;
     extern __shared__ __align__(128) unsigned char smem_base[];
@@ -145,6 +220,13 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
     }
     __syncthreads();
 
+    // the corner runs: this launch's plan, or (fused launch) plan blockIdx.z
+    const int4* runs = a.runs;
+    const int4* runblk = a.runblk;
+    if constexpr (MULTI) {
+        runs = a.mp[blockIdx.z].runs;
+        runblk = a.mp[blockIdx.z].runblk;
+    }
     long long acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
@@ -217,7 +299,7 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
             __syncthreads();
             // ---- corner sum over vertical runs: one multiply-add per (offset, corner) ----
             const int* wbase = PIPE ? wbase0 + cur * WW : wbase0;
-            run_sum<R, WP>(acc, wbase, a.runs, __ldg(a.runblk + 2 * b), __ldg(a.runblk + 2 * b + 1));
+            run_sum<R, WP>(acc, wbase, runs, __ldg(runblk + 2 * b), __ldg(runblk + 2 * b + 1));
             __syncthreads();  // this buffer is restaged two blocks later (PIPE) or next block
             if (!S64 && !PIPE && b + 1 < a.nblk) {
                 const int4 nb = a.blocks[b + 1];
@@ -226,49 +308,13 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
         }
     }
 
-    // Epilogue: normalise, threshold, compact.
-    const int u = u0 + lane;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int v = v0 + warp * R + r;
-        bool valid = (u < a.U) && (v < a.V);
-        if constexpr (FINE) {
-            if (valid) {
-                const int idx = v * a.U + u;
-                valid = (a.cand_bits[idx >> 5] >> (idx & 31)) & 1u;
-            }
-        }
-        const float rho = valid ? normalise<S64>(acc[r], a.s, a.s2, a.pitch, u, v, a.W, a.H, a.n, a.inv_n, a.Ek,
-                                                 a.scale, a.Q0)
-                                : 0.0f;
-        if (!FINE && a.rho != nullptr && valid) a.rho[(size_t)v * a.rho_pitch + u] = rho;
-        const bool pred = valid && (rho >= a.tau);
-        const unsigned m = __ballot_sync(0xffffffffu, pred);
-        if (m) {
-            const int leader = __ffs(m) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(FINE ? a.nout : a.count, __popc(m));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (pred) {
-                const int pos = base + __popc(m & ((1u << lane) - 1u));
-                if constexpr (FINE) {
-                    if (pos < a.out_cap) {
-                        sncc_match_t rec;
-                        rec.u = u;
-                        rec.v = v;
-                        rec.rho = rho;
-                        a.out[pos] = rec;
-                    } else {
-                        atomicOr(a.status, SNCC_STATUS_MATCH_OVERFLOW);
-                    }
-                } else {
-                    if (pos < a.cand_cap)
-                        a.cand[pos] = v * a.U + u;
-                    else
-                        atomicOr(a.status, SNCC_STATUS_CAND_OVERFLOW);
-                }
-            }
-        }
+    if constexpr (MULTI) {
+        const MultiPlan& mp = a.mp[blockIdx.z];
+        match_epilogue<R, S64, false>(a, acc, u0, v0, lane, warp, mp.Ek, mp.scale, mp.Q0, mp.tau, mp.rho, mp.cand,
+                                      mp.cand_cap, mp.count);
+    } else {
+        match_epilogue<R, S64, FINE>(a, acc, u0, v0, lane, warp, a.Ek, a.scale, a.Q0, a.tau, a.rho, a.cand,
+                                     a.cand_cap, a.count);
     }
 }
 
@@ -309,7 +355,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-template <int R, bool S64, int WP, bool PIPE, bool FINE, bool DIRECT>
+template <int R, bool S64, int WP, bool PIPE, bool FINE, bool DIRECT, bool MULTI = false>
 cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
     constexpr int NBUF = PIPE ? 2 : 1;
     const int RH = DIRECT ? 0 : WARPS * R + BH + 1;  // direct mode stages nothing
@@ -319,23 +365,23 @@ cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cud
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP, PIPE, FINE, DIRECT>,
+        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP, PIPE, FINE, DIRECT, MULTI>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         128 + smem_words(WARPS * R + 64 + 1, WP, NBUF) * 4);
     });
     if (attr_err != cudaSuccess) return attr_err;
     const int tu = (a.U + TILE_U - 1) / TILE_U, tv = (a.V + WARPS * R - 1) / (WARPS * R);
-    const dim3 grid = FINE ? dim3(tu * tv) : dim3(tu, tv);
-    match_kernel<R, S64, WP, PIPE, FINE, DIRECT><<<grid, WARPS * 32, sm, st>>>(map, args);
+    const dim3 grid = FINE ? dim3(tu * tv) : dim3(tu, tv, MULTI ? a.nplans : 1);
+    match_kernel<R, S64, WP, PIPE, FINE, DIRECT, MULTI><<<grid, WARPS * 32, sm, st>>>(map, args);
     return cudaGetLastError();
 }
 
-template <bool S64, int WP, bool PIPE, bool FINE, bool DIRECT = false>
+template <bool S64, int WP, bool PIPE, bool FINE, bool DIRECT = false, bool MULTI = false>
 cudaError_t dispatch_r(int R, const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
     switch (R) {
-        case 8: return launch_match<8, S64, WP, PIPE, FINE, DIRECT>(map, a, BH, st);
-        case 4: return launch_match<4, S64, WP, PIPE, FINE, DIRECT>(map, a, BH, st);
-        default: return launch_match<2, S64, WP, PIPE, FINE, DIRECT>(map, a, BH, st);
+        case 8: return launch_match<8, S64, WP, PIPE, FINE, DIRECT, MULTI>(map, a, BH, st);
+        case 4: return launch_match<4, S64, WP, PIPE, FINE, DIRECT, MULTI>(map, a, BH, st);
+        default: return launch_match<2, S64, WP, PIPE, FINE, DIRECT, MULTI>(map, a, BH, st);
     }
 }
 
@@ -534,4 +580,72 @@ extern "C" int sncc_refine_segmented_tiles(const sncc_segments* seg, const void*
     if (launch_layout<true>(*L, s_bits == 64, R, map, a, st) != cudaSuccess) return SNCC_ERR_CUDA;
     if (launch_rank_sort(recs, d_nout, out_cap, a.U, d_out, st) != cudaSuccess) return SNCC_ERR_CUDA;
     return SNCC_OK;
+}
+
+extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* const* d_plans, int n, const void* d_s,
+                                int s_bits, const int64_t* d_s2, int sat_pitch, int M, int N, const float* taus,
+                                float* const* d_rho, int rho_pitch, int32_t* const* d_cand, int cand_cap,
+                                int32_t* const* d_count, int32_t* d_status, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_match_multi");
+    using namespace sncc;
+    if (!segs || !d_plans || !taus || !d_cand || !d_count || !d_status || n < 1 || n > SNCC_MULTI_MAX || cand_cap < 0)
+        return SNCC_ERR_ARG;
+    MatchArgs a;
+    CUtensorMap map;
+    int R = 0;
+    const Layout* L = nullptr;
+    const int rc = prepare_match(segs[0], d_plans[0], d_s, s_bits, d_s2, sat_pitch, M, N, taus[0], a, map, R, L);
+    if (rc != SNCC_OK) return rc;
+    if (d_rho && rho_pitch < a.U) return SNCC_ERR_ARG;
+    const bool s64 = (s_bits == 64);
+    // every approximation: the same template size, one staged block of the
+    // same layout (templates up to 64 x 64 that are not summed directly)
+    for (int q = 0; q < n; ++q) {
+        if (!segs[q] || !plan_of(segs[q]) || !d_plans[q] || (reinterpret_cast<uintptr_t>(d_plans[q]) & 15))
+            return SNCC_ERR_ARG;
+        if (segs[q]->W != segs[0]->W || segs[q]->H != segs[0]->H) return SNCC_ERR_ARG;
+        if ((cand_cap > 0 && !d_cand[q]) || !d_count[q]) return SNCC_ERR_ARG;
+        if (!(segs[q]->Ek > 0.0) || plan_of(segs[q])->image.empty()) return SNCC_ERR_UNIFORM;
+    }
+    // grid slice z = 0 is dispatched first: the approximations with the most
+    // corners go first, so that the lighter ones fill the last wave
+    int order[kMaxMultiPlans];
+    for (int q = 0; q < n; ++q) order[q] = q;
+    std::stable_sort(order, order + n, [&](int x, int y) {
+        return plan_of(segs[x])->template_corners > plan_of(segs[y])->template_corners;
+    });
+    for (int z = 0; z < n; ++z) {
+        const int q = order[z];
+        const Plan* p = plan_of(segs[q]);
+        const Layout& Lq = layout_for(*p, s64);
+        if (Lq.nblk != 1 || Lq.nbx * Lq.nby != 1 || Lq.WP != L->WP || Lq.BH != L->BH || p->direct_count > 0)
+            return SNCC_ERR_UNSUPPORTED;
+        MultiPlan& mp = a.mp[z];
+        mp.runblk = reinterpret_cast<const int4*>(static_cast<const char*>(d_plans[q]) + Lq.runblk_offset);
+        mp.runs = reinterpret_cast<const int4*>(static_cast<const char*>(d_plans[q]) + Lq.runs_offset);
+        mp.Q0 = p->Q0;
+        mp.Ek = (float)segs[q]->Ek;
+        mp.scale = (float)std::ldexp(1.0, -p->F);
+        mp.tau = taus[q];
+        mp.cand_cap = cand_cap;
+        mp.rho = d_rho ? d_rho[q] : nullptr;
+        mp.cand = d_cand[q];
+        mp.count = d_count[q];
+    }
+    a.nplans = n;
+    a.ndirect = 0;
+    a.rho_pitch = rho_pitch;
+    a.status = d_status;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int q = 0; q < n; ++q)
+        if (cudaMemsetAsync(d_count[q], 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
+    cudaError_t e;
+    if (L->WP == 68)
+        e = s64 ? dispatch_r<true, 68, false, false, false, true>(R, map, a, L->BH, st)
+                : dispatch_r<false, 68, false, false, false, true>(R, map, a, L->BH, st);
+    else
+        e = s64 ? dispatch_r<true, 100, false, false, false, true>(R, map, a, L->BH, st)
+                : dispatch_r<false, 100, false, false, false, true>(R, map, a, L->BH, st);
+    return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }

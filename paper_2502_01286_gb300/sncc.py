@@ -32,6 +32,7 @@ STATUS_CAND_OVERFLOW, STATUS_MATCH_OVERFLOW, STATUS_WAIT_TIMEOUT, STATUS_SORT_OV
 
 EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_sat_pitch",
             "sncc_integral_workspace_bytes", "sncc_integral", "sncc_plan_bytes", "sncc_plan_upload", "sncc_match",
+            "sncc_match_multi",
             "sncc_refine_workspace_bytes", "sncc_refine", "sncc_exact_map", "sncc_get_plan_info",
             "sncc_probe_smem_read", "sncc_probe_alu", "sncc_probe_wait_timeout", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_refine_segmented_tiles",
             "sncc_refine_segmented_tiles_workspace_bytes", "sncc_batch_create",
@@ -87,6 +88,9 @@ _lib.sncc_plan_bytes.restype = C.c_size_t
 _lib.sncc_plan_upload.argtypes = [C.POINTER(_Segments), _vp, C.c_size_t, _vp]
 _lib.sncc_match.argtypes = [C.POINTER(_Segments), _vp, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_float,
                             _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp]
+_lib.sncc_match_multi.argtypes = [C.POINTER(C.POINTER(_Segments)), C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp,
+                                  C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(_vp), C.c_int,
+                                  C.POINTER(_vp), C.c_int, C.POINTER(_vp), _vp, _vp]
 _lib.sncc_refine_workspace_bytes.argtypes = [C.c_int]
 _lib.sncc_refine_workspace_bytes.restype = C.c_size_t
 _lib.sncc_refine.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64,
@@ -327,6 +331,34 @@ def match(seg: Segments, plan, tables: Tables, tau: float, bufs: MatchBuffers, c
                            tables.pitch, tables.M, tables.N, float(tau), _ptr(bufs.rho), rho_pitch,
                            bufs.cand.data_ptr(), cap, bufs.count.data_ptr(), bufs.status.data_ptr(),
                            _stream(stream)), "sncc_match")
+
+
+MULTI_MAX = 4  # SNCC_MULTI_MAX
+
+
+def match_multi(segs, plans, tables: Tables, taus, bufs, cand_cap: Optional[int] = None, stream=None) -> None:
+    """sncc_match_multi: sncc_match for up to MULTI_MAX approximations of one
+    template size in one launch; bufs[q] receives what match() would write
+    for segs[q], except that the one status word is bufs[0].status.  Raises
+    SnccError with code ERR_UNSUPPORTED when the approximations do not fit
+    one fused launch (then call match() for each)."""
+    n = len(segs)
+    if not (len(plans) == len(taus) == len(bufs) == n):
+        raise ValueError("segs, plans, taus and bufs must have the same length")
+    cap = min(b.cand.numel() for b in bufs) if cand_cap is None else cand_cap
+    with_rho = [b.rho is not None for b in bufs]
+    rho_pitch = next((b.rho.stride(0) for b in bufs if b.rho is not None), 0)
+    if any(b.rho is not None and b.rho.stride(0) != rho_pitch for b in bufs):
+        raise ValueError("all rho maps must have the same row pitch")
+    seg_arr = (C.POINTER(_Segments) * n)(*[C.pointer(sg._s) for sg in segs])
+    plan_arr = (_vp * n)(*[pl.data_ptr() for pl in plans])
+    tau_arr = (C.c_float * n)(*[float(t) for t in taus])
+    rho_arr = (_vp * n)(*[_ptr(b.rho) for b in bufs]) if any(with_rho) else None
+    cand_arr = (_vp * n)(*[b.cand.data_ptr() for b in bufs])
+    count_arr = (_vp * n)(*[b.count.data_ptr() for b in bufs])
+    _check(_lib.sncc_match_multi(seg_arr, plan_arr, n, tables.s.data_ptr(), tables.s_bits, tables.s2.data_ptr(),
+                                 tables.pitch, tables.M, tables.N, tau_arr, rho_arr, rho_pitch, cand_arr, cap,
+                                 count_arr, bufs[0].status.data_ptr(), _stream(stream)), "sncc_match_multi")
 
 
 @dataclass

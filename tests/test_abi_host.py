@@ -166,6 +166,19 @@ def test_host_argument_errors(sncc):
     assert lib.sncc_refine_segmented_tiles(seg.ref(), None, None, 32, None, 32, 64, 64, None, None, 0, 0.5, None,
                                            0, None, None, 0, None, None) == sncc.ERR_ARG
     assert lib.sncc_integral_workspace_bytes(0, 5) == 0
+    # the fused multi-approximation match: 1 .. SNCC_MULTI_MAX approximations, all pointer arrays given
+    segs = (C.POINTER(sncc._Segments) * 5)(*[C.pointer(seg._s)] * 5)
+    ptrs = (C.c_void_p * 5)(*[256] * 5)
+    taus = (C.c_float * 5)(*[0.5] * 5)
+    for n in (0, 5):
+        assert lib.sncc_match_multi(segs, ptrs, n, C.c_void_p(256), 32, C.c_void_p(256), 96, 64, 64, taus, None, 0,
+                                    ptrs, 16, ptrs, C.c_void_p(256), None) == sncc.ERR_ARG
+    assert lib.sncc_match_multi(None, ptrs, 2, C.c_void_p(256), 32, C.c_void_p(256), 96, 64, 64, taus, None, 0,
+                                ptrs, 16, ptrs, C.c_void_p(256), None) == sncc.ERR_ARG
+    assert lib.sncc_match_multi(segs, ptrs, 2, C.c_void_p(256), 32, C.c_void_p(256), 96, 64, 64, None, None, 0,
+                                ptrs, 16, ptrs, C.c_void_p(256), None) == sncc.ERR_ARG
+    assert lib.sncc_match_multi(segs, ptrs, 2, C.c_void_p(256), 32, C.c_void_p(256), 96, 64, 64, taus, None, 0,
+                                ptrs, 16, ptrs, None, None) == sncc.ERR_ARG
 
 
 def test_batch_host_work_lists(sncc):

@@ -175,6 +175,74 @@ def test_match_direct_sparse_multiblock_template(sncc, bits):
     check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, 0.5 * seg.rho_max)
 
 
+MULTI_CASES = [
+    # (M, N, W, H, bits, sigmas)
+    (256, 256, 32, 32, 32, (2.0, 4.0, 8.0)),
+    (70, 45, 13, 9, 32, (0.5, 1.0, 2.0, 3.0)),        # ragged tails, four approximations
+    (300, 200, 64, 48, 64, (3.0, 6.0)),               # 64-bit tables
+    (1920, 1080, 64, 64, 32, (5.0, 10.0, 20.0)),      # the HD workload's three thresholds
+    (130, 90, 40, 40, 32, (5.0,)),                    # a single approximation
+]
+
+
+@pytest.mark.parametrize("M,N,W,H,bits,sigmas", MULTI_CASES)
+def test_match_multi_equals_separate_calls(sncc, M, N, W, H, bits, sigmas):
+    """sncc_match_multi stages each tile once for all approximations; every
+    output (map, candidate set, count) is bit-identical to its own
+    sncc_match, and the maps agree with the oracle."""
+    c = synth.case_hd(M=M, N=N, W=W, H=H, seed=77 + W + len(sigmas))
+    segs = [sncc.build_segments(c.t, s) for s in sigmas]
+    for sg in segs:
+        assert sg.Ek > 0 and sg.plan_info()["template_corners"] > 64
+    fd = dev(c.f)
+    tb = sncc.integral(fd, s_bits=bits)
+    plans = [sncc.upload_plan(sg) for sg in segs]
+    taus = [0.6 * sg.rho_max for sg in segs]
+    sep = [sncc.alloc_match(M, N, W, H, 1 << 20) for _ in segs]
+    for sg, pl, tau, mb in zip(segs, plans, taus, sep):
+        sncc.match(sg, pl, tb, tau, mb)
+    fused = [sncc.alloc_match(M, N, W, H, 1 << 20) for _ in segs]
+    sncc.match_multi(segs, plans, tb, taus, fused)
+    torch.cuda.synchronize()
+    assert int(fused[0].status.item()) == 0
+    V, U = N - H + 1, M - W + 1
+    rows = np.unique(np.r_[0, V - 1, np.random.default_rng(M).choice(V, min(V, 6), replace=False)])
+    for q, (a, b) in enumerate(zip(sep, fused)):
+        assert torch.equal(a.rho, b.rho), q
+        n = int(a.count.item())
+        assert int(b.count.item()) == n
+        np.testing.assert_array_equal(np.sort(a.cand[:n].cpu().numpy()), np.sort(b.cand[:n].cpu().numpy()))
+        ap = O.precompute_template_approximation(c.t, sigmas[q])
+        ref = O.segmented_ncc_map(c.f, ap, "sat", rows=rows)
+        assert np.abs(b.rho.cpu().numpy()[rows] - ref[rows]).max() <= TOL
+
+
+def test_match_multi_rejects_what_it_cannot_fuse(sncc):
+    """Templates of different sizes are an argument error; a multi-block
+    template, or one summed in place (at most 64 corners), is not fused
+    (SNCC_ERR_UNSUPPORTED) and needs sncc_match."""
+    c = synth.case_plain(M=300, N=260, W=130, H=100, seed=3)
+    fd = dev(c.f)
+    tb = sncc.integral(fd)
+    small = synth.case_hd(M=300, N=260, W=48, H=40, seed=4)
+    boxes = np.full((40, 48), 50, np.uint8)   # three flat rectangles: a handful of corners
+    boxes[5:20, 8:30] = 180
+    boxes[25:35, 10:40] = 90
+    sparse = sncc.build_segments(boxes, 1.0)
+    assert 0 < sparse.plan_info()["template_corners"] <= 64
+    cases = [
+        ([sncc.build_segments(c.t, 6.0)], sncc.ERR_UNSUPPORTED),                      # 130 x 100
+        ([sncc.build_segments(small.t, 4.0), sncc.build_segments(c.t, 4.0)], sncc.ERR_ARG),
+        ([sncc.build_segments(small.t, 4.0), sparse], sncc.ERR_UNSUPPORTED),
+    ]
+    for segs, code in cases:
+        plans = [sncc.upload_plan(sg) for sg in segs]
+        bufs = [sncc.alloc_match(300, 260, segs[0].W, segs[0].H, 1024) for _ in segs]
+        with pytest.raises(sncc.SnccError) as e:
+            sncc.match_multi(segs, plans, tb, [0.5] * len(segs), bufs)
+        assert e.value.code == code
+
+
 def test_match_repeatable(sncc):
     c = synth.case_plain()
     _, _, _, a = run_match(sncc, c.f, c.t, 10.0, 0.5)
