@@ -462,6 +462,7 @@ def run_gpu(args, world, rank, local, pg):
     # pairs where the library can fuse them (same template, one block each)
     fused = len(segs) > 1
     if fused:
+        sncc.integral(fd, tables, workspace=ws)
         try:
             sncc.match_multi(segs, plans, tables, taus, mbs)
         except sncc.SnccError as e:
@@ -657,10 +658,10 @@ def run_gpu(args, world, rank, local, pg):
     dom_ops = U * V * sum(infos[i]["template_corners"] for i in dom_set)
     Rt = match_tile_rows(U, V)
     # table words a lane reads per R offsets: R + L - 1 per run of L corners
-    # (the run counts describe the 32-bit-table layout; 64-bit tables on a
-    # template of several blocks use the 64 x 64 layout)
+    # (the run counts describe the one-block layout; a template of several
+    # blocks uses the 64 x 64 layout, whose runs the plan summary omits)
     dom_words = None
-    if tables.s_bits == 32 or all(infos[i]["blocks"] == 1 for i in dom_set):
+    if all(infos[i]["blocks"] == 1 for i in dom_set):
         dom_words = U * V * sum(infos[i]["runs%d" % L] * (Rt + L - 1) for i in dom_set for L in (8, 4, 2, 1)) / Rt
     dom_runs = {L: sum(infos[i]["runs%d" % L] for i in dom_set) for L in (8, 4, 2, 1)}
 
@@ -702,7 +703,7 @@ def run_gpu(args, world, rank, local, pg):
         "speedup_vs_exact": value / (U * V / (exact_ms * 1e-3) / 1e9),
         "max_abs_dncc_vs_exact": dict(zip([str(s) for s in SIGMAS], max_dncc)),
         "per_sigma": [{"sigma_max": s, "K": seg.K, "corners": infos[i]["template_corners"],
-                       "block_corners": infos[i]["corners"] if tables.s_bits == 32 or infos[i]["blocks"] == 1
+                       "block_corners": infos[i]["corners"] if infos[i]["blocks"] == 1
                        else infos[i]["wide_corners"], "rho_max": seg.rho_max,
                        "tau_c": taus[i], "match_ms": statistics.mean(per_sigma_ms[i]),
                        "refine_ms": statistics.mean(refine_ms[i]),

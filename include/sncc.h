@@ -501,8 +501,9 @@ int sncc_exact_map(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t
 /* ------------------------------------------------------------------ */
 
 /* Shape of the matching plan built by sncc_build_segments.  blocks ..
- * runs1 describe the block layout used with 32-bit tables: one block for a
- * template up to 64 x 64, else blocks of 32 x 32. */
+ * runs1 describe the first block layout: one block for a template up to
+ * 64 x 64 (the layout the segment-sum kernel uses for such templates),
+ * else blocks of 32 x 32 (the per-candidate fine pass). */
 typedef struct {
     int32_t F;            /* fraction bits of the fixed-point weights q_i */
     int32_t blocks;       /* template blocks that hold at least one corner */
@@ -518,7 +519,7 @@ typedef struct {
     int32_t template_corners; /* nonzero corners of the whole template taken as one block: the
                                  algorithmic multiply-adds per offset (block edges add corners) */
     int32_t wide_blocks;  /* blocks and nonzero corners of the 64 x 64 block layout, which the */
-    int32_t wide_corners; /* segment-sum kernel uses with 64-bit tables for larger templates */
+    int32_t wide_corners; /* segment-sum kernels use for templates larger than 64 x 64 */
 } sncc_plan_info;
 
 /* Fills *out for seg; SNCC_ERR_UNIFORM when seg has no plan (Ek = 0). */

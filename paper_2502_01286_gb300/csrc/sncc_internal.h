@@ -33,7 +33,7 @@ struct NvtxRange {
 constexpr int TILE_U = 32;
 constexpr int WARPS = 8;
 constexpr int BLOCK_SINGLE_MAX = 64;  // a template up to 64 x 64 is one block
-constexpr int BLOCK_MULTI = 32;       // larger templates use 32 x 32 blocks
+constexpr int BLOCK_MULTI = 32;       // first layout of larger templates: 32 x 32 blocks
 
 // Host-side matching plan (built by sncc_build_segments).
 //
@@ -85,10 +85,11 @@ struct Plan {
     double n = 0.0;         // W * H
     int template_corners = 0;  // corners of the whole template taken as one block
     // lay[0]: a template up to 64 x 64 is one block (pitch 68 when it is at
-    // most 32 wide, else 100); larger ones use 32 x 32 blocks (pitch 68),
-    // which the 32-bit-table kernel double-buffers.  lay[1]: blocks of at
-    // most 64 x 64 with pitch 100, used with 64-bit tables (fewer, larger
-    // blocks halve the register staging per corner) and by the batched kernel.
+    // most 32 wide, else 100), the segment-sum kernel's layout for it;
+    // larger ones use 32 x 32 blocks (pitch 68), read by the per-candidate
+    // fine pass.  lay[1]: blocks of at most 64 x 64 with pitch 100, the
+    // segment-sum kernels' layout for templates larger than 64 x 64 (fewer,
+    // larger blocks halve the staged entries per corner).
     Layout lay[2];
     // Templates with at most DIRECT_MAX corners in all also carry their
     // whole-template corner list, int4 {X, Y, G, 0}, at direct_offset: the
@@ -110,10 +111,9 @@ Plan* plan_of(const sncc_segments* s);
 // Fills p from seg's segment table (defined in sncc_host.cpp).
 int build_plan(const sncc_segments* seg, Plan& p);
 
-// The layout the single-problem kernels use with a table of s_bits bits.
-inline const Layout& layout_for(const Plan& p, bool s64) {
-    return (s64 && p.lay[0].nbx * p.lay[0].nby > 1) ? p.lay[1] : p.lay[0];
-}
+// The layout the single-problem segment-sum kernel uses: one block for a
+// template up to 64 x 64, else 64 x 64 blocks.
+inline const Layout& layout_for(const Plan& p) { return (p.lay[0].nbx * p.lay[0].nby > 1) ? p.lay[1] : p.lay[0]; }
 
 // Writes the first min(*d_n, cap) records of `in` to `out` in ascending
 // v*U+u order (keys are distinct).  Defined in sncc_refine.cu.

@@ -111,7 +111,7 @@ SHAPES = [
     (256, 256, 32, 32, 10.0),   # the 256^2 / 32^2 workload, sigma 10
     (70, 45, 13, 9, 3.0),       # ragged tail in both directions
     (100, 100, 64, 64, 5.0),    # largest single-block template
-    (130, 90, 100, 70, 6.0),    # multi-block template (32 x 32 blocks, ragged)
+    (130, 90, 100, 70, 6.0),    # multi-block template (64 x 64 blocks, ragged)
     (40, 300, 40, 17, 4.0),     # U = 1
     (300, 40, 23, 40, 4.0),     # V = 1
     (120, 110, 37, 29, 0.0),    # sigma 0: every pixel its own segment before merging
@@ -142,10 +142,9 @@ def test_match_map_and_candidates(sncc, M, N, W, H, sigma):
 @pytest.mark.parametrize("M,N,W,H", [(200, 150, 48, 40), (300, 260, 130, 129), (420, 150, 97, 65)])
 @pytest.mark.parametrize("bits", [32, 64])
 def test_match_table_width_independent(sncc, bits, M, N, W, H):
-    """The same source through 32- and 64-bit sum tables gives one map.  The
-    multi-block templates use 32 x 32 blocks with 32-bit tables and 64 x 64
-    blocks with 64-bit ones (ragged edge blocks; tiles inside the table and
-    on its edge)."""
+    """The same source through 32- and 64-bit sum tables gives one map: one
+    TMA-staged block, and templates of several 64 x 64 blocks staged through
+    registers (ragged edge blocks; tiles inside the table and on its edge)."""
     c = synth.case_plain(M=M, N=N, W=W, H=H, seed=11 + W)
     ap = O.precompute_template_approximation(c.t, 7.0)
     seg, _, _, mb = run_match(sncc, c.f, c.t, 7.0, 0.5, s_bits=bits)
