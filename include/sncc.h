@@ -232,8 +232,9 @@ int sncc_match(const sncc_segments* seg, const void* d_plan, const void* d_s, in
  *   segs, d_plans, taus  n approximations, plans and thresholds
  *   n                    1 .. SNCC_MULTI_MAX
  *   d_rho                NULL, or n pointers (each NULL or a V x rho_pitch map)
- *   d_cand, d_count      n pointers each; cand_cap applies to every list
- *   d_status             one status word for all n (cleared first)
+ *   d_cand, d_count,     n pointers each; cand_cap applies to every list;
+ *   d_status             status word q is cleared first and receives the
+ *                        bits of approximation q
  * The other arguments are those of sncc_match.  Returns
  * SNCC_ERR_UNSUPPORTED unless every approximation has the same template
  * size, at most 64 x 64 (one staged block of the same layout), and more
@@ -243,7 +244,7 @@ int sncc_match(const sncc_segments* seg, const void* d_plan, const void* d_s, in
 int sncc_match_multi(const sncc_segments* const* segs, const void* const* d_plans, int n, const void* d_s,
                      int s_bits, const int64_t* d_s2, int sat_pitch, int M, int N, const float* taus,
                      float* const* d_rho, int rho_pitch, int32_t* const* d_cand, int cand_cap,
-                     int32_t* const* d_count, int32_t* d_status, sncc_stream_t stream);
+                     int32_t* const* d_count, int32_t* const* d_status, sncc_stream_t stream);
 
 /* ------------------------------------------------------------------ */
 /* Fine pass: exact NCC at the candidates (GPU)                        */

@@ -72,6 +72,7 @@ struct MultiPlan {
     float* rho;
     int32_t* cand;
     int32_t* count;
+    int32_t* status;
 };
 constexpr int kMaxMultiPlans = SNCC_MULTI_MAX;
 
@@ -140,7 +141,7 @@ __device__ __forceinline__ void stage_region_tma(const CUtensorMap* map, int* bu
 template <int R, bool S64, bool FINE>
 __device__ __forceinline__ void match_epilogue(const MatchArgs& a, const long long (&acc)[R], int u0, int v0, int lane,
                                                int warp, float Ek, float scale, long long Q0, float tau, float* rho_map,
-                                               int32_t* cand, int cand_cap, int32_t* count) {
+                                               int32_t* cand, int cand_cap, int32_t* count, int32_t* status) {
     const int u = u0 + lane;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -173,13 +174,13 @@ __device__ __forceinline__ void match_epilogue(const MatchArgs& a, const long lo
                         rec.rho = rho;
                         a.out[pos] = rec;
                     } else {
-                        atomicOr(a.status, SNCC_STATUS_MATCH_OVERFLOW);
+                        atomicOr(status, SNCC_STATUS_MATCH_OVERFLOW);
                     }
                 } else {
                     if (pos < cand_cap)
                         cand[pos] = v * a.U + u;
                     else
-                        atomicOr(a.status, SNCC_STATUS_CAND_OVERFLOW);
+                        atomicOr(status, SNCC_STATUS_CAND_OVERFLOW);
                 }
             }
         }
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
                 if (tid == 0 && !mbar_wait_bounded(bar, parity)) *flag = 1;
                 __syncthreads();
                 if (*flag) {
-                    if (tid == 0) atomicOr(a.status, SNCC_STATUS_WAIT_TIMEOUT);
+                    if (tid == 0) atomicOr(MULTI ? a.mp[blockIdx.z].status : a.status, SNCC_STATUS_WAIT_TIMEOUT);
                     return;
                 }
                 (void)mbar_try_wait(bar, parity);  // phase complete: acquire for this thread
@@ -286,10 +287,10 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
     if constexpr (MULTI) {
         const MultiPlan& mp = a.mp[blockIdx.z];
         match_epilogue<R, S64, false>(a, acc, u0, v0, lane, warp, mp.Ek, mp.scale, mp.Q0, mp.tau, mp.rho, mp.cand,
-                                      mp.cand_cap, mp.count);
+                                      mp.cand_cap, mp.count, mp.status);
     } else {
         match_epilogue<R, S64, FINE>(a, acc, u0, v0, lane, warp, a.Ek, a.scale, a.Q0, a.tau, a.rho, a.cand,
-                                     a.cand_cap, a.count);
+                                     a.cand_cap, a.count, a.status);
     }
 }
 
@@ -557,11 +558,19 @@ extern "C" int sncc_refine_segmented_tiles(const sncc_segments* seg, const void*
 extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* const* d_plans, int n, const void* d_s,
                                 int s_bits, const int64_t* d_s2, int sat_pitch, int M, int N, const float* taus,
                                 float* const* d_rho, int rho_pitch, int32_t* const* d_cand, int cand_cap,
-                                int32_t* const* d_count, int32_t* d_status, sncc_stream_t stream) {
+                                int32_t* const* d_count, int32_t* const* d_status, sncc_stream_t stream) {
     sncc::NvtxRange nvtx_range("sncc_match_multi");
     using namespace sncc;
     if (!segs || !d_plans || !taus || !d_cand || !d_count || !d_status || n < 1 || n > SNCC_MULTI_MAX || cand_cap < 0)
         return SNCC_ERR_ARG;
+    // every approximation: the same template size, its own outputs
+    for (int q = 0; q < n; ++q) {
+        if (!segs[q] || !plan_of(segs[q]) || !d_plans[q] || (reinterpret_cast<uintptr_t>(d_plans[q]) & 15))
+            return SNCC_ERR_ARG;
+        if (segs[q]->W != segs[0]->W || segs[q]->H != segs[0]->H) return SNCC_ERR_ARG;
+        if ((cand_cap > 0 && !d_cand[q]) || !d_count[q] || !d_status[q]) return SNCC_ERR_ARG;
+        if (!(segs[q]->Ek > 0.0) || plan_of(segs[q])->image.empty()) return SNCC_ERR_UNIFORM;
+    }
     MatchArgs a;
     CUtensorMap map;
     int R = 0;
@@ -570,15 +579,8 @@ extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* co
     if (rc != SNCC_OK) return rc;
     if (d_rho && rho_pitch < a.U) return SNCC_ERR_ARG;
     const bool s64 = (s_bits == 64);
-    // every approximation: the same template size, one staged block of the
-    // same layout (templates up to 64 x 64 that are not summed directly)
-    for (int q = 0; q < n; ++q) {
-        if (!segs[q] || !plan_of(segs[q]) || !d_plans[q] || (reinterpret_cast<uintptr_t>(d_plans[q]) & 15))
-            return SNCC_ERR_ARG;
-        if (segs[q]->W != segs[0]->W || segs[q]->H != segs[0]->H) return SNCC_ERR_ARG;
-        if ((cand_cap > 0 && !d_cand[q]) || !d_count[q]) return SNCC_ERR_ARG;
-        if (!(segs[q]->Ek > 0.0) || plan_of(segs[q])->image.empty()) return SNCC_ERR_UNIFORM;
-    }
+    // and one staged block of the same layout each (templates up to 64 x 64
+    // that are not summed directly)
     // grid slice z = 0 is dispatched first: the approximations with the most
     // corners go first, so that the lighter ones fill the last wave
     int order[kMaxMultiPlans];
@@ -603,15 +605,17 @@ extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* co
         mp.rho = d_rho ? d_rho[q] : nullptr;
         mp.cand = d_cand[q];
         mp.count = d_count[q];
+        mp.status = d_status[q];
     }
     a.nplans = n;
     a.ndirect = 0;
     a.rho_pitch = rho_pitch;
-    a.status = d_status;
+    a.status = a.mp[0].status;
     cudaStream_t st = (cudaStream_t)stream;
     for (int q = 0; q < n; ++q)
-        if (cudaMemsetAsync(d_count[q], 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
-    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
+        if (cudaMemsetAsync(d_count[q], 0, sizeof(int32_t), st) != cudaSuccess ||
+            cudaMemsetAsync(d_status[q], 0, sizeof(int32_t), st) != cudaSuccess)
+            return SNCC_ERR_CUDA;
     cudaError_t e;
     if (L->WP == 68)
         e = s64 ? dispatch_r<true, 68, false, false, true>(R, map, a, L->BH, st)

@@ -90,7 +90,7 @@ _lib.sncc_match.argtypes = [C.POINTER(_Segments), _vp, _vp, C.c_int, _vp, C.c_in
                             _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp]
 _lib.sncc_match_multi.argtypes = [C.POINTER(C.POINTER(_Segments)), C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp,
                                   C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(_vp), C.c_int,
-                                  C.POINTER(_vp), C.c_int, C.POINTER(_vp), _vp, _vp]
+                                  C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp), _vp]
 _lib.sncc_refine_workspace_bytes.argtypes = [C.c_int]
 _lib.sncc_refine_workspace_bytes.restype = C.c_size_t
 _lib.sncc_refine.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64,
@@ -339,7 +339,7 @@ MULTI_MAX = 4  # SNCC_MULTI_MAX
 def match_multi(segs, plans, tables: Tables, taus, bufs, cand_cap: Optional[int] = None, stream=None) -> None:
     """sncc_match_multi: sncc_match for up to MULTI_MAX approximations of one
     template size in one launch; bufs[q] receives what match() would write
-    for segs[q], except that the one status word is bufs[0].status.  Raises
+    for segs[q] (including bufs[q].status).  Raises
     SnccError with code ERR_UNSUPPORTED when the approximations do not fit
     one fused launch (then call match() for each)."""
     n = len(segs)
@@ -356,9 +356,10 @@ def match_multi(segs, plans, tables: Tables, taus, bufs, cand_cap: Optional[int]
     rho_arr = (_vp * n)(*[_ptr(b.rho) for b in bufs]) if any(with_rho) else None
     cand_arr = (_vp * n)(*[b.cand.data_ptr() for b in bufs])
     count_arr = (_vp * n)(*[b.count.data_ptr() for b in bufs])
+    status_arr = (_vp * n)(*[b.status.data_ptr() for b in bufs])
     _check(_lib.sncc_match_multi(seg_arr, plan_arr, n, tables.s.data_ptr(), tables.s_bits, tables.s2.data_ptr(),
                                  tables.pitch, tables.M, tables.N, tau_arr, rho_arr, rho_pitch, cand_arr, cap,
-                                 count_arr, bufs[0].status.data_ptr(), _stream(stream)), "sncc_match_multi")
+                                 count_arr, status_arr, _stream(stream)), "sncc_match_multi")
 
 
 @dataclass
@@ -574,6 +575,64 @@ class Matcher:
 
     def status(self) -> int:
         return int(self.mb.status.item())
+
+
+class MultiMatcher:
+    """Segmented-NCC matching of one template at several std thresholds (one
+    approximation each) on one GPU, e.g. the thresholds of a multi-threshold
+    search.  run(): the sum tables once, the coarse passes of every
+    approximation in one fused launch where the library accepts them
+    (sncc_match_multi: same template, up to 64 x 64, more than 64 corners
+    each), else one launch each, then the exact refine of each approximation.
+    Output q lives in mbs[q] / rbs[q]."""
+
+    def __init__(self, t: np.ndarray, sigmas, M: int, N: int, precision: float = 0.85,
+                 tau_exact: Optional[float] = None, k_max: int = 0, cand_cap: int = 1 << 20, out_cap: int = 1 << 16,
+                 keep_rho: bool = True, device="cuda"):
+        torch = _torch()
+        self.segs = [build_segments(t, sg, k_max) for sg in sigmas]
+        if not all(sg.Ek > 0 for sg in self.segs):
+            raise SnccError(ERR_UNIFORM, "MultiMatcher")
+        self.M, self.N = M, N
+        self.W, self.H = self.segs[0].W, self.segs[0].H
+        self.taus = [float(precision) * sg.rho_max for sg in self.segs]
+        self.tau_e = float(precision) if tau_exact is None else float(tau_exact)
+        self.t_dev = torch.as_tensor(np.ascontiguousarray(t, np.uint8)).to(device)
+        self.plans = [upload_plan(sg, device) for sg in self.segs]
+        self.tables = alloc_tables(M, N, None, device)
+        self.ws = integral_workspace(M, N, device)
+        self.mbs = [alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device) for _ in self.segs]
+        self.rbs = [alloc_refine(out_cap, device) for _ in self.segs]
+        self.fused = None if len(self.segs) > 1 and MULTI_MAX >= len(self.segs) else False
+
+    def run(self, f, stream=None):
+        """Launch the whole path on a (N, M) uint8 CUDA tensor (asynchronous).
+        The first run finds out whether the coarse passes fuse (the library
+        decides before it launches anything)."""
+        integral(f, self.tables, workspace=self.ws, stream=stream)
+        if self.fused is not False:
+            try:
+                match_multi(self.segs, self.plans, self.tables, self.taus, self.mbs, stream=stream)
+                self.fused = True
+            except SnccError as e:
+                if e.code != ERR_UNSUPPORTED or self.fused:
+                    raise
+                self.fused = False
+        if not self.fused:
+            for sg, pl, tau, mb in zip(self.segs, self.plans, self.taus, self.mbs):
+                match(sg, pl, self.tables, tau, mb, stream=stream)
+        for sg, mb, rb in zip(self.segs, self.mbs, self.rbs):
+            refine(f, self.t_dev, sg, mb, self.tau_e, rb, stream=stream)
+
+    def capture(self, f):
+        """Record run(f) in a CUDA graph (after one eager warm-up run)."""
+        return capture_graph(lambda: self.run(f))
+
+    def status(self) -> int:
+        s = 0
+        for mb in self.mbs:
+            s |= int(mb.status.item())
+        return s
 
 
 # ---------------------------------------------------------------------------

@@ -172,13 +172,16 @@ def test_host_argument_errors(sncc):
     taus = (C.c_float * 5)(*[0.5] * 5)
     for n in (0, 5):
         assert lib.sncc_match_multi(segs, ptrs, n, C.c_void_p(256), 32, C.c_void_p(256), 96, 64, 64, taus, None, 0,
-                                    ptrs, 16, ptrs, C.c_void_p(256), None) == sncc.ERR_ARG
+                                    ptrs, 16, ptrs, ptrs, None) == sncc.ERR_ARG
     assert lib.sncc_match_multi(None, ptrs, 2, C.c_void_p(256), 32, C.c_void_p(256), 96, 64, 64, taus, None, 0,
-                                ptrs, 16, ptrs, C.c_void_p(256), None) == sncc.ERR_ARG
+                                ptrs, 16, ptrs, ptrs, None) == sncc.ERR_ARG
     assert lib.sncc_match_multi(segs, ptrs, 2, C.c_void_p(256), 32, C.c_void_p(256), 96, 64, 64, None, None, 0,
-                                ptrs, 16, ptrs, C.c_void_p(256), None) == sncc.ERR_ARG
+                                ptrs, 16, ptrs, ptrs, None) == sncc.ERR_ARG
     assert lib.sncc_match_multi(segs, ptrs, 2, C.c_void_p(256), 32, C.c_void_p(256), 96, 64, 64, taus, None, 0,
                                 ptrs, 16, ptrs, None, None) == sncc.ERR_ARG
+    nulls = (C.c_void_p * 5)(256, None, 256, 256, 256)  # a missing status word
+    assert lib.sncc_match_multi(segs, ptrs, 2, C.c_void_p(256), 32, C.c_void_p(256), 96, 64, 64, taus, None, 0,
+                                ptrs, 16, ptrs, nulls, None) == sncc.ERR_ARG
 
 
 def test_batch_host_work_lists(sncc):

@@ -203,7 +203,7 @@ def test_match_multi_equals_separate_calls(sncc, M, N, W, H, bits, sigmas):
     fused = [sncc.alloc_match(M, N, W, H, 1 << 20) for _ in segs]
     sncc.match_multi(segs, plans, tb, taus, fused)
     torch.cuda.synchronize()
-    assert int(fused[0].status.item()) == 0
+    assert all(int(b.status.item()) == 0 for b in fused)
     V, U = N - H + 1, M - W + 1
     rows = np.unique(np.r_[0, V - 1, np.random.default_rng(M).choice(V, min(V, 6), replace=False)])
     for q, (a, b) in enumerate(zip(sep, fused)):
@@ -214,6 +214,53 @@ def test_match_multi_equals_separate_calls(sncc, M, N, W, H, bits, sigmas):
         ap = O.precompute_template_approximation(c.t, sigmas[q])
         ref = O.segmented_ncc_map(c.f, ap, "sat", rows=rows)
         assert np.abs(b.rho.cpu().numpy()[rows] - ref[rows]).max() <= TOL
+
+
+def test_match_multi_overflow_per_approximation(sncc):
+    """Each approximation's count stays exact and its own status word gets
+    the overflow bit when its list is longer than cand_cap."""
+    c = synth.case_hd(M=200, N=150, W=40, H=40, seed=31)
+    segs = [sncc.build_segments(c.t, s) for s in (2.0, 6.0)]
+    fd = dev(c.f)
+    tb = sncc.integral(fd)
+    plans = [sncc.upload_plan(sg) for sg in segs]
+    bufs = [sncc.alloc_match(200, 150, 40, 40, 64) for _ in segs]
+    sncc.match_multi(segs, plans, tb, [-1.0, 2.0], bufs)  # every offset / no offset
+    torch.cuda.synchronize()
+    assert int(bufs[0].count.item()) == 161 * 111
+    assert int(bufs[0].status.item()) == sncc.STATUS_CAND_OVERFLOW
+    assert int(bufs[1].count.item()) == 0 and int(bufs[1].status.item()) == 0
+
+
+def test_multi_matcher_graph_and_separate_matchers(sncc):
+    """MultiMatcher fuses three thresholds of one template; a captured run
+    replayed on a new source equals the eager run, and each threshold's
+    match list equals that of its own Matcher."""
+    a = synth.case_hd(M=400, N=300, W=48, H=48, seed=41)
+    b = synth.case_hd(M=400, N=300, W=48, H=48, seed=42)
+    sig = (3.0, 6.0, 12.0)
+    mm = sncc.MultiMatcher(b.t, sig, 400, 300, precision=0.6)
+    fd = dev(a.f)
+    g = mm.capture(fd)
+    assert mm.fused is True
+    fd.copy_(dev(b.f))
+    g.replay()
+    torch.cuda.synchronize()
+    got = [[x.copy() for x in sncc.matches_to_numpy(rb)] for rb in mm.rbs]
+    mm.run(fd)
+    torch.cuda.synchronize()
+    assert mm.status() == 0
+    for q, s in enumerate(sig):
+        want = sncc.matches_to_numpy(mm.rbs[q])
+        assert len(want[0]) > 0
+        for x, y in zip(got[q], want):
+            np.testing.assert_array_equal(x, y)
+        one = sncc.Matcher(b.t, s, 400, 300, precision=0.6)
+        one.run(fd)
+        torch.cuda.synchronize()
+        assert torch.equal(one.mb.rho, mm.mbs[q].rho)
+        for x, y in zip(sncc.matches_to_numpy(one.rb), want):
+            np.testing.assert_array_equal(x, y)
 
 
 def test_match_multi_rejects_what_it_cannot_fuse(sncc):
