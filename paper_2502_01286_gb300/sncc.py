@@ -635,6 +635,96 @@ class MultiMatcher:
         return s
 
 
+class StreamMatcher:
+    """Pipelined matching of a stream of frames (pinned host uint8 tensors of
+    N x M) with one template at one or more std thresholds.
+
+    Two slots, each a MultiMatcher with its own source buffer, replayed from a
+    CUDA graph.  submit(frame) copies the frame host -> device on a copy
+    stream while the previous frame is still being matched, queues the frame's
+    graph on the compute stream, and then reads back the match lists of the
+    previous frame on a third stream (waiting for that frame only), so the
+    copies and the host's work overlap the GPU's.  Returns the previous
+    frame's lists (None on the first call); flush() returns the last one.
+    A list is one (u, v, rho) triple of numpy arrays per threshold."""
+
+    def __init__(self, t: np.ndarray, sigmas, M: int, N: int, precision: float = 0.85,
+                 tau_exact: Optional[float] = None, k_max: int = 0, cand_cap: int = 1 << 20, out_cap: int = 1 << 16,
+                 keep_rho: bool = False, device="cuda"):
+        torch = _torch()
+        self.M, self.N = M, N
+        self.slots = [MultiMatcher(t, sigmas, M, N, precision, tau_exact, k_max, cand_cap, out_cap, keep_rho, device)
+                      for _ in range(2)]
+        self.src = [torch.zeros((N, M), dtype=torch.uint8, device=device) for _ in range(2)]
+        self.graphs = [sl.capture(f) for sl, f in zip(self.slots, self.src)]
+        self.compute = torch.cuda.Stream(device)
+        self.copy = torch.cuda.Stream(device)
+        self.readback = torch.cuda.Stream(device)
+        self.copied = [torch.cuda.Event() for _ in range(2)]
+        self.done = [torch.cuda.Event() for _ in range(2)]
+        self.used = [False, False]
+        self.counts = [torch.empty(len(sigmas), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        self.records = [[torch.empty((rb.cap, 3), dtype=torch.int32, pin_memory=True) for rb in sl.rbs]
+                        for sl in self.slots]
+        self.frames = 0
+        self.d2h_bytes = 0
+        torch.cuda.synchronize()
+
+    def submit(self, frame):
+        """Queue one frame; returns the previous frame's match lists."""
+        torch = _torch()
+        if frame.dtype != torch.uint8 or tuple(frame.shape) != (self.N, self.M):
+            raise ValueError("frame must be a uint8 tensor of shape (N, M)")
+        slot = self.frames & 1
+        if self.used[slot]:  # the copy reuses the source buffer of the frame two back
+            self.copy.wait_event(self.done[slot])
+        with torch.cuda.stream(self.copy):
+            self.src[slot].copy_(frame, non_blocking=True)
+            self.copied[slot].record(self.copy)
+        self.compute.wait_event(self.copied[slot])
+        with torch.cuda.stream(self.compute):
+            self.graphs[slot].replay()
+            self.done[slot].record(self.compute)
+        self.used[slot] = True
+        prev = self._collect(slot ^ 1) if self.frames > 0 else None
+        self.frames += 1
+        return prev
+
+    def flush(self):
+        """The match lists of the last submitted frame (None if there is none)."""
+        if self.frames == 0:
+            return None
+        return self._collect((self.frames - 1) & 1)
+
+    def _collect(self, slot):
+        torch = _torch()
+        rs = self.readback
+        rs.wait_event(self.done[slot])
+        rbs = self.slots[slot].rbs
+        with torch.cuda.stream(rs):
+            for q, rb in enumerate(rbs):
+                self.counts[slot][q:q + 1].copy_(rb.nout, non_blocking=True)
+        rs.synchronize()
+        ns = [min(int(c), rb.cap) for c, rb in zip(self.counts[slot].tolist(), rbs)]
+        with torch.cuda.stream(rs):
+            for n, rb, h in zip(ns, rbs, self.records[slot]):
+                if n:
+                    h[:n].copy_(rb.out[:n], non_blocking=True)
+        if any(ns):
+            rs.synchronize()
+        self.d2h_bytes += 4 * len(rbs) + 12 * sum(ns)
+        out = []
+        for n, h in zip(ns, self.records[slot]):
+            raw = h[:n].numpy()
+            out.append((raw[:, 0].astype(np.int64), raw[:, 1].astype(np.int64), raw[:, 2].copy().view(np.float32)))
+        return out
+
+    def status(self) -> int:
+        torch = _torch()
+        torch.cuda.synchronize()
+        return self.slots[0].status() | self.slots[1].status()
+
+
 # ---------------------------------------------------------------------------
 # Batched matching: many templates x several sources in one persistent launch
 # ---------------------------------------------------------------------------

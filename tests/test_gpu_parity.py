@@ -263,6 +263,35 @@ def test_multi_matcher_graph_and_separate_matchers(sncc):
             np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("sigmas", [(3.0, 6.0, 12.0), (5.0,)])
+def test_stream_matcher_equals_one_frame_at_a_time(sncc, sigmas):
+    """Five different frames through the pipelined StreamMatcher give, frame
+    by frame, the match lists of a MultiMatcher run on each frame alone."""
+    frames = [synth.case_hd(M=400, N=300, W=48, H=48, seed=60 + i) for i in range(5)]
+    t = frames[0].t
+    sm = sncc.StreamMatcher(t, sigmas, 400, 300, precision=0.6)
+    got = []
+    for c in frames:
+        r = sm.submit(torch.as_tensor(c.f).pin_memory())
+        if r is not None:
+            got.append(r)
+    got.append(sm.flush())
+    assert sm.status() == 0
+    ref = sncc.MultiMatcher(t, sigmas, 400, 300, precision=0.6)
+    assert sm.slots[0].fused == (len(sigmas) > 1)
+    nonempty = 0
+    for c, lists in zip(frames, got):
+        fd = dev(c.f)
+        ref.run(fd)
+        torch.cuda.synchronize()
+        for q, rb in enumerate(ref.rbs):
+            want = sncc.matches_to_numpy(rb)
+            nonempty += len(want[0]) > 0
+            for x, y in zip(lists[q], want):
+                np.testing.assert_array_equal(x, y)
+    assert nonempty > 0
+
+
 def test_match_multi_rejects_what_it_cannot_fuse(sncc):
     """Templates of different sizes are an argument error; a multi-block
     template, or one summed in place (at most 64 corners), is not fused
