@@ -475,20 +475,31 @@ def run_gpu(args, world, rank, local, pg):
         e.record(stream)
         return e
 
+    sides = [torch.cuda.Stream(dev) for _ in segs[1:]]
+
     def step(record_match=False):
         sncc.integral(fd, tables, workspace=ws)
         if fused:
             a = ev() if record_match else None
             sncc.match_multi(segs, plans, tables, taus, mbs)
             prev = ev() if record_match else None
-            if record_match:
+            if record_match:  # refines one after another, each timed
                 match_ev.append((-1, a, prev))
-            for i, s in enumerate(segs):
-                sncc.refine(fd, td, s, mbs[i], PRECISION, rbs[i])
-                if record_match:
+                for i, s in enumerate(segs):
+                    sncc.refine(fd, td, s, mbs[i], PRECISION, rbs[i])
                     c = ev()
                     refine_ev.append((i, prev, c))
                     prev = c
+                return
+            # the refines are independent: parallel branches of the graph
+            main = torch.cuda.current_stream()
+            for i, s in enumerate(segs):
+                st = main if i == 0 else sides[i - 1]
+                if i:
+                    st.wait_stream(main)
+                sncc.refine(fd, td, s, mbs[i], PRECISION, rbs[i], stream=st)
+            for st in sides:
+                main.wait_stream(st)
             return
         for i, s in enumerate(segs):
             a = ev() if record_match else None
@@ -701,7 +712,8 @@ def run_gpu(args, world, rank, local, pg):
         "dtype": "int64", "data": "synthetic",
         "config": dict(workload_config(args.workload, case, SIGMAS, PRECISION, U, V), seed=case_seed,
                        launch=("one CUDA graph per step: sum tables, one segment-sum launch over every "
-                               "(tile, threshold) pair, then per threshold exact refine and sort") if fused else
+                               "(tile, threshold) pair, then per threshold exact refine and sort (parallel "
+                               "branches)") if fused else
                               "one CUDA graph per step: sum tables, then per threshold segment sum, exact "
                               "refine and sort"),
         "exact_ncc": {"value": U * V / (exact_ms * 1e-3) / 1e9, "unit": UNIT, "ms": exact_ms,

@@ -604,6 +604,9 @@ class MultiMatcher:
         self.mbs = [alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device) for _ in self.segs]
         self.rbs = [alloc_refine(out_cap, device) for _ in self.segs]
         self.fused = None if len(self.segs) > 1 and MULTI_MAX >= len(self.segs) else False
+        # the refines of the approximations are independent: all but the
+        # first run on side streams (parallel branches of a captured graph)
+        self.side = [torch.cuda.Stream(device) for _ in self.segs[1:]]
 
     def run(self, f, stream=None):
         """Launch the whole path on a (N, M) uint8 CUDA tensor (asynchronous).
@@ -621,8 +624,17 @@ class MultiMatcher:
         if not self.fused:
             for sg, pl, tau, mb in zip(self.segs, self.plans, self.taus, self.mbs):
                 match(sg, pl, self.tables, tau, mb, stream=stream)
-        for sg, mb, rb in zip(self.segs, self.mbs, self.rbs):
-            refine(f, self.t_dev, sg, mb, self.tau_e, rb, stream=stream)
+        torch = _torch()
+        main = torch.cuda.current_stream() if stream is None else stream
+        for q, (sg, mb, rb) in enumerate(zip(self.segs, self.mbs, self.rbs)):
+            if q == 0:
+                refine(f, self.t_dev, sg, mb, self.tau_e, rb, stream=main)
+                continue
+            side = self.side[q - 1]
+            side.wait_stream(main)
+            refine(f, self.t_dev, sg, mb, self.tau_e, rb, stream=side)
+        for side in self.side:
+            main.wait_stream(side)
 
     def capture(self, f):
         """Record run(f) in a CUDA graph (after one eager warm-up run)."""
