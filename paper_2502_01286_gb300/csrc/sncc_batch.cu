@@ -45,7 +45,7 @@ struct TmplDesc {  // 80 bytes, one per template
     float inv_n, Ek, scale, tau;
     float tau_exact;
     int pix_offset;
-    int pad0, pad1;
+    double rn;  // 1 / n in FP64
 };
 static_assert(sizeof(TmplDesc) == 80, "template descriptor layout");
 
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(WARPS * 32) batch_match_kernel(const __grid_co
         for (int r = 0; r < R; ++r) {
             const int v = v0 + warp * R + r;
             const bool valid = (u < pd.z) && (v < pd.w);
-            const float rho = valid ? normalise<S64>(acc[r], s, s2, a.pitch, u, v, td.W, td.H, td.n, td.inv_n, td.Ek,
+            const float rho = valid ? normalise<S64>(acc[r], s, s2, a.pitch, u, v, td.W, td.H, td.n, td.rn, td.inv_n, td.Ek,
                                                      td.scale, td.Q0)
                                     : 0.0f;
             const bool pred = valid && (rho >= td.tau);
@@ -343,7 +343,8 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
             d.Q0 = p.Q0;
             d.T = sg->T;
             d.T2 = sg->T2;
-            d.inv_n = (float)(1.0 / (double)d.n);
+            d.rn = 1.0 / (double)d.n;
+            d.inv_n = (float)d.rn;
             d.Ek = (float)sg->Ek;
             d.scale = (float)std::ldexp(1.0, -p.F);
             d.tau = tau_coarse[t];

@@ -40,7 +40,7 @@
 //    tiles leaves the last wave partly empty; over the whole set the lighter
 //    slices fill it.
 //  * Epilogue: window sums from the global tables, exact integer variance
-//    n sum f^2 - (sum f)^2 divided by n in FP64, rho in FP32; the coarse pass
+//    n sum f^2 - (sum f)^2 times 1/n in FP64, rho in FP32; the coarse pass
 //    appends candidates (v*U+u) with warp-aggregated atomics, the fine mode
 //    appends (u, v, rho) records of the offsets whose candidate bit is set.
 #include <cuda.h>
@@ -88,6 +88,7 @@ struct MatchArgs {
     const int64_t* s2;
     int pitch;
     long long n;
+    double rn;  // 1 / n in FP64
     float inv_n;
     float Ek;
     float scale;  // 2^-F
@@ -153,7 +154,7 @@ __device__ __forceinline__ void match_epilogue(const MatchArgs& a, const long lo
                 valid = (a.cand_bits[idx >> 5] >> (idx & 31)) & 1u;
             }
         }
-        const float rho = valid ? normalise<S64>(acc[r], a.s, a.s2, a.pitch, u, v, a.W, a.H, a.n, a.inv_n, Ek,
+        const float rho = valid ? normalise<S64>(acc[r], a.s, a.s2, a.pitch, u, v, a.W, a.H, a.n, a.rn, a.inv_n, Ek,
                                                  scale, Q0)
                                 : 0.0f;
         if (!FINE && rho_map != nullptr && valid) rho_map[(size_t)v * a.rho_pitch + u] = rho;
@@ -438,7 +439,8 @@ int prepare_match(const sncc_segments* seg, const void* d_plan, const void* d_s,
     a.s2 = d_s2;
     a.pitch = sat_pitch;
     a.n = (long long)W * H;
-    a.inv_n = (float)(1.0 / ((double)W * H));
+    a.rn = 1.0 / ((double)W * H);
+    a.inv_n = (float)a.rn;
     a.Ek = (float)seg->Ek;
     a.scale = (float)std::ldexp(1.0, -p->F);
     a.Q0 = p->Q0;

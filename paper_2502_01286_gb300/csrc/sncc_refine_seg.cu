@@ -37,6 +37,7 @@ struct RefineSegArgs {
     const int64_t* s2;
     int pitch, U, V, W, H;
     long long n;
+    double rn;  // 1 / n in FP64
     float inv_n, Ek, scale;
     long long Q0;
     const int32_t* cand;
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) refine_seg_kernel(const Ref
             const long long var = a.n * sf2 - sf * sf;
             float rho = 0.0f;
             if (var > 0) {
-                const double ef = (double)var / (double)a.n;
+                const double ef = (double)var * a.rn;
                 const float den = sqrtf((float)ef * a.Ek);
                 const float num = ((float)(long long)acc - (float)(a.Q0 * sf) * a.inv_n) * a.scale;
                 rho = num / den;
@@ -143,7 +144,8 @@ extern "C" int sncc_refine_segmented(const sncc_segments* seg, const void* d_pla
     a.W = W;
     a.H = H;
     a.n = (long long)W * H;
-    a.inv_n = (float)(1.0 / ((double)W * H));
+    a.rn = 1.0 / ((double)W * H);
+    a.inv_n = (float)a.rn;
     a.Ek = (float)seg->Ek;
     a.scale = (float)std::ldexp(1.0, -p->F);
     a.Q0 = p->Q0;

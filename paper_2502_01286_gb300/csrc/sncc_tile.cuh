@@ -203,19 +203,21 @@ __device__ __forceinline__ void run_sum(long long (&acc)[R], const int* wbase, c
 }
 
 // rho at offset (u, v) from the exact numerator acc = 2^F num + Q0 * sum f / n
-// (Eq. 13, 15, 16 exact in integers; E_f divided in FP64; Eq. 17-18 in FP32).
+// (Eq. 13, 15, 16 exact in integers; E_f = var / n in FP64 as var times the
+// FP64 reciprocal of n, within one FP64 ulp of the quotient; Eq. 17-18 in
+// FP32).
 // A uniform window gives 0.
 template <bool S64>
 __device__ __forceinline__ float normalise(long long acc, const void* s, const int64_t* s2, int pitch, int u, int v,
-                                           int W, int H, long long n, float inv_n, float Ek, float scale,
-                                           long long Q0) {
+                                           int W, int H, long long n, double rn, float inv_n, float Ek,
+                                           float scale, long long Q0) {
     const long long sf = table_entry<S64>(s, pitch, u + W, v + H) - table_entry<S64>(s, pitch, u, v + H) -
                          table_entry<S64>(s, pitch, u + W, v) + table_entry<S64>(s, pitch, u, v);
     const long long sf2 = s2[(size_t)(v + H) * pitch + u + W] - s2[(size_t)(v + H) * pitch + u] -
                           s2[(size_t)v * pitch + u + W] + s2[(size_t)v * pitch + u];
     const long long var = n * sf2 - sf * sf;
     if (var <= 0) return 0.0f;
-    const double ef = (double)var / (double)n;
+    const double ef = (double)var * rn;  // rn = 1/n rounded once in FP64
     const float den = sqrtf((float)ef * Ek);
     const float num = ((float)acc - (float)(Q0 * sf) * inv_n) * scale;
     return num / den;
