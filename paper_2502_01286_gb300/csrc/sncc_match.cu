@@ -104,17 +104,17 @@ struct MatchArgs {
     // candidate bit of every offset and the (u, v, rho) output records
     const int32_t* tile_list;
     const int32_t* tile_count;
+    int tiles_u;
+    const uint32_t* cand_bits;
+    sncc_match_t* out;
+    int out_cap;
+    int32_t* nout;
     // direct mode: the whole template's corners {X, Y, G, 0}, read in place
     const int4* direct;
     int ndirect;
     // multi-plan mode: several approximations of one template size, one block
     int nplans;
     MultiPlan mp[kMaxMultiPlans];
-    int tiles_u;
-    const uint32_t* cand_bits;
-    sncc_match_t* out;
-    int out_cap;
-    int32_t* nout;
 };
 
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
