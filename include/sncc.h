@@ -52,7 +52,7 @@ typedef struct CUstream_st* sncc_stream_t;
 #define SNCC_ERR_CUDA (-5)      /* a CUDA runtime call or kernel launch failed */
 #define SNCC_ERR_WORKSPACE (-6) /* workspace missing, misaligned or too small */
 #define SNCC_ERR_NOMEM (-7)     /* host allocation failed */
-#define SNCC_ERR_UNSUPPORTED (-8) /* size outside what this build supports */
+#define SNCC_ERR_UNSUPPORTED (-8) /* size or shape outside what the library supports */
 
 /* Device status bits (OR-ed into the caller's int32 status word). */
 #define SNCC_STATUS_CAND_OVERFLOW 1  /* more candidates than cand_cap; count is still exact */
