@@ -573,6 +573,15 @@ extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* co
         if ((cand_cap > 0 && !d_cand[q]) || !d_count[q] || !d_status[q]) return SNCC_ERR_ARG;
         if (!(segs[q]->Ek > 0.0) || plan_of(segs[q])->image.empty()) return SNCC_ERR_UNIFORM;
     }
+    // and one staged block of the same layout each (templates up to 64 x 64
+    // that are not summed directly); decided on the host before any CUDA call
+    const Layout& L0 = layout_for(*plan_of(segs[0]));
+    for (int q = 0; q < n; ++q) {
+        const Plan* p = plan_of(segs[q]);
+        const Layout& Lq = layout_for(*p);
+        if (Lq.nblk != 1 || Lq.nbx * Lq.nby != 1 || Lq.WP != L0.WP || Lq.BH != L0.BH || p->direct_count > 0)
+            return SNCC_ERR_UNSUPPORTED;
+    }
     MatchArgs a;
     CUtensorMap map;
     int R = 0;
@@ -581,8 +590,6 @@ extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* co
     if (rc != SNCC_OK) return rc;
     if (d_rho && rho_pitch < a.U) return SNCC_ERR_ARG;
     const bool s64 = (s_bits == 64);
-    // and one staged block of the same layout each (templates up to 64 x 64
-    // that are not summed directly)
     // grid slice z = 0 is dispatched first: the approximations with the most
     // corners go first, so that the lighter ones fill the last wave
     int order[kMaxMultiPlans];
@@ -594,8 +601,6 @@ extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* co
         const int q = order[z];
         const Plan* p = plan_of(segs[q]);
         const Layout& Lq = layout_for(*p);
-        if (Lq.nblk != 1 || Lq.nbx * Lq.nby != 1 || Lq.WP != L->WP || Lq.BH != L->BH || p->direct_count > 0)
-            return SNCC_ERR_UNSUPPORTED;
         MultiPlan& mp = a.mp[z];
         mp.runblk = reinterpret_cast<const int4*>(static_cast<const char*>(d_plans[q]) + Lq.runblk_offset);
         mp.runs = reinterpret_cast<const int4*>(static_cast<const char*>(d_plans[q]) + Lq.runs_offset);

@@ -184,6 +184,30 @@ def test_host_argument_errors(sncc):
                                 ptrs, 16, ptrs, nulls, None) == sncc.ERR_ARG
 
 
+def test_match_multi_fusability_decided_on_host(sncc):
+    """sncc_match_multi declines (SNCC_ERR_UNSUPPORTED) a template of several
+    blocks or one summed in place before any CUDA call, and rejects templates
+    of different sizes as an argument error."""
+    lib = sncc.lib()
+    big = sncc.build_segments(synth.case_plain(M=300, N=260, W=130, H=100, seed=3).t, 6.0)
+    small = sncc.build_segments(synth.case_hd(M=300, N=260, W=48, H=40, seed=4).t, 4.0)
+    boxes = np.full((40, 48), 50, np.uint8)
+    boxes[5:20, 8:30] = 180
+    sparse = sncc.build_segments(boxes, 1.0)
+    assert small.plan_info()["template_corners"] > 64 and sparse.plan_info()["template_corners"] <= 64
+    ptrs = (C.c_void_p * 4)(*[256] * 4)
+    taus = (C.c_float * 4)(*[0.5] * 4)
+
+    def call(segs):
+        arr = (C.POINTER(sncc._Segments) * len(segs))(*[C.pointer(sg._s) for sg in segs])
+        return lib.sncc_match_multi(arr, ptrs, len(segs), C.c_void_p(256), 32, C.c_void_p(256), 320, 300, 260,
+                                    taus, None, 0, ptrs, 16, ptrs, ptrs, None)
+
+    assert call([big]) == sncc.ERR_UNSUPPORTED
+    assert call([small, sparse]) == sncc.ERR_UNSUPPORTED
+    assert call([small, big]) == sncc.ERR_ARG
+
+
 def test_batch_host_work_lists(sncc):
     """sncc_batch_create on the host: the work list has one item per tile of
     every (source, template) pair, and the offset / corner totals add up."""
