@@ -10,7 +10,8 @@
 //              Gt(x) = sum_o a(o) f(o + x);
 //   dL/df(p) = sum_{o : p in window(o)} a(o) c(p-o) - b(o) t0(p-o) + h(o) (fbar(o) - f(p)).
 // Templates up to 64 x 64 (every window and the template fit in shared
-// memory).  Sums run in FP32 along a template row and in FP64 across rows.
+// memory).  Sums run in FP32 along a template row (the forward pass: down a
+// template column) and in FP64 across rows (columns).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -23,7 +24,11 @@ namespace sncc {
 namespace {
 
 constexpr int kDiffMax = 64;      // largest template edge
-constexpr int kTX = 32, kTY = 8;  // offsets / pixels per CTA tile
+constexpr int kFwXB = 4;          // forward: offset rows per thread (register window)
+constexpr int kFwG = 4;           // forward: template-column groups per CTA
+constexpr int kFwGT = 256 / kFwG;  // forward: threads per group (2 warps)
+constexpr int kFwTX = 32;         // forward: offset columns per CTA (lane = column)
+constexpr int kFwTY = (kFwGT / 32) * kFwXB;  // forward: offset rows per CTA (8)
 constexpr int kGtChunks = 192;    // offset-row chunks of the Gt correlation
 constexpr int kGtYB = 16;         // template rows per Gt CTA
 constexpr int kGtXB = 8;          // template columns per Gt thread (register window)
@@ -72,6 +77,20 @@ __device__ __forceinline__ double block_sum_double(double v, double* sm) {
     return r;  // valid in thread 0
 }
 
+// Compensated (Kahan) FP32 sum: value() = s - c carries about twice the
+// FP32 precision, so column sums add up across columns without FP64 adds
+// (GB300's FP64 pipe runs at a small fraction of its FP32 rate).
+struct KahanF {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // scal[0] = kbar, scal[1] = E_k, scal[2] = E_t, scal[3] = sum a fbar, scal[4] = sum g rho_k.
 // Renders c(x) = k_i - kbar and t0 = t - tbar.  One CTA.
 __global__ void __launch_bounds__(256) diff_prep_kernel(const float* __restrict__ t, int W, int H,
@@ -116,21 +135,49 @@ __global__ void __launch_bounds__(256) diff_prep_kernel(const float* __restrict_
     }
 }
 
-// One thread per offset of a 32 x 8 tile.
+// Forward pass over a 32 x 8 tile of offsets.  The CTA's 256 threads are
+// kFwG groups of 2 warps; group g takes the template columns
+// [g W / kFwG, (g+1) W / kFwG), and thread (warp w of the group, lane l) the
+// offsets u0 + l, rows v0 + 4w .. +3.  Along a template column the thread
+// keeps the 4 source values of its 4 offsets in a register window, so each
+// template row costs one new source load and two broadcast loads (c, t0) for
+// 4 x 4 floating-point operations.  Sums run in FP32 down a template column
+// and in compensated FP32 across columns (a plain FP64 add per column and
+// offset made the kernel FP64-bound); the groups' partial sums meet in shared
+// memory, in FP64 and a fixed order.
+//   pass 1: window means (sliding column sums);
+//   pass 2: with d = f - fbar: sum d^2, sum c d, sum t0 d (E_f, numerator,
+//           exact numerator).
+__host__ __device__ constexpr int fw_region_w(int W) { return kFwTX + W - 1; }
+__host__ __device__ constexpr size_t fw_main_bytes(int W, int H) {
+    // max(staged source, c, t0 | pass-2 partials of groups 1..), rounded to 16 bytes
+    return (((size_t)fw_region_w(W) * (kFwTY + H - 1) + 2 * (size_t)W * H) * 4 >
+                    (size_t)(kFwG - 1) * kFwGT * kFwXB * 3 * 8
+                ? ((size_t)fw_region_w(W) * (kFwTY + H - 1) + 2 * (size_t)W * H) * 4
+                : (size_t)(kFwG - 1) * kFwGT * kFwXB * 3 * 8) +
+           15 & ~(size_t)15;
+}
+__host__ __device__ constexpr size_t fw_smem_bytes(int W, int H) {
+    return fw_main_bytes(W, H) + (size_t)kFwG * kFwGT * kFwXB * 8;  // + pass-1 partials
+}
+
 __global__ void __launch_bounds__(256) diff_forward_kernel(const float* __restrict__ f, int M, int N, int stride,
                                                            int W, int H, const float* __restrict__ c,
                                                            const float* __restrict__ t0, const double* scal,
                                                            float* __restrict__ rho_k, float* __restrict__ rho_t,
                                                            float* __restrict__ ef_out, float* __restrict__ fbar_out,
                                                            double* loss) {
-    extern __shared__ float sm[];
-    const int RW = kTX + W - 1, RH = kTY + H - 1;
-    float* fs = sm;                  // RH x RW source region
-    float* cs = fs + RW * RH;        // W x H
-    float* ts = cs + W * H;          // W x H
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int RW = fw_region_w(W), RH = kFwTY + H - 1;
+    const size_t main_bytes = fw_main_bytes(W, H);
+    float* fs = reinterpret_cast<float*>(smraw);        // RH x RW source region
+    float* cs = fs + RW * RH;                           // W x H
+    float* ts = cs + W * H;                             // W x H
+    double* red2 = reinterpret_cast<double*>(smraw);    // after pass 2: [g-1][t][j][3]
+    double* red1 = reinterpret_cast<double*>(smraw + main_bytes);  // [g][t][j]
     __shared__ double red[8];
     const int U = M - W + 1, V = N - H + 1;
-    const int u0 = blockIdx.x * kTX, v0 = blockIdx.y * kTY;
+    const int u0 = blockIdx.x * kFwTX, v0 = blockIdx.y * kFwTY;
     for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
         const int Y = i / RW, X = i - Y * RW;
         const int gx = u0 + X, gy = v0 + Y;
@@ -141,46 +188,115 @@ __global__ void __launch_bounds__(256) diff_forward_kernel(const float* __restri
         ts[i] = t0[i];
     }
     __syncthreads();
-    const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
-    const int u = u0 + lx, v = v0 + ly;
-    double contrib = 0.0;
-    if (u < U && v < V) {
-        const double n = (double)W * H;
-        double sf = 0.0;
-        for (int y = 0; y < H; ++y) {
-            const float* row = fs + (ly + y) * RW + lx;
-            float r = 0.0f;
-            for (int x = 0; x < W; ++x) r += row[x];
-            sf += r;
+    const int g = threadIdx.x / kFwGT, t = threadIdx.x - g * kFwGT;
+    const int lane = t & 31, wy = t >> 5;
+    const int x_lo = g * W / kFwG, x_hi = (g + 1) * W / kFwG;
+    const float* base = fs + (wy * kFwXB) * RW + lane;  // region row of offset row 0, column of the lane
+    const double n = (double)W * H;
+
+    // ---- pass 1: window sums, sum over rows y of f(row y + j) per template column ----
+    KahanF sp[kFwXB];
+    for (int x = x_lo; x < x_hi; ++x) {
+        const float* col = base + x;
+        float s0 = 0.0f;
+        for (int y = 0; y < H; ++y) s0 += col[y * RW];
+        float sj = s0;
+        sp[0].add(s0);
+#pragma unroll
+        for (int j = 1; j < kFwXB; ++j) {  // slide the window one row
+            sj += col[(H - 1 + j) * RW] - col[(j - 1) * RW];
+            sp[j].add(sj);
         }
-        const double fbar = sf / n;
-        const float fb = (float)fbar;
-        double e = 0.0, nk = 0.0, nt = 0.0;
-        for (int y = 0; y < H; ++y) {
-            const float* row = fs + (ly + y) * RW + lx;
-            const float* crow = cs + y * W;
-            const float* trow = ts + y * W;
-            float re = 0.0f, rk = 0.0f, rt = 0.0f;
-            for (int x = 0; x < W; ++x) {
-                const float d = row[x] - fb;
-                re += d * d;
-                rk += crow[x] * d;
-                rt += trow[x] * d;
-            }
-            e += re;
-            nk += rk;
-            nt += rt;
-        }
-        const double rk_ = nk / sqrt(e * scal[1]);
-        const double rt_ = nt / sqrt(e * scal[2]);
-        rho_k[(size_t)v * U + u] = (float)rk_;
-        rho_t[(size_t)v * U + u] = (float)rt_;
-        ef_out[(size_t)v * U + u] = (float)e;
-        fbar_out[(size_t)v * U + u] = fb;
-        contrib = (rk_ - rt_) * (rk_ - rt_);
     }
-    const double s = block_sum_double(contrib, red);
-    if (threadIdx.x == 0) atomicAdd(loss, s);
+#pragma unroll
+    for (int j = 0; j < kFwXB; ++j) red1[(g * kFwGT + t) * kFwXB + j] = sp[j].value();
+    __syncthreads();
+    float fb[kFwXB];
+#pragma unroll
+    for (int j = 0; j < kFwXB; ++j) {
+        double sf = 0.0;
+        for (int q = 0; q < kFwG; ++q) sf += red1[(q * kFwGT + t) * kFwXB + j];
+        fb[j] = (float)(sf / n);
+    }
+
+    // ---- pass 2: energy, approximate and exact numerators ----
+    KahanF ek[kFwXB], nkk[kFwXB], ntk[kFwXB];
+    for (int x = x_lo; x < x_hi; ++x) {
+        const float* col = base + x;
+        float re[kFwXB], rk[kFwXB], rt[kFwXB], win[kFwXB];
+#pragma unroll
+        for (int j = 0; j < kFwXB; ++j) {
+            re[j] = rk[j] = rt[j] = 0.0f;
+            win[j] = j < kFwXB - 1 ? col[j * RW] : 0.0f;  // rows 0 .. 2 in slots 0 .. 2
+        }
+        for (int y0 = 0; y0 < H; y0 += kFwXB) {
+#pragma unroll
+            for (int k = 0; k < kFwXB; ++k) {
+                const int y = y0 + k;
+                if (y < H) {
+                    win[(k + kFwXB - 1) % kFwXB] = col[(y + kFwXB - 1) * RW];  // row y + 3
+                    const float cx = cs[y * W + x], tx = ts[y * W + x];
+#pragma unroll
+                    for (int j = 0; j < kFwXB; ++j) {
+                        const float d = win[(k + j) % kFwXB] - fb[j];  // f(row y + j)
+                        re[j] += d * d;
+                        rk[j] += cx * d;
+                        rt[j] += tx * d;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kFwXB; ++j) {
+            ek[j].add(re[j]);
+            nkk[j].add(rk[j]);
+            ntk[j].add(rt[j]);
+        }
+    }
+    double e[kFwXB], nk[kFwXB], nt[kFwXB];
+#pragma unroll
+    for (int j = 0; j < kFwXB; ++j) {
+        e[j] = ek[j].value();
+        nk[j] = nkk[j].value();
+        nt[j] = ntk[j].value();
+    }
+    __syncthreads();  // the staged region is reused for the groups' partials
+    if (g > 0) {
+#pragma unroll
+        for (int j = 0; j < kFwXB; ++j) {
+            double* o = red2 + (((g - 1) * kFwGT + t) * kFwXB + j) * 3;
+            o[0] = e[j];
+            o[1] = nk[j];
+            o[2] = nt[j];
+        }
+    }
+    __syncthreads();
+    double contrib = 0.0;
+    if (g == 0) {
+        const int u = u0 + lane;
+#pragma unroll
+        for (int j = 0; j < kFwXB; ++j) {
+            for (int q = 1; q < kFwG; ++q) {
+                const double* o = red2 + (((q - 1) * kFwGT + t) * kFwXB + j) * 3;
+                e[j] += o[0];
+                nk[j] += o[1];
+                nt[j] += o[2];
+            }
+            const int v = v0 + wy * kFwXB + j;
+            if (u < U && v < V) {
+                const double rk_ = nk[j] / sqrt(e[j] * scal[1]);
+                const double rt_ = nt[j] / sqrt(e[j] * scal[2]);
+                const size_t oi = (size_t)v * U + u;
+                rho_k[oi] = (float)rk_;
+                rho_t[oi] = (float)rt_;
+                ef_out[oi] = (float)e[j];
+                fbar_out[oi] = fb[j];
+                contrib += (rk_ - rt_) * (rk_ - rt_);
+            }
+        }
+    }
+    const double sum = block_sum_double(contrib, red);
+    if (threadIdx.x == 0) atomicAdd(loss, sum);
 }
 
 // Per-offset coefficients of the backward pass, and the sums A1, A2.
@@ -292,9 +408,7 @@ __global__ void __launch_bounds__(kGfThreads, 2) diff_grad_f_kernel(const float*
     const int grp = threadIdx.x / kGfGroup, t = threadIdx.x - grp * kGfGroup;
     const int gx = t % (kGfTX / kGfXB), ry = t / (kGfTX / kGfXB);
     const int py = py0 + ry, pxb = px0 + gx * kGfXB;
-    double acc[kGfXB];
-#pragma unroll
-    for (int j = 0; j < kGfXB; ++j) acc[j] = 0.0;
+    KahanF acck[kGfXB];
     if (py < N && pxb < M) {
         for (int y = grp; y < H; y += kGfYG) {
             // offset row py - y  ->  region row ry + H - 1 - y; pixel pxb + j, x = W-1-x'
@@ -323,7 +437,7 @@ __global__ void __launch_bounds__(kGfThreads, 2) diff_grad_f_kernel(const float*
                 }
             }
 #pragma unroll
-            for (int j = 0; j < kGfXB; ++j) acc[j] += r[j];
+            for (int j = 0; j < kGfXB; ++j) acck[j].add(r[j]);
         }
     }
     // groups 1.. hand their partial sums to group 0 (the staging area is free now)
@@ -331,24 +445,23 @@ __global__ void __launch_bounds__(kGfThreads, 2) diff_grad_f_kernel(const float*
     double* part = reinterpret_cast<double*>(sm);
     if (grp > 0) {
 #pragma unroll
-        for (int j = 0; j < kGfXB; ++j) part[((size_t)(grp - 1) * kGfXB + j) * kGfGroup + t] = acc[j];
+        for (int j = 0; j < kGfXB; ++j) part[((size_t)(grp - 1) * kGfXB + j) * kGfGroup + t] = acck[j].value();
     }
     __syncthreads();
     if (grp > 0 || py >= N || pxb >= M) return;
-    for (int g = 1; g < kGfYG; ++g) {
-#pragma unroll
-        for (int j = 0; j < kGfXB; ++j) acc[j] += part[((size_t)(g - 1) * kGfXB + j) * kGfGroup + t];
-    }
 #pragma unroll
     for (int j = 0; j < kGfXB; ++j) {
         const int px = pxb + j;
         if (px >= M) break;
-        double hs = 0.0, hfs = 0.0;
+        double acc = acck[j].value();
+        for (int g = 1; g < kGfYG; ++g) acc += part[((size_t)(g - 1) * kGfXB + j) * kGfGroup + t];
+        KahanF hs, hfs;
         for (int y = max(0, py - V + 1); y < min(H, py + 1); ++y) {
-            hs += rh[(size_t)(py - y) * M + px];
-            hfs += rhf[(size_t)(py - y) * M + px];
+            hs.add(rh[(size_t)(py - y) * M + px]);
+            hfs.add(rhf[(size_t)(py - y) * M + px]);
         }
-        grad[(size_t)py * gstride + px] = (float)(acc[j] + hfs - (double)f[(size_t)py * stride + px] * hs);
+        grad[(size_t)py * gstride + px] =
+            (float)(acc + hfs.value() - (double)f[(size_t)py * stride + px] * hs.value());
     }
 }
 
@@ -372,9 +485,7 @@ __global__ void __launch_bounds__(128) diff_gt_kernel(const float* __restrict__ 
     const int y = y0 + yy, x0 = xg * kGtXB;
     const bool active = y < H;
     const int vb = (int)((long long)V * chunk / kGtChunks), ve = (int)((long long)V * (chunk + 1) / kGtChunks);
-    double accd[kGtXB];
-#pragma unroll
-    for (int j = 0; j < kGtXB; ++j) accd[j] = 0.0;
+    KahanF accd[kGtXB];
     for (int vs = vb; vs < ve; vs += kGtVS) {
         for (int us = 0; us < U; us += kGtUS) {
             __syncthreads();  // the previous block's reads are done
@@ -409,7 +520,7 @@ __global__ void __launch_bounds__(128) diff_gt_kernel(const float* __restrict__ 
                         }
                     }
 #pragma unroll
-                    for (int j = 0; j < kGtXB; ++j) accd[j] += acc[j];
+                    for (int j = 0; j < kGtXB; ++j) accd[j].add(acc[j]);
                 }
             }
         }
@@ -417,7 +528,7 @@ __global__ void __launch_bounds__(128) diff_gt_kernel(const float* __restrict__ 
     if (active) {
 #pragma unroll
         for (int j = 0; j < kGtXB; ++j)
-            if (x0 + j < W) gtp[((size_t)chunk * H + y) * W + x0 + j] = accd[j];
+            if (x0 + j < W) gtp[((size_t)chunk * H + y) * W + x0 + j] = accd[j].value();
     }
 }
 
@@ -490,9 +601,9 @@ extern "C" int sncc_diff_forward(const float* d_f, int M, int N, int f_stride, c
     if (cudaMemsetAsync(d_loss, 0, sizeof(double), st) != cudaSuccess) return SNCC_ERR_CUDA;
     diff_prep_kernel<<<1, 256, 0, st>>>(d_t, W, H, reinterpret_cast<const int4*>(d_rects), d_k, K, scal, c, t0);
     const int U = M - W + 1, V = N - H + 1;
-    const size_t sm = ((size_t)(kTX + W - 1) * (kTY + H - 1) + 2 * (size_t)W * H) * 4;
+    const size_t sm = fw_smem_bytes(W, H);
     if (set_diff_attributes() != cudaSuccess) return SNCC_ERR_CUDA;
-    dim3 grid((U + kTX - 1) / kTX, (V + kTY - 1) / kTY);
+    dim3 grid((U + kFwTX - 1) / kFwTX, (V + kFwTY - 1) / kFwTY);
     diff_forward_kernel<<<grid, 256, sm, st>>>(d_f, M, N, f_stride, W, H, c, t0, scal, d_rho_k, d_rho_t,
                                                reinterpret_cast<float*>(ws + L.ef),
                                                reinterpret_cast<float*>(ws + L.fbar), d_loss);
