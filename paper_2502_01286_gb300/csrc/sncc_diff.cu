@@ -30,6 +30,7 @@ constexpr int kFwGT = 256 / kFwG;  // forward: threads per group (2 warps)
 constexpr int kFwTX = 32;         // forward: offset columns per CTA (lane = column)
 constexpr int kFwTY = (kFwGT / 32) * kFwXB;  // forward: offset rows per CTA (8)
 constexpr int kGtChunks = 192;    // offset-row chunks of the Gt correlation
+constexpr int kGtReduceLanes = 8;  // lanes summing the chunk partials of one Gt entry
 constexpr int kGtYB = 16;         // template rows per Gt CTA
 constexpr int kGtXB = 8;          // template columns per Gt thread (register window)
 constexpr int kGtVS = 4;          // offset rows staged at a time
@@ -299,31 +300,50 @@ __global__ void __launch_bounds__(256) diff_forward_kernel(const float* __restri
     if (threadIdx.x == 0) atomicAdd(loss, sum);
 }
 
-// Per-offset coefficients of the backward pass, and the sums A1, A2.
+// Per-offset coefficients of the backward pass, and the sums A1, A2.  The
+// coefficients are FP32 (inputs and outputs are FP32); each warp sums its 32
+// terms of A1 and A2 in FP32 and the warps' sums meet in FP64.
+__device__ __forceinline__ float warp_sum_float(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __global__ void __launch_bounds__(256) diff_coeff_kernel(int UV, const float* __restrict__ rho_k,
                                                          const float* __restrict__ rho_t,
                                                          const float* __restrict__ ef,
                                                          const float* __restrict__ fbar, const double* dloss,
                                                          double* scal, float* a, float* b, float* h, float* hf) {
-    __shared__ double red[8];
+    __shared__ double red[2][8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double s1 = 0.0, s2 = 0.0;
+    float s1 = 0.0f, s2 = 0.0f;
     if (i < UV) {
-        const double d = (double)rho_k[i] - (double)rho_t[i];
-        const double g = 2.0 * (*dloss) * d;
-        const double e = ef[i];
-        const double ai = g / sqrt(e * scal[1]);
-        const double hi = g * d / e;
-        a[i] = (float)ai;
-        b[i] = (float)(g / sqrt(e * scal[2]));
-        h[i] = (float)hi;
-        hf[i] = (float)(hi * fbar[i]);
+        const float d = rho_k[i] - rho_t[i];
+        const float g = (float)(2.0 * (*dloss)) * d;
+        const float e = ef[i];
+        const float ai = g / sqrtf(e * (float)scal[1]);
+        const float hi = g * d / e;
+        a[i] = ai;
+        b[i] = g / sqrtf(e * (float)scal[2]);
+        h[i] = hi;
+        hf[i] = hi * fbar[i];
         s1 = ai * fbar[i];
         s2 = g * rho_k[i];
     }
-    const double r1 = block_sum_double(s1, red);
-    const double r2 = block_sum_double(s2, red);
+    s1 = warp_sum_float(s1);
+    s2 = warp_sum_float(s2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = s1;
+        red[1][warp] = s2;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double r1 = 0.0, r2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            r1 += red[0][w];
+            r2 += red[1][w];
+        }
         atomicAdd(&scal[3], r1);
         atomicAdd(&scal[4], r2);
     }
@@ -535,11 +555,16 @@ __global__ void __launch_bounds__(128) diff_gt_kernel(const float* __restrict__ 
 // Gt = the sum of the chunk partials, in a fixed order.
 __global__ void __launch_bounds__(256) diff_gt_reduce_kernel(int T, const double* __restrict__ gtp,
                                                              double* __restrict__ gt) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= T) return;
+    // kGtReduceLanes lanes per entry, each summing every kGtReduceLanes-th
+    // chunk, then a fixed shuffle tree
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) / kGtReduceLanes;
+    const int l = threadIdx.x % kGtReduceLanes;
     double s = 0.0;
-    for (int ch = 0; ch < kGtChunks; ++ch) s += gtp[(size_t)ch * T + i];
-    gt[i] = s;
+    if (e < T)
+        for (int ch = l; ch < kGtChunks; ch += kGtReduceLanes) s += gtp[(size_t)ch * T + e];
+#pragma unroll
+    for (int o = kGtReduceLanes / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, kGtReduceLanes);
+    if (e < T && l == 0) gt[e] = s;
 }
 
 // dL/dk_j for every segment: sum of Gt over the rectangle, minus the mean and
@@ -649,7 +674,7 @@ extern "C" int sncc_diff_backward(const float* d_f, int M, int N, int f_stride, 
     diff_gt_kernel<<<dim3((H + kGtYB - 1) / kGtYB, kGtChunks), gt_threads, 0, st>>>(d_f, M, N, f_stride, W, H, a,
                                                                                     gtp);
     double* gt = reinterpret_cast<double*>(ws + L.gt);
-    diff_gt_reduce_kernel<<<(W * H + 255) / 256, 256, 0, st>>>(W * H, gtp, gt);
+    diff_gt_reduce_kernel<<<(W * H * kGtReduceLanes + 255) / 256, 256, 0, st>>>(W * H, gtp, gt);
     diff_grad_k_kernel<<<(K + 255) / 256, 256, 0, st>>>(W, H, reinterpret_cast<const int4*>(d_rects), d_k, K, gt,
                                                         scal, d_grad_k);
     return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
