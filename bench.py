@@ -1071,7 +1071,8 @@ def run_gpu_diff(args, world, rank, local, pg):
             "config": {"workload": "diff-512x512f32-t48x48-sigma12", "segments": int(seg.K),
                        "l2": "flushed between steps (256 MiB write)",
                        "step": "loss forward + backward w.r.t. segment values and source (kernel launches: "
-                               "forward 2, backward 2 + forward 2 recomputed + 4)"},
+                               "forward 2: prep, forward; backward 6: coefficients, row sums, dL/df, Gt, "
+                               "Gt reduce, dL/dk)"},
             "forward_call_ms": fwd_ms, "backward_call_ms": bwd_ms,
             "roofline": {"bound": "alu", "kernel": "sncc_diff_backward (diff_coeff, diff_rowbox, diff_grad_f, diff_gt, "
                                                     "diff_gt_reduce, diff_grad_k)",
@@ -1081,7 +1082,7 @@ def run_gpu_diff(args, world, rank, local, pg):
             "e2e": {"value": sum_over_ranks(pg, U * V) / (e2e_ms_step * 1e-3) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": M * N * 4, "d2h_bytes_per_step": 8 + 4 * pb.K, "ms_per_step": e2e_ms_step},
             "refit": {"steps": 50, "loss_first": losses[0], "loss_last": losses[-1]},
-            "gpu_launches": args.steps * 10, "clocks": clk}
+            "gpu_launches": args.steps * 8, "clocks": clk}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
