@@ -12,8 +12,10 @@
 // copies are spaced 8 words (mod 32) apart, so the 32 lanes hit 32 banks.
 // A block adds at most 4096 * 65025 < 2^32 per offset, so the per-block
 // sums are exact in uint32 and are flushed into 64-bit totals.  The window
-// sums come from the sum tables; the final ratio is formed in double from
-// exact integers.
+// sums come from the sum tables; from the exact integers, the numerator and
+// n^2 E_f are scaled by 1/n in FP64 and the ratio is finished in FP32 (a
+// square root and a division per offset in FP64 would occupy GB300's slow
+// FP64 pipe).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -50,7 +52,8 @@ template <int R, bool S64>
 __global__ void __launch_bounds__(256)
     exact_kernel(const uint8_t* __restrict__ f, int M, int N, int f_stride, const uint8_t* __restrict__ t, int W,
                  int H, int t_stride, long long T, long long T2, const void* __restrict__ s,
-                 const int64_t* __restrict__ s2, int pitch, float* __restrict__ rho, int rho_pitch) {
+                 const int64_t* __restrict__ s2, int pitch, double rn, float etn, float* __restrict__ rho,
+                 int rho_pitch) {
     constexpr int FR = WARPS * R + kTB;  // region rows (one spare)
     constexpr int CW = copy_words(FR);
     extern __shared__ __align__(16) uint32_t smx[];
@@ -127,7 +130,6 @@ __global__ void __launch_bounds__(256)
 
     const int u = u0 + lane;
     const long long n = (long long)W * H;
-    const long long vt = n * T2 - T * T;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = v0 + warp * R + r;
@@ -138,7 +140,8 @@ __global__ void __launch_bounds__(256)
                               s2[(size_t)v * pitch + u + W] + s2[(size_t)v * pitch + u];
         const long long vf = n * sf2 - sf * sf;
         const long long num = n * (long long)acc[r] - T * sf;
-        const float out = (vf > 0 && vt > 0) ? (float)((double)num / sqrt((double)vf * (double)vt)) : 0.0f;
+        // rho = (num / n) / sqrt((vf / n) (vt / n)); etn = vt / n > 0
+        const float out = vf > 0 ? (float)((double)num * rn) / sqrtf((float)((double)vf * rn) * etn) : 0.0f;
         rho[(size_t)v * rho_pitch + u] = out;
     }
 }
@@ -146,18 +149,18 @@ __global__ void __launch_bounds__(256)
 template <int R>
 cudaError_t launch_exact(bool s64, dim3 grid, cudaStream_t st, const uint8_t* f, int M, int N, int f_stride,
                          const uint8_t* t, int W, int H, int t_stride, long long T, long long T2, const void* s,
-                         const int64_t* s2, int pitch, float* rho, int rho_pitch) {
+                         const int64_t* s2, int pitch, double rn, float etn, float* rho, int rho_pitch) {
     constexpr size_t sm = exact_smem_bytes<R>();
     cudaError_t attr = cudaFuncSetAttribute(exact_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (attr == cudaSuccess)
         attr = cudaFuncSetAttribute(exact_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (attr != cudaSuccess) return attr;
     if (s64)
-        exact_kernel<R, true><<<grid, 256, sm, st>>>(f, M, N, f_stride, t, W, H, t_stride, T, T2, s, s2, pitch, rho,
-                                                      rho_pitch);
+        exact_kernel<R, true><<<grid, 256, sm, st>>>(f, M, N, f_stride, t, W, H, t_stride, T, T2, s, s2, pitch, rn,
+                                                      etn, rho, rho_pitch);
     else
         exact_kernel<R, false><<<grid, 256, sm, st>>>(f, M, N, f_stride, t, W, H, t_stride, T, T2, s, s2, pitch,
-                                                       rho, rho_pitch);
+                                                       rn, etn, rho, rho_pitch);
     return cudaGetLastError();
 }
 
@@ -176,6 +179,8 @@ extern "C" int sncc_exact_map(const uint8_t* d_f, int M, int N, int f_stride, co
     if ((int64_t)W * H > ((int64_t)1 << 23)) return SNCC_ERR_UNSUPPORTED;
     const long long n = (long long)W * H;
     if (n * T2 - T * T <= 0) return SNCC_ERR_UNIFORM;
+    const double rn = 1.0 / (double)n;
+    const float etn = (float)((double)(n * T2 - T * T) * rn);  // E_t
     const int tu = (U + TILE_U - 1) / TILE_U;
     int R = 2;
     for (int c : {8, 4}) {
@@ -187,12 +192,12 @@ extern "C" int sncc_exact_map(const uint8_t* d_f, int M, int N, int f_stride, co
     const bool s64 = (s_bits == 64);
     if (R == 8)
         e = launch_exact<8>(s64, grid, st, d_f, M, N, f_stride, d_t, W, H, t_stride, T, T2, d_s, d_s2, sat_pitch,
-                            d_rho, rho_pitch);
+                            rn, etn, d_rho, rho_pitch);
     else if (R == 4)
         e = launch_exact<4>(s64, grid, st, d_f, M, N, f_stride, d_t, W, H, t_stride, T, T2, d_s, d_s2, sat_pitch,
-                            d_rho, rho_pitch);
+                            rn, etn, d_rho, rho_pitch);
     else
         e = launch_exact<2>(s64, grid, st, d_f, M, N, f_stride, d_t, W, H, t_stride, T, T2, d_s, d_s2, sat_pitch,
-                            d_rho, rho_pitch);
+                            rn, etn, d_rho, rho_pitch);
     return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }
