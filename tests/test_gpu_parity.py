@@ -108,7 +108,7 @@ def test_integral_rejects_int32_overflow(sncc):
 # ------------------------------------------------------------------ coarse pass
 SHAPES = [
     # (M, N, W, H, sigma)
-    (256, 256, 32, 32, 10.0),   # the 256^2 / 32^2 workload, sigma 10
+    (256, 256, 32, 32, 3.0),    # 256^2 source, 32^2 template (std 5.5 with this seed: sigma 3)
     (70, 45, 13, 9, 3.0),       # ragged tail in both directions
     (100, 100, 64, 64, 5.0),    # largest single-block template
     (130, 90, 100, 70, 6.0),    # multi-block template (64 x 64 blocks, ragged)
