@@ -132,6 +132,25 @@ def test_vertical_runs_partition_the_corners(sncc):
     assert (pi["corners"], pi["runs8"], pi["runs4"], pi["runs2"], pi["runs1"]) == (440, 44, 22, 0, 0)
 
 
+@pytest.mark.parametrize("W,H", [(1, 64), (64, 1), (3, 256), (256, 3), (65, 64), (64, 65), (700, 2), (2, 700)])
+def test_plan_shapes_thin_and_edge_templates(sncc, W, H):
+    """Thin templates and templates one pixel past a block edge: the plan's
+    blocks cover the template, the runs partition the corners, and the
+    one-block layout applies exactly up to 64 x 64."""
+    t = synth.random_image(W * 1000 + H, W, H)
+    seg = sncc.build_segments(t, 20.0)
+    if not seg.Ek > 0:
+        pytest.skip("uniform approximation")
+    pi = seg.plan_info()
+    assert 8 * pi["runs8"] + 4 * pi["runs4"] + 2 * pi["runs2"] + pi["runs1"] == pi["corners"]
+    if W <= 64 and H <= 64:
+        assert pi["blocks"] == 1 and pi["wide_blocks"] == 1 and pi["corners"] == pi["template_corners"]
+    else:
+        nb64 = -(-W // 64) * -(-H // 64)
+        assert 1 <= pi["wide_blocks"] <= nb64
+        assert pi["wide_corners"] >= pi["template_corners"]  # block edges only add corners
+
+
 def test_host_argument_errors(sncc):
     lib = sncc.lib()
     seg = sncc.build_segments(synth.case_plain().t, 10.0)
