@@ -116,6 +116,8 @@ SHAPES = [
     (300, 40, 23, 40, 4.0),     # V = 1
     (120, 110, 37, 29, 0.0),    # sigma 0: every pixel its own segment before merging
     (97, 61, 2, 1, 0.5),        # two-pixel template
+    (300, 60, 256, 3, 2.0),     # wide, three rows: 64 x 64 blocks along one axis
+    (30, 900, 3, 700, 2.0),     # tall, three columns: 11 blocks down one column
 ]
 
 
