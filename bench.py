@@ -620,14 +620,16 @@ def run_gpu(args, world, rank, local, pg):
     exact_ms = statistics.median(ex_ms)
     max_dncc = [float((m.rho - exact_rho).abs().max().item()) for m in mbs]
 
-    # --- sum tables alone: HBM roofline of the three sum-table kernels ---
+    # --- sum tables alone: HBM roofline of the three sum-table kernels,
+    # replayed from a graph as in the step ---
+    sat_graph = sncc.capture_graph(lambda: sncc.integral(fd, tables, workspace=ws))
     sat_ms = []
     for k in range(20):
         flush.fill_(k)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        sncc.integral(fd, tables, workspace=ws)
+        sat_graph.replay()
         b.record(stream)
         torch.cuda.synchronize()
         sat_ms.append(a.elapsed_time(b))
