@@ -338,6 +338,83 @@ int sncc_refine_segmented_tiles(const sncc_segments* seg, const void* d_plan, co
                                 sncc_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Frame pipeline: a stream of host frames (GPU)                       */
+/* ------------------------------------------------------------------ */
+
+/* Caller-owned device buffers of one pipeline slot (two slots alternate).
+ * Entries q < n of the per-approximation arrays are used; either every
+ * d_rho[q] is NULL (no maps) or none is. */
+typedef struct {
+    uint8_t* d_frame;                    /* N x M source, row stride M bytes */
+    void* d_s;                           /* sum tables (sncc_integral), s_bits / sat_pitch */
+    int64_t* d_s2;
+    void* d_ws;                          /* sncc_integral workspace */
+    size_t ws_bytes;
+    float* d_rho[SNCC_MULTI_MAX];        /* V x rho_pitch maps, or NULL */
+    int32_t* d_cand[SNCC_MULTI_MAX];     /* cand_cap candidates each */
+    int32_t* d_count[SNCC_MULTI_MAX];
+    int32_t* d_status[SNCC_MULTI_MAX];
+    sncc_match_t* d_out[SNCC_MULTI_MAX]; /* out_cap matches each */
+    int32_t* d_nout[SNCC_MULTI_MAX];
+    void* d_rws[SNCC_MULTI_MAX];         /* sncc_refine workspaces of rws_bytes */
+    size_t rws_bytes;
+} sncc_pipeline_slot;
+
+typedef struct sncc_pipeline_st* sncc_pipeline;
+
+/*
+ * sncc_pipeline_create - a pipeline matching a stream of frames with one
+ * template at n (1 .. SNCC_MULTI_MAX) std thresholds: per frame the sum
+ * tables, the coarse pass of every approximation (one fused launch when
+ * sncc_match_multi accepts them) and the exact refine of each (Section 5,
+ * main algorithm with an exact second stage).  Each slot's path is captured
+ * into a CUDA graph here, after one eager run per slot.
+ *
+ *   segs, d_plans, taus  the n approximations (same template size), their
+ *                        uploaded plans and coarse thresholds
+ *   d_t, t_stride        device template (uint8) for the exact refine
+ *   M, N, s_bits, sat_pitch, rho_pitch, cand_cap, out_cap
+ *                        as for sncc_integral / sncc_match / sncc_refine
+ *   tau_exact            exact-refine threshold
+ *   slots                two slots of device buffers (caller-owned; they
+ *                        must outlive the pipeline)
+ *   out                  receives the pipeline (sncc_pipeline_destroy)
+ * The library allocates no device memory; it creates three streams, four
+ * events, two graphs and a small pinned host array.
+ */
+int sncc_pipeline_create(const sncc_segments* const* segs, const void* const* d_plans, int n, const uint8_t* d_t,
+                         int t_stride, int M, int N, int s_bits, int sat_pitch, const float* taus, float tau_exact,
+                         int cand_cap, int out_cap, int rho_pitch, const sncc_pipeline_slot* slots,
+                         sncc_pipeline* out);
+
+/*
+ * sncc_pipeline_submit - queues one frame (host memory, N x M, row stride M;
+ * pinned for an asynchronous copy) and returns the previous frame's results.
+ * The frame is copied on the pipeline's copy stream once the frame that last
+ * used the slot has finished with it, and matched on the compute stream.
+ * Then the call waits for the previous frame only, and writes its match
+ * count into h_count[q] and its status word into h_status[q] (if h_status is
+ * not NULL).  Its first min(count, out_cap) matches, sorted by v*U+u, go to
+ * h_out[q] (host memory, out_cap records; pinned for speed).
+ * Returns 1 when a previous frame was reported, 0 on the first call, or a
+ * negative code.
+ */
+int sncc_pipeline_submit(sncc_pipeline p, const uint8_t* h_frame, sncc_match_t* const* h_out, int32_t* h_count,
+                         int32_t* h_status);
+
+/* The results of the last submitted frame, as above (0 if none was submitted). */
+int sncc_pipeline_flush(sncc_pipeline p, sncc_match_t* const* h_out, int32_t* h_count, int32_t* h_status);
+
+/* 1 if the coarse passes run as one fused launch, 0 if one launch each. */
+int sncc_pipeline_fused(sncc_pipeline p);
+
+/* The stream frames are matched on, e.g. to queue other work between frames. */
+sncc_stream_t sncc_pipeline_compute_stream(sncc_pipeline p);
+
+/* Waits for the pipeline's streams and releases it; safe on NULL. */
+void sncc_pipeline_destroy(sncc_pipeline p);
+
+/* ------------------------------------------------------------------ */
 /* Batched matching: many templates x several sources, one launch      */
 /* ------------------------------------------------------------------ */
 

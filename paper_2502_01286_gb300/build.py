@@ -24,7 +24,7 @@ LIB = os.path.join(OUT, "libsncc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["sncc_host.cpp", "sncc_sat.cu", "sncc_match.cu", "sncc_refine.cu", "sncc_exact.cu", "sncc_probe.cu",
            "sncc_refine_seg.cu", "sncc_batch.cu",
-           "sncc_diff.cu"]
+           "sncc_diff.cu", "sncc_pipeline.cpp"]
 
 
 def _nvcc() -> str:

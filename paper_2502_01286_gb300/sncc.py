@@ -32,7 +32,8 @@ STATUS_CAND_OVERFLOW, STATUS_MATCH_OVERFLOW, STATUS_WAIT_TIMEOUT, STATUS_SORT_OV
 
 EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_sat_pitch",
             "sncc_integral_workspace_bytes", "sncc_integral", "sncc_plan_bytes", "sncc_plan_upload", "sncc_match",
-            "sncc_match_multi",
+            "sncc_match_multi", "sncc_pipeline_create", "sncc_pipeline_submit", "sncc_pipeline_flush",
+            "sncc_pipeline_fused", "sncc_pipeline_compute_stream", "sncc_pipeline_destroy",
             "sncc_refine_workspace_bytes", "sncc_refine", "sncc_exact_map", "sncc_get_plan_info",
             "sncc_probe_smem_read", "sncc_probe_alu", "sncc_probe_wait_timeout", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_refine_segmented_tiles",
             "sncc_refine_segmented_tiles_workspace_bytes", "sncc_batch_create",
@@ -91,6 +92,24 @@ _lib.sncc_match.argtypes = [C.POINTER(_Segments), _vp, _vp, C.c_int, _vp, C.c_in
 _lib.sncc_match_multi.argtypes = [C.POINTER(C.POINTER(_Segments)), C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp,
                                   C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(_vp), C.c_int,
                                   C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp), _vp]
+
+
+class _PipelineSlot(C.Structure):
+    _fields_ = [("d_frame", _vp), ("d_s", _vp), ("d_s2", _vp), ("d_ws", _vp), ("ws_bytes", C.c_size_t),
+                ("d_rho", _vp * 4), ("d_cand", _vp * 4), ("d_count", _vp * 4), ("d_status", _vp * 4),
+                ("d_out", _vp * 4), ("d_nout", _vp * 4), ("d_rws", _vp * 4), ("rws_bytes", C.c_size_t)]
+
+
+_lib.sncc_pipeline_create.argtypes = [C.POINTER(C.POINTER(_Segments)), C.POINTER(_vp), C.c_int, _vp, C.c_int,
+                                      C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float), C.c_float, C.c_int,
+                                      C.c_int, C.c_int, C.POINTER(_PipelineSlot), C.POINTER(_vp)]
+_lib.sncc_pipeline_submit.argtypes = [_vp, _vp, C.POINTER(_vp), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+_lib.sncc_pipeline_flush.argtypes = [_vp, C.POINTER(_vp), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+_lib.sncc_pipeline_fused.argtypes = [_vp]
+_lib.sncc_pipeline_compute_stream.argtypes = [_vp]
+_lib.sncc_pipeline_compute_stream.restype = _vp
+_lib.sncc_pipeline_destroy.argtypes = [_vp]
+_lib.sncc_pipeline_destroy.restype = None
 _lib.sncc_refine_workspace_bytes.argtypes = [C.c_int]
 _lib.sncc_refine_workspace_bytes.restype = C.c_size_t
 _lib.sncc_refine.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64,
@@ -649,92 +668,115 @@ class MultiMatcher:
 
 class StreamMatcher:
     """Pipelined matching of a stream of frames (pinned host uint8 tensors of
-    N x M) with one template at one or more std thresholds.
-
-    Two slots, each a MultiMatcher with its own source buffer, replayed from a
-    CUDA graph.  submit(frame) copies the frame host -> device on a copy
-    stream while the previous frame is still being matched, queues the frame's
-    graph on the compute stream, and then reads back the match lists of the
-    previous frame on a third stream (waiting for that frame only), so the
-    copies and the host's work overlap the GPU's.  Returns the previous
-    frame's lists (None on the first call); flush() returns the last one.
-    A list is one (u, v, rho) triple of numpy arrays per threshold."""
+    N x M) with one template at one or more std thresholds, through the
+    library's native frame pipeline (sncc_pipeline_*): two slots of device
+    buffers, each slot's path captured in a CUDA graph, the next frame's copy
+    and the previous frame's read-back overlapping the current frame's
+    matching, one library call per frame.  submit(frame) returns the previous
+    frame's lists (None on the first call); flush() returns the last one.  A
+    list is one (u, v, rho) triple of numpy arrays per threshold."""
 
     def __init__(self, t: np.ndarray, sigmas, M: int, N: int, precision: float = 0.85,
                  tau_exact: Optional[float] = None, k_max: int = 0, cand_cap: int = 1 << 20, out_cap: int = 1 << 16,
                  keep_rho: bool = False, device="cuda"):
         torch = _torch()
-        self.M, self.N = M, N
-        self.slots = [MultiMatcher(t, sigmas, M, N, precision, tau_exact, k_max, cand_cap, out_cap, keep_rho, device)
-                      for _ in range(2)]
-        self.src = [torch.zeros((N, M), dtype=torch.uint8, device=device) for _ in range(2)]
-        self.graphs = [sl.capture(f) for sl, f in zip(self.slots, self.src)]
-        self.compute = torch.cuda.Stream(device)
-        self.copy = torch.cuda.Stream(device)
-        self.readback = torch.cuda.Stream(device)
-        self.copied = [torch.cuda.Event() for _ in range(2)]
-        self.done = [torch.cuda.Event() for _ in range(2)]
-        self.used = [False, False]
-        self.counts = [torch.empty(len(sigmas), dtype=torch.int32, pin_memory=True) for _ in range(2)]
-        self.records = [[torch.empty((rb.cap, 3), dtype=torch.int32, pin_memory=True) for rb in sl.rbs]
-                        for sl in self.slots]
+        self.segs = [build_segments(t, sg, k_max) for sg in sigmas]
+        n = len(self.segs)
+        if not 1 <= n <= MULTI_MAX:
+            raise ValueError("1 .. %d thresholds" % MULTI_MAX)
+        if not all(sg.Ek > 0 for sg in self.segs):
+            raise SnccError(ERR_UNIFORM, "StreamMatcher")
+        self.M, self.N, self.n = M, N, n
+        W, H = self.segs[0].W, self.segs[0].H
+        self.taus = [float(precision) * sg.rho_max for sg in self.segs]
+        self.tau_e = float(precision) if tau_exact is None else float(tau_exact)
+        self.t_dev = torch.as_tensor(np.ascontiguousarray(t, np.uint8)).to(device)
+        self.plans = [upload_plan(sg, device) for sg in self.segs]
+        self._bufs = []
+        slots = (_PipelineSlot * 2)()
+        rho_pitch = 0
+        for k in range(2):
+            frame = torch.zeros((N, M), dtype=torch.uint8, device=device)
+            tables = alloc_tables(M, N, None, device)
+            ws = integral_workspace(M, N, device)
+            mbs = [alloc_match(M, N, W, H, cand_cap, keep_rho, device) for _ in self.segs]
+            rbs = [alloc_refine(out_cap, device) for _ in self.segs]
+            sl = slots[k]
+            sl.d_frame, sl.d_s, sl.d_s2 = frame.data_ptr(), tables.s.data_ptr(), tables.s2.data_ptr()
+            sl.d_ws, sl.ws_bytes = ws.data_ptr(), ws.numel()
+            for q in range(n):
+                sl.d_rho[q] = _ptr(mbs[q].rho)
+                sl.d_cand[q], sl.d_count[q] = mbs[q].cand.data_ptr(), mbs[q].count.data_ptr()
+                sl.d_status[q] = mbs[q].status.data_ptr()
+                sl.d_out[q], sl.d_nout[q], sl.d_rws[q] = rbs[q].out.data_ptr(), rbs[q].nout.data_ptr(), rbs[q].ws.data_ptr()
+            sl.rws_bytes = rbs[0].ws.numel()
+            if keep_rho:
+                rho_pitch = mbs[0].rho.stride(0)
+            self._bufs.append((frame, tables, ws, mbs, rbs))
+        self.s_bits = self._bufs[0][1].s_bits
+        torch.cuda.synchronize()  # the buffers are allocated and zeroed before the pipeline's streams use them
+        seg_arr = (C.POINTER(_Segments) * n)(*[C.pointer(sg._s) for sg in self.segs])
+        plan_arr = (_vp * n)(*[pl.data_ptr() for pl in self.plans])
+        tau_arr = (C.c_float * n)(*self.taus)
+        h = _vp()
+        _check(_lib.sncc_pipeline_create(seg_arr, plan_arr, n, self.t_dev.data_ptr(), self.t_dev.stride(0), M, N,
+                                         self.s_bits, self._bufs[0][1].pitch, tau_arr, self.tau_e, cand_cap, out_cap,
+                                         rho_pitch, slots, C.byref(h)), "sncc_pipeline_create")
+        self._h = h
+        self.fused = bool(_lib.sncc_pipeline_fused(h))
+        self.compute = torch.cuda.ExternalStream(_lib.sncc_pipeline_compute_stream(h), device=device)
+        self.out_cap = out_cap
+        self.h_out = [torch.empty((out_cap, 3), dtype=torch.int32, pin_memory=True) for _ in self.segs]
+        self._h_out_ptrs = (_vp * n)(*[x.data_ptr() for x in self.h_out])
+        self.h_count = np.zeros(n, np.int32)
+        self.h_status = np.zeros(n, np.int32)
+        self._pc = self.h_count.ctypes.data_as(C.POINTER(C.c_int32))
+        self._ps = self.h_status.ctypes.data_as(C.POINTER(C.c_int32))
         self.frames = 0
         self.d2h_bytes = 0
-        torch.cuda.synchronize()
+        self.status_bits = 0
+
+    def _lists(self):
+        self.d2h_bytes += 8 * self.n
+        out = []
+        for q in range(self.n):
+            m = min(int(self.h_count[q]), self.out_cap)
+            self.status_bits |= int(self.h_status[q])
+            self.d2h_bytes += 12 * m
+            raw = self.h_out[q][:m].numpy()
+            out.append((raw[:, 0].astype(np.int64), raw[:, 1].astype(np.int64), raw[:, 2].copy().view(np.float32)))
+        return out
 
     def submit(self, frame):
         """Queue one frame; returns the previous frame's match lists."""
         torch = _torch()
-        if frame.dtype != torch.uint8 or tuple(frame.shape) != (self.N, self.M):
-            raise ValueError("frame must be a uint8 tensor of shape (N, M)")
-        slot = self.frames & 1
-        if self.used[slot]:  # the copy reuses the source buffer of the frame two back
-            self.copy.wait_event(self.done[slot])
-        with torch.cuda.stream(self.copy):
-            self.src[slot].copy_(frame, non_blocking=True)
-            self.copied[slot].record(self.copy)
-        self.compute.wait_event(self.copied[slot])
-        with torch.cuda.stream(self.compute):
-            self.graphs[slot].replay()
-            self.done[slot].record(self.compute)
-        self.used[slot] = True
-        prev = self._collect(slot ^ 1) if self.frames > 0 else None
+        if frame.dtype != torch.uint8 or tuple(frame.shape) != (self.N, self.M) or frame.is_cuda or \
+                not frame.is_contiguous():
+            raise ValueError("frame must be a contiguous host uint8 tensor of shape (N, M)")
+        rc = _lib.sncc_pipeline_submit(self._h, frame.data_ptr(), self._h_out_ptrs, self._pc, self._ps)
+        if rc < 0:
+            _check(rc, "sncc_pipeline_submit")
         self.frames += 1
-        return prev
+        return self._lists() if rc == 1 else None
 
     def flush(self):
         """The match lists of the last submitted frame (None if there is none)."""
-        if self.frames == 0:
-            return None
-        return self._collect((self.frames - 1) & 1)
-
-    def _collect(self, slot):
-        torch = _torch()
-        rs = self.readback
-        rs.wait_event(self.done[slot])
-        rbs = self.slots[slot].rbs
-        with torch.cuda.stream(rs):
-            for q, rb in enumerate(rbs):
-                self.counts[slot][q:q + 1].copy_(rb.nout, non_blocking=True)
-        rs.synchronize()
-        ns = [min(int(c), rb.cap) for c, rb in zip(self.counts[slot].tolist(), rbs)]
-        with torch.cuda.stream(rs):
-            for n, rb, h in zip(ns, rbs, self.records[slot]):
-                if n:
-                    h[:n].copy_(rb.out[:n], non_blocking=True)
-        if any(ns):
-            rs.synchronize()
-        self.d2h_bytes += 4 * len(rbs) + 12 * sum(ns)
-        out = []
-        for n, h in zip(ns, self.records[slot]):
-            raw = h[:n].numpy()
-            out.append((raw[:, 0].astype(np.int64), raw[:, 1].astype(np.int64), raw[:, 2].copy().view(np.float32)))
-        return out
+        rc = _lib.sncc_pipeline_flush(self._h, self._h_out_ptrs, self._pc, self._ps)
+        if rc < 0:
+            _check(rc, "sncc_pipeline_flush")
+        return self._lists() if rc == 1 else None
 
     def status(self) -> int:
-        torch = _torch()
-        torch.cuda.synchronize()
-        return self.slots[0].status() | self.slots[1].status()
+        """OR of the status words of every frame reported so far."""
+        return self.status_bits
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sncc_pipeline_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 # ---------------------------------------------------------------------------

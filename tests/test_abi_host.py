@@ -227,6 +227,30 @@ def test_match_multi_fusability_decided_on_host(sncc):
     assert call([small, big]) == sncc.ERR_ARG
 
 
+def test_pipeline_host_argument_errors(sncc):
+    """The frame pipeline rejects bad arguments before any CUDA call, and
+    its query and release calls are safe on a null handle."""
+    lib = sncc.lib()
+    seg = sncc.build_segments(synth.case_hd(M=300, N=260, W=48, H=40, seed=4).t, 4.0)
+    segs = (C.POINTER(sncc._Segments) * 1)(C.pointer(seg._s))
+    plans = (C.c_void_p * 1)(256)
+    taus = (C.c_float * 1)(0.5)
+    slots = (sncc._PipelineSlot * 2)()
+    h = C.c_void_p()
+    args = lambda n, sl, cap: (segs, plans, n, C.c_void_p(256), 48, 300, 260, 32, 320, taus, 0.8, cap, 16, 0, sl,
+                               C.byref(h))
+    assert lib.sncc_pipeline_create(*args(0, slots, 16)) == sncc.ERR_ARG
+    assert lib.sncc_pipeline_create(*args(5, slots, 16)) == sncc.ERR_ARG
+    assert lib.sncc_pipeline_create(*args(1, None, 16)) == sncc.ERR_ARG
+    assert lib.sncc_pipeline_create(*args(1, slots, 0)) == sncc.ERR_ARG
+    assert lib.sncc_pipeline_create(*args(1, slots, 16)) == sncc.ERR_ARG  # empty slot buffers
+    assert h.value is None
+    assert lib.sncc_pipeline_fused(None) == sncc.ERR_ARG
+    assert lib.sncc_pipeline_compute_stream(None) is None
+    assert lib.sncc_pipeline_submit(None, None, None, None, None) == sncc.ERR_ARG
+    lib.sncc_pipeline_destroy(None)
+
+
 def test_batch_host_work_lists(sncc):
     """sncc_batch_create on the host: the work list has one item per tile of
     every (source, template) pair, and the offset / corner totals add up."""

@@ -267,8 +267,9 @@ def test_multi_matcher_graph_and_separate_matchers(sncc):
 
 @pytest.mark.parametrize("sigmas", [(3.0, 6.0, 12.0), (5.0,)])
 def test_stream_matcher_equals_one_frame_at_a_time(sncc, sigmas):
-    """Five different frames through the pipelined StreamMatcher give, frame
-    by frame, the match lists of a MultiMatcher run on each frame alone."""
+    """Five different frames through the pipelined StreamMatcher (the
+    library's native frame pipeline) give, frame by frame, the match lists
+    of a MultiMatcher run on each frame alone."""
     frames = [synth.case_hd(M=400, N=300, W=48, H=48, seed=60 + i) for i in range(5)]
     t = frames[0].t
     sm = sncc.StreamMatcher(t, sigmas, 400, 300, precision=0.6)
@@ -280,7 +281,7 @@ def test_stream_matcher_equals_one_frame_at_a_time(sncc, sigmas):
     got.append(sm.flush())
     assert sm.status() == 0
     ref = sncc.MultiMatcher(t, sigmas, 400, 300, precision=0.6)
-    assert sm.slots[0].fused == (len(sigmas) > 1)
+    assert sm.fused == (len(sigmas) > 1)
     nonempty = 0
     for c, lists in zip(frames, got):
         fd = dev(c.f)
