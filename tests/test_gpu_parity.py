@@ -269,10 +269,11 @@ def test_multi_matcher_graph_and_separate_matchers(sncc):
 def test_stream_matcher_equals_one_frame_at_a_time(sncc, sigmas):
     """Five different frames through the pipelined StreamMatcher (the
     library's native frame pipeline) give, frame by frame, the match lists
-    of a MultiMatcher run on each frame alone."""
+    of a MultiMatcher run on each frame alone, and the last frame's rho maps
+    equal that run's."""
     frames = [synth.case_hd(M=400, N=300, W=48, H=48, seed=60 + i) for i in range(5)]
     t = frames[0].t
-    sm = sncc.StreamMatcher(t, sigmas, 400, 300, precision=0.6)
+    sm = sncc.StreamMatcher(t, sigmas, 400, 300, precision=0.6, keep_rho=True)
     got = []
     for c in frames:
         r = sm.submit(torch.as_tensor(c.f).pin_memory())
@@ -293,6 +294,10 @@ def test_stream_matcher_equals_one_frame_at_a_time(sncc, sigmas):
             for x, y in zip(lists[q], want):
                 np.testing.assert_array_equal(x, y)
     assert nonempty > 0
+    # the last frame's maps in its slot equal the one-frame run's
+    last = sm._bufs[(len(frames) - 1) % 2][3]
+    for q in range(len(sigmas)):
+        assert torch.equal(last[q].rho, ref.mbs[q].rho)
 
 
 def test_match_multi_rejects_what_it_cannot_fuse(sncc):
