@@ -1,13 +1,16 @@
 #!/usr/bin/env python3
 """Benchmark of the segmented-NCC hot path on GB300.
 
-Workload (default "hd"): a 1920 x 1080 uint8 source (blobs plus 1/f noise)
-and a 64 x 64 template cropped from it with sigma-3 noise, std thresholds
-5, 10 and 20 swept, coarse precision 0.85 (tau_c = 0.85 * rho_max), exact
-refine threshold 0.85.  One step = one pass of the whole path over the source:
-the sum tables once, then for each threshold the coarse pass (segmented NCC
+Workload (default "texture"): a 4096 x 4096 uint8 high-texture source (300
+random rectangles plus 1/f noise) and a 256 x 256 template cropped from it,
+std threshold 5 (a few thousand segments), coarse precision 0.85
+(tau_c = 0.85 * rho_max), exact refine threshold 0.85, 64-bit sum tables,
+exact direct NCC timed on the same GPU beside it.  One step = one pass of the
+whole path over the source: the sum tables, the coarse pass (segmented NCC
 map, threshold, candidates) and the exact refine of the candidates.  The
-metric counts offsets evaluated: 3 * U * V per step.
+metric counts offsets evaluated: U * V per step and threshold.  Other
+workloads (--workload): "hd" (1920 x 1080, 64 x 64, thresholds 5, 10, 20),
+"plain", "batch", "diff".
 
 Printed: one JSON line (rank 0).  Timing: CUDA events on the launching stream
 around every step, an L2 flush (a 256 MiB write) between steps outside the
@@ -38,8 +41,10 @@ UNIT = "Goffsets/s"
 L2_FLUSH_BYTES = 256 << 20
 
 # name -> (case factory name, std thresholds swept in one step, precision p).
-# "hd" is the workload the metric is quoted on; the others are measured on
-# request (--workload) and are otherwise parity-test cases.
+# "texture" is the workload the metric is quoted on (the largest single
+# problem, where the comparison with exact NCC on the same GPU is made); the
+# others are measured on request (--workload) and are otherwise parity-test
+# cases.
 WORKLOADS = {
     "hd": ("case_hd", (5.0, 10.0, 20.0), 0.85),
     "plain": ("case_plain", (10.0,), 0.9),
@@ -70,7 +75,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["sncc", "reference"], default="sncc")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="hd")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="texture")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     return ap.parse_args()
@@ -191,7 +196,9 @@ class ClockSampler:
 def oracle_sample(case, sigmas, rows_per_sigma, seed=0, precision=None):
     """Runs the oracle's version of one step on `rows_per_sigma` offset rows
     per threshold: sum tables + segmented NCC (Eq. 10 - 18) on those rows,
-    candidates, exact refine.  Returns (offsets, seconds, threads, maps)."""
+    candidates, exact refine.  Returns (offsets, seconds, threads, maps) with
+    maps[sigma] = (rows, rho map (NaN outside the rows), matches (ascending
+    v*U+u), their exact rho)."""
     import oracle as O
     f, t = case.f, case.t
     N, M = f.shape
@@ -207,11 +214,47 @@ def oracle_sample(case, sigmas, rows_per_sigma, seed=0, precision=None):
         t0 = time.perf_counter()
         rho = O.segmented_ncc_map(f, ap, "sat", rows=rows, nthreads=threads)
         cand = O.candidates(rho, p * ap.rho_max)
-        O.refine(f, t, cand, U, p)
+        idx, rho_e = O.refine(f, t, cand, U, p)
         secs += time.perf_counter() - t0
         total += len(rows) * U
-        maps[s] = (rows, rho)
+        maps[s] = (rows, rho, idx, rho_e)
     return total, secs, threads, maps
+
+
+TOL = 1e-5  # the parity bar: |rho_gpu - rho_oracle| and the G13 decision band
+
+
+def sampled_set_check(f, t, rows, rho64, idx_o, rho_o, cand_gpu, match_gpu, U, tau_c, tau_e):
+    """The GPU's candidate and match sets on the oracle's sampled offset rows.
+    G13: every offset with rho64 >= tau_c + TOL must be a candidate and every
+    one with rho64 < tau_c - TOL must not; offsets inside the band may go
+    either way and are counted.  The match lists may differ only at offsets
+    inside the coarse band or inside the exact band around tau_e."""
+    import oracle as O
+    V = rho64.shape[0]
+    on_rows = np.zeros(V, bool)
+    on_rows[rows] = True
+    got_c = np.zeros(rho64.shape, bool)
+    cg = np.asarray(cand_gpu, np.int64)
+    got_c.ravel()[cg] = True
+    r, g = rho64[rows], got_c[rows]
+    band = (r >= tau_c - TOL) & (r < tau_c + TOL)
+    violations = int(np.sum(g & (r < tau_c - TOL)) + np.sum(~g & (r >= tau_c + TOL)))
+    mu, mv, mrho = match_gpu
+    sel = on_rows[mv]
+    key_g = mv[sel].astype(np.int64) * U + mu[sel]
+    diff = np.setxor1d(key_g, idx_o)
+    if diff.size:
+        ex = O.ncc_exact_at(f, t, (diff % U).astype(np.int32), (diff // U).astype(np.int32))
+        amb = (np.abs(rho64.ravel()[diff] - tau_c) < TOL) | (np.abs(ex - tau_e) < TOL)
+        outside = int(np.sum(~amb))
+    else:
+        outside = 0
+    common, ig, io = np.intersect1d(key_g, idx_o, return_indices=True)
+    drho = float(np.abs(mrho[sel][ig].astype(np.float64) - rho_o[io]).max()) if common.size else 0.0
+    return {"g13_band_offsets": int(band.sum()), "g13_violations": violations,
+            "candidates_on_rows": int(g.sum()), "matches_oracle": int(idx_o.size), "matches_gpu": int(key_g.size),
+            "match_diff_outside_bands": outside, "max_abs_drho_matches": drho}
 
 
 def calibrate_rows(case, sigmas, budget_s: float) -> int:
@@ -255,7 +298,8 @@ def run_reference(args, world, rank, pg):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.workload, case, sigmas, precision, U, V),
+            "data": "synthetic",
+            "config": workload_config(args.workload, case, sigmas, precision, U, V, case_seed_of(args.workload)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -315,14 +359,15 @@ def run_reference_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(name, case, sigmas, precision, U, V):
+def workload_config(name, case, sigmas, precision, U, V, seed):
+    """The workload as both arms describe it (the same dict in each)."""
     N, M = case.f.shape
     H, W = case.t.shape
     bits = 32 if 255 * M * N < 2 ** 31 else 64
     return {"workload": "%s-%dx%d-t%dx%d-sigma%s" % (name, M, N, W, H, "-".join("%g" % s for s in sigmas)),
             "source": [M, N], "template": [W, H], "sigma_max": list(sigmas), "precision": precision,
             "offsets_per_step": len(sigmas) * U * V, "l2": "flushed between steps (256 MiB write)",
-            "sum_tables": "s int%d, s2 int64" % bits}
+            "sum_tables": "s int%d, s2 int64" % bits, "seed": seed}
 
 
 # ---------------------------------------------------------------------------
@@ -337,16 +382,18 @@ def kernel_hash() -> str:
 
 
 def recorded_traffic(workload: str):
-    """DRAM bytes per launch of the segment-sum kernel from a committed ncu
-    summary, if it was taken on the current kernel source."""
+    """DRAM bytes per launch of the segment-sum kernel on this workload from
+    the committed ncu records, if one was taken on the current kernel
+    source; else None."""
     p = os.path.join(ROOT, "profiles", "match_kernel_traffic.json")
     try:
         d = json.load(open(p))
     except (OSError, ValueError):
         return None
-    if d.get("kernel_hash") != kernel_hash() or d.get("workload") != workload:
-        return None
-    return d.get("dram_bytes_per_launch")
+    for r in d.get("records", []):
+        if r.get("workload") == workload and r.get("kernel_hash") == kernel_hash():
+            return r.get("dram_bytes_per_launch")
+    return None
 
 
 def measured_peaks():
@@ -452,7 +499,7 @@ def run_gpu(args, world, rank, local, pg):
     ws = sncc.integral_workspace(M, N, dev)
     cand_cap, out_cap = U * V, 1 << 16
     mbs = [sncc.alloc_match(M, N, W, H, cand_cap, True, dev) for _ in SIGMAS]
-    rbs = [sncc.alloc_refine(out_cap, dev) for _ in SIGMAS]
+    rbs = [sncc.alloc_refine(M, N, W, H, out_cap, dev) for _ in SIGMAS]
     taus = [PRECISION * s.rho_max for s in segs]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -698,26 +745,31 @@ def run_gpu(args, world, rank, local, pg):
                          "sum tables + segmented NCC + candidates + exact refine" % (min(rows, V), U, V,
                                                                                   list(SIGMAS)),
                "seconds": secs}
-        errs, nrows = [], 0
+        errs, nrows, sets = [], 0, {}
         for i, s in enumerate(SIGMAS):
-            rws, rho = maps[s]
+            rws, rho, idx_o, rho_o = maps[s]
             g = mbs[i].rho[torch.as_tensor(rws, device=dev)].cpu().numpy().astype(np.float64)
             errs.append(float(np.abs(g - rho[rws]).max()))
             nrows += len(rws)
+            n_c = min(counts[i], mbs[i].cand.numel())
+            sets[str(s)] = sampled_set_check(case.f, case.t, rws, rho, idx_o, rho_o,
+                                             mbs[i].cand[:n_c].cpu().numpy(), sncc.matches_to_numpy(rbs[i]),
+                                             U, taus[i], PRECISION)
         oracle_check = {"max_abs_drho_vs_oracle": max(errs), "offset_rows_checked": nrows,
-                        "offsets_checked": nrows * U}
+                        "offsets_checked": nrows * U, "tolerance": TOL,
+                        "candidate_and_match_sets": sets,
+                        "g13_band_offsets": sum(v["g13_band_offsets"] for v in sets.values()),
+                        "g13_violations": sum(v["g13_violations"] for v in sets.values())}
 
     peaks = measured_peaks()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
-        "config": dict(workload_config(args.workload, case, SIGMAS, PRECISION, U, V), seed=case_seed,
-                       launch=("one CUDA graph per step: sum tables, one segment-sum launch over every "
-                               "(tile, threshold) pair, then per threshold exact refine and sort (parallel "
-                               "branches)") if fused else
-                              "one CUDA graph per step: sum tables, then per threshold segment sum, exact "
-                              "refine and sort"),
+        "config": workload_config(args.workload, case, SIGMAS, PRECISION, U, V, case_seed),
+        "launch": ("one CUDA graph per step: sum tables, one segment-sum launch over every (tile, threshold) "
+                   "pair, then per threshold exact refine and sort (parallel branches)") if fused else
+                  "one CUDA graph per step: sum tables, then per threshold segment sum, exact refine and sort",
         "exact_ncc": {"value": U * V / (exact_ms * 1e-3) / 1e9, "unit": UNIT, "ms": exact_ms,
                       "kernel": "direct integer correlation, dp4a (4 byte MACs per instruction)",
                       "roofline": exact_roofline(U * V * W * H, exact_ms, ceil)},
@@ -748,7 +800,8 @@ def run_gpu(args, world, rank, local, pg):
                 "how": "StreamMatcher over %d frames: per frame an L2 flush and the frame's graph on the compute "
                        "stream, the host-to-device copy on a copy stream, the previous frame's match lists read "
                        "back on a third stream; wall clock from the first submit to the last list" % e2e_steps},
-        "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS + (1 + 2 * len(SIGMAS) if fused else 3 * len(SIGMAS))),
+        "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS + (1 if fused else len(SIGMAS)) +
+                                      sncc.REFINE_KERNELS * len(SIGMAS)),
         "clocks": clk, "wall_s_timed": wall,
     }
     if cpu is not None:
@@ -925,7 +978,7 @@ def run_gpu_batch(args, world, rank, local, pg):
         "e2e": {"value": offsets / (e2e_ms_step * 1e-3) / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": sum(f.size for f in srcs), "d2h_bytes_per_step": d2h / e2e_steps,
                 "ms_per_step": e2e_ms_step},
-        "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS * len(srcs) + 3),
+        "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS * len(srcs) + 1 + sncc.REFINE_KERNELS),
         "clocks": clk, "wall_s_timed": wall,
     }
     if cpu is not None:

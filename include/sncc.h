@@ -27,6 +27,14 @@
  *   word, which the caller reads after synchronising the stream; the calls
  *   that take one clear it first, in stream order.
  *
+ * SNCC_STATUS_WAIT_TIMEOUT means that a copy into a CTA's shared memory did
+ * not complete within one second.  The CTA then stops without waiting any
+ * longer, so that copy may still land later in shared memory that another
+ * CTA of the same or a later launch is using.  Discard the outputs of that
+ * call and of every call queued after it on the stream, and do not trust
+ * further results from the context; the limit exists so that a stuck copy
+ * ends in an error instead of a hung GPU.
+ *
  * Thread safety: calls are reentrant; concurrent calls must not share
  * output buffers or workspaces.
  */
@@ -57,7 +65,8 @@ typedef struct CUstream_st* sncc_stream_t;
 /* Device status bits (OR-ed into the caller's int32 status word). */
 #define SNCC_STATUS_CAND_OVERFLOW 1  /* more candidates than cand_cap; count is still exact */
 #define SNCC_STATUS_MATCH_OVERFLOW 2 /* more matches than out_cap; count is still exact */
-#define SNCC_STATUS_WAIT_TIMEOUT 4   /* a bounded wait on an asynchronous copy ran out */
+#define SNCC_STATUS_WAIT_TIMEOUT 4   /* a bounded wait on an asynchronous copy ran out: treat as
+                                        fatal for the stream (see below) */
 #define SNCC_STATUS_SORT_OVERFLOW 8  /* more matches than the sort scratch holds */
 
 /* Human-readable text of a return code (static storage). */
@@ -88,6 +97,9 @@ typedef struct {
     int64_t T, T2;      /* sum of t and of t^2 (exact) */
     double err_bound;   /* bound on |rho_gpu - rho| from weight quantisation */
     void* plan;         /* library-private matching plan (host memory) */
+    double sigma_t;     /* population std of the whole template, sqrt(n T2 - T^2) / n
+                           (the input of sigma_max,fast = 0.99 sigma_t and
+                           sigma_max,slow = 0.1 sigma_t, Section 5) */
 } sncc_segments;
 
 /*
@@ -114,6 +126,18 @@ int sncc_build_segments(const uint8_t* t, int W, int H, int t_stride, double sig
 
 /* Releases what sncc_build_segments allocated; safe on a zeroed struct. */
 void sncc_free_segments(sncc_segments* s);
+
+/*
+ * sncc_template_sigma - sigma_t, the population std of a template: the std
+ * of Eq. 2 taken over the whole template, which the main algorithm of
+ * Section 5 scales into its two thresholds (sigma_max,fast = 0.99 sigma_t,
+ * sigma_max,slow = 0.1 sigma_t).  Computed as sqrt(n T2 - T^2) / n from the
+ * exact sums T and T2 (the radicand exact in 64-bit integers).
+ *   t, W, H, t_stride  host template (uint8)
+ *   sigma_t            receives the value (0 for a uniform template)
+ * Returns SNCC_OK, SNCC_ERR_ARG or SNCC_ERR_UNSUPPORTED (W*H > 2^23).
+ */
+int sncc_template_sigma(const uint8_t* t, int W, int H, int t_stride, double* sigma_t);
 
 /* ------------------------------------------------------------------ */
 /* Sum tables (GPU)                                                    */
@@ -169,6 +193,10 @@ int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int
  *
  * The first call on a device (with that device current) looks up the
  * array's device address; make that first call before any stream capture.
+ * The address is kept per device together with the identity of the context
+ * it was taken in; a call made in another context (after cudaDeviceReset, or
+ * once the primary context was destroyed and created again) looks it up
+ * anew, so make the first call after such a reset outside a capture too.
  * Every call shares the one array and leaves its contents behind; nothing
  * in it needs to start at zero, because each call writes every entry it
  * later reads.  Calls whose executions overlap on the GPU (other streams,
@@ -256,8 +284,11 @@ typedef struct {
     float rho;
 } sncc_match_t;
 
-/* Scratch bytes sncc_refine needs for out_cap matches. */
-size_t sncc_refine_workspace_bytes(int out_cap);
+/* Scratch bytes sncc_refine and sncc_refine_segmented need for out_cap
+ * matches on an M x N source with a W x H template: the unsorted match
+ * records, plus one bit per offset and a prefix count per 32 offsets for the
+ * sorted write-out (about U*V/4 bytes).  0 for invalid sizes. */
+size_t sncc_refine_workspace_bytes(int M, int N, int W, int H, int out_cap);
 
 /*
  * sncc_refine - exact NCC (Eq. 1) at each candidate and the match list.
@@ -276,9 +307,15 @@ size_t sncc_refine_workspace_bytes(int out_cap);
  *   tau                  exact threshold
  *   d_out, out_cap       matches sorted by v*U+u
  *   d_nout               int32, receives the exact match count (may exceed
- *                        out_cap: SNCC_STATUS_MATCH_OVERFLOW)
- *   d_ws, ws_bytes       workspace, >= sncc_refine_workspace_bytes(out_cap)
+ *                        out_cap: SNCC_STATUS_MATCH_OVERFLOW; then the
+ *                        out_cap matches that were stored are written, sorted)
+ *   d_ws, ws_bytes       workspace, >= sncc_refine_workspace_bytes(M, N, W, H,
+ *                        out_cap), 16-byte aligned
  *   d_status             int32 status word (not cleared: sncc_match clears it)
+ * The sort is a sorted compaction: one bit per offset, a prefix count of the
+ * set bits and a scatter, O(U*V/32 + matches) work; lists of at most 2048
+ * matches are ranked by direct comparison instead.  The candidates must be
+ * distinct offsets (as sncc_match writes them).
  */
 int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t* d_t, int W, int H, int t_stride,
                 int64_t T, int64_t T2, const int32_t* d_cand, const int32_t* d_count, int cand_cap, float tau,
@@ -304,7 +341,8 @@ int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t* d
  *   tau                     fine threshold
  *   d_out, out_cap, d_nout  matches sorted by v*U+u and their exact count
  *                           (SNCC_STATUS_MATCH_OVERFLOW beyond out_cap)
- *   d_ws, ws_bytes          workspace, >= sncc_refine_workspace_bytes(out_cap)
+ *   d_ws, ws_bytes          workspace, >= sncc_refine_workspace_bytes(M, N,
+ *                           seg->W, seg->H, out_cap), 16-byte aligned
  *   d_status                int32 status word (not cleared)
  */
 int sncc_refine_segmented(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits,
@@ -326,7 +364,8 @@ int sncc_refine_segmented(const sncc_segments* seg, const void* d_plan, const vo
  *   d_ws, ws_bytes          256-byte aligned workspace of at least
  *                           sncc_refine_segmented_tiles_workspace_bytes(M, N, W, H, out_cap)
  *                           (match records, one candidate bit per offset,
- *                           a flag and a list entry per tile)
+ *                           a flag and a list entry per tile, the sort
+ *                           scratch)
  * Errors as sncc_refine_segmented; SNCC_ERR_WORKSPACE for a missing, short or
  * misaligned workspace.
  */
@@ -356,7 +395,8 @@ typedef struct {
     int32_t* d_status[SNCC_MULTI_MAX];
     sncc_match_t* d_out[SNCC_MULTI_MAX]; /* out_cap matches each */
     int32_t* d_nout[SNCC_MULTI_MAX];
-    void* d_rws[SNCC_MULTI_MAX];         /* sncc_refine workspaces of rws_bytes */
+    void* d_rws[SNCC_MULTI_MAX];         /* sncc_refine workspaces of rws_bytes
+                                            (sncc_refine_workspace_bytes(M, N, W, H, out_cap)) */
     size_t rws_bytes;
 } sncc_pipeline_slot;
 
@@ -392,6 +432,8 @@ int sncc_pipeline_create(const sncc_segments* const* segs, const void* const* d_
  * pinned for an asynchronous copy) and returns the previous frame's results.
  * The frame is copied on the pipeline's copy stream once the frame that last
  * used the slot has finished with it, and matched on the compute stream.
+ * The call returns only after that copy has completed, so h_frame may be
+ * refilled as soon as it returns.
  * Then the call waits for the previous frame only, and writes its match
  * count into h_count[q] and its status word into h_status[q] (if h_status is
  * not NULL).  Its first min(count, out_cap) matches, sorted by v*U+u, go to
@@ -495,8 +537,10 @@ int sncc_batch_autotune(sncc_batch* b, const void* d_buf, const void* const* d_s
                         int s_bits, int sat_pitch, int32_t* d_cand, int cand_cap, int32_t* d_count,
                         int32_t* d_counter, int32_t* d_status, int reps, sncc_stream_t stream, float* ms_out);
 
-/* Scratch bytes sncc_batch_refine needs for out_cap matches. */
-size_t sncc_batch_refine_workspace_bytes(int out_cap);
+/* Scratch bytes sncc_batch_refine needs for out_cap matches of batch b: the
+ * unsorted records plus one bit per offset of every pair for the sorted
+ * write-out.  0 for a NULL batch or a negative out_cap. */
+size_t sncc_batch_refine_workspace_bytes(const sncc_batch* b, int out_cap);
 
 /*
  * sncc_batch_refine - exact NCC (Eq. 1) at every batch candidate; matches
@@ -504,7 +548,8 @@ size_t sncc_batch_refine_workspace_bytes(int out_cap);
  *   d_f[s], f_stride       device sources (uint8, M x N)
  *   d_cand, d_count, cand_cap  from sncc_batch_match
  *   d_out, out_cap, d_nout matches and their exact count
- *   d_ws, ws_bytes         workspace, >= sncc_batch_refine_workspace_bytes
+ *   d_ws, ws_bytes         workspace, >= sncc_batch_refine_workspace_bytes(b,
+ *                          out_cap), 16-byte aligned
  *   d_status               status word (not cleared)
  */
 int sncc_batch_refine(const sncc_batch* b, const void* d_buf, const uint8_t* const* d_f, int f_stride,

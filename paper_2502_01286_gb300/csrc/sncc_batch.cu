@@ -29,6 +29,7 @@
 
 #include "sncc.h"
 #include "sncc_internal.h"
+#include "sncc_sort.cuh"
 #include "sncc_tile.cuh"
 
 namespace sncc {
@@ -210,37 +211,16 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(const __grid_constant
     }
 }
 
-// out[rank] = in[i] with the key (pair, v*U+u); ranks by counting smaller keys.
-__global__ void __launch_bounds__(256) batch_sort_kernel(const sncc_batch_match_t* __restrict__ in,
-                                                         const int* __restrict__ nout, int cap,
-                                                         const int4* __restrict__ pairs,
-                                                         sncc_batch_match_t* __restrict__ out) {
-    constexpr int CH = 1024;
-    __shared__ long long keys[CH];
-    const int n = min(*nout, cap);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x * blockDim.x >= n) return;  // uniform per CTA
-    auto key_of = [&](const sncc_batch_match_t& m) -> long long {
-        return ((long long)m.pair << 32) | (unsigned)(m.v * pairs[m.pair].z + m.u);
-    };
-    const bool mine = i < n;
-    sncc_batch_match_t me;
-    long long key = 0;
-    if (mine) {
-        me = in[i];
-        key = key_of(me);
+// The sort key of a batch match: its offset in the concatenation of every
+// pair's offset space, pair-major (base[pair] + v*U + u), so that the sorted
+// list is ordered by (pair, v*U+u).
+struct BatchKey {
+    const int4* pairs;
+    const long long* base;
+    __device__ __forceinline__ long long operator()(const sncc_batch_match_t& m) const {
+        return base[m.pair] + (long long)m.v * pairs[m.pair].z + m.u;
     }
-    int rank = 0;
-    for (int c0 = 0; c0 < n; c0 += CH) {
-        const int len = min(CH, n - c0);
-        __syncthreads();
-        for (int j = threadIdx.x; j < len; j += blockDim.x) keys[j] = key_of(in[c0 + j]);
-        __syncthreads();
-        if (mine)
-            for (int j = 0; j < len; ++j) rank += (keys[j] < key) ? 1 : 0;
-    }
-    if (mine) out[rank] = me;
-}
+};
 
 size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
@@ -252,7 +232,7 @@ struct sncc_batch_s {
     std::vector<sncc::TmplDesc> tmpl;
     std::vector<int32_t> corner_counts;    // nonzero corners per template in the 64 x 64 layout (the work)
     std::vector<int32_t> template_corners;  // corners of each whole template (the algorithmic count)
-    size_t off_pairs = 0, off_tmpl = 0, off_blocks = 0, off_runblk = 0, off_runs = 0, off_pix = 0,
+    size_t off_pairs = 0, off_pbase = 0, off_tmpl = 0, off_blocks = 0, off_runblk = 0, off_runs = 0, off_pix = 0,
            off_items[3] = {0, 0, 0};
     int n_items[3] = {0, 0, 0};
     std::vector<unsigned char> image;
@@ -386,6 +366,12 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
                 b->offsets += (double)U * V;
             }
         const int npairs = n_templates * n_sources;
+        std::vector<long long> pbase(npairs);  // first sort key of each pair
+        long long key_end = 0;
+        for (int pi = 0; pi < npairs; ++pi) {
+            pbase[pi] = key_end;
+            key_end += (long long)pairs[4 * pi + 2] * pairs[4 * pi + 3];
+        }
         std::vector<int> order(npairs);
         for (int i = 0; i < npairs; ++i) order[i] = i;
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
@@ -407,6 +393,8 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
         size_t off = 0;
         b->off_pairs = off;
         off = align16(off + pairs.size() * 4);
+        b->off_pbase = off;
+        off = align16(off + pbase.size() * 8);
         b->off_tmpl = off;
         off = align16(off + b->tmpl.size() * sizeof(TmplDesc));
         b->off_blocks = off;
@@ -423,6 +411,7 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
         }
         b->image.assign(off, 0);
         std::memcpy(b->image.data() + b->off_pairs, pairs.data(), pairs.size() * 4);
+        std::memcpy(b->image.data() + b->off_pbase, pbase.data(), pbase.size() * 8);
         std::memcpy(b->image.data() + b->off_tmpl, b->tmpl.data(), b->tmpl.size() * sizeof(TmplDesc));
         std::memcpy(b->image.data() + b->off_blocks, blocks.data(), blocks.size() * 4);
         if (!runblk.empty()) std::memcpy(b->image.data() + b->off_runblk, runblk.data(), runblk.size() * 4);
@@ -561,9 +550,19 @@ extern "C" int sncc_batch_autotune(sncc_batch* b, const void* d_buf, const void*
     return rc;
 }
 
-extern "C" size_t sncc_batch_refine_workspace_bytes(int out_cap) {
-    if (out_cap <= 0) return 16;
-    return ((size_t)out_cap * sizeof(sncc_batch_match_t) + 15) / 16 * 16;
+namespace {
+// Match records (out_cap, padded to 256 bytes), then the sort scratch over
+// every pair's offsets.
+size_t batch_refine_ws(const sncc_batch* b, int out_cap, size_t* sort_offset) {
+    const size_t recs = ((size_t)(out_cap > 0 ? out_cap : 1) * sizeof(sncc_batch_match_t) + 255) / 256 * 256;
+    if (sort_offset) *sort_offset = recs;
+    return recs + sncc::sort_layout((long long)b->offsets).total;
+}
+}  // namespace
+
+extern "C" size_t sncc_batch_refine_workspace_bytes(const sncc_batch* b, int out_cap) {
+    if (!b || out_cap < 0) return 0;
+    return batch_refine_ws(b, out_cap, nullptr);
 }
 
 extern "C" int sncc_batch_refine(const sncc_batch* b, const void* d_buf, const uint8_t* const* d_f, int f_stride,
@@ -575,7 +574,7 @@ extern "C" int sncc_batch_refine(const sncc_batch* b, const void* d_buf, const u
     if (!b || !d_buf || !d_f || !d_count || !d_nout || !d_status || f_stride < b->M || cand_cap < 0 || out_cap < 0)
         return SNCC_ERR_ARG;
     if ((cand_cap > 0 && !d_cand) || (out_cap > 0 && !d_out)) return SNCC_ERR_ARG;
-    if (out_cap > 0 && (!d_ws || ws_bytes < sncc_batch_refine_workspace_bytes(out_cap) ||
+    if (out_cap > 0 && (!d_ws || ws_bytes < sncc_batch_refine_workspace_bytes(b, out_cap) ||
                         (reinterpret_cast<uintptr_t>(d_ws) & 15)))
         return SNCC_ERR_WORKSPACE;
     BatchRefineArgs a;
@@ -599,12 +598,17 @@ extern "C" int sncc_batch_refine(const sncc_batch* b, const void* d_buf, const u
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(d_nout, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
     if (cand_cap == 0) return SNCC_OK;
-    const int grid = cand_cap < 152 * 8 ? cand_cap : 152 * 8;
+    const int cap_ctas = 8 * (sm_count() > 0 ? sm_count() : 1);
+    const int grid = cand_cap < cap_ctas ? cand_cap : cap_ctas;
     batch_refine_kernel<<<grid, 256, 0, st>>>(a);
     if (cudaGetLastError() != cudaSuccess) return SNCC_ERR_CUDA;
     if (out_cap > 0) {
-        batch_sort_kernel<<<(out_cap + 255) / 256, 256, 0, st>>>(a.scratch, d_nout, out_cap, a.pairs, d_out);
-        if (cudaGetLastError() != cudaSuccess) return SNCC_ERR_CUDA;
+        size_t sort_off = 0;
+        batch_refine_ws(b, out_cap, &sort_off);
+        const BatchKey key{a.pairs, reinterpret_cast<const long long*>(base + b->off_pbase)};
+        if (launch_sorted_compaction(a.scratch, d_nout, out_cap, key, (long long)b->offsets,
+                                     static_cast<char*>(d_ws) + sort_off, d_out, cap_ctas, st) != cudaSuccess)
+            return SNCC_ERR_CUDA;
     }
     return SNCC_OK;
 }

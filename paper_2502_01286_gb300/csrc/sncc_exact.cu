@@ -182,9 +182,10 @@ extern "C" int sncc_exact_map(const uint8_t* d_f, int M, int N, int f_stride, co
     const double rn = 1.0 / (double)n;
     const float etn = (float)((double)(n * T2 - T * T) * rn);  // E_t
     const int tu = (U + TILE_U - 1) / TILE_U;
+    const int sms = sm_count() > 0 ? sm_count() : 1;
     int R = 2;
     for (int c : {8, 4}) {
-        if ((long long)tu * ((V + WARPS * c - 1) / (WARPS * c)) >= 2 * 152) { R = c; break; }
+        if ((long long)tu * ((V + WARPS * c - 1) / (WARPS * c)) >= 2 * sms) { R = c; break; }
     }
     dim3 grid(tu, (V + WARPS * R - 1) / (WARPS * R));
     cudaStream_t st = (cudaStream_t)stream;

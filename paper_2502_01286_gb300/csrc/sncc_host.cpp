@@ -6,6 +6,7 @@
 // but the statistics of each candidate rectangle come from exact integer sum
 // tables of the template instead of per-pixel loops.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -312,6 +313,21 @@ int build_plan(const sncc_segments* s, Plan& p) {
 
 Plan* plan_of(const sncc_segments* s) { return s ? static_cast<Plan*>(s->plan) : nullptr; }
 
+int sm_count() {
+    constexpr int kMaxDevices = 128;
+    static std::atomic<int> cached[kMaxDevices];  // 0 = not yet queried
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+    if (dev < kMaxDevices) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 0;
+    if (dev < kMaxDevices) cached[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 const char* error_string(int code) {
     switch (code) {
         case SNCC_OK: return "ok";
@@ -325,6 +341,13 @@ const char* error_string(int code) {
         case SNCC_ERR_UNSUPPORTED: return "size not supported";
         default: return "unknown error";
     }
+}
+
+// The population std of a template from its exact sums (the Eq. 2 std taken
+// over the whole template): sqrt(n T2 - T^2) / n, the radicand exact in int64.
+double template_sigma(int64_t n, int64_t T, int64_t T2) {
+    const int64_t var_n2 = n * T2 - T * T;
+    return var_n2 > 0 ? std::sqrt((double)var_n2) / (double)n : 0.0;
 }
 
 }  // namespace sncc
@@ -374,6 +397,7 @@ int sncc_build_segments(const uint8_t* t, int W, int H, int t_stride, double sig
         out->sigma_used = used;
         out->T = T;
         out->T2 = T2;
+        out->sigma_t = template_sigma(n, T, T2);
         // Eq. 7: sum_i n_i k_i = sum_i (segment sum) = T, so kbar = T / n.
         out->kbar = (double)T / (double)n;
         out->seg = static_cast<sncc_seg*>(std::malloc(sizeof(sncc_seg) * (k.size() ? k.size() : 1)));
@@ -409,6 +433,20 @@ int sncc_build_segments(const uint8_t* t, int W, int H, int t_stride, double sig
         sncc_free_segments(out);
         return SNCC_ERR_NOMEM;
     }
+    return SNCC_OK;
+}
+
+int sncc_template_sigma(const uint8_t* t, int W, int H, int t_stride, double* sigma_t) {
+    if (!t || !sigma_t || W <= 0 || H <= 0 || t_stride < W) return SNCC_ERR_ARG;
+    if ((int64_t)W * H > ((int64_t)1 << 23)) return SNCC_ERR_UNSUPPORTED;
+    int64_t T = 0, T2 = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int64_t v = t[(size_t)y * t_stride + x];
+            T += v;
+            T2 += v * v;
+        }
+    *sigma_t = sncc::template_sigma((int64_t)W * H, T, T2);
     return SNCC_OK;
 }
 

@@ -116,11 +116,26 @@ int build_plan(const sncc_segments* seg, Plan& p);
 inline const Layout& layout_for(const Plan& p) { return (p.lay[0].nbx * p.lay[0].nby > 1) ? p.lay[1] : p.lay[0]; }
 
 // Writes the first min(*d_n, cap) records of `in` to `out` in ascending
-// v*U+u order (keys are distinct).  Defined in sncc_refine.cu.
-cudaError_t launch_rank_sort(const sncc_match_t* in, const int32_t* d_n, int cap, int U, sncc_match_t* out,
-                             cudaStream_t st);
+// v*U+u order (keys are distinct), with match_sort_bytes(U, V) bytes of
+// scratch at sort_ws (16-byte aligned).  Defined in sncc_refine.cu.
+size_t match_sort_bytes(int U, int V);
+cudaError_t launch_match_sort(const sncc_match_t* in, const int32_t* d_n, int cap, int U, int V, void* sort_ws,
+                              sncc_match_t* out, cudaStream_t st);
+
+// Workspace of sncc_refine and sncc_refine_segmented: out_cap match records
+// (padded to 256 bytes), then the sort scratch at *sort_offset.
+size_t refine_workspace_bytes(int M, int N, int W, int H, int out_cap, size_t* sort_offset);
 
 // Status helpers.
 const char* error_string(int code);
+
+// Streaming multiprocessors of the current device, queried once per device
+// (grid sizes and tile heights are chosen against it); 0 if the query fails.
+int sm_count();
+
+// Whether sncc_match_multi can fuse these n approximations into one launch,
+// decided on the host alone: SNCC_OK, SNCC_ERR_UNSUPPORTED (not fusable),
+// SNCC_ERR_UNIFORM (some Ek = 0) or SNCC_ERR_ARG.  Defined in sncc_match.cu.
+int multi_fusable(const sncc_segments* const* segs, const void* const* d_plans, int n);
 
 }  // namespace sncc

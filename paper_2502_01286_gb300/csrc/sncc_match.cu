@@ -382,9 +382,10 @@ cudaError_t launch_layout(const Layout& L, bool s64, int R, const CUtensorMap& m
 // per SM.
 int choose_r(int U, int V) {
     const int tu = (U + TILE_U - 1) / TILE_U;
+    const int sms = sm_count() > 0 ? sm_count() : 1;
     for (int R : {8, 4}) {
         const long long ctas = (long long)tu * ((V + WARPS * R - 1) / (WARPS * R));
-        if (ctas >= 2 * 152) return R;
+        if (ctas >= 2 * sms) return R;
     }
     return 2;
 }
@@ -453,9 +454,9 @@ int prepare_match(const sncc_segments* seg, const void* d_plan, const void* d_s,
 
 // Workspace of sncc_refine_segmented_tiles, in order: match records
 // (out_cap, 16-byte aligned), candidate bits (one per offset), tile flags,
-// tile list, tile count.
+// tile list, tile count, the sort scratch.
 struct TilesLayout {
-    size_t recs, bits, flags, list, count, total;
+    size_t recs, bits, flags, list, count, sort, total;
     int ntiles, rows;
 };
 
@@ -477,11 +478,35 @@ TilesLayout tiles_layout(int M, int N, int W, int H, int out_cap) {
     o = al(o + (size_t)t.ntiles * 4);
     t.count = o;
     o = al(o + 16);
+    t.sort = o;
+    o = al(o + match_sort_bytes(U, V));
     t.total = o;
     return t;
 }
 
 }  // namespace
+
+int multi_fusable(const sncc_segments* const* segs, const void* const* d_plans, int n) {
+    if (!segs || !d_plans || n < 1 || n > SNCC_MULTI_MAX) return SNCC_ERR_ARG;
+    // every approximation: the same template size and a plan
+    for (int q = 0; q < n; ++q) {
+        if (!segs[q] || !plan_of(segs[q]) || !d_plans[q] || (reinterpret_cast<uintptr_t>(d_plans[q]) & 15))
+            return SNCC_ERR_ARG;
+        if (segs[q]->W != segs[0]->W || segs[q]->H != segs[0]->H) return SNCC_ERR_ARG;
+        if (!(segs[q]->Ek > 0.0) || plan_of(segs[q])->image.empty()) return SNCC_ERR_UNIFORM;
+    }
+    // and one staged block of the same layout each (templates up to 64 x 64
+    // that are not summed directly)
+    const Layout& L0 = layout_for(*plan_of(segs[0]));
+    for (int q = 0; q < n; ++q) {
+        const Plan* p = plan_of(segs[q]);
+        const Layout& Lq = layout_for(*p);
+        if (Lq.nblk != 1 || Lq.nbx * Lq.nby != 1 || Lq.WP != L0.WP || Lq.BH != L0.BH || p->direct_count > 0)
+            return SNCC_ERR_UNSUPPORTED;
+    }
+    return SNCC_OK;
+}
+
 }  // namespace sncc
 
 extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const void* d_s, int s_bits,
@@ -542,7 +567,8 @@ extern "C" int sncc_refine_segmented_tiles(const sncc_segments* seg, const void*
     if (cudaMemsetAsync(ws + t.bits, 0, t.list - t.bits, st) != cudaSuccess) return SNCC_ERR_CUDA;  // bits, flags
     if (cudaMemsetAsync(tcount, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
     if (cand_cap == 0) return SNCC_OK;
-    mark_candidate_tiles<<<2 * 152, 256, 0, st>>>(d_cand, d_count, cand_cap, a.U, a.V, a.tiles_u, t.rows, bits, flags);
+    const int sms = sm_count() > 0 ? sm_count() : 1;
+    mark_candidate_tiles<<<2 * sms, 256, 0, st>>>(d_cand, d_count, cand_cap, a.U, a.V, a.tiles_u, t.rows, bits, flags);
     list_tiles<<<(t.ntiles + 255) / 256, 256, 0, st>>>(flags, t.ntiles, list, tcount);
     if (cudaGetLastError() != cudaSuccess) return SNCC_ERR_CUDA;
     a.tile_list = list;
@@ -553,7 +579,8 @@ extern "C" int sncc_refine_segmented_tiles(const sncc_segments* seg, const void*
     a.nout = d_nout;
     a.status = d_status;
     if (launch_layout<true>(*L, s_bits == 64, R, map, a, st) != cudaSuccess) return SNCC_ERR_CUDA;
-    if (launch_rank_sort(recs, d_nout, out_cap, a.U, d_out, st) != cudaSuccess) return SNCC_ERR_CUDA;
+    if (out_cap > 0 && launch_match_sort(recs, d_nout, out_cap, a.U, a.V, ws + t.sort, d_out, st) != cudaSuccess)
+        return SNCC_ERR_CUDA;
     return SNCC_OK;
 }
 
@@ -565,23 +592,10 @@ extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* co
     using namespace sncc;
     if (!segs || !d_plans || !taus || !d_cand || !d_count || !d_status || n < 1 || n > SNCC_MULTI_MAX || cand_cap < 0)
         return SNCC_ERR_ARG;
-    // every approximation: the same template size, its own outputs
-    for (int q = 0; q < n; ++q) {
-        if (!segs[q] || !plan_of(segs[q]) || !d_plans[q] || (reinterpret_cast<uintptr_t>(d_plans[q]) & 15))
-            return SNCC_ERR_ARG;
-        if (segs[q]->W != segs[0]->W || segs[q]->H != segs[0]->H) return SNCC_ERR_ARG;
+    for (int q = 0; q < n; ++q)  // every approximation has its own outputs
         if ((cand_cap > 0 && !d_cand[q]) || !d_count[q] || !d_status[q]) return SNCC_ERR_ARG;
-        if (!(segs[q]->Ek > 0.0) || plan_of(segs[q])->image.empty()) return SNCC_ERR_UNIFORM;
-    }
-    // and one staged block of the same layout each (templates up to 64 x 64
-    // that are not summed directly); decided on the host before any CUDA call
-    const Layout& L0 = layout_for(*plan_of(segs[0]));
-    for (int q = 0; q < n; ++q) {
-        const Plan* p = plan_of(segs[q]);
-        const Layout& Lq = layout_for(*p);
-        if (Lq.nblk != 1 || Lq.nbx * Lq.nby != 1 || Lq.WP != L0.WP || Lq.BH != L0.BH || p->direct_count > 0)
-            return SNCC_ERR_UNSUPPORTED;
-    }
+    const int fz = multi_fusable(segs, d_plans, n);  // decided on the host before any CUDA call
+    if (fz != SNCC_OK) return fz;
     MatchArgs a;
     CUtensorMap map;
     int R = 0;

@@ -8,7 +8,8 @@
 // launch where sncc_match_multi accepts them - and the exact refines) is
 // captured once into a CUDA graph.  Per frame, one call:
 //   - copies the frame host -> device on a copy stream, after the frame that
-//     last used the slot has finished with it;
+//     last used the slot has finished with it, and returns only once that
+//     copy is complete (the caller may then refill its host buffer);
 //   - launches the slot's graph on the compute stream once the copy is done;
 //   - waits on a read-back stream for the previous frame only and copies its
 //     match counts, records and status words to the caller's host memory.
@@ -173,13 +174,10 @@ extern "C" int sncc_pipeline_create(const sncc_segments* const* segs, const void
             release(p);
             return SNCC_ERR_CUDA;
         }
-    // fuse the coarse passes if the library accepts the approximations (it
-    // decides on the host, before any CUDA call)
+    // fuse the coarse passes if the library accepts the approximations (a
+    // host-only decision; nothing is launched)
     if (n > 1) {
-        const sncc_pipeline_slot& b = p->slot[0];
-        const int rc = sncc_match_multi(p->segs, p->plans, n, b.d_s, s_bits, b.d_s2, sat_pitch, M, N, p->taus,
-                                        b.d_rho[0] ? b.d_rho : nullptr, rho_pitch, b.d_cand, cand_cap, b.d_count,
-                                        b.d_status, (sncc_stream_t)p->compute);
+        const int rc = sncc::multi_fusable(p->segs, p->plans, n);
         if (rc != SNCC_OK && rc != SNCC_ERR_UNSUPPORTED) {
             release(p);
             return rc;
@@ -228,6 +226,9 @@ extern "C" int sncc_pipeline_submit(sncc_pipeline p, const uint8_t* h_frame, snc
         cudaGraphLaunch(p->exec[k], p->compute) != cudaSuccess || cudaEventRecord(p->done[k], p->compute) != cudaSuccess)
         return SNCC_ERR_CUDA;
     p->used[k] = true;
+    // the caller may refill h_frame once this returns: wait for its copy
+    // (it overlaps the previous frame's matching, which is waited for next)
+    if (cudaEventSynchronize(p->copied[k]) != cudaSuccess) return SNCC_ERR_CUDA;
     const bool prev = p->frames > 0;
     ++p->frames;
     return prev ? collect(p, k ^ 1, h_out, h_count, h_status) : 0;

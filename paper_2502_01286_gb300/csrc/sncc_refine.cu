@@ -6,8 +6,9 @@
 // synchronisation is needed): the CTA sums f*t, f and f^2 over the window in
 // exact 64-bit integers, then thread 0 forms
 //   rho = (n Sft - T Sf) / sqrt((n Sff - Sf^2)(n T2 - T^2))
-// in double and appends (u, v, rho) when rho >= tau.  A rank sort then
-// writes the matches in ascending v*U+u order, so the output is deterministic
+// in double and appends (u, v, rho) when rho >= tau.  A sorted compaction
+// (one bit per offset, a prefix count, a scatter: sncc_sort.cuh) then writes
+// the matches in ascending v*U+u order, so the output is deterministic
 // although candidates arrive in atomic order.
 #include <cuda_runtime.h>
 
@@ -15,13 +16,12 @@
 
 #include "sncc.h"
 #include "sncc_internal.h"
+#include "sncc_sort.cuh"
 
 namespace sncc {
 namespace {
 
 constexpr int kRefineThreads = 256;
-constexpr int kSortThreads = 256;
-constexpr int kSortChunk = 2048;
 
 __device__ __forceinline__ long long warp_sum(long long v) {
 #pragma unroll
@@ -91,49 +91,33 @@ __global__ void __launch_bounds__(kRefineThreads)
     }
 }
 
-// out[rank(i)] = in[i], rank = number of stored matches with a smaller key
-// (keys v*U+u are distinct).
-__global__ void __launch_bounds__(kSortThreads)
-    rank_sort_kernel(const sncc_match_t* __restrict__ in, const int32_t* __restrict__ d_nout, int cap, int U,
-                     sncc_match_t* __restrict__ out) {
-    __shared__ int keys[kSortChunk];
-    const int n = min(*d_nout, cap);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x * blockDim.x >= n) return;  // uniform per CTA
-    const bool mine = i < n;
-    sncc_match_t me;
-    int key = 0;
-    if (mine) {
-        me = in[i];
-        key = me.v * U + me.u;
-    }
-    int rank = 0;
-    for (int c0 = 0; c0 < n; c0 += kSortChunk) {
-        const int len = min(kSortChunk, n - c0);
-        __syncthreads();
-        for (int j = threadIdx.x; j < len; j += blockDim.x) keys[j] = in[c0 + j].v * U + in[c0 + j].u;
-        __syncthreads();
-        if (mine)
-            for (int j = 0; j < len; ++j) rank += (keys[j] < key) ? 1 : 0;
-    }
-    if (mine) out[rank] = me;
-}
+// The sort key of a match: its linear offset v*U + u.
+struct MatchKey {
+    int U;
+    __device__ __forceinline__ long long operator()(const sncc_match_t& m) const { return (long long)m.v * U + m.u; }
+};
 
 }  // namespace
 
-cudaError_t launch_rank_sort(const sncc_match_t* in, const int32_t* d_n, int cap, int U, sncc_match_t* out,
-                             cudaStream_t st) {
-    if (cap <= 0) return cudaSuccess;
-    const int sgrid = (cap + kSortThreads - 1) / kSortThreads;
-    rank_sort_kernel<<<sgrid, kSortThreads, 0, st>>>(in, d_n, cap, U, out);
-    return cudaGetLastError();
+size_t match_sort_bytes(int U, int V) { return sort_layout((long long)U * V).total; }
+
+cudaError_t launch_match_sort(const sncc_match_t* in, const int32_t* d_n, int cap, int U, int V, void* sort_ws,
+                              sncc_match_t* out, cudaStream_t st) {
+    const int ctas = 8 * (sm_count() > 0 ? sm_count() : 1);
+    return launch_sorted_compaction(in, d_n, cap, MatchKey{U}, (long long)U * V, sort_ws, out, ctas, st);
+}
+
+size_t refine_workspace_bytes(int M, int N, int W, int H, int out_cap, size_t* sort_offset) {
+    const size_t recs = ((size_t)(out_cap > 0 ? out_cap : 1) * sizeof(sncc_match_t) + 255) / 256 * 256;
+    if (sort_offset) *sort_offset = recs;
+    return recs + match_sort_bytes(M - W + 1, N - H + 1);
 }
 
 }  // namespace sncc
 
-extern "C" size_t sncc_refine_workspace_bytes(int out_cap) {
-    if (out_cap <= 0) return 16;
-    return ((size_t)out_cap * sizeof(sncc_match_t) + 15) / 16 * 16;
+extern "C" size_t sncc_refine_workspace_bytes(int M, int N, int W, int H, int out_cap) {
+    if (M <= 0 || N <= 0 || W <= 0 || H <= 0 || W > M || H > N || out_cap < 0) return 0;
+    return sncc::refine_workspace_bytes(M, N, W, H, out_cap, nullptr);
 }
 
 extern "C" int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t* d_t, int W, int H,
@@ -146,7 +130,7 @@ extern "C" int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const
     if (f_stride < M || t_stride < W || M < W || N < H || cand_cap < 0 || out_cap < 0) return SNCC_ERR_ARG;
     if ((cand_cap > 0 && !d_cand) || (out_cap > 0 && !d_out)) return SNCC_ERR_ARG;
     if ((int64_t)W * H > ((int64_t)1 << 23)) return SNCC_ERR_UNSUPPORTED;
-    if (out_cap > 0 && (!d_ws || ws_bytes < sncc_refine_workspace_bytes(out_cap) ||
+    if (out_cap > 0 && (!d_ws || ws_bytes < sncc_refine_workspace_bytes(M, N, W, H, out_cap) ||
                         (reinterpret_cast<uintptr_t>(d_ws) & 15)))
         return SNCC_ERR_WORKSPACE;
     const int U = M - W + 1, V = N - H + 1;
@@ -155,11 +139,18 @@ extern "C" int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const
     if (cudaMemsetAsync(d_nout, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
     if (cand_cap == 0) return SNCC_OK;
     sncc_match_t* scratch = static_cast<sncc_match_t*>(d_ws);
-    int grid = cand_cap < 152 * 8 ? cand_cap : 152 * 8;
+    const int cap_ctas = 8 * (sm_count() > 0 ? sm_count() : 1);
+    const int grid = cand_cap < cap_ctas ? cand_cap : cap_ctas;
     refine_kernel<<<grid, kRefineThreads, 0, st>>>(d_f, f_stride, d_t, W, H, t_stride, (long long)T, (long long)T2,
                                                    d_cand, d_count, cand_cap, tau, U, V, scratch, out_cap, d_nout,
                                                    d_status);
     if (cudaGetLastError() != cudaSuccess) return SNCC_ERR_CUDA;
-    if (launch_rank_sort(scratch, d_nout, out_cap, U, d_out, st) != cudaSuccess) return SNCC_ERR_CUDA;
+    if (out_cap > 0) {
+        size_t sort_off = 0;
+        refine_workspace_bytes(M, N, W, H, out_cap, &sort_off);
+        if (launch_match_sort(scratch, d_nout, out_cap, U, V, static_cast<char*>(d_ws) + sort_off, d_out, st) !=
+            cudaSuccess)
+            return SNCC_ERR_CUDA;
+    }
     return SNCC_OK;
 }

@@ -123,7 +123,7 @@ extern "C" int sncc_refine_segmented(const sncc_segments* seg, const void* d_pla
     if (s_bits == 32 && (int64_t)255 * M * N >= ((int64_t)1 << 31)) return SNCC_ERR_DTYPE;
     if ((int64_t)U * V >= ((int64_t)1 << 31)) return SNCC_ERR_UNSUPPORTED;
     if (reinterpret_cast<uintptr_t>(d_plan) & 15) return SNCC_ERR_ARG;
-    if (out_cap > 0 && (!d_ws || ws_bytes < sncc_refine_workspace_bytes(out_cap) ||
+    if (out_cap > 0 && (!d_ws || ws_bytes < sncc_refine_workspace_bytes(M, N, W, H, out_cap) ||
                         (reinterpret_cast<uintptr_t>(d_ws) & 15)))
         return SNCC_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
@@ -158,12 +158,19 @@ extern "C" int sncc_refine_segmented(const sncc_segments* seg, const void* d_pla
     a.nout = d_nout;
     a.status = d_status;
     const int want = (cand_cap + kWarpsPerCta - 1) / kWarpsPerCta;
-    const int grid = want < 152 * 16 ? want : 152 * 16;
+    const int cap_ctas = 16 * (sm_count() > 0 ? sm_count() : 1);
+    const int grid = want < cap_ctas ? want : cap_ctas;
     if (s_bits == 64)
         refine_seg_kernel<true><<<grid, kWarpsPerCta * 32, 0, st>>>(a);
     else
         refine_seg_kernel<false><<<grid, kWarpsPerCta * 32, 0, st>>>(a);
     if (cudaGetLastError() != cudaSuccess) return SNCC_ERR_CUDA;
-    if (launch_rank_sort(a.scratch, d_nout, out_cap, U, d_out, st) != cudaSuccess) return SNCC_ERR_CUDA;
+    if (out_cap > 0) {
+        size_t sort_off = 0;
+        refine_workspace_bytes(M, N, W, H, out_cap, &sort_off);
+        if (launch_match_sort(a.scratch, d_nout, out_cap, U, V, static_cast<char*>(d_ws) + sort_off, d_out, st) !=
+            cudaSuccess)
+            return SNCC_ERR_CUDA;
+    }
     return SNCC_OK;
 }

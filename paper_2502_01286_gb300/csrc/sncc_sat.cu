@@ -22,6 +22,9 @@
 // carries are small arrays.
 #include <cuda_runtime.h>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
@@ -480,21 +483,56 @@ static __device__ __align__(256) int32_t sncc_noalloc_scratch[SNCC_NOALLOC_SCRAT
 namespace {
 
 constexpr int kNoallocMaxDevices = 128;
+struct NoallocEntry {
+    unsigned long long ctx_id;  // context the address was taken in (0 = none yet)
+    void* addr;
+};
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kNoallocMaxDevices] = {};
+NoallocEntry g_noalloc[kNoallocMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the array's name as a device pointer).
+// Unique identity of the calling thread's current context, 0 if unknown.
+// A device reset, or a primary context released and retained again, gives a
+// new identity, and the module (with its arrays) may then sit elsewhere.
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || c == nullptr || get_id(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device (host code
+// cannot use the array's name as a device pointer).  Looked up once per
+// device and context: a call in a context other than the one the cached
+// address was taken in looks it up again; if the context cannot be
+// identified, it is looked up on every call.
 int noalloc_scratch_address(void** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return SNCC_ERR_CUDA;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_addr[dev] == nullptr) {
+    NoallocEntry& e = g_noalloc[dev];
+    if (ctx == 0 || e.ctx_id != ctx || e.addr == nullptr) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, sncc_noalloc_scratch) != cudaSuccess || p == nullptr) return SNCC_ERR_CUDA;
-        g_noalloc_addr[dev] = p;
+        e.ctx_id = ctx;
+        e.addr = p;
     }
-    *out = g_noalloc_addr[dev];
+    *out = e.addr;
     return SNCC_OK;
 }
 

@@ -30,7 +30,8 @@ ERR_ARG, ERR_UNIFORM, ERR_DTYPE, ERR_CAPACITY, ERR_CUDA, ERR_WORKSPACE, ERR_NOME
     -1, -2, -3, -4, -5, -6, -7, -8
 STATUS_CAND_OVERFLOW, STATUS_MATCH_OVERFLOW, STATUS_WAIT_TIMEOUT, STATUS_SORT_OVERFLOW = 1, 2, 4, 8
 
-EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_sat_pitch",
+EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_free_segments", "sncc_template_sigma",
+            "sncc_sat_pitch",
             "sncc_integral_workspace_bytes", "sncc_integral", "sncc_plan_bytes", "sncc_plan_upload", "sncc_match",
             "sncc_match_multi", "sncc_pipeline_create", "sncc_pipeline_submit", "sncc_pipeline_flush",
             "sncc_pipeline_fused", "sncc_pipeline_compute_stream", "sncc_pipeline_destroy",
@@ -58,7 +59,7 @@ class _Segments(C.Structure):
     _fields_ = [("seg", C.POINTER(_Seg)), ("K", C.c_int32), ("K_split", C.c_int32), ("W", C.c_int32),
                 ("H", C.c_int32), ("sigma_used", C.c_double), ("kbar", C.c_double), ("Ek", C.c_double),
                 ("rho_max", C.c_double), ("T", C.c_int64), ("T2", C.c_int64), ("err_bound", C.c_double),
-                ("plan", C.c_void_p)]
+                ("plan", C.c_void_p), ("sigma_t", C.c_double)]
 
 
 class PlanInfo(C.Structure):
@@ -78,6 +79,7 @@ _lib.sncc_error_string.argtypes = [C.c_int]
 _lib.sncc_version.restype = C.c_char_p
 _lib.sncc_build_segments.argtypes = [_vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(_Segments)]
 _lib.sncc_free_segments.argtypes = [C.POINTER(_Segments)]
+_lib.sncc_template_sigma.argtypes = [_vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
 _lib.sncc_free_segments.restype = None
 _lib.sncc_sat_pitch.argtypes = [C.c_int]
 _lib.sncc_integral_workspace_bytes.argtypes = [C.c_int, C.c_int]
@@ -110,7 +112,7 @@ _lib.sncc_pipeline_compute_stream.argtypes = [_vp]
 _lib.sncc_pipeline_compute_stream.restype = _vp
 _lib.sncc_pipeline_destroy.argtypes = [_vp]
 _lib.sncc_pipeline_destroy.restype = None
-_lib.sncc_refine_workspace_bytes.argtypes = [C.c_int]
+_lib.sncc_refine_workspace_bytes.argtypes = [C.c_int] * 5
 _lib.sncc_refine_workspace_bytes.restype = C.c_size_t
 _lib.sncc_refine.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64,
                              _vp, _vp, C.c_int, C.c_float, _vp, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp]
@@ -137,7 +139,7 @@ _lib.sncc_batch_get_info.argtypes = [_vp, C.POINTER(BatchInfo)]
 _lib.sncc_batch_match.argtypes = [_vp, _vp, _pp, _pp, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp, _vp, _vp]
 _lib.sncc_batch_autotune.argtypes = [_vp, _vp, _pp, _pp, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp, _vp, C.c_int,
                                      _vp, C.POINTER(C.c_float)]
-_lib.sncc_batch_refine_workspace_bytes.argtypes = [C.c_int]
+_lib.sncc_batch_refine_workspace_bytes.argtypes = [_vp, C.c_int]
 _lib.sncc_batch_refine_workspace_bytes.restype = C.c_size_t
 _lib.sncc_batch_refine.argtypes = [_vp, _vp, _pp, C.c_int, _vp, _vp, C.c_int, _vp, C.c_int, _vp, _vp, C.c_size_t,
                                    _vp, _vp]
@@ -204,6 +206,7 @@ class Segments:
     T = property(lambda self: int(self._s.T))
     T2 = property(lambda self: int(self._s.T2))
     err_bound = property(lambda self: float(self._s.err_bound))
+    sigma_t = property(lambda self: float(self._s.sigma_t))
 
     @property
     def table(self) -> np.ndarray:
@@ -288,6 +291,9 @@ def integral_workspace(M: int, N: int, device="cuda"):
 # kernels one sncc_integral call launches: column sums of bands, band scan,
 # band emit
 INTEGRAL_KERNELS = 3
+# kernels one sncc_refine launches: the exact NCC at the candidates, then the
+# sorted write-out (mark or rank, scan, scatter)
+REFINE_KERNELS = 4
 
 
 def integral(f, tables: Optional[Tables] = None, s_bits: Optional[int] = None, workspace=None, stream=None) -> Tables:
@@ -389,12 +395,17 @@ class RefineBuffers:
     cap: int
 
 
-def alloc_refine(out_cap: int, device="cuda") -> RefineBuffers:
+def alloc_refine(M: int, N: int, W: int, H: int, out_cap: int, device="cuda") -> RefineBuffers:
+    """Match records and workspace of sncc_refine / sncc_refine_segmented for
+    an M x N source and a W x H template (the workspace holds the records
+    before sorting and one bit per offset for the sort)."""
     torch = _torch()
+    nbytes = int(_lib.sncc_refine_workspace_bytes(M, N, W, H, out_cap))
+    if nbytes == 0:
+        raise SnccError(ERR_ARG, "sncc_refine_workspace_bytes")
     return RefineBuffers(out=torch.empty((max(out_cap, 1), 3), dtype=torch.int32, device=device),
                          nout=torch.zeros(1, dtype=torch.int32, device=device),
-                         ws=torch.empty(int(_lib.sncc_refine_workspace_bytes(out_cap)), dtype=torch.uint8,
-                                        device=device),
+                         ws=torch.empty(nbytes, dtype=torch.uint8, device=device),
                          cap=out_cap)
 
 
@@ -496,8 +507,15 @@ def probe_alu(kind: int, sink, ctas: int, iters: int, stream=None) -> int:
 # The whole path, as a user calls it
 # ---------------------------------------------------------------------------
 def template_sigma(t: np.ndarray) -> float:
-    """sigma_t of the paper's thresholds: the population std of the template."""
-    return float(np.asarray(t, np.float64).std())
+    """sigma_t of the paper's thresholds: the population std of the template
+    (sncc_template_sigma, from its exact integer sums)."""
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.uint8))
+    if t.ndim != 2:
+        raise ValueError("template must be 2-D (H, W)")
+    H, W = t.shape
+    out = C.c_double()
+    _check(_lib.sncc_template_sigma(t.ctypes.data, W, H, W, C.byref(out)), "sncc_template_sigma")
+    return float(out.value)
 
 
 class PaperMatcher:
@@ -524,7 +542,7 @@ class PaperMatcher:
         self.tables = alloc_tables(M, N, None, device)
         self.ws = integral_workspace(M, N, device)
         self.mb = alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device)
-        self.rb = alloc_refine(out_cap, device)
+        self.rb = alloc_refine(M, N, self.W, self.H, out_cap, device)
         self.tws = tiles_workspace(M, N, self.W, self.H, out_cap, device)
 
     def run(self, f, stream=None):
@@ -579,7 +597,7 @@ class Matcher:
         self.tables = alloc_tables(M, N, None, device)
         self.ws = integral_workspace(M, N, device)
         self.mb = alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device)
-        self.rb = alloc_refine(out_cap, device)
+        self.rb = alloc_refine(M, N, self.W, self.H, out_cap, device)
 
     def run(self, f, stream=None):
         """Launch the whole path on a (N, M) uint8 CUDA tensor (asynchronous)."""
@@ -621,7 +639,7 @@ class MultiMatcher:
         self.tables = alloc_tables(M, N, None, device)
         self.ws = integral_workspace(M, N, device)
         self.mbs = [alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device) for _ in self.segs]
-        self.rbs = [alloc_refine(out_cap, device) for _ in self.segs]
+        self.rbs = [alloc_refine(M, N, self.W, self.H, out_cap, device) for _ in self.segs]
         self.fused = None if len(self.segs) > 1 and MULTI_MAX >= len(self.segs) else False
         # the refines of the approximations are independent: all but the
         # first run on side streams (parallel branches of a captured graph)
@@ -700,7 +718,7 @@ class StreamMatcher:
             tables = alloc_tables(M, N, None, device)
             ws = integral_workspace(M, N, device)
             mbs = [alloc_match(M, N, W, H, cand_cap, keep_rho, device) for _ in self.segs]
-            rbs = [alloc_refine(out_cap, device) for _ in self.segs]
+            rbs = [alloc_refine(M, N, W, H, out_cap, device) for _ in self.segs]
             sl = slots[k]
             sl.d_frame, sl.d_s, sl.d_s2 = frame.data_ptr(), tables.s.data_ptr(), tables.s2.data_ptr()
             sl.d_ws, sl.ws_bytes = ws.data_ptr(), ws.numel()
@@ -823,7 +841,7 @@ class Batch:
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         self.out = torch.empty((max(out_cap, 1), 4), dtype=torch.int32, device=device)
         self.nout = torch.zeros(1, dtype=torch.int32, device=device)
-        self.rws = torch.empty(int(_lib.sncc_batch_refine_workspace_bytes(out_cap)), dtype=torch.uint8,
+        self.rws = torch.empty(int(_lib.sncc_batch_refine_workspace_bytes(h, out_cap)), dtype=torch.uint8,
                                device=device)
         self._s = (C.c_void_p * n_sources)(*[tb.s.data_ptr() for tb in self.tables])
         self._s2 = (C.c_void_p * n_sources)(*[tb.s2.data_ptr() for tb in self.tables])

@@ -12,6 +12,29 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
 
 
+# Offsets whose FP64 oracle value lies within the parity tolerance of a
+# threshold, where the FP32 decision may legitimately go either way (the
+# reading of bit-exact candidate sets): every candidate-set check records its
+# count here, and the session summary reports them.
+G13_BAND_COUNTS = []
+
+
+def record_band_count(what: str, band: int, checked: int) -> None:
+    G13_BAND_COUNTS.append((what, int(band), int(checked)))
+
+
+def pytest_terminal_summary(terminalreporter):
+    if not G13_BAND_COUNTS:
+        return
+    tot = sum(b for _, b, _ in G13_BAND_COUNTS)
+    n = sum(c for _, _, c in G13_BAND_COUNTS)
+    terminalreporter.write_line("G13 band offsets (decision may go either way): %d of %d offsets checked in %d sets"
+                                % (tot, n, len(G13_BAND_COUNTS)))
+    for what, b, c in G13_BAND_COUNTS:
+        if b:
+            terminalreporter.write_line("  %s: %d of %d" % (what, b, c))
+
+
 def load_golden(name):
     """Parse a hand-derived fixture from tests/golden (format in its README)."""
     path = os.path.join(ROOT, "tests", "golden", name)

@@ -106,6 +106,19 @@ def test_uniform_template_has_zero_energy(sncc):
     assert sncc.lib().sncc_plan_upload(seg.ref(), C.c_void_p(16), 0, None) == sncc.ERR_UNIFORM
 
 
+@pytest.mark.parametrize("shape,seed", [((32, 32), 1), ((256, 256), 2), ((7, 3), 3), ((1, 1), 4), ((48, 17), 5)])
+def test_template_sigma_is_population_std(sncc, shape, seed):
+    """sigma_t (Section 5's input to sigma_max,fast and sigma_max,slow) from
+    the library, both through sncc_template_sigma and in sncc_segments,
+    against numpy's population std of the pixels."""
+    t = synth.random_image(seed, shape[1], shape[0])
+    want = float(np.asarray(t, np.float64).std())
+    got = sncc.template_sigma(t)
+    assert got == pytest.approx(want, rel=1e-12, abs=1e-12)
+    assert sncc.build_segments(t, 5.0).sigma_t == got
+    assert sncc.template_sigma(np.full((9, 4), 200, np.uint8)) == 0.0
+
+
 def test_quantisation_error_bound_is_small(sncc):
     c = synth.case_hd(M=200, N=200)
     for sigma in (5.0, 10.0, 20.0):

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from conftest import record_band_count
 from paper_2502_01286_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -43,9 +44,11 @@ def run_match(sncc, f, t, sigma, tau, cand_cap=1 << 20, k_max=0, s_bits=None):
     return seg, fd, tb, mb
 
 
-def check_candidates(rho64, cand, count, tau, rows=None):
+def check_candidates(rho64, cand, count, tau, rows=None, what=""):
     """Every offset with rho64 >= tau + TOL is a candidate and every one with
-    rho64 < tau - TOL is not; returns the number of offsets inside the band."""
+    rho64 < tau - TOL is not; the number of offsets inside the band (where
+    either decision is right) is recorded for the session summary and
+    returned."""
     V, U = rho64.shape
     cand = np.asarray(cand, np.int64)
     assert len(np.unique(cand)) == len(cand) == count
@@ -57,7 +60,9 @@ def check_candidates(rho64, cand, count, tau, rows=None):
     g = got[sel]
     assert np.all(g[r >= tau + TOL])
     assert not np.any(g[r < tau - TOL])
-    return int(np.sum((r >= tau - TOL) & (r < tau + TOL)))
+    band = int(np.sum((r >= tau - TOL) & (r < tau + TOL)))
+    record_band_count(what or "candidates at tau %.6f" % tau, band, r.size)
+    return band
 
 
 # ------------------------------------------------------------------ sum tables
@@ -138,7 +143,7 @@ def test_match_map_and_candidates(sncc, M, N, W, H, sigma):
     assert err <= TOL, err
     assert int(mb.status.item()) == 0
     cnt = int(mb.count.item())
-    check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, tau)
+    check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, tau, what="%dx%d t%dx%d sigma %g" % (M, N, W, H, sigma))
 
 
 @pytest.mark.parametrize("M,N,W,H", [(200, 150, 48, 40), (300, 260, 130, 129), (420, 150, 97, 65)])
@@ -173,7 +178,7 @@ def test_match_direct_sparse_multiblock_template(sncc, bits):
     ref = O.segmented_ncc_map(c.f, ap, "sat")
     assert np.abs(mb.rho.cpu().numpy() - ref).max() <= TOL
     cnt = int(mb.count.item())
-    check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, 0.5 * seg.rho_max)
+    check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, 0.5 * seg.rho_max, what="direct %d-bit" % bits)
 
 
 MULTI_CASES = [
@@ -300,6 +305,35 @@ def test_stream_matcher_equals_one_frame_at_a_time(sncc, sigmas):
         assert torch.equal(last[q].rho, ref.mbs[q].rho)
 
 
+def test_stream_matcher_reuses_one_pinned_frame(sncc):
+    """A caller that refills one pinned host buffer for every frame, and
+    overwrites it as soon as submit returns, gets each frame's own match
+    lists: submit returns only once the frame's copy is done."""
+    frames = [synth.case_hd(M=400, N=300, W=48, H=48, seed=80 + i) for i in range(4)]
+    t = frames[0].t
+    sm = sncc.StreamMatcher(t, (4.0,), 400, 300, precision=0.6)
+    buf = torch.empty((300, 400), dtype=torch.uint8).pin_memory()
+    got = []
+    for c in frames:
+        buf.copy_(torch.as_tensor(c.f))
+        r = sm.submit(buf)
+        buf.fill_(0)  # the next frame's data would land here now
+        if r is not None:
+            got.append(r)
+    got.append(sm.flush())
+    assert sm.status() == 0
+    ref = sncc.Matcher(t, 4.0, 400, 300, precision=0.6)
+    nonempty = 0
+    for c, lists in zip(frames, got):
+        ref.run(dev(c.f))
+        torch.cuda.synchronize()
+        want = sncc.matches_to_numpy(ref.rb)
+        nonempty += len(want[0]) > 0
+        for x, y in zip(lists[0], want):
+            np.testing.assert_array_equal(x, y)
+    assert nonempty > 0
+
+
 def test_match_multi_rejects_what_it_cannot_fuse(sncc):
     """Templates of different sizes are an argument error; a multi-block
     template, or one summed in place (at most 64 corners), is not fused
@@ -392,25 +426,61 @@ def test_match_hd_full_size_sampled(sncc, sigma):
     got = mb.rho.cpu().numpy()
     assert np.abs(got[rows] - ref[rows]).max() <= TOL
     cnt = int(mb.count.item())
-    check_candidates(ref, mb.cand[:min(cnt, mb.cand.numel())].cpu().numpy(), cnt, tau, rows=rows)
+    check_candidates(ref, mb.cand[:min(cnt, mb.cand.numel())].cpu().numpy(), cnt, tau, rows=rows,
+                     what="hd sigma %g, %d rows" % (sigma, len(rows)))
 
 
 def test_match_texture_full_size_sampled(sncc):
     """4096 x 4096 high-texture source with a 256 x 256 template at sigma 5
-    (thousands of segments, 64-bit sum tables), full launch, sampled rows."""
+    (thousands of segments, 64-bit sum tables, the register-staged 64 x 64
+    block instance of the segment-sum kernel), full launch in the bench's
+    configuration, on sampled offset rows: the map, the candidate set (G13
+    rule at tau_c = 0.85 rho_max) and the exact refine's matches (Eq. 1;
+    main algorithm steps 7a-7j with the exact second stage) against the
+    oracle.  A second run at precision 0.5 gives about 7.6e5 candidates in
+    all, and thousands of candidates and matches on those rows."""
     c = synth.case_texture()
+    N, M = c.f.shape
+    H, W = c.t.shape
+    U, V = M - W + 1, N - H + 1
     ap = O.precompute_template_approximation(c.t, 5.0)
     assert ap.K > 1000
-    tau = c.precision * ap.rho_max
-    seg, fd, tb, mb = run_match(sncc, c.f, c.t, 5.0, tau)
-    assert tb.s_bits == 64
-    V = 4096 - 256 + 1
-    rows = np.array([0, 1234, c.origin[1], V - 1])
+    rows = np.unique(np.r_[0, 1, 1234, c.origin[1] - 1, c.origin[1], c.origin[1] + 1, V - 1,
+                           np.random.default_rng(3).choice(V, 9, replace=False)])
     ref = O.segmented_ncc_map(c.f, ap, "sat", rows=rows)
-    got = mb.rho.cpu().numpy()
-    assert np.abs(got[rows] - ref[rows]).max() <= TOL
     u0, v0 = c.origin
-    assert abs(got[v0, u0] - ap.rho_max) <= TOL  # noise-free crop: rho = NCC(t, k)
+    td = dev(c.t)
+    for p in (c.precision, 0.5):
+        tau = p * ap.rho_max
+        seg, fd, tb, mb = run_match(sncc, c.f, c.t, 5.0, tau, cand_cap=U * V)
+        assert tb.s_bits == 64
+        got = mb.rho.cpu().numpy()
+        assert np.abs(got[rows] - ref[rows]).max() <= TOL
+        assert abs(got[v0, u0] - ap.rho_max) <= TOL  # noise-free crop: rho = NCC(t, k)
+        cnt = int(mb.count.item())
+        assert int(mb.status.item()) == 0
+        check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, tau, rows=rows,
+                         what="texture p %g, %d rows" % (p, len(rows)))
+        # exact refine of the full candidate list; its matches on the sampled
+        # rows against the oracle's refine of the oracle's candidates there
+        rb = sncc.alloc_refine(M, N, W, H, U * V // 4)
+        sncc.refine(fd, td, seg, mb, p, rb)
+        torch.cuda.synchronize()
+        assert int(mb.status.item()) == 0
+        u, v, rho = sncc.matches_to_numpy(rb)
+        key = v.astype(np.int64) * U + u
+        assert np.all(np.diff(key) > 0)
+        sel = np.isin(v, rows)
+        assert np.abs(rho[sel] - O.ncc_exact_at(c.f, c.t, u[sel], v[sel])).max(initial=0) <= TOL
+        idx_o, rho_o = O.refine(c.f, c.t, O.candidates(ref, tau), U, p)
+        diff = np.setxor1d(key[sel], idx_o)
+        if diff.size:
+            ex = O.ncc_exact_at(c.f, c.t, (diff % U).astype(np.int32), (diff // U).astype(np.int32))
+            amb = (np.abs(ref.ravel()[diff] - tau) < TOL) | (np.abs(ex - p) < TOL)
+            assert np.all(amb), diff[~amb][:10]
+        assert v0 * U + u0 in set(key.tolist())
+        if p < 0.6:
+            assert sel.sum() > 500  # many candidates and matches on the sampled rows
 
 
 # ------------------------------------------------------------------ fine pass
@@ -431,7 +501,7 @@ def test_refine_matches_oracle(sncc, M, N, W, H, sigma, p):
     rho_seg, idx_o, rho_o = oracle_matches(c.f, c.t, ap, tau_c, tau_e)
     seg, fd, tb, mb = run_match(sncc, c.f, c.t, sigma, tau_c)
     td = dev(c.t)
-    rb = sncc.alloc_refine(1 << 14)
+    rb = sncc.alloc_refine(M, N, W, H, 1 << 14)
     sncc.refine(fd, td, seg, mb, tau_e, rb)
     torch.cuda.synchronize()
     assert int(mb.status.item()) == 0
@@ -454,10 +524,37 @@ def test_refine_matches_oracle(sncc, M, N, W, H, sigma, p):
         assert c.origin[1] * U + c.origin[0] in got
 
 
+def test_refine_many_matches_sorted(sncc):
+    """Over 10^5 matches (a 1024 x 1024 source, every offset a candidate,
+    exact threshold 0.1): the sorted write-out (one bit per offset, prefix
+    counts, scatter) returns exactly the oracle's matches in ascending
+    v*U+u order with their exact rho (Eq. 1); matches within the tolerance
+    of the threshold may go either way."""
+    c = synth.case_hd(M=1024, N=1024, W=32, H=32, seed=2024)
+    N, M = c.f.shape
+    H, W = c.t.shape
+    U, V = M - W + 1, N - H + 1
+    seg, fd, tb, mb = run_match(sncc, c.f, c.t, 6.0, -1.0, cand_cap=U * V)
+    assert int(mb.count.item()) == U * V
+    rb = sncc.alloc_refine(M, N, W, H, U * V)
+    sncc.refine(fd, dev(c.t), seg, mb, 0.1, rb)
+    torch.cuda.synchronize()
+    assert int(mb.status.item()) == 0
+    u, v, rho = sncc.matches_to_numpy(rb)
+    assert len(u) == int(rb.nout.item()) > 100000
+    key = v.astype(np.int64) * U + u
+    assert np.all(np.diff(key) > 0)
+    ex = O.ncc_exact_map(c.f, c.t)
+    assert np.abs(rho - ex[v, u]).max() <= TOL
+    want = np.flatnonzero(ex.ravel() >= 0.1)
+    diff = np.setxor1d(key, want)
+    assert np.all(np.abs(ex.ravel()[diff] - 0.1) < TOL), diff[:10]
+
+
 def test_refine_output_overflow(sncc):
     c = synth.case_plain()
     seg, fd, tb, mb = run_match(sncc, c.f, c.t, 10.0, -1.0)
-    rb = sncc.alloc_refine(10)
+    rb = sncc.alloc_refine(256, 256, 32, 32, 10)
     sncc.refine(fd, dev(c.t), seg, mb, -1.0, rb)
     torch.cuda.synchronize()
     assert int(rb.nout.item()) == (256 - 31) ** 2
@@ -584,9 +681,9 @@ def test_fine_stage_per_candidate_and_tiled_agree(sncc, M, N, W, H, p, seed, bit
     fd = dev(c.f)
     tb = sncc.integral(fd, s_bits=bits)
     sncc.match(m.fast, m.plan_fast, tb, m.tau_fast, m.mb)
-    rb1 = sncc.alloc_refine(1 << 16)
+    rb1 = sncc.alloc_refine(M, N, W, H, 1 << 16)
     sncc.refine_segmented(m.slow, m.plan_slow, tb, m.mb, m.tau_slow, rb1)
-    rb2 = sncc.alloc_refine(1 << 16)
+    rb2 = sncc.alloc_refine(M, N, W, H, 1 << 16)
     ws = sncc.tiles_workspace(M, N, W, H, 1 << 16)
     sncc.refine_segmented_tiles(m.slow, m.plan_slow, tb, m.mb, m.tau_slow, rb2, ws)
     torch.cuda.synchronize()
@@ -603,7 +700,7 @@ def test_fine_stage_tiled_output_overflow(sncc):
     fd = dev(c.f)
     tb = sncc.integral(fd)
     sncc.match(m.fast, m.plan_fast, tb, m.tau_fast, m.mb)
-    rb = sncc.alloc_refine(7)
+    rb = sncc.alloc_refine(256, 256, 32, 32, 7)
     ws = sncc.tiles_workspace(256, 256, 32, 32, 7)
     sncc.refine_segmented_tiles(m.slow, m.plan_slow, tb, m.mb, m.tau_slow, rb, ws)
     torch.cuda.synchronize()
