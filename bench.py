@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["sncc", "reference"], default="sncc")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="texture")
+    ap.add_argument("--shard", choices=["replicas", "bands"], default="replicas",
+                    help="N > 1: each rank its own problem (replicas, weak scaling) or one source split into bands "
+                         "of offset rows with an H - 1 row halo (bands, strong scaling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     return ap.parse_args()
@@ -481,8 +484,24 @@ def run_gpu(args, world, rank, local, pg):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    case, SIGMAS, PRECISION = make_case(args.workload, rank)  # independent problem per rank
-    case_seed = case_seed_of(args.workload, rank)
+    band = None
+    if args.shard == "bands" and world > 1:
+        # one source for every rank: rank r runs the unchanged path on its
+        # band of offset rows (source rows [v0, v1 + H - 1)); the only
+        # exchange is the gather of the match lists after the timed region
+        import dataclasses
+        from paper_2502_01286_gb300 import shard
+        case, SIGMAS, PRECISION = make_case(args.workload, 0)
+        case_seed = case_seed_of(args.workload, 0)
+        full_N, full_M = case.f.shape
+        band = shard.bands(full_N, case.t.shape[0], world)[rank]
+        if band.empty:
+            raise SystemExit("more ranks than offset rows")
+        full_case = case
+        case = dataclasses.replace(case, f=np.ascontiguousarray(case.f[band.src_y0:band.src_y1]))
+    else:
+        case, SIGMAS, PRECISION = make_case(args.workload, rank)  # independent problem per rank
+        case_seed = case_seed_of(args.workload, rank)
     N, M = case.f.shape
     H, W = case.t.shape
     U, V = M - W + 1, N - H + 1
@@ -734,6 +753,22 @@ def run_gpu(args, world, rank, local, pg):
 
     value = sum_over_ranks(pg, offsets_per_step) / (ms_per_step * 1e-3) / 1e9
     e2e_value = sum_over_ranks(pg, offsets_per_step) / (e2e_ms_step * 1e-3) / 1e9
+    band_info = None
+    if band is not None:
+        # the one exchange of the band split: every rank's match list, in the
+        # full source's offsets, gathered on rank 0 (after the timed region)
+        from paper_2502_01286_gb300 import shard
+        U_full = full_M - W + 1
+        per_sigma = []
+        for i, rb in enumerate(rbs):
+            u_, v_, rho_ = sncc.matches_to_numpy(rb)
+            got = shard.gather_matches(shard.to_global(band, U_full, u_, v_), rho_)
+            if rank == 0:
+                per_sigma.append({"sigma_max": SIGMAS[i], "matches": int(got[0].size)})
+        band_info = {"ranks": world, "rows": [band.v0, band.v1], "source_rows": [band.src_y0, band.src_y1],
+                     "source": [full_M, full_N], "gathered": per_sigma,
+                     "how": "rank r owns offset rows [v0, v1) and reads source rows [v0, v1 + H - 1); its own sum "
+                            "tables give the same box sums; one gather of the match lists to rank 0"}
 
     cpu = None
     oracle_check = None
@@ -764,9 +799,11 @@ def run_gpu(args, world, rank, local, pg):
     peaks = measured_peaks()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int64", "data": "synthetic",
-        "config": workload_config(args.workload, case, SIGMAS, PRECISION, U, V, case_seed),
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong" if band is not None else "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": workload_config(args.workload, case, SIGMAS, PRECISION, U, V, case_seed) if band is None else
+                  workload_config(args.workload, full_case, SIGMAS, PRECISION, full_M - W + 1, full_N - H + 1,
+                                  case_seed),
         "launch": ("one CUDA graph per step: sum tables, one segment-sum launch over every (tile, threshold) "
                    "pair, then per threshold exact refine and sort (parallel branches)") if fused else
                   "one CUDA graph per step: sum tables, then per threshold segment sum, exact refine and sort",
@@ -808,6 +845,8 @@ def run_gpu(args, world, rank, local, pg):
         line["cpu_baseline"] = cpu
     if oracle_check is not None:
         line["oracle_check"] = oracle_check
+    if band_info is not None:
+        line["shard"] = band_info
     if rank == 0:
         print(json.dumps(line), flush=True)
 
