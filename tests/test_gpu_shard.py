@@ -81,13 +81,13 @@ def test_bands_equal_one_launch_texture(sncc, world):
 def test_bands_equal_one_launch_hd_ragged(sncc):
     """HD source (1920 x 1080, 64 x 64 template) in 7 bands of 145 or 146
     offset rows: tile heights and table widths change per band, the list
-    does not."""
+    does not (precision 0.25)."""
     c = synth.case_hd()
     N, M = c.f.shape
     H, W = c.t.shape
     U, V = M - W + 1, N - H + 1
-    _, idx_full, rho_full = run_full(sncc, c, 10.0, 0.5, U * V, 1 << 20)
-    idx, rho, _ = run_bands(sncc, c, 10.0, 0.5, 7, U * V, 1 << 20)
-    assert idx_full.size > 100
+    _, idx_full, rho_full = run_full(sncc, c, 10.0, 0.25, U * V, 1 << 20)
+    idx, rho, _ = run_bands(sncc, c, 10.0, 0.25, 7, U * V, 1 << 20)
+    assert idx_full.size > 1000  # about 6000 at precision 0.25, spread over every band
     np.testing.assert_array_equal(idx, idx_full)
     np.testing.assert_array_equal(rho, rho_full)
