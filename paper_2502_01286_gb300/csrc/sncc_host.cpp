@@ -153,11 +153,9 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
     L.WP = WP;
     L.nbx = (W + BW - 1) / BW;
     L.nby = (H + BH - 1) / BH;
-    std::vector<int32_t> blocks, corners, runblk, runs, chainblk, chains;
+    std::vector<int32_t> blocks, corners, runblk, runs;
     L.max_corners = 0;
     L.nonzero_corners = 0;
-    L.chain_loads8 = 0;
-    L.run_loads8 = 0;
     for (int k = 0; k < 4; ++k) L.runs[k] = 0;
     for (int by_i = 0; by_i < L.nby; ++by_i) {
         for (int bx_i = 0; bx_i < L.nbx; ++bx_i) {
@@ -222,43 +220,9 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
                     if (k < 3)  // pad the record to its int4 units
                         while (cls[k].size() % (4 * RUN_INT4[k]) != 0) cls[k].push_back(0);
                     ++L.runs[k];
-                    L.run_loads8 += 8 + len - 1;
                     Y += len;
                 }
             }
-            // Corner chains: down each column, every corner reuses the rows
-            // of the window the previous corner of the column loaded.
-            chainblk.push_back((int32_t)(chains.size() / 4));
-            const size_t chain_start = chains.size();
-            int phase = 0, last = 0;
-            for (int X = 0; X <= bw; ++X) {
-                const int32_t* col = &G[(size_t)X * (bh + 1)];
-                int prev = -CHAIN_FRESH;
-                for (int Y = 0; Y <= bh; ++Y) {
-                    if (col[Y] == 0) continue;
-                    const int gap = Y - prev;
-                    int D, P;
-                    if (gap >= CHAIN_FRESH) {
-                        D = CHAIN_FRESH;
-                        P = 0;
-                        L.chain_loads8 += 8;
-                    } else {
-                        D = gap;
-                        P = (phase + gap) % CHAIN_WIN;
-                        L.chain_loads8 += gap;
-                    }
-                    last = Y * WP + X;
-                    chains.push_back(last | ((P * (CHAIN_FRESH + 1) + D) << 16));
-                    chains.push_back(col[Y]);
-                    phase = P;
-                    prev = Y;
-                }
-            }
-            if (((chains.size() - chain_start) / 2) % 2 != 0) {  // a whole int4: pad with a no-op record
-                chains.push_back(last | ((phase * (CHAIN_FRESH + 1)) << 16));
-                chains.push_back(0);
-            }
-            chainblk.push_back((int32_t)((chains.size() - chain_start) / 4));
             while (cls[3].size() % 8 != 0) cls[3].push_back(0);  // whole groups of 4 single corners
             for (int k = 0; k < 4; ++k) {
                 runblk.push_back((int32_t)(runs.size() / 4));
@@ -277,12 +241,6 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
     image.insert(image.end(), runblk.begin(), runblk.end());
     L.runs_offset = image.size() * 4;
     image.insert(image.end(), runs.begin(), runs.end());
-    while (image.size() % 4 != 0) image.push_back(0);  // 16-byte aligned sections
-    L.chainblk_offset = image.size() * 4;
-    image.insert(image.end(), chainblk.begin(), chainblk.end());
-    while (image.size() % 4 != 0) image.push_back(0);
-    L.chains_offset = image.size() * 4;
-    image.insert(image.end(), chains.begin(), chains.end());
     L.end_offset = image.size() * 4;
 }
 

@@ -60,22 +60,7 @@ constexpr int BLOCK_MULTI = 32;       // first layout of larger templates: 32 x 
 //    {G7, 0, 0, 0}, a run of 4 is {idx, G0, G1, G2} {G3, 0, 0, 0}, a run of
 //    2 is {idx, G0, G1, 0}, with idx = Y * WP + X; single corners are int2
 //    {idx, G}, two per int4, padded with zero weights to a multiple of 4
-//    (n1 counts corners, not int4 units);
-//  * int2 chainblk[nblk] = {first, npairs}: block b's corner chain, npairs
-//    int4 units of chains[] from int4 index `first`;
-//  * int4 chains[]: the same corners once more, column by column and down
-//    each column, as int2 records {idx | code << 16, G} two per int4 (an odd
-//    chain ends with a record of weight 0 and no loads).  A lane keeps the
-//    region words of the rows its R offset rows need in a circular window of
-//    8 registers: logical row r of the current corner sits in register
-//    (P + r) mod 8.  code = P * 9 + D, where D is the corner's distance in
-//    rows from the previous corner of its column (1 .. 7: the rows that
-//    corner loaded are reused, min(D, R) new rows are loaded) or 8 (a new
-//    column or a gap of 8 rows or more: all R rows are loaded), and P is the
-//    phase, (previous P + D) mod 8 when D < 8.  D = 0 loads nothing (the
-//    padding record).
-constexpr int CHAIN_WIN = 8;     // registers of the circular window (the largest R)
-constexpr int CHAIN_FRESH = 8;   // D of a corner that loads all its rows
+//    (n1 counts corners, not int4 units).
 struct Layout {
     int BW = 0, BH = 0;     // block size (the last block in a row/column may be smaller)
     int nbx = 0, nby = 0;   // blocks across / down
@@ -85,14 +70,10 @@ struct Layout {
     int total_corners = 0;  // including the zero-weight padding
     int nonzero_corners = 0;
     int runs[4] = {0, 0, 0, 0};  // vertical runs of 8, 4, 2 and 1 corners, over all blocks
-    long long chain_loads8 = 0;  // region words one lane loads over all chains with R = 8
-    long long run_loads8 = 0;    // the same over the vertical runs
     size_t blocks_offset = 0;
     size_t corners_offset = 0;
     size_t runblk_offset = 0;
     size_t runs_offset = 0;
-    size_t chainblk_offset = 0;
-    size_t chains_offset = 0;
     size_t end_offset = 0;  // one past the section
 };
 

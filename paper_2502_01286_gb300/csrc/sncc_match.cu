@@ -49,7 +49,6 @@
 
 #include <cstdint>
 #include <algorithm>
-#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -67,8 +66,6 @@ namespace {
 struct MultiPlan {
     const int4* runblk;
     const int4* runs;
-    const int2* chainblk;
-    const int4* chains;
     long long Q0;
     float Ek, scale, tau;
     int cand_cap;
@@ -83,8 +80,6 @@ struct MatchArgs {
     const int4* blocks;
     const int4* runblk;  // two per block
     const int4* runs;
-    const int2* chainblk;  // one per block
-    const int4* chains;
     int nblk;
     int RH;  // region rows = 8R + BH + 1
     int M, N;
@@ -193,7 +188,7 @@ __device__ __forceinline__ void match_epilogue(const MatchArgs& a, const long lo
     }
 }
 
-template <int R, bool S64, int WP, bool FINE, bool DIRECT, bool MULTI, bool REGS, bool CHAIN>
+template <int R, bool S64, int WP, bool FINE, bool DIRECT, bool MULTI, bool REGS>
 __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUtensorMap tmap, const MatchArgs a) {
     constexpr bool TMA = !S64 && !REGS;  // else the region is staged through registers
     extern __shared__ __align__(128) unsigned char smem_base[];
@@ -224,17 +219,12 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
     }
     __syncthreads();
 
-    // the corner runs or chains: this launch's plan, or (fused launch) plan
-    // blockIdx.z
+    // the corner runs: this launch's plan, or (fused launch) plan blockIdx.z
     const int4* runs = a.runs;
     const int4* runblk = a.runblk;
-    const int4* chains = a.chains;
-    const int2* chainblk = a.chainblk;
     if constexpr (MULTI) {
         runs = a.mp[blockIdx.z].runs;
         runblk = a.mp[blockIdx.z].runblk;
-        chains = a.mp[blockIdx.z].chains;
-        chainblk = a.mp[blockIdx.z].chainblk;
     }
     long long acc[R];
 #pragma unroll
@@ -289,13 +279,8 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
                 stage_region_regs<S64, WP>(a.s, a.pitch, a.M, a.N, work, u0 + blk.x, v0 + blk.y, RH, lane, warp);
             }
             __syncthreads();
-            // ---- corner sum: one multiply-add per (offset, corner) ----
-            if constexpr (CHAIN) {
-                const int2 cb = __ldg(chainblk + b);
-                chain_sum<R, WP>(acc, wbase, chains + cb.x, cb.y);
-            } else {
-                run_sum<R, WP>(acc, wbase, runs, __ldg(runblk + 2 * b), __ldg(runblk + 2 * b + 1));
-            }
+            // ---- corner sum over vertical runs: one multiply-add per (offset, corner) ----
+            run_sum<R, WP>(acc, wbase, runs, __ldg(runblk + 2 * b), __ldg(runblk + 2 * b + 1));
             __syncthreads();  // the region buffer is restaged for the next block
         }
     }
@@ -347,7 +332,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-template <int R, bool S64, int WP, bool FINE, bool DIRECT, bool MULTI, bool REGS, bool CHAIN>
+template <int R, bool S64, int WP, bool FINE, bool DIRECT, bool MULTI, bool REGS>
 cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
     const int RH = DIRECT ? 0 : WARPS * R + BH + 1;  // direct mode stages nothing
     MatchArgs args = a;
@@ -356,44 +341,24 @@ cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cud
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP, FINE, DIRECT, MULTI, REGS, CHAIN>,
+        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP, FINE, DIRECT, MULTI, REGS>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         128 + smem_words(WARPS * R + 64 + 1, WP) * 4);
     });
     if (attr_err != cudaSuccess) return attr_err;
     const int tu = (a.U + TILE_U - 1) / TILE_U, tv = (a.V + WARPS * R - 1) / (WARPS * R);
     const dim3 grid = FINE ? dim3(tu * tv) : dim3(tu, tv, MULTI ? a.nplans : 1);
-    match_kernel<R, S64, WP, FINE, DIRECT, MULTI, REGS, CHAIN><<<grid, WARPS * 32, sm, st>>>(map, args);
+    match_kernel<R, S64, WP, FINE, DIRECT, MULTI, REGS><<<grid, WARPS * 32, sm, st>>>(map, args);
     return cudaGetLastError();
 }
 
 template <bool S64, int WP, bool FINE, bool DIRECT = false, bool MULTI = false, bool REGS = false>
-cudaError_t dispatch_r(int R, const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st, bool chain) {
-    if (chain && !DIRECT) {
-        switch (R) {
-            case 8: return launch_match<8, S64, WP, FINE, DIRECT, MULTI, REGS, true>(map, a, BH, st);
-            case 4: return launch_match<4, S64, WP, FINE, DIRECT, MULTI, REGS, true>(map, a, BH, st);
-            default: return launch_match<2, S64, WP, FINE, DIRECT, MULTI, REGS, true>(map, a, BH, st);
-        }
-    }
+cudaError_t dispatch_r(int R, const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
     switch (R) {
-        case 8: return launch_match<8, S64, WP, FINE, DIRECT, MULTI, REGS, false>(map, a, BH, st);
-        case 4: return launch_match<4, S64, WP, FINE, DIRECT, MULTI, REGS, false>(map, a, BH, st);
-        default: return launch_match<2, S64, WP, FINE, DIRECT, MULTI, REGS, false>(map, a, BH, st);
+        case 8: return launch_match<8, S64, WP, FINE, DIRECT, MULTI, REGS>(map, a, BH, st);
+        case 4: return launch_match<4, S64, WP, FINE, DIRECT, MULTI, REGS>(map, a, BH, st);
+        default: return launch_match<2, S64, WP, FINE, DIRECT, MULTI, REGS>(map, a, BH, st);
     }
-}
-
-// Corner sum by chains (sliding register windows down each column) or by
-// vertical runs.  SNCC_SEGSUM=runs|chains overrides the choice (measurement).
-bool use_chains(const Layout& L) {
-    static int forced = [] {
-        const char* e = std::getenv("SNCC_SEGSUM");
-        if (e && std::strcmp(e, "runs") == 0) return 0;
-        if (e && std::strcmp(e, "chains") == 0) return 1;
-        return -1;
-    }();
-    if (forced >= 0) return forced == 1;
-    return L.chain_loads8 < L.run_loads8;
 }
 
 // The segment-sum launch on a prepared MatchArgs: picks the kernel instance
@@ -402,16 +367,15 @@ bool use_chains(const Layout& L) {
 template <bool FINE>
 cudaError_t launch_layout(const Layout& L, bool s64, int R, const CUtensorMap& map, const MatchArgs& a,
                           cudaStream_t st) {
-    const bool ch = use_chains(L);
     if (a.ndirect > 0)  // sparse template: no staging
-        return s64 ? dispatch_r<true, 100, FINE, true>(R, map, a, 0, st, false)
-                   : dispatch_r<false, 100, FINE, true>(R, map, a, 0, st, false);
+        return s64 ? dispatch_r<true, 100, FINE, true>(R, map, a, 0, st)
+                   : dispatch_r<false, 100, FINE, true>(R, map, a, 0, st);
     if (s64)
-        return L.WP == 68 ? dispatch_r<true, 68, FINE>(R, map, a, L.BH, st, ch)
-                          : dispatch_r<true, 100, FINE>(R, map, a, L.BH, st, ch);
-    if (L.nblk > 1) return dispatch_r<false, 100, FINE, false, false, true>(R, map, a, L.BH, st, ch);
-    return L.WP == 68 ? dispatch_r<false, 68, FINE>(R, map, a, L.BH, st, ch)
-                      : dispatch_r<false, 100, FINE>(R, map, a, L.BH, st, ch);
+        return L.WP == 68 ? dispatch_r<true, 68, FINE>(R, map, a, L.BH, st)
+                          : dispatch_r<true, 100, FINE>(R, map, a, L.BH, st);
+    if (L.nblk > 1) return dispatch_r<false, 100, FINE, false, false, true>(R, map, a, L.BH, st);
+    return L.WP == 68 ? dispatch_r<false, 68, FINE>(R, map, a, L.BH, st)
+                      : dispatch_r<false, 100, FINE>(R, map, a, L.BH, st);
 }
 
 // Offsets per thread: the largest R in {8, 4, 2} that still gives two CTAs
@@ -464,8 +428,6 @@ int prepare_match(const sncc_segments* seg, const void* d_plan, const void* d_s,
     a.blocks = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.blocks_offset);
     a.runblk = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.runblk_offset);
     a.runs = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.runs_offset);
-    a.chainblk = reinterpret_cast<const int2*>(static_cast<const char*>(d_plan) + L.chainblk_offset);
-    a.chains = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + L.chains_offset);
     a.nblk = L.nblk;
     a.RH = RH;
     a.M = M;
@@ -656,8 +618,6 @@ extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* co
         MultiPlan& mp = a.mp[z];
         mp.runblk = reinterpret_cast<const int4*>(static_cast<const char*>(d_plans[q]) + Lq.runblk_offset);
         mp.runs = reinterpret_cast<const int4*>(static_cast<const char*>(d_plans[q]) + Lq.runs_offset);
-        mp.chainblk = reinterpret_cast<const int2*>(static_cast<const char*>(d_plans[q]) + Lq.chainblk_offset);
-        mp.chains = reinterpret_cast<const int4*>(static_cast<const char*>(d_plans[q]) + Lq.chains_offset);
         mp.Q0 = p->Q0;
         mp.Ek = (float)segs[q]->Ek;
         mp.scale = (float)std::ldexp(1.0, -p->F);
@@ -677,23 +637,12 @@ extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* co
         if (cudaMemsetAsync(d_count[q], 0, sizeof(int32_t), st) != cudaSuccess ||
             cudaMemsetAsync(d_status[q], 0, sizeof(int32_t), st) != cudaSuccess)
             return SNCC_ERR_CUDA;
-    // chains for the fused launch when they need fewer loads over all
-    // approximations together (one kernel instance for every slice)
-    long long cl = 0, rl = 0;
-    for (int q = 0; q < n; ++q) {
-        cl += layout_for(*plan_of(segs[q])).chain_loads8;
-        rl += layout_for(*plan_of(segs[q])).run_loads8;
-    }
-    Layout sum;
-    sum.chain_loads8 = cl;
-    sum.run_loads8 = rl;
-    const bool ch = use_chains(sum);
     cudaError_t e;
     if (L->WP == 68)
-        e = s64 ? dispatch_r<true, 68, false, false, true>(R, map, a, L->BH, st, ch)
-                : dispatch_r<false, 68, false, false, true>(R, map, a, L->BH, st, ch);
+        e = s64 ? dispatch_r<true, 68, false, false, true>(R, map, a, L->BH, st)
+                : dispatch_r<false, 68, false, false, true>(R, map, a, L->BH, st);
     else
-        e = s64 ? dispatch_r<true, 100, false, false, true>(R, map, a, L->BH, st, ch)
-                : dispatch_r<false, 100, false, false, true>(R, map, a, L->BH, st, ch);
+        e = s64 ? dispatch_r<true, 100, false, false, true>(R, map, a, L->BH, st)
+                : dispatch_r<false, 100, false, false, true>(R, map, a, L->BH, st);
     return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }

@@ -202,61 +202,6 @@ __device__ __forceinline__ void run_sum(long long (&acc)[R], const int* wbase, c
     corner_sum<R, WP>(acc, wbase, runs + d1.z, d1.w);
 }
 
-// One corner of a chain (see Layout in sncc_internal.h): the rows this
-// corner needs that the window does not hold yet are loaded into their
-// registers of the circular window, then the corner's weight is applied to
-// the R rows.  P (phase) and D (distance to the previous corner of the
-// column, CHAIN_FRESH for none within reach) are compile-time, so every
-// window index is static and the window stays in registers.
-template <int R, int WP, int P, int D>
-__device__ __forceinline__ void chain_corner(long long (&acc)[R], int (&win)[CHAIN_WIN], const int* w, int g) {
-    constexpr int first = (D == 0) ? R : ((D >= R) ? 0 : R - D);  // rows first .. R-1 are new
-#pragma unroll
-    for (int r = first; r < R; ++r) win[(P + r) % CHAIN_WIN] = w[r * WP];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] += (long long)g * (long long)win[(P + r) % CHAIN_WIN];
-}
-
-// Dispatches a chain record {idx | code << 16, g} to its (P, D) instance:
-// one warp-uniform indexed branch per corner.
-template <int R, int WP>
-__device__ __forceinline__ void chain_step(long long (&acc)[R], int (&win)[CHAIN_WIN], const int* wbase, int x,
-                                           int g) {
-    const int* w = wbase + (x & 0xffff);
-    switch (x >> 16) {
-#define SNCC_CHAIN_CASE(P, D) \
-    case (P) * (CHAIN_FRESH + 1) + (D): chain_corner<R, WP, P, D>(acc, win, w, g); break;
-#define SNCC_CHAIN_PHASE(P)                                                                             \
-    SNCC_CHAIN_CASE(P, 0) SNCC_CHAIN_CASE(P, 1) SNCC_CHAIN_CASE(P, 2) SNCC_CHAIN_CASE(P, 3)            \
-    SNCC_CHAIN_CASE(P, 4) SNCC_CHAIN_CASE(P, 5) SNCC_CHAIN_CASE(P, 6) SNCC_CHAIN_CASE(P, 7)            \
-    SNCC_CHAIN_CASE(P, 8)
-        SNCC_CHAIN_PHASE(0) SNCC_CHAIN_PHASE(1) SNCC_CHAIN_PHASE(2) SNCC_CHAIN_PHASE(3)
-        SNCC_CHAIN_PHASE(4) SNCC_CHAIN_PHASE(5) SNCC_CHAIN_PHASE(6) SNCC_CHAIN_PHASE(7)
-#undef SNCC_CHAIN_PHASE
-#undef SNCC_CHAIN_CASE
-        default: break;
-    }
-}
-static_assert(CHAIN_WIN == 8 && CHAIN_FRESH == 8, "the chain dispatch lists phases 0..7 and distances 0..8");
-
-// acc[r] += the block's corner sum over its chain: npairs int4 units of two
-// records each, the next unit loaded while the current one is applied.
-template <int R, int WP>
-__device__ __forceinline__ void chain_sum(long long (&acc)[R], const int* wbase, const int4* rec, int npairs) {
-    static_assert(R <= CHAIN_WIN, "the window holds at most CHAIN_WIN rows");
-    if (npairs <= 0) return;
-    int win[CHAIN_WIN];
-#pragma unroll
-    for (int i = 0; i < CHAIN_WIN; ++i) win[i] = 0;
-    int4 nx = __ldg(rec);
-    for (int i = 0; i < npairs; ++i) {
-        const int4 c = nx;
-        if (i + 1 < npairs) nx = __ldg(rec + i + 1);
-        chain_step<R, WP>(acc, win, wbase, c.x, c.y);
-        chain_step<R, WP>(acc, win, wbase, c.z, c.w);
-    }
-}
-
 // rho at offset (u, v) from the exact numerator acc = 2^F num + Q0 * sum f / n
 // (Eq. 13, 15, 16 exact in integers; E_f = var / n in FP64 as var times the
 // FP64 reciprocal of n, within one FP64 ulp of the quotient; Eq. 17-18 in
