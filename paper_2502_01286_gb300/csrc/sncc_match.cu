@@ -49,7 +49,6 @@
 
 #include <cstdint>
 #include <algorithm>
-#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -124,8 +123,6 @@ __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / 
 //   work[align32(RH*WP)] | row0[128] | col0[160] | mbarrier (8 B) | flag
 __host__ __device__ constexpr int work_words(int RH, int WP) { return align_up(RH * WP, 32); }
 __host__ __device__ constexpr int smem_words(int RH, int WP) { return work_words(RH, WP) + 128 + 160 + 4; }
-// double-buffered kernel: two buffers | row0[128] | col0[160] | 2 mbarriers | flag
-__host__ __device__ constexpr int smem_words_db(int RH, int WP) { return 2 * work_words(RH, WP) + 128 + 160 + 8; }
 
 // 32-bit tables: starts the TMA tile copy of a block's region into `buf`
 // (thread 0 issues; completion on `bar`).
@@ -298,86 +295,6 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
     }
 }
 
-// Multi-block templates (64 x 64 blocks, region pitch 100) with a 32-bit
-// table: the regions of blocks b and b + 1 are copied by TMA into two
-// buffers while block b's corners are summed, so that the copies overlap the
-// multiply-adds instead of alternating with them.  Each buffer is re-based
-// in place once its copy has landed.  Shared memory: two RH x 100 word
-// buffers (104 KB with R = 8), so two CTAs share an SM.
-template <int R, bool FINE>
-__global__ void __launch_bounds__(256, 2) match_kernel_db(const __grid_constant__ CUtensorMap tmap, const MatchArgs a) {
-    constexpr int WP = 100;
-    extern __shared__ __align__(128) unsigned char smem_base[];
-    int* buf0 = reinterpret_cast<int*>(smem_base + ((128u - (smem_u32(smem_base) & 127u)) & 127u));
-    const int RH = a.RH;
-    int* buf1 = buf0 + work_words(RH, WP);
-    int* row0 = buf1 + work_words(RH, WP);
-    int* col0 = row0 + 128;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(col0 + 160);  // two mbarriers
-    volatile int* flag = reinterpret_cast<volatile int*>(bar + 2);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int u0 = blockIdx.x * TILE_U, v0 = blockIdx.y * (WARPS * R);
-    if constexpr (FINE) {  // a 1-D grid over the listed tiles; the rest exit at once
-        if ((int)blockIdx.x >= *a.tile_count) return;
-        const int t = a.tile_list[blockIdx.x];
-        u0 = (t % a.tiles_u) * TILE_U;
-        v0 = (t / a.tiles_u) * (WARPS * R);
-    }
-    const int nblk = a.nblk;
-    const uint32_t box_bytes = (uint32_t)(RH * WP * 4);
-    auto issue = [&](int b, int* dst, uint64_t* br) {  // thread 0 only
-        const int4 blk = a.blocks[b];
-        fence_proxy_async();
-        mbar_arrive_expect_tx(br, box_bytes);
-        tma_load_2d(dst, &tmap, u0 + blk.x, v0 + blk.y, br);
-    };
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
-        fence_mbar_init();
-        *flag = 0;
-        issue(0, buf0, bar);
-        if (nblk > 1) issue(1, buf1, bar + 1);
-    }
-    __syncthreads();
-
-    long long acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = 0;
-    uint32_t parity = 0u;  // phase parity expected next on both barriers (they advance together)
-    for (int b = 0; b < nblk; ++b) {
-        const int k = b & 1;
-        int* work = k ? buf1 : buf0;
-        if (tid == 0 && !mbar_wait_bounded(bar + k, parity)) *flag = 1;
-        __syncthreads();
-        if (*flag) {
-            if (tid == 0) atomicOr(a.status, SNCC_STATUS_WAIT_TIMEOUT);
-            return;
-        }
-        (void)mbar_try_wait(bar + k, parity);  // phase complete: acquire for this thread
-        if (k == 1) parity ^= 1u;
-        // re-base the region to its own origin (wrapped 32-bit arithmetic)
-        for (int X = tid; X < WP; X += WARPS * 32) row0[X] = work[X];
-        for (int Y = tid; Y < RH; Y += WARPS * 32) col0[Y] = work[Y * WP];
-        __syncthreads();
-        const uint32_t c00 = (uint32_t)row0[0];
-        for (int Y = warp; Y < RH; Y += WARPS) {
-            const uint32_t cy = (uint32_t)col0[Y] - c00;
-            for (int X = lane; X < WP; X += 32)
-                work[Y * WP + X] = (int)((uint32_t)work[Y * WP + X] - (uint32_t)row0[X] - cy);
-        }
-        __syncthreads();
-        // ---- corner sum over vertical runs: one multiply-add per (offset, corner) ----
-        run_sum<R, WP>(acc, work + warp * R * WP + lane, a.runs, __ldg(a.runblk + 2 * b), __ldg(a.runblk + 2 * b + 1));
-        fence_proxy_async();  // this thread's accesses to the buffer precede the next copy into it
-        __syncthreads();
-        if (tid == 0 && b + 2 < nblk) issue(b + 2, work, bar + k);
-    }
-    match_epilogue<R, false, FINE>(a, acc, u0, v0, lane, warp, a.Ek, a.scale, a.Q0, a.tau, a.rho, a.cand,
-                                   a.cand_cap, a.count, a.status);
-}
-
 // Fine mode, step 1: the candidate bit of every listed offset, and a flag on
 // every tile (32 x rows offsets) that holds a candidate.
 __global__ void __launch_bounds__(256) mark_candidate_tiles(const int32_t* __restrict__ cand,
@@ -444,56 +361,19 @@ cudaError_t dispatch_r(int R, const CUtensorMap& map, const MatchArgs& a, int BH
     }
 }
 
-// The double-buffered launch (multi-block templates, either table width).
-template <int R, bool FINE>
-cudaError_t launch_db(const CUtensorMap& map, const MatchArgs& a, int BH, cudaStream_t st) {
-    constexpr int WP = 100;
-    const int RH = WARPS * R + BH + 1;
-    MatchArgs args = a;
-    args.RH = RH;
-    const size_t sm = 128 + (size_t)smem_words_db(RH, WP) * 4;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(match_kernel_db<R, FINE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        128 + smem_words_db(WARPS * R + 64 + 1, WP) * 4);
-    });
-    if (attr_err != cudaSuccess) return attr_err;
-    const int tu = (a.U + TILE_U - 1) / TILE_U, tv = (a.V + WARPS * R - 1) / (WARPS * R);
-    const dim3 grid = FINE ? dim3(tu * tv) : dim3(tu, tv);
-    match_kernel_db<R, FINE><<<grid, WARPS * 32, sm, st>>>(map, args);
-    return cudaGetLastError();
-}
-
-// Templates larger than 64 x 64 (the 64 x 64 block layout) with a 32-bit
-// table take the double-buffered kernel.
-inline bool uses_db(const Plan& p, bool s64) { return !s64 && p.lay[0].nbx * p.lay[0].nby > 1; }
-
 // The segment-sum launch on a prepared MatchArgs: picks the kernel instance
-// for the layout and table width.  Sparse templates: corners read in place.
-// One block: TMA staging (32-bit tables) or register staging (64-bit).
-// Several 64 x 64 blocks: double-buffered TMA staging.
+// for the layout and table width.  One block (32-bit tables): TMA staging;
+// 64 x 64 blocks of a larger template, or 64-bit tables: register staging.
 template <bool FINE>
-cudaError_t launch_layout(const Plan& p, const Layout& L, bool s64, int R, const CUtensorMap& map,
-                          const MatchArgs& a, cudaStream_t st) {
+cudaError_t launch_layout(const Layout& L, bool s64, int R, const CUtensorMap& map, const MatchArgs& a,
+                          cudaStream_t st) {
     if (a.ndirect > 0)  // sparse template: no staging
         return s64 ? dispatch_r<true, 100, FINE, true>(R, map, a, 0, st)
                    : dispatch_r<false, 100, FINE, true>(R, map, a, 0, st);
-    static const bool db_off = std::getenv("SNCC_DB_OFF") != nullptr;  // measurement only
-    if (db_off && uses_db(p, s64)) {
-        if (s64) return dispatch_r<true, 100, FINE>(R, map, a, L.BH, st);
-        return dispatch_r<false, 100, FINE, false, false, true>(R, map, a, L.BH, st);
-    }
-    if (uses_db(p, s64)) {
-        switch (R) {
-            case 8: return launch_db<8, FINE>(map, a, L.BH, st);
-            case 4: return launch_db<4, FINE>(map, a, L.BH, st);
-            default: return launch_db<2, FINE>(map, a, L.BH, st);
-        }
-    }
     if (s64)
         return L.WP == 68 ? dispatch_r<true, 68, FINE>(R, map, a, L.BH, st)
                           : dispatch_r<true, 100, FINE>(R, map, a, L.BH, st);
+    if (L.nblk > 1) return dispatch_r<false, 100, FINE, false, false, true>(R, map, a, L.BH, st);
     return L.WP == 68 ? dispatch_r<false, 68, FINE>(R, map, a, L.BH, st)
                       : dispatch_r<false, 100, FINE>(R, map, a, L.BH, st);
 }
@@ -651,8 +531,7 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(d_count, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
     if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
-    return launch_layout<false>(*plan_of(seg), *L, s_bits == 64, R, map, a, st) == cudaSuccess ? SNCC_OK
-                                                                                            : SNCC_ERR_CUDA;
+    return launch_layout<false>(*L, s_bits == 64, R, map, a, st) == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }
 
 extern "C" size_t sncc_refine_segmented_tiles_workspace_bytes(int M, int N, int W, int H, int out_cap) {
@@ -699,7 +578,7 @@ extern "C" int sncc_refine_segmented_tiles(const sncc_segments* seg, const void*
     a.out_cap = out_cap;
     a.nout = d_nout;
     a.status = d_status;
-    if (launch_layout<true>(*plan_of(seg), *L, s_bits == 64, R, map, a, st) != cudaSuccess) return SNCC_ERR_CUDA;
+    if (launch_layout<true>(*L, s_bits == 64, R, map, a, st) != cudaSuccess) return SNCC_ERR_CUDA;
     if (out_cap > 0 && launch_match_sort(recs, d_nout, out_cap, a.U, a.V, ws + t.sort, d_out, st) != cudaSuccess)
         return SNCC_ERR_CUDA;
     return SNCC_OK;
