@@ -215,7 +215,7 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
                         }
                     }
                     const int len = RUN_LEN[k];
-                    cls[k].push_back(Y * WP + X);
+                    cls[k].push_back(4 * (Y * WP + X));  // byte offset in the region
                     for (int i = 0; i < len; ++i) cls[k].push_back(col[Y + i]);
                     if (k < 3)  // pad the record to its int4 units
                         while (cls[k].size() % (4 * RUN_INT4[k]) != 0) cls[k].push_back(0);

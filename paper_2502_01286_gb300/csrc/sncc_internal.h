@@ -58,9 +58,10 @@ constexpr int BLOCK_MULTI = 32;       // first layout of larger templates: 32 x 
 //    nonzero); first* index int4 units of runs[];
 //  * int4 runs[]: a run of 8 is {idx, G0, G1, G2} {G3, G4, G5, G6}
 //    {G7, 0, 0, 0}, a run of 4 is {idx, G0, G1, G2} {G3, 0, 0, 0}, a run of
-//    2 is {idx, G0, G1, 0}, with idx = Y * WP + X; single corners are int2
-//    {idx, G}, two per int4, padded with zero weights to a multiple of 4
-//    (n1 counts corners, not int4 units).
+//    2 is {idx, G0, G1, 0}, with idx = 4 (Y * WP + X), the byte offset of
+//    the run's first word in the region; single corners are int2 {idx, G},
+//    two per int4, padded with zero weights to a multiple of 4 (n1 counts
+//    corners, not int4 units).
 struct Layout {
     int BW = 0, BH = 0;     // block size (the last block in a row/column may be smaller)
     int nbx = 0, nby = 0;   // blocks across / down

@@ -119,27 +119,27 @@ __device__ __forceinline__ void stage_region_regs(const void* s, int pitch, int 
     }
 }
 
+// off is the corner's byte offset in the region (a plain add to the lane's
+// base address).
 template <int R, int WP>
 __device__ __forceinline__ void apply_corner(long long (&acc)[R], const int* wbase, int off, int g) {
-    const int* w = wbase + off;
+    const int* w = reinterpret_cast<const int*>(reinterpret_cast<const char*>(wbase) + off);
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] += (long long)g * (long long)w[r * WP];
 }
 
 // acc[r] += sum over the block's corner records of G * region(row r + Y, col X).
-// Records come two per 16-byte load, one group of four ahead of their use;
-// `count` is a multiple of 4 (zero-weight padding) and `cq` 16-byte aligned.
+// Records come two per 16-byte load, four per iteration; `count` is a
+// multiple of 4 (zero-weight padding) and `cq` 16-byte aligned.  The loads
+// are issued at the top of each iteration and the loop is unrolled twice,
+// so that the next group's loads overlap this group's multiply-adds without
+// register copies (other warps hide the rest of their latency).
 template <int R, int WP>
 __device__ __forceinline__ void corner_sum(long long (&acc)[R], const int* wbase, const int4* cq, int count) {
     const int groups = count >> 2;
-    if (groups <= 0) return;
-    int4 n0 = __ldg(cq), n1 = __ldg(cq + 1);
+#pragma unroll 2
     for (int g = 0; g < groups; ++g) {
-        const int4 c0 = n0, c1 = n1;
-        if (g + 1 < groups) {
-            n0 = __ldg(cq + 2 * g + 2);
-            n1 = __ldg(cq + 2 * g + 3);
-        }
+        const int4 c0 = __ldg(cq + 2 * g), c1 = __ldg(cq + 2 * g + 1);
         apply_corner<R, WP>(acc, wbase, c0.x, c0.y);
         apply_corner<R, WP>(acc, wbase, c0.z, c0.w);
         apply_corner<R, WP>(acc, wbase, c1.x, c1.y);
@@ -147,13 +147,13 @@ __device__ __forceinline__ void corner_sum(long long (&acc)[R], const int* wbase
     }
 }
 
-// A vertical run of L corners at rows Y .. Y+L-1 of column X (idx = Y*WP + X)
+// A vertical run of L corners at rows Y .. Y+L-1 of column X (idx = 4 (Y*WP + X))
 // with weights g[0..L-1]: offset row r needs the region words of rows
 // Y+r .. Y+r+L-1, so the R rows of a lane share R + L - 1 loads, and each
 // load feeds up to L multiply-adds instead of one.
 template <int R, int WP, int L>
 __device__ __forceinline__ void apply_run(long long (&acc)[R], const int* wbase, int idx, const int (&g)[L]) {
-    const int* w = wbase + idx;
+    const int* w = reinterpret_cast<const int*>(reinterpret_cast<const char*>(wbase) + idx);  // idx in bytes
     int v[R + L - 1];
 #pragma unroll
     for (int i = 0; i < R + L - 1; ++i) v[i] = w[i * WP];
@@ -164,25 +164,19 @@ __device__ __forceinline__ void apply_run(long long (&acc)[R], const int* wbase,
 }
 
 // All runs of length L of one block: `n` records of S int4 units each
-// ({idx, G0, ...}), the next record loaded while the current one is applied.
+// ({idx, G0, ...}), loaded at the top of each iteration (unrolled twice).
 template <int R, int WP, int L, int S>
 __device__ __forceinline__ void run_class(long long (&acc)[R], const int* wbase, const int4* rec, int n) {
-    if (n <= 0) return;
-    int4 nx[S];
-#pragma unroll
-    for (int k = 0; k < S; ++k) nx[k] = __ldg(rec + k);
+#pragma unroll 2
     for (int i = 0; i < n; ++i) {
         int wd[4 * S];
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            wd[4 * k + 0] = nx[k].x;
-            wd[4 * k + 1] = nx[k].y;
-            wd[4 * k + 2] = nx[k].z;
-            wd[4 * k + 3] = nx[k].w;
-        }
-        if (i + 1 < n) {
-#pragma unroll
-            for (int k = 0; k < S; ++k) nx[k] = __ldg(rec + (size_t)(i + 1) * S + k);
+            const int4 q = __ldg(rec + (size_t)i * S + k);
+            wd[4 * k + 0] = q.x;
+            wd[4 * k + 1] = q.y;
+            wd[4 * k + 2] = q.z;
+            wd[4 * k + 3] = q.w;
         }
         int g[L];
 #pragma unroll
