@@ -743,13 +743,11 @@ def run_gpu(args, world, rank, local, pg):
     # one multiply-add per (offset, corner)
     dom_ops = U * V * sum(infos[i]["template_corners"] for i in dom_set)
     Rt = match_tile_rows(U, V)
-    # table words a lane reads per R offsets: R + L - 1 per run of L corners
-    # (the run counts describe the one-block layout; a template of several
-    # blocks uses the 64 x 64 layout, whose runs the plan summary omits)
-    dom_words = None
-    if all(infos[i]["blocks"] == 1 for i in dom_set):
-        dom_words = U * V * sum(infos[i]["runs%d" % L] * (Rt + L - 1) for i in dom_set for L in (8, 4, 2, 1)) / Rt
+    # table words a lane reads per R offset rows: R per record (run, pair or
+    # single corner) plus the rows each record spans beyond its first
+    dom_words = U * V * sum(infos[i]["sum_records"] * Rt + infos[i]["sum_extra_rows"] for i in dom_set) / Rt
     dom_runs = {L: sum(infos[i]["runs%d" % L] for i in dom_set) for L in (8, 4, 2, 1)}
+    dom_runs["pairs"] = sum(infos[i]["pairs"] for i in dom_set)
 
     value = sum_over_ranks(pg, offsets_per_step) / (ms_per_step * 1e-3) / 1e9
     e2e_value = sum_over_ranks(pg, offsets_per_step) / (e2e_ms_step * 1e-3) / 1e9

@@ -638,11 +638,19 @@ typedef struct {
     int32_t runs8;        /* the corners regrouped into vertical runs (consecutive rows of */
     int32_t runs4;        /* one column, all weights nonzero) of 8, 4, 2 and 1 corners: */
     int32_t runs2;        /* 8 runs8 + 4 runs4 + 2 runs2 + runs1 = corners.  The segment-sum */
-    int32_t runs1;        /* kernels read R + L - 1 table words per run of L for R rows. */
+    int32_t runs1;        /* kernels read R + L - 1 table words per run of L for R rows; the
+                             pairs below R + D words for two corners D rows apart. */
     int32_t template_corners; /* nonzero corners of the whole template taken as one block: the
                                  algorithmic multiply-adds per offset (block edges add corners) */
     int32_t wide_blocks;  /* blocks and nonzero corners of the 64 x 64 block layout, which the */
     int32_t wide_corners; /* segment-sum kernels use for templates larger than 64 x 64 */
+    int32_t pairs;        /* first layout: pairs of corners of one column 2 .. 7 rows apart with no
+                             corner between them (8 runs8 + 4 runs4 + 2 runs2 + 2 pairs + runs1 =
+                             corners) */
+    int32_t sum_records;  /* the layout the segment-sum kernel walks (one block, else 64 x 64
+                             blocks): its run, pair and single-corner records ... */
+    int64_t sum_extra_rows; /* ... and the rows they span beyond their first, summed: a lane computing
+                               R offset rows reads sum_records * R + sum_extra_rows table words */
 } sncc_plan_info;
 
 /* Fills *out for seg; SNCC_ERR_UNIFORM when seg has no plan (Ek = 0). */

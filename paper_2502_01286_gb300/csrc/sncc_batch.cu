@@ -54,7 +54,7 @@ struct BatchArgs {
     const int4* pairs;  // {source, template, U, V}
     const TmplDesc* tmpl;
     const int4* blocks;
-    const int4* runblk;  // two per block
+    const int4* runblk;  // RUNBLK_INT4 per block
     const int4* runs;
     const int2* items;  // {pair, (tile row << 16) | tile column}
     int n_items;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(WARPS * 32) batch_match_kernel(const __grid_co
                                        warp, TILE_U + bw + 1);
             __syncthreads();
             const int gb = td.blk_first + b;
-            run_sum<R, WP>(acc, wbase, a.runs, __ldg(a.runblk + 2 * gb), __ldg(a.runblk + 2 * gb + 1));
+            run_sum<R, WP>(acc, wbase, a.runs, a.runblk + RUNBLK_INT4 * gb);
             __syncthreads();
         }
         const int u = u0 + lane;
@@ -341,8 +341,8 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
             const size_t run_words = (L.end_offset - L.runs_offset) / 4;
             for (int k = 0; k < L.nblk; ++k) {
                 for (int j = 0; j < 4; ++j) blocks.push_back(img_blocks[4 * k + j]);
-                for (int j = 0; j < 8; ++j)  // firsts (even words) move by run_base
-                    runblk.push_back(img_runblk[8 * k + j] + ((j % 2 == 0) ? run_base : 0));
+                for (int j = 0; j < 4 * RUNBLK_INT4; ++j)  // firsts (even words) move by run_base
+                    runblk.push_back(img_runblk[4 * RUNBLK_INT4 * k + j] + ((j % 2 == 0) ? run_base : 0));
             }
             runs.insert(runs.end(), img_runs, img_runs + run_words);
             b->tmpl.push_back(d);

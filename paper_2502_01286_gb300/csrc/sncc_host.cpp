@@ -156,7 +156,10 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
     std::vector<int32_t> blocks, corners, runblk, runs;
     L.max_corners = 0;
     L.nonzero_corners = 0;
+    L.records = 0;
+    L.extra_rows = 0;
     for (int k = 0; k < 4; ++k) L.runs[k] = 0;
+    for (int k = 0; k < PAIR_GAPS; ++k) L.pairs[k] = 0;
     for (int by_i = 0; by_i < L.nby; ++by_i) {
         for (int bx_i = 0; bx_i < L.nbx; ++bx_i) {
             const int bx = bx_i * BW, by = by_i * BH;
@@ -194,8 +197,11 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
             // Vertical runs: walking each column downwards, the first
             // uncovered corner starts the longest run of 8, 4 or 2 whose rows
             // all hold corners (and stay inside the block's corner grid);
-            // otherwise it is a single corner.
-            std::vector<int32_t> cls[4];
+            // otherwise it pairs with the next corner of the column if that
+            // one is 2 .. 7 rows below (the rows between them hold none),
+            // else it is a single corner.  A lane then reads each table word
+            // its record spans once for all of the record's corners.
+            std::vector<int32_t> cls[4], pcls[PAIR_GAPS];
             for (int X = 0; X <= bw; ++X) {
                 const int32_t* col = &G[(size_t)X * (bh + 1)];
                 for (int Y = 0; Y <= bh;) {
@@ -214,12 +220,29 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
                             break;
                         }
                     }
+                    ++L.records;
+                    if (k == 3) {  // no run: a pair with the next corner of the column?
+                        int d = 1;
+                        while (d <= PAIR_MAX_GAP && Y + d <= bh && col[Y + d] == 0) ++d;
+                        if (d >= PAIR_MIN_GAP && d <= PAIR_MAX_GAP && Y + d <= bh) {
+                            std::vector<int32_t>& pc = pcls[d - PAIR_MIN_GAP];
+                            pc.push_back(4 * (Y * WP + X));
+                            pc.push_back(col[Y]);
+                            pc.push_back(col[Y + d]);
+                            pc.push_back(0);
+                            ++L.pairs[d - PAIR_MIN_GAP];
+                            L.extra_rows += d;
+                            Y += d + 1;
+                            continue;
+                        }
+                    }
                     const int len = RUN_LEN[k];
                     cls[k].push_back(4 * (Y * WP + X));  // byte offset in the region
                     for (int i = 0; i < len; ++i) cls[k].push_back(col[Y + i]);
                     if (k < 3)  // pad the record to its int4 units
                         while (cls[k].size() % (4 * RUN_INT4[k]) != 0) cls[k].push_back(0);
                     ++L.runs[k];
+                    L.extra_rows += len - 1;
                     Y += len;
                 }
             }
@@ -229,6 +252,12 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
                 runblk.push_back(k < 3 ? (int32_t)(cls[k].size() / (4 * RUN_INT4[k])) : (int32_t)(cls[3].size() / 2));
                 runs.insert(runs.end(), cls[k].begin(), cls[k].end());
             }
+            for (int k = 0; k < PAIR_GAPS; ++k) {
+                runblk.push_back((int32_t)(runs.size() / 4));
+                runblk.push_back((int32_t)(pcls[k].size() / 4));
+                runs.insert(runs.end(), pcls[k].begin(), pcls[k].end());
+            }
+            static_assert(8 + 2 * PAIR_GAPS == 4 * RUNBLK_INT4, "runblk holds the run, single and pair classes");
         }
     }
     L.nblk = (int)(blocks.size() / 4);
@@ -469,6 +498,11 @@ int sncc_get_plan_info(const sncc_segments* seg, sncc_plan_info* out) {
     out->template_corners = p->template_corners;
     out->wide_blocks = p->lay[1].nblk;
     out->wide_corners = p->lay[1].nonzero_corners;
+    out->pairs = 0;
+    for (int k = 0; k < sncc::PAIR_GAPS; ++k) out->pairs += L.pairs[k];
+    const sncc::Layout& S = sncc::layout_for(*p);
+    out->sum_records = S.records;
+    out->sum_extra_rows = S.extra_rows;
     return SNCC_OK;
 }
 

@@ -34,6 +34,8 @@ constexpr int TILE_U = 32;
 constexpr int WARPS = 8;
 constexpr int BLOCK_SINGLE_MAX = 64;  // a template up to 64 x 64 is one block
 constexpr int BLOCK_MULTI = 32;       // first layout of larger templates: 32 x 32 blocks
+constexpr int PAIR_MIN_GAP = 2, PAIR_MAX_GAP = 7;  // gaps of the corner-pair records
+constexpr int PAIR_GAPS = PAIR_MAX_GAP - PAIR_MIN_GAP + 1;
 
 // Host-side matching plan (built by sncc_build_segments).
 //
@@ -52,16 +54,21 @@ constexpr int BLOCK_MULTI = 32;       // first layout of larger templates: 32 x 
 //  * int2 corners[total] = {Y * WP + X, G}, the plain corner list; each
 //    block's list starts on a multiple of 4 corners and is padded with zero
 //    weights to a multiple of 4;
-//  * int4 runblk[2 * nblk] = {first8, n8, first4, n4}, {first2, n2, first1,
-//    n1}: the same corners of block b regrouped into vertical runs (a run of
-//    L corners occupies rows Y .. Y+L-1 of one column X, every weight
-//    nonzero); first* index int4 units of runs[];
+//  * int4 runblk[RUNBLK_INT4 * nblk] = {first8, n8, first4, n4}, {first2,
+//    n2, first1, n1}, {firstp2, np2, firstp3, np3}, {firstp4, np4, firstp5,
+//    np5}, {firstp6, np6, firstp7, np7}: the same corners of block b
+//    regrouped into vertical runs (a run of L corners occupies rows Y ..
+//    Y+L-1 of one column X, every weight nonzero), pairs (two corners of one
+//    column D = 2 .. 7 rows apart, with no corner between them) and single
+//    corners; first* index int4 units of runs[];
 //  * int4 runs[]: a run of 8 is {idx, G0, G1, G2} {G3, G4, G5, G6}
 //    {G7, 0, 0, 0}, a run of 4 is {idx, G0, G1, G2} {G3, 0, 0, 0}, a run of
-//    2 is {idx, G0, G1, 0}, with idx = 4 (Y * WP + X), the byte offset of
-//    the run's first word in the region; single corners are int2 {idx, G},
-//    two per int4, padded with zero weights to a multiple of 4 (n1 counts
-//    corners, not int4 units).
+//    2 is {idx, G0, G1, 0}, a pair is {idx, G0, G1, 0} (G1 at row Y + D),
+//    with idx = 4 (Y * WP + X), the byte offset of the record's first word
+//    in the region; single corners are int2 {idx, G}, two per int4, padded
+//    with zero weights to a multiple of 4 (n1 counts corners, not int4
+//    units).  A lane computing R offset rows reads R + L - 1 words for a run
+//    of L, R + D for a pair and R for a single corner.
 struct Layout {
     int BW = 0, BH = 0;     // block size (the last block in a row/column may be smaller)
     int nbx = 0, nby = 0;   // blocks across / down
@@ -71,6 +78,9 @@ struct Layout {
     int total_corners = 0;  // including the zero-weight padding
     int nonzero_corners = 0;
     int runs[4] = {0, 0, 0, 0};  // vertical runs of 8, 4, 2 and 1 corners, over all blocks
+    int pairs[PAIR_GAPS] = {};   // pairs of corners D = 2 .. 7 rows apart, over all blocks
+    int records = 0;             // run, pair and single-corner records, over all blocks
+    long long extra_rows = 0;    // sum over records of the rows spanned beyond the first
     size_t blocks_offset = 0;
     size_t corners_offset = 0;
     size_t runblk_offset = 0;
@@ -106,6 +116,8 @@ constexpr int DIRECT_MAX = 64;
 // Lengths of the vertical corner runs and the int4 units one run occupies.
 constexpr int RUN_LEN[4] = {8, 4, 2, 1};
 constexpr int RUN_INT4[3] = {3, 2, 1};
+// int4 descriptors per block (runblk), and the pair gaps 2 .. 7.
+constexpr int RUNBLK_INT4 = 5;
 
 Plan* plan_of(const sncc_segments* s);
 

@@ -78,7 +78,7 @@ constexpr int kMaxMultiPlans = SNCC_MULTI_MAX;
 
 struct MatchArgs {
     const int4* blocks;
-    const int4* runblk;  // two per block
+    const int4* runblk;  // RUNBLK_INT4 per block
     const int4* runs;
     int nblk;
     int RH;  // region rows = 8R + BH + 1
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256) match_kernel(const __grid_constant__ CUte
             }
             __syncthreads();
             // ---- corner sum over vertical runs: one multiply-add per (offset, corner) ----
-            run_sum<R, WP>(acc, wbase, runs, __ldg(runblk + 2 * b), __ldg(runblk + 2 * b + 1));
+            run_sum<R, WP>(acc, wbase, runs, runblk + RUNBLK_INT4 * b);
             __syncthreads();  // the region buffer is restaged for the next block
         }
     }

@@ -185,14 +185,48 @@ __device__ __forceinline__ void run_class(long long (&acc)[R], const int* wbase,
     }
 }
 
-// acc[r] += the block's corner sum, from its vertical runs: d0 = {first8,
-// n8, first4, n4}, d1 = {first2, n2, first1, n1} (first* in int4 units of
-// `runs`, n1 single corners in groups of four).
+// Two corners of one column D rows apart, weights g0 (row Y) and g1 (row
+// Y + D): the lane's R rows share R + D region loads.
+template <int R, int WP, int D>
+__device__ __forceinline__ void apply_pair(long long (&acc)[R], const int* wbase, int idx, int g0, int g1) {
+    const int* w = reinterpret_cast<const int*>(reinterpret_cast<const char*>(wbase) + idx);  // idx in bytes
+    int v[R + D];
+#pragma unroll
+    for (int i = 0; i < R + D; ++i) v[i] = (i < R || i >= D) ? w[i * WP] : 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] += (long long)g0 * (long long)v[r];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] += (long long)g1 * (long long)v[r + D];
+}
+
+// All pairs of gap D of one block: `n` records {idx, g0, g1, 0}.
+template <int R, int WP, int D>
+__device__ __forceinline__ void pair_class(long long (&acc)[R], const int* wbase, const int4* rec, int n) {
+#pragma unroll 2
+    for (int i = 0; i < n; ++i) {
+        const int4 q = __ldg(rec + i);
+        apply_pair<R, WP, D>(acc, wbase, q.x, q.y, q.z);
+    }
+}
+
+// acc[r] += the block's corner sum, from its records: desc[0] = {first8,
+// n8, first4, n4}, desc[1] = {first2, n2, first1, n1}, desc[2..4] = {first,
+// n} of the pairs of gap 2 .. 7 (first* in int4 units of `runs`, n1 single
+// corners in groups of four).
 template <int R, int WP>
-__device__ __forceinline__ void run_sum(long long (&acc)[R], const int* wbase, const int4* runs, int4 d0, int4 d1) {
+__device__ __forceinline__ void run_sum(long long (&acc)[R], const int* wbase, const int4* runs, const int4* desc) {
+    static_assert(PAIR_MIN_GAP == 2 && PAIR_MAX_GAP == 7 && RUNBLK_INT4 == 5, "descriptor layout");
+    const int4 d0 = __ldg(desc), d1 = __ldg(desc + 1), d2 = __ldg(desc + 2), d3 = __ldg(desc + 3),
+               d4 = __ldg(desc + 4);
     run_class<R, WP, 8, 3>(acc, wbase, runs + d0.x, d0.y);
     run_class<R, WP, 4, 2>(acc, wbase, runs + d0.z, d0.w);
     run_class<R, WP, 2, 1>(acc, wbase, runs + d1.x, d1.y);
+    pair_class<R, WP, 2>(acc, wbase, runs + d2.x, d2.y);
+    pair_class<R, WP, 3>(acc, wbase, runs + d2.z, d2.w);
+    pair_class<R, WP, 4>(acc, wbase, runs + d3.x, d3.y);
+    pair_class<R, WP, 5>(acc, wbase, runs + d3.z, d3.w);
+    pair_class<R, WP, 6>(acc, wbase, runs + d4.x, d4.y);
+    pair_class<R, WP, 7>(acc, wbase, runs + d4.z, d4.w);
     corner_sum<R, WP>(acc, wbase, runs + d1.z, d1.w);
 }
 

@@ -127,7 +127,8 @@ def test_quantisation_error_bound_is_small(sncc):
 
 
 def test_vertical_runs_partition_the_corners(sncc):
-    # every nonzero corner lands in exactly one run of 8, 4, 2 or 1
+    # every nonzero corner lands in exactly one run of 8, 4, 2 or 1 or one
+    # pair of corners 2 .. 7 rows apart
     yy, xx = np.mgrid[0:19, 0:21]
     checker = ((xx + yy) % 2 * 200).astype(np.uint8)
     cases = [synth.case_hd(M=200, N=200).t, synth.case_plain().t, checker,
@@ -138,11 +139,19 @@ def test_vertical_runs_partition_the_corners(sncc):
             if seg.Ek == 0.0:
                 continue
             pi = seg.plan_info()
-            assert 8 * pi["runs8"] + 4 * pi["runs4"] + 2 * pi["runs2"] + pi["runs1"] == pi["corners"]
+            assert 8 * pi["runs8"] + 4 * pi["runs4"] + 2 * pi["runs2"] + 2 * pi["pairs"] + pi["runs1"] == \
+                pi["corners"]
     # a 1-pixel checkerboard puts a corner on every point of the 22 x 20
     # corner grid: each column of 20 splits into runs of 8, 8 and 4
     pi = sncc.build_segments(checker, 1.0).plan_info()
     assert (pi["corners"], pi["runs8"], pi["runs4"], pi["runs2"], pi["runs1"]) == (440, 44, 22, 0, 0)
+    # three horizontal bands of height 3 (values 10, 200, 50) on a 4 x 9
+    # template: corners only in columns 0 and 4, at rows 0, 3, 6 and 9, so
+    # each column gives two pairs 3 rows apart; each pair spans 3 extra rows
+    bands = np.repeat(np.array([10, 200, 50], np.uint8), 3)[:, None] * np.ones((1, 4), np.uint8)
+    pi = sncc.build_segments(bands, 1.0).plan_info()
+    assert (pi["corners"], pi["pairs"], pi["runs8"], pi["runs4"], pi["runs2"], pi["runs1"]) == (8, 4, 0, 0, 0, 0)
+    assert (pi["sum_records"], pi["sum_extra_rows"]) == (4, 12)
 
 
 @pytest.mark.parametrize("W,H", [(1, 64), (64, 1), (3, 256), (256, 3), (65, 64), (64, 65), (700, 2), (2, 700)])
@@ -155,7 +164,7 @@ def test_plan_shapes_thin_and_edge_templates(sncc, W, H):
     if not seg.Ek > 0:
         pytest.skip("uniform approximation")
     pi = seg.plan_info()
-    assert 8 * pi["runs8"] + 4 * pi["runs4"] + 2 * pi["runs2"] + pi["runs1"] == pi["corners"]
+    assert 8 * pi["runs8"] + 4 * pi["runs4"] + 2 * pi["runs2"] + 2 * pi["pairs"] + pi["runs1"] == pi["corners"]
     if W <= 64 and H <= 64:
         assert pi["blocks"] == 1 and pi["wide_blocks"] == 1 and pi["corners"] == pi["template_corners"]
     else:
