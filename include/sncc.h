@@ -645,12 +645,15 @@ typedef struct {
     int32_t wide_blocks;  /* blocks and nonzero corners of the 64 x 64 block layout, which the */
     int32_t wide_corners; /* segment-sum kernels use for templates larger than 64 x 64 */
     int32_t pairs;        /* first layout: pairs of corners of one column 2 .. 7 rows apart with no
-                             corner between them (8 runs8 + 4 runs4 + 2 runs2 + 2 pairs + runs1 =
-                             corners) */
+                             corner between them */
     int32_t sum_records;  /* the layout the segment-sum kernel walks (one block, else 64 x 64
                              blocks): its run, pair and single-corner records ... */
     int64_t sum_extra_rows; /* ... and the rows they span beyond their first, summed: a lane computing
                                R offset rows reads sum_records * R + sum_extra_rows table words */
+    int32_t strided8;     /* first layout: runs of 8, 4 and 3 corners on every second row of one */
+    int32_t strided4;     /* column (none between), and patterns of corners at rows Y, Y+2, Y+3: */
+    int32_t strided3;     /* 8 runs8 + 4 runs4 + 2 runs2 + 2 pairs + runs1 + 8 strided8 + */
+    int32_t t023;         /* 4 strided4 + 3 strided3 + 3 t023 = corners */
 } sncc_plan_info;
 
 /* Fills *out for seg; SNCC_ERR_UNIFORM when seg has no plan (Ek = 0). */

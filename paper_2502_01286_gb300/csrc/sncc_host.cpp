@@ -160,6 +160,8 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
     L.extra_rows = 0;
     for (int k = 0; k < 4; ++k) L.runs[k] = 0;
     for (int k = 0; k < PAIR_GAPS; ++k) L.pairs[k] = 0;
+    for (int k = 0; k < 3; ++k) L.runs2[k] = 0;
+    L.t21 = 0;
     for (int by_i = 0; by_i < L.nby; ++by_i) {
         for (int bx_i = 0; bx_i < L.nbx; ++bx_i) {
             const int bx = bx_i * BW, by = by_i * BH;
@@ -197,11 +199,14 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
             // Vertical runs: walking each column downwards, the first
             // uncovered corner starts the longest run of 8, 4 or 2 whose rows
             // all hold corners (and stay inside the block's corner grid);
-            // otherwise it pairs with the next corner of the column if that
-            // one is 2 .. 7 rows below (the rows between them hold none),
-            // else it is a single corner.  A lane then reads each table word
-            // its record spans once for all of the record's corners.
-            std::vector<int32_t> cls[4], pcls[PAIR_GAPS];
+            // otherwise the longest stride-2 run of 8, 4 or 3 (corners every
+            // second row, none between), or corners at rows Y, Y+2, Y+3
+            // (none at Y+1), or it pairs with the next corner of the column
+            // if that one is 2 .. 7 rows below (the rows between them hold
+            // none), else it is a single corner.  A lane then reads each
+            // table word its record spans once for all of the record's
+            // corners.
+            std::vector<int32_t> cls[4], pcls[PAIR_GAPS], s2cls[3], tcls;
             for (int X = 0; X <= bw; ++X) {
                 const int32_t* col = &G[(size_t)X * (bh + 1)];
                 for (int Y = 0; Y <= bh;) {
@@ -221,7 +226,39 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
                         }
                     }
                     ++L.records;
-                    if (k == 3) {  // no run: a pair with the next corner of the column?
+                    if (k == 3) {  // no run: a stride-2 run?
+                        int k2 = -1;
+                        for (int c = 0; c < 3 && k2 < 0; ++c) {
+                            const int len = RUN2_LEN[c];
+                            if (Y + 2 * (len - 1) > bh) continue;
+                            bool ok = true;
+                            for (int i = 0; i < len && ok; ++i) ok = col[Y + 2 * i] != 0;
+                            for (int i = 0; i + 1 < len && ok; ++i) ok = col[Y + 2 * i + 1] == 0;
+                            if (ok) k2 = c;
+                        }
+                        if (k2 >= 0) {
+                            const int len = RUN2_LEN[k2];
+                            std::vector<int32_t>& sc = s2cls[k2];
+                            sc.push_back(4 * (Y * WP + X));
+                            for (int i = 0; i < len; ++i) sc.push_back(col[Y + 2 * i]);
+                            while (sc.size() % 4 != 0) sc.push_back(0);
+                            ++L.runs2[k2];
+                            L.extra_rows += 2 * (len - 1);
+                            Y += 2 * (len - 1) + 1;
+                            continue;
+                        }
+                        if (Y + 3 <= bh && col[Y + 1] == 0 && col[Y + 2] != 0 && col[Y + 3] != 0) {
+                            tcls.push_back(4 * (Y * WP + X));
+                            tcls.push_back(col[Y]);
+                            tcls.push_back(col[Y + 2]);
+                            tcls.push_back(col[Y + 3]);
+                            ++L.t21;
+                            L.extra_rows += 3;
+                            Y += 4;
+                            continue;
+                        }
+                    }
+                    if (k == 3) {  // a pair with the next corner of the column?
                         int d = 1;
                         while (d <= PAIR_MAX_GAP && Y + d <= bh && col[Y + d] == 0) ++d;
                         if (d >= PAIR_MIN_GAP && d <= PAIR_MAX_GAP && Y + d <= bh) {
@@ -257,7 +294,17 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
                 runblk.push_back((int32_t)(pcls[k].size() / 4));
                 runs.insert(runs.end(), pcls[k].begin(), pcls[k].end());
             }
-            static_assert(8 + 2 * PAIR_GAPS == 4 * RUNBLK_INT4, "runblk holds the run, single and pair classes");
+            for (int k = 0; k < 3; ++k) {  // stride-2 runs: records of RUN_INT4[k] int4 units
+                runblk.push_back((int32_t)(runs.size() / 4));
+                const int units = k == 0 ? 3 : (k == 1 ? 2 : 1);
+                runblk.push_back((int32_t)(s2cls[k].size() / (4 * units)));
+                while (s2cls[k].size() % (4 * units) != 0) s2cls[k].push_back(0);
+                runs.insert(runs.end(), s2cls[k].begin(), s2cls[k].end());
+            }
+            runblk.push_back((int32_t)(runs.size() / 4));
+            runblk.push_back((int32_t)(tcls.size() / 4));
+            runs.insert(runs.end(), tcls.begin(), tcls.end());
+            static_assert(8 + 2 * PAIR_GAPS + 8 == 4 * RUNBLK_INT4, "runblk holds every record class");
         }
     }
     L.nblk = (int)(blocks.size() / 4);
@@ -503,6 +550,10 @@ int sncc_get_plan_info(const sncc_segments* seg, sncc_plan_info* out) {
     const sncc::Layout& S = sncc::layout_for(*p);
     out->sum_records = S.records;
     out->sum_extra_rows = S.extra_rows;
+    out->strided8 = L.runs2[0];
+    out->strided4 = L.runs2[1];
+    out->strided3 = L.runs2[2];
+    out->t023 = L.t21;
     return SNCC_OK;
 }
 

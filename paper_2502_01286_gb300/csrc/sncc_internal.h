@@ -56,14 +56,18 @@ constexpr int PAIR_GAPS = PAIR_MAX_GAP - PAIR_MIN_GAP + 1;
 //    weights to a multiple of 4;
 //  * int4 runblk[RUNBLK_INT4 * nblk] = {first8, n8, first4, n4}, {first2,
 //    n2, first1, n1}, {firstp2, np2, firstp3, np3}, {firstp4, np4, firstp5,
-//    np5}, {firstp6, np6, firstp7, np7}: the same corners of block b
-//    regrouped into vertical runs (a run of L corners occupies rows Y ..
-//    Y+L-1 of one column X, every weight nonzero), pairs (two corners of one
-//    column D = 2 .. 7 rows apart, with no corner between them) and single
-//    corners; first* index int4 units of runs[];
+//    np5}, {firstp6, np6, firstp7, np7}, {firsts8, ns8, firsts4, ns4},
+//    {firsts3, ns3, firstt, nt}: the same corners of block b regrouped into
+//    vertical runs (a run of L corners occupies rows Y .. Y+L-1 of one
+//    column X, every weight nonzero), stride-2 runs of 8, 4 and 3 (rows Y,
+//    Y+2, .., none between), the rows-(Y, Y+2, Y+3) pattern, pairs (two
+//    corners of one column D = 2 .. 7 rows apart, with no corner between
+//    them) and single corners; first* index int4 units of runs[];
 //  * int4 runs[]: a run of 8 is {idx, G0, G1, G2} {G3, G4, G5, G6}
 //    {G7, 0, 0, 0}, a run of 4 is {idx, G0, G1, G2} {G3, 0, 0, 0}, a run of
 //    2 is {idx, G0, G1, 0}, a pair is {idx, G0, G1, 0} (G1 at row Y + D),
+//    stride-2 runs are laid out as runs of the same length, the (0, 2, 3)
+//    pattern is {idx, G0, G1, G2},
 //    with idx = 4 (Y * WP + X), the byte offset of the record's first word
 //    in the region; single corners are int2 {idx, G}, two per int4, padded
 //    with zero weights to a multiple of 4 (n1 counts corners, not int4
@@ -79,6 +83,8 @@ struct Layout {
     int nonzero_corners = 0;
     int runs[4] = {0, 0, 0, 0};  // vertical runs of 8, 4, 2 and 1 corners, over all blocks
     int pairs[PAIR_GAPS] = {};   // pairs of corners D = 2 .. 7 rows apart, over all blocks
+    int runs2[3] = {0, 0, 0};    // stride-2 runs of 8, 4 and 3 corners, over all blocks
+    int t21 = 0;                 // rows-(0, 2, 3) patterns, over all blocks
     int records = 0;             // run, pair and single-corner records, over all blocks
     long long extra_rows = 0;    // sum over records of the rows spanned beyond the first
     size_t blocks_offset = 0;
@@ -117,7 +123,9 @@ constexpr int DIRECT_MAX = 64;
 constexpr int RUN_LEN[4] = {8, 4, 2, 1};
 constexpr int RUN_INT4[3] = {3, 2, 1};
 // int4 descriptors per block (runblk), and the pair gaps 2 .. 7.
-constexpr int RUNBLK_INT4 = 5;
+constexpr int RUNBLK_INT4 = 7;
+// Stride-2 runs (corners every second row, none between) of 8, 4 and 3.
+constexpr int RUN2_LEN[3] = {8, 4, 3};
 
 Plan* plan_of(const sncc_segments* s);
 

@@ -147,25 +147,51 @@ __device__ __forceinline__ void corner_sum(long long (&acc)[R], const int* wbase
     }
 }
 
-// A vertical run of L corners at rows Y .. Y+L-1 of column X (idx = 4 (Y*WP + X))
-// with weights g[0..L-1]: offset row r needs the region words of rows
-// Y+r .. Y+r+L-1, so the R rows of a lane share R + L - 1 loads, and each
-// load feeds up to L multiply-adds instead of one.
-template <int R, int WP, int L>
+// A vertical run of L corners at rows Y, Y+T, .., Y+(L-1)T of column X
+// (stride T = 1 or 2, idx = 4 (Y*WP + X)) with weights g[0..L-1]: offset
+// row r needs the region words of rows Y+r+lT, so the R rows of a lane share
+// R + (L-1)T loads, and each load feeds up to L multiply-adds instead of one.
+template <int R, int WP, int L, int T = 1>
 __device__ __forceinline__ void apply_run(long long (&acc)[R], const int* wbase, int idx, const int (&g)[L]) {
     const int* w = reinterpret_cast<const int*>(reinterpret_cast<const char*>(wbase) + idx);  // idx in bytes
-    int v[R + L - 1];
+    int v[R + (L - 1) * T];
 #pragma unroll
-    for (int i = 0; i < R + L - 1; ++i) v[i] = w[i * WP];
+    for (int i = 0; i < R + (L - 1) * T; ++i) v[i] = w[i * WP];
 #pragma unroll
     for (int l = 0; l < L; ++l)
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] += (long long)g[l] * (long long)v[r + l];
+        for (int r = 0; r < R; ++r) acc[r] += (long long)g[l] * (long long)v[r + l * T];
 }
 
-// All runs of length L of one block: `n` records of S int4 units each
-// ({idx, G0, ...}), loaded at the top of each iteration (unrolled twice).
-template <int R, int WP, int L, int S>
+// Corners at rows Y, Y+2 and Y+3 of one column (weights g0, g1, g2): R + 3
+// shared loads for the three.
+template <int R, int WP>
+__device__ __forceinline__ void apply_t21(long long (&acc)[R], const int* wbase, int idx, int g0, int g1, int g2) {
+    const int* w = reinterpret_cast<const int*>(reinterpret_cast<const char*>(wbase) + idx);  // idx in bytes
+    int v[R + 3];
+#pragma unroll
+    for (int i = 0; i < R + 3; ++i) v[i] = w[i * WP];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] += (long long)g0 * (long long)v[r];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] += (long long)g1 * (long long)v[r + 2];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] += (long long)g2 * (long long)v[r + 3];
+}
+
+// All records {idx, g0, g1, g2} of the rows-(0, 2, 3) pattern of one block.
+template <int R, int WP>
+__device__ __forceinline__ void t21_class(long long (&acc)[R], const int* wbase, const int4* rec, int n) {
+#pragma unroll 2
+    for (int i = 0; i < n; ++i) {
+        const int4 q = __ldg(rec + i);
+        apply_t21<R, WP>(acc, wbase, q.x, q.y, q.z, q.w);
+    }
+}
+
+// All runs of length L (stride T) of one block: `n` records of S int4 units
+// each ({idx, G0, ...}), loaded at the top of each iteration (unrolled twice).
+template <int R, int WP, int L, int S, int T = 1>
 __device__ __forceinline__ void run_class(long long (&acc)[R], const int* wbase, const int4* rec, int n) {
 #pragma unroll 2
     for (int i = 0; i < n; ++i) {
@@ -181,7 +207,7 @@ __device__ __forceinline__ void run_class(long long (&acc)[R], const int* wbase,
         int g[L];
 #pragma unroll
         for (int l = 0; l < L; ++l) g[l] = wd[1 + l];
-        apply_run<R, WP, L>(acc, wbase, wd[0], g);
+        apply_run<R, WP, L, T>(acc, wbase, wd[0], g);
     }
 }
 
@@ -211,16 +237,22 @@ __device__ __forceinline__ void pair_class(long long (&acc)[R], const int* wbase
 
 // acc[r] += the block's corner sum, from its records: desc[0] = {first8,
 // n8, first4, n4}, desc[1] = {first2, n2, first1, n1}, desc[2..4] = {first,
-// n} of the pairs of gap 2 .. 7 (first* in int4 units of `runs`, n1 single
-// corners in groups of four).
+// n} of the pairs of gap 2 .. 7, desc[5] = {first, n} of the stride-2 runs
+// of 8 and 4, desc[6] = {first, n} of the stride-2 runs of 3 and of the
+// rows-(0, 2, 3) pattern (first* in int4 units of `runs`, n1 single corners
+// in groups of four).
 template <int R, int WP>
 __device__ __forceinline__ void run_sum(long long (&acc)[R], const int* wbase, const int4* runs, const int4* desc) {
-    static_assert(PAIR_MIN_GAP == 2 && PAIR_MAX_GAP == 7 && RUNBLK_INT4 == 5, "descriptor layout");
+    static_assert(PAIR_MIN_GAP == 2 && PAIR_MAX_GAP == 7 && RUNBLK_INT4 == 7, "descriptor layout");
     const int4 d0 = __ldg(desc), d1 = __ldg(desc + 1), d2 = __ldg(desc + 2), d3 = __ldg(desc + 3),
-               d4 = __ldg(desc + 4);
+               d4 = __ldg(desc + 4), d5 = __ldg(desc + 5), d6 = __ldg(desc + 6);
     run_class<R, WP, 8, 3>(acc, wbase, runs + d0.x, d0.y);
     run_class<R, WP, 4, 2>(acc, wbase, runs + d0.z, d0.w);
     run_class<R, WP, 2, 1>(acc, wbase, runs + d1.x, d1.y);
+    run_class<R, WP, 8, 3, 2>(acc, wbase, runs + d5.x, d5.y);
+    run_class<R, WP, 4, 2, 2>(acc, wbase, runs + d5.z, d5.w);
+    run_class<R, WP, 3, 1, 2>(acc, wbase, runs + d6.x, d6.y);
+    t21_class<R, WP>(acc, wbase, runs + d6.z, d6.w);
     pair_class<R, WP, 2>(acc, wbase, runs + d2.x, d2.y);
     pair_class<R, WP, 3>(acc, wbase, runs + d2.z, d2.w);
     pair_class<R, WP, 4>(acc, wbase, runs + d3.x, d3.y);

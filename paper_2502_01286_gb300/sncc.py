@@ -67,7 +67,8 @@ class PlanInfo(C.Structure):
                 ("corners", C.c_int32), ("max_corners", C.c_int32), ("Q0", C.c_int64), ("runs8", C.c_int32),
                 ("runs4", C.c_int32), ("runs2", C.c_int32), ("runs1", C.c_int32), ("template_corners", C.c_int32),
                 ("wide_blocks", C.c_int32), ("wide_corners", C.c_int32), ("pairs", C.c_int32),
-                ("sum_records", C.c_int32), ("sum_extra_rows", C.c_int64)]
+                ("sum_records", C.c_int32), ("sum_extra_rows", C.c_int64), ("strided8", C.c_int32),
+                ("strided4", C.c_int32), ("strided3", C.c_int32), ("t023", C.c_int32)]
 
 
 class MatchT(C.Structure):

@@ -126,6 +126,12 @@ def test_quantisation_error_bound_is_small(sncc):
         assert 0 < seg.err_bound < 5e-6
 
 
+def covered(pi):
+    """Corners in the plan's records (runs, stride-2 runs, patterns, pairs, singles)."""
+    return (8 * pi["runs8"] + 4 * pi["runs4"] + 2 * pi["runs2"] + 2 * pi["pairs"] + pi["runs1"] +
+            8 * pi["strided8"] + 4 * pi["strided4"] + 3 * pi["strided3"] + 3 * pi["t023"])
+
+
 def test_vertical_runs_partition_the_corners(sncc):
     # every nonzero corner lands in exactly one run of 8, 4, 2 or 1 or one
     # pair of corners 2 .. 7 rows apart
@@ -139,8 +145,7 @@ def test_vertical_runs_partition_the_corners(sncc):
             if seg.Ek == 0.0:
                 continue
             pi = seg.plan_info()
-            assert 8 * pi["runs8"] + 4 * pi["runs4"] + 2 * pi["runs2"] + 2 * pi["pairs"] + pi["runs1"] == \
-                pi["corners"]
+            assert covered(pi) == pi["corners"]
     # a 1-pixel checkerboard puts a corner on every point of the 22 x 20
     # corner grid: each column of 20 splits into runs of 8, 8 and 4
     pi = sncc.build_segments(checker, 1.0).plan_info()
@@ -152,6 +157,21 @@ def test_vertical_runs_partition_the_corners(sncc):
     pi = sncc.build_segments(bands, 1.0).plan_info()
     assert (pi["corners"], pi["pairs"], pi["runs8"], pi["runs4"], pi["runs2"], pi["runs1"]) == (8, 4, 0, 0, 0, 0)
     assert (pi["sum_records"], pi["sum_extra_rows"]) == (4, 12)
+    # bands of height 2 (values 10, 200, 50, 120) on a 4 x 8 template: corners
+    # in columns 0 and 4 at rows 0, 2, 4, 6, 8: a stride-2 run of 4 (rows 0 -
+    # 6, 6 extra rows) and a single corner per column
+    bands2 = np.repeat(np.array([10, 200, 50, 120], np.uint8), 2)[:, None] * np.ones((1, 4), np.uint8)
+    pi = sncc.build_segments(bands2, 1.0).plan_info()
+    assert (pi["corners"], pi["strided4"], pi["runs1"], pi["pairs"], pi["strided8"], pi["strided3"]) == \
+        (10, 2, 2, 0, 0, 0)
+    assert (pi["sum_records"], pi["sum_extra_rows"]) == (4, 12)
+    # bands of heights 2, 1, 1 on a 3 x 4 template: corners in columns 0
+    # and 3 at rows 0, 2, 3 and 4; rows 0, 2, 3 form the (Y, Y+2, Y+3)
+    # pattern (3 extra rows) and row 4 is a single corner, per column
+    t3 = np.array([[10] * 3, [10] * 3, [200] * 3, [60] * 3], np.uint8)
+    pi = sncc.build_segments(t3, 1.0).plan_info()
+    assert (pi["corners"], pi["t023"], pi["runs1"], covered(pi)) == (8, 2, 2, 8)
+    assert (pi["sum_records"], pi["sum_extra_rows"]) == (4, 6)
 
 
 @pytest.mark.parametrize("W,H", [(1, 64), (64, 1), (3, 256), (256, 3), (65, 64), (64, 65), (700, 2), (2, 700)])
@@ -164,7 +184,7 @@ def test_plan_shapes_thin_and_edge_templates(sncc, W, H):
     if not seg.Ek > 0:
         pytest.skip("uniform approximation")
     pi = seg.plan_info()
-    assert 8 * pi["runs8"] + 4 * pi["runs4"] + 2 * pi["runs2"] + 2 * pi["pairs"] + pi["runs1"] == pi["corners"]
+    assert covered(pi) == pi["corners"]
     if W <= 64 and H <= 64:
         assert pi["blocks"] == 1 and pi["wide_blocks"] == 1 and pi["corners"] == pi["template_corners"]
     else:
