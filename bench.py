@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["sncc", "reference"], default="sncc")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="texture")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["crossover"], default="texture")
     ap.add_argument("--shard", choices=["replicas", "bands"], default="replicas",
                     help="N > 1: each rank its own problem (replicas, weak scaling) or one source split into bands "
                          "of offset rows with an H - 1 row halo (bands, strong scaling)")
@@ -277,6 +277,10 @@ def run_reference(args, world, rank, pg):
     """The reference arm: the FP64 CPU oracle as it stands, timed on the host
     cores, each step a bounded sample of the same workload."""
     if rank != 0:
+        return
+    if args.workload == "crossover":
+        print(json.dumps({"impl": "reference", "unavailable": "the crossover sweep compares two GPU kernels; "
+                                                              "the oracle's timing is reported per workload"}))
         return
     if args.workload == "batch":
         return run_reference_batch(args)
@@ -1024,6 +1028,122 @@ def run_gpu_batch(args, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+CROSSOVER_SIGMAS = (2.75, 3.0, 3.25, 3.5, 3.75, 4.0, 4.25, 4.5, 5.0, 6.0, 8.0, 12.0, 20.0, 40.0)
+
+
+def run_gpu_crossover(args, world, rank, local, pg):
+    """Where segmented NCC stops beating exact NCC on this GPU: the 4096^2 /
+    256^2 texture workload at std thresholds from 2.75 to 40, so that the
+    approximation's corners per template pixel, P / (W H), run from about 0.4
+    down to 0.01.  At each threshold: the whole path (sum tables, coarse
+    pass, exact refine, one graph per step) timed with CUDA events after an
+    L2 flush, the same-GPU exact comparator, and max |rho_seg - rho_exact|
+    over every offset (the accuracy the speedup is bought with)."""
+    import torch
+    from paper_2502_01286_gb300 import build as lib_build
+    if rank == 0 or not os.path.exists(lib_build.LIB):
+        lib_build.build()
+    barrier(pg)
+    from paper_2502_01286_gb300 import sncc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    case, _, precision = make_case("texture", rank)
+    N, M = case.f.shape
+    H, W = case.t.shape
+    U, V = M - W + 1, N - H + 1
+    fd = torch.as_tensor(case.f).to(dev)
+    td = torch.as_tensor(case.t).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    tables = sncc.alloc_tables(M, N, None, dev)
+    ws = sncc.integral_workspace(M, N, dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for k in range(reps):
+            flush.fill_(k & 0xff)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    sncc.integral(fd, tables, workspace=ws)
+    exact_rho = torch.empty((V, U), dtype=torch.float32, device=dev)
+    seg0 = sncc.build_segments(case.t, 5.0)
+    exact_ms = timed(lambda: sncc.exact_map(fd, td, seg0.T, seg0.T2, tables, exact_rho), 10)
+    exact_value = U * V / (exact_ms * 1e-3) / 1e9
+    clocks = ClockSampler(local)
+    clocks.mark_start()
+    sweep = []
+    for sigma in CROSSOVER_SIGMAS:
+        t0 = time.perf_counter()
+        seg = sncc.build_segments(case.t, sigma)
+        prep_s = time.perf_counter() - t0
+        if not seg.Ek > 0:
+            continue
+        pi = seg.plan_info()
+        plan = sncc.upload_plan(seg, dev)
+        mb = sncc.alloc_match(M, N, W, H, U * V, True, dev)
+        rb = sncc.alloc_refine(M, N, W, H, 1 << 16, dev)
+        tau = precision * seg.rho_max
+
+        def step():
+            sncc.integral(fd, tables, workspace=ws)
+            sncc.match(seg, plan, tables, tau, mb)
+            sncc.refine(fd, td, seg, mb, precision, rb)
+
+        g = sncc.capture_graph(step)
+        reps = 5
+        step_ms = timed(g.replay, reps)
+        match_ms = timed(lambda: sncc.match(seg, plan, tables, tau, mb), reps)
+        g.replay()
+        torch.cuda.synchronize()
+        value = U * V / (step_ms * 1e-3) / 1e9
+        sweep.append({"sigma_max": sigma, "K": seg.K, "corners": pi["template_corners"],
+                      "corners_per_pixel": pi["template_corners"] / float(W * H), "prep_s": prep_s,
+                      "step_ms": step_ms, "match_ms": match_ms, "value": value,
+                      "speedup_vs_exact": value / exact_value,
+                      "max_abs_dncc_vs_exact": float((mb.rho - exact_rho).abs().max().item()),
+                      "candidates": int(mb.count.item()), "matches": int(rb.nout.item()),
+                      "status": int(mb.status.item())})
+        del g, mb, rb, plan
+    clocks.mark_end()
+    clk = clocks.stop()
+    # the crossover: where the speedup falls through 1, interpolated in
+    # log(corners per pixel) between the two bracketing thresholds
+    cross = None
+    pts = sorted(sweep, key=lambda e: e["corners_per_pixel"])
+    for lo, hi in zip(pts, pts[1:]):
+        if lo["speedup_vs_exact"] >= 1.0 > hi["speedup_vs_exact"]:
+            import math
+            t = (math.log(lo["speedup_vs_exact"])) / (math.log(lo["speedup_vs_exact"]) - math.log(hi["speedup_vs_exact"]))
+            cpp = math.exp(math.log(lo["corners_per_pixel"]) +
+                           t * (math.log(hi["corners_per_pixel"]) - math.log(lo["corners_per_pixel"])))
+            cross = {"corners_per_pixel": cpp, "corners": cpp * W * H,
+                     "between_sigma": [lo["sigma_max"], hi["sigma_max"]], "between_K": [lo["K"], hi["K"]],
+                     "how": "speedup interpolated linearly in log(speedup) against log(P / (W H))"}
+    ref = next((e for e in sweep if e["sigma_max"] == 5.0), sweep[0])
+    line = {"metric": METRIC, "value": ref["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ref["step_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "crossover-texture-4096x4096-t256x256-sigma%g-%g" % (CROSSOVER_SIGMAS[0],
+                                                                                         CROSSOVER_SIGMAS[-1]),
+                       "precision": precision, "l2": "flushed before every timed call (256 MiB write)",
+                       "value_is": "the sigma 5 point of the sweep"},
+            "exact_ncc": {"value": exact_value, "unit": UNIT, "ms": exact_ms,
+                          "kernel": "direct integer correlation, dp4a (4 byte MACs per instruction)"},
+            "sweep": sweep, "crossover": cross, "clocks": clk,
+            "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS + 1 + sncc.REFINE_KERNELS)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_gpu_diff(args, world, rank, local, pg):
     """Differentiation workload: loss between segmented and exact NCC over a
     512 x 512 float source (48 x 48 template, segmentation at std 12), one
@@ -1188,6 +1308,8 @@ def main():
         run_reference(args, world, rank, pg)
     elif args.workload == "diff":
         run_gpu_diff(args, world, rank, local, pg)
+    elif args.workload == "crossover":
+        run_gpu_crossover(args, world, rank, local, pg)
     elif args.workload == "batch":
         run_gpu_batch(args, world, rank, local, pg)
     else:

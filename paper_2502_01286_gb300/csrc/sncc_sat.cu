@@ -40,7 +40,9 @@ constexpr int kLaneCols = 8;                  // output columns per lane
 constexpr int kTileCols = 32 * kLaneCols;     // output columns per warp tile
 constexpr int kMaxTiles = 16384 / kTileCols;  // tiles of the widest table (M + 1 <= 16384)
 constexpr int kMaxR = 64;                     // rows per band at most
-constexpr int kTargetTiles = 32 * 152;        // about 32 warp tiles (band x 256 columns) per SM
+constexpr int kTargetTiles = 4864;           // warp tiles (band x 256 columns) in all: about 32 per SM
+                                              // of a 152-SM part; fixed, so that the workspace size
+                                              // depends on the source size alone
 
 struct SatGeometry {
     int R;   // rows per band
