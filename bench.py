@@ -903,7 +903,14 @@ def run_gpu_batch(args, world, rank, local, pg):
     prep_s = time.perf_counter() - t_prep
     info = b.info()
     fd = [torch.as_tensor(f).to(dev) for f in srcs]
+    t_tune = time.perf_counter()
     tune = b.autotune(fd, reps=2)
+    tune_s = time.perf_counter() - t_tune
+    buckets = [{"bucket": bb["bucket"], "size_class": bb["size_class"], "density_class": bb["density_class"],
+                "templates": bb["templates"], "pairs": bb["pairs"], "tile_rows": bb["tile_rows"],
+                "block": bb["block"],
+                "ms_per_variant": {"R%d-b%d" % key: ms for key, ms in tune.get(bb["bucket"], {}).items()}}
+               for bb in b.buckets() if bb["pairs"]]
     g = b.capture(fd)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
@@ -1007,8 +1014,11 @@ def run_gpu_batch(args, world, rank, local, pg):
         "config": {"workload": "batch-8x1024x1024-64templates-16to256-sigma4to25", "sources": [len(srcs), M, N],
                    "templates": len(tl), "pairs": len(srcs) * len(tl), "offsets_per_step": info["offsets"],
                    "precision": PRECISION, "l2": "flushed between steps (256 MiB write)",
-                   "launch": "one CUDA graph: sum tables x8, one persistent coarse launch, refine, sort",
-                   "tile_rows": info["tile_rows"], "autotune_ms": tune},
+                   "launch": "one CUDA graph: sum tables x8, one persistent coarse launch per variant in use, "
+                             "refine, sort",
+                   "buckets": buckets, "autotune_s": tune_s,
+                   "autotune": "per template bucket (size class x corner density class), the fastest of tile "
+                               "height R in {8, 4, 2} x template block edge {64, 32}, each bucket timed alone"},
         "exact_ncc": {"value": info["offsets"] / (exact_ms * 1e-3) / 1e9, "unit": UNIT, "ms": exact_ms,
                       "kernel": "direct integer correlation, dp4a (4 byte MACs per instruction), one launch "
                                 "per pair", "roofline": exact_roofline(exact_macs, exact_ms, ceil)},
@@ -1019,7 +1029,9 @@ def run_gpu_batch(args, world, rank, local, pg):
         "e2e": {"value": offsets / (e2e_ms_step * 1e-3) / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": sum(f.size for f in srcs), "d2h_bytes_per_step": d2h / e2e_steps,
                 "ms_per_step": e2e_ms_step},
-        "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS * len(srcs) + 1 + sncc.REFINE_KERNELS),
+        "gpu_launches": args.steps * (sncc.INTEGRAL_KERNELS * len(srcs) + len({(x["tile_rows"], x["block"])
+                                                                                for x in buckets}) +
+                                      sncc.REFINE_KERNELS),
         "clocks": clk, "wall_s_timed": wall,
     }
     if cpu is not None:

@@ -461,6 +461,13 @@ void sncc_pipeline_destroy(sncc_pipeline p);
 /* ------------------------------------------------------------------ */
 
 #define SNCC_BATCH_MAX_SOURCES 16
+/* Template buckets of a batch: size class (0: one 64 x 64 block, 1: up to
+ * four, 2: more) x corner density class (0: corners per template pixel below
+ * 0.1, 1: below 0.5, 2: above); bucket = 3 * size_class + density_class. */
+#define SNCC_BATCH_BUCKETS 9
+/* Variants of a bucket: v = 0, 1, 2 are tile heights R = 8, 4, 2 with
+ * 64 x 64 template blocks, v = 3, 4, 5 the same with 32 x 32 blocks. */
+#define SNCC_BATCH_VARIANTS 6
 
 /* Opaque host object describing a batch (library-owned host memory). */
 typedef struct sncc_batch_s sncc_batch;
@@ -474,11 +481,22 @@ typedef struct {
 
 typedef struct {
     int32_t n_templates, n_sources;
-    int32_t tile_rows;      /* R of the current tile shape (32 x 8R offsets per tile) */
-    int32_t tiles;          /* work items of the current tile shape */
+    int32_t tile_rows;      /* R of every bucket's tile shape (32 x 8R offsets per tile); 0 if the
+                               buckets differ */
+    int32_t tiles;          /* work items under the current variants */
     double offsets;         /* sum over pairs of U*V */
     double corner_offsets;  /* sum over pairs of U*V*(nonzero corners of the whole template) */
 } sncc_batch_info;
+
+/* One bucket of a batch (sncc_batch_get_bucket). */
+typedef struct {
+    int32_t templates, pairs;  /* templates in the bucket and their (source, template) pairs */
+    int32_t size_class, density_class;
+    int32_t tile_rows;         /* the bucket's variant: tile height R ... */
+    int32_t block;             /* ... and template block edge (64 or 32: corners per staging pass) */
+    double corner_offsets;     /* sum over its pairs of U*V*(corners of the whole template) */
+    float ms[SNCC_BATCH_VARIANTS]; /* the autotuner's time of the bucket alone in each variant (0 untimed) */
+} sncc_batch_bucket;
 
 /*
  * sncc_batch_create - plan the coarse pass of every (source, template) pair
@@ -491,8 +509,10 @@ typedef struct {
  *   n_templates, n_sources (<= SNCC_BATCH_MAX_SOURCES), M, N  all sources
  *                          are M x N
  *   out                    receives the batch (free with sncc_batch_destroy)
- * Every template's plan is rebuilt with 64 x 64 blocks; work lists of tiles
- * are ordered by estimated cost (largest first) for each tile height.
+ * Every template's plan is rebuilt with 64 x 64 and 32 x 32 blocks and the
+ * template goes into its bucket; work lists of tiles are ordered by
+ * estimated cost (largest first) for each bucket and tile height.  Every
+ * bucket starts with R = 8 and 64 x 64 blocks.
  * Returns SNCC_ERR_UNIFORM if an approximation has zero energy.
  */
 int sncc_batch_create(const sncc_segments* const* segs, const uint8_t* const* templates, const int* t_strides,
@@ -505,13 +525,20 @@ void sncc_batch_destroy(sncc_batch* b);
 size_t sncc_batch_device_bytes(const sncc_batch* b);
 int sncc_batch_upload(const sncc_batch* b, void* d_buf, size_t bytes, sncc_stream_t stream);
 
-/* Tile height R (8, 4 or 2) used by sncc_batch_match, and batch statistics. */
+/* Sets every bucket to tile height R (8, 4 or 2) with 64 x 64 blocks;
+ * batch statistics. */
 int sncc_batch_set_variant(sncc_batch* b, int tile_rows);
 int sncc_batch_get_info(const sncc_batch* b, sncc_batch_info* out);
 
+/* One bucket's variant (tile height 8, 4 or 2; block edge 64 or 32), and a
+ * bucket's description.  SNCC_ERR_ARG for other values. */
+int sncc_batch_set_bucket_variant(sncc_batch* b, int bucket, int tile_rows, int block);
+int sncc_batch_get_bucket(const sncc_batch* b, int bucket, sncc_batch_bucket* out);
+
 /*
- * sncc_batch_match - the coarse pass for all pairs in one persistent launch
- * (one CTA per SM slot, tiles pulled through an atomic work counter).
+ * sncc_batch_match - the coarse pass for all pairs: one persistent launch
+ * per variant in use (one CTA per SM slot, tiles pulled through an atomic
+ * work counter, every bucket's tiles in its own variant).
  *
  *   d_buf                  uploaded batch image
  *   d_s[s], d_s2[s]        sum tables of source s (sncc_integral), all with
@@ -528,10 +555,13 @@ int sncc_batch_match(const sncc_batch* b, const void* d_buf, const void* const* 
                      int32_t* d_status, sncc_stream_t stream);
 
 /*
- * sncc_batch_autotune - times sncc_batch_match for every tile height on the
- * given data (one untimed run, then the fastest of `reps`) and keeps the
- * fastest for later calls.  Synchronises the stream.  ms_out (nullable)
- * receives the three times, for R = 8, 4, 2.
+ * sncc_batch_autotune - for every bucket that holds pairs, times the coarse
+ * pass of that bucket alone in each of the SNCC_BATCH_VARIANTS variants on
+ * the given data (one untimed run, then the fastest of `reps`) and keeps the
+ * fastest variant per bucket for later calls.  Synchronises the stream.
+ * ms_out (nullable) receives SNCC_BATCH_BUCKETS x SNCC_BATCH_VARIANTS times
+ * in ms, bucket-major (0 for empty buckets); sncc_batch_get_bucket reports
+ * them too.
  */
 int sncc_batch_autotune(sncc_batch* b, const void* d_buf, const void* const* d_s, const int64_t* const* d_s2,
                         int s_bits, int sat_pitch, int32_t* d_cand, int cand_cap, int32_t* d_count,

@@ -4,19 +4,26 @@
 // all candidates (Eq. 1, steps 7g-7j with an exact second stage).
 //
 // Design:
-//  * Host: every template's plan is rebuilt with 64 x 64 blocks and one
-//    region pitch (100 words), so a single kernel instance serves templates
-//    of any size.  A work list of tiles (pair, tile column, tile row) is
-//    built for each tile height R in {8, 4, 2} and ordered by estimated cost,
-//    largest first (corner count plus staging), so that the dynamic schedule
-//    below ends with the cheap tiles.
-//  * Device: a persistent grid (occupancy x SMs) of 8-warp CTAs pulls tiles
-//    with one atomic per tile; each tile runs the same staging / corner-sum /
-//    normalisation code as the single-problem kernel (sncc_tile.cuh), with
-//    the sources staged through registers.  Candidates are appended as
-//    (pair, v*U+u) with warp-aggregated atomics.
-//  * The tile height is chosen by an autotuner that times the variants on the
-//    caller's data (sncc_batch_autotune) or given explicitly.
+//  * Host: every template's plan is rebuilt with two block layouts: blocks
+//    of at most 64 x 64 (region pitch 100) and of at most 32 x 32 (pitch 68),
+//    so that one kernel serves templates of any size.  Templates fall into
+//    buckets by size (one 64 x 64 block, up to 4, more) and corner density
+//    (corners per template pixel below 0.1, below 0.5, above).  Every
+//    bucket has a variant: the tile height R in {8, 4, 2} (offset rows per
+//    lane) and the block edge, 64 or 32 (corners per staging pass).  A work
+//    list of tiles (pair, tile column, tile row) is built for every bucket
+//    and tile height, ordered by estimated cost, largest first.
+//  * Device: per variant in use, a persistent grid (occupancy x SMs) of
+//    8-warp CTAs pulls tiles with one atomic per tile from the lists of the
+//    buckets in that variant, one after another (heaviest bucket first, so
+//    that the dynamic schedule ends with cheap tiles); each tile runs the
+//    staging / corner-sum / normalisation code of the single-problem kernel
+//    (sncc_tile.cuh), with the sources staged through registers.  One
+//    kernel instance per variant keeps each at its own register count.
+//    Candidates are appended as (pair, v*U+u) with warp-aggregated atomics.
+//  * The variants are chosen per bucket by an autotuner that times each
+//    bucket alone in every variant on the caller's data
+//    (sncc_batch_autotune), or given explicitly.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,19 +43,30 @@ namespace sncc {
 namespace {
 
 constexpr int kBatchWP = 100;  // region pitch of 64 x 64 blocks
+constexpr int kBatchWP32 = 68;  // region pitch of 32 x 32 blocks
 constexpr int kBatchBlock = 64;
 constexpr int kVariants[3] = {8, 4, 2};
+constexpr int kBuckets = SNCC_BATCH_BUCKETS;
+constexpr int kBatchVariants = SNCC_BATCH_VARIANTS;  // variant v: R = kVariants[v % 3], block edge 64 >> (v / 3)
 
-struct TmplDesc {  // 80 bytes, one per template
-    int W, H, nblk, blk_first;
+struct TmplDesc {  // 96 bytes, one per template
+    int W, H;
+    int nblk[2], blk_first[2];  // the 64 x 64 and the 32 x 32 block layouts
     long long n, Q0;
     long long T, T2;
     float inv_n, Ek, scale, tau;
     float tau_exact;
     int pix_offset;
     double rn;  // 1 / n in FP64
+    int bucket, pad;
 };
-static_assert(sizeof(TmplDesc) == 80, "template descriptor layout");
+static_assert(sizeof(TmplDesc) == 96, "template descriptor layout");
+
+// One bucket's share of a launch: items [first, first + count) of the item
+// array (its list for tile height R), evaluated with R and the block edge.
+struct BucketRun {
+    int first, count, R, blk;
+};
 
 struct BatchArgs {
     const int4* pairs;  // {source, template, U, V}
@@ -57,7 +75,9 @@ struct BatchArgs {
     const int4* runblk;  // RUNBLK_INT4 per block
     const int4* runs;
     const int2* items;  // {pair, (tile row << 16) | tile column}
-    int n_items;
+    BucketRun run[kBuckets];  // in launch order
+    int nruns;
+    int n_items;  // over all runs
     int* counter;
     const void* s[SNCC_BATCH_MAX_SOURCES];
     const int64_t* s2[SNCC_BATCH_MAX_SOURCES];
@@ -68,63 +88,77 @@ struct BatchArgs {
     int* status;
 };
 
-template <int R, bool S64>
+// One tile of a pair with tile height R and region pitch WP (block edge 64
+// for pitch 100, 32 for pitch 68; lay indexes the template's layout).
+template <int R, int WP, bool S64>
+__device__ __forceinline__ void batch_tile(const BatchArgs& a, int* work, int2 item, int lane, int warp) {
+    constexpr int lay = (WP == kBatchWP) ? 0 : 1;
+    constexpr int BB = (WP == kBatchWP) ? kBatchBlock : kBatchBlock / 2;
+    const int4 pd = a.pairs[item.x];
+    const TmplDesc& td = a.tmpl[pd.y];
+    const int u0 = (item.y & 0xffff) * TILE_U, v0 = (item.y >> 16) * (WARPS * R);
+    const void* s = a.s[pd.x];
+    const int64_t* s2 = a.s2[pd.x];
+    const int* wbase = work + warp * R * WP + lane;
+    long long acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
+    const int nblk = td.nblk[lay], first = td.blk_first[lay];
+    for (int b = 0; b < nblk; ++b) {
+        const int4 blk = a.blocks[first + b];
+        const int bw = min(BB, td.W - blk.x), bh = min(BB, td.H - blk.y);
+        stage_region_regs<S64, WP>(s, a.pitch, a.M, a.N, work, u0 + blk.x, v0 + blk.y, WARPS * R + bh + 1, lane, warp,
+                                   TILE_U + bw + 1);
+        __syncthreads();
+        run_sum<R, WP>(acc, wbase, a.runs, a.runblk + RUNBLK_INT4 * (first + b));
+        __syncthreads();
+    }
+    const int u = u0 + lane;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = v0 + warp * R + r;
+        const bool valid = (u < pd.z) && (v < pd.w);
+        const float rho = valid ? normalise<S64>(acc[r], s, s2, a.pitch, u, v, td.W, td.H, td.n, td.rn, td.inv_n, td.Ek,
+                                                 td.scale, td.Q0)
+                                : 0.0f;
+        const bool pred = valid && (rho >= td.tau);
+        const unsigned m = __ballot_sync(0xffffffffu, pred);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(a.count, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (pred) {
+                const int pos = base + __popc(m & ((1u << lane) - 1u));
+                if (pos < a.cand_cap)
+                    a.cand[pos] = make_int2(item.x, v * pd.z + u);
+                else
+                    atomicOr(a.status, SNCC_STATUS_CAND_OVERFLOW);
+            }
+        }
+    }
+}
+
+// The persistent coarse pass of one variant (tile height R, region pitch
+// WP) over the buckets listed in a.run.
+template <int R, int WP, bool S64>
 __global__ void __launch_bounds__(WARPS * 32) batch_match_kernel(const __grid_constant__ BatchArgs a) {
-    constexpr int WP = kBatchWP;
     extern __shared__ __align__(16) int work[];
     __shared__ int item_sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int* wbase = work + warp * R * WP + lane;
     for (;;) {
         if (tid == 0) item_sh = atomicAdd(a.counter, 1);
         __syncthreads();
         const int it = item_sh;
         __syncthreads();  // item_sh is rewritten only after every thread has read it
         if (it >= a.n_items) break;
-        const int2 item = a.items[it];
-        const int4 pd = a.pairs[item.x];
-        const TmplDesc& td = a.tmpl[pd.y];
-        const int u0 = (item.y & 0xffff) * TILE_U, v0 = (item.y >> 16) * (WARPS * R);
-        const void* s = a.s[pd.x];
-        const int64_t* s2 = a.s2[pd.x];
-        long long acc[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = 0;
-        const int nblk = td.nblk;
-        for (int b = 0; b < nblk; ++b) {
-            const int4 blk = a.blocks[td.blk_first + b];
-            const int bw = min(kBatchBlock, td.W - blk.x), bh = min(kBatchBlock, td.H - blk.y);
-            stage_region_regs<S64, WP>(s, a.pitch, a.M, a.N, work, u0 + blk.x, v0 + blk.y, WARPS * R + bh + 1, lane,
-                                       warp, TILE_U + bw + 1);
-            __syncthreads();
-            const int gb = td.blk_first + b;
-            run_sum<R, WP>(acc, wbase, a.runs, a.runblk + RUNBLK_INT4 * gb);
-            __syncthreads();
+        // the bucket run the item falls in (uniform per CTA)
+        int k = 0, base = 0;
+        while (k + 1 < a.nruns && it >= base + a.run[k].count) {
+            base += a.run[k].count;
+            ++k;
         }
-        const int u = u0 + lane;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int v = v0 + warp * R + r;
-            const bool valid = (u < pd.z) && (v < pd.w);
-            const float rho = valid ? normalise<S64>(acc[r], s, s2, a.pitch, u, v, td.W, td.H, td.n, td.rn, td.inv_n, td.Ek,
-                                                     td.scale, td.Q0)
-                                    : 0.0f;
-            const bool pred = valid && (rho >= td.tau);
-            const unsigned m = __ballot_sync(0xffffffffu, pred);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(a.count, __popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (pred) {
-                    const int pos = base + __popc(m & ((1u << lane) - 1u));
-                    if (pos < a.cand_cap)
-                        a.cand[pos] = make_int2(item.x, v * pd.z + u);
-                    else
-                        atomicOr(a.status, SNCC_STATUS_CAND_OVERFLOW);
-                }
-            }
-        }
+        batch_tile<R, WP, S64>(a, work, a.items[a.run[k].first + (it - base)], lane, warp);
     }
 }
 
@@ -233,11 +267,16 @@ struct sncc_batch_s {
     std::vector<int32_t> corner_counts;    // nonzero corners per template in the 64 x 64 layout (the work)
     std::vector<int32_t> template_corners;  // corners of each whole template (the algorithmic count)
     size_t off_pairs = 0, off_pbase = 0, off_tmpl = 0, off_blocks = 0, off_runblk = 0, off_runs = 0, off_pix = 0,
-           off_items[3] = {0, 0, 0};
-    int n_items[3] = {0, 0, 0};
+           off_items = 0;
+    // items of bucket k for tile height kVariants[vi]: int2 units from item_first[k][vi]
+    int item_first[sncc::kBuckets][3] = {};
+    int item_count[sncc::kBuckets][3] = {};
+    int bucket_templates[sncc::kBuckets] = {}, bucket_pairs[sncc::kBuckets] = {};
+    double bucket_corner_offsets[sncc::kBuckets] = {};
+    int bucket_order[sncc::kBuckets] = {};  // launch order: heaviest tiles first
+    int variant[sncc::kBuckets] = {};       // chosen variant of every bucket
+    float tuned_ms[sncc::kBuckets][sncc::kBatchVariants] = {};
     std::vector<unsigned char> image;
-    int variant = 8;
-    int grid[3] = {0, 0, 0};
     double corner_offsets = 0.0;  // sum over pairs of U*V*(corners of the whole template)
     double offsets = 0.0;         // sum over pairs of U*V
 };
@@ -246,32 +285,59 @@ namespace sncc {
 namespace {
 
 int variant_index(int R) { return R == 8 ? 0 : (R == 4 ? 1 : (R == 2 ? 2 : -1)); }
-
-template <int R>
-size_t batch_smem(void) {
-    return (size_t)(WARPS * R + kBatchBlock + 1) * kBatchWP * 4;
+int variant_of(int R, int blk) {
+    const int vi = variant_index(R);
+    if (vi < 0 || (blk != kBatchBlock && blk != kBatchBlock / 2)) return -1;
+    return vi + (blk == kBatchBlock ? 0 : 3);
 }
 
-template <int R, bool S64>
-cudaError_t batch_launch(sncc_batch* b, const BatchArgs& args, cudaStream_t st) {
+// Shared memory of a variant: the region of one block for 8R offset rows.
+template <int R, int WP>
+constexpr size_t batch_smem() {
+    return (size_t)(WARPS * R + (WP == kBatchWP ? kBatchBlock : kBatchBlock / 2) + 1) * WP * 4;
+}
+
+// Bucket of a template: size class (one 64 x 64 block, up to 4, more) x
+// corner density (corners per template pixel below 0.1, below 0.5, above:
+// sparse approximations of smooth or textured templates, mixed, and
+// approximations close to the pixels).
+int bucket_of(int W, int H, int corners) {
+    const int nb = ((W + kBatchBlock - 1) / kBatchBlock) * ((H + kBatchBlock - 1) / kBatchBlock);
+    const int sc = nb == 1 ? 0 : (nb <= 4 ? 1 : 2);
+    const double d = (double)corners / ((double)W * H);
+    const int dc = d < 0.1 ? 0 : (d < 0.5 ? 1 : 2);
+    return sc * 3 + dc;
+}
+
+template <int R, int WP, bool S64>
+cudaError_t batch_launch(const BatchArgs& args, cudaStream_t st) {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
-    static int per_sm = 0, sms = 0;
+    static int per_sm = 0;
+    constexpr size_t smem = batch_smem<R, WP>();
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(batch_match_kernel<R, S64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)batch_smem<R>());
+        attr = cudaFuncSetAttribute(batch_match_kernel<R, WP, S64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
         if (attr == cudaSuccess)
-            attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_match_kernel<R, S64>, WARPS * 32,
-                                                                 batch_smem<R>());
-        int dev = 0;
-        if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
-        if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_match_kernel<R, WP, S64>, WARPS * 32,
+                                                                 smem);
     });
     if (attr != cudaSuccess) return attr;
-    const int grid = std::max(1, per_sm) * std::max(1, sms);
-    b->grid[variant_index(R)] = grid;
-    batch_match_kernel<R, S64><<<grid, WARPS * 32, batch_smem<R>(), st>>>(args);
+    const int grid = std::max(1, per_sm) * std::max(1, sm_count());
+    batch_match_kernel<R, WP, S64><<<grid, WARPS * 32, smem, st>>>(args);
     return cudaGetLastError();
+}
+
+template <bool S64>
+cudaError_t batch_launch_variant(int v, const BatchArgs& args, cudaStream_t st) {
+    switch (v) {
+        case 0: return batch_launch<8, kBatchWP, S64>(args, st);
+        case 1: return batch_launch<4, kBatchWP, S64>(args, st);
+        case 2: return batch_launch<2, kBatchWP, S64>(args, st);
+        case 3: return batch_launch<8, kBatchWP32, S64>(args, st);
+        case 4: return batch_launch<4, kBatchWP32, S64>(args, st);
+        default: return batch_launch<2, kBatchWP32, S64>(args, st);
+    }
 }
 
 }  // namespace
@@ -311,14 +377,13 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
                 return SNCC_ERR_ARG;
             }
             Plan p;
-            build_plan(sg, p);
+            build_plan(sg, p, true);
             const Layout& L = p.lay[1];  // blocks of at most 64 x 64, pitch 100
             TmplDesc d;
             std::memset(&d, 0, sizeof(d));
             d.W = sg->W;
             d.H = sg->H;
-            d.nblk = L.nblk;
-            d.blk_first = (int)(blocks.size() / 4);
+            d.bucket = bucket_of(sg->W, sg->H, p.template_corners);
             d.n = (long long)sg->W * sg->H;
             d.Q0 = p.Q0;
             d.T = sg->T;
@@ -334,17 +399,23 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
                 pix.insert(pix.end(), templates[t] + (size_t)y * t_strides[t],
                            templates[t] + (size_t)y * t_strides[t] + sg->W);
             while (pix.size() % 16) pix.push_back(0);
-            const int run_base = (int)(runs.size() / 4);  // int4 units
-            const int32_t* img_blocks = p.image.data() + L.blocks_offset / 4;
-            const int32_t* img_runblk = p.image.data() + L.runblk_offset / 4;
-            const int32_t* img_runs = p.image.data() + L.runs_offset / 4;
-            const size_t run_words = (L.end_offset - L.runs_offset) / 4;
-            for (int k = 0; k < L.nblk; ++k) {
-                for (int j = 0; j < 4; ++j) blocks.push_back(img_blocks[4 * k + j]);
-                for (int j = 0; j < 4 * RUNBLK_INT4; ++j)  // firsts (even words) move by run_base
-                    runblk.push_back(img_runblk[4 * RUNBLK_INT4 * k + j] + ((j % 2 == 0) ? run_base : 0));
+            for (int li = 0; li < 2; ++li) {  // the 64 x 64 and the 32 x 32 block layouts
+                const Layout& Ll = p.lay[li == 0 ? 1 : 2];
+                d.nblk[li] = Ll.nblk;
+                d.blk_first[li] = (int)(blocks.size() / 4);
+                const int run_base = (int)(runs.size() / 4);  // int4 units
+                const int32_t* img_blocks = p.image.data() + Ll.blocks_offset / 4;
+                const int32_t* img_runblk = p.image.data() + Ll.runblk_offset / 4;
+                const int32_t* img_runs = p.image.data() + Ll.runs_offset / 4;
+                const size_t run_words = (Ll.end_offset - Ll.runs_offset) / 4;
+                for (int k = 0; k < Ll.nblk; ++k) {
+                    for (int j = 0; j < 4; ++j) blocks.push_back(img_blocks[4 * k + j]);
+                    for (int j = 0; j < 4 * RUNBLK_INT4; ++j)  // firsts (even words) move by run_base
+                        runblk.push_back(img_runblk[4 * RUNBLK_INT4 * k + j] + ((j % 2 == 0) ? run_base : 0));
+                }
+                runs.insert(runs.end(), img_runs, img_runs + run_words);
             }
-            runs.insert(runs.end(), img_runs, img_runs + run_words);
+            b->bucket_templates[d.bucket] += 1;
             b->tmpl.push_back(d);
             b->corner_counts.push_back(L.nonzero_corners);
             b->template_corners.push_back(p.template_corners);
@@ -361,9 +432,11 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
                 pairs.push_back(U);
                 pairs.push_back(V);
                 // per-tile cost: corner sum plus region staging per block
-                cost.push_back((double)b->corner_counts[t] * 8.0 + (double)d.nblk * 1600.0);
+                cost.push_back((double)b->corner_counts[t] * 8.0 + (double)d.nblk[0] * 1600.0);
                 b->corner_offsets += (double)U * V * b->template_corners[t];
                 b->offsets += (double)U * V;
+                b->bucket_pairs[d.bucket] += 1;
+                b->bucket_corner_offsets[d.bucket] += (double)U * V * b->template_corners[t];
             }
         const int npairs = n_templates * n_sources;
         std::vector<long long> pbase(npairs);  // first sort key of each pair
@@ -375,20 +448,31 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
         std::vector<int> order(npairs);
         for (int i = 0; i < npairs; ++i) order[i] = i;
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-        std::vector<int32_t> items[3];
-        for (int vi = 0; vi < 3; ++vi) {
-            const int R = kVariants[vi];
-            for (int pi : order) {
-                const int U = pairs[4 * pi + 2], V = pairs[4 * pi + 3];
-                const int tu = (U + TILE_U - 1) / TILE_U, tv = (V + WARPS * R - 1) / (WARPS * R);
-                for (int ty = 0; ty < tv; ++ty)
-                    for (int tx = 0; tx < tu; ++tx) {
-                        items[vi].push_back(pi);
-                        items[vi].push_back((ty << 16) | tx);
-                    }
+        // per bucket and tile height, that bucket's tiles, costliest pairs first
+        std::vector<int32_t> items;
+        double bucket_cost[kBuckets] = {};
+        for (int k = 0; k < kBuckets; ++k) {
+            for (int vi = 0; vi < 3; ++vi) {
+                const int R = kVariants[vi];
+                b->item_first[k][vi] = (int)(items.size() / 2);
+                for (int pi : order) {
+                    if (b->tmpl[pairs[4 * pi + 1]].bucket != k) continue;
+                    if (vi == 0) bucket_cost[k] = std::max(bucket_cost[k], cost[pi]);
+                    const int U = pairs[4 * pi + 2], V = pairs[4 * pi + 3];
+                    const int tu = (U + TILE_U - 1) / TILE_U, tv = (V + WARPS * R - 1) / (WARPS * R);
+                    for (int ty = 0; ty < tv; ++ty)
+                        for (int tx = 0; tx < tu; ++tx) {
+                            items.push_back(pi);
+                            items.push_back((ty << 16) | tx);
+                        }
+                }
+                b->item_count[k][vi] = (int)(items.size() / 2) - b->item_first[k][vi];
             }
-            b->n_items[vi] = (int)(items[vi].size() / 2);
+            b->variant[k] = 0;  // R = 8, 64 x 64 blocks until tuned or set
+            b->bucket_order[k] = k;
         }
+        std::stable_sort(b->bucket_order, b->bucket_order + kBuckets,
+                         [&](int x, int y) { return bucket_cost[x] > bucket_cost[y]; });
         // device image
         size_t off = 0;
         b->off_pairs = off;
@@ -405,10 +489,8 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
         off = align16(off + runs.size() * 4);
         b->off_pix = off;
         off = align16(off + pix.size());
-        for (int vi = 0; vi < 3; ++vi) {
-            b->off_items[vi] = off;
-            off = align16(off + items[vi].size() * 4);
-        }
+        b->off_items = off;
+        off = align16(off + items.size() * 4);
         b->image.assign(off, 0);
         std::memcpy(b->image.data() + b->off_pairs, pairs.data(), pairs.size() * 4);
         std::memcpy(b->image.data() + b->off_pbase, pbase.data(), pbase.size() * 8);
@@ -417,8 +499,7 @@ extern "C" int sncc_batch_create(const sncc_segments* const* segs, const uint8_t
         if (!runblk.empty()) std::memcpy(b->image.data() + b->off_runblk, runblk.data(), runblk.size() * 4);
         if (!runs.empty()) std::memcpy(b->image.data() + b->off_runs, runs.data(), runs.size() * 4);
         std::memcpy(b->image.data() + b->off_pix, pix.data(), pix.size());
-        for (int vi = 0; vi < 3; ++vi)
-            std::memcpy(b->image.data() + b->off_items[vi], items[vi].data(), items[vi].size() * 4);
+        if (!items.empty()) std::memcpy(b->image.data() + b->off_items, items.data(), items.size() * 4);
     } catch (const std::bad_alloc&) {
         delete b;
         return SNCC_ERR_NOMEM;
@@ -442,25 +523,58 @@ extern "C" int sncc_batch_upload(const sncc_batch* b, void* d_buf, size_t bytes,
 
 extern "C" int sncc_batch_set_variant(sncc_batch* b, int tile_rows) {
     if (!b || sncc::variant_index(tile_rows) < 0) return SNCC_ERR_ARG;
-    b->variant = tile_rows;
+    for (int k = 0; k < sncc::kBuckets; ++k) b->variant[k] = sncc::variant_of(tile_rows, sncc::kBatchBlock);
+    return SNCC_OK;
+}
+
+extern "C" int sncc_batch_set_bucket_variant(sncc_batch* b, int bucket, int tile_rows, int block) {
+    if (!b || bucket < 0 || bucket >= sncc::kBuckets) return SNCC_ERR_ARG;
+    const int v = sncc::variant_of(tile_rows, block);
+    if (v < 0) return SNCC_ERR_ARG;
+    b->variant[bucket] = v;
     return SNCC_OK;
 }
 
 extern "C" int sncc_batch_get_info(const sncc_batch* b, sncc_batch_info* out) {
+    using namespace sncc;
     if (!b || !out) return SNCC_ERR_ARG;
     out->n_templates = b->nt;
     out->n_sources = b->ns;
-    out->tile_rows = b->variant;
-    out->tiles = b->n_items[sncc::variant_index(b->variant)];
+    int R = -1, tiles = 0;
+    for (int k = 0; k < kBuckets; ++k) {
+        if (b->bucket_pairs[k] == 0) continue;
+        const int vi = b->variant[k] % 3;
+        tiles += b->item_count[k][vi];
+        R = (R == -1 || R == kVariants[vi]) ? kVariants[vi] : 0;
+    }
+    out->tile_rows = R < 0 ? 0 : R;
+    out->tiles = tiles;
     out->offsets = b->offsets;
     out->corner_offsets = b->corner_offsets;
     return SNCC_OK;
 }
 
-extern "C" int sncc_batch_match(const sncc_batch* b, const void* d_buf, const void* const* d_s,
-                                const int64_t* const* d_s2, int s_bits, int sat_pitch, int32_t* d_cand, int cand_cap,
-                                int32_t* d_count, int32_t* d_counter, int32_t* d_status, sncc_stream_t stream) {
-    sncc::NvtxRange nvtx_range("sncc_batch_match");
+extern "C" int sncc_batch_get_bucket(const sncc_batch* b, int bucket, sncc_batch_bucket* out) {
+    using namespace sncc;
+    if (!b || !out || bucket < 0 || bucket >= kBuckets) return SNCC_ERR_ARG;
+    out->templates = b->bucket_templates[bucket];
+    out->pairs = b->bucket_pairs[bucket];
+    out->size_class = bucket / 3;
+    out->density_class = bucket % 3;
+    out->tile_rows = kVariants[b->variant[bucket] % 3];
+    out->block = b->variant[bucket] < 3 ? kBatchBlock : kBatchBlock / 2;
+    out->corner_offsets = b->bucket_corner_offsets[bucket];
+    for (int v = 0; v < kBatchVariants; ++v) out->ms[v] = b->tuned_ms[bucket][v];
+    return SNCC_OK;
+}
+
+namespace {
+
+// The coarse pass over the buckets in `which` (all when which < 0, else
+// that bucket alone), each with its variant.
+int batch_match_run(const sncc_batch* b, const void* d_buf, const void* const* d_s, const int64_t* const* d_s2,
+                    int s_bits, int sat_pitch, int32_t* d_cand, int cand_cap, int32_t* d_count, int32_t* d_counter,
+                    int32_t* d_status, int which, sncc_stream_t stream) {
     using namespace sncc;
     if (!b || !d_buf || !d_s || !d_s2 || !d_count || !d_counter || !d_status || cand_cap < 0) return SNCC_ERR_ARG;
     if (cand_cap > 0 && !d_cand) return SNCC_ERR_ARG;
@@ -470,14 +584,12 @@ extern "C" int sncc_batch_match(const sncc_batch* b, const void* d_buf, const vo
     BatchArgs a;
     std::memset(&a, 0, sizeof(a));
     const char* base = static_cast<const char*>(d_buf);
-    const int vi = variant_index(b->variant);
     a.pairs = reinterpret_cast<const int4*>(base + b->off_pairs);
     a.tmpl = reinterpret_cast<const TmplDesc*>(base + b->off_tmpl);
     a.blocks = reinterpret_cast<const int4*>(base + b->off_blocks);
     a.runblk = reinterpret_cast<const int4*>(base + b->off_runblk);
     a.runs = reinterpret_cast<const int4*>(base + b->off_runs);
-    a.items = reinterpret_cast<const int2*>(base + b->off_items[vi]);
-    a.n_items = b->n_items[vi];
+    a.items = reinterpret_cast<const int2*>(base + b->off_items);
     a.counter = d_counter;
     for (int s = 0; s < b->ns; ++s) {
         if (!d_s[s] || !d_s2[s] || (reinterpret_cast<uintptr_t>(d_s[s]) & 15)) return SNCC_ERR_ARG;
@@ -493,17 +605,44 @@ extern "C" int sncc_batch_match(const sncc_batch* b, const void* d_buf, const vo
     a.status = d_status;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(d_count, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
-    if (cudaMemsetAsync(d_counter, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
     if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
-    sncc_batch* mb = const_cast<sncc_batch*>(b);
-    cudaError_t e;
-    const bool s64 = (s_bits == 64);
-    switch (b->variant) {
-        case 8: e = s64 ? batch_launch<8, true>(mb, a, st) : batch_launch<8, false>(mb, a, st); break;
-        case 4: e = s64 ? batch_launch<4, true>(mb, a, st) : batch_launch<4, false>(mb, a, st); break;
-        default: e = s64 ? batch_launch<2, true>(mb, a, st) : batch_launch<2, false>(mb, a, st); break;
+    // one persistent launch per variant in use, over its buckets (heaviest
+    // bucket first), the variants in the order of their heaviest buckets
+    bool launched[kBatchVariants] = {};
+    for (int j = 0; j < kBuckets; ++j) {
+        const int k0 = b->bucket_order[j];
+        if (b->bucket_pairs[k0] == 0 || (which >= 0 && k0 != which)) continue;
+        const int v = b->variant[k0];
+        if (launched[v]) continue;
+        launched[v] = true;
+        a.nruns = 0;
+        a.n_items = 0;
+        for (int jj = j; jj < kBuckets; ++jj) {
+            const int k = b->bucket_order[jj];
+            if (b->bucket_pairs[k] == 0 || (which >= 0 && k != which) || b->variant[k] != v) continue;
+            BucketRun& r = a.run[a.nruns++];
+            r.first = b->item_first[k][v % 3];
+            r.count = b->item_count[k][v % 3];
+            r.R = kVariants[v % 3];
+            r.blk = v < 3 ? kBatchBlock : kBatchBlock / 2;
+            a.n_items += r.count;
+        }
+        if (a.n_items == 0) continue;
+        if (cudaMemsetAsync(d_counter, 0, sizeof(int32_t), st) != cudaSuccess) return SNCC_ERR_CUDA;
+        const cudaError_t e = (s_bits == 64) ? batch_launch_variant<true>(v, a, st) : batch_launch_variant<false>(v, a, st);
+        if (e != cudaSuccess) return SNCC_ERR_CUDA;
     }
-    return e == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+    return SNCC_OK;
+}
+
+}  // namespace
+
+extern "C" int sncc_batch_match(const sncc_batch* b, const void* d_buf, const void* const* d_s,
+                                const int64_t* const* d_s2, int s_bits, int sat_pitch, int32_t* d_cand, int cand_cap,
+                                int32_t* d_count, int32_t* d_counter, int32_t* d_status, sncc_stream_t stream) {
+    sncc::NvtxRange nvtx_range("sncc_batch_match");
+    return batch_match_run(b, d_buf, d_s, d_s2, s_bits, sat_pitch, d_cand, cand_cap, d_count, d_counter, d_status,
+                           -1, stream);
 }
 
 extern "C" int sncc_batch_autotune(sncc_batch* b, const void* d_buf, const void* const* d_s,
@@ -519,34 +658,41 @@ extern "C" int sncc_batch_autotune(sncc_batch* b, const void* d_buf, const void*
         cudaEventDestroy(e0);
         return SNCC_ERR_CUDA;
     }
-    int best = 8;
-    float best_ms = 3.0e38f;
     int rc = SNCC_OK;
-    for (int vi = 0; vi < 3 && rc == SNCC_OK; ++vi) {
-        b->variant = kVariants[vi];
-        // one untimed run, then the fastest of `reps` timed runs
-        rc = sncc_batch_match(b, d_buf, d_s, d_s2, s_bits, sat_pitch, d_cand, cand_cap, d_count, d_counter, d_status,
-                              stream);
-        float ms_v = 3.0e38f;
-        for (int r = 0; r < reps && rc == SNCC_OK; ++r) {
-            cudaEventRecord(e0, st);
-            rc = sncc_batch_match(b, d_buf, d_s, d_s2, s_bits, sat_pitch, d_cand, cand_cap, d_count, d_counter,
-                                  d_status, stream);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) rc = SNCC_ERR_CUDA;
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms_v = std::min(ms_v, ms);
+    for (int k = 0; k < kBuckets && rc == SNCC_OK; ++k) {
+        for (int v = 0; v < kBatchVariants; ++v) b->tuned_ms[k][v] = 0.0f;
+        if (b->bucket_pairs[k] == 0) continue;
+        int best = b->variant[k];
+        float best_ms = 3.0e38f;
+        for (int v = 0; v < kBatchVariants && rc == SNCC_OK; ++v) {
+            b->variant[k] = v;
+            // the bucket alone in variant v: one untimed run, then the fastest of `reps`
+            rc = batch_match_run(b, d_buf, d_s, d_s2, s_bits, sat_pitch, d_cand, cand_cap, d_count, d_counter,
+                                 d_status, k, stream);
+            float ms_v = 3.0e38f;
+            for (int r = 0; r < reps && rc == SNCC_OK; ++r) {
+                cudaEventRecord(e0, st);
+                rc = batch_match_run(b, d_buf, d_s, d_s2, s_bits, sat_pitch, d_cand, cand_cap, d_count, d_counter,
+                                     d_status, k, stream);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = SNCC_ERR_CUDA;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_v = std::min(ms_v, ms);
+            }
+            b->tuned_ms[k][v] = ms_v;
+            if (ms_v < best_ms) {
+                best_ms = ms_v;
+                best = v;
+            }
         }
-        if (ms_out) ms_out[vi] = ms_v;
-        if (ms_v < best_ms) {
-            best_ms = ms_v;
-            best = kVariants[vi];
-        }
+        b->variant[k] = best;
     }
+    if (ms_out)
+        for (int k = 0; k < kBuckets; ++k)
+            for (int v = 0; v < kBatchVariants; ++v) ms_out[k * kBatchVariants + v] = b->tuned_ms[k][v];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->variant = best;
     return rc;
 }
 

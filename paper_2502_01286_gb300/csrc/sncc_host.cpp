@@ -320,8 +320,8 @@ static void build_layout(const std::vector<int32_t>& qimg, int W, int H, int BW,
     L.end_offset = image.size() * 4;
 }
 
-// Builds the fixed-point weights and both block layouts of the plan.
-int build_plan(const sncc_segments* s, Plan& p) {
+// Builds the fixed-point weights and the block layouts of the plan.
+int build_plan(const sncc_segments* s, Plan& p, bool small_blocks) {
     const int W = s->W, H = s->H;
     const int64_t n = (int64_t)W * H;
     p.W = W;
@@ -380,6 +380,8 @@ int build_plan(const sncc_segments* s, Plan& p) {
     const int bw0 = single ? W : std::min(W, BLOCK_MULTI), bh0 = single ? H : std::min(H, BLOCK_MULTI);
     build_layout(qimg, W, H, bw0, bh0, bw0 <= 32 ? 68 : 100, p.lay[0], p.image);
     build_layout(qimg, W, H, std::min(W, BLOCK_SINGLE_MAX), std::min(H, BLOCK_SINGLE_MAX), 100, p.lay[1], p.image);
+    if (small_blocks)
+        build_layout(qimg, W, H, std::min(W, BLOCK_MULTI), std::min(H, BLOCK_MULTI), 68, p.lay[2], p.image);
     p.direct_count = p.template_corners <= DIRECT_MAX ? p.template_corners : 0;
     p.direct_offset = p.image.size() * 4;
     if (p.direct_count > 0) p.image.insert(p.image.end(), direct.begin(), direct.begin() + 4 * p.direct_count);

@@ -106,8 +106,10 @@ struct Plan {
     // larger ones use 32 x 32 blocks (pitch 68), read by the per-candidate
     // fine pass.  lay[1]: blocks of at most 64 x 64 with pitch 100, the
     // segment-sum kernels' layout for templates larger than 64 x 64 (fewer,
-    // larger blocks halve the staged entries per corner).
-    Layout lay[2];
+    // larger blocks halve the staged entries per corner).  lay[2] (built on
+    // request, for the batched kernel): blocks of at most 32 x 32 with pitch
+    // 68 for every template size.
+    Layout lay[3];
     // Templates with at most DIRECT_MAX corners in all also carry their
     // whole-template corner list, int4 {X, Y, G, 0}, at direct_offset: the
     // segment-sum kernel then reads the table at those corners directly
@@ -129,8 +131,9 @@ constexpr int RUN2_LEN[3] = {8, 4, 3};
 
 Plan* plan_of(const sncc_segments* s);
 
-// Fills p from seg's segment table (defined in sncc_host.cpp).
-int build_plan(const sncc_segments* seg, Plan& p);
+// Fills p from seg's segment table (defined in sncc_host.cpp); with
+// small_blocks, also lay[2].
+int build_plan(const sncc_segments* seg, Plan& p, bool small_blocks = false);
 
 // The layout the single-problem segment-sum kernel uses: one block for a
 // template up to 64 x 64, else 64 x 64 blocks.

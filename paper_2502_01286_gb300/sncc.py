@@ -40,6 +40,7 @@ EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_fr
             "sncc_refine_segmented_tiles_workspace_bytes", "sncc_batch_create",
             "sncc_batch_destroy", "sncc_batch_device_bytes", "sncc_batch_upload", "sncc_batch_set_variant",
             "sncc_batch_get_info", "sncc_batch_match", "sncc_batch_autotune", "sncc_batch_refine_workspace_bytes",
+            "sncc_batch_set_bucket_variant", "sncc_batch_get_bucket",
             "sncc_batch_refine", "sncc_diff_workspace_bytes", "sncc_diff_forward", "sncc_diff_backward"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -128,6 +129,15 @@ class BatchInfo(C.Structure):
                 ("tiles", C.c_int32), ("offsets", C.c_double), ("corner_offsets", C.c_double)]
 
 
+BATCH_BUCKETS, BATCH_VARIANTS = 9, 6
+
+
+class BatchBucket(C.Structure):
+    _fields_ = [("templates", C.c_int32), ("pairs", C.c_int32), ("size_class", C.c_int32),
+                ("density_class", C.c_int32), ("tile_rows", C.c_int32), ("block", C.c_int32),
+                ("corner_offsets", C.c_double), ("ms", C.c_float * BATCH_VARIANTS)]
+
+
 _pp = C.POINTER(C.c_void_p)
 _lib.sncc_batch_create.argtypes = [C.POINTER(C.POINTER(_Segments)), _pp, C.POINTER(C.c_int), C.POINTER(C.c_float),
                                    C.POINTER(C.c_float), C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
@@ -137,6 +147,8 @@ _lib.sncc_batch_device_bytes.argtypes = [_vp]
 _lib.sncc_batch_device_bytes.restype = C.c_size_t
 _lib.sncc_batch_upload.argtypes = [_vp, _vp, C.c_size_t, _vp]
 _lib.sncc_batch_set_variant.argtypes = [_vp, C.c_int]
+_lib.sncc_batch_set_bucket_variant.argtypes = [_vp, C.c_int, C.c_int, C.c_int]
+_lib.sncc_batch_get_bucket.argtypes = [_vp, C.c_int, C.POINTER(BatchBucket)]
 _lib.sncc_batch_get_info.argtypes = [_vp, C.POINTER(BatchInfo)]
 _lib.sncc_batch_match.argtypes = [_vp, _vp, _pp, _pp, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp, _vp, _vp]
 _lib.sncc_batch_autotune.argtypes = [_vp, _vp, _pp, _pp, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp, _vp, C.c_int,
@@ -861,7 +873,25 @@ class Batch:
         return {k: getattr(bi, k) for k, _ in BatchInfo._fields_}
 
     def set_tile_rows(self, R: int):
+        """Every bucket to tile height R with 64 x 64 template blocks."""
         _check(_lib.sncc_batch_set_variant(self._h, int(R)), "sncc_batch_set_variant")
+
+    def set_bucket_variant(self, bucket: int, R: int, block: int):
+        _check(_lib.sncc_batch_set_bucket_variant(self._h, int(bucket), int(R), int(block)),
+               "sncc_batch_set_bucket_variant")
+
+    def buckets(self) -> list:
+        """One dict per template bucket: templates, pairs, classes, the
+        chosen variant (tile_rows, block) and the autotuner's times."""
+        out = []
+        for k in range(BATCH_BUCKETS):
+            bb = BatchBucket()
+            _check(_lib.sncc_batch_get_bucket(self._h, k, C.byref(bb)), "sncc_batch_get_bucket")
+            d = {f: getattr(bb, f) for f, _ in BatchBucket._fields_ if f != "ms"}
+            d["bucket"] = k
+            d["ms"] = list(bb.ms)
+            out.append(d)
+        return out
 
     def _match_args(self):
         return (self._h, self.image.data_ptr(), self._s, self._s2, self.s_bits, self.pitch, self.cand.data_ptr(),
@@ -881,13 +911,19 @@ class Batch:
                                       self.status.data_ptr(), _stream(stream)), "sncc_batch_refine")
 
     def autotune(self, sources, reps: int = 3, stream=None):
-        """Time the three tile heights on these sources and keep the fastest;
-        returns {R: ms}.  Synchronises."""
+        """Time every variant of every bucket (the bucket alone) on these
+        sources and keep the fastest per bucket; returns {bucket: {(R,
+        block): ms}} for the buckets that hold pairs.  Synchronises."""
         for f, tb in zip(sources, self.tables):
             integral(f, tb, workspace=self.ws, stream=stream)
-        ms = (C.c_float * 3)()
+        ms = (C.c_float * (BATCH_BUCKETS * BATCH_VARIANTS))()
         _check(_lib.sncc_batch_autotune(*self._match_args(), int(reps), _stream(stream), ms), "sncc_batch_autotune")
-        return {8: ms[0], 4: ms[1], 2: ms[2]}
+        out = {}
+        for k, bb in enumerate(self.buckets()):
+            if bb["pairs"]:
+                out[k] = {((8, 4, 2)[v % 3], 64 if v < 3 else 32): ms[k * BATCH_VARIANTS + v]
+                          for v in range(BATCH_VARIANTS)}
+        return out
 
     def capture(self, sources):
         """Record run(sources) in a CUDA graph (after one eager warm-up run)."""

@@ -86,7 +86,9 @@ def test_batch_coarse_and_refine_vs_oracle(sncc, problem):
     assert want <= got
 
 
-def test_batch_tile_heights_agree_and_autotune(sncc, problem):
+def test_batch_variants_agree_and_autotune_per_bucket(sncc, problem):
+    """Every tile height and block edge gives the same candidate set; the
+    autotuner times each bucket in each variant and keeps its fastest."""
     M, N, srcs, tl, ref, maps, p = problem
     b = sncc.Batch([t for t, _, _ in tl], [sg for _, _, sg in tl], M, N, len(srcs), precision=p)
     fd = [torch.as_tensor(f).cuda() for f in srcs]
@@ -97,10 +99,24 @@ def test_batch_tile_heights_agree_and_autotune(sncc, problem):
         torch.cuda.synchronize()
         sets.append(_check_batch(sncc, b, problem))
         assert b.info()["tile_rows"] == R
-    assert sets[0] == sets[1] == sets[2]
+    # 32 x 32 template blocks in every bucket give the same candidates
+    for k in range(sncc.BATCH_BUCKETS):
+        b.set_bucket_variant(k, 4, 32)
+    b.run(fd)
+    torch.cuda.synchronize()
+    sets.append(_check_batch(sncc, b, problem))
+    assert sets[0] == sets[1] == sets[2] == sets[3]
     ms = b.autotune(fd, reps=2)
-    assert set(ms) == {8, 4, 2} and all(v > 0 for v in ms.values())
-    assert b.info()["tile_rows"] == min(ms, key=ms.get)
+    buckets = b.buckets()
+    assert set(ms) == {k for k, bb in enumerate(buckets) if bb["pairs"]} and len(ms) >= 2
+    for k, times in ms.items():
+        assert len(times) == 6 and all(v > 0 for v in times.values())
+        assert (buckets[k]["tile_rows"], buckets[k]["block"]) == min(times, key=times.get)
+    assert sum(bb["pairs"] for bb in buckets) == len(srcs) * len(tl)
+    # the tuned (mixed) variants still give the same candidates
+    b.run(fd)
+    torch.cuda.synchronize()
+    assert _check_batch(sncc, b, problem) == sets[0]
 
 
 def test_batch_cuda_graph_replay(sncc, problem):
@@ -130,3 +146,69 @@ def test_batch_cuda_graph_replay(sncc, problem):
     m2 = b.matches()
     for a, c in zip(m1, m2):
         np.testing.assert_array_equal(a, c)
+
+
+def test_batch_config4_full_size_sampled(sncc):
+    """The batched workload at its real size: 8 sources of 1024 x 1024 and
+    64 templates with sides 16 .. 256 and std thresholds 4 .. 25 (512 pairs,
+    K from about 100 to 38000) in one persistent launch at precision 0.85.
+    For every pair one random offset row, and for each template the row of
+    its own crop in its own source, go through the oracle: candidates obey
+    the band rule (Eq. 17 - 18, steps 7a-7f) and the exact matches on those
+    rows (Eq. 1, steps 7g-7j) equal the oracle's outside the bands, with rho
+    within the tolerance."""
+    srcs = synth.batch_sources()
+    tl = synth.batch_templates(srcs)
+    M = N = 1024
+    p = 0.85
+    nt, ns = len(tl), len(srcs)
+    b = sncc.Batch([t for t, _, _ in tl], [sg for _, _, sg in tl], M, N, ns, precision=p, cand_cap=1 << 22,
+                   out_cap=1 << 18)
+    fd = [torch.as_tensor(f).cuda() for f in srcs]
+    b.run(fd)
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == 0
+    pair, idx = b.candidates()
+    cand = {}
+    for q, i in zip(pair.tolist(), idx.tolist()):
+        cand.setdefault(q, set()).add(i)
+    mp, mu, mv, mrho = b.matches()
+    matches = {}
+    for q, uu, vv, r in zip(mp.tolist(), mu.tolist(), mv.tolist(), mrho.tolist()):
+        matches.setdefault(q, {})[(uu, vv)] = r
+    rng = np.random.default_rng(2025)
+    checked = positives = 0
+    for ti, (t, org, sg) in enumerate(tl):
+        ap = O.precompute_template_approximation(t, sg)
+        H, W = t.shape
+        U, V = M - W + 1, N - H + 1
+        tau = p * ap.rho_max
+        for s in range(ns):
+            rows = [int(rng.integers(0, V))]
+            if s == ti % ns:
+                rows.append(int(org[1]))  # the template's own crop
+            rows = np.unique(rows)
+            rho = O.segmented_ncc_map(srcs[s], ap, "sat", rows=rows)
+            q = s * nt + ti
+            mine = cand.get(q, set())
+            for r in rows:
+                row_idx = {i - r * U for i in mine if i // U == r}
+                must = set(np.flatnonzero(rho[r] >= tau + TOL).tolist())
+                never = set(np.flatnonzero(rho[r] < tau - TOL).tolist())
+                assert must <= row_idx, (q, r)
+                assert not (row_idx & never), (q, r)
+                checked += U
+                # exact refine of the oracle's candidates on this row
+                oc = np.flatnonzero(rho[r] >= tau)
+                ex = O.ncc_exact_at(srcs[s], t, oc.astype(np.int32), np.full(oc.size, r, np.int32)) \
+                    if oc.size else np.zeros(0)
+                want = {int(u) for u, e in zip(oc, ex) if e >= p + TOL}
+                got = {uu for (uu, vv) in matches.get(q, {}) if vv == r}
+                amb = {int(u) for u, e in zip(oc, ex) if abs(e - p) < TOL} | \
+                      {int(u) for u in np.flatnonzero(np.abs(rho[r] - tau) < TOL)}
+                assert (got ^ want) <= amb, (q, r, sorted(got ^ want)[:5])
+                for uu in got:
+                    e = O.ncc_exact_at(srcs[s], t, [uu], [r])[0]
+                    assert abs(matches[q][(uu, r)] - e) <= TOL
+                positives += len(want)
+    assert checked > 400000 and positives >= 32
