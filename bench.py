@@ -370,11 +370,10 @@ def workload_config(name, case, sigmas, precision, U, V, seed):
     """The workload as both arms describe it (the same dict in each)."""
     N, M = case.f.shape
     H, W = case.t.shape
-    bits = 32 if 255 * M * N < 2 ** 31 else 64
     return {"workload": "%s-%dx%d-t%dx%d-sigma%s" % (name, M, N, W, H, "-".join("%g" % s for s in sigmas)),
             "source": [M, N], "template": [W, H], "sigma_max": list(sigmas), "precision": precision,
             "offsets_per_step": len(sigmas) * U * V, "l2": "flushed between steps (256 MiB write)",
-            "sum_tables": "s int%d, s2 int64" % bits, "seed": seed}
+            "sum_tables": "s int32 (modulo 2^32), s2 int64", "seed": seed}
 
 
 # ---------------------------------------------------------------------------
@@ -518,7 +517,7 @@ def run_gpu(args, world, rank, local, pg):
     fd = torch.as_tensor(case.f).to(dev)
     td = torch.as_tensor(case.t).to(dev)
     plans = [sncc.upload_plan(s, dev) for s in segs]
-    tables = sncc.alloc_tables(M, N, None, dev)
+    tables = sncc.alloc_tables(M, N, sncc.match_bits(M, N, segs), dev)
     ws = sncc.integral_workspace(M, N, dev)
     cand_cap, out_cap = U * V, 1 << 16
     mbs = [sncc.alloc_match(M, N, W, H, cand_cap, True, dev) for _ in SIGMAS]
@@ -1067,7 +1066,7 @@ def run_gpu_crossover(args, world, rank, local, pg):
     fd = torch.as_tensor(case.f).to(dev)
     td = torch.as_tensor(case.t).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    tables = sncc.alloc_tables(M, N, None, dev)
+    tables = sncc.alloc_tables(M, N, sncc.match_bits(M, N), dev)
     ws = sncc.integral_workspace(M, N, dev)
 
     def timed(fn, reps):

@@ -55,7 +55,7 @@ typedef struct CUstream_st* sncc_stream_t;
 #define SNCC_OK 0
 #define SNCC_ERR_ARG (-1)       /* bad argument: null pointer, size, stride, bits */
 #define SNCC_ERR_UNIFORM (-2)   /* uniform template or zero-energy approximation (Section 2) */
-#define SNCC_ERR_DTYPE (-3)     /* a 32-bit table was requested where sums can reach 2^31 */
+#define SNCC_ERR_DTYPE (-3)     /* a wrapped 32-bit table where whole entries are read */
 #define SNCC_ERR_CAPACITY (-4)  /* a host-visible capacity is too small */
 #define SNCC_ERR_CUDA (-5)      /* a CUDA runtime call or kernel launch failed */
 #define SNCC_ERR_WORKSPACE (-6) /* workspace missing, misaligned or too small */
@@ -165,10 +165,22 @@ size_t sncc_integral_workspace_bytes(int M, int N);
  *                        multiple of 4
  *   d_ws, ws_bytes       workspace, >= sncc_integral_workspace_bytes(M, N),
  *                        16-byte aligned
- * s_bits = 32 needs 255*M*N < 2^31 (else SNCC_ERR_DTYPE); sums stay exact.
+ * With s_bits = 32 the entries of s are the sums modulo 2^32 (two's
+ * complement): exact while 255*M*N < 2^31, wrapped beyond.  Every window sum
+ * the library forms from a table (at most 255*W*H < 2^31, as W*H <= 2^23) is
+ * a difference of entries and exact in wrapped 32-bit arithmetic, so the
+ * segment-sum, batch and exact-map calls take wrapped tables; only
+ * sncc_refine_segmented, which reads whole entries, rejects them
+ * (SNCC_ERR_DTYPE).  A 32-bit table writes 12 bytes per pixel instead of 16.
  */
 int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int s_bits, int64_t* d_s2,
                   int sat_pitch, void* d_ws, size_t ws_bytes, sncc_stream_t stream);
+
+/* Templates with at most this many corners in all (sncc_plan_info.template_corners)
+ * are summed by sncc_match straight from the corners' table entries, without
+ * staging; that needs whole entries, so with a 32-bit s that may wrap
+ * (255*M*N >= 2^31) they take the staged path instead. */
+#define SNCC_DIRECT_MAX_CORNERS 64
 
 /* Size of the library's built-in scratch array used by sncc_integral_noalloc. */
 #define SNCC_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -229,7 +241,11 @@ int sncc_plan_upload(const sncc_segments* seg, void* d_plan, size_t plan_bytes, 
  * Offsets with rho >= tau are candidates.
  *
  *   seg, d_plan          approximation and its uploaded plan
- *   d_s, s_bits, d_s2    sum tables from sncc_integral, pitch sat_pitch
+ *   d_s, s_bits, d_s2    sum tables from sncc_integral, pitch sat_pitch (a
+ *                        wrapped 32-bit s is fine: only differences below
+ *                        2^31 are used, and a template of at most 64 corners
+ *                        then takes the staged path instead of reading its
+ *                        corners' entries directly)
  *   M, N                 source size
  *   tau                  coarse threshold (e.g. precision * rho_max)
  *   d_rho, rho_pitch     optional FP32 map, V rows x rho_pitch (>= U)
@@ -334,7 +350,9 @@ int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const uint8_t* d
  * Matches have rho >= tau.
  *
  *   seg, d_plan             fine approximation and its uploaded plan
- *   d_s, s_bits, d_s2       sum tables from sncc_integral, pitch sat_pitch
+ *   d_s, s_bits, d_s2       sum tables from sncc_integral, pitch sat_pitch;
+ *                           a 32-bit s must not wrap (255*M*N < 2^31, else
+ *                           SNCC_ERR_DTYPE): this walk reads whole entries
  *   M, N                    source size
  *   d_cand, d_count         candidates and count from sncc_match; the first
  *                           min(*d_count, cand_cap) are read
@@ -671,7 +689,9 @@ typedef struct {
     int32_t runs1;        /* kernels read R + L - 1 table words per run of L for R rows; the
                              pairs below R + D words for two corners D rows apart. */
     int32_t template_corners; /* nonzero corners of the whole template taken as one block: the
-                                 algorithmic multiply-adds per offset (block edges add corners) */
+                                 algorithmic multiply-adds per offset (block edges add corners);
+                                 at most SNCC_DIRECT_MAX_CORNERS: sncc_match reads these corners'
+                                 table entries directly unless a 32-bit s may wrap */
     int32_t wide_blocks;  /* blocks and nonzero corners of the 64 x 64 block layout, which the */
     int32_t wide_corners; /* segment-sum kernels use for templates larger than 64 x 64 */
     int32_t pairs;        /* first layout: pairs of corners of one column 2 .. 7 rows apart with no

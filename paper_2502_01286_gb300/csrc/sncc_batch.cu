@@ -579,7 +579,6 @@ int batch_match_run(const sncc_batch* b, const void* d_buf, const void* const* d
     if (!b || !d_buf || !d_s || !d_s2 || !d_count || !d_counter || !d_status || cand_cap < 0) return SNCC_ERR_ARG;
     if (cand_cap > 0 && !d_cand) return SNCC_ERR_ARG;
     if ((s_bits != 32 && s_bits != 64) || sat_pitch < b->M + 1) return SNCC_ERR_ARG;
-    if (s_bits == 32 && (int64_t)255 * b->M * b->N >= ((int64_t)1 << 31)) return SNCC_ERR_DTYPE;
     if (reinterpret_cast<uintptr_t>(d_buf) & 15) return SNCC_ERR_ARG;
     BatchArgs a;
     std::memset(&a, 0, sizeof(a));

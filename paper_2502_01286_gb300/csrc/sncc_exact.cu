@@ -22,6 +22,7 @@
 
 #include "sncc.h"
 #include "sncc_internal.h"
+#include "sncc_tile.cuh"
 
 namespace sncc {
 namespace {
@@ -30,14 +31,6 @@ constexpr int kTB = 64;            // template block edge
 constexpr int kRB = TILE_U + kTB + 4;  // source region row, bytes (100)
 constexpr int kRW = kRB / 4;           // source region row, words (25)
 constexpr int kTR = kTB + 8;           // staged template rows (8 >= R zero rows)
-
-template <bool S64>
-__device__ __forceinline__ long long sat_read(const void* s, int pitch, int X, int Y) {
-    if constexpr (S64)
-        return static_cast<const long long*>(s)[(size_t)Y * pitch + X];
-    else
-        return static_cast<const int*>(s)[(size_t)Y * pitch + X];
-}
 
 // words of one byte-shifted copy of a region of FR rows, padded so that the
 // four copies start 8 banks apart
@@ -134,8 +127,7 @@ __global__ void __launch_bounds__(256)
     for (int r = 0; r < R; ++r) {
         const int v = v0 + warp * R + r;
         if (u >= U || v >= V) continue;
-        const long long sf = sat_read<S64>(s, pitch, u + W, v + H) - sat_read<S64>(s, pitch, u, v + H) -
-                             sat_read<S64>(s, pitch, u + W, v) + sat_read<S64>(s, pitch, u, v);
+        const long long sf = window_sum<S64>(s, pitch, u, v, W, H);
         const long long sf2 = s2[(size_t)(v + H) * pitch + u + W] - s2[(size_t)(v + H) * pitch + u] -
                               s2[(size_t)v * pitch + u + W] + s2[(size_t)v * pitch + u];
         const long long vf = n * sf2 - sf * sf;

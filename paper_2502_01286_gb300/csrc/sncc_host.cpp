@@ -411,7 +411,7 @@ const char* error_string(int code) {
         case SNCC_OK: return "ok";
         case SNCC_ERR_ARG: return "invalid argument";
         case SNCC_ERR_UNIFORM: return "uniform template or zero-energy approximation";
-        case SNCC_ERR_DTYPE: return "32-bit sum table would overflow";
+        case SNCC_ERR_DTYPE: return "32-bit sum table wraps where whole entries are read";
         case SNCC_ERR_CAPACITY: return "capacity too small";
         case SNCC_ERR_CUDA: return "CUDA error";
         case SNCC_ERR_WORKSPACE: return "workspace missing, misaligned or too small";

@@ -119,7 +119,7 @@ struct Plan {
     std::vector<int32_t> image;  // both layouts, the direct list, then 4 zero words
 };
 
-constexpr int DIRECT_MAX = 64;
+constexpr int DIRECT_MAX = SNCC_DIRECT_MAX_CORNERS;
 
 // Lengths of the vertical corner runs and the int4 units one run occupies.
 constexpr int RUN_LEN[4] = {8, 4, 2, 1};

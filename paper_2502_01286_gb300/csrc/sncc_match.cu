@@ -402,7 +402,6 @@ int prepare_match(const sncc_segments* seg, const void* d_plan, const void* d_s,
     const int U = M - W + 1, V = N - H + 1;
     if (W <= 0 || H <= 0 || U <= 0 || V <= 0) return SNCC_ERR_ARG;
     if (sat_pitch < M + 1 || (sat_pitch & 3)) return SNCC_ERR_ARG;
-    if (s_bits == 32 && (int64_t)255 * M * N >= ((int64_t)1 << 31)) return SNCC_ERR_DTYPE;
     if ((reinterpret_cast<uintptr_t>(d_plan) & 15) || (reinterpret_cast<uintptr_t>(d_s) & 15)) return SNCC_ERR_ARG;
     if ((int64_t)U * V >= ((int64_t)1 << 31)) return SNCC_ERR_UNSUPPORTED;
 
@@ -447,7 +446,12 @@ int prepare_match(const sncc_segments* seg, const void* d_plan, const void* d_s,
     a.Q0 = p->Q0;
     a.tau = tau;
     a.tiles_u = (U + TILE_U - 1) / TILE_U;
-    a.ndirect = p->direct_count;
+    // The whole-template corner list reads table entries themselves, which a
+    // 32-bit table holds only modulo 2^32 once 255*M*N reaches 2^31; staged
+    // regions and window sums are differences below 2^31 (W*H <= 2^23), exact
+    // in wrapped 32-bit arithmetic.
+    const bool wraps = !s64 && (int64_t)255 * M * N >= ((int64_t)1 << 31);
+    a.ndirect = wraps ? 0 : p->direct_count;
     a.direct = reinterpret_cast<const int4*>(static_cast<const char*>(d_plan) + p->direct_offset);
     return SNCC_OK;
 }

@@ -3,29 +3,32 @@
 // Layout: padded tables of (N+1) rows x pitch elements, entry [Y*pitch + X]
 // = sum of f over x < X, y < Y (row 0 and column 0 are zero).
 //
-// The table is produced band by band (R rows each).  A band is independent
-// once its column carries are known:
-//   1. band column sums: for every band and column, the sum of f (and f^2)
-//      over the band's rows;
-//   2. band scan: exclusive prefix of those over the bands, i.e. for every
-//      band and column the sum of the column above the band;
-//   3. band emit (one CTA of 8 warps per band): the band's columns are cut
-//      into 256-column tiles, one lane per 8 output columns.  The CTA first
-//      sums, per tile, the column carries and every row's own values, and
-//      prefixes those sums over the tiles (the corner above-left of each tile
-//      and each row's sum left of it); then each warp walks its tiles row by
-//      row: running column sums in registers, a lane prefix and one warp scan
-//      per row (no CTA barrier), values relative to the tile in int32 and the
-//      carries added in int64, and 16-byte stores.
+// The table is produced band by band (R rows each) and, inside a band, tile
+// by tile (256 output columns).  A (band, tile) is independent once three
+// kinds of sums outside it are known, which the first two passes provide:
+//   1. band column sums: for every band and column the sum of f (and f^2)
+//      over the band's rows; and the row sums of every 256-column chunk of
+//      every row;
+//   2. band scan: exclusive prefix of the column sums over the bands (the
+//      column carries: for every band and column the sum of the column
+//      above the band), and per band the sums of the carries over every
+//      32-column chunk;
+//   3. band emit, one warp per (band, tile): from those it forms the corner
+//      above-left of the tile and, per row, the row sum left of the tile;
+//      then it walks the band's rows with running band-relative column sums
+//      in registers (one lane per 8 columns), a lane prefix and a 32-bit
+//      warp scan per row, adds one 64-bit base per lane, and stores each
+//      tile row through a warp staging buffer as 512-byte stores.
 // Algorithmic traffic: 1 B/px read, 4 or 8 B/px (s) + 8 B/px (s^2) written;
-// pass 1 and the emit's first phase read f once more each (from L2), and the
-// carries are small arrays.
+// pass 1 and the emit read f once each (the second time mostly from L2), and
+// the carry and chunk arrays are small.
 #include <cuda_runtime.h>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 
@@ -35,32 +38,37 @@
 namespace sncc {
 namespace {
 
-constexpr int kEmitWarps = 8;                 // warps per band-emit CTA
+constexpr int kEmitWarps = 8;                 // warps per band-emit CTA, one (band, tile) each
 constexpr int kLaneCols = 8;                  // output columns per lane
 constexpr int kTileCols = 32 * kLaneCols;     // output columns per warp tile
-constexpr int kMaxTiles = 16384 / kTileCols;  // tiles of the widest table (M + 1 <= 16384)
 constexpr int kMaxR = 64;                     // rows per band at most
-constexpr int kTargetTiles = 4864;           // warp tiles (band x 256 columns) in all: about 32 per SM
-                                              // of a 152-SM part; fixed, so that the workspace size
-                                              // depends on the source size alone
+constexpr int kTargetTiles = 4864;           // warp tiles (band x 256 columns) in all, at most: sizes
+                                              // the workspace, and bounds the launch's whole waves
+constexpr int kCarryChunk = 32;               // columns per carry chunk sum (one scan CTA)
 
 struct SatGeometry {
     int R;   // rows per band
     int nb;  // bands
-    int nc;  // 256-column tiles per band
+    int nc;  // 256-column tiles per band (output columns 0 .. M)
+    int nk;  // whole 256-column source chunks per row (the left sums read no other)
+    int nj;  // whole 32-column carry chunks (the corners read no other)
 };
 
+// The workspace geometry: bands sized for about kTargetTiles warp tiles,
+// fixed, so that the workspace size depends on the source size alone.
 SatGeometry sat_geometry(int M, int N) {
     SatGeometry g;
     g.nc = (M + 1 + kTileCols - 1) / kTileCols;  // tiles cover output columns 0 .. M
-    // bands of R rows with about kTargetTiles warp tiles in all; the column-sum
-    // workspace is then 2 * (N / R) * M * 4 bytes <= about 12.6 MB for any
-    // source up to 10^8 pixels
+    // tile c reads the chunks left of X0 = 256c <= M: whole ones only
+    g.nk = M / kTileCols;
+    g.nj = M / kCarryChunk;
+    // bands of R rows with about kTargetTiles warp tiles in all; the column
+    // sums are then 8 (N / R) M bytes, at most M N / 8 (12.5 MB for 10^8
+    // pixels), the row chunk sums M N / 32 and the carry chunk sums M N / 128
+    // at most
     long long r = ((long long)N * g.nc + kTargetTiles - 1) / kTargetTiles;
     // at least N/256 rows (2 to 8): short sources keep about 256 bands for
-    // parallelism, taller ones fewer, shorter passes over the bands (on a
-    // 1920 x 1080 source N/256 took 23.7 us against 25.7 us for N/128 and
-    // 31.9 us for N/512)
+    // parallelism, taller ones fewer, shorter passes over the bands
     const long long rmin = std::min(8LL, std::max(2LL, (long long)N / 256));
     if (r < rmin) r = rmin;
     if (r > kMaxR) r = kMaxR;
@@ -70,115 +78,85 @@ SatGeometry sat_geometry(int M, int N) {
     return g;
 }
 
-// Pass 1: cs1[b][x] = sum_{y in band b} f(x,y); cs2 the same for f^2.
-__global__ void sat_band_colsum(const uint8_t* __restrict__ f, int M, int N, int stride, int R,
-                                int32_t* __restrict__ cs1, int32_t* __restrict__ cs2) {
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    const int b = blockIdx.y;
-    if (x0 >= M) return;
-    const int y0 = b * R;
-    const int y1 = min(y0 + R, N);
-    int a0 = 0, a1 = 0, a2 = 0, a3 = 0, q0 = 0, q1 = 0, q2 = 0, q3 = 0;
-    const bool vec = (x0 + 3 < M) && ((stride & 3) == 0) && ((reinterpret_cast<uintptr_t>(f) & 3) == 0);
-    auto word = [&](int y) -> uint32_t {
-        const uint8_t* row = f + (size_t)y * stride;
-        if (vec) return __ldg(reinterpret_cast<const uint32_t*>(row + x0));
-        uint32_t w = row[x0];
-        if (x0 + 1 < M) w |= (uint32_t)row[x0 + 1] << 8;
-        if (x0 + 2 < M) w |= (uint32_t)row[x0 + 2] << 16;
-        if (x0 + 3 < M) w |= (uint32_t)row[x0 + 3] << 24;
-        return w;
-    };
-    auto add = [&](uint32_t w) {
-        const int p0 = w & 0xff, p1 = (w >> 8) & 0xff, p2 = (w >> 16) & 0xff, p3 = w >> 24;
-        a0 += p0; a1 += p1; a2 += p2; a3 += p3;
-        q0 += p0 * p0; q1 += p1 * p1; q2 += p2 * p2; q3 += p3 * p3;
-    };
-    int y = y0;
-    for (; y + 4 <= y1; y += 4) {  // four rows of loads in flight
-        const uint32_t w0 = word(y), w1 = word(y + 1), w2 = word(y + 2), w3 = word(y + 3);
-        add(w0); add(w1); add(w2); add(w3);
-    }
-    for (; y < y1; ++y) add(word(y));
-    int32_t* o1 = cs1 + (size_t)b * M + x0;
-    int32_t* o2 = cs2 + (size_t)b * M + x0;
-    o1[0] = a0; o2[0] = q0;
-    if (x0 + 1 < M) { o1[1] = a1; o2[1] = q1; }
-    if (x0 + 2 < M) { o1[2] = a2; o2[2] = q2; }
-    if (x0 + 3 < M) { o1[3] = a3; o2[3] = q3; }
+// The launch geometry on a device with `slots` resident emit warps: bands no
+// shorter than the workspace geometry's (so no more of them, and the
+// workspace holds their sums), as short as lets every (band, tile) warp run
+// in a whole number of waves, the largest that kTargetTiles allows.  With
+// slots = 0 (unknown) it is the workspace geometry.
+SatGeometry sat_launch_geometry(int M, int N, long long slots) {
+    SatGeometry g = sat_geometry(M, N);
+    if (slots <= 0) return g;
+    const long long target = std::max(1LL, kTargetTiles / slots) * slots;
+    const long long rmax = std::min<long long>(kMaxR, N);
+    long long r = std::max<long long>(g.R, ((long long)N * g.nc + target - 1) / target);
+    while (r < rmax && ((N + r - 1) / r) * g.nc > target) ++r;
+    g.R = (int)std::min(r, rmax);
+    g.nb = (N + g.R - 1) / g.R;
+    return g;
 }
 
-// Pass 2: in place, cs[b][x] := sum_{b' < b} cs[b'][x] (exclusive over bands).
-// One CTA per 32 columns: lane = column (coalesced rows), warp w of 32 owns a
-// contiguous run of bands; run totals are exchanged through shared memory,
-// so every warp walks only nb/32 bands, twice.
-constexpr int kScanWarps = 32;
+// Workspace: column sums cs1, cs2 (nb x cp int32, cp = M rounded up to a
+// multiple of 4 so that rows take 16-byte stores; carries after pass 2), row
+// chunk sums rs1, rs2 (N x nk int32, by source row), carry chunk sums ch1,
+// ch2 (nb x nj int64); a section may be empty.  Laid out for the workspace
+// geometry, which has at least as many bands as any launch geometry.
+struct SatWorkspace {
+    size_t cs1, cs2, rs1, rs2, ch1, ch2, total;
+};
 
-__global__ void __launch_bounds__(kScanWarps * 32) sat_band_scan(int M, int nb, int32_t* __restrict__ cs1,
-                                                                 int32_t* __restrict__ cs2) {
-    __shared__ int32_t tot1[kScanWarps][32], tot2[kScanWarps][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x = blockIdx.x * 32 + lane;
-    const int per = (nb + kScanWarps - 1) / kScanWarps;
-    const int b0 = min(warp * per, nb), b1 = min(b0 + per, nb);
-    int32_t s1 = 0, s2 = 0;
-    if (x < M) {
-        int b = b0;
-        for (; b + 8 <= b1; b += 8) {
-            int32_t v1[8], v2[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                v1[i] = cs1[(size_t)(b + i) * M + x];
-                v2[i] = cs2[(size_t)(b + i) * M + x];
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { s1 += v1[i]; s2 += v2[i]; }
-        }
-        for (; b < b1; ++b) { s1 += cs1[(size_t)b * M + x]; s2 += cs2[(size_t)b * M + x]; }
-    }
-    tot1[warp][lane] = s1;
-    tot2[warp][lane] = s2;
-    __syncthreads();
-    int32_t r1 = 0, r2 = 0;
-    for (int w = 0; w < warp; ++w) { r1 += tot1[w][lane]; r2 += tot2[w][lane]; }
-    if (x >= M) return;
-    int b = b0;
-    for (; b + 8 <= b1; b += 8) {
-        int32_t v1[8], v2[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            v1[i] = cs1[(size_t)(b + i) * M + x];
-            v2[i] = cs2[(size_t)(b + i) * M + x];
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            cs1[(size_t)(b + i) * M + x] = r1;
-            cs2[(size_t)(b + i) * M + x] = r2;
-            r1 += v1[i];
-            r2 += v2[i];
-        }
-    }
-    for (; b < b1; ++b) {
-        const int32_t v1 = cs1[(size_t)b * M + x], v2 = cs2[(size_t)b * M + x];
-        cs1[(size_t)b * M + x] = r1;
-        cs2[(size_t)b * M + x] = r2;
-        r1 += v1;
-        r2 += v2;
-    }
+int col_pitch(int M) { return (M + 3) & ~3; }
+
+SatWorkspace sat_workspace(int M, int N, const SatGeometry& g) {
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    SatWorkspace w;
+    size_t o = 0;
+    w.cs1 = o;
+    o = al(o + (size_t)g.nb * col_pitch(M) * 4);
+    w.cs2 = o;
+    o = al(o + (size_t)g.nb * col_pitch(M) * 4);
+    w.rs1 = o;
+    o = al(o + (size_t)N * g.nk * 4);
+    w.rs2 = o;
+    o = al(o + (size_t)N * g.nk * 4);
+    w.ch1 = o;
+    o = al(o + (size_t)g.nb * g.nj * 8);
+    w.ch2 = o;
+    o = al(o + (size_t)g.nb * g.nj * 8);
+    w.total = o;
+    return w;
 }
 
-// Pass 3: one CTA per band b.  Output column X of the table holds sources
-// x < X, so tile c (outputs X = 256c .. 256c+255) owns the sources
-// x = 256c - 1 .. 256c + 254, and lane l of a tile the sources
-// 256c + 8l - 1 .. 256c + 8l + 6.  For output (X, Y) of the band, Y = y + 1:
-//   s = [x < 256c-1, y < y0]        corner[c]        (prefix of P over tiles)
-//     + [x < 256c-1, y0 <= y' <= y] sum of left[c][y'] (prefix of T over tiles)
-//     + [own x <= X-1, y < y0]      top carry of the lane's column
-//     + [own x <= X-1, y0 <= y' <= y] running column sums, prefixed along the tile.
-// The first two come from the CTA's first phase (P: a tile's column carries
-// summed; T: a tile's own values of one row summed), the last two from a lane
-// prefix plus a warp scan.  Relative sums of one band and tile stay below
-// 256 * 64 * 65025 < 2^31.
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Warp sum of non-negative 32-bit values whose total fits 32 bits: one
+// reduction instruction.
+__device__ __forceinline__ int32_t warp_sum_u32(int32_t v) {
+    return (int32_t)__reduce_add_sync(0xffffffffu, (uint32_t)v);
+}
+
+// Warp sum of non-negative 32-bit values as a 64-bit total: the low and
+// high halves reduced separately (each total below 2^21).
+__device__ __forceinline__ int64_t warp_sum_wide(int32_t v) {
+    const uint32_t lo = __reduce_add_sync(0xffffffffu, (uint32_t)v & 0xffffu);
+    const uint32_t hi = __reduce_add_sync(0xffffffffu, (uint32_t)v >> 16);
+    return ((int64_t)hi << 16) + (int64_t)lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_exclusive_scan(T v, int lane) {
+    T inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    return inc - v;
+}
 
 // Raw source bytes xa .. xa+7 of a row (zero from column M on), one 8-byte
 // load when aligned and inside the row.
@@ -193,9 +171,177 @@ __device__ __forceinline__ uint2 load_word(const uint8_t* row, int M, int xa, bo
     return make_uint2(lo, hi);
 }
 
-// Lane l of a tile starting at output column X0 owns the sources
-// x = X0 + 8l - 1 .. X0 + 8l + 6: bytes 0..6 of its own word (xa = X0 + 8l)
-// and byte 7 of the previous lane's word; lane 0 reads x = X0 - 1 itself.
+__device__ __forceinline__ int byte_of(uint2 w, int e) {
+    return (int)(((e < 4) ? (w.x >> (8 * e)) : (w.y >> (8 * (e - 4)))) & 0xffu);
+}
+
+// Pass 1: cs1[b][x] = sum_{y in band b} f(x, y), cs2 the same for f^2
+// (rows of cp columns, those past M zero); and rs1[y nk + k] = sum of f
+// over columns 256k .. 256k+255 of row y (rs2 for f^2), for the whole
+// chunks k < nk.  A lane owns 8 columns, a warp one 256-column chunk; the
+// next four rows load while four are summed.
+constexpr int kColRows = 4;
+
+__global__ void __launch_bounds__(256) sat_band_colsum(const uint8_t* __restrict__ f, int M, int N, int stride,
+                                                       int R, int nk, int cp, int32_t* __restrict__ cs1,
+                                                       int32_t* __restrict__ cs2, int32_t* __restrict__ rs1,
+                                                       int32_t* __restrict__ rs2) {
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * kLaneCols;
+    const int k = x0 / kTileCols;  // the warp's chunk
+    if (x0 - kLaneCols * lane >= cp) return;  // the whole warp is past the row
+    const int b = blockIdx.y;
+    const int y0 = b * R, y1 = min(y0 + R, N);
+    const bool vec = ((stride & 7) == 0) && ((reinterpret_cast<uintptr_t>(f) & 7) == 0);
+    int a[kLaneCols], q[kLaneCols];
+#pragma unroll
+    for (int e = 0; e < kLaneCols; ++e) a[e] = q[e] = 0;
+    auto load_rows = [&](uint2 (&w)[kColRows], int y) {
+#pragma unroll
+        for (int i = 0; i < kColRows; ++i)
+            w[i] = (x0 < M && y + i < y1) ? load_word(f + (size_t)(y + i) * stride, M, x0, vec) : make_uint2(0u, 0u);
+    };
+    uint2 cur[kColRows], nxt[kColRows];
+    load_rows(cur, y0);
+    for (int y = y0; y < y1; y += kColRows) {  // warp-uniform
+        if (y + kColRows < y1) load_rows(nxt, y + kColRows);
+        int s1[kColRows], s2[kColRows];
+#pragma unroll
+        for (int i = 0; i < kColRows; ++i) {
+            s1[i] = s2[i] = 0;
+#pragma unroll
+            for (int e = 0; e < kLaneCols; ++e) {
+                const int p = byte_of(cur[i], e);
+                a[e] += p;
+                q[e] += p * p;
+                s1[i] += p;
+                s2[i] += p * p;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kColRows; ++i) {
+            s1[i] = warp_sum_u32(s1[i]);  // at most 255^2 x 256 < 2^31
+            s2[i] = warp_sum_u32(s2[i]);
+        }
+        if (lane == 0 && k < nk) {
+#pragma unroll
+            for (int i = 0; i < kColRows; ++i)
+                if (y + i < y1) {
+                    rs1[(size_t)(y + i) * nk + k] = s1[i];
+                    rs2[(size_t)(y + i) * nk + k] = s2[i];
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < kColRows; ++i) cur[i] = nxt[i];
+    }
+    // columns x0 .. x0+7 as two 16-byte stores each (cp and x0 are multiples
+    // of 4; columns from M to cp hold zeros)
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (x0 + 4 * h < cp) {
+            *reinterpret_cast<int4*>(cs1 + (size_t)b * cp + x0 + 4 * h) =
+                make_int4(a[4 * h], a[4 * h + 1], a[4 * h + 2], a[4 * h + 3]);
+            *reinterpret_cast<int4*>(cs2 + (size_t)b * cp + x0 + 4 * h) =
+                make_int4(q[4 * h], q[4 * h + 1], q[4 * h + 2], q[4 * h + 3]);
+        }
+}
+
+// Pass 2: in place, cs[b][x] := sum_{b' < b} cs[b'][x] (exclusive over
+// bands), and ch[b][j] = sum of the new cs[b][x] over the 32 columns of
+// chunk j = blockIdx.x when it is whole (j < nj).  One CTA per 32 columns:
+// lane = column (coalesced rows), warp w of 32 owns a contiguous run of
+// bands; run totals are exchanged through shared memory, so every warp
+// walks only nb/32 bands, twice, eight bands' loads at a time.
+constexpr int kScanWarps = 32;
+constexpr int kScanBatch = 4;
+
+__global__ void __launch_bounds__(kScanWarps * 32) sat_band_scan(int M, int nb, int nj, int cp,
+                                                                 int32_t* __restrict__ cs1,
+                                                                 int32_t* __restrict__ cs2,
+                                                                 int64_t* __restrict__ ch1,
+                                                                 int64_t* __restrict__ ch2) {
+    __shared__ int32_t tot1[kScanWarps][32], tot2[kScanWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = blockIdx.x * 32 + lane;
+    const bool in = x < M;
+    const int per = (nb + kScanWarps - 1) / kScanWarps;
+    const int b0 = min(warp * per, nb), b1 = min(b0 + per, nb);
+    int32_t s1 = 0, s2 = 0;
+    for (int b = b0; b < b1; b += kScanBatch) {  // warp-uniform
+        int32_t v1[kScanBatch], v2[kScanBatch];
+#pragma unroll
+        for (int i = 0; i < kScanBatch; ++i) {
+            const bool ok = in && b + i < b1;
+            v1[i] = ok ? cs1[(size_t)(b + i) * cp + x] : 0;
+            v2[i] = ok ? cs2[(size_t)(b + i) * cp + x] : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kScanBatch; ++i) {
+            s1 += v1[i];
+            s2 += v2[i];
+        }
+    }
+    tot1[warp][lane] = s1;
+    tot2[warp][lane] = s2;
+    __syncthreads();
+    int32_t r1 = 0, r2 = 0;
+    for (int w = 0; w < warp; ++w) {
+        r1 += tot1[w][lane];
+        r2 += tot2[w][lane];
+    }
+    // every lane stays in the loop (the chunk sums reduce over the warp);
+    // columns past M contribute zeros
+    for (int b = b0; b < b1; b += kScanBatch) {
+        int32_t v1[kScanBatch], v2[kScanBatch];
+#pragma unroll
+        for (int i = 0; i < kScanBatch; ++i) {
+            const bool ok = in && b + i < b1;
+            v1[i] = ok ? cs1[(size_t)(b + i) * cp + x] : 0;
+            v2[i] = ok ? cs2[(size_t)(b + i) * cp + x] : 0;
+        }
+        // v becomes the exclusive carries (zero past M)
+#pragma unroll
+        for (int i = 0; i < kScanBatch; ++i) {
+            const int32_t t1 = v1[i], t2 = v2[i];
+            v1[i] = in ? r1 : 0;
+            v2[i] = in ? r2 : 0;
+            if (in && b + i < b1) {
+                cs1[(size_t)(b + i) * cp + x] = r1;
+                cs2[(size_t)(b + i) * cp + x] = r2;
+            }
+            r1 += t1;
+            r2 += t2;
+        }
+        if ((int)blockIdx.x < nj) {  // block-uniform
+#pragma unroll
+            for (int i = 0; i < kScanBatch; ++i) {
+                const int64_t c1 = warp_sum_wide(v1[i]), c2 = warp_sum_wide(v2[i]);
+                if (lane == 0 && b + i < b1) {
+                    ch1[(size_t)(b + i) * nj + blockIdx.x] = c1;
+                    ch2[(size_t)(b + i) * nj + blockIdx.x] = c2;
+                }
+            }
+        }
+    }
+}
+
+// Pass 3: one warp per (band b, tile c).  Output column X of the table holds
+// sources x < X, so tile c (outputs X = 256c .. 256c+255, X0 = 256c) owns
+// the sources x = X0 - 1 .. X0 + 254, and lane l the sources
+// X0 + 8l - 1 .. X0 + 8l + 6: bytes 0..6 of its own word (xa = X0 + 8l) and
+// byte 7 of the previous lane's word; lane 0 reads x = X0 - 1 itself.  For
+// output (X, Y) with Y = y0 + r + 1 (row r of the band), X = X0 + 8l + e + ... :
+//   s = P                               sum over x < X0-1, y < y0 (corner)
+//     + L[r]                            sum over x < X0-1, y0 <= y <= y0+r (left)
+//     + sum_{x' = X0-1 .. x} carry[x']  (above the band, own columns)
+//     + sum_{x' = X0-1 .. x} rel_r[x']  (band rows so far, own columns)
+// P and the carries of the lanes before this one form one 64-bit base per
+// lane.  L[r] covers x < X0 - 1 and the band rows 0 .. r: int32 for f (at
+// most 255 x 16383 x 64 < 2^31), int64 for f^2.  The band rows of the lanes
+// before this one take a 32-bit scan (at most 31 x 8 x 64 x 255^2 < 2^31).
+// Each of the lane's own columns (carry plus band rows, at most 255^2 N <
+// 2^31) is then added to a 64-bit running sum that starts at the base plus
+// those two.
 struct LaneRow {
     uint2 w;
     int edge;  // lane 0: source X0 - 1 (0 outside the row); other lanes unused
@@ -209,52 +355,26 @@ __device__ __forceinline__ LaneRow load_lane_row(const uint8_t* row, int M, int 
     return r;
 }
 
-__device__ __forceinline__ void unpack_lane_row(const LaneRow& r, int lane, int (&v)[8]) {
+// The lane's eight sources x = X0 + 8l - 1 + e as the bytes e of one packed
+// pair: the previous lane's last byte (lane 0: the edge) and its own first
+// seven.
+__device__ __forceinline__ uint2 unpack_lane_row(const LaneRow& r, int lane) {
     const uint32_t prev = __shfl_up_sync(0xffffffffu, r.w.y, 1);
-    v[0] = (lane > 0) ? (int)(prev >> 24) : r.edge;
-#pragma unroll
-    for (int e = 1; e < 8; ++e)
-        v[e] = (int)(((e - 1 < 4) ? (r.w.x >> (8 * (e - 1))) : (r.w.y >> (8 * (e - 5)))) & 0xff);
+    const uint32_t first = (lane > 0) ? (prev >> 24) : (uint32_t)r.edge;
+    return make_uint2((r.w.x << 8) | first, __funnelshift_l(r.w.x, r.w.y, 8));
 }
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_exclusive_scan(T v, int lane) {
-    T inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const T t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    return inc - v;
-}
-
-constexpr int kAhead = 4;  // source rows in flight per warp
+constexpr int kAhead = 2;  // source rows in flight per warp
 constexpr int kLaneStride = 80;  // staging bytes per lane: up to 64 data + 16 pad (conflict-free quarter-warps)
 constexpr int kStageBytes = 32 * kLaneStride;
+constexpr int kWarpSmem = kStageBytes + kMaxR * (4 + 8);  // staging, then the left sums L1[R] (int32), L2[R] (int64)
+static_assert(kStageBytes % 16 == 0 && kWarpSmem % 16 == 0, "per-warp shared memory keeps 16-byte alignment");
 
-// Writes the lane's eight outputs a + col[0], a + col[0] + col[1], ... (as T)
-// into the warp's staging buffer, then the warp stores the 256 values of the
-// tile row to dst with 16-byte lane-consecutive stores (512 bytes each).
+// The warp stores the 256 values (as T) its lanes wrote into the staging
+// buffer (lane l's eight at lane l * kLaneStride) to dst with 16-byte
+// lane-consecutive stores (512 bytes each).
 template <typename T>
-__device__ __forceinline__ void stage_row(unsigned char* stage, int lane, const int32_t (&col)[kLaneCols], int64_t a,
-                                          T* dst) {
-    T o[kLaneCols];
-#pragma unroll
-    for (int e = 0; e < kLaneCols; ++e) {
-        a += col[e];
-        o[e] = (T)a;
-    }
-    unsigned char* mine = stage + lane * kLaneStride;
-#pragma unroll
-    for (int k = 0; k < (int)(kLaneCols * sizeof(T)) / 16; ++k)
-        *reinterpret_cast<int4*>(mine + 16 * k) = *reinterpret_cast<const int4*>(reinterpret_cast<const char*>(o) + 16 * k);
+__device__ __forceinline__ void stage_flush(const unsigned char* stage, int lane, T* dst) {
     __syncwarp();
     constexpr int rowbytes = kTileCols * (int)sizeof(T);
 #pragma unroll
@@ -269,166 +389,201 @@ __device__ __forceinline__ void stage_row(unsigned char* stage, int lane, const 
 
 template <typename ST>
 __global__ void __launch_bounds__(kEmitWarps * 32, 3) sat_band_emit(const uint8_t* __restrict__ f, int M, int N,
-                                                                 int stride, int R, int nc, int pitch,
-                                                                 const int32_t* __restrict__ ca1,
+                                                                 int stride, int R, int nb, int nc, int nk, int nj,
+                                                                 int cp, int pitch, const int32_t* __restrict__ ca1,
                                                                  const int32_t* __restrict__ ca2,
-                                                                 ST* __restrict__ s, int64_t* __restrict__ s2) {
+                                                                 const int32_t* __restrict__ rs1,
+                                                                 const int32_t* __restrict__ rs2,
+                                                                 const int64_t* __restrict__ ch1,
+                                                                 const int64_t* __restrict__ ch2, ST* __restrict__ s,
+                                                                 int64_t* __restrict__ s2) {
     extern __shared__ __align__(16) unsigned char emit_smem[];
-    // per-warp output staging (lane stride 80 bytes: 64 data + 16 pad), then
-    // the per-tile row sums T (nc x R int32 each)
-    unsigned char* stage = emit_smem + (size_t)(threadIdx.x >> 5) * kStageBytes;
-    int32_t* T1 = reinterpret_cast<int32_t*>(emit_smem + kEmitWarps * kStageBytes);
-    int32_t* T2 = T1 + (size_t)nc * R;
-    __shared__ int64_t P1[kMaxTiles], P2[kMaxTiles];
-    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pair = blockIdx.x * kEmitWarps + warp;
+    if (pair >= nb * nc) return;  // whole warp
+    const int b = pair / nc, c = pair % nc;
+    unsigned char* stage = emit_smem + (size_t)warp * kWarpSmem;
+    int32_t* L1 = reinterpret_cast<int32_t*>(stage + kStageBytes);
+    int64_t* L2 = reinterpret_cast<int64_t*>(stage + kStageBytes + kMaxR * 4);
     const int y0 = b * R, nr = min(R, N - y0);
-    const int32_t* cab1 = ca1 + (size_t)b * M;  // column sums above this band
-    const int32_t* cab2 = ca2 + (size_t)b * M;
+    const int X0 = c * kTileCols, Xl = X0 + kLaneCols * lane;
+    const int32_t* cab1 = ca1 + (size_t)b * cp;  // column sums above this band
+    const int32_t* cab2 = ca2 + (size_t)b * cp;
     const bool vec = ((stride & 7) == 0) && ((reinterpret_cast<uintptr_t>(f) & 7) == 0);
     const uint8_t* fband = f + (size_t)y0 * stride;
 
-    // Phase 1: per tile, the column sums above the band over its sources (P)
-    // and every row's own values (T), each summed over the tile.
-    for (int c = warp; c < nc; c += kEmitWarps) {
-        const int X0 = c * kTileCols;
-        int64_t p1 = 0, p2 = 0;
-#pragma unroll
-        for (int e = 0; e < kLaneCols; ++e) {
-            const int x = X0 + kLaneCols * lane - 1 + e;
-            if (x >= 0 && x < M) {
-                p1 += cab1[x];
-                p2 += cab2[x];
+    // ---- prologue: the corner P and the left sums L[r] ----
+    int64_t p1 = 0, p2 = 0;
+    for (int j = lane; j < c * (kTileCols / kCarryChunk); j += 32) {
+        p1 += ch1[(size_t)b * nj + j];
+        p2 += ch2[(size_t)b * nj + j];
+    }
+    p1 = warp_sum(p1);
+    p2 = warp_sum(p2);
+    if (c > 0) {  // the chunks cover x < X0; the corner stops at X0 - 1
+        p1 -= cab1[X0 - 1];
+        p2 -= cab2[X0 - 1];
+    }
+    // lane l owns band rows l and l + 32: its row's chunk sums left of X0
+    // less the edge pixel x = X0 - 1, then an inclusive scan over the rows
+    int32_t cum1 = 0;  // running totals of the rows before this half
+    int64_t cum2 = 0;
+    for (int h = 0; h * 32 < nr; ++h) {
+        const int r = h * 32 + lane;
+        int32_t l1 = 0, l2 = 0;
+        if (r < nr) {
+            const int32_t* q1 = rs1 + (size_t)(y0 + r) * nk;
+            const int32_t* q2 = rs2 + (size_t)(y0 + r) * nk;
+#pragma unroll 4
+            for (int k = 0; k < c; ++k) {
+                l1 += q1[k];
+                l2 += q2[k];
+            }
+            if (c > 0) {
+                const int e = fband[(size_t)r * stride + X0 - 1];
+                l1 -= e;
+                l2 -= e * e;
             }
         }
-        p1 = warp_sum(p1);
-        p2 = warp_sum(p2);
-        if (lane == 0) {
-            P1[c] = p1;
-            P2[c] = p2;
+        const int32_t i1 = cum1 + l1 + warp_exclusive_scan(l1, lane);
+        const int64_t i2 = cum2 + (int64_t)l2 + warp_exclusive_scan((int64_t)l2, lane);
+        if (r < nr) {
+            L1[r] = i1;
+            L2[r] = i2;
         }
-        for (int r0 = 0; r0 < nr; r0 += kAhead) {
-            LaneRow q[kAhead];
-#pragma unroll
-            for (int i = 0; i < kAhead; ++i)
-                if (r0 + i < nr) q[i] = load_lane_row(fband + (size_t)(r0 + i) * stride, M, X0, lane, vec);
-#pragma unroll
-            for (int i = 0; i < kAhead; ++i) {
-                if (r0 + i >= nr) break;
-                int v[8];
-                unpack_lane_row(q[i], lane, v);
-                int t1 = 0, t2 = 0;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    t1 += v[e];
-                    t2 += v[e] * v[e];
-                }
-                t1 = warp_sum(t1);
-                t2 = warp_sum(t2);
-                if (lane == 0) {
-                    T1[c * R + r0 + i] = t1;
-                    T2[c * R + r0 + i] = t2;
-                }
-            }
-        }
+        cum1 = __shfl_sync(0xffffffffu, i1, 31);
+        cum2 = __shfl_sync(0xffffffffu, i2, 31);
     }
-    __syncthreads();
-    // Exclusive prefixes over the tiles: thread r < nr for row r, thread nr for P.
-    if ((int)threadIdx.x < nr) {
-        const int r = threadIdx.x;
-        int32_t a1 = 0, a2 = 0;
-        for (int c = 0; c < nc; ++c) {
-            const int32_t t1 = T1[c * R + r], t2 = T2[c * R + r];
-            T1[c * R + r] = a1;
-            T2[c * R + r] = a2;
-            a1 += t1;
-            a2 += t2;
-        }
-    } else if ((int)threadIdx.x == nr) {
-        int64_t a1 = 0, a2 = 0;
-        for (int c = 0; c < nc; ++c) {
-            const int64_t p1 = P1[c], p2 = P2[c];
-            P1[c] = a1;
-            P2[c] = a2;
-            a1 += p1;
-            a2 += p2;
-        }
+    // the lane's columns: col[e] = carry above the band plus the band's rows
+    // so far (fits 32 bits: at most 65025 N < 2^31); the 64-bit base is the
+    // corner plus the carries of the lanes before this one
+    int32_t col1[kLaneCols], col2[kLaneCols];
+    uint32_t tc1 = 0, tc2 = 0;  // the lane's carry totals
+#pragma unroll
+    for (int e = 0; e < kLaneCols; ++e) {
+        const int x = Xl - 1 + e;
+        const bool in = (x >= 0 && x < M);
+        col1[e] = in ? cab1[x] : 0;
+        col2[e] = in ? cab2[x] : 0;
+        tc1 += (uint32_t)col1[e];
+        tc2 += (uint32_t)col2[e];
     }
-    __syncthreads();
+    const int64_t base1 = p1 + warp_exclusive_scan((int64_t)tc1, lane);
+    const int64_t base2 = p2 + warp_exclusive_scan((int64_t)tc2, lane);
+    __syncwarp();
 
-    // Phase 2: the band's outputs, tile by tile.  col holds the lane's
-    // absolute column sums (above the band plus the band's rows so far), which
-    // fit int32; the prefix along the tile is formed in int64 as it is stored.
     if (b == 0) {  // row Y = 0 of the table is zero
-        for (int X = threadIdx.x; X <= M; X += blockDim.x) {
+        for (int X = X0 + lane; X < min(X0 + kTileCols, M + 1); X += 32) {
             s[X] = 0;
             s2[X] = 0;
         }
     }
-    for (int c = warp; c < nc; c += kEmitWarps) {
-        const int X0 = c * kTileCols, Xl = X0 + kLaneCols * lane;
-        int32_t col1[kLaneCols], col2[kLaneCols];
+
+    // ---- the band's rows, two per iteration so that their scans overlap ----
+    const bool full_tile = (X0 + kTileCols - 1 <= M);  // warp-uniform
+    unsigned char* mine = stage + lane * kLaneStride;
+    // one row's outputs: 64-bit running sums from the base plus the row part
+    // before the lane, one column at a time
+    auto emit_row = [&](int r, int32_t pre1, int64_t pre2) {
+        ST* srow = s + (size_t)(y0 + r + 1) * pitch;
+        int64_t* s2row = s2 + (size_t)(y0 + r + 1) * pitch;
+        int64_t run1 = base1 + pre1, run2 = base2 + pre2;
+        if (full_tile) {
+            // through the warp's staging buffer, so that every global store
+            // instruction writes 512 contiguous bytes
+            if constexpr (sizeof(ST) == 8) {
 #pragma unroll
-        for (int e = 0; e < kLaneCols; ++e) {
-            const int x = Xl - 1 + e;
-            const bool in = (x >= 0 && x < M);
-            col1[e] = in ? cab1[x] : 0;
-            col2[e] = in ? cab2[x] : 0;
-        }
-        int64_t left1 = P1[c], left2 = P2[c];  // corner, then plus the rows' left sums
-        const bool full_tile = (X0 + kTileCols - 1 <= M);  // warp-uniform
-        LaneRow q[kAhead];
-#pragma unroll
-        for (int i = 0; i < kAhead; ++i)
-            if (i < nr) q[i] = load_lane_row(fband + (size_t)i * stride, M, X0, lane, vec);
-        for (int r = 0; r < nr; ++r) {
-            int v[8];
-            unpack_lane_row(q[0], lane, v);
-#pragma unroll
-            for (int i = 0; i < kAhead - 1; ++i) q[i] = q[i + 1];
-            if (r + kAhead < nr) q[kAhead - 1] = load_lane_row(fband + (size_t)(r + kAhead) * stride, M, X0, lane, vec);
-            int64_t t1 = 0, t2 = 0;
-#pragma unroll
-            for (int e = 0; e < kLaneCols; ++e) {
-                col1[e] += v[e];
-                col2[e] += v[e] * v[e];
-                t1 += col1[e];
-                t2 += col2[e];
-            }
-            left1 += T1[c * R + r];
-            left2 += T2[c * R + r];
-            int64_t a1 = left1 + warp_exclusive_scan(t1, lane), a2 = left2 + warp_exclusive_scan(t2, lane);
-            ST* srow = s + (size_t)(y0 + r + 1) * pitch;
-            int64_t* s2row = s2 + (size_t)(y0 + r + 1) * pitch;
-            if (full_tile) {
-                // through the warp's staging buffer, so that every global store
-                // instruction writes 512 contiguous bytes
-                stage_row<ST>(stage, lane, col1, a1, srow + X0);
-                stage_row<int64_t>(stage, lane, col2, a2, s2row + X0);
+                for (int e = 0; e < kLaneCols; e += 2) {
+                    const int64_t o0 = (run1 += col1[e]);
+                    const int64_t o1 = (run1 += col1[e + 1]);
+                    *reinterpret_cast<longlong2*>(mine + 8 * e) = make_longlong2(o0, o1);
+                }
             } else {
 #pragma unroll
-                for (int e = 0; e < kLaneCols; ++e) {
-                    a1 += col1[e];
-                    a2 += col2[e];
-                    if (Xl + e <= M) {
-                        srow[Xl + e] = (ST)a1;
-                        s2row[Xl + e] = a2;
-                    }
+                for (int e = 0; e < kLaneCols; e += 4) {
+                    int4 o;
+                    o.x = (int)(run1 += col1[e]);
+                    o.y = (int)(run1 += col1[e + 1]);
+                    o.z = (int)(run1 += col1[e + 2]);
+                    o.w = (int)(run1 += col1[e + 3]);
+                    *reinterpret_cast<int4*>(mine + 4 * e) = o;
+                }
+            }
+            stage_flush<ST>(stage, lane, srow + X0);
+#pragma unroll
+            for (int e = 0; e < kLaneCols; e += 2) {
+                const int64_t o0 = (run2 += col2[e]);
+                const int64_t o1 = (run2 += col2[e + 1]);
+                *reinterpret_cast<longlong2*>(mine + 8 * e) = make_longlong2(o0, o1);
+            }
+            stage_flush<int64_t>(stage, lane, s2row + X0);
+        } else {
+#pragma unroll
+            for (int e = 0; e < kLaneCols; ++e) {
+                run1 += col1[e];
+                run2 += col2[e];
+                if (Xl + e <= M) {
+                    srow[Xl + e] = (ST)run1;
+                    s2row[Xl + e] = run2;
                 }
             }
         }
+    };
+    LaneRow q[kAhead];
+#pragma unroll
+    for (int i = 0; i < kAhead; ++i)
+        if (i < nr) q[i] = load_lane_row(fband + (size_t)i * stride, M, X0, lane, vec);
+    for (int r = 0; r < nr; ++r) {
+        const uint2 va = unpack_lane_row(q[0], lane);
+#pragma unroll
+        for (int i = 0; i < kAhead - 1; ++i) q[i] = q[i + 1];
+        if (r + kAhead < nr) q[kAhead - 1] = load_lane_row(fband + (size_t)(r + kAhead) * stride, M, X0, lane, vec);
+        uint32_t a1 = 0, a2 = 0;
+#pragma unroll
+        for (int e = 0; e < kLaneCols; ++e) {
+            const int pa = byte_of(va, e);
+            col1[e] += pa;
+            col2[e] += pa * pa;
+            a1 += (uint32_t)col1[e];
+            a2 += (uint32_t)col2[e];
+        }
+        emit_row(r, L1[r] + (int32_t)warp_exclusive_scan(a1 - tc1, lane),
+                 L2[r] + (int64_t)warp_exclusive_scan(a2 - tc2, lane));
     }
 }
 
-// The emit kernel's dynamic shared memory can exceed the 48 KB default
-// (staging 20 KB + row sums up to 32 KB).
+// Emit warps resident on the whole current device at once (0 if unknown),
+// cached per device: both table widths' kernels, the smaller.
+long long emit_slots() {
+    constexpr int kMaxDevices = 128;
+    static std::atomic<long long> cached[kMaxDevices];  // 0 = not yet queried
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+    if (dev < kMaxDevices) {
+        const long long c = cached[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    const size_t smem = (size_t)kEmitWarps * kWarpSmem;
+    int n32 = 0, n64 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n32, sat_band_emit<int32_t>, kEmitWarps * 32, smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n64, sat_band_emit<int64_t>, kEmitWarps * 32, smem) !=
+            cudaSuccess)
+        return 0;
+    const long long n = (long long)std::min(n32, n64) * kEmitWarps * sm_count();
+    if (n <= 0) return 0;
+    if (dev < kMaxDevices) cached[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 cudaError_t set_emit_attributes() {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        const int most = kEmitWarps * kStageBytes + 2 * kMaxTiles * kMaxR * (int)sizeof(int32_t);
-        err = cudaFuncSetAttribute(sat_band_emit<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        const int smem = kEmitWarps * kWarpSmem;
+        err = cudaFuncSetAttribute(sat_band_emit<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(sat_band_emit<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+            err = cudaFuncSetAttribute(sat_band_emit<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
     return err;
 }
@@ -439,7 +594,7 @@ cudaError_t set_emit_attributes() {
 extern "C" size_t sncc_integral_workspace_bytes(int M, int N) {
     if (M <= 0 || N <= 0) return 0;
     const sncc::SatGeometry g = sncc::sat_geometry(M, N);
-    return (size_t)2 * g.nb * (size_t)M * sizeof(int32_t) + 256;
+    return sncc::sat_workspace(M, N, g).total;
 }
 
 extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, void* d_s, int s_bits, int64_t* d_s2,
@@ -451,27 +606,37 @@ extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, voi
     if (M > 16383 || N > 65535) return SNCC_ERR_UNSUPPORTED;
     if (sat_pitch < M + 1 || (sat_pitch & 3)) return SNCC_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(d_s) & 15) || (reinterpret_cast<uintptr_t>(d_s2) & 15)) return SNCC_ERR_ARG;
-    // s fits in int32 only while its largest entry 255*M*N does; the column
-    // sums of f^2 kept in int32 need N*65025 < 2^31.
-    if (s_bits == 32 && (int64_t)255 * M * N >= ((int64_t)1 << 31)) return SNCC_ERR_DTYPE;
+    // A 32-bit s holds the sums modulo 2^32 (exact while 255*M*N < 2^31); the
+    // column sums of f^2 kept in int32 need N*65025 < 2^31.
     if ((int64_t)N * 65025 >= ((int64_t)1 << 31)) return SNCC_ERR_UNSUPPORTED;
     if (!d_ws || ws_bytes < sncc_integral_workspace_bytes(M, N) || (reinterpret_cast<uintptr_t>(d_ws) & 15))
         return SNCC_ERR_WORKSPACE;
-    const SatGeometry g = sat_geometry(M, N);
-    int32_t* cs1 = static_cast<int32_t*>(d_ws);
-    int32_t* cs2 = cs1 + (size_t)g.nb * M;
+    const SatWorkspace w = sat_workspace(M, N, sat_geometry(M, N));
+    const SatGeometry g = sat_launch_geometry(M, N, emit_slots());
+    char* ws = static_cast<char*>(d_ws);
+    int32_t* cs1 = reinterpret_cast<int32_t*>(ws + w.cs1);
+    int32_t* cs2 = reinterpret_cast<int32_t*>(ws + w.cs2);
+    int32_t* rs1 = reinterpret_cast<int32_t*>(ws + w.rs1);
+    int32_t* rs2 = reinterpret_cast<int32_t*>(ws + w.rs2);
+    int64_t* ch1 = reinterpret_cast<int64_t*>(ws + w.ch1);
+    int64_t* ch2 = reinterpret_cast<int64_t*>(ws + w.ch2);
     cudaStream_t st = (cudaStream_t)stream;
-    dim3 g1((M / 4 + 1 + 255) / 256, g.nb);
-    sat_band_colsum<<<g1, 256, 0, st>>>(d_f, M, N, f_stride, g.R, cs1, cs2);
-    sat_band_scan<<<(M + 31) / 32, kScanWarps * 32, 0, st>>>(M, g.nb, cs1, cs2);
-    const size_t smem = (size_t)kEmitWarps * kStageBytes + (size_t)2 * g.nc * g.R * sizeof(int32_t);
+    const dim3 g1((M + 256 * kLaneCols - 1) / (256 * kLaneCols), g.nb);
+    const int cp = col_pitch(M);
+    sat_band_colsum<<<g1, 256, 0, st>>>(d_f, M, N, f_stride, g.R, g.nk, cp, cs1, cs2, rs1, rs2);
+    sat_band_scan<<<(M + kCarryChunk - 1) / kCarryChunk, kScanWarps * 32, 0, st>>>(M, g.nb, g.nj, cp, cs1, cs2,
+                                                                                   ch1, ch2);
     if (set_emit_attributes() != cudaSuccess) return SNCC_ERR_CUDA;
+    const int ctas = (g.nb * g.nc + kEmitWarps - 1) / kEmitWarps;
+    const size_t smem = (size_t)kEmitWarps * kWarpSmem;
     if (s_bits == 32)
-        sat_band_emit<int32_t><<<g.nb, kEmitWarps * 32, smem, st>>>(d_f, M, N, f_stride, g.R, g.nc, sat_pitch, cs1,
-                                                                   cs2, static_cast<int32_t*>(d_s), d_s2);
+        sat_band_emit<int32_t><<<ctas, kEmitWarps * 32, smem, st>>>(d_f, M, N, f_stride, g.R, g.nb, g.nc, g.nk, g.nj,
+                                                                    cp, sat_pitch, cs1, cs2, rs1, rs2, ch1, ch2,
+                                                                    static_cast<int32_t*>(d_s), d_s2);
     else
-        sat_band_emit<int64_t><<<g.nb, kEmitWarps * 32, smem, st>>>(d_f, M, N, f_stride, g.R, g.nc, sat_pitch, cs1,
-                                                                   cs2, static_cast<int64_t*>(d_s), d_s2);
+        sat_band_emit<int64_t><<<ctas, kEmitWarps * 32, smem, st>>>(d_f, M, N, f_stride, g.R, g.nb, g.nc, g.nk, g.nj,
+                                                                    cp, sat_pitch, cs1, cs2, rs1, rs2, ch1, ch2,
+                                                                    static_cast<int64_t*>(d_s), d_s2);
     return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }
 

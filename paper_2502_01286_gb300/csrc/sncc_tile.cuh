@@ -1,6 +1,7 @@
 // sncc_tile.cuh - device building blocks shared by the single-problem and
-// the batched segment-sum kernels: register staging of a re-based sum-table
-// region, the corner sum, and the normalisation of Eq. 13 - Eq. 18.
+// the batched segment-sum kernels (and the exact comparator's window sums):
+// register staging of a re-based sum-table region, the corner sum, and the
+// normalisation of Eq. 13 - Eq. 18.
 #pragma once
 
 #include <cstdint>
@@ -16,6 +17,23 @@ __device__ __forceinline__ long long table_entry(const void* s, int pitch, int X
         return static_cast<const long long*>(s)[(size_t)Y * pitch + X];
     else
         return static_cast<const int*>(s)[(size_t)Y * pitch + X];
+}
+
+// Sum of f over the W x H window at (u, v) from four table entries.  A
+// 32-bit table may hold its entries modulo 2^32; the window sum (at most
+// 255 W H < 2^31 for W H <= 2^23) is then exact as a wrapped 32-bit
+// difference.
+template <bool S64>
+__device__ __forceinline__ long long window_sum(const void* s, int pitch, int u, int v, int W, int H) {
+    if constexpr (S64) {
+        const long long* t = static_cast<const long long*>(s);
+        return t[(size_t)(v + H) * pitch + u + W] - t[(size_t)(v + H) * pitch + u] - t[(size_t)v * pitch + u + W] +
+               t[(size_t)v * pitch + u];
+    } else {
+        const uint32_t* t = static_cast<const uint32_t*>(s);
+        return (long long)(int32_t)(t[(size_t)(v + H) * pitch + u + W] - t[(size_t)(v + H) * pitch + u] -
+                                    t[(size_t)v * pitch + u + W] + t[(size_t)v * pitch + u]);
+    }
 }
 
 // Low 32 bits of entry (X, Y) of an int32 or int64 table (little endian).
@@ -271,8 +289,7 @@ template <bool S64>
 __device__ __forceinline__ float normalise(long long acc, const void* s, const int64_t* s2, int pitch, int u, int v,
                                            int W, int H, long long n, double rn, float inv_n, float Ek,
                                            float scale, long long Q0) {
-    const long long sf = table_entry<S64>(s, pitch, u + W, v + H) - table_entry<S64>(s, pitch, u, v + H) -
-                         table_entry<S64>(s, pitch, u + W, v) + table_entry<S64>(s, pitch, u, v);
+    const long long sf = window_sum<S64>(s, pitch, u, v, W, H);
     const long long sf2 = s2[(size_t)(v + H) * pitch + u + W] - s2[(size_t)(v + H) * pitch + u] -
                           s2[(size_t)v * pitch + u + W] + s2[(size_t)v * pitch + u];
     const long long var = n * sf2 - sf * sf;

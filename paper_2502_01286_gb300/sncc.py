@@ -274,7 +274,8 @@ def _ptr(t) -> Optional[int]:
 @dataclass
 class Tables:
     """Padded sum tables of one source: s (int32 or int64) and s2 (int64),
-    each (N+1, pitch) on the device."""
+    each (N+1, pitch) on the device.  An int32 s holds the sums modulo 2^32
+    (exact while 255*M*N < 2^31)."""
     s: "object"
     s2: "object"
     s_bits: int
@@ -284,8 +285,28 @@ class Tables:
 
 
 def choose_bits(M: int, N: int) -> int:
-    """int32 where 255*M*N cannot overflow it, int64 otherwise."""
+    """int32 where 255*M*N cannot overflow it, int64 otherwise: tables whose
+    entries are the sums themselves."""
     return 32 if 255 * M * N < 2 ** 31 else 64
+
+
+DIRECT_MAX_CORNERS = 64  # SNCC_DIRECT_MAX_CORNERS
+
+
+def match_bits(M: int, N: int, segs=()) -> int:
+    """Width of s for matching the approximations `segs` on an M x N source.
+
+    The segment-sum kernels read s only through differences no larger than
+    a template window (255*W*H < 2^31), which a 32-bit table holds exactly
+    even where its entries wrap modulo 2^32: 32 bits (12 bytes per pixel
+    written instead of 16, half the bytes per staged region word).  A
+    template of at most DIRECT_MAX_CORNERS corners is summed from its
+    corners' entries themselves, without staging; where a 32-bit table may
+    wrap it would be staged instead, so such a matcher keeps 64 bits."""
+    if 255 * M * N < 2 ** 31:
+        return 32
+    sparse = any(sg.plan_info()["template_corners"] <= DIRECT_MAX_CORNERS for sg in segs)
+    return 64 if sparse else 32
 
 
 def alloc_tables(M: int, N: int, s_bits: Optional[int] = None, device="cuda") -> Tables:
@@ -553,7 +574,7 @@ class PaperMatcher:
         self.tau_slow = float(precision) * self.slow.rho_max
         self.plan_fast = upload_plan(self.fast, device)
         self.plan_slow = upload_plan(self.slow, device)
-        self.tables = alloc_tables(M, N, None, device)
+        self.tables = alloc_tables(M, N, match_bits(M, N, (self.fast, self.slow)), device)
         self.ws = integral_workspace(M, N, device)
         self.mb = alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device)
         self.rb = alloc_refine(M, N, self.W, self.H, out_cap, device)
@@ -608,7 +629,7 @@ class Matcher:
         self.device = device
         self.t_dev = torch.as_tensor(np.ascontiguousarray(t, np.uint8)).to(device)
         self.plan = upload_plan(self.seg, device)
-        self.tables = alloc_tables(M, N, None, device)
+        self.tables = alloc_tables(M, N, match_bits(M, N, (self.seg,)), device)
         self.ws = integral_workspace(M, N, device)
         self.mb = alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device)
         self.rb = alloc_refine(M, N, self.W, self.H, out_cap, device)
@@ -650,7 +671,7 @@ class MultiMatcher:
         self.tau_e = float(precision) if tau_exact is None else float(tau_exact)
         self.t_dev = torch.as_tensor(np.ascontiguousarray(t, np.uint8)).to(device)
         self.plans = [upload_plan(sg, device) for sg in self.segs]
-        self.tables = alloc_tables(M, N, None, device)
+        self.tables = alloc_tables(M, N, match_bits(M, N, self.segs), device)
         self.ws = integral_workspace(M, N, device)
         self.mbs = [alloc_match(M, N, self.W, self.H, cand_cap, keep_rho, device) for _ in self.segs]
         self.rbs = [alloc_refine(M, N, self.W, self.H, out_cap, device) for _ in self.segs]
@@ -729,7 +750,7 @@ class StreamMatcher:
         rho_pitch = 0
         for k in range(2):
             frame = torch.zeros((N, M), dtype=torch.uint8, device=device)
-            tables = alloc_tables(M, N, None, device)
+            tables = alloc_tables(M, N, match_bits(M, N, self.segs), device)
             ws = integral_workspace(M, N, device)
             mbs = [alloc_match(M, N, W, H, cand_cap, keep_rho, device) for _ in self.segs]
             rbs = [alloc_refine(M, N, W, H, out_cap, device) for _ in self.segs]
@@ -846,7 +867,7 @@ class Batch:
         self.image = torch.empty(max(16, nbytes), dtype=torch.uint8, device=device)
         _check(_lib.sncc_batch_upload(h, self.image.data_ptr(), self.image.numel(), _stream(None)),
                "sncc_batch_upload")
-        self.tables = [alloc_tables(M, N, None, device) for _ in range(n_sources)]
+        self.tables = [alloc_tables(M, N, match_bits(M, N), device) for _ in range(n_sources)]
         self.ws = integral_workspace(M, N, device)
         self.cand_cap, self.out_cap = cand_cap, out_cap
         self.cand = torch.empty(2 * max(cand_cap, 1), dtype=torch.int32, device=device)

@@ -207,8 +207,10 @@ def test_host_argument_errors(sncc):
     assert lib.sncc_integral(None, 10, 10, 10, None, 32, None, 32, None, 0, None) == sncc.ERR_ARG
     assert lib.sncc_integral(C.c_void_p(256), 10, 10, 10, C.c_void_p(256), 16, C.c_void_p(256), 32, None, 0,
                              None) == sncc.ERR_ARG
-    assert lib.sncc_integral(C.c_void_p(256), 4096, 4096, 4096, C.c_void_p(256), 32, C.c_void_p(256), 4128,
-                             C.c_void_p(256), 1 << 30, None) == sncc.ERR_DTYPE
+    # a 32-bit table that wraps (255 M N >= 2^31) is refused only where whole entries are read
+    assert lib.sncc_refine_segmented(seg.ref(), C.c_void_p(256), C.c_void_p(256), 32, C.c_void_p(256), 4128, 4096,
+                                     4096, None, C.c_void_p(256), 0, 0.5, None, 0, C.c_void_p(256), None, 0,
+                                     C.c_void_p(256), None) == sncc.ERR_DTYPE
     assert lib.sncc_integral(C.c_void_p(256), 10, 10, 10, C.c_void_p(256), 32, C.c_void_p(256), 32, None, 0,
                              None) == sncc.ERR_WORKSPACE
     assert lib.sncc_match(seg.ref(), None, None, 32, None, 32, 64, 64, 0.5, None, 0, None, 0, None, None,
@@ -336,3 +338,40 @@ def test_batch_host_work_lists(sncc):
     st1 = (C.c_int * 1)(8)
     t1 = (C.c_float * 1)(0.5)
     assert lib.sncc_batch_create(arr1, pix1, st1, t1, t1, 1, 1, M, N, C.byref(h)) == sncc.ERR_UNIFORM
+
+
+def test_noalloc_scratch_covers_every_source_up_to_1e8_pixels(sncc):
+    """The allocation-free sum tables promise every source of up to 10^8
+    pixels: the workspace sncc_integral asks for stays within the built-in
+    scratch for the tallest source of each width (the band sums grow with N
+    at a fixed width), across the band-geometry regimes (few bands of 64
+    rows, many short bands, a single partial 256-column tile), and a source
+    past the limit asks for more."""
+    lib = sncc.lib()
+    cap = sncc.NOALLOC_SCRATCH_BYTES
+    worst = 0
+    for M in [1, 2, 31, 32, 33, 255, 256, 257, 511, 512, 1000, 1525, 1563, 1920, 4096, 6100, 10000, 15622, 16383]:
+        top = min(65535, 10 ** 8 // M)
+        for N in {top, top - 1, top - 63, top // 2 + 1, max(1, top // 7)}:
+            need = lib.sncc_integral_workspace_bytes(M, N)
+            assert 0 < need <= cap, (M, N, need)
+            worst = max(worst, need)
+    assert worst > cap // 2  # the scan reaches the large end of the range
+    assert lib.sncc_integral_workspace_bytes(16383, 65535) > cap
+
+
+def test_match_table_width_policy(sncc):
+    """The matchers' tables: 32-bit (entries modulo 2^32) unless the source is
+    large enough for a 32-bit table to wrap and a template is sparse enough
+    for the direct corner read, which needs whole entries; the Python limit
+    is the header's."""
+    text = open(os.path.join(ROOT, "include", "sncc.h")).read()
+    assert int(re.search(r"#define SNCC_DIRECT_MAX_CORNERS (\d+)", text).group(1)) == sncc.DIRECT_MAX_CORNERS
+    dense = sncc.build_segments(synth.case_texture(M=300, N=300, W=256, H=256).t, 5.0)
+    sparse = sncc.build_segments(synth.case_plain().t, 10.0)
+    assert dense.plan_info()["template_corners"] > sncc.DIRECT_MAX_CORNERS
+    assert sparse.plan_info()["template_corners"] <= sncc.DIRECT_MAX_CORNERS
+    assert sncc.match_bits(4096, 4096, (dense,)) == 32
+    assert sncc.match_bits(4096, 4096, (dense, sparse)) == 64
+    assert sncc.match_bits(2048, 2048, (sparse,)) == 32  # 255 M N < 2^31: never wraps
+    assert sncc.match_bits(4096, 4096) == 32

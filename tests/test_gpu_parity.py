@@ -103,11 +103,101 @@ def test_integral_int64_full_size(sncc):
     assert int(tb.s[-1, 4096]) == int(s[-1, -1])
 
 
-def test_integral_rejects_int32_overflow(sncc):
-    f = torch.zeros((4096, 4096), dtype=torch.uint8, device="cuda")
-    with pytest.raises(sncc.SnccError) as e:
-        sncc.integral(f, s_bits=32)
-    assert e.value.code == sncc.ERR_DTYPE
+def wrap32(a):
+    """Exact sums as the int32 entries of a 32-bit table: modulo 2^32, two's
+    complement."""
+    return (np.asarray(a).astype(np.int64) & 0xFFFFFFFF).astype(np.uint32).view(np.int32)
+
+
+def test_integral_int32_wraps_modulo_2_32(sncc):
+    """A 32-bit s on a source whose sums pass 2^32 (8192 x 3000, values 200
+    to 255): sampled rows hold the exact sums modulo 2^32, and window sums
+    formed from them in wrapped 32-bit arithmetic equal the exact ones."""
+    M, N = 8192, 3000
+    f = synth.random_image(19, M, N, lo=200)
+    tb = sncc.integral(dev(f), s_bits=32)
+    torch.cuda.synchronize()
+    s, s2 = O.sum_tables(f)
+    assert s[-1, -1] > 2 ** 32  # the entries wrap at least once
+    for rows in (slice(0, 3), slice(1500, 1503), slice(N - 2, N + 1)):
+        np.testing.assert_array_equal(tb.s[rows, :M + 1].cpu().numpy(), wrap32(s[rows]))
+        np.testing.assert_array_equal(tb.s2[rows, :M + 1].cpu().numpy(), s2[rows].astype(np.int64))
+    t32 = tb.s[:, :M + 1].cpu().numpy()
+    g = np.random.default_rng(4)
+    for _ in range(200):
+        W, H = int(g.integers(1, 2897)), int(g.integers(1, 2897))  # 255 W H < 2^31
+        u, v = int(g.integers(0, M - W + 1)), int(g.integers(0, N - H + 1))
+        d = (int(t32[v + H, u + W]) - int(t32[v + H, u]) - int(t32[v, u + W]) + int(t32[v, u])) & 0xFFFFFFFF
+        got = d - (1 << 32) if d >= 1 << 31 else d
+        want = int(s[v + H, u + W] - s[v + H, u] - s[v, u + W] + s[v, u])  # exact in float64 (< 2^53)
+        assert got == want, (u, v, W, H)
+
+
+def test_wrapped_tables_equal_int64_texture(sncc):
+    """The texture workload (4096 x 4096 source, the 256 x 256 template at
+    sigma 5, precision 0.5) on the 32-bit tables the
+    matchers use and on 64-bit tables: the staged region words, window sums
+    and integer numerators are the same, so the rho maps, candidate sets,
+    refined matches and the exact comparator's map are identical."""
+    c = synth.case_texture()
+    N, M = c.f.shape
+    H, W = c.t.shape
+    U, V = M - W + 1, N - H + 1
+    seg = sncc.build_segments(c.t, 5.0)
+    plan = sncc.upload_plan(seg)
+    fd, td = dev(c.f), dev(c.t)
+    out = {}
+    for bits in (32, 64):
+        tb = sncc.integral(fd, s_bits=bits)
+        mb = sncc.alloc_match(M, N, W, H, U * V // 8)
+        sncc.match(seg, plan, tb, 0.5 * seg.rho_max, mb)
+        rb = sncc.alloc_refine(M, N, W, H, 1 << 20)
+        sncc.refine(fd, td, seg, mb, 0.5, rb)
+        ex = sncc.exact_map(fd, td, seg.T, seg.T2, tb)
+        torch.cuda.synchronize()
+        assert int(mb.status.item()) == 0
+        cnt = int(mb.count.item())
+        out[bits] = (mb.rho.clone(), np.sort(mb.cand[:cnt].cpu().numpy()), sncc.matches_to_numpy(rb), ex.clone())
+    assert 255 * M * N >= 2 ** 31  # a size whose 32-bit table may wrap (the sparse-template test wraps one)
+    a, b = out[32], out[64]
+    assert torch.equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    assert a[1].size > 1000
+    for x, y in zip(a[2], b[2]):
+        np.testing.assert_array_equal(x, y)
+    assert torch.equal(a[3], b[3])
+
+
+def test_wrapped_tables_sparse_template(sncc):
+    """A template of at most 64 corners reads its corners' table entries
+    directly; on a wrapping 32-bit table it takes the staged path instead.
+    Its rho map equals the direct read of 64-bit tables exactly (the same
+    integer numerator either way), on a bright 4096 x 3000 source (values 150
+    to 255, sums past 2^31) holding the template, three boxes on a flat
+    background, at one offset."""
+    f = synth.random_image(23, 4096, 3000, lo=150)
+    t = np.full((48, 48), 160, np.uint8)
+    t[5:20, 8:30] = 230
+    t[25:45, 3:15] = 185
+    t[30:40, 28:44] = 205
+    u0, v0 = 1234, 2001
+    f[v0:v0 + 48, u0:u0 + 48] = t
+    seg = sncc.build_segments(t, 10.0)
+    assert seg.plan_info()["template_corners"] <= 64
+    N, M = f.shape
+    plan = sncc.upload_plan(seg)
+    fd = dev(f)
+    maps = {}
+    for bits in (32, 64):
+        tb = sncc.integral(fd, s_bits=bits)
+        mb = sncc.alloc_match(M, N, 48, 48, 1 << 16)
+        sncc.match(seg, plan, tb, 0.9 * seg.rho_max, mb)
+        torch.cuda.synchronize()
+        assert int(mb.status.item()) == 0
+        maps[bits] = mb.rho.clone()
+    assert int(f.astype(np.int64).sum()) >= 2 ** 31
+    assert torch.equal(maps[32], maps[64])
+    assert abs(float(maps[32][v0, u0]) - seg.rho_max) <= TOL
 
 
 # ------------------------------------------------------------------ coarse pass
