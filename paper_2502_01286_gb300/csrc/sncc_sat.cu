@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 #include <cstdint>
 #include <mutex>
 
@@ -193,9 +194,12 @@ __global__ void __launch_bounds__(256) sat_band_colsum(const uint8_t* __restrict
     const int b = blockIdx.y;
     const int y0 = b * R, y1 = min(y0 + R, N);
     const bool vec = ((stride & 7) == 0) && ((reinterpret_cast<uintptr_t>(f) & 7) == 0);
-    int a[kLaneCols], q[kLaneCols];
+    // column sums of f two to a word, in 16-bit halves (a band's sum is at
+    // most 255 x 64 < 2^16): columns (0, 2), (1, 3), (4, 6), (5, 7)
+    uint32_t a02 = 0, a13 = 0, a46 = 0, a57 = 0;
+    int q[kLaneCols];
 #pragma unroll
-    for (int e = 0; e < kLaneCols; ++e) a[e] = q[e] = 0;
+    for (int e = 0; e < kLaneCols; ++e) q[e] = 0;
     auto load_rows = [&](uint2 (&w)[kColRows], int y) {
 #pragma unroll
         for (int i = 0; i < kColRows; ++i)
@@ -208,15 +212,19 @@ __global__ void __launch_bounds__(256) sat_band_colsum(const uint8_t* __restrict
         int s1[kColRows], s2[kColRows];
 #pragma unroll
         for (int i = 0; i < kColRows; ++i) {
-            s1[i] = s2[i] = 0;
+            const uint32_t lo = cur[i].x, hi = cur[i].y;
+            a02 += lo & 0x00ff00ffu;
+            a13 += (lo >> 8) & 0x00ff00ffu;
+            a46 += hi & 0x00ff00ffu;
+            a57 += (hi >> 8) & 0x00ff00ffu;
 #pragma unroll
             for (int e = 0; e < kLaneCols; ++e) {
                 const int p = byte_of(cur[i], e);
-                a[e] += p;
                 q[e] += p * p;
-                s1[i] += p;
-                s2[i] += p * p;
             }
+            // the row's sums over the lane's eight bytes: four byte products each
+            s1[i] = (int)__dp4a(hi, 0x01010101u, __dp4a(lo, 0x01010101u, 0u));
+            s2[i] = (int)__dp4a(hi, hi, __dp4a(lo, lo, 0u));
         }
 #pragma unroll
         for (int i = 0; i < kColRows; ++i) {
@@ -236,6 +244,8 @@ __global__ void __launch_bounds__(256) sat_band_colsum(const uint8_t* __restrict
     }
     // columns x0 .. x0+7 as two 16-byte stores each (cp and x0 are multiples
     // of 4; columns from M to cp hold zeros)
+    const int a[kLaneCols] = {(int)(a02 & 0xffffu), (int)(a13 & 0xffffu), (int)(a02 >> 16), (int)(a13 >> 16),
+                              (int)(a46 & 0xffffu), (int)(a57 & 0xffffu), (int)(a46 >> 16), (int)(a57 >> 16)};
 #pragma unroll
     for (int h = 0; h < 2; ++h)
         if (x0 + 4 * h < cp) {
@@ -458,18 +468,18 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 3) sat_band_emit(const uint8_
     // so far (fits 32 bits: at most 65025 N < 2^31); the 64-bit base is the
     // corner plus the carries of the lanes before this one
     int32_t col1[kLaneCols], col2[kLaneCols];
-    uint32_t tc1 = 0, tc2 = 0;  // the lane's carry totals
+    int64_t tc1 = 0, tc2 = 0;  // the lane's carry totals (8 x 255^2 N may pass 2^32)
 #pragma unroll
     for (int e = 0; e < kLaneCols; ++e) {
         const int x = Xl - 1 + e;
         const bool in = (x >= 0 && x < M);
         col1[e] = in ? cab1[x] : 0;
         col2[e] = in ? cab2[x] : 0;
-        tc1 += (uint32_t)col1[e];
-        tc2 += (uint32_t)col2[e];
+        tc1 += col1[e];
+        tc2 += col2[e];
     }
-    const int64_t base1 = p1 + warp_exclusive_scan((int64_t)tc1, lane);
-    const int64_t base2 = p2 + warp_exclusive_scan((int64_t)tc2, lane);
+    const int64_t base1 = p1 + warp_exclusive_scan(tc1, lane);
+    const int64_t base2 = p2 + warp_exclusive_scan(tc2, lane);
     __syncwarp();
 
     if (b == 0) {  // row Y = 0 of the table is zero
@@ -479,33 +489,36 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 3) sat_band_emit(const uint8_
         }
     }
 
-    // ---- the band's rows, two per iteration so that their scans overlap ----
+    // ---- the band's rows ----
     const bool full_tile = (X0 + kTileCols - 1 <= M);  // warp-uniform
     unsigned char* mine = stage + lane * kLaneStride;
-    // one row's outputs: 64-bit running sums from the base plus the row part
-    // before the lane, one column at a time
+    // one row's outputs: running sums from the base plus the row part before
+    // the lane, one column at a time (64-bit, or for a 32-bit s its low 32
+    // bits, which is all the table keeps)
+    using RunT = typename std::conditional<sizeof(ST) == 8, int64_t, uint32_t>::type;
     auto emit_row = [&](int r, int32_t pre1, int64_t pre2) {
         ST* srow = s + (size_t)(y0 + r + 1) * pitch;
         int64_t* s2row = s2 + (size_t)(y0 + r + 1) * pitch;
-        int64_t run1 = base1 + pre1, run2 = base2 + pre2;
+        RunT run1 = (RunT)(base1 + pre1);
+        int64_t run2 = base2 + pre2;
         if (full_tile) {
             // through the warp's staging buffer, so that every global store
             // instruction writes 512 contiguous bytes
             if constexpr (sizeof(ST) == 8) {
 #pragma unroll
                 for (int e = 0; e < kLaneCols; e += 2) {
-                    const int64_t o0 = (run1 += col1[e]);
-                    const int64_t o1 = (run1 += col1[e + 1]);
+                    const int64_t o0 = (run1 += (RunT)col1[e]);
+                    const int64_t o1 = (run1 += (RunT)col1[e + 1]);
                     *reinterpret_cast<longlong2*>(mine + 8 * e) = make_longlong2(o0, o1);
                 }
             } else {
 #pragma unroll
                 for (int e = 0; e < kLaneCols; e += 4) {
                     int4 o;
-                    o.x = (int)(run1 += col1[e]);
-                    o.y = (int)(run1 += col1[e + 1]);
-                    o.z = (int)(run1 += col1[e + 2]);
-                    o.w = (int)(run1 += col1[e + 3]);
+                    o.x = (int)(run1 += (RunT)col1[e]);
+                    o.y = (int)(run1 += (RunT)col1[e + 1]);
+                    o.z = (int)(run1 += (RunT)col1[e + 2]);
+                    o.w = (int)(run1 += (RunT)col1[e + 3]);
                     *reinterpret_cast<int4*>(mine + 4 * e) = o;
                 }
             }
@@ -520,7 +533,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 3) sat_band_emit(const uint8_
         } else {
 #pragma unroll
             for (int e = 0; e < kLaneCols; ++e) {
-                run1 += col1[e];
+                run1 += (RunT)col1[e];
                 run2 += col2[e];
                 if (Xl + e <= M) {
                     srow[Xl + e] = (ST)run1;
@@ -533,22 +546,23 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 3) sat_band_emit(const uint8_
 #pragma unroll
     for (int i = 0; i < kAhead; ++i)
         if (i < nr) q[i] = load_lane_row(fband + (size_t)i * stride, M, X0, lane, vec);
+    // the band's rows so far summed over the lane's columns, for the scans
+    // (at most 8 x 64 x 255^2 < 2^31)
+    uint32_t d1 = 0, d2 = 0;
     for (int r = 0; r < nr; ++r) {
         const uint2 va = unpack_lane_row(q[0], lane);
 #pragma unroll
         for (int i = 0; i < kAhead - 1; ++i) q[i] = q[i + 1];
         if (r + kAhead < nr) q[kAhead - 1] = load_lane_row(fband + (size_t)(r + kAhead) * stride, M, X0, lane, vec);
-        uint32_t a1 = 0, a2 = 0;
 #pragma unroll
         for (int e = 0; e < kLaneCols; ++e) {
             const int pa = byte_of(va, e);
             col1[e] += pa;
             col2[e] += pa * pa;
-            a1 += (uint32_t)col1[e];
-            a2 += (uint32_t)col2[e];
         }
-        emit_row(r, L1[r] + (int32_t)warp_exclusive_scan(a1 - tc1, lane),
-                 L2[r] + (int64_t)warp_exclusive_scan(a2 - tc2, lane));
+        d1 = __dp4a(va.y, 0x01010101u, __dp4a(va.x, 0x01010101u, d1));
+        d2 = __dp4a(va.y, va.y, __dp4a(va.x, va.x, d2));
+        emit_row(r, L1[r] + (int32_t)warp_exclusive_scan(d1, lane), L2[r] + (int64_t)warp_exclusive_scan(d2, lane));
     }
 }
 

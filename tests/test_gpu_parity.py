@@ -66,10 +66,14 @@ def check_candidates(rho64, cand, count, tau, rows=None, what=""):
 
 
 # ------------------------------------------------------------------ sum tables
-@pytest.mark.parametrize("M,N", [(1, 1), (5, 3), (33, 17), (257, 129), (256, 256), (1920, 1080), (4095, 7)])
+@pytest.mark.parametrize("M,N", [(1, 1), (5, 3), (33, 17), (257, 129), (256, 256), (1920, 1080), (4095, 7),
+                                 (300, 20000)])
 @pytest.mark.parametrize("bits", [32, 64])
 def test_integral_bit_exact(sncc, M, N, bits):
-    f = synth.random_image(1000 + M + N, M, N)
+    """Every entry against the oracle's tables.  The 300 x 20000 source is
+    bright (values 200 to 255): a lane's eight carries of f^2 then sum past
+    2^32 in the lower bands."""
+    f = synth.random_image(1000 + M + N, M, N, lo=200 if N > 8192 else 0)
     tb = sncc.integral(dev(f), s_bits=bits)
     torch.cuda.synchronize()
     s, s2 = O.sum_tables(f)
