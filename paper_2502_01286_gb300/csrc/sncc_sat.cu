@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(kScanWarps * 32) sat_band_scan(int M, int nb, 
                                                                  int64_t* __restrict__ ch1,
                                                                  int64_t* __restrict__ ch2) {
     __shared__ int32_t tot1[kScanWarps][32], tot2[kScanWarps][32];
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the column sums are complete
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = blockIdx.x * 32 + lane;
     const bool in = x < M;
@@ -408,6 +409,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 3) sat_band_emit(const uint8_
                                                                  const int64_t* __restrict__ ch2, ST* __restrict__ s,
                                                                  int64_t* __restrict__ s2) {
     extern __shared__ __align__(16) unsigned char emit_smem[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the carries are complete
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pair = blockIdx.x * kEmitWarps + warp;
     if (pair >= nb * nc) return;  // whole warp
@@ -638,20 +640,35 @@ extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, voi
     const dim3 g1((M + 256 * kLaneCols - 1) / (256 * kLaneCols), g.nb);
     const int cp = col_pitch(M);
     sat_band_colsum<<<g1, 256, 0, st>>>(d_f, M, N, f_stride, g.R, g.nk, cp, cs1, cs2, rs1, rs2);
-    sat_band_scan<<<(M + kCarryChunk - 1) / kCarryChunk, kScanWarps * 32, 0, st>>>(M, g.nb, g.nj, cp, cs1, cs2,
-                                                                                   ch1, ch2);
+    // the scan and the emit launch while their predecessor drains and wait
+    // for it in the kernel (programmatic dependent launch)
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t c2 = {};
+    c2.gridDim = dim3((M + kCarryChunk - 1) / kCarryChunk);
+    c2.blockDim = dim3(kScanWarps * 32);
+    c2.stream = st;
+    c2.attrs = pdl;
+    c2.numAttrs = 1;
+    if (cudaLaunchKernelEx(&c2, sat_band_scan, M, g.nb, g.nj, cp, cs1, cs2, ch1, ch2) != cudaSuccess)
+        return SNCC_ERR_CUDA;
     if (set_emit_attributes() != cudaSuccess) return SNCC_ERR_CUDA;
-    const int ctas = (g.nb * g.nc + kEmitWarps - 1) / kEmitWarps;
-    const size_t smem = (size_t)kEmitWarps * kWarpSmem;
-    if (s_bits == 32)
-        sat_band_emit<int32_t><<<ctas, kEmitWarps * 32, smem, st>>>(d_f, M, N, f_stride, g.R, g.nb, g.nc, g.nk, g.nj,
-                                                                    cp, sat_pitch, cs1, cs2, rs1, rs2, ch1, ch2,
-                                                                    static_cast<int32_t*>(d_s), d_s2);
-    else
-        sat_band_emit<int64_t><<<ctas, kEmitWarps * 32, smem, st>>>(d_f, M, N, f_stride, g.R, g.nb, g.nc, g.nk, g.nj,
-                                                                    cp, sat_pitch, cs1, cs2, rs1, rs2, ch1, ch2,
-                                                                    static_cast<int64_t*>(d_s), d_s2);
-    return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+    cudaLaunchConfig_t c3 = c2;
+    c3.gridDim = dim3((g.nb * g.nc + kEmitWarps - 1) / kEmitWarps);
+    c3.blockDim = dim3(kEmitWarps * 32);
+    c3.dynamicSmemBytes = (size_t)kEmitWarps * kWarpSmem;
+    const cudaError_t e3 =
+        s_bits == 32
+            ? cudaLaunchKernelEx(&c3, sat_band_emit<int32_t>, d_f, M, N, f_stride, g.R, g.nb, g.nc, g.nk, g.nj, cp,
+                                 sat_pitch, (const int32_t*)cs1, (const int32_t*)cs2, (const int32_t*)rs1,
+                                 (const int32_t*)rs2, (const int64_t*)ch1, (const int64_t*)ch2,
+                                 static_cast<int32_t*>(d_s), d_s2)
+            : cudaLaunchKernelEx(&c3, sat_band_emit<int64_t>, d_f, M, N, f_stride, g.R, g.nb, g.nc, g.nk, g.nj, cp,
+                                 sat_pitch, (const int32_t*)cs1, (const int32_t*)cs2, (const int32_t*)rs1,
+                                 (const int32_t*)rs2, (const int64_t*)ch1, (const int64_t*)ch2,
+                                 static_cast<int64_t*>(d_s), d_s2);
+    return e3 == cudaSuccess && cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------
