@@ -163,6 +163,12 @@ def random_image(seed: int, M: int, N: int, lo: int = 0, hi: int = 256) -> np.nd
     return rng(seed).integers(lo, hi, size=(N, M), dtype=np.int64).astype(np.uint8)
 
 
+def random_image_u8(seed: int, M: int, N: int, lo: int = 0, hi: int = 256) -> np.ndarray:
+    """Uniform random uint8 image (N, M) drawn as bytes directly, for sources
+    of hundreds of megapixels."""
+    return rng(seed).integers(lo, hi, size=(N, M), dtype=np.uint8)
+
+
 def case_diff(M: int = 512, N: int = 512, W: int = 48, H: int = 48, seed: int = BASE_SEED + 5,
               noise: float = 2.0, sigma_max: float = 12.0):
     """Float source for the differentiation workload: 20 blobs plus 1/f noise

@@ -137,6 +137,83 @@ def test_integral_int32_wraps_modulo_2_32(sncc):
         assert got == want, (u, v, W, H)
 
 
+@pytest.fixture(scope="module")
+def max_source():
+    """The largest source sncc_integral takes, 16383 x 33025 (M <= 16383, and
+    N 65025 < 2^31 for the int32 column sums of f^2), bright (values 200 to
+    255), and its exact table rows Y = 0, 1, 2, 16512, N - 1, N by the
+    definition: the column sums of the rows above Y, prefix-summed along the
+    row (in chunks of rows, so no full-size int64 copy is made)."""
+    M, N = 16383, 33025
+    f = synth.random_image_u8(41, M, N, lo=200)
+    rows = [0, 1, 2, 16512, N - 1, N]
+    want, want2 = {}, {}
+    acc = np.zeros(M, np.int64)
+    acc2 = np.zeros(M, np.int64)
+    prev = 0
+    for Y in rows:
+        for y in range(prev, Y, 1024):
+            blk = f[y:min(Y, y + 1024)].astype(np.int64)
+            acc += blk.sum(0)
+            acc2 += (blk * blk).sum(0)
+        prev = Y
+        want[Y] = np.concatenate([[0], np.cumsum(acc)])
+        want2[Y] = np.concatenate([[0], np.cumsum(acc2)])
+    return f, rows, want, want2
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+def test_integral_maximum_source(sncc, max_source, bits):
+    """Sampled rows of the tables of the largest source: s2 exact, s exact
+    (64-bit) or modulo 2^32 (32-bit, wrapping about ten times)."""
+    f, rows, want, want2 = max_source
+    N, M = f.shape
+    tb = sncc.integral(dev(f), s_bits=bits)
+    torch.cuda.synchronize()
+    assert want[N][-1] > 8 * 2 ** 32
+    for Y in rows:
+        got = tb.s[Y, :M + 1].cpu().numpy()
+        np.testing.assert_array_equal(got, want[Y] if bits == 64 else wrap32(want[Y]))
+        np.testing.assert_array_equal(tb.s2[Y, :M + 1].cpu().numpy(), want2[Y])
+    del tb
+    torch.cuda.empty_cache()
+
+
+def test_match_maximum_template_area(sncc):
+    """The largest template area (W H = 2^23: 2048 x 4096), where a window sum
+    of f can reach 255 W H, just under 2^31, on a 2100 x 4600 source of
+    values 200 to 255 whose 32-bit table wraps (sum of f past 2^31).  The
+    approximation (sigma 1: 4637 segments, 2048 blocks of 64 x 64) equals the
+    oracle's; the rho maps on 32- and 64-bit tables are identical and within
+    1e-5 of the oracle on sampled rows; the crop offset gives rho_max."""
+    c = synth.case_plain(M=2100, N=4600, W=2048, H=4096, noise=0.0)
+    f = (200 + (c.f.astype(np.int64) - 39) * 55 // 189).clip(0, 255).astype(np.uint8)
+    u0, v0 = c.origin
+    t = np.ascontiguousarray(f[v0:v0 + 4096, u0:u0 + 2048])
+    N, M = f.shape
+    U, V = M - 2048 + 1, N - 4096 + 1
+    assert int(f.astype(np.int64).sum()) >= 2 ** 31
+    ap = O.precompute_template_approximation(t, 1.0)
+    seg = sncc.build_segments(t, 1.0)
+    assert seg.K == ap.K
+    plan = sncc.upload_plan(seg)
+    fd = dev(f)
+    maps = {}
+    for bits in (32, 64):
+        tb = sncc.integral(fd, s_bits=bits)
+        mb = sncc.alloc_match(M, N, 2048, 4096, U * V)
+        sncc.match(seg, plan, tb, 0.9 * seg.rho_max, mb)
+        torch.cuda.synchronize()
+        assert int(mb.status.item()) == 0
+        maps[bits] = mb.rho.clone()
+    assert torch.equal(maps[32], maps[64])
+    rows = np.unique(np.r_[0, 1, v0, V - 1, np.random.default_rng(7).choice(V, 12, replace=False)])
+    ref = O.segmented_ncc_map(f, ap, "sat", rows=rows)
+    got = maps[32].cpu().numpy()
+    assert np.abs(got[rows] - ref[rows]).max() <= TOL
+    assert abs(got[v0, u0] - ap.rho_max) <= TOL
+
+
 def test_wrapped_tables_equal_int64_texture(sncc):
     """The texture workload (4096 x 4096 source, the 256 x 256 template at
     sigma 5, precision 0.5) on the 32-bit tables the
