@@ -620,7 +620,8 @@ size_t sncc_diff_workspace_bytes(int M, int N, int W, int H);
  *
  * L = sum over offsets (u, v) of (rho_k(u, v) - rho_t(u, v))^2.
  *   d_f, M, N, f_stride  float32 source (row stride in elements)
- *   d_t, W, H            float32 template, contiguous (W, H <= 64)
+ *   d_t, W, H            float32 template, contiguous (W, H <= 256; the
+ *                        kernels take it in blocks of at most 64 x 64)
  *   d_rects, d_k, K      segmentation: K records {x, y, w, h} (int32) tiling
  *                        the template, and the segment values (float32)
  *   d_rho_k, d_rho_t     outputs, (N-H+1) x (M-W+1) float32 each

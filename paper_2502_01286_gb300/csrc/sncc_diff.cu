@@ -9,9 +9,10 @@
 //   dL/dk_j  = sum_{x in S_j} Gt(x) - n_j sum_o a fbar - n_j c_j sum_o g rho_k / E_k,
 //              Gt(x) = sum_o a(o) f(o + x);
 //   dL/df(p) = sum_{o : p in window(o)} a(o) c(p-o) - b(o) t0(p-o) + h(o) (fbar(o) - f(p)).
-// Templates up to 64 x 64 (every window and the template fit in shared
-// memory).  Sums run in FP32 along a template row (the forward pass: down a
-// template column) and in FP64 across rows (columns).
+// Templates up to 256 x 256, taken in blocks of at most 64 x 64 (a block's
+// window region and the block of the template fit in shared memory).  Sums
+// run in FP32 along a template row (the forward pass: down a template column)
+// and in compensated FP32 across rows (columns) and blocks.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -23,7 +24,8 @@
 namespace sncc {
 namespace {
 
-constexpr int kDiffMax = 64;      // largest template edge
+constexpr int kDiffMax = 256;     // largest template edge
+constexpr int kDiffBlk = 64;      // template block edge the forward and dL/df kernels stage at a time
 constexpr int kFwXB = 4;          // forward: offset rows per thread (register window)
 constexpr int kFwG = 4;           // forward: template-column groups per CTA
 constexpr int kFwGT = 256 / kFwG;  // forward: threads per group (2 warps)
@@ -137,26 +139,32 @@ __global__ void __launch_bounds__(256) diff_prep_kernel(const float* __restrict_
 }
 
 // Forward pass over a 32 x 8 tile of offsets.  The CTA's 256 threads are
-// kFwG groups of 2 warps; group g takes the template columns
-// [g W / kFwG, (g+1) W / kFwG), and thread (warp w of the group, lane l) the
-// offsets u0 + l, rows v0 + 4w .. +3.  Along a template column the thread
-// keeps the 4 source values of its 4 offsets in a register window, so each
-// template row costs one new source load and two broadcast loads (c, t0) for
-// 4 x 4 floating-point operations.  Sums run in FP32 down a template column
-// and in compensated FP32 across columns (a plain FP64 add per column and
-// offset made the kernel FP64-bound); the groups' partial sums meet in shared
-// memory, in FP64 and a fixed order.
-//   pass 1: window means (sliding column sums);
+// kFwG groups of 2 warps; within each template block group g takes the
+// block's columns [g Wb / kFwG, (g+1) Wb / kFwG), and thread (warp w of the
+// group, lane l) the offsets u0 + l, rows v0 + 4w .. +3.  Along a template
+// column the thread keeps the 4 source values of its 4 offsets in a register
+// window, so each template row costs one new source load and two broadcast
+// loads (c, t0) for 4 x 4 floating-point operations.  Sums run in FP32 down a
+// template column and in compensated FP32 across columns and blocks (a plain
+// FP64 add per column and offset made the kernel FP64-bound); the groups'
+// partial sums meet in shared memory, in FP64 and a fixed order.
+//   pass 1: window means (sliding column sums), over every block;
 //   pass 2: with d = f - fbar: sum d^2, sum c d, sum t0 d (E_f, numerator,
-//           exact numerator).
+//           exact numerator), over every block again (a template of one
+//           block is staged once for both passes).
 __host__ __device__ constexpr int fw_region_w(int W) { return kFwTX + W - 1; }
+__host__ __device__ constexpr int blk_edge(int E) { return E < kDiffBlk ? E : kDiffBlk; }
 __host__ __device__ constexpr size_t fw_main_bytes(int W, int H) {
-    // max(staged source, c, t0 | pass-2 partials of groups 1..), rounded to 16 bytes
-    return (((size_t)fw_region_w(W) * (kFwTY + H - 1) + 2 * (size_t)W * H) * 4 >
+    // max(staged source, c, t0 of the largest block | pass-2 partials of groups 1..), rounded to 16 bytes
+    return (((size_t)fw_region_w(blk_edge(W)) * (kFwTY + blk_edge(H) - 1) + 2 * (size_t)blk_edge(W) * blk_edge(H)) *
+                        4 >
                     (size_t)(kFwG - 1) * kFwGT * kFwXB * 3 * 8
-                ? ((size_t)fw_region_w(W) * (kFwTY + H - 1) + 2 * (size_t)W * H) * 4
+                ? ((size_t)fw_region_w(blk_edge(W)) * (kFwTY + blk_edge(H) - 1) +
+                   2 * (size_t)blk_edge(W) * blk_edge(H)) *
+                      4
                 : (size_t)(kFwG - 1) * kFwGT * kFwXB * 3 * 8) +
-           15 & ~(size_t)15;
+               15 &
+           ~(size_t)15;
 }
 __host__ __device__ constexpr size_t fw_smem_bytes(int W, int H) {
     return fw_main_bytes(W, H) + (size_t)kFwG * kFwGT * kFwXB * 8;  // + pass-1 partials
@@ -169,44 +177,59 @@ __global__ void __launch_bounds__(256) diff_forward_kernel(const float* __restri
                                                            float* __restrict__ ef_out, float* __restrict__ fbar_out,
                                                            double* loss) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int RW = fw_region_w(W), RH = kFwTY + H - 1;
+    const int Wb = blk_edge(W), Hb = blk_edge(H);  // the largest block
+    const int RW = fw_region_w(Wb);                // region pitch
     const size_t main_bytes = fw_main_bytes(W, H);
-    float* fs = reinterpret_cast<float*>(smraw);        // RH x RW source region
-    float* cs = fs + RW * RH;                           // W x H
-    float* ts = cs + W * H;                             // W x H
+    float* fs = reinterpret_cast<float*>(smraw);        // source region of a block, pitch RW
+    float* cs = fs + RW * (kFwTY + Hb - 1);             // c of a block, pitch bw
+    float* ts = cs + Wb * Hb;                           // t0 of a block, pitch bw
     double* red2 = reinterpret_cast<double*>(smraw);    // after pass 2: [g-1][t][j][3]
     double* red1 = reinterpret_cast<double*>(smraw + main_bytes);  // [g][t][j]
     __shared__ double red[8];
     const int U = M - W + 1, V = N - H + 1;
     const int u0 = blockIdx.x * kFwTX, v0 = blockIdx.y * kFwTY;
-    for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
-        const int Y = i / RW, X = i - Y * RW;
-        const int gx = u0 + X, gy = v0 + Y;
-        fs[i] = (gx < M && gy < N) ? f[(size_t)gy * stride + gx] : 0.0f;
-    }
-    for (int i = threadIdx.x; i < W * H; i += blockDim.x) {
-        cs[i] = c[i];
-        ts[i] = t0[i];
-    }
-    __syncthreads();
+    const bool one_block = (W <= kDiffBlk && H <= kDiffBlk);
+    // the source region of block (bx, by) of size bw x bh, and its c and t0
+    auto stage = [&](int bx, int by, int bw, int bh, bool tmpl) {
+        const int rw = fw_region_w(bw), rh = kFwTY + bh - 1;
+        for (int i = threadIdx.x; i < rw * rh; i += blockDim.x) {
+            const int Y = i / rw, X = i - Y * rw;
+            const int gx = u0 + bx + X, gy = v0 + by + Y;
+            fs[Y * RW + X] = (gx < M && gy < N) ? f[(size_t)gy * stride + gx] : 0.0f;
+        }
+        if (tmpl)
+            for (int i = threadIdx.x; i < bw * bh; i += blockDim.x) {
+                const int y = i / bw, x = i - y * bw;
+                cs[i] = c[(by + y) * W + bx + x];
+                ts[i] = t0[(by + y) * W + bx + x];
+            }
+    };
     const int g = threadIdx.x / kFwGT, t = threadIdx.x - g * kFwGT;
     const int lane = t & 31, wy = t >> 5;
-    const int x_lo = g * W / kFwG, x_hi = (g + 1) * W / kFwG;
     const float* base = fs + (wy * kFwXB) * RW + lane;  // region row of offset row 0, column of the lane
     const double n = (double)W * H;
 
     // ---- pass 1: window sums, sum over rows y of f(row y + j) per template column ----
     KahanF sp[kFwXB];
-    for (int x = x_lo; x < x_hi; ++x) {
-        const float* col = base + x;
-        float s0 = 0.0f;
-        for (int y = 0; y < H; ++y) s0 += col[y * RW];
-        float sj = s0;
-        sp[0].add(s0);
+    for (int by = 0; by < H; by += kDiffBlk) {
+        for (int bx = 0; bx < W; bx += kDiffBlk) {
+            const int bw = min(kDiffBlk, W - bx), bh = min(kDiffBlk, H - by);
+            __syncthreads();  // the previous block's reads are done
+            stage(bx, by, bw, bh, one_block);
+            __syncthreads();
+            const int x_lo = g * bw / kFwG, x_hi = (g + 1) * bw / kFwG;
+            for (int x = x_lo; x < x_hi; ++x) {
+                const float* col = base + x;
+                float s0 = 0.0f;
+                for (int y = 0; y < bh; ++y) s0 += col[y * RW];
+                float sj = s0;
+                sp[0].add(s0);
 #pragma unroll
-        for (int j = 1; j < kFwXB; ++j) {  // slide the window one row
-            sj += col[(H - 1 + j) * RW] - col[(j - 1) * RW];
-            sp[j].add(sj);
+                for (int j = 1; j < kFwXB; ++j) {  // slide the window one row
+                    sj += col[(bh - 1 + j) * RW] - col[(j - 1) * RW];
+                    sp[j].add(sj);
+                }
+            }
         }
     }
 #pragma unroll
@@ -222,36 +245,47 @@ __global__ void __launch_bounds__(256) diff_forward_kernel(const float* __restri
 
     // ---- pass 2: energy, approximate and exact numerators ----
     KahanF ek[kFwXB], nkk[kFwXB], ntk[kFwXB];
-    for (int x = x_lo; x < x_hi; ++x) {
-        const float* col = base + x;
-        float re[kFwXB], rk[kFwXB], rt[kFwXB], win[kFwXB];
+    for (int by = 0; by < H; by += kDiffBlk) {
+        for (int bx = 0; bx < W; bx += kDiffBlk) {
+            const int bw = min(kDiffBlk, W - bx), bh = min(kDiffBlk, H - by);
+            if (!one_block) {
+                __syncthreads();
+                stage(bx, by, bw, bh, true);
+                __syncthreads();
+            }
+            const int x_lo = g * bw / kFwG, x_hi = (g + 1) * bw / kFwG;
+            for (int x = x_lo; x < x_hi; ++x) {
+                const float* col = base + x;
+                float re[kFwXB], rk[kFwXB], rt[kFwXB], win[kFwXB];
 #pragma unroll
-        for (int j = 0; j < kFwXB; ++j) {
-            re[j] = rk[j] = rt[j] = 0.0f;
-            win[j] = j < kFwXB - 1 ? col[j * RW] : 0.0f;  // rows 0 .. 2 in slots 0 .. 2
-        }
-        for (int y0 = 0; y0 < H; y0 += kFwXB) {
+                for (int j = 0; j < kFwXB; ++j) {
+                    re[j] = rk[j] = rt[j] = 0.0f;
+                    win[j] = j < kFwXB - 1 ? col[j * RW] : 0.0f;  // rows 0 .. 2 in slots 0 .. 2
+                }
+                for (int y0 = 0; y0 < bh; y0 += kFwXB) {
 #pragma unroll
-            for (int k = 0; k < kFwXB; ++k) {
-                const int y = y0 + k;
-                if (y < H) {
-                    win[(k + kFwXB - 1) % kFwXB] = col[(y + kFwXB - 1) * RW];  // row y + 3
-                    const float cx = cs[y * W + x], tx = ts[y * W + x];
+                    for (int k = 0; k < kFwXB; ++k) {
+                        const int y = y0 + k;
+                        if (y < bh) {
+                            win[(k + kFwXB - 1) % kFwXB] = col[(y + kFwXB - 1) * RW];  // row y + 3
+                            const float cx = cs[y * bw + x], tx = ts[y * bw + x];
 #pragma unroll
-                    for (int j = 0; j < kFwXB; ++j) {
-                        const float d = win[(k + j) % kFwXB] - fb[j];  // f(row y + j)
-                        re[j] += d * d;
-                        rk[j] += cx * d;
-                        rt[j] += tx * d;
+                            for (int j = 0; j < kFwXB; ++j) {
+                                const float d = win[(k + j) % kFwXB] - fb[j];  // f(row y + j)
+                                re[j] += d * d;
+                                rk[j] += cx * d;
+                                rt[j] += tx * d;
+                            }
+                        }
                     }
                 }
-            }
-        }
 #pragma unroll
-        for (int j = 0; j < kFwXB; ++j) {
-            ek[j].add(re[j]);
-            nkk[j].add(rk[j]);
-            ntk[j].add(rt[j]);
+                for (int j = 0; j < kFwXB; ++j) {
+                    ek[j].add(re[j]);
+                    nkk[j].add(rk[j]);
+                    ntk[j].add(rt[j]);
+                }
+            }
         }
     }
     double e[kFwXB], nk[kFwXB], nt[kFwXB];
@@ -371,12 +405,13 @@ __global__ void __launch_bounds__(256) diff_rowbox_kernel(int M, int U, int W, c
 // dL/df(p) = sum_x [a(p-x) c(x) - b(p-x) t0(x)] + sum_x hf(p-x) - f(p) sum_x h(p-x)
 // over template positions x with p - x a valid offset.  A CTA covers 64 x 16
 // pixels with kGfYG groups of threads; thread (g, ry, gx) owns pixels
-// px0 + 8gx .. +7 of row py0 + ry for the template rows y = g, g + kGfYG, ...,
-// and the groups' partial sums meet in shared memory at the end.  The a and b
-// regions the tile needs are staged in shared memory, with the template's
-// columns reversed (x' = W-1-x, zero-padded to a multiple of 8), so that along
-// x' the thread's eight pixels read one sliding window of eight consecutive
-// region columns: each step loads one new a and one new b value and does 16
+// px0 + 8gx .. +7 of row py0 + ry for the rows y = g, g + kGfYG, ... of each
+// template block, and the groups' partial sums meet in shared memory at the
+// end.  For each block of at most 64 x 64 the a and b regions the tile needs
+// are staged in shared memory, with the block's columns reversed
+// (x' = bw-1-x, zero-padded to a multiple of 8), so that along x' the
+// thread's eight pixels read one sliding window of eight consecutive region
+// columns: each step loads one new a and one new b value and does 16
 // multiply-adds.  The h and h*fbar window sums come from the row sums of
 // diff_rowbox_kernel, summed over template rows in FP64.
 constexpr int kGfTX = 64, kGfTY = 16, kGfXB = 8, kGfYG = 4;
@@ -385,10 +420,11 @@ constexpr int kGfThreads = kGfGroup * kGfYG;
 
 __host__ __device__ inline int gf_w8(int W) { return (W + 7) & ~7; }
 __host__ __device__ inline int gf_rw(int W) { return kGfTX + gf_w8(W) - 1 + 1; }  // region pitch (one spare)
-// dynamic shared memory: the staged a, b regions and reversed c, t0, or the
-// partial sums of groups 1.. (whichever is larger)
+// dynamic shared memory: the staged a, b regions and reversed c, t0 of the
+// largest block, or the partial sums of groups 1.. (whichever is larger)
 __host__ __device__ inline size_t gf_smem(int W, int H) {
-    const size_t stage = (2 * (size_t)gf_rw(W) * (kGfTY + H - 1) + 2 * (size_t)H * gf_w8(W)) * 4;
+    const int bw = blk_edge(W), bh = blk_edge(H);
+    const size_t stage = (2 * (size_t)gf_rw(bw) * (kGfTY + bh - 1) + 2 * (size_t)bh * gf_w8(bw)) * 4;
     const size_t part = (size_t)(kGfYG - 1) * kGfGroup * kGfXB * 8;
     return stage > part ? stage : part;
 }
@@ -402,62 +438,71 @@ __global__ void __launch_bounds__(kGfThreads, 2) diff_grad_f_kernel(const float*
                                                                  const float* __restrict__ rhf,
                                                                  float* __restrict__ grad, int gstride) {
     extern __shared__ __align__(16) float sm[];
-    const int W8 = gf_w8(W), RW = gf_rw(W), RH = kGfTY + H - 1;
+    const int RW = gf_rw(blk_edge(W)), RHmax = kGfTY + blk_edge(H) - 1;  // region pitch and rows of the largest block
     const int U = M - W + 1, V = N - H + 1;
     float* as = sm;
-    float* bs = as + RW * RH;
-    float* cr = bs + RW * RH;  // H x W8, reversed columns
-    float* tr = cr + H * W8;
+    float* bs = as + RW * RHmax;
+    float* cr = bs + RW * RHmax;  // bh x w8 of a block, reversed columns
+    float* tr = cr + blk_edge(H) * gf_w8(blk_edge(W));
     const int px0 = blockIdx.x * kGfTX, py0 = blockIdx.y * kGfTY;
-    const int ox0 = px0 - (W - 1), oy0 = py0 - (H - 1);
-    for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
-        const int Y = i / RW, X = i - Y * RW;
-        const int ou = ox0 + X, ov = oy0 + Y;
-        const bool in = (ou >= 0 && ov >= 0 && ou < U && ov < V);
-        const size_t o = in ? (size_t)ov * U + ou : 0;
-        as[i] = in ? a[o] : 0.0f;
-        bs[i] = in ? b[o] : 0.0f;
-    }
-    for (int i = threadIdx.x; i < H * W8; i += blockDim.x) {
-        const int y = i / W8, xr = i - y * W8;
-        const bool in = xr < W;
-        cr[i] = in ? c[y * W + (W - 1 - xr)] : 0.0f;
-        tr[i] = in ? t0[y * W + (W - 1 - xr)] : 0.0f;
-    }
-    __syncthreads();
     const int grp = threadIdx.x / kGfGroup, t = threadIdx.x - grp * kGfGroup;
     const int gx = t % (kGfTX / kGfXB), ry = t / (kGfTX / kGfXB);
     const int py = py0 + ry, pxb = px0 + gx * kGfXB;
     KahanF acck[kGfXB];
-    if (py < N && pxb < M) {
-        for (int y = grp; y < H; y += kGfYG) {
-            // offset row py - y  ->  region row ry + H - 1 - y; pixel pxb + j, x = W-1-x'
-            // ->  offset column pxb + j - x  ->  region column gx*8 + j + x'
-            const float* arow = as + (ry + H - 1 - y) * RW + gx * kGfXB;
-            const float* brow = bs + (ry + H - 1 - y) * RW + gx * kGfXB;
-            const float* crow = cr + y * W8;
-            const float* trow = tr + y * W8;
-            float r[kGfXB], wa[kGfXB], wb[kGfXB];
-#pragma unroll
-            for (int j = 0; j < kGfXB; ++j) r[j] = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kGfXB - 1; ++j) {
-                wa[j] = arow[j];
-                wb[j] = brow[j];
+    for (int by = 0; by < H; by += kDiffBlk) {
+        for (int bx = 0; bx < W; bx += kDiffBlk) {
+            const int bw = min(kDiffBlk, W - bx), bh = min(kDiffBlk, H - by);
+            const int w8 = gf_w8(bw), rw = kGfTX + w8, rh = kGfTY + bh - 1;
+            // offsets o = p - x for x in the block: columns from px0 - (bx + bw - 1), rows from py0 - (by + bh - 1)
+            const int ox0 = px0 - (bx + bw - 1), oy0 = py0 - (by + bh - 1);
+            __syncthreads();  // the previous block's reads are done
+            for (int i = threadIdx.x; i < rw * rh; i += blockDim.x) {
+                const int Y = i / rw, X = i - Y * rw;
+                const int ou = ox0 + X, ov = oy0 + Y;
+                const bool in = (ou >= 0 && ov >= 0 && ou < U && ov < V);
+                const size_t o = in ? (size_t)ov * U + ou : 0;
+                as[Y * RW + X] = in ? a[o] : 0.0f;
+                bs[Y * RW + X] = in ? b[o] : 0.0f;
             }
-            for (int xq = 0; xq < W8; xq += kGfXB) {
+            for (int i = threadIdx.x; i < bh * w8; i += blockDim.x) {
+                const int y = i / w8, xr = i - y * w8;
+                const bool in = xr < bw;
+                cr[i] = in ? c[(by + y) * W + bx + (bw - 1 - xr)] : 0.0f;
+                tr[i] = in ? t0[(by + y) * W + bx + (bw - 1 - xr)] : 0.0f;
+            }
+            __syncthreads();
+            if (py < N && pxb < M) {
+                for (int y = grp; y < bh; y += kGfYG) {
+                    // offset row py - (by + y)  ->  region row ry + bh - 1 - y; pixel pxb + j, block
+                    // column bw-1-x'  ->  offset column pxb + j - bx - (bw-1-x')  ->  region column gx*8 + j + x'
+                    const float* arow = as + (ry + bh - 1 - y) * RW + gx * kGfXB;
+                    const float* brow = bs + (ry + bh - 1 - y) * RW + gx * kGfXB;
+                    const float* crow = cr + y * w8;
+                    const float* trow = tr + y * w8;
+                    float r[kGfXB], wa[kGfXB], wb[kGfXB];
 #pragma unroll
-                for (int k = 0; k < kGfXB; ++k) {
-                    // wa[(k + j) % 8] holds region column xq + k + j
-                    wa[(k + kGfXB - 1) % kGfXB] = arow[xq + k + kGfXB - 1];
-                    wb[(k + kGfXB - 1) % kGfXB] = brow[xq + k + kGfXB - 1];
-                    const float cv = crow[xq + k], tv = trow[xq + k];
+                    for (int j = 0; j < kGfXB; ++j) r[j] = 0.0f;
 #pragma unroll
-                    for (int j = 0; j < kGfXB; ++j) r[j] += wa[(k + j) % kGfXB] * cv - wb[(k + j) % kGfXB] * tv;
+                    for (int j = 0; j < kGfXB - 1; ++j) {
+                        wa[j] = arow[j];
+                        wb[j] = brow[j];
+                    }
+                    for (int xq = 0; xq < w8; xq += kGfXB) {
+#pragma unroll
+                        for (int k = 0; k < kGfXB; ++k) {
+                            // wa[(k + j) % 8] holds region column xq + k + j
+                            wa[(k + kGfXB - 1) % kGfXB] = arow[xq + k + kGfXB - 1];
+                            wb[(k + kGfXB - 1) % kGfXB] = brow[xq + k + kGfXB - 1];
+                            const float cv = crow[xq + k], tv = trow[xq + k];
+#pragma unroll
+                            for (int j = 0; j < kGfXB; ++j)
+                                r[j] += wa[(k + j) % kGfXB] * cv - wb[(k + j) % kGfXB] * tv;
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < kGfXB; ++j) acck[j].add(r[j]);
                 }
             }
-#pragma unroll
-            for (int j = 0; j < kGfXB; ++j) acck[j].add(r[j]);
         }
     }
     // groups 1.. hand their partial sums to group 0 (the staging area is free now)
@@ -486,8 +531,9 @@ __global__ void __launch_bounds__(kGfThreads, 2) diff_grad_f_kernel(const float*
 }
 
 // Partial Gt(x, y) = sum_{o in chunk} a(o) f(o + (x, y)): grid
-// (ceil(H / kGtYB), kGtChunks), kGtYB * ceil(W / kGtXB) threads; thread
-// (yy, xg) owns template row y0 + yy and columns xg*kGtXB .. +kGtXB-1.  The
+// (ceil(H / kGtYB), kGtChunks, ceil(W / 64)), kGtYB * ceil(min(W, 64) / kGtXB)
+// threads; in template column block z (columns 64z .. 64z+63) thread
+// (yy, xg) owns template row y0 + yy and block columns xg*kGtXB .. +kGtXB-1.  The
 // CTA stages up to kGtVS offset rows x kGtUS offset columns of a, and the source
 // rows and columns they meet, in shared memory; along u the thread keeps the
 // last kGtXB source values in registers, so each step is one broadcast load
@@ -498,12 +544,13 @@ __global__ void __launch_bounds__(128) diff_gt_kernel(const float* __restrict__ 
     __shared__ float fs[(kGtVS + kGtYB - 1) * kGtFW];
     __shared__ float as[kGtVS * kGtUS];
     const int U = M - W + 1, V = N - H + 1;
-    const int XG = (W + kGtXB - 1) / kGtXB;
+    const int xb = blockIdx.z * kDiffBlk, bw = min(kDiffBlk, W - xb);
+    const int XG = (bw + kGtXB - 1) / kGtXB;
     const int y0 = blockIdx.x * kGtYB, chunk = blockIdx.y;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int yy = tid / XG, xg = tid - yy * XG;
     const int y = y0 + yy, x0 = xg * kGtXB;
-    const bool active = y < H;
+    const bool active = yy < kGtYB && y < H;
     const int vb = (int)((long long)V * chunk / kGtChunks), ve = (int)((long long)V * (chunk + 1) / kGtChunks);
     KahanF accd[kGtXB];
     for (int vs = vb; vs < ve; vs += kGtVS) {
@@ -516,7 +563,7 @@ __global__ void __launch_bounds__(128) diff_gt_kernel(const float* __restrict__ 
             }
             for (int i = tid; i < (kGtVS + kGtYB - 1) * kGtFW; i += nthr) {
                 const int rr = i / kGtFW, cc = i - rr * kGtFW;
-                const int row = vs + y0 + rr, col = us + cc;
+                const int row = vs + y0 + rr, col = us + xb + cc;
                 fs[i] = (row < N && col < M) ? f[(size_t)row * stride + col] : 0.0f;
             }
             __syncthreads();
@@ -548,7 +595,7 @@ __global__ void __launch_bounds__(128) diff_gt_kernel(const float* __restrict__ 
     if (active) {
 #pragma unroll
         for (int j = 0; j < kGtXB; ++j)
-            if (x0 + j < W) gtp[((size_t)chunk * H + y) * W + x0 + j] = accd[j].value();
+            if (x0 + j < bw) gtp[((size_t)chunk * H + y) * W + xb + x0 + j] = accd[j].value();
     }
 }
 
@@ -598,7 +645,7 @@ cudaError_t set_diff_attributes() {
 
 bool diff_args_ok(int M, int N, int W, int H, int K, int f_stride) {
     return M > 0 && N > 0 && W > 0 && H > 0 && W <= kDiffMax && H <= kDiffMax && W <= M && H <= N && K > 0 &&
-           K <= W * H && f_stride >= M && 256 / W >= 1;
+           K <= W * H && f_stride >= M;
 }
 
 }  // namespace
@@ -670,9 +717,9 @@ extern "C" int sncc_diff_backward(const float* d_f, int M, int N, int f_stride, 
     dim3 gridf((M + kGfTX - 1) / kGfTX, (N + kGfTY - 1) / kGfTY);
     diff_grad_f_kernel<<<gridf, kGfThreads, smf, st>>>(d_f, M, N, f_stride, W, H, c, t0, a, b, rh, rhf, d_grad_f,
                                                        grad_f_stride);
-    const int gt_threads = kGtYB * ((W + kGtXB - 1) / kGtXB);
-    diff_gt_kernel<<<dim3((H + kGtYB - 1) / kGtYB, kGtChunks), gt_threads, 0, st>>>(d_f, M, N, f_stride, W, H, a,
-                                                                                    gtp);
+    const int gt_threads = kGtYB * ((blk_edge(W) + kGtXB - 1) / kGtXB);
+    diff_gt_kernel<<<dim3((H + kGtYB - 1) / kGtYB, kGtChunks, (W + kDiffBlk - 1) / kDiffBlk), gt_threads, 0, st>>>(
+        d_f, M, N, f_stride, W, H, a, gtp);
     double* gt = reinterpret_cast<double*>(ws + L.gt);
     diff_gt_reduce_kernel<<<(W * H * kGtReduceLanes + 255) / 256, 256, 0, st>>>(W * H, gtp, gt);
     diff_grad_k_kernel<<<(K + 255) / 256, 256, 0, st>>>(W, H, reinterpret_cast<const int4*>(d_rects), d_k, K, gt,

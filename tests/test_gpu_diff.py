@@ -132,3 +132,50 @@ def test_backward_after_another_forward_on_the_same_workspace(sncc, problem):
     for g1, g2 in ((ka.grad, kc.grad), (kb.grad, kd2.grad)):
         assert float((g1 - g2).abs().max()) <= 1e-6 * float(g2.abs().max())
     assert float((ka.grad - kb.grad).abs().max()) > 1e-3 * float(kb.grad.abs().max())
+
+
+def test_diff_multi_block_template_vs_oracle(sncc):
+    """A 150 x 100 template (blocks of 64 x 64: three columns of blocks, the
+    last 22 wide, and two rows, the last 36 high) on a 200 x 150 float
+    source: the loss, both maps and both gradients against the FP64 oracle,
+    and one segment value and two source pixels against FP64 central
+    differences (step 1e-3)."""
+    f, t, org, sigma = synth.case_diff(M=200, N=150, W=150, H=100)
+    seg = sncc.build_segments(np.rint(np.clip(t, 0, 255)).astype(np.uint8), sigma)
+    rects = seg.table
+    k0 = np.array([t[y:y + h, x:x + w].mean() for x, y, w, h in rects], np.float64)
+    k0 = k0 + np.random.default_rng(2).normal(0.0, 1.5, size=len(k0))
+    k32 = k0.astype(np.float32)
+    N, M = f.shape
+    pb = sncc.DiffProblem(t, rects, M, N)
+    fd = torch.as_tensor(f).cuda().requires_grad_(True)
+    kd = torch.as_tensor(k32).cuda().requires_grad_(True)
+    rho_k, rho_t, loss0 = sncc._diff_forward(pb, fd.detach(), kd.detach())
+    torch.cuda.synchronize()
+    f64, t64, k64 = f.astype(np.float64), t.astype(np.float64), k32.astype(np.float64)
+    ref = D.gradients(f64, t64, rects, k64)
+    fw = D.forward(f64, t64, rects, k64)
+    assert np.abs(rho_k.cpu().numpy() - fw["rho_k"]).max() <= 1e-5
+    assert np.abs(rho_t.cpu().numpy() - fw["rho_t"]).max() <= 1e-5
+    assert abs(float(loss0.item()) - fw["loss"]) <= 1e-5 * fw["loss"]
+    loss = pb.loss(fd, kd)
+    loss.backward()
+    torch.cuda.synchronize()
+    gk = kd.grad.cpu().numpy()
+    gf = fd.grad.cpu().numpy()
+    assert rel(gk, ref["dk"]) <= 1e-4
+    assert rel(gf, ref["df"]) <= 1e-4
+    h = 1e-3
+    j = int(np.abs(ref["dk"]).argmax())
+    kp, km = k64.copy(), k64.copy()
+    kp[j] += h
+    km[j] -= h
+    num = (D.forward(f64, t64, rects, kp)["loss"] - D.forward(f64, t64, rects, km)["loss"]) / (2 * h)
+    assert abs(gk[j] - num) <= 1e-4 * np.abs(ref["dk"]).max(), (j, gk[j], num)
+    y, x = np.unravel_index(int(np.abs(ref["df"]).argmax()), f.shape)
+    for (py, px) in [(int(y), int(x)), (120, 70)]:
+        fp, fm = f64.copy(), f64.copy()
+        fp[py, px] += h
+        fm[py, px] -= h
+        num = (D.forward(fp, t64, rects, k64)["loss"] - D.forward(fm, t64, rects, k64)["loss"]) / (2 * h)
+        assert abs(gf[py, px] - num) <= 1e-4 * np.abs(ref["df"]).max(), (py, px, gf[py, px], num)
