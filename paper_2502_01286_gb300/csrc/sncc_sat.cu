@@ -40,6 +40,9 @@ namespace sncc {
 namespace {
 
 constexpr int kEmitWarps = 8;                 // warps per band-emit CTA, one (band, tile) each
+constexpr int kEmitMinCtas = 24 / kEmitWarps;  // resident emit CTAs per SM the registers must allow (80 each)
+constexpr int kColThreads = 32;               // threads per column-sum CTA (8 columns each): one-warp CTAs
+                                              // spread the (band, chunk) warps evenly over the SMs
 constexpr int kLaneCols = 8;                  // output columns per lane
 constexpr int kTileCols = 32 * kLaneCols;     // output columns per warp tile
 constexpr int kMaxR = 64;                     // rows per band at most
@@ -183,7 +186,7 @@ __device__ __forceinline__ int byte_of(uint2 w, int e) {
 // next four rows load while four are summed.
 constexpr int kColRows = 4;
 
-__global__ void __launch_bounds__(256) sat_band_colsum(const uint8_t* __restrict__ f, int M, int N, int stride,
+__global__ void __launch_bounds__(kColThreads) sat_band_colsum(const uint8_t* __restrict__ f, int M, int N, int stride,
                                                        int R, int nk, int cp, int32_t* __restrict__ cs1,
                                                        int32_t* __restrict__ cs2, int32_t* __restrict__ rs1,
                                                        int32_t* __restrict__ rs2) {
@@ -399,7 +402,7 @@ __device__ __forceinline__ void stage_flush(const unsigned char* stage, int lane
 }
 
 template <typename ST>
-__global__ void __launch_bounds__(kEmitWarps * 32, 3) sat_band_emit(const uint8_t* __restrict__ f, int M, int N,
+__global__ void __launch_bounds__(kEmitWarps * 32, kEmitMinCtas) sat_band_emit(const uint8_t* __restrict__ f, int M, int N,
                                                                  int stride, int R, int nb, int nc, int nk, int nj,
                                                                  int cp, int pitch, const int32_t* __restrict__ ca1,
                                                                  const int32_t* __restrict__ ca2,
@@ -637,9 +640,9 @@ extern "C" int sncc_integral(const uint8_t* d_f, int M, int N, int f_stride, voi
     int64_t* ch1 = reinterpret_cast<int64_t*>(ws + w.ch1);
     int64_t* ch2 = reinterpret_cast<int64_t*>(ws + w.ch2);
     cudaStream_t st = (cudaStream_t)stream;
-    const dim3 g1((M + 256 * kLaneCols - 1) / (256 * kLaneCols), g.nb);
+    const dim3 g1((M + kColThreads * kLaneCols - 1) / (kColThreads * kLaneCols), g.nb);
     const int cp = col_pitch(M);
-    sat_band_colsum<<<g1, 256, 0, st>>>(d_f, M, N, f_stride, g.R, g.nk, cp, cs1, cs2, rs1, rs2);
+    sat_band_colsum<<<g1, kColThreads, 0, st>>>(d_f, M, N, f_stride, g.R, g.nk, cp, cs1, cs2, rs1, rs2);
     // the scan and the emit launch while their predecessor drains and wait
     // for it in the kernel (programmatic dependent launch)
     cudaLaunchAttribute pdl[1];
