@@ -410,10 +410,13 @@ def measured_peaks():
 
 
 def measure_ceilings(sncc, torch, stream, dev):
-    """On-chip ceilings measured live by the library's probes (best of 5):
+    """Ceilings measured live by the library's probes (best of 5):
     shared-memory read GB/s, dp4a and 32x32->64-bit multiply-add
-    instructions per second (lane operations)."""
-    sink = torch.empty(152 * 8 * 256, dtype=torch.int32, device=dev)
+    instructions per second (lane operations), and the HBM write rate of
+    16-byte stores over 1 GiB."""
+    set_sm_count(torch, dev)
+    ctas = SM_COUNT * 8
+    sink = torch.empty(ctas * 256, dtype=torch.int32, device=dev)
 
     def best(launch):
         launch(8)
@@ -428,13 +431,32 @@ def measure_ceilings(sncc, torch, stream, dev):
             rates.append(n / (a.elapsed_time(b) * 1e-3))
         return max(rates)
 
-    return {"smem_gbs": best(lambda it: sncc.probe_smem_read(sink, 152 * 8, it)) / 1e9,
-            "dp4a_per_s": best(lambda it: sncc.probe_alu(sncc.PROBE_DP4A, sink, 152 * 8, it // 4)),
-            "imad_wide_per_s": best(lambda it: sncc.probe_alu(sncc.PROBE_IMAD_WIDE, sink, 152 * 8, it // 4))}
+    wbuf = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+    sncc.probe_hbm_write(wbuf)
+    wrates = []
+    for _ in range(5):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n = sncc.probe_hbm_write(wbuf)
+        b.record(stream)
+        torch.cuda.synchronize()
+        wrates.append(n / (a.elapsed_time(b) * 1e-3))
+    del wbuf
+    return {"smem_gbs": best(lambda it: sncc.probe_smem_read(sink, ctas, it)) / 1e9,
+            "dp4a_per_s": best(lambda it: sncc.probe_alu(sncc.PROBE_DP4A, sink, ctas, it // 4)),
+            "imad_wide_per_s": best(lambda it: sncc.probe_alu(sncc.PROBE_IMAD_WIDE, sink, ctas, it // 4)),
+            "hbm_write_gbs": max(wrates) / 1e9}
 
 
 IMAD_WIDE_PER_CLK_SM = 32  # 16-lane integer multiplier per SM sub-partition, two passes per 64-bit product
-SM_COUNT, SM_MAX_MHZ = 152, 2070
+SM_COUNT, SM_MAX_MHZ = 152, 2070  # SM count replaced by the device's own at the first measurement
+
+
+def set_sm_count(torch, dev):
+    """The SM count of the device the bench runs on (for the nominal peaks)."""
+    global SM_COUNT
+    SM_COUNT = int(torch.cuda.get_device_properties(dev).multi_processor_count)
 
 
 def match_tile_rows(U, V):
@@ -455,7 +477,7 @@ def segsum_roofline(kernel, corner_ops, ms, ceil, traffic=None, smem_words=None,
     peak = SM_COUNT * IMAD_WIDE_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
     out = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "Tops/s",
            "frac": achieved / peak, "traffic": traffic, "ops_per_launch": corner_ops, "ms_per_launch": ms,
-           "peak_source": "152 SMs x 32 IMAD.WIDE lane-ops/clk/SM x 2070 MHz (nominal)",
+           "peak_source": "%d SMs x 32 IMAD.WIDE lane-ops/clk/SM x %d MHz (nominal)" % (SM_COUNT, SM_MAX_MHZ),
            "imad_wide_probe": {"peak": ceil["imad_wide_per_s"] / 1e12, "unit": "Tops/s",
                                "frac": achieved * 1e12 / ceil["imad_wide_per_s"],
                                "source": "measured: IMAD.WIDE instruction probe (all SMs), this run"}}
@@ -486,6 +508,7 @@ def run_gpu(args, world, rank, local, pg):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    set_sm_count(torch, dev)
     stream = torch.cuda.current_stream()
     band = None
     if args.shard == "bands" and world > 1:
@@ -825,7 +848,11 @@ def run_gpu(args, world, rank, local, pg):
         "sum_tables": {"ms": sat_med, "algorithmic_bytes": sat_bytes,
                        "achieved_gbs": sat_bytes / (sat_med * 1e-3) / 1e9,
                        "frac_of_hbm": (sat_bytes / (sat_med * 1e-3) / 1e9) / peaks_hbm if peaks_hbm else None,
-                       "peak": "MEASURED_PEAKS hbm_gbs"},
+                       "peak": "MEASURED_PEAKS hbm_gbs",
+                       # the tables are almost all 16-byte stores: also against the write rate of such stores
+                       "write_probe_gbs": ceil["hbm_write_gbs"],
+                       "frac_of_write_probe": (sat_bytes / (sat_med * 1e-3) / 1e9) / ceil["hbm_write_gbs"],
+                       "write_probe_source": "measured: 16-byte store probe over 1 GiB (all SMs), this run"},
         "paper_two_stage": two,
         "roofline": segsum_roofline("match_kernel" + (" (fused over %d thresholds)" % len(SIGMAS) if fused else ""),
                                     dom_ops, dom_ms, ceil, traffic=recorded_traffic(args.workload),
@@ -893,6 +920,7 @@ def run_gpu_batch(args, world, rank, local, pg):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    set_sm_count(torch, dev)
     stream = torch.cuda.current_stream()
     srcs, tl = batch_problem(rank)
     N, M = srcs[0].shape
@@ -1058,6 +1086,7 @@ def run_gpu_crossover(args, world, rank, local, pg):
     from paper_2502_01286_gb300 import sncc
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    set_sm_count(torch, dev)
     stream = torch.cuda.current_stream()
     case, _, precision = make_case("texture", rank)
     N, M = case.f.shape
@@ -1167,6 +1196,7 @@ def run_gpu_diff(args, world, rank, local, pg):
     from paper_2502_01286_gb300 import sncc, synth
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    set_sm_count(torch, dev)
     stream = torch.cuda.current_stream()
     f, t, org, sigma = synth.case_diff(seed=synth.BASE_SEED + 5 + 1000 * rank)
     N, M = f.shape
@@ -1301,7 +1331,8 @@ def run_gpu_diff(args, world, rank, local, pg):
                                                     "diff_gt_reduce, diff_grad_k)",
                          "achieved": bwd_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": bwd_tflops / fp32_peak,
                          "traffic": None, "flops_per_launch": bwd_flops, "ms_per_launch": bwd_ms,
-                         "peak_source": "152 SMs x 128 FP32 FMA lanes x 2 x 2070 MHz (nominal)"},
+                         "peak_source": "%d SMs x 128 FP32 FMA lanes x 2 x %d MHz (nominal)" % (SM_COUNT,
+                                                                                                 SM_MAX_MHZ)},
             "e2e": {"value": sum_over_ranks(pg, U * V) / (e2e_ms_step * 1e-3) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": M * N * 4, "d2h_bytes_per_step": 8 + 4 * pb.K, "ms_per_step": e2e_ms_step},
             "refit": {"steps": 50, "loss_first": losses[0], "loss_last": losses[-1]},

@@ -739,6 +739,15 @@ int sncc_probe_wait_timeout(int32_t* d_status, sncc_stream_t stream);
 #define SNCC_PROBE_IMAD_WIDE 1
 int sncc_probe_alu(int kind, int32_t* d_sink, int ctas, int iters, sncc_stream_t stream);
 
+/* HBM write-bandwidth probe: writes all `bytes` of d_buf (device, 16-byte
+ * aligned, a multiple of 16, best larger than L2) with 16-byte stores; entry
+ * i (16 bytes) becomes {lo, hi ^ 0x5a5a5a5a, 3 lo, lo ^ 0xffff} for the low
+ * and high 32 bits of i.  The sum tables are almost all such stores, so the
+ * benchmark reports them against this rate as well as against the copy
+ * bandwidth; not part of the matching path.  SNCC_ERR_ARG for a null,
+ * unaligned or ragged buffer. */
+int sncc_probe_hbm_write(void* d_buf, size_t bytes, sncc_stream_t stream);
+
 /* Library version string. */
 const char* sncc_version(void);
 

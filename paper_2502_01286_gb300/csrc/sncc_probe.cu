@@ -6,12 +6,16 @@
 // loop.  Instruction rates: the segment-sum kernel adds one 32 x 32 -> 64-bit
 // integer multiply-add per (offset, corner), and the exact comparator one
 // four-way byte dot product (dp4a) per four template pixels; probe_alu issues
-// only that instruction, in eight independent chains per thread.
+// only that instruction, in eight independent chains per thread.  HBM write
+// bandwidth: the sum tables are almost all 16-byte stores (12 or 16 bytes
+// written per pixel against 1 read); probe_hbm_write writes a buffer larger
+// than L2 with 16-byte stores and nothing else.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "sncc.h"
+#include "sncc_internal.h"
 #include "sncc_ptx.cuh"
 
 namespace sncc {
@@ -104,8 +108,24 @@ __global__ void __launch_bounds__(32) probe_wait_timeout(int32_t* __restrict__ s
     if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u)) atomicOr(status, SNCC_STATUS_WAIT_TIMEOUT);
 }
 
+// Grid-stride 16-byte stores of a pattern that depends on the address.
+__global__ void __launch_bounds__(256) probe_hbm_write(int4* __restrict__ buf, size_t n16) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+        const uint32_t lo = (uint32_t)i, hi = (uint32_t)(i >> 32);
+        buf[i] = make_int4((int)lo, (int)(hi ^ 0x5a5a5a5au), (int)(lo * 3u), (int)(lo ^ 0xffffu));
+    }
+}
+
 }  // namespace
 }  // namespace sncc
+
+extern "C" int sncc_probe_hbm_write(void* d_buf, size_t bytes, sncc_stream_t stream) {
+    if (!d_buf || bytes < 16 || (bytes & 15) || (reinterpret_cast<uintptr_t>(d_buf) & 15)) return SNCC_ERR_ARG;
+    const int sms = sncc::sm_count() > 0 ? sncc::sm_count() : 1;
+    sncc::probe_hbm_write<<<sms * 8, 256, 0, (cudaStream_t)stream>>>(static_cast<int4*>(d_buf), bytes / 16);
+    return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
+}
 
 extern "C" int sncc_probe_smem_read(int32_t* d_sink, int ctas, int iters, sncc_stream_t stream) {
     if (!d_sink || ctas <= 0 || iters <= 0) return SNCC_ERR_ARG;

@@ -36,7 +36,7 @@ EXPORTED = ["sncc_error_string", "sncc_version", "sncc_build_segments", "sncc_fr
             "sncc_match_multi", "sncc_pipeline_create", "sncc_pipeline_submit", "sncc_pipeline_flush",
             "sncc_pipeline_fused", "sncc_pipeline_compute_stream", "sncc_pipeline_destroy",
             "sncc_refine_workspace_bytes", "sncc_refine", "sncc_exact_map", "sncc_get_plan_info",
-            "sncc_probe_smem_read", "sncc_probe_alu", "sncc_probe_wait_timeout", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_refine_segmented_tiles",
+            "sncc_probe_smem_read", "sncc_probe_alu", "sncc_probe_wait_timeout", "sncc_probe_hbm_write", "sncc_integral_noalloc", "sncc_refine_segmented", "sncc_refine_segmented_tiles",
             "sncc_refine_segmented_tiles_workspace_bytes", "sncc_batch_create",
             "sncc_batch_destroy", "sncc_batch_device_bytes", "sncc_batch_upload", "sncc_batch_set_variant",
             "sncc_batch_get_info", "sncc_batch_match", "sncc_batch_autotune", "sncc_batch_refine_workspace_bytes",
@@ -167,6 +167,7 @@ _lib.sncc_get_plan_info.argtypes = [C.POINTER(_Segments), C.POINTER(PlanInfo)]
 _lib.sncc_probe_smem_read.argtypes = [_vp, C.c_int, C.c_int, _vp]
 _lib.sncc_probe_alu.argtypes = [C.c_int, _vp, C.c_int, C.c_int, _vp]
 _lib.sncc_probe_wait_timeout.argtypes = [_vp, _vp]
+_lib.sncc_probe_hbm_write.argtypes = [_vp, C.c_size_t, _vp]
 _lib.sncc_exact_map.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int64,
                                 C.c_int64, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp]
 
@@ -523,6 +524,14 @@ def probe_smem_read(sink, ctas: int, iters: int, stream=None) -> int:
 
 
 PROBE_DP4A, PROBE_IMAD_WIDE = 0, 1
+
+
+def probe_hbm_write(buf, stream=None) -> int:
+    """Launches the HBM write probe over the whole uint8 buffer; returns the
+    bytes written."""
+    n = buf.numel() * buf.element_size()
+    _check(_lib.sncc_probe_hbm_write(buf.data_ptr(), n, _stream(stream)), "sncc_probe_hbm_write")
+    return n
 
 
 def probe_wait_timeout(status, stream=None) -> None:

@@ -223,6 +223,9 @@ def test_host_argument_errors(sncc):
     assert lib.sncc_probe_alu(2, C.c_void_p(256), 1, 1, None) == sncc.ERR_ARG
     assert lib.sncc_probe_alu(sncc.PROBE_DP4A, C.c_void_p(256), 0, 1, None) == sncc.ERR_ARG
     assert lib.sncc_probe_alu(sncc.PROBE_IMAD_WIDE, None, 1, 1, None) == sncc.ERR_ARG
+    assert lib.sncc_probe_hbm_write(None, 1 << 20, None) == sncc.ERR_ARG
+    assert lib.sncc_probe_hbm_write(C.c_void_p(256), 1000, None) == sncc.ERR_ARG  # not a multiple of 16
+    assert lib.sncc_probe_hbm_write(C.c_void_p(264), 1 << 20, None) == sncc.ERR_ARG  # not 16-byte aligned
     assert lib.sncc_refine_segmented_tiles_workspace_bytes(0, 5, 1, 1, 4) == 0
     assert lib.sncc_refine_segmented_tiles_workspace_bytes(64, 64, 65, 8, 4) == 0
     assert lib.sncc_refine_segmented_tiles_workspace_bytes(256, 256, 32, 32, 16) >= 225 * 225 // 8

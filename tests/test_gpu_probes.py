@@ -77,6 +77,20 @@ def test_smem_probe_runs(sncc):
     torch.cuda.synchronize()
 
 
+def test_hbm_write_probe_writes_every_entry(sncc):
+    """Every 16-byte entry i of a buffer larger than L2 holds the header's
+    pattern {lo, hi ^ 0x5a5a5a5a, 3 lo, lo ^ 0xffff} after the probe."""
+    import torch
+    buf = torch.full((160 << 20,), 7, dtype=torch.uint8, device="cuda")
+    assert sncc.probe_hbm_write(buf) == 160 << 20
+    torch.cuda.synchronize()
+    got = buf.view(torch.int32).view(-1, 4).cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    i = np.arange(got.shape[0], dtype=np.int64)
+    lo, hi = i & 0xFFFFFFFF, i >> 32
+    want = np.stack([lo, hi ^ 0x5A5A5A5A, (lo * 3) & 0xFFFFFFFF, lo ^ 0xFFFF], axis=1)
+    assert np.array_equal(got, want)
+
+
 def test_bounded_wait_gives_up_and_reports(sncc):
     """A wait that nothing completes ends after the wait limit with the
     timeout status bit, and the context keeps working afterwards."""
