@@ -1,7 +1,8 @@
 // sncc_sat.cu - exact integer sum tables of f and f^2 (Eq. 10 and Eq. 14).
 //
 // Layout: padded tables of (N+1) rows x pitch elements, entry [Y*pitch + X]
-// = sum of f over x < X, y < Y (row 0 and column 0 are zero).
+// = sum of f over x < X, y < Y (row 0 and column 0 are zero); a 32-bit s
+// keeps the sums modulo 2^32.
 //
 // The table is produced band by band (R rows each) and, inside a band, tile
 // by tile (256 output columns).  A (band, tile) is independent once three
@@ -19,6 +20,8 @@
 //      in registers (one lane per 8 columns), a lane prefix and a 32-bit
 //      warp scan per row, adds one 64-bit base per lane, and stores each
 //      tile row through a warp staging buffer as 512-byte stores.
+// The scan and the emit are launched as programmatic dependents of the
+// pass before them and wait for it in the kernel.
 // Algorithmic traffic: 1 B/px read, 4 or 8 B/px (s) + 8 B/px (s^2) written;
 // pass 1 and the emit read f once each (the second time mostly from L2), and
 // the carry and chunk arrays are small.
