@@ -311,16 +311,21 @@ int bucket_of(int W, int H, int corners) {
 
 template <int R, int WP, bool S64>
 cudaError_t batch_launch(const BatchArgs& args, cudaStream_t st) {
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    static int per_sm = 0;
+    static std::atomic<int> done[kDeviceSlots];
+    static std::atomic<int> per_sm_of[kDeviceSlots];  // resident CTAs per SM, per device
     constexpr size_t smem = batch_smem<R, WP>();
-    std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(batch_match_kernel<R, WP, S64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem);
-        if (attr == cudaSuccess)
-            attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_match_kernel<R, WP, S64>, WARPS * 32,
-                                                                 smem);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+    const bool slot = dev >= 0 && dev < kDeviceSlots;
+    int per_sm = slot ? per_sm_of[dev].load(std::memory_order_relaxed) : 0;
+    const cudaError_t attr = once_per_device(done, [&] {
+        cudaError_t e = cudaFuncSetAttribute(batch_match_kernel<R, WP, S64>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_match_kernel<R, WP, S64>, WARPS * 32,
+                                                              smem);
+        if (e == cudaSuccess && slot) per_sm_of[dev].store(per_sm, std::memory_order_relaxed);
+        return e;
     });
     if (attr != cudaSuccess) return attr;
     const int grid = std::max(1, per_sm) * std::max(1, sm_count());

@@ -631,16 +631,16 @@ __global__ void __launch_bounds__(256) diff_grad_k_kernel(int W, int H, const in
     grad_k[j] = (float)(s - nj * scal[3] - nj * cj * scal[4] / scal[1]);
 }
 
-// Opt-in shared-memory limits of the two large-tile kernels (once per process).
+// Opt-in shared-memory limits of the two large-tile kernels (once per device).
 cudaError_t set_diff_attributes() {
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
-        err = cudaFuncSetAttribute(diff_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    static std::atomic<int> done[kDeviceSlots];
+    return once_per_device(done, [] {
+        cudaError_t err =
+            cudaFuncSetAttribute(diff_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         if (err == cudaSuccess)
             err = cudaFuncSetAttribute(diff_grad_f_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+        return err;
     });
-    return err;
 }
 
 bool diff_args_ok(int M, int N, int W, int H, int K, int f_stride) {

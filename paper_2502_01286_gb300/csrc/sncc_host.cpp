@@ -392,17 +392,16 @@ int build_plan(const sncc_segments* s, Plan& p, bool small_blocks) {
 Plan* plan_of(const sncc_segments* s) { return s ? static_cast<Plan*>(s->plan) : nullptr; }
 
 int sm_count() {
-    constexpr int kMaxDevices = 128;
-    static std::atomic<int> cached[kMaxDevices];  // 0 = not yet queried
+    static std::atomic<int> cached[kDeviceSlots];  // 0 = not yet queried
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
-    if (dev < kMaxDevices) {
+    if (dev < kDeviceSlots) {
         const int c = cached[dev].load(std::memory_order_relaxed);
         if (c > 0) return c;
     }
     int n = 0;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 0;
-    if (dev < kMaxDevices) cached[dev].store(n, std::memory_order_relaxed);
+    if (dev < kDeviceSlots) cached[dev].store(n, std::memory_order_relaxed);
     return n;
 }
 

@@ -2,6 +2,7 @@
 // units (host plan layout, tile geometry, launch helpers).  Not installed.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -12,6 +13,26 @@
 #include "sncc.h"
 
 namespace sncc {
+
+// Devices whose one-time kernel set-up is remembered (ordinals beyond this
+// repeat it on every call, which is still correct).
+constexpr int kDeviceSlots = 128;
+
+// Runs `set` (a callable returning cudaError_t) for the current device
+// unless it already succeeded there.  Kernel attributes such as the opt-in
+// shared-memory limit, and occupancy figures, belong to a device, so a
+// process that uses several GPUs sets them on each.
+template <typename F>
+cudaError_t once_per_device(std::atomic<int> (&done)[kDeviceSlots], F&& set) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool slot = dev >= 0 && dev < kDeviceSlots;
+    if (slot && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    e = set();
+    if (e == cudaSuccess && slot) done[dev].store(1, std::memory_order_release);
+    return e;
+}
 
 // An NVTX range around one ABI call (visible to profilers; a no-op otherwise).
 struct NvtxRange {

@@ -338,12 +338,11 @@ cudaError_t launch_match(const CUtensorMap& map, const MatchArgs& a, int BH, cud
     MatchArgs args = a;
     args.RH = RH;
     const size_t sm = 128 + (size_t)smem_words(RH, WP) * 4;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(match_kernel<R, S64, WP, FINE, DIRECT, MULTI, REGS>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        128 + smem_words(WARPS * R + 64 + 1, WP) * 4);
+    static std::atomic<int> done[kDeviceSlots];
+    const cudaError_t attr_err = once_per_device(done, [] {
+        return cudaFuncSetAttribute(match_kernel<R, S64, WP, FINE, DIRECT, MULTI, REGS>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    128 + smem_words(WARPS * R + 64 + 1, WP) * 4);
     });
     if (attr_err != cudaSuccess) return attr_err;
     const int tu = (a.U + TILE_U - 1) / TILE_U, tv = (a.V + WARPS * R - 1) / (WARPS * R);

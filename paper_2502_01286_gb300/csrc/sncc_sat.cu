@@ -577,11 +577,10 @@ __global__ void __launch_bounds__(kEmitWarps * 32, kEmitMinCtas) sat_band_emit(c
 // Emit warps resident on the whole current device at once (0 if unknown),
 // cached per device: both table widths' kernels, the smaller.
 long long emit_slots() {
-    constexpr int kMaxDevices = 128;
-    static std::atomic<long long> cached[kMaxDevices];  // 0 = not yet queried
+    static std::atomic<long long> cached[kDeviceSlots];  // 0 = not yet queried
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
-    if (dev < kMaxDevices) {
+    if (dev < kDeviceSlots) {
         const long long c = cached[dev].load(std::memory_order_relaxed);
         if (c > 0) return c;
     }
@@ -594,20 +593,19 @@ long long emit_slots() {
         return 0;
     const long long n = (long long)std::min(n32, n64) * kEmitWarps * sm_count();
     if (n <= 0) return 0;
-    if (dev < kMaxDevices) cached[dev].store(n, std::memory_order_relaxed);
+    if (dev < kDeviceSlots) cached[dev].store(n, std::memory_order_relaxed);
     return n;
 }
 
 cudaError_t set_emit_attributes() {
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
+    static std::atomic<int> done[kDeviceSlots];
+    return once_per_device(done, [] {
         const int smem = kEmitWarps * kWarpSmem;
-        err = cudaFuncSetAttribute(sat_band_emit<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t err = cudaFuncSetAttribute(sat_band_emit<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (err == cudaSuccess)
             err = cudaFuncSetAttribute(sat_band_emit<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        return err;
     });
-    return err;
 }
 
 }  // namespace
