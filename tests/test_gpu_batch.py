@@ -212,3 +212,52 @@ def test_batch_config4_full_size_sampled(sncc):
                     assert abs(matches[q][(uu, r)] - e) <= TOL
                 positives += len(want)
     assert checked > 400000 and positives >= 32
+
+
+def test_batch_on_wrapping_sources_equals_single_matches_on_int64_tables(sncc):
+    """Two bright textured 4096 x 2800 sources (values 150 to 255: sums past
+    2^31, so the batch's 32-bit tables wrap) and two templates cropped from
+    the first (128 x 96 and 200 x 150, std threshold 5: 202 and 814
+    segments): every pair's
+    candidate set and exact match list equal those of the single-template
+    path on 64-bit tables (the same integer numerators and window sums)."""
+    M, N = 4096, 2800
+    base = synth.case_texture(M=M, N=N, W=200, H=150)
+    srcs = [(150 + base.f.astype(np.int64) * 105 // 255).astype(np.uint8)]
+    srcs.append(np.ascontiguousarray(srcs[0][::-1, ::-1]))
+    assert int(srcs[0].astype(np.int64).sum()) >= 2 ** 31
+    u0, v0 = base.origin
+    tl = [np.ascontiguousarray(srcs[0][v0:v0 + 96, u0:u0 + 128]), np.ascontiguousarray(srcs[0][v0:v0 + 150, u0:u0 + 200])]
+    sig, p = 5.0, 0.95
+    b = sncc.Batch(tl, [sig, sig], M, N, 2, precision=p, cand_cap=1 << 23, out_cap=1 << 20)
+    fd = [torch.as_tensor(f).cuda() for f in srcs]
+    b.run(fd)
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == 0
+    pair, idx = b.candidates()
+    mp, mu, mv, mrho = b.matches()
+    nt = len(tl)
+    total = 0
+    for s, f in enumerate(fd):
+        tb = sncc.integral(f, s_bits=64)
+        for ti, t in enumerate(tl):
+            seg = sncc.build_segments(t, sig)
+            plan = sncc.upload_plan(seg)
+            H, W = t.shape
+            mb = sncc.alloc_match(M, N, W, H, 1 << 23)
+            sncc.match(seg, plan, tb, p * seg.rho_max, mb)
+            rb = sncc.alloc_refine(M, N, W, H, 1 << 20)
+            sncc.refine(f, torch.as_tensor(t).cuda(), seg, mb, p, rb)
+            torch.cuda.synchronize()
+            q = s * nt + ti
+            want = np.sort(mb.cand[:int(mb.count.item())].cpu().numpy())
+            got = np.sort(idx[pair == q])
+            np.testing.assert_array_equal(got, want)
+            u, v, rho = sncc.matches_to_numpy(rb)
+            sel = mp == q
+            np.testing.assert_array_equal(mu[sel], u)
+            np.testing.assert_array_equal(mv[sel], v)
+            np.testing.assert_array_equal(mrho[sel], rho)
+            assert int(mb.status.item()) == 0
+            total += len(want)
+    assert total > 0 and len(mu) > 0
