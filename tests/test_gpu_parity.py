@@ -255,7 +255,8 @@ def test_wrapped_tables_sparse_template(sncc):
     Its rho map equals the direct read of 64-bit tables exactly (the same
     integer numerator either way), on a bright 4096 x 3000 source (values 150
     to 255, sums past 2^31) holding the template, three boxes on a flat
-    background, at one offset."""
+    background, at one offset.  The exact comparator's map and the paper's
+    tile-by-tile fine stage are identical on both tables as well."""
     f = synth.random_image(23, 4096, 3000, lo=150)
     t = np.full((48, 48), 160, np.uint8)
     t[5:20, 8:30] = 230
@@ -265,20 +266,32 @@ def test_wrapped_tables_sparse_template(sncc):
     f[v0:v0 + 48, u0:u0 + 48] = t
     seg = sncc.build_segments(t, 10.0)
     assert seg.plan_info()["template_corners"] <= 64
+    fine = sncc.build_segments(t, 2.0)
     N, M = f.shape
-    plan = sncc.upload_plan(seg)
-    fd = dev(f)
-    maps = {}
+    plan, plan_fine = sncc.upload_plan(seg), sncc.upload_plan(fine)
+    fd, td = dev(f), dev(t)
+    maps, exact, lists = {}, {}, {}
     for bits in (32, 64):
         tb = sncc.integral(fd, s_bits=bits)
         mb = sncc.alloc_match(M, N, 48, 48, 1 << 16)
         sncc.match(seg, plan, tb, 0.9 * seg.rho_max, mb)
+        exact[bits] = sncc.exact_map(fd, td, seg.T, seg.T2, tb)  # window sums from the table
+        # the paper's fine stage on the tiles that hold the coarse candidates, from the same table
+        rb = sncc.alloc_refine(M, N, 48, 48, 1 << 16)
+        ws = sncc.tiles_workspace(M, N, 48, 48, 1 << 16)
+        sncc.refine_segmented_tiles(fine, plan_fine, tb, mb, 0.9 * fine.rho_max, rb, ws)
         torch.cuda.synchronize()
         assert int(mb.status.item()) == 0
         maps[bits] = mb.rho.clone()
+        lists[bits] = sncc.matches_to_numpy(rb)
     assert int(f.astype(np.int64).sum()) >= 2 ** 31
     assert torch.equal(maps[32], maps[64])
     assert abs(float(maps[32][v0, u0]) - seg.rho_max) <= TOL
+    assert torch.equal(exact[32], exact[64])
+    assert abs(float(exact[32][v0, u0]) - 1.0) <= TOL
+    for x, y in zip(lists[32], lists[64]):
+        np.testing.assert_array_equal(x, y)
+    assert (v0 * (M - 47) + u0) in (lists[32][1].astype(np.int64) * (M - 47) + lists[32][0]).tolist()
 
 
 # ------------------------------------------------------------------ coarse pass
