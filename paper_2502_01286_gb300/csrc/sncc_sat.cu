@@ -267,9 +267,12 @@ __global__ void __launch_bounds__(kColThreads) sat_band_colsum(const uint8_t* __
 // chunk j = blockIdx.x when it is whole (j < nj).  One CTA per 32 columns:
 // lane = column (coalesced rows), warp w of 32 owns a contiguous run of
 // bands; run totals are exchanged through shared memory, so every warp
-// walks only nb/32 bands, twice, eight bands' loads at a time.
+// walks only nb/32 bands: once, held in registers, where that is at most
+// kScanHold bands (4096 rows in bands of 20, 1080 in bands of 4), else twice,
+// kScanBatch bands' loads at a time.
 constexpr int kScanWarps = 32;
 constexpr int kScanBatch = 4;
+constexpr int kScanHold = 10;
 
 __global__ void __launch_bounds__(kScanWarps * 32) sat_band_scan(int M, int nb, int nj, int cp,
                                                                  int32_t* __restrict__ cs1,
@@ -283,6 +286,48 @@ __global__ void __launch_bounds__(kScanWarps * 32) sat_band_scan(int M, int nb, 
     const bool in = x < M;
     const int per = (nb + kScanWarps - 1) / kScanWarps;
     const int b0 = min(warp * per, nb), b1 = min(b0 + per, nb);
+    if (per <= kScanHold) {  // block-uniform: the warp's bands stay in registers
+        int32_t v1[kScanHold], v2[kScanHold];
+#pragma unroll
+        for (int i = 0; i < kScanHold; ++i) {
+            const bool ok = in && b0 + i < b1;
+            v1[i] = ok ? cs1[(size_t)(b0 + i) * cp + x] : 0;
+            v2[i] = ok ? cs2[(size_t)(b0 + i) * cp + x] : 0;
+        }
+        int32_t t1 = 0, t2 = 0;
+#pragma unroll
+        for (int i = 0; i < kScanHold; ++i) {
+            t1 += v1[i];
+            t2 += v2[i];
+        }
+        tot1[warp][lane] = t1;
+        tot2[warp][lane] = t2;
+        __syncthreads();
+        int32_t r1 = 0, r2 = 0;
+        for (int w = 0; w < warp; ++w) {
+            r1 += tot1[w][lane];
+            r2 += tot2[w][lane];
+        }
+#pragma unroll
+        for (int i = 0; i < kScanHold; ++i) {
+            if (b0 + i >= b1) break;  // warp-uniform
+            const int32_t c1 = in ? r1 : 0, c2 = in ? r2 : 0;
+            if (in) {
+                cs1[(size_t)(b0 + i) * cp + x] = r1;
+                cs2[(size_t)(b0 + i) * cp + x] = r2;
+            }
+            r1 += v1[i];
+            r2 += v2[i];
+            if ((int)blockIdx.x < nj) {  // block-uniform
+                const int64_t h1 = warp_sum_wide(c1), h2 = warp_sum_wide(c2);
+                if (lane == 0) {
+                    ch1[(size_t)(b0 + i) * nj + blockIdx.x] = h1;
+                    ch2[(size_t)(b0 + i) * nj + blockIdx.x] = h2;
+                }
+            }
+        }
+        return;
+    }
     int32_t s1 = 0, s2 = 0;
     for (int b = b0; b < b1; b += kScanBatch) {  // warp-uniform
         int32_t v1[kScanBatch], v2[kScanBatch];
