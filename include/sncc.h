@@ -17,6 +17,13 @@
  *   sncc_segments is host memory owned by the library (sncc_free_segments).
  *   Scratch space is passed in as a caller-owned workspace whose size the
  *   matching *_workspace_bytes call returns.
+ *   Alignment: every device array must be aligned to its element (4 bytes
+ *   for int32 and float, 8 for int64, double and the candidate pairs of the
+ *   batch calls, 16 for plans, rectangle lists and batch buffers); sum
+ *   tables read by the segment-sum and batch calls must start on 16 bytes
+ *   with a pitch that is a multiple of 4, as sncc_integral writes them.
+ *   Byte arrays (sources, templates) have no alignment rule.  A call given a
+ *   misaligned pointer returns SNCC_ERR_ARG before launching anything.
  *
  * Streams and errors
  *   Device entry points are asynchronous on the given stream (NULL = the
@@ -560,7 +567,7 @@ int sncc_batch_get_bucket(const sncc_batch* b, int bucket, sncc_batch_bucket* ou
  *
  *   d_buf                  uploaded batch image
  *   d_s[s], d_s2[s]        sum tables of source s (sncc_integral), all with
- *                          the same s_bits and sat_pitch
+ *                          the same s_bits and sat_pitch (a multiple of 4)
  *   d_cand, cand_cap       candidates as int32 pairs {pair, v*U+u}
  *                          (2*cand_cap int32), unordered
  *   d_count                exact candidate count (may exceed cand_cap:

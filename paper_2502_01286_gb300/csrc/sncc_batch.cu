@@ -583,8 +583,10 @@ int batch_match_run(const sncc_batch* b, const void* d_buf, const void* const* d
     using namespace sncc;
     if (!b || !d_buf || !d_s || !d_s2 || !d_count || !d_counter || !d_status || cand_cap < 0) return SNCC_ERR_ARG;
     if (cand_cap > 0 && !d_cand) return SNCC_ERR_ARG;
-    if ((s_bits != 32 && s_bits != 64) || sat_pitch < b->M + 1) return SNCC_ERR_ARG;
-    if (reinterpret_cast<uintptr_t>(d_buf) & 15) return SNCC_ERR_ARG;
+    if ((s_bits != 32 && s_bits != 64) || sat_pitch < b->M + 1 || (sat_pitch & 3)) return SNCC_ERR_ARG;
+    if (misaligned(d_buf, 16) || misaligned(d_cand, 8) || misaligned(d_count, 4) || misaligned(d_counter, 4) ||
+        misaligned(d_status, 4))
+        return SNCC_ERR_ARG;
     BatchArgs a;
     std::memset(&a, 0, sizeof(a));
     const char* base = static_cast<const char*>(d_buf);
@@ -596,7 +598,7 @@ int batch_match_run(const sncc_batch* b, const void* d_buf, const void* const* d
     a.items = reinterpret_cast<const int2*>(base + b->off_items);
     a.counter = d_counter;
     for (int s = 0; s < b->ns; ++s) {
-        if (!d_s[s] || !d_s2[s] || (reinterpret_cast<uintptr_t>(d_s[s]) & 15)) return SNCC_ERR_ARG;
+        if (!d_s[s] || !d_s2[s] || misaligned(d_s[s], 16) || misaligned(d_s2[s], 8)) return SNCC_ERR_ARG;
         a.s[s] = d_s[s];
         a.s2[s] = d_s2[s];
     }
@@ -724,6 +726,9 @@ extern "C" int sncc_batch_refine(const sncc_batch* b, const void* d_buf, const u
     if (!b || !d_buf || !d_f || !d_count || !d_nout || !d_status || f_stride < b->M || cand_cap < 0 || out_cap < 0)
         return SNCC_ERR_ARG;
     if ((cand_cap > 0 && !d_cand) || (out_cap > 0 && !d_out)) return SNCC_ERR_ARG;
+    if (misaligned(d_buf, 16) || misaligned(d_cand, 8) || misaligned(d_count, 4) || misaligned(d_out, 4) ||
+        misaligned(d_nout, 4) || misaligned(d_status, 4))
+        return SNCC_ERR_ARG;
     if (out_cap > 0 && (!d_ws || ws_bytes < sncc_batch_refine_workspace_bytes(b, out_cap) ||
                         (reinterpret_cast<uintptr_t>(d_ws) & 15)))
         return SNCC_ERR_WORKSPACE;

@@ -663,6 +663,9 @@ extern "C" int sncc_diff_forward(const float* d_f, int M, int N, int f_stride, c
     using namespace sncc;
     if (!d_f || !d_t || !d_rects || !d_k || !d_rho_k || !d_rho_t || !d_loss) return SNCC_ERR_ARG;
     if (!diff_args_ok(M, N, W, H, K, f_stride)) return SNCC_ERR_ARG;
+    if (misaligned(d_f, 4) || misaligned(d_t, 4) || misaligned(d_rects, 16) || misaligned(d_k, 4) ||
+        misaligned(d_rho_k, 4) || misaligned(d_rho_t, 4) || misaligned(d_loss, 8))
+        return SNCC_ERR_ARG;
     const DiffLayout L = diff_layout(M, N, W, H);
     if (!d_ws || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return SNCC_ERR_WORKSPACE;
     char* ws = static_cast<char*>(d_ws);
@@ -690,6 +693,9 @@ extern "C" int sncc_diff_backward(const float* d_f, int M, int N, int f_stride, 
     using namespace sncc;
     if (!d_f || !d_rects || !d_k || !d_rho_k || !d_rho_t || !d_dloss || !d_grad_f || !d_grad_k) return SNCC_ERR_ARG;
     if (!diff_args_ok(M, N, W, H, K, f_stride) || grad_f_stride < M) return SNCC_ERR_ARG;
+    if (misaligned(d_f, 4) || misaligned(d_rects, 16) || misaligned(d_k, 4) || misaligned(d_rho_k, 4) ||
+        misaligned(d_rho_t, 4) || misaligned(d_dloss, 8) || misaligned(d_grad_f, 4) || misaligned(d_grad_k, 4))
+        return SNCC_ERR_ARG;
     const DiffLayout L = diff_layout(M, N, W, H);
     if (!d_ws || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return SNCC_ERR_WORKSPACE;
     char* ws = static_cast<char*>(d_ws);

@@ -166,6 +166,7 @@ extern "C" int sncc_exact_map(const uint8_t* d_f, int M, int N, int f_stride, co
     using namespace sncc;
     if (!d_f || !d_t || !d_s || !d_s2 || !d_rho || W <= 0 || H <= 0 || M < W || N < H) return SNCC_ERR_ARG;
     if (f_stride < M || t_stride < W || (s_bits != 32 && s_bits != 64) || sat_pitch < M + 1) return SNCC_ERR_ARG;
+    if (misaligned(d_s, s_bits / 8) || misaligned(d_s2, 8) || misaligned(d_rho, 4)) return SNCC_ERR_ARG;
     const int U = M - W + 1, V = N - H + 1;
     if (rho_pitch < U) return SNCC_ERR_ARG;
     if ((int64_t)W * H > ((int64_t)1 << 23)) return SNCC_ERR_UNSUPPORTED;

@@ -34,6 +34,14 @@ cudaError_t once_per_device(std::atomic<int> (&done)[kDeviceSlots], F&& set) {
     return e;
 }
 
+// True when p is not a multiple of `bytes` (a power of two).  Entry points
+// reject such device pointers before any launch: the kernels load and store
+// them by their element type (4, 8 or 16 bytes), and a misaligned access is
+// a device fault, not an error code.
+inline bool misaligned(const void* p, size_t bytes) {
+    return (reinterpret_cast<uintptr_t>(p) & (bytes - 1)) != 0;
+}
+
 // An NVTX range around one ABI call (visible to profilers; a no-op otherwise).
 struct NvtxRange {
     explicit NvtxRange(const char* name) { nvtxRangePushA(name); }

@@ -401,7 +401,7 @@ int prepare_match(const sncc_segments* seg, const void* d_plan, const void* d_s,
     const int U = M - W + 1, V = N - H + 1;
     if (W <= 0 || H <= 0 || U <= 0 || V <= 0) return SNCC_ERR_ARG;
     if (sat_pitch < M + 1 || (sat_pitch & 3)) return SNCC_ERR_ARG;
-    if ((reinterpret_cast<uintptr_t>(d_plan) & 15) || (reinterpret_cast<uintptr_t>(d_s) & 15)) return SNCC_ERR_ARG;
+    if (misaligned(d_plan, 16) || misaligned(d_s, 16) || misaligned(d_s2, 8)) return SNCC_ERR_ARG;
     if ((int64_t)U * V >= ((int64_t)1 << 31)) return SNCC_ERR_UNSUPPORTED;
 
     const bool s64 = (s_bits == 64);
@@ -518,6 +518,8 @@ extern "C" int sncc_match(const sncc_segments* seg, const void* d_plan, const vo
     sncc::NvtxRange nvtx_range("sncc_match");
     using namespace sncc;
     if (!d_count || !d_status || cand_cap < 0 || (cand_cap > 0 && !d_cand)) return SNCC_ERR_ARG;
+    if (misaligned(d_rho, 4) || misaligned(d_cand, 4) || misaligned(d_count, 4) || misaligned(d_status, 4))
+        return SNCC_ERR_ARG;
     MatchArgs a;
     CUtensorMap map;
     int R = 0;
@@ -551,6 +553,9 @@ extern "C" int sncc_refine_segmented_tiles(const sncc_segments* seg, const void*
     using namespace sncc;
     if (!d_count || !d_nout || !d_status || cand_cap < 0 || out_cap < 0) return SNCC_ERR_ARG;
     if ((cand_cap > 0 && !d_cand) || (out_cap > 0 && !d_out)) return SNCC_ERR_ARG;
+    if (misaligned(d_cand, 4) || misaligned(d_count, 4) || misaligned(d_out, 4) || misaligned(d_nout, 4) ||
+        misaligned(d_status, 4))
+        return SNCC_ERR_ARG;
     MatchArgs a;
     CUtensorMap map;
     int R = 0;
@@ -595,8 +600,12 @@ extern "C" int sncc_match_multi(const sncc_segments* const* segs, const void* co
     using namespace sncc;
     if (!segs || !d_plans || !taus || !d_cand || !d_count || !d_status || n < 1 || n > SNCC_MULTI_MAX || cand_cap < 0)
         return SNCC_ERR_ARG;
-    for (int q = 0; q < n; ++q)  // every approximation has its own outputs
+    for (int q = 0; q < n; ++q) {  // every approximation has its own outputs
         if ((cand_cap > 0 && !d_cand[q]) || !d_count[q] || !d_status[q]) return SNCC_ERR_ARG;
+        if ((d_rho && misaligned(d_rho[q], 4)) || misaligned(d_cand[q], 4) || misaligned(d_count[q], 4) ||
+            misaligned(d_status[q], 4))
+            return SNCC_ERR_ARG;
+    }
     const int fz = multi_fusable(segs, d_plans, n);  // decided on the host before any CUDA call
     if (fz != SNCC_OK) return fz;
     MatchArgs a;

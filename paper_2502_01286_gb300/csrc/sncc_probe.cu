@@ -128,13 +128,14 @@ extern "C" int sncc_probe_hbm_write(void* d_buf, size_t bytes, sncc_stream_t str
 }
 
 extern "C" int sncc_probe_smem_read(int32_t* d_sink, int ctas, int iters, sncc_stream_t stream) {
-    if (!d_sink || ctas <= 0 || iters <= 0) return SNCC_ERR_ARG;
+    if (!d_sink || ctas <= 0 || iters <= 0 || sncc::misaligned(d_sink, 4)) return SNCC_ERR_ARG;
     sncc::probe_smem_read<<<ctas, 256, 0, (cudaStream_t)stream>>>(d_sink, iters);
     return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }
 
 extern "C" int sncc_probe_alu(int kind, int32_t* d_sink, int ctas, int iters, sncc_stream_t stream) {
-    if (!d_sink || ctas <= 0 || iters <= 0 || (kind != SNCC_PROBE_DP4A && kind != SNCC_PROBE_IMAD_WIDE))
+    if (!d_sink || ctas <= 0 || iters <= 0 || (kind != SNCC_PROBE_DP4A && kind != SNCC_PROBE_IMAD_WIDE) ||
+        sncc::misaligned(d_sink, 4))
         return SNCC_ERR_ARG;
     if (kind == SNCC_PROBE_DP4A)
         sncc::probe_dp4a<<<ctas, 256, 0, (cudaStream_t)stream>>>(d_sink, iters, 0x01020304u);
@@ -144,7 +145,7 @@ extern "C" int sncc_probe_alu(int kind, int32_t* d_sink, int ctas, int iters, sn
 }
 
 extern "C" int sncc_probe_wait_timeout(int32_t* d_status, sncc_stream_t stream) {
-    if (!d_status) return SNCC_ERR_ARG;
+    if (!d_status || sncc::misaligned(d_status, 4)) return SNCC_ERR_ARG;
     sncc::probe_wait_timeout<<<1, 32, 0, (cudaStream_t)stream>>>(d_status);
     return cudaGetLastError() == cudaSuccess ? SNCC_OK : SNCC_ERR_CUDA;
 }

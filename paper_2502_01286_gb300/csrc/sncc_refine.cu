@@ -129,6 +129,9 @@ extern "C" int sncc_refine(const uint8_t* d_f, int M, int N, int f_stride, const
     if (!d_f || !d_t || !d_count || !d_nout || !d_status || W <= 0 || H <= 0) return SNCC_ERR_ARG;
     if (f_stride < M || t_stride < W || M < W || N < H || cand_cap < 0 || out_cap < 0) return SNCC_ERR_ARG;
     if ((cand_cap > 0 && !d_cand) || (out_cap > 0 && !d_out)) return SNCC_ERR_ARG;
+    if (misaligned(d_cand, 4) || misaligned(d_count, 4) || misaligned(d_out, 4) || misaligned(d_nout, 4) ||
+        misaligned(d_status, 4))
+        return SNCC_ERR_ARG;
     if ((int64_t)W * H > ((int64_t)1 << 23)) return SNCC_ERR_UNSUPPORTED;
     if (out_cap > 0 && (!d_ws || ws_bytes < sncc_refine_workspace_bytes(M, N, W, H, out_cap) ||
                         (reinterpret_cast<uintptr_t>(d_ws) & 15)))

@@ -120,6 +120,9 @@ extern "C" int sncc_refine_segmented(const sncc_segments* seg, const void* d_pla
     const int W = seg->W, H = seg->H;
     const int U = M - W + 1, V = N - H + 1;
     if (U <= 0 || V <= 0 || sat_pitch < M + 1) return SNCC_ERR_ARG;
+    if (misaligned(d_s, s_bits / 8) || misaligned(d_s2, 8) || misaligned(d_cand, 4) || misaligned(d_count, 4) ||
+        misaligned(d_out, 4) || misaligned(d_nout, 4) || misaligned(d_status, 4))
+        return SNCC_ERR_ARG;
     // the per-candidate walk reads table entries themselves: a 32-bit table
     // must hold them exactly
     if (s_bits == 32 && (int64_t)255 * M * N >= ((int64_t)1 << 31)) return SNCC_ERR_DTYPE;

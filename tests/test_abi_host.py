@@ -250,6 +250,68 @@ def test_host_argument_errors(sncc):
                                 ptrs, 16, ptrs, nulls, None) == sncc.ERR_ARG
 
 
+def test_misaligned_device_pointers_are_rejected(sncc):
+    """Every call loads and stores its device arrays by their element type; a
+    pointer off that alignment, or a batch table pitch that is not a multiple
+    of 4, is an argument error found on the host instead of a device fault.
+    Address 256 stands for an aligned pointer; 258, 260 and 264 are off by 2,
+    4 and 8 bytes."""
+    lib = sncc.lib()
+    seg = sncc.build_segments(synth.case_plain().t, 10.0)  # 32 x 32 template
+    ok, a2, a4, a8 = (C.c_void_p(x) for x in (256, 258, 260, 264))
+    # segment sum: tables 16 (s) and 8 (s2) bytes, outputs 4
+    match = lambda s_, s2_, cnt, st: lib.sncc_match(seg.ref(), ok, s_, 32, s2_, 96, 64, 64, 0.5, None, 0, ok, 16,
+                                                    cnt, st, None)
+    assert match(ok, a4, ok, ok) == sncc.ERR_ARG
+    assert match(a8, ok, ok, ok) == sncc.ERR_ARG
+    assert match(ok, ok, a2, ok) == sncc.ERR_ARG
+    assert match(ok, ok, ok, a2) == sncc.ERR_ARG
+    # the per-candidate fine stage and the exact map read whole entries
+    assert lib.sncc_refine_segmented(seg.ref(), ok, ok, 32, a4, 96, 64, 64, ok, ok, 16, 0.5, ok, 16, ok, ok,
+                                     1 << 20, ok, None) == sncc.ERR_ARG
+    assert lib.sncc_refine_segmented(seg.ref(), ok, a4, 64, ok, 96, 64, 64, ok, ok, 16, 0.5, ok, 16, ok, ok,
+                                     1 << 20, ok, None) == sncc.ERR_ARG
+    exact = lambda s_, bits, s2_, rho: lib.sncc_exact_map(ok, 64, 64, 64, ok, 8, 8, 8, 64 * 7, 64 * 49, s_, bits,
+                                                          s2_, 96, rho, 57, None)
+    assert exact(ok, 32, ok, ok) == sncc.ERR_UNIFORM  # aligned: reaches the template check
+    assert exact(ok, 32, a4, ok) == sncc.ERR_ARG
+    assert exact(a4, 64, ok, ok) == sncc.ERR_ARG
+    assert exact(ok, 32, ok, a2) == sncc.ERR_ARG
+    # exact refine: candidate, count and match arrays
+    refine = lambda cand, cnt, out: lib.sncc_refine(ok, 64, 64, 64, ok, 8, 8, 8, 64 * 7, 64 * 49, cand, cnt, 16,
+                                                    0.5, out, 16, ok, ok, 1 << 20, ok, None)
+    assert refine(a2, ok, ok) == sncc.ERR_ARG
+    assert refine(ok, a2, ok) == sncc.ERR_ARG
+    assert refine(ok, ok, a2) == sncc.ERR_ARG
+    # differentiation: float arrays 4 bytes, the int4 rectangle list 16
+    diff = lambda f_, rects: lib.sncc_diff_forward(f_, 64, 64, 64, ok, 8, 8, rects, ok, 4, ok, ok, ok, ok,
+                                                   1 << 20, None)
+    assert diff(a2, ok) == sncc.ERR_ARG
+    assert diff(ok, a8) == sncc.ERR_ARG
+    assert lib.sncc_probe_alu(sncc.PROBE_DP4A, a2, 1, 1, None) == sncc.ERR_ARG
+    # batch: the staged regions load two entries at once, so the pitch is a multiple of 4
+    srcs = synth.batch_sources(count=1, M=120, N=100)
+    tl = synth.batch_templates(srcs, count=2, lo=16, hi=40)
+    segs = [sncc.build_segments(t, sg) for t, _, sg in tl]
+    arr = (C.POINTER(sncc._Segments) * 2)(*[C.pointer(sg._s) for sg in segs])
+    ts = [np.ascontiguousarray(t) for t, _, _ in tl]
+    pix = (C.c_void_p * 2)(*[t.ctypes.data for t in ts])
+    strides = (C.c_int * 2)(*[t.shape[1] for t in ts])
+    taus = (C.c_float * 2)(0.5, 0.5)
+    h = C.c_void_p()
+    assert lib.sncc_batch_create(arr, pix, strides, taus, taus, 2, 1, 120, 100, C.byref(h)) == 0
+    try:
+        good = (C.c_void_p * 1)(256)
+        bad4 = (C.c_void_p * 1)(260)
+        bm = lambda s_, s2_, pitch, cand: lib.sncc_batch_match(h, ok, s_, s2_, 32, pitch, cand, 16, ok, ok, ok, None)
+        assert bm(good, good, 122, ok) == sncc.ERR_ARG  # >= M + 1 but not a multiple of 4
+        assert bm(good, bad4, 124, ok) == sncc.ERR_ARG
+        assert bm(bad4, good, 124, ok) == sncc.ERR_ARG
+        assert bm(good, good, 124, a4) == sncc.ERR_ARG  # candidate pairs are 8-byte records
+    finally:
+        lib.sncc_batch_destroy(h)
+
+
 def test_match_multi_fusability_decided_on_host(sncc):
     """sncc_match_multi declines (SNCC_ERR_UNSUPPORTED) a template of several
     blocks or one summed in place before any CUDA call, and rejects templates
