@@ -634,7 +634,8 @@ size_t sncc_diff_workspace_bytes(int M, int N, int W, int H);
  *   d_rho_k, d_rho_t     outputs, (N-H+1) x (M-W+1) float32 each
  *   d_loss               output, one double
  *   d_ws, ws_bytes       workspace (256-byte aligned)
- * Every window is assumed non-uniform.
+ * Every window is assumed non-uniform.  Offsets: (M-W+1)(N-H+1) < 2^31 and
+ * N-H+1 <= 65535, else SNCC_ERR_UNSUPPORTED (also for sncc_diff_backward).
  */
 int sncc_diff_forward(const float* d_f, int M, int N, int f_stride, const float* d_t, int W, int H,
                       const int32_t* d_rects, const float* d_k, int K, float* d_rho_k, float* d_rho_t,

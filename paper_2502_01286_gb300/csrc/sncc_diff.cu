@@ -648,6 +648,13 @@ bool diff_args_ok(int M, int N, int W, int H, int K, int f_stride) {
            K <= W * H && f_stride >= M;
 }
 
+// The offset maps are indexed in int (U V < 2^31) and the backward row-box
+// pass takes one grid row per offset row (V <= 65535).
+bool diff_size_ok(int M, int N, int W, int H) {
+    const int64_t U = M - W + 1, V = N - H + 1;
+    return U * V < ((int64_t)1 << 31) && V <= 65535;
+}
+
 }  // namespace
 }  // namespace sncc
 
@@ -663,6 +670,7 @@ extern "C" int sncc_diff_forward(const float* d_f, int M, int N, int f_stride, c
     using namespace sncc;
     if (!d_f || !d_t || !d_rects || !d_k || !d_rho_k || !d_rho_t || !d_loss) return SNCC_ERR_ARG;
     if (!diff_args_ok(M, N, W, H, K, f_stride)) return SNCC_ERR_ARG;
+    if (!diff_size_ok(M, N, W, H)) return SNCC_ERR_UNSUPPORTED;
     if (misaligned(d_f, 4) || misaligned(d_t, 4) || misaligned(d_rects, 16) || misaligned(d_k, 4) ||
         misaligned(d_rho_k, 4) || misaligned(d_rho_t, 4) || misaligned(d_loss, 8))
         return SNCC_ERR_ARG;
@@ -693,6 +701,7 @@ extern "C" int sncc_diff_backward(const float* d_f, int M, int N, int f_stride, 
     using namespace sncc;
     if (!d_f || !d_rects || !d_k || !d_rho_k || !d_rho_t || !d_dloss || !d_grad_f || !d_grad_k) return SNCC_ERR_ARG;
     if (!diff_args_ok(M, N, W, H, K, f_stride) || grad_f_stride < M) return SNCC_ERR_ARG;
+    if (!diff_size_ok(M, N, W, H)) return SNCC_ERR_UNSUPPORTED;
     if (misaligned(d_f, 4) || misaligned(d_rects, 16) || misaligned(d_k, 4) || misaligned(d_rho_k, 4) ||
         misaligned(d_rho_t, 4) || misaligned(d_dloss, 8) || misaligned(d_grad_f, 4) || misaligned(d_grad_k, 4))
         return SNCC_ERR_ARG;

@@ -288,6 +288,11 @@ def test_misaligned_device_pointers_are_rejected(sncc):
                                                    1 << 20, None)
     assert diff(a2, ok) == sncc.ERR_ARG
     assert diff(ok, a8) == sncc.ERR_ARG
+    # more offsets than the int-indexed maps hold, or offset rows than grid rows
+    assert lib.sncc_diff_forward(ok, 50000, 50000, 50000, ok, 8, 8, ok, ok, 4, ok, ok, ok, ok, 1 << 20,
+                                 None) == sncc.ERR_UNSUPPORTED
+    assert lib.sncc_diff_forward(ok, 16, 70000, 16, ok, 8, 8, ok, ok, 4, ok, ok, ok, ok, 1 << 20,
+                                 None) == sncc.ERR_UNSUPPORTED
     assert lib.sncc_probe_alu(sncc.PROBE_DP4A, a2, 1, 1, None) == sncc.ERR_ARG
     # batch: the staged regions load two entries at once, so the pitch is a multiple of 4
     srcs = synth.batch_sources(count=1, M=120, N=100)
