@@ -5,6 +5,8 @@ Bars: sum tables and segment tables bit-exact; NCC maps within 1e-5 absolute;
 candidate and match sets exact outside a +-1e-5 band around each threshold
 (inside the band the FP32 decision may legitimately go either way, and such
 offsets are counted); match values within 1e-5."""
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -105,6 +107,57 @@ def test_integral_int64_full_size(sncc):
         np.testing.assert_array_equal(tb.s[rows, :4097].cpu().numpy(), s[rows].astype(np.int64))
         np.testing.assert_array_equal(tb.s2[rows, :4097].cpu().numpy(), s2[rows].astype(np.int64))
     assert int(tb.s[-1, 4096]) == int(s[-1, -1])
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+def test_table_pitch_any_multiple_of_4(sncc, bits):
+    """Tables whose pitch is a multiple of 4 but not of 32 (304 for a
+    300-column source): the sums, the segment-sum maps of a one-block
+    template (TMA staging on a 32-bit table) and of a multi-block template
+    (register staging), the exact map, and the batch's candidates and matches
+    equal those of the default pitch bit for bit."""
+    M, N, P = 300, 260, 304
+    assert P % 4 == 0 and P % 32 != 0 and P >= M + 1 and sncc.sat_pitch(M) != P
+    one = synth.case_hd(M=M, N=N, W=48, H=40, seed=4)
+    multi = synth.case_plain(M=M, N=N, W=130, H=100, seed=3)
+    fd = dev(one.f)
+    ref = sncc.integral(fd, s_bits=bits)
+    dt = torch.int32 if bits == 32 else torch.int64
+    tb = sncc.Tables(torch.zeros((N + 1, P), dtype=dt, device="cuda"),
+                     torch.zeros((N + 1, P), dtype=torch.int64, device="cuda"), bits, P, M, N)
+    sncc.integral(fd, tb)
+    torch.cuda.synchronize()
+    assert torch.equal(tb.s[:, :M + 1], ref.s[:, :M + 1]) and torch.equal(tb.s2[:, :M + 1], ref.s2[:, :M + 1])
+    for t, sigma in ((one.t, 4.0), (multi.t, 6.0)):
+        seg = sncc.build_segments(t, sigma)
+        plan = sncc.upload_plan(seg)
+        out = []
+        for tables in (ref, tb):
+            mb = sncc.alloc_match(M, N, seg.W, seg.H, 1 << 16)
+            sncc.match(seg, plan, tables, 0.0, mb)
+            rho = sncc.exact_map(fd, dev(t), seg.T, seg.T2, tables)
+            torch.cuda.synchronize()
+            n = int(mb.count.item())
+            assert int(mb.status.item()) == 0 and n > 0
+            out.append((mb.rho.clone(), sorted(mb.cand[:n].tolist()), rho.clone()))
+        assert torch.equal(out[0][0], out[1][0]) and out[0][1] == out[1][1] and torch.equal(out[0][2], out[1][2])
+    # the batch's staged regions at the same pitch
+    tl = [(one.t, 4.0), (multi.t, 6.0)]
+    res = []
+    for pitch in (None, P):
+        b = sncc.Batch([t for t, _ in tl], [sg for _, sg in tl], M, N, 1, precision=0.7)
+        if pitch is not None:
+            b.tables = [sncc.Tables(torch.zeros((N + 1, P), dtype=b.tables[0].s.dtype, device="cuda"),
+                                    torch.zeros((N + 1, P), dtype=torch.int64, device="cuda"), b.s_bits, P, M, N)]
+            b._s = (C.c_void_p * 1)(b.tables[0].s.data_ptr())
+            b._s2 = (C.c_void_p * 1)(b.tables[0].s2.data_ptr())
+            b.pitch = P
+        b.run([fd])
+        torch.cuda.synchronize()
+        assert int(b.status.item()) == 0
+        pair, idx = b.candidates()
+        res.append((sorted(zip(pair.tolist(), idx.tolist())), [a.tolist() for a in b.matches()]))
+    assert res[0][1][0] and res[0] == res[1]
 
 
 def wrap32(a):
