@@ -450,13 +450,29 @@ def measure_ceilings(sncc, torch, stream, dev):
 
 
 IMAD_WIDE_PER_CLK_SM = 32  # 16-lane integer multiplier per SM sub-partition, two passes per 64-bit product
-SM_COUNT, SM_MAX_MHZ = 152, 2070  # SM count replaced by the device's own at the first measurement
+# GB300's figures, replaced by the device's own at the first measurement
+SM_COUNT, SM_MAX_MHZ = 152, 2070
+
+
+def device_max_sm_mhz(gpu_index: int):
+    """The maximum SM clock nvidia-smi reports for this GPU (None if it
+    cannot be read)."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        return int(float(out.stdout.strip().splitlines()[0]))
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        return None
 
 
 def set_sm_count(torch, dev):
-    """The SM count of the device the bench runs on (for the nominal peaks)."""
-    global SM_COUNT
+    """The SM count and maximum SM clock of the device the bench runs on
+    (for the nominal peaks)."""
+    global SM_COUNT, SM_MAX_MHZ
     SM_COUNT = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    mhz = device_max_sm_mhz(dev.index if dev.index is not None else 0)
+    if mhz:
+        SM_MAX_MHZ = mhz
 
 
 def match_tile_rows(U, V):
