@@ -383,6 +383,59 @@ def test_match_map_and_candidates(sncc, M, N, W, H, sigma):
     check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, tau, what="%dx%d t%dx%d sigma %g" % (M, N, W, H, sigma))
 
 
+def _random_cases(n=20, seed=20261203):
+    """Seeded random problems: the three source generators, templates of 2 to
+    159 pixels a side, sources up to 160 columns and 140 rows wider, std
+    thresholds from 0 (every pixel its own segment) to 12, both table widths."""
+    g = np.random.default_rng(seed)
+    cases = []
+    for i in range(n):
+        W, H = int(g.integers(2, 160)), int(g.integers(2, 160))
+        M, N = W + int(g.integers(0, 160)), H + int(g.integers(0, 140))
+        sigma = float(g.choice([0.0, 1.0, 3.0, 6.0, 12.0]))
+        p = float(g.choice([0.5, 0.7, 0.9]))
+        cases.append((i, ("plain", "texture", "hd")[i % 3], M, N, W, H, sigma, (32, 64)[(i // 3) % 2], p,
+                      int(g.integers(0, 1 << 30))))
+    return cases
+
+
+@pytest.mark.parametrize("i,kind,M,N,W,H,sigma,bits,p,seed", _random_cases())
+def test_random_problems_whole_path(sncc, i, kind, M, N, W, H, sigma, bits, p, seed):
+    """The whole path on a random problem against the oracle: the segment
+    table bit for bit, the map within 1e-5, the candidate set by the band
+    rule, and the exact refine's sorted matches (values within 1e-5, the set
+    equal outside the two threshold bands)."""
+    c = getattr(synth, "case_" + kind)(M=M, N=N, W=W, H=H, seed=seed)
+    seg = sncc.build_segments(c.t, sigma)
+    if not seg.Ek > 0:
+        pytest.skip("uniform approximation")
+    ap = O.precompute_template_approximation(c.t, sigma)
+    np.testing.assert_array_equal(seg.table, ap.segments)
+    tau_c = p * ap.rho_max
+    U, V = M - W + 1, N - H + 1
+    seg, fd, tb, mb = run_match(sncc, c.f, c.t, sigma, tau_c, cand_cap=U * V, s_bits=bits)
+    ref = O.segmented_ncc_map(c.f, ap, "sat")
+    assert np.abs(mb.rho.cpu().numpy() - ref).max() <= TOL
+    assert int(mb.status.item()) == 0
+    cnt = int(mb.count.item())
+    check_candidates(ref, mb.cand[:cnt].cpu().numpy(), cnt, tau_c,
+                     what="random %d: %s %dx%d t%dx%d sigma %g" % (i, kind, M, N, W, H, sigma))
+    rb = sncc.alloc_refine(M, N, W, H, U * V)
+    sncc.refine(fd, dev(c.t), seg, mb, p, rb)
+    torch.cuda.synchronize()
+    assert int(mb.status.item()) == 0
+    u, v, rho = sncc.matches_to_numpy(rb)
+    key = v.astype(np.int64) * U + u
+    assert np.all(np.diff(key) > 0)
+    assert np.abs(rho - O.ncc_exact_at(c.f, c.t, u, v)).max(initial=0) <= TOL
+    idx_o, _ = O.refine(c.f, c.t, O.candidates(ref, tau_c), U, p)
+    diff = np.setxor1d(key, idx_o)
+    if diff.size:
+        ex = O.ncc_exact_at(c.f, c.t, (diff % U).astype(np.int32), (diff // U).astype(np.int32))
+        amb = (np.abs(ref.ravel()[diff] - tau_c) < TOL) | (np.abs(ex - p) < TOL)
+        assert np.all(amb), diff[~amb][:10]
+
+
 @pytest.mark.parametrize("M,N,W,H", [(200, 150, 48, 40), (300, 260, 130, 129), (420, 150, 97, 65)])
 @pytest.mark.parametrize("bits", [32, 64])
 def test_match_table_width_independent(sncc, bits, M, N, W, H):
