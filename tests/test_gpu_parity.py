@@ -166,6 +166,41 @@ def wrap32(a):
     return (np.asarray(a).astype(np.int64) & 0xFFFFFFFF).astype(np.uint32).view(np.int32)
 
 
+def _random_sat_shapes(n=24, seed=2026120301):
+    """Seeded random sources for the sum tables: general, tall and narrow,
+    wide and short, and medium shapes (every band height, tile count and
+    ragged edge the launch geometry picks), each a column window of a wider
+    image at a random (often odd) offset."""
+    g = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        kind = i % 4
+        if kind == 0:
+            M, N = int(g.integers(1, 5000)), int(g.integers(1, 3000))
+        elif kind == 1:
+            M, N = int(g.integers(1, 300)), int(g.integers(3000, 24000))
+        elif kind == 2:
+            M, N = int(g.integers(3000, 16384)), int(g.integers(1, 200))
+        else:
+            M, N = int(g.integers(200, 2500)), int(g.integers(200, 2500))
+        pad = int(g.integers(0, 40))
+        out.append((i, M, N, pad, int(g.integers(0, pad + 1)), (32, 64)[i % 2], int(g.integers(0, 1 << 30))))
+    return out
+
+
+@pytest.mark.parametrize("i,M,N,pad,x0,bits,seed", _random_sat_shapes())
+def test_integral_random_shapes(sncc, i, M, N, pad, x0, bits, seed):
+    """Both tables of a random source against the oracle's, bit for bit (the
+    32-bit s modulo 2^32)."""
+    big = synth.random_image_u8(seed, M + pad, N)
+    tb = sncc.integral(dev(big)[:, x0:x0 + M], s_bits=bits)
+    torch.cuda.synchronize()
+    s, s2 = O.sum_tables(np.ascontiguousarray(big[:, x0:x0 + M]))
+    want = s.astype(np.int64) if bits == 64 else wrap32(s).astype(np.int64)
+    np.testing.assert_array_equal(tb.s[:, :M + 1].cpu().numpy().astype(np.int64), want)
+    np.testing.assert_array_equal(tb.s2[:, :M + 1].cpu().numpy(), s2.astype(np.int64))
+
+
 def test_integral_int32_wraps_modulo_2_32(sncc):
     """A 32-bit s on a source whose sums pass 2^32 (8192 x 3000, values 200
     to 255): sampled rows hold the exact sums modulo 2^32, and window sums
