@@ -261,3 +261,57 @@ def test_batch_on_wrapping_sources_equals_single_matches_on_int64_tables(sncc):
             assert int(mb.status.item()) == 0
             total += len(want)
     assert total > 0 and len(mu) > 0
+
+
+def _random_batches(n=3, seed=2026120302):
+    """Seeded random batches: source size, source and template counts,
+    template sides from 8 up to the source, precision, and one variant (tile
+    height, template block edge) per bucket."""
+    g = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        M, N = int(g.integers(150, 420)), int(g.integers(150, 420))
+        out.append((i, M, N, int(g.integers(1, 4)), int(g.integers(4, 8)), min(M, N, 256) - 1,
+                    float(g.choice([0.6, 0.75, 0.9])), int(g.integers(0, 1 << 30)),
+                    [(int(g.choice([8, 4, 2])), int(g.choice([64, 32]))) for _ in range(16)]))
+    return out
+
+
+@pytest.mark.parametrize("i,M,N,ns,nt,hi,p,seed,variants", _random_batches())
+def test_batch_random_problems_vs_oracle(sncc, i, M, N, ns, nt, hi, p, seed, variants):
+    """A random batch in mixed per-bucket variants: every pair's candidates by
+    the band rule against the oracle's map, and the exact matches (sorted,
+    values within 1e-5, every oracle match outside the bands present)."""
+    srcs = synth.batch_sources(count=ns, M=M, N=N, seed=seed)
+    tl = synth.batch_templates(srcs, count=nt, seed=seed + 1, lo=8, hi=hi)
+    ref = [O.precompute_template_approximation(t, sg) for t, _, sg in tl]
+    b = sncc.Batch([t for t, _, _ in tl], [sg for _, _, sg in tl], M, N, ns, precision=p)
+    for k in range(sncc.BATCH_BUCKETS):
+        b.set_bucket_variant(k, *variants[k % len(variants)])
+    b.run([torch.as_tensor(f).cuda() for f in srcs])
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == 0
+    pair, idx = b.candidates()
+    got = set(zip(pair.tolist(), idx.tolist()))
+    assert len(got) == len(pair)
+    mp, mu, mv, mrho = b.matches()
+    keys = [(int(q), int(vv) * (M - tl[int(q) % nt][0].shape[1] + 1) + int(uu)) for q, uu, vv in zip(mp, mu, mv)]
+    assert keys == sorted(keys)
+    for s in range(ns):
+        for ti, ap in enumerate(ref):
+            W = tl[ti][0].shape[1]
+            U = M - W + 1
+            rho = O.segmented_ncc_map(srcs[s], ap, "sat")
+            flat = rho.ravel()
+            tau = p * ap.rho_max
+            pid = s * nt + ti
+            mine = {j for (q, j) in got if q == pid}
+            assert set(np.flatnonzero(flat >= tau + TOL).tolist()) <= mine, pid
+            assert not (mine & set(np.flatnonzero(flat < tau - TOL).tolist())), pid
+            sel = mp == pid
+            u, v, r = mu[sel], mv[sel], mrho[sel]
+            if u.size:
+                ex = O.ncc_exact_at(srcs[s], tl[ti][0], u.astype(np.int32), v.astype(np.int32))
+                assert np.abs(ex - r).max() <= TOL and ex.min() >= p - TOL
+            idx_o, _ = O.refine(srcs[s], tl[ti][0], O.candidates(rho, tau + TOL), U, p + TOL)
+            assert set(idx_o.tolist()) <= set((v.astype(np.int64) * U + u).tolist()), pid
