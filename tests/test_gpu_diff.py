@@ -179,3 +179,44 @@ def test_diff_multi_block_template_vs_oracle(sncc):
         fm[py, px] -= h
         num = (D.forward(fp, t64, rects, k64)["loss"] - D.forward(fm, t64, rects, k64)["loss"]) / (2 * h)
         assert abs(gf[py, px] - num) <= 1e-4 * np.abs(ref["df"]).max(), (py, px, gf[py, px], num)
+
+
+def _random_diff_problems(n=4, seed=2026120303):
+    """Seeded random problems: templates of 4 to 130 pixels a side (one block
+    or several 64 x 64 blocks), sources 8 to 120 columns and rows larger, std
+    thresholds 6 to 16."""
+    g = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        W, H = int(g.integers(4, 131)), int(g.integers(4, 131))
+        M, N = W + int(g.integers(8, 120)), H + int(g.integers(8, 100))
+        out.append((i, M, N, W, H, float(g.choice([6.0, 9.0, 12.0, 16.0])), int(g.integers(0, 1 << 30))))
+    return out
+
+
+@pytest.mark.parametrize("i,M,N,W,H,sigma,seed", _random_diff_problems())
+def test_diff_random_problems_vs_oracle(sncc, i, M, N, W, H, sigma, seed):
+    """Both maps and the loss within 1e-5, both gradients within 1e-4
+    relative of the FP64 oracle's analytic ones."""
+    f, t, org, _ = synth.case_diff(M=M, N=N, W=W, H=H, seed=seed)
+    seg = sncc.build_segments(np.rint(np.clip(t, 0, 255)).astype(np.uint8), sigma)
+    rects = seg.table
+    k0 = np.array([t[y:y + h, x:x + w].mean() for x, y, w, h in rects], np.float64)
+    k0 = k0 + np.random.default_rng(seed).normal(0.0, 1.5, size=len(k0))
+    k32 = k0.astype(np.float32)
+    pb = sncc.DiffProblem(t, rects, M, N)
+    fd = torch.as_tensor(f).cuda().requires_grad_(True)
+    kd = torch.as_tensor(k32).cuda().requires_grad_(True)
+    rho_k, rho_t, loss0 = sncc._diff_forward(pb, fd.detach(), kd.detach())
+    loss = pb.loss(fd, kd)
+    loss.backward()
+    torch.cuda.synchronize()
+    f64, t64, k64 = f.astype(np.float64), t.astype(np.float64), k32.astype(np.float64)
+    fw = D.forward(f64, t64, rects, k64)
+    ref = D.gradients(f64, t64, rects, k64)
+    assert np.abs(rho_k.cpu().numpy() - fw["rho_k"]).max() <= 1e-5
+    assert np.abs(rho_t.cpu().numpy() - fw["rho_t"]).max() <= 1e-5
+    assert abs(float(loss0.item()) - fw["loss"]) <= 1e-5 * fw["loss"]
+    assert abs(float(loss.item()) - fw["loss"]) <= 1e-5 * fw["loss"]
+    assert rel(kd.grad.cpu().numpy(), ref["dk"]) <= 1e-4
+    assert rel(fd.grad.cpu().numpy(), ref["df"]) <= 1e-4
