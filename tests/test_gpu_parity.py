@@ -995,6 +995,46 @@ def test_paper_two_stage_matches_oracle(sncc, M, N, W, H, p, seed):
     assert len(r["idx"]) > 0
 
 
+def _random_paper_problems(n=6, seed=2026120304):
+    """Seeded random problems for the paper's own search: the three source
+    generators, templates of 8 to 150 pixels a side, precision 0.3 to 0.9."""
+    g = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        W, H = int(g.integers(8, 151)), int(g.integers(8, 151))
+        M, N = W + int(g.integers(20, 200)), H + int(g.integers(20, 160))
+        out.append((i, ("plain", "texture", "hd")[i % 3], M, N, W, H, float(g.choice([0.3, 0.5, 0.7, 0.9])),
+                    int(g.integers(0, 1 << 30))))
+    return out
+
+
+@pytest.mark.parametrize("i,kind,M,N,W,H,p,seed", _random_paper_problems())
+def test_paper_two_stage_random_problems(sncc, i, kind, M, N, W, H, p, seed):
+    """The paper's two-approximation search on random problems against the
+    oracle's main algorithm: both segment tables bit for bit, the k_fast map
+    within 1e-5, the k_slow values of the matches within 1e-5, and the match
+    set equal outside the two threshold bands."""
+    c = getattr(synth, "case_" + kind)(M=M, N=N, W=W, H=H, seed=seed)
+    r = O.main_algorithm(c.f, c.t, precision=p)
+    m = sncc.PaperMatcher(c.t, M, N, precision=p)
+    np.testing.assert_array_equal(m.fast.table, r["fast"].segments)
+    np.testing.assert_array_equal(m.slow.table, r["slow"].segments)
+    m.run(dev(c.f))
+    torch.cuda.synchronize()
+    assert m.status() == 0
+    assert np.abs(m.mb.rho.cpu().numpy() - r["rho_fast"]).max() <= TOL
+    u, v, rho = sncc.matches_to_numpy(m.rb)
+    U = M - W + 1
+    key = v.astype(np.int64) * U + u
+    assert np.all(np.diff(key) > 0)
+    full_s = O.segmented_ncc_map(c.f, r["slow"], "sat")
+    if u.size:
+        assert np.abs(rho - full_s[v, u]).max() <= TOL
+    amb = (np.abs(r["rho_fast"].ravel() - r["thr_fast"]) < TOL) | (np.abs(full_s.ravel() - r["thr_slow"]) < TOL)
+    diff = set(key.tolist()) ^ set(r["idx"].tolist())
+    assert all(amb[d] for d in diff), sorted(diff)[:10]
+
+
 @pytest.mark.parametrize("M,N,W,H,p,seed,bits", [(300, 220, 64, 48, 0.6, 5, 32), (260, 200, 100, 70, 0.5, 9, 64),
                                                  (256, 256, 32, 32, 0.3, 0, 32)])
 def test_fine_stage_per_candidate_and_tiled_agree(sncc, M, N, W, H, p, seed, bits):
