@@ -312,6 +312,12 @@ def run_reference(args, world, rank, pg):
     print(json.dumps(line), flush=True)
 
 
+def diff_config(seg):
+    """The differentiation workload as both arms describe it."""
+    return {"workload": "diff-512x512f32-t48x48-sigma12", "segments": int(seg.K),
+            "l2": "flushed between steps (256 MiB write)"}
+
+
 def run_reference_diff(args):
     """The oracle's FP64 loss and analytic gradients (oracle/diff.py) on a
     128 x 128 crop of the differentiation source with the same template."""
@@ -333,7 +339,7 @@ def run_reference_diff(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "diff-512x512f32-t48x48-sigma12"},
+            "config": diff_config(seg),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "loss + analytic gradients on a 128 x 128 crop (81 x 81 offsets) per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -359,7 +365,7 @@ def run_reference_batch(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batch-8x1024x1024-64templates-16to256-sigma4to25"},
+            "config": batch_config(srcs, tl),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": "up to %d random offset rows of each of 8 random pairs per step" % rows},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -936,6 +942,15 @@ def run_gpu(args, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def batch_config(srcs, tl):
+    """The batch workload as both arms describe it (the same dict in each)."""
+    N, M = srcs[0].shape
+    offsets = len(srcs) * sum((M - t.shape[1] + 1) * (N - t.shape[0] + 1) for t, _, _ in tl)
+    return {"workload": "batch-8x1024x1024-64templates-16to256-sigma4to25", "sources": [len(srcs), M, N],
+            "templates": len(tl), "pairs": len(srcs) * len(tl), "offsets_per_step": offsets,
+            "precision": PRECISION, "l2": "flushed between steps (256 MiB write)"}
+
+
 def batch_problem(rank: int = 0):
     """8 sources of 1024 x 1024 (blobs + 1/f noise) and 64 templates with
     sides U{16..256} and std thresholds U(4, 25): all 512 pairs."""
@@ -1095,11 +1110,8 @@ def run_gpu_batch(args, world, rank, local, pg):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "batch-8x1024x1024-64templates-16to256-sigma4to25", "sources": [len(srcs), M, N],
-                   "templates": len(tl), "pairs": len(srcs) * len(tl), "offsets_per_step": info["offsets"],
-                   "precision": PRECISION, "l2": "flushed between steps (256 MiB write)",
-                   "launch": "one CUDA graph: sum tables x8, one persistent coarse launch per variant in use, "
-                             "refine, sort",
+        "config": batch_config(srcs, tl),
+        "launch": {"graph": "sum tables x8, one persistent coarse launch per variant in use, refine, sort",
                    "buckets": buckets, "autotune_s": tune_s,
                    "autotune": "per template bucket (size class x corner density class), the fastest of tile "
                                "height R in {8, 4, 2} x template block edge {64, 32}, each bucket timed alone"},
@@ -1378,11 +1390,9 @@ def run_gpu_diff(args, world, rank, local, pg):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "diff-512x512f32-t48x48-sigma12", "segments": int(seg.K),
-                       "l2": "flushed between steps (256 MiB write)",
-                       "step": "loss forward + backward w.r.t. segment values and source (kernel launches: "
-                               "forward 2: prep, forward; backward 6: coefficients, row sums, dL/df, Gt, "
-                               "Gt reduce, dL/dk)"},
+            "config": diff_config(seg),
+            "step": "loss forward + backward w.r.t. segment values and source (kernel launches: forward 2: prep, "
+                    "forward; backward 6: coefficients, row sums, dL/df, Gt, Gt reduce, dL/dk)",
             "forward_call_ms": fwd_ms, "backward_call_ms": bwd_ms,
             "roofline": {"bound": "alu", "kernel": "sncc_diff_backward (diff_coeff, diff_rowbox, diff_grad_f, diff_gt, "
                                                     "diff_gt_reduce, diff_grad_k)",
