@@ -410,6 +410,36 @@ def test_batch_host_work_lists(sncc):
     assert lib.sncc_batch_create(arr1, pix1, st1, t1, t1, 1, 1, M, N, C.byref(h)) == sncc.ERR_UNIFORM
 
 
+def test_bench_batch_accounting_matches_the_library(sncc):
+    """The benchmark's batch config counts the offsets per step itself (both
+    arms print it); the count equals the library's own for the same batch."""
+    import importlib.util
+    import pathlib
+    path = pathlib.Path(__file__).resolve().parent.parent / "bench.py"
+    spec = importlib.util.spec_from_file_location("bench_for_test", path)
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    srcs = synth.batch_sources(count=3, M=150, N=120)
+    tl = synth.batch_templates(srcs, count=6, lo=16, hi=100)
+    segs = [sncc.build_segments(t, sg) for t, _, sg in tl]
+    arr = (C.POINTER(sncc._Segments) * len(tl))(*[C.pointer(sg._s) for sg in segs])
+    ts = [np.ascontiguousarray(t) for t, _, _ in tl]
+    pix = (C.c_void_p * len(tl))(*[t.ctypes.data for t in ts])
+    strides = (C.c_int * len(tl))(*[t.shape[1] for t in ts])
+    taus = (C.c_float * len(tl))(*([0.5] * len(tl)))
+    h = C.c_void_p()
+    lib = sncc.lib()
+    assert lib.sncc_batch_create(arr, pix, strides, taus, taus, len(tl), 3, 150, 120, C.byref(h)) == 0
+    try:
+        info = sncc.BatchInfo()
+        assert lib.sncc_batch_get_info(h, C.byref(info)) == 0
+        cfg = bench.batch_config(srcs, tl)
+        assert cfg["offsets_per_step"] == int(info.offsets)
+        assert cfg["sources"] == [3, 150, 120] and cfg["pairs"] == 18 == cfg["templates"] * 3
+    finally:
+        lib.sncc_batch_destroy(h)
+
+
 def test_noalloc_scratch_covers_every_source_up_to_1e8_pixels(sncc):
     """The allocation-free sum tables promise every source of up to 10^8
     pixels: the workspace sncc_integral asks for stays within the built-in
