@@ -27,10 +27,10 @@ namespace {
 constexpr int kDiffMax = 256;     // largest template edge
 constexpr int kDiffBlk = 64;      // template block edge the forward and dL/df kernels stage at a time
 constexpr int kFwXB = 4;          // forward: offset rows per thread (register window)
-constexpr int kFwG = 4;           // forward: template-column groups per CTA
-constexpr int kFwGT = 256 / kFwG;  // forward: threads per group (2 warps)
+constexpr int kFwG = 2;           // forward: template-column groups per CTA
+constexpr int kFwGT = 256 / kFwG;  // forward: threads per group (4 warps)
 constexpr int kFwTX = 32;         // forward: offset columns per CTA (lane = column)
-constexpr int kFwTY = (kFwGT / 32) * kFwXB;  // forward: offset rows per CTA (8)
+constexpr int kFwTY = (kFwGT / 32) * kFwXB;  // forward: offset rows per CTA (16)
 constexpr int kGtChunks = 192;    // offset-row chunks of the Gt correlation
 constexpr int kGtReduceLanes = 8;  // lanes summing the chunk partials of one Gt entry
 constexpr int kGtYB = 16;         // template rows per Gt CTA
@@ -138,8 +138,8 @@ __global__ void __launch_bounds__(256) diff_prep_kernel(const float* __restrict_
     }
 }
 
-// Forward pass over a 32 x 8 tile of offsets.  The CTA's 256 threads are
-// kFwG groups of 2 warps; within each template block group g takes the
+// Forward pass over a 32 x 16 tile of offsets.  The CTA's 256 threads are
+// kFwG groups of 4 warps; within each template block group g takes the
 // block's columns [g Wb / kFwG, (g+1) Wb / kFwG), and thread (warp w of the
 // group, lane l) the offsets u0 + l, rows v0 + 4w .. +3.  Along a template
 // column the thread keeps the 4 source values of its 4 offsets in a register
